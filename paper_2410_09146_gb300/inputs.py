@@ -1,0 +1,238 @@
+"""Seeded synthetic workloads for the GRMHD stage (shared by the tests, the bench and the CUDA path).
+
+This module holds grid set-ups and random initial data only; it contains none of the
+method's arithmetic (no metric, no prim->cons map, no flux, no con2prim). Random
+numbers come from numpy's PCG64 generator, whose stream is the same on every platform.
+
+Workloads (sizes and distributions follow the stage's standard test problems):
+  * ``linear_wave``  uniform Minkowski state plus a small-amplitude eigenmode along x (the
+    eigenvector is passed in by the caller), periodic, the setting of the paper's
+    linear-wave convergence tests (Sec. 4.1.1).
+  * ``kerr_schild_random``  Kerr-Schild (a = 0.9) cube [3, 23]^3 outside the horizon with
+    smooth seeded random fields: rho log-uniform in [1e-6, 1], P = 0.01 rho^(5/3),
+    flat-norm |W v| from a Lorentz factor log-uniform in [1, 10], and B the discrete
+    corner-to-cell curl of a node-centred vector potential whose amplitude follows a
+    magnetisation target log-uniform in [1e-2, 50] (so Toth's corner divergence of B is
+    zero up to roundoff). Ghost zones are filled from the same fields (fixed ghosts).
+  * ``c2p_states``  i.i.d. primitive states for the flat con2prim batch: rho, W, sigma
+    log-uniform over [1e-8, 1], [1, 50], [1e-4, 1e3], P = 0.01 rho^(5/3) 10^U(-1,1),
+    isotropic velocity and field directions.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Tuple
+
+import numpy as np
+
+GAMMA_DEFAULT = 5.0 / 3.0
+
+
+@dataclasses.dataclass
+class Setup:
+    """Grid and physics options of one meshblock (names follow the paper's notation)."""
+    n: Tuple[int, int, int]
+    ng: int = 4
+    x0: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    dx: Tuple[float, float, float] = (1.0, 1.0, 1.0)
+    metric: str = "minkowski"          # "minkowski" | "kerr_schild"
+    spin: float = 0.0
+    mass: float = 1.0
+    gamma_eos: float = GAMMA_DEFAULT
+    recon: str = "plm_mc"              # "constant" | "plm_minmod" | "plm_mc" | "weno5z_aoah"
+    riemann: str = "llf"               # "llf" | "hll"
+    bc: str = "periodic"               # "periodic" | "fixed"
+    rho_floor0: float = 1e-10
+    eps_floor0: float = 1e-8
+    floor_r_exp: float = 2.0
+    w_max: float = 100.0
+    c2p_tol: float = 1e-10
+    c2p_max_iter: int = 30
+    cfl: float = 0.4
+    weno_eps: float = 1e-26
+    precision: str = "fp64"            # "fp64" | "mixed"
+
+    @property
+    def ghosted(self):
+        return tuple(k + 2 * self.ng for k in self.n)
+
+    def prim_shape(self):
+        nx, ny, nz = self.n
+        g = 2 * self.ng
+        return (8, nz + g, ny + g, nx + g)
+
+    def cons_shape(self):
+        nx, ny, nz = self.n
+        return (8, nz, ny, nx)
+
+    def cell_centres(self, d: int, ghosts: bool = True):
+        n = self.n[d]
+        lo = -self.ng if ghosts else 0
+        hi = n + self.ng if ghosts else n
+        return self.x0[d] + (np.arange(lo, hi) + 0.5) * self.dx[d]
+
+
+# ----------------------------------------------------------------------------- set-ups
+def linear_wave_setup(n: int = 32, ny: int | None = None, nz: int | None = None, recon: str = "plm_mc",
+                      riemann: str = "llf") -> Setup:
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    return Setup(n=(n, ny, nz), x0=(0.0, 0.0, 0.0), dx=(1.0 / n, 1.0 / n, 1.0 / n), metric="minkowski",
+                 recon=recon, riemann=riemann, bc="periodic")
+
+
+def kerr_schild_setup(n: int = 128, recon: str = "plm_mc", riemann: str = "hll", precision: str = "fp64",
+                      lo: float = 3.0, hi: float = 23.0) -> Setup:
+    h = (hi - lo) / n
+    return Setup(n=(n, n, n), x0=(lo, lo, lo), dx=(h, h, h), metric="kerr_schild", spin=0.9, mass=1.0,
+                 recon=recon, riemann=riemann, bc="fixed", precision=precision)
+
+
+# ----------------------------------------------------------------------------- generators
+def linear_wave_prims(s: Setup, background, eigvec, amplitude: float = 1e-6) -> np.ndarray:
+    """Primitive array [8][nz+2g][ny+2g][nx+2g]: background + amplitude * eigvec * sin(2 pi x / L)."""
+    P = np.empty(s.prim_shape())
+    x = s.cell_centres(0)
+    L = s.n[0] * s.dx[0]
+    ph = np.sin(2.0 * math.pi * (x - s.x0[0]) / L)
+    for v in range(8):
+        P[v] = background[v] + amplitude * eigvec[v] * ph[None, None, :]
+    return P
+
+
+class _SmoothField:
+    """Sum of random Fourier modes on the unit cube, normalised to unit variance."""
+
+    def __init__(self, rng: np.random.Generator, nmodes: int = 8, kmax: int = 3):
+        ks = []
+        while len(ks) < nmodes:
+            k = rng.integers(-kmax, kmax + 1, size=3)
+            if np.any(k != 0):
+                ks.append(k)
+        self.k = np.array(ks, dtype=np.float64)
+        self.phi = rng.uniform(0.0, 2.0 * math.pi, size=nmodes)
+        self.amp = rng.normal(size=nmodes)
+        self.norm = 1.0 / math.sqrt(0.5 * float(np.sum(self.amp ** 2)))
+
+    def __call__(self, ux, uy, uz):
+        """Evaluate on the tensor grid ux (x) uy (x) uz of unit-cube coordinates -> [z][y][x]."""
+        out = np.zeros((len(uz), len(uy), len(ux)))
+        for m in range(len(self.amp)):
+            ex = np.exp(1j * (2.0 * math.pi * self.k[m, 0] * ux + self.phi[m]))
+            ey = np.exp(1j * (2.0 * math.pi * self.k[m, 1] * uy))
+            ez = np.exp(1j * (2.0 * math.pi * self.k[m, 2] * uz))
+            yz = ez[:, None] * ey[None, :]
+            out += self.amp[m] * np.imag(yz[:, :, None] * ex[None, None, :])
+        return out * self.norm
+
+
+def _to_uniform(g):
+    """Map an approximately standard-normal field to (0, 1) through the normal CDF."""
+    from scipy.special import erf
+    return np.clip(0.5 * (1.0 + erf(g / math.sqrt(2.0))), 0.0, 1.0)
+
+
+def kerr_schild_random_prims(s: Setup, seed: int = 1, rho_range=(1e-6, 1.0), w_range=(1.0, 10.0),
+                             sigma_range=(1e-2, 50.0), p_coef: float = 0.01, kmax: int = 3) -> np.ndarray:
+    """Smooth seeded random primitives over the ghosted block (see module docstring).
+
+    ``kmax`` bounds the integer wavenumbers of the Fourier modes (per unit cube); small grids
+    use kmax = 1 so that the fields stay resolved.
+    """
+    rng = np.random.default_rng(seed)
+    f_rho, f_w, f_sig = (_SmoothField(rng, kmax=kmax) for _ in range(3))
+    f_dir = [_SmoothField(rng, kmax=kmax) for _ in range(3)]
+    f_a = [_SmoothField(rng, kmax=kmax) for _ in range(3)]
+    nx, ny, nz = s.n
+    ng = s.ng
+    span = [s.n[d] * s.dx[d] for d in range(3)]
+
+    def unit(d, x):
+        return (x - s.x0[d]) / span[d]
+
+    xc = [unit(d, s.cell_centres(d)) for d in range(3)]
+    xn = [unit(d, s.x0[d] + np.arange(-ng, s.n[d] + ng + 1) * s.dx[d]) for d in range(3)]
+
+    def logu(field, lo, hi, grid):
+        u = _to_uniform(field(*grid))
+        return 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * u)
+
+    P = np.empty(s.prim_shape())
+    rho = logu(f_rho, *rho_range, xc)
+    W = logu(f_w, *w_range, xc)
+    P[0] = rho
+    P[4] = p_coef * rho ** (5.0 / 3.0) / (s.gamma_eos - 1.0)
+    dirs = np.stack([f(*xc) for f in f_dir])
+    dirs /= np.sqrt(np.sum(dirs ** 2, axis=0)) + 1e-300
+    P[1:4] = np.sqrt(W * W - 1.0) * dirs
+    del dirs
+
+    # Node-centred vector potential with amplitude W sqrt(sigma_target rho) evaluated at the nodes.
+    rho_n = logu(f_rho, *rho_range, xn)
+    W_n = logu(f_w, *w_range, xn)
+    sig_n = logu(f_sig, *sigma_range, xn)
+    amp = W_n * np.sqrt(sig_n * rho_n)
+    del rho_n, W_n, sig_n
+    A = [amp * f(*xn) for f in f_a]
+    del amp
+    B = _corner_curl(A, s.dx)
+    # One global scale so the median of |B|^2 / (rho W^2) matches the median target sigma.
+    proxy = np.sum(B ** 2, axis=0) / (rho * W * W)
+    target = math.sqrt(sigma_range[0] * sigma_range[1])
+    scale = math.sqrt(target / float(np.median(proxy)))
+    P[5:8] = B * scale
+    return P
+
+
+def _corner_curl(A, dx):
+    """Cell-centred curl of node-centred A: B_x = mu_x(D_y mu_z A_z - D_z mu_y A_y) and cyclic.
+
+    A[c] has shape [nz+1][ny+1][nx+1] over the cell corners; the result is [3][nz][ny][nx].
+    mu_d averages the two nodes along d; D_d differences them and divides by dx_d.
+    """
+    def mu(a, ax):
+        sl0 = [slice(None)] * 3; sl1 = [slice(None)] * 3
+        sl0[ax] = slice(0, -1); sl1[ax] = slice(1, None)
+        return 0.5 * (a[tuple(sl0)] + a[tuple(sl1)])
+
+    def D(a, ax, h):
+        sl0 = [slice(None)] * 3; sl1 = [slice(None)] * 3
+        sl0[ax] = slice(0, -1); sl1[ax] = slice(1, None)
+        return (a[tuple(sl1)] - a[tuple(sl0)]) / h
+
+    ax_of = {0: 2, 1: 1, 2: 0}  # array axis of the x, y, z direction ([z][y][x] order)
+    out = []
+    for c in range(3):
+        a, b = (c + 1) % 3, (c + 2) % 3
+        # B_c = mu_c (D_a mu_b A_b - D_b mu_a A_a)
+        t1 = D(mu(A[b], ax_of[b]), ax_of[a], dx[a])
+        t2 = D(mu(A[a], ax_of[a]), ax_of[b], dx[b])
+        out.append(mu(t1 - t2, ax_of[c]))
+    return np.stack(out)
+
+
+def c2p_states(n: int, seed: int = 4, gamma_eos: float = GAMMA_DEFAULT, rho_range=(1e-8, 1.0), w_range=(1.0, 50.0),
+               sigma_range=(1e-4, 1e3)) -> np.ndarray:
+    """i.i.d. primitive states [n][8] (rho, W v^i, rho eps, B^i) in flat space.
+
+    |B| is set from the magnetisation proxy sigma ~ B^2/(rho W^2); the caller maps them to
+    conserved states with its own prim->cons routine.
+    """
+    rng = np.random.default_rng(seed)
+
+    def logu(lo, hi):
+        return 10.0 ** rng.uniform(math.log10(lo), math.log10(hi), size=n)
+
+    rho = logu(*rho_range)
+    W = logu(*w_range)
+    sig = logu(*sigma_range)
+    press = 0.01 * rho ** (5.0 / 3.0) * 10.0 ** rng.uniform(-1.0, 1.0, size=n)
+    dv = rng.normal(size=(n, 3)); dv /= np.linalg.norm(dv, axis=1, keepdims=True)
+    db = rng.normal(size=(n, 3)); db /= np.linalg.norm(db, axis=1, keepdims=True)
+    P = np.empty((n, 8))
+    P[:, 0] = rho
+    P[:, 1:4] = np.sqrt(W * W - 1.0)[:, None] * dv
+    P[:, 4] = press / (gamma_eos - 1.0)
+    P[:, 5:8] = (W * np.sqrt(sig * rho))[:, None] * db
+    return P

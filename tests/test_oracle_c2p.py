@@ -1,0 +1,98 @@
+"""Pins of the oracle's con2prim (paper Sec. 3.1, the Kastaun et al. 2021 recovery) and floors (Sec. 3.2).
+
+The prim->cons map is pinned independently (test_oracle_fluid); con2prim is its inverse, so
+* on well-conditioned states (W <= 10, b^2/rho <= 10, p/rho >= 1e-4) prim -> cons -> prim
+  returns rho and W v to 1e-12 and rho eps to 1e-14 of the energy scale (tau + D), which is
+  the conditioning of that cancellation;
+* on the full sampled range the backward error |U(P') - U| / |U| stays at roundoff
+  (forward errors there are bounded by the conditioning, not by the solver);
+* B = 0, v = 0 has the closed form rho = D, rho eps = tau;
+* floors and the W ceiling fire exactly when their conditions hold; bad input is flagged.
+"""
+import numpy as np
+
+from paper_2410_09146_gb300 import inputs as I
+
+
+def _wellcond(n, seed):
+    rng = np.random.default_rng(seed)
+    P = np.zeros((n, 8))
+    P[:, 0] = 10 ** rng.uniform(-4, 0, n)
+    W = 10 ** rng.uniform(0, 1, n)
+    d = rng.normal(size=(n, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+    P[:, 1:4] = np.sqrt(W * W - 1)[:, None] * d
+    P[:, 4] = P[:, 0] * 10 ** rng.uniform(-4, 0, n) / (2.0 / 3.0)
+    sig = 10 ** rng.uniform(-3, 1, n)
+    db = rng.normal(size=(n, 3)); db /= np.linalg.norm(db, axis=1, keepdims=True)
+    P[:, 5:8] = np.sqrt(sig * P[:, 0])[:, None] * db
+    return P
+
+
+def test_roundtrip_wellconditioned_minkowski_and_ks(orc):
+    for setup, lo, hi in ((I.linear_wave_setup(8), 0.0, 1.0), (I.kerr_schild_setup(8), 3.0, 23.0)):
+        p = orc.params(setup)
+        n = 3000
+        P = _wellcond(n, 11)
+        x = np.random.default_rng(12).uniform(lo, hi, (n, 3))
+        U = orc.prim2con_points(p, x, P)["U"]
+        P2, st, it = orc.c2p_points(p, x, U, floors=False)
+        assert np.all(st == 0)
+        np.testing.assert_allclose(P2[:, 0], P[:, 0], rtol=1e-12)
+        # rho eps is recovered from tau + D by cancellation: its error scales with (tau + D), not u.
+        sg = orc.geom_points(p, x)["sqrtgam"]
+        escale = (U[:, 4] + U[:, 0]) / sg
+        assert np.max(np.abs(P2[:, 4] - P[:, 4]) / escale) < 1e-14
+        W = np.sqrt(1 + np.sum(P[:, 1:4] ** 2, 1))
+        np.testing.assert_allclose(P2[:, 1:4], P[:, 1:4], rtol=0, atol=1e-12 * W.max())
+        np.testing.assert_allclose(P2[:, 5:8], P[:, 5:8], rtol=4e-16)  # sqrt(gamma) round trip
+
+
+def test_backward_error_full_range(orc):
+    p = orc.params(I.linear_wave_setup(8))
+    P = I.c2p_states(5000, seed=3)
+    x = np.zeros((len(P), 3))
+    U = orc.prim2con_points(p, x, P)["U"]
+    P2, st, it = orc.c2p_points(p, x, U, floors=False)
+    assert np.all(st == 0)
+    U2 = orc.prim2con_points(p, x, P2)["U"]
+    scale = np.abs(U[:, 0]) + np.abs(U[:, 4]) + np.linalg.norm(U[:, 1:4], axis=1)
+    be = np.max(np.abs(U2 - U), axis=1) / scale
+    assert np.max(be) < 1e-11
+    assert np.median(be) < 1e-14
+
+
+def test_static_unmagnetised_closed_form(orc):
+    p = orc.params(I.linear_wave_setup(8))
+    rng = np.random.default_rng(5)
+    n = 100
+    U = np.zeros((n, 8))
+    U[:, 0] = 10 ** rng.uniform(-6, 0, n)
+    U[:, 4] = U[:, 0] * 10 ** rng.uniform(-6, 2, n)
+    P, st, it = orc.c2p_points(p, np.zeros((n, 3)), U, floors=False)
+    np.testing.assert_allclose(P[:, 0], U[:, 0], rtol=1e-15)
+    np.testing.assert_allclose(P[:, 4], U[:, 4], rtol=1e-13)
+    assert np.all(P[:, 1:4] == 0)
+
+
+def test_floors_and_bad_input(orc):
+    s = I.kerr_schild_setup(8)
+    p = orc.params(s)
+    x = np.array([[5.0, 5.0, 5.0]] * 5)
+    r = np.sqrt(75.0)  # a = 0.9 barely changes r at this distance; the oracle uses the Kerr-Schild r
+    P = np.array([[1e-14, 0, 0, 0, 1e-30, 0, 0, 0],        # both floors
+                  [1.0, 0, 0, 0, 1e-14, 0, 0, 0],          # eps floor only
+                  [1.0, 300.0, 0, 0, 1.0, 0, 0, 0],         # W ceiling
+                  [1.0, 0.1, 0, 0, 1.0, 0, 0, 0],           # untouched
+                  [1.0, 0.1, 0, 0, 1.0, 0, 0, 0]])
+    U = orc.prim2con_points(p, x, P)["U"]
+    U[4, 0] = np.nan
+    P2, st, it = orc.c2p_points(p, x, U, floors=True)
+    g = orc.geom_points(p, x)
+    assert st[0] & orc.ST_RHO_FLOOR and st[0] & orc.ST_EPS_FLOOR
+    assert st[1] == orc.ST_EPS_FLOOR
+    assert st[2] == orc.ST_W_CAP
+    assert st[3] == 0
+    assert st[4] & orc.ST_BAD_INPUT
+    assert P2[0, 0] >= 1e-10 / r ** 2 * 0.99
+    W = np.sqrt(1 + np.einsum("ni,nij,nj->n", P2[:, 1:4], g["gam"], P2[:, 1:4]))
+    np.testing.assert_allclose(W[2], 100.0, rtol=1e-13)

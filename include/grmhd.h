@@ -1,0 +1,154 @@
+/* C ABI of the GB300 GRMHD stage library (libgrmhd.so).
+ *
+ * The library advances the Valencia-formulation GRMHD equations of Barker et al., "Phoebus:
+ * Performance Portable GRRMHD for Relativistic Astrophysics" (arXiv:2410.09146) by one explicit
+ * Runge-Kutta stage of the conservative finite-volume update on one logically Cartesian
+ * meshblock with ghost zones:
+ *   (sqrt(gamma) U)_t + (sqrt(-g) F^i)_i = sqrt(-g) S          Sec. 2.1, eq. (conservation law)
+ * in the fixed order: reconstruction (PLM minmod / MC, WENO5-Z-AOAH; Sec. 3.1, App. B), LLF or
+ * HLL Riemann fluxes (Sec. 3.1), Toth flux-CT of the cell-centred field (Sec. 3.1), flux
+ * divergence plus geometric sources (Sec. 2.1 eq. (source vector)) with an analytic Minkowski or
+ * Kerr-Schild metric (Sec. 2.3), and per-cell con2prim (Kastaun et al. 2021, Sec. 3.1) with
+ * floors (Sec. 3.2) and an ideal-gas EOS (Sec. 2.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Return 0 on success, a negative GRMHD_E* code on error; grmhd_last_error() then holds a
+ *    message. A con2prim failure in a cell is NOT a call error: it is reported per cell in the
+ *    status array and summed in the statistics.
+ *  - The library allocates no device memory. The caller passes one device workspace of at least
+ *    grmhd_workspace_bytes() bytes (256-byte aligned) and a CUDA stream; both are borrowed for the
+ *    lifetime of the context. All other pointers are borrowed for the call only.
+ *  - Calls are asynchronous on the context's stream, except those that write host memory, which
+ *    synchronise the stream before returning.
+ *  - No global state besides a thread-local message buffer for failed grmhd_create calls: contexts
+ *    are independent; one context must not be used from two threads at the same time.
+ *  - Array layouts are C order with x fastest. Primitives P = (rho, W v^1, W v^2, W v^3, rho eps,
+ *    B^1, B^2, B^3) (Sec. 2.1 eq. (primitive vector)) are [8][nz+2ng][ny+2ng][nx+2ng] including
+ *    ghosts; conserved states U = sqrt(gamma) (D, S_1, S_2, S_3, tau, B^1, B^2, B^3)
+ *    (Sec. 2.1 eq. (conserved vector), densitized) are [8][nz][ny][nx] over the interior.
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define GRMHD_OK 0
+#define GRMHD_E_INVALID (-1)     /* bad parameter, size or pointer */
+#define GRMHD_E_CUDA (-2)        /* a CUDA call or kernel launch failed */
+#define GRMHD_E_WORKSPACE (-3)   /* workspace too small or misaligned */
+#define GRMHD_E_UNSUPPORTED (-4) /* option combination not built */
+
+/* options */
+#define GRMHD_MINKOWSKI 0
+#define GRMHD_KERR_SCHILD 1 /* Cartesian Kerr-Schild, spin a = spin * mass along z */
+
+#define GRMHD_RECON_CONSTANT 0
+#define GRMHD_RECON_PLM_MINMOD 1
+#define GRMHD_RECON_PLM_MC 2
+#define GRMHD_RECON_WENO5Z_AOAH 3
+
+#define GRMHD_RIEMANN_LLF 0
+#define GRMHD_RIEMANN_HLL 1
+
+#define GRMHD_BC_PERIODIC 0     /* ghosts refilled from the interior at the start of every stage */
+#define GRMHD_BC_FIXED 1        /* ghosts keep the values given to grmhd_set_prims */
+
+#define GRMHD_FP64 0            /* every step in double precision */
+#define GRMHD_MIXED 1           /* reconstruction, fluxes, EMFs and sources in float; P stored in float;
+                                   state accumulation and con2prim in double */
+
+#define GRMHD_HOST 0
+#define GRMHD_DEVICE 1
+
+/* what grmhd_get returns */
+#define GRMHD_GET_PRIMS 0       /* double [8][nz+2ng][ny+2ng][nx+2ng] */
+#define GRMHD_GET_CONS 1        /* double [8][nz][ny][nx], the current state */
+#define GRMHD_GET_STATUS 2      /* uint8 [nz][ny][nx], last stage's con2prim/floor bits (GRMHD_ST_*) */
+#define GRMHD_GET_STATS 3       /* uint64 [8] of the last stage (or batch): con2prim iterations, cells with
+                                   rho floor, eps floor, W cap, not converged, bad input, max iterations
+                                   of a cell, reserved (0) */
+#define GRMHD_GET_DT 4          /* double [1]: the time step of the last first stage (CFL rule) */
+
+/* per-cell status bits */
+#define GRMHD_ST_RHO_FLOOR 1
+#define GRMHD_ST_EPS_FLOOR 2
+#define GRMHD_ST_W_CAP 4
+#define GRMHD_ST_NOT_CONVERGED 8
+#define GRMHD_ST_BAD_INPUT 16
+
+typedef struct grmhd_ctx grmhd_ctx;
+
+typedef struct {
+  int nx, ny, nz, ng;         /* interior cells per direction (0,0,0 for a con2prim-only context); ghosts */
+  double x0[3];               /* coordinate of the interior's lower corner */
+  double dx[3];               /* cell widths */
+  int metric;                 /* GRMHD_MINKOWSKI | GRMHD_KERR_SCHILD (Sec. 2.3) */
+  double spin, mass;          /* Kerr-Schild a/M and M */
+  double gamma_eos;           /* ideal-gas index, P = (gamma_eos - 1) rho eps (Sec. 2.2) */
+  int recon, riemann, precision, bc;
+  double rho_floor0;          /* rho >= rho_floor0 r^-floor_r_exp (Kerr-Schild r) or rho_floor0 (Sec. 3.2) */
+  double eps_floor0;          /* rho eps >= rho eps_floor0 r^-floor_r_exp */
+  double floor_r_exp;
+  double w_max;               /* Lorentz-factor ceiling */
+  double c2p_tol;             /* relative tolerance of the con2prim root in mu = 1/(h W) */
+  int c2p_max_iter;           /* iteration cap of the root solve */
+  double cfl;                 /* dt = cfl / max_d(max |lambda_d| / dx_d) when the stage picks dt */
+  double weno_eps;            /* epsilon of the WENO5-Z weights (App. B eq. (nonlinear weights)) */
+} grmhd_params;
+
+/* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */
+size_t grmhd_workspace_bytes(const grmhd_params* p);
+
+/* Create a context on the current CUDA device. `workspace` is a device pointer to at least
+ * grmhd_workspace_bytes(p) bytes, 256-byte aligned (may be NULL when that is 0); `stream` is a
+ * cudaStream_t (NULL = default stream). Both stay owned by the caller and must outlive the context.
+ * Errors: GRMHD_E_INVALID (bad parameters), GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED. */
+int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* stream, grmhd_ctx** out);
+
+/* Load primitives P (double, [8][nz+2ng][ny+2ng][nx+2ng] including ghosts; `where` = GRMHD_HOST or
+ * GRMHD_DEVICE) and derive the conserved state of the interior (Sec. 2.1 eq. (conserved vector)).
+ * Resets the Runge-Kutta slot bookkeeping. */
+int grmhd_set_prims(grmhd_ctx* c, const double* P, int where);
+
+/* Overwrite the current conserved state with U (double [8][nz][ny][nx]) without touching P; used
+ * with grmhd_set_prims to restore a checkpoint taken with grmhd_get. */
+int grmhd_set_cons(grmhd_ctx* c, const double* U, int where);
+
+/* One Runge-Kutta stage (a0..a6 of the stage; Sec. 3.1):
+ *   Unew = g0 U0 + g1 Ucur + beta dt L(Ucur)
+ * where U0 is the state at the start of the step (the input of the last stage with g0 == 0) and
+ * L = -sum_d dF^d/dx^d + sqrt(-g) S with CT fluxes for B; then con2prim + floors update P.
+ * A stage with g0 == 0 starts a new step. dt > 0 is used as given; dt <= 0 takes the CFL time step,
+ * computed on the device from this stage's face speeds when g0 == 0 and reused by later stages of
+ * the step. Asynchronous. Errors: GRMHD_E_INVALID, GRMHD_E_CUDA. */
+int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt);
+
+/* One SSP-RK2 (Heun) step: stages (0, 1, 1) and (1/2, 1/2, 1/2) with the same dt (dt <= 0: CFL). */
+int grmhd_rk2_step(grmhd_ctx* c, double dt);
+
+/* Con2prim of a flat-space batch (local orthonormal frame, Minkowski floors): U and P are device
+ * arrays [8][n] (structure of arrays) of densitized conserved / primitive variables; status (uint8 [n])
+ * and iters (int [n]) may be NULL. flags bit 0: P holds a warm-start guess on entry. Uses the
+ * context's gamma_eos, floors, tolerance and stream. Asynchronous. */
+int grmhd_c2p(grmhd_ctx* c, long long n, const double* U, double* P, uint8_t* status, int* iters, int flags);
+
+/* Copy `what` (GRMHD_GET_*) to dst (`where` = GRMHD_HOST synchronises the stream). */
+int grmhd_get(grmhd_ctx* c, int what, void* dst, int where);
+
+/* Last error message of the context (or of the last failed grmhd_create when c is NULL). */
+const char* grmhd_last_error(const grmhd_ctx* c);
+
+/* Release the context (the workspace and stream stay with the caller). */
+void grmhd_destroy(grmhd_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRMHD_H */

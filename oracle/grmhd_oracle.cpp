@@ -810,6 +810,17 @@ int orc_stage(const orc_params* p, double* P, const double* U0, const double* Uc
             recon_cell(p->recon, sR, p->weno_eps, qm, qp);
             PR[v] = qm;
           }
+          // Reading (the paper is silent on reconstruction failure): a face whose reconstructed
+          // density is not positive or internal energy is negative on either side takes the
+          // first-order (cell) values of both neighbours.
+          if (!(PL[0] > 0.0) || !(PL[4] >= 0.0) || !(PR[0] > 0.0) || !(PR[4] >= 0.0)) {
+            int cl[3] = {i, j, k};
+            cl[d] -= 1;
+            for (int v = 0; v < 8; ++v) {
+              PL[v] = P[v * gn + g.gi(cl[0], cl[1], cl[2])];
+              PR[v] = P[v * gn + g.gi(i, j, k)];
+            }
+          }
           double xf[3] = {g.xc(0, i), g.xc(1, j), g.xc(2, k)};
           xf[d] = g.xf(d, c[d]);
           Geom G;

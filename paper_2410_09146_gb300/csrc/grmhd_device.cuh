@@ -1,0 +1,539 @@
+// Device-side building blocks of the GRMHD Runge-Kutta stage (sm_103a).
+//
+// Method: Barker et al., "Phoebus" (arXiv:2410.09146) -- Valencia GRMHD, Sec. 2.1;
+// analytic metric, Sec. 2.3; second-order FV with LLF/HLL, PLM/WENO5-Z-AOAH, Toth flux-CT
+// and Kastaun con2prim, Sec. 3.1; floors, Sec. 3.2; WENO5-Z-AOAH, App. B.
+//
+// Everything here is templated on the arithmetic type R (double for the all-FP64 form,
+// float for the reconstruction / flux / EMF / source part of the mixed form).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace grmhd {
+
+enum { MINKOWSKI = 0, KERR_SCHILD = 1 };
+enum { RECON_CONSTANT = 0, RECON_PLM_MINMOD = 1, RECON_PLM_MC = 2, RECON_WENO5Z = 3 };
+enum { RIEMANN_LLF = 0, RIEMANN_HLL = 1 };
+enum { ST_RHO_FLOOR = 1, ST_EPS_FLOOR = 2, ST_W_CAP = 4, ST_NOT_CONVERGED = 8, ST_BAD_INPUT = 16 };
+enum { NV = 8 };
+
+// Kernel-side copy of the run parameters (passed by value).
+struct DevParams {
+  int nx, ny, nz, ng;
+  int gx, gy, gz;            // ghosted extents
+  long long gsize;           // gx*gy*gz: stride between variables of P, F, E
+  long long isize;           // nx*ny*nz: stride between variables of U
+  double x0[3], dx[3], idx[3];
+  double a, M;               // spin parameter a = spin*M, mass M
+  double gamma_eos;
+  int metric, recon, riemann, bc;
+  double rho_floor0, eps_floor0, floor_r_exp, w_max;
+  double c2p_tol;
+  int c2p_max_iter;
+  double cfl, weno_eps;
+};
+
+// Arguments of the update kernel (a5 + a6).
+struct StageArgs {
+  const double* U0;
+  const double* Ucur;
+  double* Unew;
+  uint8_t* status;
+  const double* dt_dev;          // used when use_dev_dt != 0
+  unsigned long long* stats;     // [0] iterations, [1] rho floor, [2] eps floor, [3] W cap, [4] not converged,
+                                 // [5] bad input, [6] max iterations
+  double g0, g1, beta, dt;
+  int use_dev_dt;
+};
+
+
+// ------------------------------------------------------------------ metric (Sec. 2.3)
+// gam / gamu hold the symmetric 3x3 in the order xx, xy, xz, yy, yz, zz.
+template <class R>
+struct Metric {
+  R alpha, beta[3], gam[6], gamu[6], sqrtgam;
+};
+
+__host__ __device__ constexpr int sym3(int i, int j) {
+  return i <= j ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
+}
+
+template <class R>
+__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+
+// Kerr-Schild core: r, f = 2 M r^3/(r^4 + a^2 z^2), spatial l_i (l_0 = 1).
+template <class R>
+__device__ __forceinline__ void ks_core(R x, R y, R z, R a, R M, R& r, R& r2, R& f, R l[3]) {
+  const R R2 = x * x + y * y + z * z;
+  const R A = R2 - a * a;
+  const R sq = sqrt(A * A + R(4) * a * a * z * z);
+  r2 = R(0.5) * (A + sq);
+  r = sqrt(r2);
+  f = R(2) * M * r * r2 / (r2 * r2 + a * a * z * z);
+  const R ira = rcp(r2 + a * a);
+  l[0] = (r * x + a * y) * ira;
+  l[1] = (r * y - a * x) * ira;
+  l[2] = z / r;
+}
+
+// 3+1 quantities in closed form: alpha = (1+f)^-1/2, beta^i = f l^i/(1+f),
+// gamma_ij = delta_ij + f l_i l_j, gamma^ij = delta^ij - f l^i l^j/(1+f), sqrt(gamma) = (1+f)^1/2,
+// sqrt(-g) = alpha sqrt(gamma) = 1.
+template <class R, int METRIC>
+__device__ __forceinline__ void metric_at(const DevParams& p, R x, R y, R z, Metric<R>& m, R* rks = nullptr) {
+  if (METRIC == MINKOWSKI) {
+    m.alpha = R(1);
+    m.sqrtgam = R(1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) m.beta[i] = R(0);
+#pragma unroll
+    for (int t = 0; t < 6; ++t) m.gam[t] = m.gamu[t] = (t == 0 || t == 3 || t == 5) ? R(1) : R(0);
+    if (rks) *rks = R(1);
+  } else {
+    R r, r2, f, l[3];
+    ks_core<R>(x, y, z, R(p.a), R(p.M), r, r2, f, l);
+    if (rks) *rks = r;
+    const R sg = sqrt(R(1) + f);
+    const R ip = rcp(R(1) + f);
+    m.sqrtgam = sg;
+    m.alpha = rcp(sg);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) m.beta[i] = f * ip * l[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const R ll = l[i] * l[j];
+        m.gam[sym3(i, j)] = (i == j ? R(1) : R(0)) + f * ll;
+        m.gamu[sym3(i, j)] = (i == j ? R(1) : R(0)) - f * ip * ll;
+      }
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void lower3(const R g[6], const R v[3], R out[3]) {
+  out[0] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];
+  out[1] = g[1] * v[0] + g[3] * v[1] + g[4] * v[2];
+  out[2] = g[2] * v[0] + g[4] * v[1] + g[5] * v[2];
+}
+
+// ------------------------------------------------------------------ fluid (Sec. 2.1)
+// Densitized conserved vector sqrt(gamma) U, flux sqrt(-g) F^d and the two characteristic
+// speeds of one face side, from the primitive vector P = (rho, W v^i, rho eps, B^i).
+template <class R>
+struct FaceSide {
+  R U[NV], F[NV], lm, lp;
+};
+
+template <class R>
+__device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, int d, R gamma_eos,
+                                             FaceSide<R>& s) {
+  const R rho = P[0], u = P[4];
+  const R ut[3] = {P[1], P[2], P[3]};
+  const R B[3] = {P[5], P[6], P[7]};
+  R utl[3], Bl[3];
+  lower3(m.gam, ut, utl);
+  lower3(m.gam, B, Bl);
+  const R usq = ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2];
+  const R W = sqrt(R(1) + usq);
+  const R iW = rcp(W);
+  const R ia = rcp(m.alpha);
+  R v[3], vl[3], vt[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    v[i] = ut[i] * iW;
+    vl[i] = utl[i] * iW;
+    vt[i] = m.alpha * v[i] - m.beta[i];
+  }
+  const R B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const R Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const R ab0 = W * Bv;                       // alpha b^0
+  const R b2 = (B2 + ab0 * ab0) * iW * iW;    // b^2
+  R bl[3];                                    // b_j = B_j / W + alpha b^0 v_j
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bl[i] = Bl[i] * iW + ab0 * vl[i];
+  const R pgas = (gamma_eos - R(1)) * u;
+  const R rhoh = rho + u + pgas;
+  const R w = rhoh + b2;
+  const R pstar = pgas + R(0.5) * b2;
+  const R D = rho * W;
+  const R wW2 = w * W * W;
+  R Uc[NV];
+  Uc[0] = D;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Uc[1 + j] = wW2 * vl[j] - ab0 * bl[j];
+  Uc[4] = wW2 - pstar - ab0 * ab0 - D;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Uc[5 + k] = B[k];
+  const R vtd = vt[d] * ia;
+  const R Bd = B[d];
+  s.F[0] = D * vtd;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) s.F[1 + j] = Uc[1 + j] * vtd + (j == d ? pstar : R(0)) - bl[j] * Bd * iW;
+  s.F[4] = Uc[4] * vtd + pstar * v[d] - ab0 * Bd * iW;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s.F[5 + k] = B[k] * vtd - Bd * vt[k] * ia;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) s.U[q] = m.sqrtgam * Uc[q];  // sqrt(-g) = 1: F is already densitized
+  // Valencia characteristic speeds with the approximate fast speed c^2 = vA^2 + cs^2 (1 - vA^2).
+  const R cs2 = gamma_eos * pgas / rhoh;
+  const R va2 = b2 / (rhoh + b2);
+  const R c2 = va2 + cs2 * (R(1) - va2);
+  const R v2 = usq * iW * iW;
+  const R vd = v[d];
+  R disc = (R(1) - v2) * (m.gamu[sym3(d, d)] * (R(1) - v2 * c2) - vd * vd * (R(1) - c2));
+  disc = disc > R(0) ? disc : R(0);
+  const R pre = m.alpha / (R(1) - v2 * c2);
+  const R sq = sqrt(c2 * disc);
+  const R base = vd * (R(1) - c2);
+  s.lp = pre * (base + sq) - m.beta[d];
+  s.lm = pre * (base - sq) - m.beta[d];
+}
+
+// Hydro part of the densitized conserved vector only (used after floors).
+template <class R>
+__device__ __forceinline__ void prim_to_cons5(const R P[NV], const Metric<R>& m, R gamma_eos, R U5[5]) {
+  const R ut[3] = {P[1], P[2], P[3]};
+  const R B[3] = {P[5], P[6], P[7]};
+  R utl[3], Bl[3];
+  lower3(m.gam, ut, utl);
+  lower3(m.gam, B, Bl);
+  const R usq = ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2];
+  const R W = sqrt(R(1) + usq);
+  const R iW = rcp(W);
+  R vl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) vl[i] = utl[i] * iW;
+  const R B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const R Bv = B[0] * vl[0] + B[1] * vl[1] + B[2] * vl[2];
+  const R ab0 = W * Bv;
+  const R b2 = (B2 + ab0 * ab0) * iW * iW;
+  const R pgas = (gamma_eos - R(1)) * P[4];
+  const R w = P[0] + P[4] + pgas + b2;
+  const R D = P[0] * W;
+  const R wW2 = w * W * W;
+  U5[0] = m.sqrtgam * D;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) U5[1 + j] = m.sqrtgam * (wW2 * vl[j] - ab0 * (Bl[j] * iW + ab0 * vl[j]));
+  U5[4] = m.sqrtgam * (wW2 - (pgas + R(0.5) * b2) - ab0 * ab0 - D);
+}
+
+// ------------------------------------------------------------------ reconstruction (Sec. 3.1, App. B)
+template <class R>
+__device__ __forceinline__ R mc_slope(R dm, R dp) {
+  if (!(dm * dp > R(0))) return R(0);
+  const R c = R(0.5) * (dm + dp);
+  const R m = fmin(fmin(R(2) * fabs(dm), R(2) * fabs(dp)), fabs(c));
+  return dm > R(0) ? m : -m;
+}
+
+template <class R>
+__device__ __forceinline__ R minmod_slope(R dm, R dp) {
+  if (!(dm * dp > R(0))) return R(0);
+  const R m = fmin(fabs(dm), fabs(dp));
+  return dm > R(0) ? m : -m;
+}
+
+// WENO5-Z value at the face on the f2 -> f3 side of the centre value f2 (stencil f0..f4),
+// and its nonlinear weights. Candidates are the third-order cell-average forms, linear weights
+// (1/10, 6/10, 3/10), tau_Z = |beta_2 - beta_0|, exponent p = 2.
+template <class R>
+__device__ __forceinline__ R weno5z_face(R f0, R f1, R f2, R f3, R f4, R eps, R w[3]) {
+  const R P0 = (R(2) * f0 - R(7) * f1 + R(11) * f2) * R(1.0 / 6.0);
+  const R P1 = (-f1 + R(5) * f2 + R(2) * f3) * R(1.0 / 6.0);
+  const R P2 = (R(2) * f2 + R(5) * f3 - f4) * R(1.0 / 6.0);
+  R t0 = f0 - R(2) * f1 + f2, s0 = f0 - R(4) * f1 + R(3) * f2;
+  R t1 = f1 - R(2) * f2 + f3, s1 = f1 - f3;
+  R t2 = f2 - R(2) * f3 + f4, s2 = R(3) * f2 - R(4) * f3 + f4;
+  const R b0 = R(13.0 / 12.0) * t0 * t0 + R(0.25) * s0 * s0;
+  const R b1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * s1 * s1;
+  const R b2 = R(13.0 / 12.0) * t2 * t2 + R(0.25) * s2 * s2;
+  const R tau = fabs(b2 - b0);
+  R q0 = tau / (b0 + eps), q1 = tau / (b1 + eps), q2 = tau / (b2 + eps);
+  if (sizeof(R) == 4) {  // keep q^2 inside the float range; a clamped q still dominates its weight
+    q0 = fmin(q0, R(1e15));
+    q1 = fmin(q1, R(1e15));
+    q2 = fmin(q2, R(1e15));
+  }
+  const R a0 = R(0.1) * (R(1) + q0 * q0);
+  const R a1 = R(0.6) * (R(1) + q1 * q1);
+  const R a2 = R(0.3) * (R(1) + q2 * q2);
+  const R is = rcp(a0 + a1 + a2);
+  w[0] = a0 * is;
+  w[1] = a1 * is;
+  w[2] = a2 * is;
+  return w[0] * P0 + w[1] * P1 + w[2] * P2;
+}
+
+template <class R>
+__device__ __forceinline__ R weno_sigma_side(const R w[3]) {
+  return R(3) * w[0] * w[1] * w[2] / (R(0.3) * w[0] * w[1] + R(0.6) * w[0] * w[2] + R(0.1) * w[1] * w[2]);
+}
+
+// Face values of the centre cell c = f[2]: qm at its lower face, qp at its upper face.
+template <class R, int RECON>
+__device__ __forceinline__ void recon_cell(R f0, R f1, R f2, R f3, R f4, R eps, R& qm, R& qp) {
+  if (RECON == RECON_CONSTANT) {
+    qm = qp = f2;
+  } else if (RECON == RECON_PLM_MINMOD || RECON == RECON_PLM_MC) {
+    const R s = RECON == RECON_PLM_MC ? mc_slope(f2 - f1, f3 - f2) : minmod_slope(f2 - f1, f3 - f2);
+    qm = f2 - R(0.5) * s;
+    qp = f2 + R(0.5) * s;
+  } else {
+    R wp[3], wm[3];
+    const R P5p = weno5z_face<R>(f0, f1, f2, f3, f4, eps, wp);
+    const R P5m = weno5z_face<R>(f4, f3, f2, f1, f0, eps, wm);  // mirrored stencil x -> -x
+    const R sp = weno_sigma_side(wp), sm = weno_sigma_side(wm);
+    R sigma = sp + sm > R(0) ? R(2) * sp * sm / (sp + sm) : R(0);  // both sides can underflow in float
+    sigma = sigma > R(1) ? R(1) : sigma;
+    const R s = mc_slope(f2 - f1, f3 - f2);
+    qp = sigma * P5p + (R(1) - sigma) * (f2 + R(0.5) * s);
+    qm = sigma * P5m + (R(1) - sigma) * (f2 - R(0.5) * s);
+  }
+}
+
+// ------------------------------------------------------------------ Riemann solvers (Sec. 3.1)
+template <class R>
+__device__ __forceinline__ R riemann_flux(int riemann, const FaceSide<R>& L, const FaceSide<R>& Rs, R Fh[NV]) {
+  const R cmax = fmax(fmax(fabs(L.lm), fabs(L.lp)), fmax(fabs(Rs.lm), fabs(Rs.lp)));
+  if (riemann == RIEMANN_LLF) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Fh[q] = R(0.5) * (L.F[q] + Rs.F[q]) - R(0.5) * cmax * (Rs.U[q] - L.U[q]);
+  } else {
+    const R cl = fmin(R(0), fmin(L.lm, Rs.lm));
+    const R cr = fmax(R(0), fmax(L.lp, Rs.lp));
+    const R den = cr - cl;
+    if (den == R(0)) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Fh[q] = R(0.5) * (L.F[q] + Rs.F[q]);
+    } else {
+      const R id = rcp(den);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Fh[q] = (cr * L.F[q] - cl * Rs.F[q] + cr * cl * (Rs.U[q] - L.U[q])) * id;
+    }
+  }
+  return cmax;
+}
+
+// ------------------------------------------------------------------ con2prim (Sec. 3.1)
+// Kastaun, Kalinani & Ciolfi (2021): with q = tau/D, r_i = S_i/D, b^i = B^i/sqrt(D), the unknown
+// mu = 1/(h W) is the root of f(mu) = mu - 1/(nu(mu) + mu rbar^2(mu)) in [0, mu_+], mu_+ the root
+// of mu^2 (1 + rbar^2(mu)) = 1 (h0 = 1 for the ideal gas). Solved by a bracketed Newton iteration
+// whose derivative comes from forward-mode dual numbers, warm-started from the previous primitives.
+struct Dual {
+  double v, d;
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return {a + b.v, b.d}; }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return {a - b.v, -b.d}; }
+__device__ __forceinline__ Dual drcp(Dual a) {
+  const double r = 1.0 / a.v;
+  return {r, -a.d * r * r};
+}
+__device__ __forceinline__ Dual dsqrt(Dual a) {
+  const double s = sqrt(a.v);
+  return {s, a.d * 0.5 / s};
+}
+
+struct C2PIn {
+  double D, q, r2, b2, rb, rb2, gm1, v0sq;
+};
+
+__device__ __forceinline__ double c2p_rbar2(const C2PIn& c, double mu, double& x) {
+  x = 1.0 / (1.0 + mu * c.b2);
+  return x * x * c.r2 + mu * x * (1.0 + x) * c.rb2;
+}
+
+// Master function value and derivative at mu; also the intermediate W, rho, eps and x.
+struct C2PEval {
+  double f, df, x, W, rho, eps;
+};
+
+__device__ __forceinline__ C2PEval c2p_master(const C2PIn& c, double mu_v) {
+  const Dual mu = {mu_v, 1.0};
+  const Dual x = drcp(1.0 + c.b2 * mu);
+  const Dual rb = c.r2 * (x * x) + c.rb2 * (mu * x * (1.0 + x));
+  const Dual qbar = (c.q - 0.5 * c.b2) - (0.5 * (c.b2 * c.r2 - c.rb2)) * (mu * mu * x * x);
+  Dual vh2 = mu * mu * rb;
+  if (vh2.v > c.v0sq) vh2 = {c.v0sq, 0.0};
+  const Dual iW = dsqrt(1.0 - vh2);        // 1/W
+  const Dual W = drcp(iW);
+  const Dual rho = c.D * iW;
+  Dual eps = W * (qbar - mu * rb) + vh2 * W * W * drcp(1.0 + W);
+  if (eps.v < 0.0) eps = {0.0, 0.0};
+  // a = P/(rho (1 + eps)) = (Gamma - 1) eps/(1 + eps) for the ideal gas
+  const Dual onepe = 1.0 + eps;
+  const Dual a = c.gm1 * eps * drcp(onepe);
+  const Dual nuA = (1.0 + a) * onepe * iW;
+  const Dual nuB = (1.0 + a) * (1.0 + qbar - mu * rb);
+  const Dual nu = nuA.v >= nuB.v ? nuA : nuB;
+  const Dual f = mu - drcp(nu + mu * rb);
+  C2PEval e;
+  e.f = f.v;
+  e.df = f.d;
+  e.x = x.v;
+  e.W = W.v;
+  e.rho = rho.v;
+  e.eps = eps.v;
+  return e;
+}
+
+// Upper end of the bracket: root of g(mu) = mu^2 (1 + rbar^2(mu)) - 1 on (0, 1].
+__device__ __forceinline__ double c2p_mu_plus(const C2PIn& c) {
+  double x;
+  double g1 = 1.0 * (1.0 + c2p_rbar2(c, 1.0, x)) - 1.0;
+  if (!(g1 > 0.0)) return 1.0;
+  double lo = 0.0, hi = 1.0;
+  double mu = 1.0 / sqrt(1.0 + c.r2);  // root when b = 0
+  if (!(mu > lo && mu < hi)) mu = 0.5;
+  for (int it = 0; it < 60; ++it) {
+    const double xx = 1.0 / (1.0 + mu * c.b2);
+    const double dx = -c.b2 * xx * xx;
+    const double rb = xx * xx * c.r2 + mu * xx * (1.0 + xx) * c.rb2;
+    const double drb = 2.0 * xx * dx * c.r2 + c.rb2 * (xx * (1.0 + xx) + mu * dx * (1.0 + 2.0 * xx));
+    const double g = mu * mu * (1.0 + rb) - 1.0;
+    const double dg = 2.0 * mu * (1.0 + rb) + mu * mu * drb;
+    if (g < 0.0) lo = mu; else hi = mu;
+    double nmu = mu - g / dg;
+    if (!(nmu > lo && nmu < hi)) nmu = 0.5 * (lo + hi);
+    const bool done = fabs(nmu - mu) <= 1e-15 * nmu;
+    mu = nmu;
+    if (done || hi - lo <= 1e-15 * hi) break;
+  }
+  return mu;
+}
+
+// Recover primitives from undensitized (D, S_j, tau, B^k). Returns the status bits of the solve
+// (0, ST_NOT_CONVERGED or ST_BAD_INPUT); floors are separate.
+template <class R>
+__device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, const double Uc[NV],
+                                        double mu_guess, double Pout[NV], int& iters) {
+  iters = 0;
+  bool finite = true;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) finite = finite && isfinite(Uc[q]);
+  if (!finite || !(Uc[0] > 0.0)) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Pout[q] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Pout[5 + k] = isfinite(Uc[5 + k]) ? Uc[5 + k] : 0.0;
+    return ST_BAD_INPUT;
+  }
+  double gam[6], gamu[6];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    gam[t] = (double)m.gam[t];
+    gamu[t] = (double)m.gamu[t];
+  }
+  C2PIn c;
+  c.D = Uc[0];
+  const double iD = 1.0 / c.D;
+  c.q = Uc[4] * iD;
+  const double rl[3] = {Uc[1] * iD, Uc[2] * iD, Uc[3] * iD};
+  double ru[3];
+  lower3(gamu, rl, ru);
+  const double isD = 1.0 / sqrt(c.D);
+  const double bu[3] = {Uc[5] * isD, Uc[6] * isD, Uc[7] * isD};
+  double bl[3];
+  lower3(gam, bu, bl);
+  c.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
+  c.b2 = bu[0] * bl[0] + bu[1] * bl[1] + bu[2] * bl[2];
+  c.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
+  c.rb2 = c.rb * c.rb;
+  c.gm1 = p.gamma_eos - 1.0;
+  c.v0sq = c.r2 / (1.0 + c.r2);
+  const double mup = c2p_mu_plus(c);
+  double lo = 0.0, hi = mup;
+  double mu = mu_guess;
+  if (!(mu > lo && mu < hi)) mu = 0.5 * mup;
+  int st = ST_NOT_CONVERGED;
+  C2PEval e;
+  const int maxit = p.c2p_max_iter;
+  for (int it = 0; it < maxit; ++it) {
+    e = c2p_master(c, mu);
+    ++iters;
+    if (e.f == 0.0 || (e.f < 0.0 && mu == mup)) {
+      // exact root, or f(mu_+) <= 0: the root sits on the bracket end (cold limit, eps = 0)
+      st = 0;
+      break;
+    }
+    if (e.f < 0.0) lo = mu; else hi = mu;
+    double nmu = mu - e.f / e.df;
+    if (!(nmu >= lo && nmu <= hi) || !(e.df > 0.0))
+      nmu = (nmu > hi && hi == mup && e.df > 0.0) ? mup : 0.5 * (lo + hi);  // try the unevaluated end first
+    const bool conv = fabs(nmu - mu) <= p.c2p_tol * nmu;
+    mu = nmu;
+    if (conv) {
+      // one more Newton step past the tolerance
+      e = c2p_master(c, mu);
+      ++iters;
+      nmu = mu - e.f / e.df;
+      if (nmu >= lo && nmu <= hi && e.df > 0.0) mu = nmu;
+      st = 0;
+      break;
+    }
+    if (hi - lo <= 1e-16 * hi) {
+      st = 0;
+      break;
+    }
+  }
+  e = c2p_master(c, mu);
+  const double W = e.W;
+  Pout[0] = e.rho;
+  const double mx = mu * e.x;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Pout[1 + i] = W * mx * (ru[i] + mu * c.rb * bu[i]);
+  Pout[4] = e.rho * e.eps;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Pout[5 + k] = Uc[5 + k];
+  return st;
+}
+
+// Floors (Sec. 3.2): rho >= rho0 r^-n, rho eps >= rho eps0 r^-n (r the Kerr-Schild radius; 1 in
+// Minkowski), and the Lorentz-factor ceiling W <= w_max.
+template <int METRIC>
+__device__ __forceinline__ int apply_floors(const DevParams& p, const double gam[6], double r, double P[NV]) {
+  double fr = 1.0;
+  if (METRIC == KERR_SCHILD) fr = p.floor_r_exp == 2.0 ? 1.0 / (r * r) : pow(r, -p.floor_r_exp);
+  const double rho_flr = p.rho_floor0 * fr;
+  const double eps_flr = p.eps_floor0 * fr;
+  int st = 0;
+  if (!(P[0] >= rho_flr)) {
+    P[0] = rho_flr;
+    st |= ST_RHO_FLOOR;
+  }
+  if (!(P[4] >= P[0] * eps_flr)) {
+    P[4] = P[0] * eps_flr;
+    st |= ST_EPS_FLOOR;
+  }
+  const double ut[3] = {P[1], P[2], P[3]};
+  double utl[3];
+  lower3(gam, ut, utl);
+  const double usq = ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2];
+  if (sqrt(1.0 + usq) > p.w_max) {
+    const double s = sqrt((p.w_max * p.w_max - 1.0) / usq);
+    P[1] *= s;
+    P[2] *= s;
+    P[3] *= s;
+    st |= ST_W_CAP;
+  }
+  return st;
+}
+
+// mu = 1/(h W) of a primitive state, the con2prim warm start.
+template <class R>
+__device__ __forceinline__ double mu_of_prims(const double P[NV], const double gam[6], double gamma_eos) {
+  const double ut[3] = {P[1], P[2], P[3]};
+  double utl[3];
+  lower3(gam, ut, utl);
+  const double W = sqrt(1.0 + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
+  const double h = 1.0 + gamma_eos * P[4] / P[0];  // 1 + eps + p/rho = 1 + Gamma u/rho
+  return 1.0 / (h * W);
+}
+
+}  // namespace grmhd

@@ -1,0 +1,102 @@
+// All-FP64 form of the stage kernels (every step in double precision) and the shared launchers.
+#include "grmhd_kernels.cuh"
+#include "grmhd_launch.h"
+
+namespace grmhd {
+
+int grid_for(long long n, int threads) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  long long b = (n + threads - 1) / threads;
+  const long long cap = (long long)sms * 16;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+namespace {
+
+using R = double;
+using T = double;
+
+template <int METRIC>
+cudaError_t flux_m(const DevParams& p, const T* P, R* F, unsigned long long* ms, int d, int track, cudaStream_t s) {
+  const long long n = (long long)(p.nx + (d == 0 ? 1 : 2)) * (p.ny + (d == 1 ? 1 : 2)) * (p.nz + (d == 2 ? 1 : 2));
+  const int g = grid_for(n, 128);
+  switch (p.recon) {
+    case RECON_CONSTANT: k_flux<R, T, METRIC, RECON_CONSTANT><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    case RECON_PLM_MINMOD: k_flux<R, T, METRIC, RECON_PLM_MINMOD><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    case RECON_PLM_MC: k_flux<R, T, METRIC, RECON_PLM_MC><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    case RECON_WENO5Z: k_flux<R, T, METRIC, RECON_WENO5Z><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t ghost(const DevParams& p, void* P, cudaStream_t s) {
+  k_ghost_periodic<T><<<grid_for(p.gsize, 256), 256, 0, s>>>((T*)P, p);
+  return cudaGetLastError();
+}
+
+cudaError_t flux(const DevParams& p, const void* P, void* F, unsigned long long* ms, int d, int track, cudaStream_t s) {
+  return p.metric == KERR_SCHILD ? flux_m<KERR_SCHILD>(p, (const T*)P, (R*)F, ms, d, track, s)
+                                 : flux_m<MINKOWSKI>(p, (const T*)P, (R*)F, ms, d, track, s);
+}
+
+cudaError_t emf(const DevParams& p, const void* Fx, const void* Fy, const void* Fz, void* E, cudaStream_t s) {
+  const long long n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+  k_emf<R><<<grid_for(n, 256), 256, 0, s>>>((const R*)Fx, (const R*)Fy, (const R*)Fz, (R*)E, p);
+  return cudaGetLastError();
+}
+
+cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, const void* Fz, const void* E,
+                   const StageArgs& a, cudaStream_t s) {
+  const int g = grid_for(p.isize, 128);
+  if (p.metric == KERR_SCHILD)
+    k_update<KERR_SCHILD, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
+  else
+    k_update<MINKOWSKI, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
+  return cudaGetLastError();
+}
+
+cudaError_t prim2con(const DevParams& p, const void* P, double* U, cudaStream_t s) {
+  const int g = grid_for(p.isize, 128);
+  if (p.metric == KERR_SCHILD)
+    k_prim2con<KERR_SCHILD, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+  else
+    k_prim2con<MINKOWSKI, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+  return cudaGetLastError();
+}
+
+cudaError_t load_prims(const DevParams& p, const double* src, void* P, cudaStream_t s) {
+  return cudaMemcpyAsync(P, src, sizeof(double) * NV * p.gsize, cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t store_prims(const DevParams& p, const void* P, double* dst, cudaStream_t s) {
+  return cudaMemcpyAsync(dst, P, sizeof(double) * NV * p.gsize, cudaMemcpyDeviceToDevice, s);
+}
+
+const FormLaunchers kFp64 = {ghost, flux, emf, update, prim2con, load_prims, store_prims, 8, 8};
+
+}  // namespace
+
+const FormLaunchers& fp64_launchers() { return kFp64; }
+
+cudaError_t launch_finalize_dt(const unsigned long long* ms, double* dt, const DevParams& p, cudaStream_t s) {
+  k_finalize_dt<<<1, 32, 0, s>>>(ms, dt, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c2p_batch(const double* U, double* P, uint8_t* status, int* iters, long long n, int flags,
+                             const DevParams& p, unsigned long long* stats, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_c2p_batch<<<grid_for(n, 128), 128, 0, s>>>(U, P, status, iters, n, flags, p, stats);
+  return cudaGetLastError();
+}
+
+}  // namespace grmhd

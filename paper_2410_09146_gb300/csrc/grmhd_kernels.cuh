@@ -1,0 +1,438 @@
+// Kernels of one GRMHD Runge-Kutta stage (a0 ghost fill, a1 metric, a2 reconstruction,
+// a3 Riemann flux, a4 constrained transport, a5 divergence + sources + RK combination,
+// a6 con2prim + floors, a7 time step). Layouts, all with x fastest:
+//   P   [8][gz][gy][gx]  primitives incl. ghosts (type T: double, or float in the mixed form)
+//   U   [8][nz][ny][nx]  densitized conserved state (double)
+//   F_d [8][gz][gy][gx]  face fluxes of direction d; entry (i,j,k) is the lower d-face of cell (i,j,k)
+//   E   [3][gz][gy][gx]  edge EMFs; component c at (i,j,k) is the c-directed edge at the lower
+//                        corner of cell (i,j,k) in the two directions transverse to c
+#pragma once
+
+#include "grmhd_device.cuh"
+
+namespace grmhd {
+
+__device__ __forceinline__ long long gidx(const DevParams& p, int i, int j, int k) {
+  return ((long long)(k + p.ng) * p.gy + (j + p.ng)) * p.gx + (i + p.ng);
+}
+
+__device__ __forceinline__ long long iidx(const DevParams& p, int i, int j, int k) {
+  return ((long long)k * p.ny + j) * p.nx + i;
+}
+
+// a0: periodic ghost fill (every ghost cell copies its wrapped interior cell).
+template <class T>
+__global__ void k_ghost_periodic(T* __restrict__ P, DevParams p) {
+  const long long n = p.gsize;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int gi = (int)(t % p.gx);
+    const int gj = (int)((t / p.gx) % p.gy);
+    const int gk = (int)(t / ((long long)p.gx * p.gy));
+    const int i = gi - p.ng, j = gj - p.ng, k = gk - p.ng;
+    if (i >= 0 && i < p.nx && j >= 0 && j < p.ny && k >= 0 && k < p.nz) continue;
+    const int si = ((i % p.nx) + p.nx) % p.nx, sj = ((j % p.ny) + p.ny) % p.ny, sk = ((k % p.nz) + p.nz) % p.nz;
+    const long long src = gidx(p, si, sj, sk);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) P[q * n + t] = P[q * n + src];
+  }
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// a1 + a2 + a3: one thread per face of direction d in the box
+//   face index along d in [0, n_d], transverse cell indices in [-1, n_t]
+// (the transverse halo feeds the CT edge averages). Writes the Riemann flux and, for interior
+// faces, reduces max |lambda| into ms[d].
+template <class R, class T, int METRIC, int RECON>
+__global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __restrict__ F,
+                                              unsigned long long* __restrict__ ms, DevParams p, int d,
+                                              int track_speed) {
+  const int ex = p.nx + (d == 0 ? 1 : 2), ey = p.ny + (d == 1 ? 1 : 2), ez = p.nz + (d == 2 ? 1 : 2);
+  const int ox = d == 0 ? 0 : -1, oy = d == 1 ? 0 : -1, oz = d == 2 ? 0 : -1;
+  const long long nface = (long long)ex * ey * ez;
+  const long long stride = d == 0 ? 1 : (d == 1 ? (long long)p.gx : (long long)p.gx * p.gy);
+  R cm_local = R(0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nface;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % ex) + ox;
+    const int j = (int)((t / ex) % ey) + oy;
+    const int k = (int)(t / ((long long)ex * ey)) + oz;
+    const long long g = gidx(p, i, j, k);
+    R PL[NV], PR[NV];
+    const R eps = R(p.weno_eps);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const T* Pq = P + q * p.gsize + g;
+      const R fm3 = RECON == RECON_WENO5Z ? R(Pq[-3 * stride]) : R(0);
+      const R fm2 = RECON != RECON_CONSTANT ? R(Pq[-2 * stride]) : R(0);
+      const R fm1 = R(Pq[-stride]);
+      const R f0 = R(Pq[0]);
+      const R fp1 = RECON != RECON_CONSTANT ? R(Pq[stride]) : R(0);
+      const R fp2 = RECON == RECON_WENO5Z ? R(Pq[2 * stride]) : R(0);
+      R qm, qp;
+      recon_cell<R, RECON>(fm3, fm2, fm1, f0, fp1, eps, qm, qp);  // cell c - e_d
+      PL[q] = qp;
+      recon_cell<R, RECON>(fm2, fm1, f0, fp1, fp2, eps, qm, qp);  // cell c
+      PR[q] = qm;
+    }
+    // A face whose reconstructed density is not positive or internal energy is negative on
+    // either side takes the first-order (cell) values of both neighbours.
+    if (!(PL[0] > R(0)) || !(PL[4] >= R(0)) || !(PR[0] > R(0)) || !(PR[4] >= R(0))) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        PL[q] = R(P[q * p.gsize + g - stride]);
+        PR[q] = R(P[q * p.gsize + g]);
+      }
+    }
+    R xf[3] = {R(p.x0[0] + (i + 0.5) * p.dx[0]), R(p.x0[1] + (j + 0.5) * p.dx[1]), R(p.x0[2] + (k + 0.5) * p.dx[2])};
+    const int cd = d == 0 ? i : (d == 1 ? j : k);
+    xf[d] = R(p.x0[d] + cd * p.dx[d]);
+    Metric<R> m;
+    metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
+    FaceSide<R> L, Rs;
+    prim_to_face<R>(PL, m, d, R(p.gamma_eos), L);
+    prim_to_face<R>(PR, m, d, R(p.gamma_eos), Rs);
+    R Fh[NV];
+    const R cm = riemann_flux<R>(p.riemann, L, Rs, Fh);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
+    const bool interior = (d == 0 || (i >= 0 && i < p.nx)) && (d == 1 || (j >= 0 && j < p.ny)) &&
+                          (d == 2 || (k >= 0 && k < p.nz));
+    if (interior && cm > cm_local) cm_local = cm;
+  }
+  if (track_speed) {
+    double v = (double)cm_local;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) atomic_max_pos(ms + d, v);
+    }
+  }
+}
+
+// a7: dt = cfl / max_d(max|lambda_d| / dx_d)
+static __global__ void k_finalize_dt(const unsigned long long* ms, double* dt, DevParams p) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double m = 0.0;
+    for (int d = 0; d < 3; ++d) m = fmax(m, __longlong_as_double((long long)ms[d]) / p.dx[d]);
+    *dt = p.cfl / m;
+  }
+}
+
+// a4: Toth flux-CT edge EMFs, Omega_k = 1/4 (sum of the 4 F^j_{B^i} - sum of the 4 F^i_{B^j})
+// around the edge for (i, j, k) cyclic. Thread box [0, nx] x [0, ny] x [0, nz].
+template <class R>
+__global__ void k_emf(const R* __restrict__ Fx, const R* __restrict__ Fy, const R* __restrict__ Fz,
+                      R* __restrict__ E, DevParams p) {
+  const int ex = p.nx + 1, ey = p.ny + 1, ez = p.nz + 1;
+  const long long n = (long long)ex * ey * ez;
+  const long long G = p.gsize;
+  const long long sy = p.gx, sz = (long long)p.gx * p.gy;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
+    const long long g = gidx(p, i, j, k);
+    if (k < p.nz)  // Omega_z(fi = i, fj = j, k)
+      E[2 * G + g] = R(0.25) * (Fy[5 * G + g - 1] + Fy[5 * G + g] - Fx[6 * G + g - sy] - Fx[6 * G + g]);
+    if (i < p.nx)  // Omega_x(i, fj = j, fk = k)
+      E[0 * G + g] = R(0.25) * (Fz[6 * G + g - sy] + Fz[6 * G + g] - Fy[7 * G + g - sz] - Fy[7 * G + g]);
+    if (j < p.ny)  // Omega_y(fi = i, j, fk = k)
+      E[1 * G + g] = R(0.25) * (Fx[7 * G + g - sz] + Fx[7 * G + g] - Fz[5 * G + g - 1] - Fz[5 * G + g]);
+  }
+}
+
+// Geometric source terms at a cell centre (Sec. 2.1 source vector, without the radiation
+// four-force), returned densitized (sqrt(-g) = 1): S[0] = 0, S[1..3] = S_j, S[4] = S_tau.
+// For Kerr-Schild, g = eta + f l l makes S_j = 1/2 T^{mu nu} d_j g_{mu nu}
+//   = 1/2 [d_j f (l.T.l) + 2 f (d_j l).T.l],
+// and S_tau = alpha (T^{k0} d_k ln alpha - T^{mu nu} Gamma^0_{mu nu}) with
+//   T^{mu nu} Gamma^0_{mu nu} = g^{0 lambda} (Q_lambda - S_lambda), Q_lambda = T^{k nu} d_k g_{lambda nu}.
+template <class R>
+__device__ __forceinline__ void ks_sources(const DevParams& p, R x, R y, R z, const R P[NV], const Metric<R>& m,
+                                           R S[5]) {
+  const R a = R(p.a), M = R(p.M);
+  R r, r2, f, l[3];
+  ks_core<R>(x, y, z, a, M, r, r2, f, l);
+  const R xs[3] = {x, y, z};
+  const R R2 = x * x + y * y + z * z;
+  const R sq = R(2) * r2 - (R2 - a * a);
+  const R Sig = r2 * r2 + a * a * z * z;
+  const R ira = rcp(r2 + a * a);
+  const R ir = rcp(r);
+  R dr[3], df[3], dl[3][3];  // dl[k][i] = d_k l_i
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    dr[kk] = (xs[kk] * r2 + (kk == 2 ? a * a * z : R(0))) * ir / sq;
+    const R dSig = R(4) * r * r2 * dr[kk] + (kk == 2 ? R(2) * a * a * z : R(0));
+    df[kk] = f * (R(3) * dr[kk] * ir - dSig / Sig);
+    dl[kk][0] = ((dr[kk] * x + (kk == 0 ? r : R(0)) + (kk == 1 ? a : R(0))) - R(2) * r * dr[kk] * l[0]) * ira;
+    dl[kk][1] = ((dr[kk] * y + (kk == 1 ? r : R(0)) - (kk == 0 ? a : R(0))) - R(2) * r * dr[kk] * l[1]) * ira;
+    dl[kk][2] = ((kk == 2 ? R(1) : R(0)) - l[2] * dr[kk]) * ir;
+  }
+  // fluid four-vectors
+  const R ut[3] = {P[1], P[2], P[3]};
+  const R B[3] = {P[5], P[6], P[7]};
+  R utl[3], Bl[3];
+  lower3(m.gam, ut, utl);
+  lower3(m.gam, B, Bl);
+  const R W = sqrt(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
+  const R iW = rcp(W), ia = rcp(m.alpha);
+  R vt[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) vt[i] = m.alpha * ut[i] * iW - m.beta[i];
+  const R Bv = (B[0] * utl[0] + B[1] * utl[1] + B[2] * utl[2]) * iW;
+  const R B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const R ab0 = W * Bv;
+  const R b2 = (B2 + ab0 * ab0) * iW * iW;
+  R uc[4], bc[4];
+  uc[0] = W * ia;
+  bc[0] = ab0 * ia;
+  const R b0 = bc[0];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    uc[1 + i] = W * ia * vt[i];
+    bc[1 + i] = B[i] * iW + b0 * vt[i];
+  }
+  const R pg = (R(p.gamma_eos) - R(1)) * P[4];
+  const R w = P[0] + P[4] + pg + b2;
+  const R pt = pg + R(0.5) * b2;
+  // g^{mu nu}
+  const R ia2 = ia * ia;
+  R gu[4][4];
+  gu[0][0] = -ia2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gu[0][1 + i] = gu[1 + i][0] = m.beta[i] * ia2;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gu[1 + i][1 + j] = m.gamu[sym3(i, j)] - m.beta[i] * m.beta[j] * ia2;
+  }
+  R T[4][4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) T[mu][nu] = w * uc[mu] * uc[nu] + pt * gu[mu][nu] - bc[mu] * bc[nu];
+  const R L4[4] = {R(1), l[0], l[1], l[2]};
+  R tv[4];  // t^mu = T^{mu nu} l_nu
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) tv[mu] = T[mu][0] + T[mu][1] * l[0] + T[mu][2] * l[1] + T[mu][3] * l[2];
+  const R ltl = tv[0] + l[0] * tv[1] + l[1] * tv[2] + l[2] * tv[3];
+  R Sj[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const R dlt = dl[j][0] * tv[1] + dl[j][1] * tv[2] + dl[j][2] * tv[3];
+    Sj[j] = R(0.5) * df[j] * ltl + f * dlt;
+  }
+  R A = R(0), C = R(0), Bq[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    A += df[kk] * tv[1 + kk];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      C += T[1 + kk][1 + i] * dl[kk][i];
+      Bq[i] += dl[kk][i] * tv[1 + kk];
+    }
+  }
+  const R AfC = A + f * C;
+  // g^{00} = -(1+f), g^{0i} = f l_i; Q_0 = A + f C, Q_j = l_j (A + f C) + f B_j
+  R tg = -(R(1) + f) * AfC;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) tg += f * l[j] * (l[j] * AfC + f * Bq[j] - Sj[j]);
+  const R dla = -R(0.5) * (T[1][0] * df[0] + T[2][0] * df[1] + T[3][0] * df[2]) / (R(1) + f);
+  S[0] = R(0);
+  S[1] = Sj[0];
+  S[2] = Sj[1];
+  S[3] = Sj[2];
+  S[4] = m.alpha * (dla - tg);
+  (void)L4;
+}
+
+// a5 + a6: one thread per interior cell. Divergence of the face fluxes (CT fluxes for B),
+// sources, RK combination Unew = g0 U0 + g1 Ucur + beta dt L, con2prim warm-started from the
+// current primitives, floors, and the re-derived hydro state when a floor fired.
+template <int METRIC, class R, class T>
+__global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __restrict__ Fx,
+                                                const R* __restrict__ Fy, const R* __restrict__ Fz,
+                                                const R* __restrict__ E, StageArgs a, DevParams p) {
+  const long long n = p.isize;
+  const long long G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
+  const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
+  const double bdt = a.beta * dt;
+  unsigned int it_sum = 0, c_rho = 0, c_eps = 0, c_w = 0, c_nc = 0, c_bad = 0, it_max = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+    const long long g = gidx(p, i, j, k);
+    const double xc = p.x0[0] + (i + 0.5) * p.dx[0];
+    const double yc = p.x0[1] + (j + 0.5) * p.dx[1];
+    const double zc = p.x0[2] + (k + 0.5) * p.dx[2];
+    double Pc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Pc[q] = (double)P[q * G + g];
+    R L[NV];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const R div = (Fx[q * G + g + 1] - Fx[q * G + g]) * R(p.idx[0]) + (Fy[q * G + g + sy] - Fy[q * G + g]) * R(p.idx[1]) +
+                    (Fz[q * G + g + sz] - Fz[q * G + g]) * R(p.idx[2]);
+      L[q] = -div;
+    }
+    const R* Ex = E;
+    const R* Ey = E + G;
+    const R* Ez = E + 2 * G;
+    const R h = R(0.5);
+    // CT fluxes of B (normal components vanish)
+    const R FyBx_p = h * (Ez[g + sy] + Ez[g + sy + 1]), FyBx_m = h * (Ez[g] + Ez[g + 1]);
+    const R FzBx_p = -h * (Ey[g + sz] + Ey[g + sz + 1]), FzBx_m = -h * (Ey[g] + Ey[g + 1]);
+    const R FxBy_p = -h * (Ez[g + 1] + Ez[g + 1 + sy]), FxBy_m = -h * (Ez[g] + Ez[g + sy]);
+    const R FzBy_p = h * (Ex[g + sz] + Ex[g + sz + sy]), FzBy_m = h * (Ex[g] + Ex[g + sy]);
+    const R FxBz_p = h * (Ey[g + 1] + Ey[g + 1 + sz]), FxBz_m = h * (Ey[g] + Ey[g + sz]);
+    const R FyBz_p = -h * (Ex[g + sy] + Ex[g + sy + sz]), FyBz_m = -h * (Ex[g] + Ex[g + sz]);
+    L[5] = -((FyBx_p - FyBx_m) * R(p.idx[1]) + (FzBx_p - FzBx_m) * R(p.idx[2]));
+    L[6] = -((FxBy_p - FxBy_m) * R(p.idx[0]) + (FzBy_p - FzBy_m) * R(p.idx[2]));
+    L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
+    Metric<double> m;
+    double rks;
+    metric_at<double, METRIC>(p, xc, yc, zc, m, &rks);
+    if (METRIC == KERR_SCHILD) {
+      R Sr[5];
+      R Pr[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Pr[q] = R(Pc[q]);
+      Metric<R> mr;
+      metric_at<R, METRIC>(p, R(xc), R(yc), R(zc), mr);
+      ks_sources<R>(p, R(xc), R(yc), R(zc), Pr, mr, Sr);
+#pragma unroll
+      for (int q = 1; q < 5; ++q) L[q] += Sr[q];
+    }
+    double Un[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double u = a.g1 * a.Ucur[q * n + t];
+      if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
+      Un[q] = u + bdt * (double)L[q];
+    }
+    // a6: con2prim on the undensitized state, warm-started from the current primitives
+    const double isg = 1.0 / m.sqrtgam;
+    double Uc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
+    const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
+    double Pn[NV];
+    int iters;
+    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
+    st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
+    if (st) {
+      double U5[5];
+      prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Un[q] = U5[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
+    a.status[t] = (uint8_t)st;
+    it_sum += iters;
+    it_max = iters > (int)it_max ? iters : it_max;
+    c_rho += (st & ST_RHO_FLOOR) != 0;
+    c_eps += (st & ST_EPS_FLOOR) != 0;
+    c_w += (st & ST_W_CAP) != 0;
+    c_nc += (st & ST_NOT_CONVERGED) != 0;
+    c_bad += (st & ST_BAD_INPUT) != 0;
+  }
+  if (a.stats) {
+    // warp-level sums, one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      it_sum += __shfl_xor_sync(0xffffffffu, it_sum, o);
+      c_rho += __shfl_xor_sync(0xffffffffu, c_rho, o);
+      c_eps += __shfl_xor_sync(0xffffffffu, c_eps, o);
+      c_w += __shfl_xor_sync(0xffffffffu, c_w, o);
+      c_nc += __shfl_xor_sync(0xffffffffu, c_nc, o);
+      c_bad += __shfl_xor_sync(0xffffffffu, c_bad, o);
+      it_max = max(it_max, __shfl_xor_sync(0xffffffffu, it_max, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(a.stats + 0, (unsigned long long)it_sum);
+      if (c_rho) atomicAdd(a.stats + 1, (unsigned long long)c_rho);
+      if (c_eps) atomicAdd(a.stats + 2, (unsigned long long)c_eps);
+      if (c_w) atomicAdd(a.stats + 3, (unsigned long long)c_w);
+      if (c_nc) atomicAdd(a.stats + 4, (unsigned long long)c_nc);
+      if (c_bad) atomicAdd(a.stats + 5, (unsigned long long)c_bad);
+      atomicMax(a.stats + 6, (unsigned long long)it_max);
+    }
+  }
+}
+
+// Densitized conserved state of the interior from the primitives (set-up and checkpoint restore).
+template <int METRIC, class T>
+__global__ void k_prim2con(const T* __restrict__ P, double* __restrict__ U, DevParams p) {
+  const long long n = p.isize, G = p.gsize;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+    const long long g = gidx(p, i, j, k);
+    double Pc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Pc[q] = (double)P[q * G + g];
+    Metric<double> m;
+    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                              p.x0[2] + (k + 0.5) * p.dx[2], m);
+    double U5[5];
+    prim_to_cons5<double>(Pc, m, p.gamma_eos, U5);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q * n + t] = U5[q];
+#pragma unroll
+    for (int q = 5; q < NV; ++q) U[q * n + t] = m.sqrtgam * Pc[q];
+  }
+}
+
+// Flat-space con2prim over a batch: U, P are [8][n] (structure of arrays).
+// flags bit 0: use P as the warm start.
+static __global__ void k_c2p_batch(const double* __restrict__ U, double* __restrict__ P, uint8_t* __restrict__ status,
+                            int* __restrict__ iters_out, long long n, int flags, DevParams p,
+                            unsigned long long* stats) {
+  unsigned int it_sum = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    Metric<double> m;
+    metric_at<double, MINKOWSKI>(p, 0.0, 0.0, 0.0, m);
+    double Uc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Uc[q] = U[q * n + t];
+    double mu0 = -1.0;
+    if (flags & 1) {
+      double Pg[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Pg[q] = P[q * n + t];
+      mu0 = mu_of_prims<double>(Pg, m.gam, p.gamma_eos);
+    }
+    double Pn[NV];
+    int iters;
+    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
+    st |= apply_floors<MINKOWSKI>(p, m.gam, 1.0, Pn);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) P[q * n + t] = Pn[q];
+    if (status) status[t] = (uint8_t)st;
+    if (iters_out) iters_out[t] = iters;
+    it_sum += iters;
+  }
+  if (stats) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) it_sum += __shfl_xor_sync(0xffffffffu, it_sum, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(stats, (unsigned long long)it_sum);
+  }
+}
+
+template <class Tin, class Tout>
+__global__ void k_convert(const Tin* __restrict__ a, Tout* __restrict__ b, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    b[t] = (Tout)a[t];
+}
+
+}  // namespace grmhd

@@ -1,0 +1,36 @@
+// Internal launcher interface between the C-ABI layer and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grmhd_device.cuh"
+
+namespace grmhd {
+
+// Launchers for one arithmetic form. R is the flux/EMF type, T the storage type of P:
+// form 0 = all double, form 1 = mixed (float fluxes and P).
+struct FormLaunchers {
+  cudaError_t (*ghost)(const DevParams& p, void* P, cudaStream_t s);
+  cudaError_t (*flux)(const DevParams& p, const void* P, void* F, unsigned long long* ms, int d, int track,
+                      cudaStream_t s);
+  cudaError_t (*emf)(const DevParams& p, const void* Fx, const void* Fy, const void* Fz, void* E, cudaStream_t s);
+  cudaError_t (*update)(const DevParams& p, void* P, const void* Fx, const void* Fy, const void* Fz, const void* E,
+                        const StageArgs& a, cudaStream_t s);
+  cudaError_t (*prim2con)(const DevParams& p, const void* P, double* U, cudaStream_t s);
+  cudaError_t (*load_prims)(const DevParams& p, const double* src, void* P, cudaStream_t s);   // double -> storage
+  cudaError_t (*store_prims)(const DevParams& p, const void* P, double* dst, cudaStream_t s);  // storage -> double
+  int p_bytes;  // bytes per stored primitive
+  int r_bytes;  // bytes per flux / EMF value
+};
+
+const FormLaunchers& fp64_launchers();
+const FormLaunchers& mixed_launchers();
+
+cudaError_t launch_finalize_dt(const unsigned long long* ms, double* dt, const DevParams& p, cudaStream_t s);
+cudaError_t launch_c2p_batch(const double* U, double* P, uint8_t* status, int* iters, long long n, int flags,
+                             const DevParams& p, unsigned long long* stats, cudaStream_t s);
+
+int grid_for(long long n, int threads);
+
+}  // namespace grmhd

@@ -1,0 +1,80 @@
+// Mixed form of the stage kernels: reconstruction, Riemann fluxes, EMFs and sources in float with
+// P stored in float; the state accumulation and con2prim stay in double (inside k_update).
+#include "grmhd_kernels.cuh"
+#include "grmhd_launch.h"
+
+namespace grmhd {
+
+namespace {
+
+using R = float;
+using T = float;
+
+template <int METRIC>
+cudaError_t flux_m(const DevParams& p, const T* P, R* F, unsigned long long* ms, int d, int track, cudaStream_t s) {
+  const long long n = (long long)(p.nx + (d == 0 ? 1 : 2)) * (p.ny + (d == 1 ? 1 : 2)) * (p.nz + (d == 2 ? 1 : 2));
+  const int g = grid_for(n, 128);
+  switch (p.recon) {
+    case RECON_CONSTANT: k_flux<R, T, METRIC, RECON_CONSTANT><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    case RECON_PLM_MINMOD: k_flux<R, T, METRIC, RECON_PLM_MINMOD><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    case RECON_PLM_MC: k_flux<R, T, METRIC, RECON_PLM_MC><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    case RECON_WENO5Z: k_flux<R, T, METRIC, RECON_WENO5Z><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t ghost(const DevParams& p, void* P, cudaStream_t s) {
+  k_ghost_periodic<T><<<grid_for(p.gsize, 256), 256, 0, s>>>((T*)P, p);
+  return cudaGetLastError();
+}
+
+cudaError_t flux(const DevParams& p, const void* P, void* F, unsigned long long* ms, int d, int track, cudaStream_t s) {
+  return p.metric == KERR_SCHILD ? flux_m<KERR_SCHILD>(p, (const T*)P, (R*)F, ms, d, track, s)
+                                 : flux_m<MINKOWSKI>(p, (const T*)P, (R*)F, ms, d, track, s);
+}
+
+cudaError_t emf(const DevParams& p, const void* Fx, const void* Fy, const void* Fz, void* E, cudaStream_t s) {
+  const long long n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+  k_emf<R><<<grid_for(n, 256), 256, 0, s>>>((const R*)Fx, (const R*)Fy, (const R*)Fz, (R*)E, p);
+  return cudaGetLastError();
+}
+
+cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, const void* Fz, const void* E,
+                   const StageArgs& a, cudaStream_t s) {
+  const int g = grid_for(p.isize, 128);
+  if (p.metric == KERR_SCHILD)
+    k_update<KERR_SCHILD, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
+  else
+    k_update<MINKOWSKI, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
+  return cudaGetLastError();
+}
+
+cudaError_t prim2con(const DevParams& p, const void* P, double* U, cudaStream_t s) {
+  const int g = grid_for(p.isize, 128);
+  if (p.metric == KERR_SCHILD)
+    k_prim2con<KERR_SCHILD, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+  else
+    k_prim2con<MINKOWSKI, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+  return cudaGetLastError();
+}
+
+cudaError_t load_prims(const DevParams& p, const double* src, void* P, cudaStream_t s) {
+  const long long n = NV * p.gsize;
+  k_convert<double, float><<<grid_for(n, 256), 256, 0, s>>>(src, (float*)P, n);
+  return cudaGetLastError();
+}
+
+cudaError_t store_prims(const DevParams& p, const void* P, double* dst, cudaStream_t s) {
+  const long long n = NV * p.gsize;
+  k_convert<float, double><<<grid_for(n, 256), 256, 0, s>>>((const float*)P, dst, n);
+  return cudaGetLastError();
+}
+
+const FormLaunchers kMixed = {ghost, flux, emf, update, prim2con, load_prims, store_prims, 4, 4};
+
+}  // namespace
+
+const FormLaunchers& mixed_launchers() { return kMixed; }
+
+}  // namespace grmhd

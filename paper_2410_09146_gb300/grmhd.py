@@ -1,0 +1,224 @@
+"""Python binding of libgrmhd.so: argument marshalling only, same names as the C ABI (include/grmhd.h).
+
+Every step of the stage runs in the library's CUDA kernels; PyTorch only supplies the device
+workspace and the stream. There is no CPU fallback: if the library is missing or cannot be loaded,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgrmhd.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "grmhd.h")
+
+GRMHD_OK, GRMHD_E_INVALID, GRMHD_E_CUDA, GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED = 0, -1, -2, -3, -4
+GRMHD_HOST, GRMHD_DEVICE = 0, 1
+GRMHD_GET_PRIMS, GRMHD_GET_CONS, GRMHD_GET_STATUS, GRMHD_GET_STATS, GRMHD_GET_DT = 0, 1, 2, 3, 4
+RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3}
+RIEMANN = {"llf": 0, "hll": 1}
+METRIC = {"minkowski": 0, "kerr_schild": 1}
+BC = {"periodic": 0, "fixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+ST_RHO_FLOOR, ST_EPS_FLOOR, ST_W_CAP, ST_NOT_CONVERGED, ST_BAD_INPUT = 1, 2, 4, 8, 16
+
+
+class GrmhdError(RuntimeError):
+    pass
+
+
+class grmhd_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("ng", ctypes.c_int),
+        ("x0", ctypes.c_double * 3), ("dx", ctypes.c_double * 3),
+        ("metric", ctypes.c_int), ("spin", ctypes.c_double), ("mass", ctypes.c_double),
+        ("gamma_eos", ctypes.c_double),
+        ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("precision", ctypes.c_int), ("bc", ctypes.c_int),
+        ("rho_floor0", ctypes.c_double), ("eps_floor0", ctypes.c_double), ("floor_r_exp", ctypes.c_double),
+        ("w_max", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_max_iter", ctypes.c_int),
+        ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def exported_names():
+    """Function names declared in include/grmhd.h."""
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(grmhd_[a-z0-9_]+)\s*\(", src)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GrmhdError(f"{LIB_PATH} is not built: run paper_2410_09146_gb300.build.build() "
+                             "(the CUDA library has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, P = ctypes.c_void_p, ctypes.POINTER(grmhd_params)
+        L.grmhd_workspace_bytes.argtypes = [P]
+        L.grmhd_workspace_bytes.restype = ctypes.c_size_t
+        L.grmhd_create.argtypes = [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.grmhd_set_prims.argtypes = [vp, vp, ctypes.c_int]
+        L.grmhd_set_cons.argtypes = [vp, vp, ctypes.c_int]
+        L.grmhd_stage.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.grmhd_rk2_step.argtypes = [vp, ctypes.c_double]
+        L.grmhd_c2p.argtypes = [vp, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int]
+        L.grmhd_get.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+        L.grmhd_last_error.argtypes = [vp]
+        L.grmhd_last_error.restype = ctypes.c_char_p
+        L.grmhd_destroy.argtypes = [vp]
+        L.grmhd_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def params(setup) -> grmhd_params:
+    """Parameter struct from an ``inputs.Setup`` (or any object with the same fields)."""
+    p = grmhd_params()
+    p.nx, p.ny, p.nz = setup.n
+    p.ng = setup.ng
+    p.x0[:] = list(setup.x0)
+    p.dx[:] = list(setup.dx)
+    p.metric = METRIC[setup.metric]
+    p.spin, p.mass, p.gamma_eos = setup.spin, setup.mass, setup.gamma_eos
+    p.recon, p.riemann = RECON[setup.recon], RIEMANN[setup.riemann]
+    p.precision, p.bc = PRECISION[setup.precision], BC[setup.bc]
+    p.rho_floor0, p.eps_floor0, p.floor_r_exp, p.w_max = (setup.rho_floor0, setup.eps_floor0, setup.floor_r_exp,
+                                                          setup.w_max)
+    p.c2p_tol, p.c2p_max_iter, p.cfl, p.weno_eps = setup.c2p_tol, setup.c2p_max_iter, setup.cfl, setup.weno_eps
+    return p
+
+
+def _check(rc, ctx=None):
+    if rc != GRMHD_OK:
+        msg = lib().grmhd_last_error(ctx)
+        raise GrmhdError(f"libgrmhd error {rc}: {msg.decode() if msg else ''}")
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array (host) or a torch tensor (device)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data, GRMHD_HOST
+    assert a.is_contiguous()
+    return a.data_ptr(), (GRMHD_DEVICE if a.is_cuda else GRMHD_HOST)
+
+
+# ------------------------------------------------------------------ thin wrappers with the C names
+def grmhd_workspace_bytes(p: grmhd_params) -> int:
+    return int(lib().grmhd_workspace_bytes(ctypes.byref(p)))
+
+
+def grmhd_create(p: grmhd_params, workspace_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib().grmhd_create(ctypes.byref(p), ctypes.c_void_p(workspace_ptr), nbytes, ctypes.c_void_p(stream_ptr),
+                              ctypes.byref(out)))
+    return out.value
+
+
+def grmhd_set_prims(ctx: int, P) -> None:
+    ptr, where = _ptr(P)
+    _check(lib().grmhd_set_prims(ctx, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_set_cons(ctx: int, U) -> None:
+    ptr, where = _ptr(U)
+    _check(lib().grmhd_set_cons(ctx, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_stage(ctx: int, g0: float, g1: float, beta: float, dt: float) -> None:
+    _check(lib().grmhd_stage(ctx, g0, g1, beta, dt), ctx)
+
+
+def grmhd_rk2_step(ctx: int, dt: float) -> None:
+    _check(lib().grmhd_rk2_step(ctx, dt), ctx)
+
+
+def grmhd_c2p(ctx: int, n: int, U_ptr: int, P_ptr: int, status_ptr: int = 0, iters_ptr: int = 0,
+              flags: int = 0) -> None:
+    vp = ctypes.c_void_p
+    _check(lib().grmhd_c2p(ctx, n, vp(U_ptr), vp(P_ptr), vp(status_ptr or None), vp(iters_ptr or None), flags), ctx)
+
+
+def grmhd_get(ctx: int, what: int, dst) -> None:
+    ptr, where = _ptr(dst)
+    _check(lib().grmhd_get(ctx, what, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_destroy(ctx: int) -> None:
+    lib().grmhd_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience object
+class Context:
+    """One meshblock context: owns a torch workspace tensor and borrows a torch stream."""
+
+    def __init__(self, setup, device: int = 0, stream=None):
+        import torch
+        self.setup = setup
+        self.p = params(setup)
+        nbytes = grmhd_workspace_bytes(self.p)
+        if nbytes == 0 and setup.n != (0, 0, 0):
+            raise GrmhdError("invalid parameters: " + lib().grmhd_last_error(None).decode())
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        self.ws_ptr = (base + 255) // 256 * 256
+        self.ws_bytes = nbytes
+        self.ctx = grmhd_create(self.p, self.ws_ptr, nbytes, self.stream.cuda_stream)
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            grmhd_destroy(self.ctx)
+            self.ctx = None
+
+    def set_prims(self, P):
+        grmhd_set_prims(self.ctx, P)
+
+    def set_cons(self, U):
+        grmhd_set_cons(self.ctx, U)
+
+    def stage(self, g0, g1, beta, dt=0.0):
+        grmhd_stage(self.ctx, g0, g1, beta, dt)
+
+    def rk2_step(self, dt=0.0):
+        grmhd_rk2_step(self.ctx, dt)
+
+    def get(self, what, out=None):
+        s = self.setup
+        shapes = {GRMHD_GET_PRIMS: (s.prim_shape(), np.float64), GRMHD_GET_CONS: (s.cons_shape(), np.float64),
+                  GRMHD_GET_STATUS: (s.cons_shape()[1:], np.uint8), GRMHD_GET_STATS: ((8,), np.uint64),
+                  GRMHD_GET_DT: ((1,), np.float64)}
+        if out is None:
+            shape, dt = shapes[what]
+            out = np.empty(shape, dt)
+        grmhd_get(self.ctx, what, out)
+        return out
+
+    def prims(self):
+        return self.get(GRMHD_GET_PRIMS)
+
+    def cons(self):
+        return self.get(GRMHD_GET_CONS)
+
+    def status(self):
+        return self.get(GRMHD_GET_STATUS)
+
+    def stats(self):
+        return self.get(GRMHD_GET_STATS)
+
+    def dt(self):
+        return float(self.get(GRMHD_GET_DT)[0])
+
+    def c2p(self, U, P, status=None, iters=None, flags=0):
+        """Flat-space con2prim batch of torch device tensors U, P of shape [8][n] (float64)."""
+        n = U.shape[1]
+        grmhd_c2p(self.ctx, n, U.data_ptr(), P.data_ptr(), 0 if status is None else status.data_ptr(),
+                  0 if iters is None else iters.data_ptr(), flags)

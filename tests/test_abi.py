@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every entry point include/grmhd.h declares (no GPU needed).
+
+Only host-side entry points that touch no device run here: workspace sizing and parameter
+validation of grmhd_create.
+"""
+import ctypes
+
+import pytest
+
+from paper_2410_09146_gb300 import build as B
+from paper_2410_09146_gb300 import grmhd as G
+from paper_2410_09146_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return G.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = G.exported_names()
+    assert {"grmhd_create", "grmhd_set_prims", "grmhd_stage", "grmhd_c2p", "grmhd_get",
+            "grmhd_destroy", "grmhd_last_error", "grmhd_workspace_bytes"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_workspace_bytes_and_validation(lib):
+    s = I.kerr_schild_setup(16)
+    p = G.params(s)
+    nb = G.grmhd_workspace_bytes(p)
+    G_ = (16 + 8) ** 3
+    assert nb >= 8 * G_ * 8 + 3 * 8 * 16 ** 3 * 8 + 3 * 8 * G_ * 8
+    s.precision = "mixed"
+    assert G.grmhd_workspace_bytes(G.params(s)) < nb
+    bad = G.params(s)
+    bad.ng = 2
+    bad.recon = G.RECON["weno5z_aoah"]
+    assert G.grmhd_workspace_bytes(bad) == 0
+    out = ctypes.c_void_p()
+    rc = lib.grmhd_create(ctypes.byref(bad), None, 0, None, ctypes.byref(out))
+    assert rc == G.GRMHD_E_INVALID and out.value is None
+    assert b"ng" in lib.grmhd_last_error(None)
+    # too-small workspace is rejected before any device work
+    p2 = G.params(I.kerr_schild_setup(8))
+    rc = lib.grmhd_create(ctypes.byref(p2), ctypes.c_void_p(256), 16, None, ctypes.byref(out))
+    assert rc == G.GRMHD_E_WORKSPACE
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """Every field offset of the ctypes mirror equals the C compiler's offsetof on include/grmhd.h."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    names = [f[0] for f in G.grmhd_params._fields_]
+    body = "".join(f'printf("%zu\\n", offsetof(grmhd_params, {n}));' for n in names)
+    src = tmp_path / "layout.c"
+    src.write_text(f'#include "{G.HEADER}"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   f'int main(void){{printf("%zu\\n", sizeof(grmhd_params));{body}return 0;}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
+    vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(G.grmhd_params)
+    assert vals[1:] == [getattr(G.grmhd_params, n).offset for n in names]

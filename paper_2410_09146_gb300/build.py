@@ -11,7 +11,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgrmhd.so")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["grmhd_api.cu", "grmhd_fp64.cu", "grmhd_mixed.cu"]
+SOURCES = ["grmhd_api.cu", "grmhd_fp64.cu", "grmhd_mixed.cu", "grmhd_batch.cu"]
+# The all-FP64 stage kernels round every double operation separately, as the FP64 reference does.
+PER_SOURCE_FLAGS = {"grmhd_fp64.cu": ["-fmad=false"]}
 HEADERS = ["grmhd_device.cuh", "grmhd_kernels.cuh", "grmhd_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
@@ -42,7 +44,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + deps_common):
-            cmd = [nvcc(), *ARCH, *FLAGS, *extra_flags, "-c", s, "-o", o]
+            cmd = [nvcc(), *ARCH, *FLAGS, *PER_SOURCE_FLAGS.get(src, []), *extra_flags, "-c", s, "-o", o]
             jobs.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

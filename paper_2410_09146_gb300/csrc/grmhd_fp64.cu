@@ -1,23 +1,9 @@
-// All-FP64 form of the stage kernels (every step in double precision) and the shared launchers.
+// All-FP64 form of the stage kernels (every step in double precision). Built without FMA
+// contraction (-fmad=false) so that every double operation rounds as the FP64 reference does.
 #include "grmhd_kernels.cuh"
 #include "grmhd_launch.h"
 
 namespace grmhd {
-
-int grid_for(long long n, int threads) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  long long b = (n + threads - 1) / threads;
-  const long long cap = (long long)sms * 16;
-  if (b > cap) b = cap;
-  if (b < 1) b = 1;
-  return (int)b;
-}
 
 namespace {
 
@@ -86,17 +72,5 @@ const FormLaunchers kFp64 = {ghost, flux, emf, update, prim2con, load_prims, sto
 }  // namespace
 
 const FormLaunchers& fp64_launchers() { return kFp64; }
-
-cudaError_t launch_finalize_dt(const unsigned long long* ms, double* dt, const DevParams& p, cudaStream_t s) {
-  k_finalize_dt<<<1, 32, 0, s>>>(ms, dt, p);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_c2p_batch(const double* U, double* P, uint8_t* status, int* iters, long long n, int flags,
-                             const DevParams& p, unsigned long long* stats, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  k_c2p_batch<<<grid_for(n, 128), 128, 0, s>>>(U, P, status, iters, n, flags, p, stats);
-  return cudaGetLastError();
-}
 
 }  // namespace grmhd

@@ -81,20 +81,24 @@ def interior_points(s):
     return np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
 
 
-def c2p_condition(orc, p, xyz, U, sg, rel=1e-9, seed=0):
-    """Per-cell con2prim condition number: scaled primitive change / relative change of U."""
+def c2p_condition(orc, p, xyz, U, sg, rel=1e-9, seed=0, ndir=3):
+    """Per-cell con2prim condition number: the largest scaled primitive change over `ndir` random sign
+    perturbations of relative size `rel` of the conserved state, divided by `rel`."""
     Un = U.reshape(8, -1).T.copy()
     P0, _, _ = orc.c2p_points(p, xyz, Un, floors=False)
-    r = np.random.default_rng(seed).choice([-1.0, 1.0], size=Un.shape)
-    P1, _, _ = orc.c2p_points(p, xyz, Un * (1.0 + rel * r), floors=False)
     shp = U.shape[1:]
-    a = np.zeros((8,) + tuple(d + 2 for d in shp))
-    b = np.zeros_like(a)
     inner = (slice(None),) + (slice(1, -1),) * 3
-    a[inner] = P1.T.reshape((8,) + shp)
+    b = np.zeros((8,) + tuple(d + 2 for d in shp))
     b[inner] = P0.T.reshape((8,) + shp)
-    e = rel_err_prims(a, b, U, sg, 1)
-    return np.max(e, axis=0) / rel
+    rng = np.random.default_rng(seed)
+    kappa = np.zeros(shp)
+    for _ in range(ndir):
+        r = rng.choice([-1.0, 1.0], size=Un.shape)
+        P1, _, _ = orc.c2p_points(p, xyz, Un * (1.0 + rel * r), floors=False)
+        a = np.zeros_like(b)
+        a[inner] = P1.T.reshape((8,) + shp)
+        kappa = np.maximum(kappa, np.max(rel_err_prims(a, b, U, sg, 1), axis=0) / rel)
+    return kappa
 
 
 def compare_stage(orc, s, p, P_in, U0, U_in, g0, g1, beta, dt, P_out, U_out, st_out, sg=None):

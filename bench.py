@@ -1,0 +1,366 @@
+"""Benchmark of the GRMHD Runge-Kutta stage on GB300: zone-updates/s per RK stage.
+
+One "step" is one Runge-Kutta stage (reconstruction, Riemann fluxes, CT, divergence + sources, RK
+combination, con2prim + floors, CFL reduction) over one meshblock. Default workload: the 256^3 Kerr-Schild
+(a = 0.9) block of seeded random primitives (rho log-uniform in [1e-6, 1], P = 0.01 rho^5/3, W to 10,
+sigma to 50; fixed ghosts), WENO5-Z-AOAH + HLL, in the mixed form (float reconstruction / fluxes / EMFs /
+sources, double accumulation and con2prim); the all-FP64 form of the same workload and the L1 distance
+between the two are reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--n 256] [--impl reference]
+
+Multi-GPU (torchrun): every rank advances its own independent block (seed + rank); there is no data-path
+collective, so the scaling is weak and the value is the sum of all ranks' zone updates over the slowest
+rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s per RK stage at 1 GB300 (mixed vs all-FP64, at stated L1 err)"
+UNIT = "zone-updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def workload(n, precision, rank=0):
+    from paper_2410_09146_gb300 import inputs as I
+    s = I.kerr_schild_setup(n, recon="weno5z_aoah", riemann="hll", precision=precision)
+    return s, 2 + rank
+
+
+def stage_coeffs(k):
+    return (0.0, 1.0, 1.0) if k % 2 == 0 else (0.5, 0.5, 0.5)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        load = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- our arm
+def time_stages(ctx, k0, n_stages):
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for k in range(n_stages):
+        g0, g1, b = stage_coeffs(k0 + k)
+        ctx.stage(g0, g1, b, 0.0)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2410_09146_gb300 import build as B
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2410_09146_gb300 import grmhd as G
+    from paper_2410_09146_gb300 import inputs as I
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    s_mix, seed = workload(n, "mixed", rank)
+    P = I.kerr_schild_random_prims(s_mix, seed=seed)
+    cells = n ** 3
+    # ---- mixed form: warm-up, timed region (device events, clocks sampled)
+    ctx = G.Context(s_mix)
+    ctx.set_prims(P)
+    for k in range(args.warmup):
+        ctx.stage(*stage_coeffs(k), 0.0)
+    k0 = args.warmup + (args.warmup % 2)
+    if args.warmup % 2:
+        ctx.stage(*stage_coeffs(args.warmup), 0.0)
+    barrier()
+    with ClockSampler(local) as clk:
+        ms = time_stages(ctx, k0, args.steps)
+        barrier()
+    ms = max_over_ranks(ms)
+    clocks = clk.summary()
+    stats = ctx.stats()
+    # ---- per-kernel timing pass (events around each kernel group, same stream)
+    ctx.set_timing(True)
+    time_stages(ctx, k0, min(args.steps, 8))
+    kt, kst = ctx.timing()
+    ctx.set_timing(False)
+    del ctx
+    torch.cuda.empty_cache()
+    # ---- end to end through the C ABI with pinned host buffers: H2D of P, stage, D2H of P
+    ctx = G.Context(s_mix)
+    Ph = torch.from_numpy(P).pin_memory()
+    Po = torch.empty_like(Ph).pin_memory()
+    ctx.set_prims(Ph)
+    ctx.stage(0.0, 1.0, 1.0, 0.0)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(2, min(args.steps, 6))
+    for k in range(e2e_steps):
+        ctx.set_prims(Ph)
+        ctx.stage(0.0, 1.0, 1.0, 0.0)
+        G.grmhd_get(ctx.ctx, G.GRMHD_GET_PRIMS, Po)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    del ctx
+    torch.cuda.empty_cache()
+    # ---- all-FP64 form of the same workload, and the L1 distance after one RK2 step
+    s64, _ = workload(n, "fp64", rank)
+    c64 = G.Context(s64)
+    c64.set_prims(P)
+    c64.rk2_step(0.0)
+    U64 = c64.cons()
+    P64 = c64.prims()
+    for k in range(2):
+        c64.stage(*stage_coeffs(k), 0.0)
+    barrier()
+    ms64 = time_stages(c64, 0, args.fp64_steps)
+    barrier()
+    ms64 = max_over_ranks(ms64)
+    del c64
+    torch.cuda.empty_cache()
+    cm = G.Context(s_mix)
+    cm.set_prims(P)
+    cm.rk2_step(0.0)
+    from tests.parity import l1_rel
+    ng = s_mix.ng
+    inner = (slice(None),) + (slice(ng, -ng),) * 3
+    l1u = l1_rel(cm.cons(), U64)
+    l1p = l1_rel(cm.prims()[inner], P64[inner])
+    del cm
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    per_stage = ms / args.steps
+    value = world * cells * args.steps / (ms / 1e3)
+    fp64_value = world * cells * args.fp64_steps / (ms64 / 1e3)
+    # dominant kernel group and its roofline
+    per_kernel = {k: v / max(kst, 1) for k, v in kt.items()}
+    dom = max(per_kernel, key=per_kernel.get)
+    peaks = measured_peaks()
+    roof = roofline(dom, per_kernel[dom], n, s_mix, stats, peaks)
+    G_cells = (n + 2 * s_mix.ng) ** 3
+    h2d = 8 * G_cells * 8
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_stage, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic (seeded random Kerr-Schild primitives)",
+        "config": {"workload": f"kerr_schild_random_{n}^3_weno5z_aoah_hll_mixed", "n": n, "ghosts": s_mix.ng,
+                   "metric": "kerr_schild a=0.9", "recon": "weno5z_aoah", "riemann": "hll", "precision": "mixed",
+                   "cfl": s_mix.cfl, "l2": f"state of {8 * G_cells * 4 / 1e9 + 24 * cells * 8 / 1e9:.1f} GB, "
+                   "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+        "fp64": {"value": fp64_value, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                 "speedup_mixed_over_fp64": value / fp64_value},
+        "l1_mixed_vs_fp64": {"after": "one RK2 step", "U": [float(x) for x in l1u], "P": [float(x) for x in l1p],
+                             "max": float(max(l1u.max(), l1p.max()))},
+        "c2p": {"iterations_per_cell": float(stats[0]) / cells, "eps_floor_cells": int(stats[2]),
+                "w_cap_cells": int(stats[3]), "max_iterations": int(stats[6])},
+        "kernels_ms_per_stage": per_kernel,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": h2d},
+        "gpu_launches": 5 * args.steps + (args.steps + 1) // 2,  # 3 flux + EMF + update per stage, CFL finalise per step
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(n_sample=80, n_stages=1)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(dom, ms, n, s, stats, peaks):
+    """Roofline of the dominant kernel group: HBM for the flux/EMF kernels (algorithmic bytes), FP64 ALU for
+    the update kernel (con2prim in double)."""
+    cells = n ** 3
+    hbm = peaks.get("hbm_gbs", 6786.6)
+    if dom == "update":
+        # algorithmic bytes of the update: read P (float), U0, Ucur, 6 face fluxes x 5 hydro + 12 EMFs (float),
+        # write Unew, P, status
+        bytes_cell = 8 * 4 + 2 * 64 + (6 * 5 + 12) * 4 + 64 + 32 + 1
+    elif dom.startswith("flux"):
+        bytes_cell = 8 * 4 * (1.0 + 6.0 / n) + 8 * 4 * (1.0 + 2.0 / n) ** 2  # read P, write one flux per face
+    else:
+        bytes_cell = 3 * 2 * 4 * 8 + 3 * 4
+    achieved = bytes_cell * cells / (ms / 1e3) / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "ms_per_launch": ms, "bytes_per_cell": bytes_cell,
+            "note": "measured peak (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+# ----------------------------------------------------------------------------- oracle baselines
+def _oracle_stage_worker(args):
+    n, seed = args
+    import oracle
+    from paper_2410_09146_gb300 import inputs as I
+    s = I.kerr_schild_setup(n, recon="weno5z_aoah", riemann="hll")
+    lo = 3.0 + (seed % 4) * 0.5
+    s.x0 = (lo, lo, lo)
+    p = oracle.params(s)
+    P = I.kerr_schild_random_prims(s, seed=seed)
+    U = oracle.prim2con_grid(p, P)
+    t = time.perf_counter()
+    oracle.stage(p, P, None, U, 0.0, 1.0, 1.0, 0.0)
+    return n ** 3, time.perf_counter() - t
+
+
+def cpu_baseline(n_sample=64, n_stages=1):
+    """The oracle as it stands, serial on one host core, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    zones, secs = 0, 0.0
+    for k in range(n_stages):
+        z, t = _oracle_stage_worker((n_sample, 2 + k))
+        zones += z
+        secs += t
+    return {"value": zones / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_stages} stage(s) of a {n_sample}^3 block of the same workload (FP64 oracle, serial)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on all host cores, each core one independent sample block per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n_sample = 40
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for w in range(args.warmup):
+            pool.map(_oracle_stage_worker, [(n_sample, 100 + w * cores + c) for c in range(cores)])
+        t0 = time.perf_counter()
+        zones = 0
+        for k in range(args.steps):
+            res = pool.map(_oracle_stage_worker, [(n_sample, 1000 + k * cores + c) for c in range(cores)])
+            zones += sum(r[0] for r in res)
+        secs = time.perf_counter() - t0
+    value = zones / secs
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded random Kerr-Schild primitives)",
+           "config": {"workload": f"kerr_schild_random_{args.n}^3_weno5z_aoah_hll_mixed",
+                      "sample": f"{cores} independent {n_sample}^3 blocks per step"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"per step, one RK stage of {cores} independent {n_sample}^3 blocks of the "
+                                      "same workload, one FP64 oracle process per core"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,17 @@ int grmhd_c2p(grmhd_ctx* c, long long n, const double* U, double* P, uint8_t* st
 /* Copy `what` (GRMHD_GET_*) to dst (`where` = GRMHD_HOST synchronises the stream). */
 int grmhd_get(grmhd_ctx* c, int what, void* dst, int where);
 
+/* Per-kernel timing (tracing aid, off by default): with `on` != 0 every later stage records CUDA events
+ * on the context's stream around its kernel groups. Creating the events is the only host-side cost;
+ * the records are asynchronous. */
+int grmhd_set_timing(grmhd_ctx* c, int on);
+
+/* Accumulated device milliseconds per kernel group since the last call, ms[6] = ghost fill, flux x,
+ * flux y, flux z (each including its share of the CFL reduction), EMF, update (divergence + sources +
+ * RK + con2prim + floors), and the number of stages they cover; resets the totals. Synchronises on
+ * the last recorded event. */
+int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
+
 /* Last error message of the context (or of the last failed grmhd_create when c is NULL). */
 const char* grmhd_last_error(const grmhd_ctx* c);
 

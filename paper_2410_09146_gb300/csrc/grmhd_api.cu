@@ -26,6 +26,11 @@ struct grmhd_ctx {
   unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats
   int s0, sc;                // slot of U0 and of the current state
   bool has_state;
+  bool timing;               // record CUDA events around each kernel group
+  cudaEvent_t ev[8];         // ghost | flux x | flux y | flux z | emf | update | end
+  double t_ms[6];            // accumulated ms per kernel group since the last read
+  int t_stages;              // stages accumulated
+  bool t_pending;            // events of the last stage not yet read
   char err[256];
 };
 
@@ -121,6 +126,22 @@ int fail(grmhd_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) 
   } while (0)
 
 bool batch_only(const grmhd_ctx* c) { return c->dp.isize == 0; }
+
+// Fold the events of the last timed stage into the per-kernel totals (synchronises on its last event).
+cudaError_t collect_timing(grmhd_ctx* c) {
+  if (!c->t_pending) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(c->ev[6]);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < 6; ++k) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]);
+    if (e != cudaSuccess) return e;
+    c->t_ms[k] += ms;
+  }
+  c->t_stages += 1;
+  c->t_pending = false;
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -231,15 +252,24 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   const bool track = auto_dt && first;
   const FormLaunchers& L = *c->L;
   const cudaStream_t s = c->stream;
+  if (c->timing) CK(collect_timing(c), "reading kernel timings");
+#define TMARK(k) \
+  if (c->timing) CK(cudaEventRecord(c->ev[k], s), "recording a timing event")
   unsigned long long* ms = c->scal;
   double* dt_dev = (double*)(c->scal + 3);
   unsigned long long* stats = c->scal + 8;
   CK(cudaMemsetAsync(stats, 0, 7 * sizeof(unsigned long long), s), "clearing stats");
   if (track) CK(cudaMemsetAsync(ms, 0, 3 * sizeof(unsigned long long), s), "clearing speeds");
+  TMARK(0);
   if (c->prm.bc == GRMHD_BC_PERIODIC) CK(L.ghost(c->dp, c->P, s), "ghost fill");
-  for (int d = 0; d < 3; ++d) CK(L.flux(c->dp, c->P, c->F[d], ms, d, track ? 1 : 0, s), "flux");
+  for (int d = 0; d < 3; ++d) {
+    TMARK(1 + d);
+    CK(L.flux(c->dp, c->P, c->F[d], ms, d, track ? 1 : 0, s), "flux");
+  }
   if (track) CK(launch_finalize_dt(ms, dt_dev, c->dp, s), "time step");
+  TMARK(4);
   CK(L.emf(c->dp, c->F[0], c->F[1], c->F[2], c->E, s), "EMF");
+  TMARK(5);
   StageArgs a;
   a.U0 = c->Uslot[c->s0];
   a.Ucur = c->Uslot[c->sc];
@@ -253,6 +283,9 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   a.dt = dt;
   a.use_dev_dt = auto_dt ? 1 : 0;
   CK(L.update(c->dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
+  TMARK(6);
+#undef TMARK
+  if (c->timing) c->t_pending = true;
   c->sc = dst;
   return GRMHD_OK;
 }
@@ -311,8 +344,37 @@ int grmhd_get(grmhd_ctx* c, int what, void* dst, int where) {
   return GRMHD_OK;
 }
 
+int grmhd_set_timing(grmhd_ctx* c, int on) {
+  if (!c) return GRMHD_E_INVALID;
+  if (on && !c->timing) {
+    for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&c->ev[k]), "creating timing events");
+  }
+  if (!on && c->timing) {
+    CK(collect_timing(c), "reading kernel timings");
+    for (int k = 0; k < 7; ++k) cudaEventDestroy(c->ev[k]);
+  }
+  c->timing = on != 0;
+  return GRMHD_OK;
+}
+
+int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages) {
+  if (!c || !ms) return GRMHD_E_INVALID;
+  if (c->timing) CK(collect_timing(c), "reading kernel timings");
+  for (int k = 0; k < 6; ++k) {
+    ms[k] = c->t_ms[k];
+    c->t_ms[k] = 0.0;
+  }
+  if (stages) *stages = c->t_stages;
+  c->t_stages = 0;
+  return GRMHD_OK;
+}
+
 const char* grmhd_last_error(const grmhd_ctx* c) { return c ? c->err : g_create_err; }
 
-void grmhd_destroy(grmhd_ctx* c) { delete c; }
+void grmhd_destroy(grmhd_ctx* c) {
+  if (c && c->timing)
+    for (int k = 0; k < 7; ++k) cudaEventDestroy(c->ev[k]);
+  delete c;
+}
 
 }  // extern "C"

@@ -322,58 +322,75 @@ __device__ __forceinline__ R riemann_flux(int riemann, const FaceSide<R>& L, con
 // mu = 1/(h W) is the root of f(mu) = mu - 1/(nu(mu) + mu rbar^2(mu)) in [0, mu_+], mu_+ the root
 // of mu^2 (1 + rbar^2(mu)) = 1 (h0 = 1 for the ideal gas). Solved by a bracketed Newton iteration
 // whose derivative comes from forward-mode dual numbers, warm-started from the previous primitives.
+// The all-FP64 form iterates in double; the mixed form iterates in float and finishes with one
+// double Newton step (quadratic convergence turns the float root into a double one), falling back
+// to the double iteration when the float phase does not settle.
+template <class T>
 struct Dual {
-  double v, d;
+  T v, d;
 };
-__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-__device__ __forceinline__ Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
-__device__ __forceinline__ Dual operator+(double a, Dual b) { return {a + b.v, b.d}; }
-__device__ __forceinline__ Dual operator-(double a, Dual b) { return {a - b.v, -b.d}; }
-__device__ __forceinline__ Dual drcp(Dual a) {
-  const double r = 1.0 / a.v;
+template <class T>
+__device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> operator+(T a, Dual<T> b) { return {a + b.v, b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return {a - b.v, -b.d}; }
+template <class T>
+__device__ __forceinline__ Dual<T> drcp(Dual<T> a) {
+  const T r = T(1) / a.v;
   return {r, -a.d * r * r};
 }
-__device__ __forceinline__ Dual dsqrt(Dual a) {
-  const double s = sqrt(a.v);
-  return {s, a.d * 0.5 / s};
+template <class T>
+__device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
+  const T s = sqrt(a.v);
+  return {s, a.d * T(0.5) / s};
 }
 
+template <class T>
 struct C2PIn {
-  double D, q, r2, b2, rb, rb2, gm1, v0sq;
+  T D, q, r2, b2, rb, rb2, gm1, v0sq;
 };
 
-__device__ __forceinline__ double c2p_rbar2(const C2PIn& c, double mu, double& x) {
-  x = 1.0 / (1.0 + mu * c.b2);
-  return x * x * c.r2 + mu * x * (1.0 + x) * c.rb2;
+template <class T>
+__device__ __forceinline__ T c2p_rbar2(const C2PIn<T>& c, T mu, T& x) {
+  x = T(1) / (T(1) + mu * c.b2);
+  return x * x * c.r2 + mu * x * (T(1) + x) * c.rb2;
 }
 
 // Master function value and derivative at mu; also the intermediate W, rho, eps and x.
+template <class T>
 struct C2PEval {
-  double f, df, x, W, rho, eps;
+  T f, df, x, W, rho, eps;
 };
 
-__device__ __forceinline__ C2PEval c2p_master(const C2PIn& c, double mu_v) {
-  const Dual mu = {mu_v, 1.0};
-  const Dual x = drcp(1.0 + c.b2 * mu);
-  const Dual rb = c.r2 * (x * x) + c.rb2 * (mu * x * (1.0 + x));
-  const Dual qbar = (c.q - 0.5 * c.b2) - (0.5 * (c.b2 * c.r2 - c.rb2)) * (mu * mu * x * x);
-  Dual vh2 = mu * mu * rb;
-  if (vh2.v > c.v0sq) vh2 = {c.v0sq, 0.0};
-  const Dual iW = dsqrt(1.0 - vh2);        // 1/W
-  const Dual W = drcp(iW);
-  const Dual rho = c.D * iW;
-  Dual eps = W * (qbar - mu * rb) + vh2 * W * W * drcp(1.0 + W);
-  if (eps.v < 0.0) eps = {0.0, 0.0};
+template <class T>
+__device__ __forceinline__ C2PEval<T> c2p_master(const C2PIn<T>& c, T mu_v) {
+  typedef Dual<T> D;
+  const D mu = {mu_v, T(1)};
+  const D x = drcp(T(1) + c.b2 * mu);
+  const D rb = c.r2 * (x * x) + c.rb2 * (mu * x * (T(1) + x));
+  const D qbar = (c.q - T(0.5) * c.b2) - (T(0.5) * (c.b2 * c.r2 - c.rb2)) * (mu * mu * x * x);
+  D vh2 = mu * mu * rb;
+  if (vh2.v > c.v0sq) vh2 = {c.v0sq, T(0)};
+  const D iW = dsqrt(T(1) - vh2);  // 1/W
+  const D W = drcp(iW);
+  const D rho = c.D * iW;
+  D eps = W * (qbar - mu * rb) + vh2 * W * W * drcp(T(1) + W);
+  if (eps.v < T(0)) eps = {T(0), T(0)};
   // a = P/(rho (1 + eps)) = (Gamma - 1) eps/(1 + eps) for the ideal gas
-  const Dual onepe = 1.0 + eps;
-  const Dual a = c.gm1 * eps * drcp(onepe);
-  const Dual nuA = (1.0 + a) * onepe * iW;
-  const Dual nuB = (1.0 + a) * (1.0 + qbar - mu * rb);
-  const Dual nu = nuA.v >= nuB.v ? nuA : nuB;
-  const Dual f = mu - drcp(nu + mu * rb);
-  C2PEval e;
+  const D onepe = T(1) + eps;
+  const D a = c.gm1 * eps * drcp(onepe);
+  const D nuA = (T(1) + a) * onepe * iW;
+  const D nuB = (T(1) + a) * (T(1) + qbar - mu * rb);
+  const D nu = nuA.v >= nuB.v ? nuA : nuB;
+  const D f = mu - drcp(nu + mu * rb);
+  C2PEval<T> e;
   e.f = f.v;
   e.df = f.d;
   e.x = x.v;
@@ -383,62 +400,88 @@ __device__ __forceinline__ C2PEval c2p_master(const C2PIn& c, double mu_v) {
   return e;
 }
 
-// Upper end of the bracket: root of g(mu) = mu^2 (1 + rbar^2(mu)) - 1 on (0, 1].
-__device__ __forceinline__ double c2p_mu_plus(const C2PIn& c) {
-  double x;
-  double g1 = 1.0 * (1.0 + c2p_rbar2(c, 1.0, x)) - 1.0;
-  if (!(g1 > 0.0)) return 1.0;
-  double lo = 0.0, hi = 1.0;
-  double mu = 1.0 / sqrt(1.0 + c.r2);  // root when b = 0
-  if (!(mu > lo && mu < hi)) mu = 0.5;
-  for (int it = 0; it < 60; ++it) {
-    const double xx = 1.0 / (1.0 + mu * c.b2);
-    const double dx = -c.b2 * xx * xx;
-    const double rb = xx * xx * c.r2 + mu * xx * (1.0 + xx) * c.rb2;
-    const double drb = 2.0 * xx * dx * c.r2 + c.rb2 * (xx * (1.0 + xx) + mu * dx * (1.0 + 2.0 * xx));
-    const double g = mu * mu * (1.0 + rb) - 1.0;
-    const double dg = 2.0 * mu * (1.0 + rb) + mu * mu * drb;
-    if (g < 0.0) lo = mu; else hi = mu;
-    double nmu = mu - g / dg;
-    if (!(nmu > lo && nmu < hi)) nmu = 0.5 * (lo + hi);
-    const bool done = fabs(nmu - mu) <= 1e-15 * nmu;
+// Upper end of the bracket: root of g(mu) = mu^2 (1 + rbar^2(mu)) - 1 on (0, 1], Newton safeguarded
+// by bisection, from `mu` (<= 0: the b = 0 root), to relative step `rtol`.
+template <class T>
+__device__ __forceinline__ T c2p_mu_plus(const C2PIn<T>& c, T mu, T rtol, int maxit) {
+  T x;
+  const T g1 = (T(1) + c2p_rbar2(c, T(1), x)) - T(1);
+  if (!(g1 > T(0))) return T(1);
+  T lo = T(0), hi = T(1);
+  if (!(mu > lo && mu < hi)) mu = T(1) / sqrt(T(1) + c.r2);
+  if (!(mu > lo && mu < hi)) mu = T(0.5);
+  for (int it = 0; it < maxit; ++it) {
+    const T xx = T(1) / (T(1) + mu * c.b2);
+    const T dx = -c.b2 * xx * xx;
+    const T rb = xx * xx * c.r2 + mu * xx * (T(1) + xx) * c.rb2;
+    const T drb = T(2) * xx * dx * c.r2 + c.rb2 * (xx * (T(1) + xx) + mu * dx * (T(1) + T(2) * xx));
+    const T g = mu * mu * (T(1) + rb) - T(1);
+    const T dg = T(2) * mu * (T(1) + rb) + mu * mu * drb;
+    if (g < T(0)) lo = mu; else hi = mu;
+    T nmu = mu - g / dg;
+    if (!(nmu > lo && nmu < hi)) nmu = T(0.5) * (lo + hi);
+    const bool done = fabs(nmu - mu) <= rtol * nmu;
     mu = nmu;
-    if (done || hi - lo <= 1e-15 * hi) break;
+    if (done || hi - lo <= rtol * hi) break;
   }
   return mu;
 }
 
-// Recover primitives from undensitized (D, S_j, tau, B^k). Returns the status bits of the solve
-// (0, ST_NOT_CONVERGED or ST_BAD_INPUT); floors are separate.
+// Bracketed Newton iteration on [0, mup] from mu (double or float). Returns 0 when converged (the
+// root, or mu_+ when f(mu_+) <= 0: the cold limit eps = 0), ST_NOT_CONVERGED otherwise.
+template <class T>
+__device__ __forceinline__ int c2p_newton(const C2PIn<T>& c, T mup, T& mu, T tol, int maxit, int& iters,
+                                          bool extra_step) {
+  T lo = T(0), hi = mup;
+  if (!(mu > lo && mu < hi)) mu = T(0.5) * mup;
+  for (int it = 0; it < maxit; ++it) {
+    const C2PEval<T> e = c2p_master(c, mu);
+    ++iters;
+    if (e.f == T(0) || (e.f < T(0) && mu == mup)) return 0;
+    if (e.f < T(0)) lo = mu; else hi = mu;
+    T nmu = mu - e.f / e.df;
+    if (!(nmu >= lo && nmu <= hi) || !(e.df > T(0)))
+      nmu = (nmu > hi && hi == mup && e.df > T(0)) ? mup : T(0.5) * (lo + hi);  // try the unevaluated end first
+    const bool conv = fabs(nmu - mu) <= tol * nmu;
+    mu = nmu;
+    if (conv) {
+      if (extra_step) {  // one more Newton step past the tolerance
+        const C2PEval<T> e2 = c2p_master(c, mu);
+        ++iters;
+        nmu = mu - e2.f / e2.df;
+        if (nmu >= lo && nmu <= hi && e2.df > T(0)) mu = nmu;
+      }
+      return 0;
+    }
+    if (hi - lo <= T(1e-16) * hi) return 0;
+  }
+  return ST_NOT_CONVERGED;
+}
+
+// Undensitized (D, S_j, tau, B^k) -> inputs of the master function. Returns ST_BAD_INPUT for
+// non-finite values or D <= 0.
 template <class R>
-__device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, const double Uc[NV],
-                                        double mu_guess, double Pout[NV], int& iters) {
-  iters = 0;
+__device__ __forceinline__ int c2p_setup(const DevParams& p, const Metric<R>& m, const double Uc[NV], C2PIn<double>& c,
+                                         double ru[3], double bu[3]) {
   bool finite = true;
 #pragma unroll
   for (int q = 0; q < NV; ++q) finite = finite && isfinite(Uc[q]);
-  if (!finite || !(Uc[0] > 0.0)) {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) Pout[q] = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) Pout[5 + k] = isfinite(Uc[5 + k]) ? Uc[5 + k] : 0.0;
-    return ST_BAD_INPUT;
-  }
+  if (!finite || !(Uc[0] > 0.0)) return ST_BAD_INPUT;
   double gam[6], gamu[6];
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
     gam[t] = (double)m.gam[t];
     gamu[t] = (double)m.gamu[t];
   }
-  C2PIn c;
   c.D = Uc[0];
   const double iD = 1.0 / c.D;
   c.q = Uc[4] * iD;
   const double rl[3] = {Uc[1] * iD, Uc[2] * iD, Uc[3] * iD};
-  double ru[3];
   lower3(gamu, rl, ru);
   const double isD = 1.0 / sqrt(c.D);
-  const double bu[3] = {Uc[5] * isD, Uc[6] * isD, Uc[7] * isD};
+  bu[0] = Uc[5] * isD;
+  bu[1] = Uc[6] * isD;
+  bu[2] = Uc[7] * isD;
   double bl[3];
   lower3(gam, bu, bl);
   c.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
@@ -447,42 +490,13 @@ __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, 
   c.rb2 = c.rb * c.rb;
   c.gm1 = p.gamma_eos - 1.0;
   c.v0sq = c.r2 / (1.0 + c.r2);
-  const double mup = c2p_mu_plus(c);
-  double lo = 0.0, hi = mup;
-  double mu = mu_guess;
-  if (!(mu > lo && mu < hi)) mu = 0.5 * mup;
-  int st = ST_NOT_CONVERGED;
-  C2PEval e;
-  const int maxit = p.c2p_max_iter;
-  for (int it = 0; it < maxit; ++it) {
-    e = c2p_master(c, mu);
-    ++iters;
-    if (e.f == 0.0 || (e.f < 0.0 && mu == mup)) {
-      // exact root, or f(mu_+) <= 0: the root sits on the bracket end (cold limit, eps = 0)
-      st = 0;
-      break;
-    }
-    if (e.f < 0.0) lo = mu; else hi = mu;
-    double nmu = mu - e.f / e.df;
-    if (!(nmu >= lo && nmu <= hi) || !(e.df > 0.0))
-      nmu = (nmu > hi && hi == mup && e.df > 0.0) ? mup : 0.5 * (lo + hi);  // try the unevaluated end first
-    const bool conv = fabs(nmu - mu) <= p.c2p_tol * nmu;
-    mu = nmu;
-    if (conv) {
-      // one more Newton step past the tolerance
-      e = c2p_master(c, mu);
-      ++iters;
-      nmu = mu - e.f / e.df;
-      if (nmu >= lo && nmu <= hi && e.df > 0.0) mu = nmu;
-      st = 0;
-      break;
-    }
-    if (hi - lo <= 1e-16 * hi) {
-      st = 0;
-      break;
-    }
-  }
-  e = c2p_master(c, mu);
+  return 0;
+}
+
+// Primitives at the root mu.
+__device__ __forceinline__ void c2p_output(const C2PIn<double>& c, double mu, const double ru[3], const double bu[3],
+                                           const double Uc[NV], double Pout[NV]) {
+  const C2PEval<double> e = c2p_master(c, mu);
   const double W = e.W;
   Pout[0] = e.rho;
   const double mx = mu * e.x;
@@ -491,6 +505,89 @@ __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, 
   Pout[4] = e.rho * e.eps;
 #pragma unroll
   for (int k = 0; k < 3; ++k) Pout[5 + k] = Uc[5 + k];
+}
+
+__device__ __forceinline__ void c2p_bad_output(const double Uc[NV], double Pout[NV]) {
+#pragma unroll
+  for (int q = 0; q < 5; ++q) Pout[q] = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Pout[5 + k] = isfinite(Uc[5 + k]) ? Uc[5 + k] : 0.0;
+}
+
+// All-FP64 con2prim: double Newton to |d mu| <= c2p_tol mu plus one more step. Returns the status
+// bits of the solve (0, ST_NOT_CONVERGED or ST_BAD_INPUT); floors are separate.
+template <class R>
+__device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, const double Uc[NV],
+                                        double mu_guess, double Pout[NV], int& iters) {
+  iters = 0;
+  C2PIn<double> c;
+  double ru[3], bu[3];
+  if (c2p_setup<R>(p, m, Uc, c, ru, bu)) {
+    c2p_bad_output(Uc, Pout);
+    return ST_BAD_INPUT;
+  }
+  const double mup = c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
+  double mu = mu_guess;
+  const int st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, iters, true);
+  c2p_output(c, mu, ru, bu, Uc, Pout);
+  return st;
+}
+
+// Mixed-form con2prim: the same root, iterated in float to a relative step of 2e-6, then one double
+// Newton step; double iteration only when the float phase fails or the double step is not small.
+template <class R>
+__device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R>& m, const double Uc[NV],
+                                              double mu_guess, double Pout[NV], int& iters) {
+  iters = 0;
+  C2PIn<double> c;
+  double ru[3], bu[3];
+  if (c2p_setup<R>(p, m, Uc, c, ru, bu)) {
+    c2p_bad_output(Uc, Pout);
+    return ST_BAD_INPUT;
+  }
+  C2PIn<float> cf;
+  cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
+  cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
+  const float mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
+  float muf = (float)mu_guess;
+  int itf = 0;
+  const int stf = c2p_newton<float>(cf, mupf, muf, 2e-6f, 24, itf, false);
+  iters = itf;
+  double mu = (double)muf;
+  bool done = false;
+  if (stf == 0 && isfinite(mu) && mu > 0.0) {
+    if (muf >= mupf) {
+      // float root on the bracket end (cold limit): settle mu_+ in double and test f there
+      const double mup = c2p_mu_plus<double>(c, (double)mupf, 1e-15, 8);
+      const C2PEval<double> e = c2p_master(c, mup);
+      ++iters;
+      if (!(e.f > 0.0)) {
+        mu = mup;
+        done = true;
+      } else {
+        mu = mup;
+      }
+    }
+    if (!done) {
+      const C2PEval<double> e = c2p_master(c, mu);
+      ++iters;
+      const double step = -e.f / e.df;
+      const double nmu = mu + step;
+      if (e.df > 0.0 && nmu > 0.0 && fabs(step) <= 1e-6 * nmu && nmu <= (double)mupf * (1.0 + 1e-5)) {
+        mu = nmu;
+        done = true;
+      }
+    }
+  }
+  int st = 0;
+  if (!done) {  // float phase did not settle: full double iteration
+    const double mup = c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
+    mu = mu_guess;
+    int it64 = 0;
+    st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, it64, true);
+    iters += it64;
+  }
+  c2p_output(c, mu, ru, bu, Uc, Pout);
   return st;
 }
 

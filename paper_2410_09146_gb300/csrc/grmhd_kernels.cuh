@@ -87,9 +87,11 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
         PR[q] = R(P[q * p.gsize + g]);
       }
     }
-    R xf[3] = {R(p.x0[0] + (i + 0.5) * p.dx[0]), R(p.x0[1] + (j + 0.5) * p.dx[1]), R(p.x0[2] + (k + 0.5) * p.dx[2])};
+    // face centre, in the flux arithmetic type
+    R xf[3] = {R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
+               R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2])};
     const int cd = d == 0 ? i : (d == 1 ? j : k);
-    xf[d] = R(p.x0[d] + cd * p.dx[d]);
+    xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
     Metric<R> m;
     metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
     FaceSide<R> L, Rs;
@@ -104,18 +106,18 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
     if (interior && cm > cm_local) cm_local = cm;
   }
   if (track_speed) {
-    double v = (double)cm_local;
+    R v = cm_local;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __shared__ double red[32];
+    __shared__ R red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) red[wid] = v;
     __syncthreads();
     if (wid == 0) {
-      v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+      v = lane < (int)(blockDim.x >> 5) ? red[lane] : R(0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0) atomic_max_pos(ms + d, v);
+      if (lane == 0) atomic_max_pos(ms + d, (double)v);
     }
   }
 }
@@ -326,7 +328,8 @@ __global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __re
     const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
     double Pn[NV];
     int iters;
-    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
+    int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters)
+                            : con2prim<double>(p, m, Uc, mu0, Pn, iters);
     st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
     if (st) {
       double U5[5];

@@ -70,6 +70,8 @@ def lib():
         L.grmhd_rk2_step.argtypes = [vp, ctypes.c_double]
         L.grmhd_c2p.argtypes = [vp, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int]
         L.grmhd_get.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+        L.grmhd_set_timing.argtypes = [vp, ctypes.c_int]
+        L.grmhd_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         L.grmhd_last_error.argtypes = [vp]
         L.grmhd_last_error.restype = ctypes.c_char_p
         L.grmhd_destroy.argtypes = [vp]
@@ -151,6 +153,20 @@ def grmhd_get(ctx: int, what: int, dst) -> None:
     _check(lib().grmhd_get(ctx, what, ctypes.c_void_p(ptr), where), ctx)
 
 
+def grmhd_set_timing(ctx: int, on: bool) -> None:
+    _check(lib().grmhd_set_timing(ctx, int(on)), ctx)
+
+
+KERNEL_GROUPS = ("ghost", "flux_x", "flux_y", "flux_z", "emf", "update")
+
+
+def grmhd_get_timing(ctx: int):
+    ms = (ctypes.c_double * 6)()
+    n = ctypes.c_int(0)
+    _check(lib().grmhd_get_timing(ctx, ms, ctypes.byref(n)), ctx)
+    return dict(zip(KERNEL_GROUPS, list(ms))), n.value
+
+
 def grmhd_destroy(ctx: int) -> None:
     lib().grmhd_destroy(ctx)
 
@@ -216,6 +232,13 @@ class Context:
 
     def dt(self):
         return float(self.get(GRMHD_GET_DT)[0])
+
+    def set_timing(self, on=True):
+        grmhd_set_timing(self.ctx, on)
+
+    def timing(self):
+        """(ms per kernel group accumulated since the last call, number of stages)."""
+        return grmhd_get_timing(self.ctx)
 
     def c2p(self, U, P, status=None, iters=None, flags=0):
         """Flat-space con2prim batch of torch device tensors U, P of shape [8][n] (float64)."""

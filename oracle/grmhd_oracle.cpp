@@ -543,7 +543,9 @@ static void con2prim_point(const orc_params& p, const Geom& G, const double* Uc,
   }
   c.rb2 = rb * rb;
   c.gm1 = p.gamma_eos - 1.0;
-  c.v0sq = c.r2 / (1.0 + c.r2);  // physical bound v^2 <= r^2/(h0^2 + r^2), h0 = 1
+  // Velocity bound inside the solve: the physical bound v^2 <= r^2/(h0^2 + r^2) (h0 = 1), and the
+  // Lorentz-factor ceiling v^2 <= 1 - 1/w_max^2 (reading: it keeps W(mu) bounded for unphysical states).
+  c.v0sq = std::min(c.r2 / (1.0 + c.r2), 1.0 - 1.0 / (p.w_max * p.w_max));
   // Upper bracket mu_+ from f_a on (0, 1/h0].
   double mup = 1.0;
   double fa1 = fa_of(c, 1.0);

@@ -417,9 +417,10 @@ __device__ __forceinline__ T c2p_mu_plus(const C2PIn<T>& c, T mu, T rtol, int ma
     const T drb = T(2) * xx * dx * c.r2 + c.rb2 * (xx * (T(1) + xx) + mu * dx * (T(1) + T(2) * xx));
     const T g = mu * mu * (T(1) + rb) - T(1);
     const T dg = T(2) * mu * (T(1) + rb) + mu * mu * drb;
+    if (g == T(0)) return mu;  // exact root
     if (g < T(0)) lo = mu; else hi = mu;
     T nmu = mu - g / dg;
-    if (!(nmu > lo && nmu < hi)) nmu = T(0.5) * (lo + hi);
+    if (!(nmu >= lo && nmu <= hi)) nmu = T(0.5) * (lo + hi);
     const bool done = fabs(nmu - mu) <= rtol * nmu;
     mu = nmu;
     if (done || hi - lo <= rtol * hi) break;
@@ -489,7 +490,8 @@ __device__ __forceinline__ int c2p_setup(const DevParams& p, const Metric<R>& m,
   c.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
   c.rb2 = c.rb * c.rb;
   c.gm1 = p.gamma_eos - 1.0;
-  c.v0sq = c.r2 / (1.0 + c.r2);
+  // velocity bound of the solve: physical bound r^2/(1 + r^2) and the Lorentz-factor ceiling
+  c.v0sq = fmin(c.r2 / (1.0 + c.r2), 1.0 - 1.0 / (p.w_max * p.w_max));
   return 0;
 }
 

@@ -72,7 +72,8 @@ extern "C" {
 #define GRMHD_GET_STATUS 2      /* uint8 [nz][ny][nx], last stage's con2prim/floor bits (GRMHD_ST_*) */
 #define GRMHD_GET_STATS 3       /* uint64 [8] of the last stage (or batch): con2prim iterations, cells with
                                    rho floor, eps floor, W cap, not converged, bad input, max iterations
-                                   of a cell, reserved (0) */
+                                   of a cell, cells the mixed form's float con2prim phase handed to the
+                                   double iteration */
 #define GRMHD_GET_DT 4          /* double [1]: the time step of the last first stage (CFL rule) */
 
 /* per-cell status bits */

@@ -23,7 +23,8 @@ struct grmhd_ctx {
   void* F[3];
   void* E;
   uint8_t* status;
-  unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats
+  int* worklist;             // mixed form: deferred con2prim cells (NULL in the FP64 form)
+  unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats, [16] worklist count
   int s0, sc;                // slot of U0 and of the current state
   bool has_state;
   bool timing;               // record CUDA events around each kernel group
@@ -42,7 +43,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t P, U[3], F[3], E, status, scal, total;
+  size_t P, U[3], F[3], E, status, worklist, scal, total;
 };
 
 bool valid_params(const grmhd_params* p, char* msg, size_t n) {
@@ -85,6 +86,7 @@ Layout layout_of(const grmhd_params* p) {
     for (int d = 0; d < 3; ++d) l.F[d] = take(8 * G * pb);
     l.E = take(3 * G * pb);
     l.status = take(I);
+    if (p->precision == GRMHD_MIXED) l.worklist = take(I * sizeof(int));
   }
   l.total = off;
   return l;
@@ -187,6 +189,7 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
     for (int d = 0; d < 3; ++d) c->F[d] = c->ws + l.F[d];
     c->E = c->ws + l.E;
     c->status = (uint8_t*)(c->ws + l.status);
+    c->worklist = p->precision == GRMHD_MIXED ? (int*)(c->ws + l.worklist) : nullptr;
   }
   c->s0 = c->sc = 0;
   c->has_state = false;
@@ -258,7 +261,7 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   unsigned long long* ms = c->scal;
   double* dt_dev = (double*)(c->scal + 3);
   unsigned long long* stats = c->scal + 8;
-  CK(cudaMemsetAsync(stats, 0, 7 * sizeof(unsigned long long), s), "clearing stats");
+  CK(cudaMemsetAsync(stats, 0, 9 * sizeof(unsigned long long), s), "clearing stats and the worklist count");
   if (track) CK(cudaMemsetAsync(ms, 0, 3 * sizeof(unsigned long long), s), "clearing speeds");
   TMARK(0);
   if (c->prm.bc == GRMHD_BC_PERIODIC) CK(L.ghost(c->dp, c->P, s), "ghost fill");
@@ -282,6 +285,8 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   a.beta = beta;
   a.dt = dt;
   a.use_dev_dt = auto_dt ? 1 : 0;
+  a.worklist = c->worklist;
+  a.wl_count = (unsigned int*)(c->scal + 16);
   CK(L.update(c->dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
   TMARK(6);
 #undef TMARK

@@ -46,6 +46,8 @@ struct StageArgs {
                                  // [5] bad input, [6] max iterations
   double g0, g1, beta, dt;
   int use_dev_dt;
+  int* worklist;                 // mixed form: cells whose float con2prim phase did not settle
+  unsigned int* wl_count;        // number of entries in worklist
 };
 
 
@@ -400,6 +402,28 @@ __device__ __forceinline__ C2PEval<T> c2p_master(const C2PIn<T>& c, T mu_v) {
   return e;
 }
 
+// Master-function intermediates without the derivative (final evaluation at the root).
+template <class T>
+__device__ __forceinline__ C2PEval<T> c2p_master_value(const C2PIn<T>& c, T mu) {
+  const T x = T(1) / (T(1) + c.b2 * mu);
+  const T rb = c.r2 * (x * x) + c.rb2 * (mu * x * (T(1) + x));
+  const T qbar = (c.q - T(0.5) * c.b2) - (T(0.5) * (c.b2 * c.r2 - c.rb2)) * (mu * mu * x * x);
+  T vh2 = mu * mu * rb;
+  if (vh2 > c.v0sq) vh2 = c.v0sq;
+  const T iW = sqrt(T(1) - vh2);
+  const T W = T(1) / iW;
+  T eps = W * (qbar - mu * rb) + vh2 * W * W / (T(1) + W);
+  if (eps < T(0)) eps = T(0);
+  C2PEval<T> e;
+  e.f = T(0);
+  e.df = T(0);
+  e.x = x;
+  e.W = W;
+  e.rho = c.D * iW;
+  e.eps = eps;
+  return e;
+}
+
 // Upper end of the bracket: root of g(mu) = mu^2 (1 + rbar^2(mu)) - 1 on (0, 1], Newton safeguarded
 // by bisection, from `mu` (<= 0: the b = 0 root), to relative step `rtol`.
 template <class T>
@@ -498,7 +522,7 @@ __device__ __forceinline__ int c2p_setup(const DevParams& p, const Metric<R>& m,
 // Primitives at the root mu.
 __device__ __forceinline__ void c2p_output(const C2PIn<double>& c, double mu, const double ru[3], const double bu[3],
                                            const double Uc[NV], double Pout[NV]) {
-  const C2PEval<double> e = c2p_master(c, mu);
+  const C2PEval<double> e = c2p_master_value(c, mu);
   const double W = e.W;
   Pout[0] = e.rho;
   const double mx = mu * e.x;
@@ -537,9 +561,11 @@ __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, 
 
 // Mixed-form con2prim: the same root, iterated in float to a relative step of 2e-6, then one double
 // Newton step; double iteration only when the float phase fails or the double step is not small.
+enum { C2P_DEFERRED = 256 };  // returned by con2prim_mixed(defer = true): the cell needs the double iteration
+
 template <class R>
 __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R>& m, const double Uc[NV],
-                                              double mu_guess, double Pout[NV], int& iters) {
+                                              double mu_guess, double Pout[NV], int& iters, bool defer = false) {
   iters = 0;
   C2PIn<double> c;
   double ru[3], bu[3];
@@ -582,6 +608,7 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
     }
   }
   int st = 0;
+  if (!done && defer) return C2P_DEFERRED;
   if (!done) {  // float phase did not settle: full double iteration
     const double mup = c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
     mu = mu_guess;

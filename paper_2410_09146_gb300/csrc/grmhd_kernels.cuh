@@ -328,8 +328,16 @@ __global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __re
     const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
     double Pn[NV];
     int iters;
-    int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters)
+    int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters, a.worklist != nullptr)
                             : con2prim<double>(p, m, Uc, mu0, Pn, iters);
+    if (st == C2P_DEFERRED) {
+      // finished by k_update_deferred: keep P (the warm start), store the new conserved state
+#pragma unroll
+      for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+      a.worklist[atomicAdd(a.wl_count, 1u)] = (int)t;
+      it_sum += iters;
+      continue;
+    }
     st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
     if (st) {
       double U5[5];
@@ -370,6 +378,73 @@ __global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __re
       if (c_nc) atomicAdd(a.stats + 4, (unsigned long long)c_nc);
       if (c_bad) atomicAdd(a.stats + 5, (unsigned long long)c_bad);
       atomicMax(a.stats + 6, (unsigned long long)it_max);
+    }
+  }
+}
+
+// Mixed form, second pass: cells whose float con2prim phase did not settle run the full double
+// iteration here, grouped so that a warp's lanes do the same work. Unew holds their conserved state.
+template <int METRIC, class T>
+__global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, StageArgs a, DevParams p) {
+  const long long n = p.isize, G = p.gsize;
+  const unsigned int cnt = *a.wl_count;
+  unsigned int it_sum = 0, c_rho = 0, c_eps = 0, c_w = 0, c_nc = 0, it_max = 0;
+  for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
+    const long long t = a.worklist[w];
+    const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+    const long long g = gidx(p, i, j, k);
+    Metric<double> m;
+    double rks;
+    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                              p.x0[2] + (k + 0.5) * p.dx[2], m, &rks);
+    double Pc[NV], Un[NV], Uc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      Pc[q] = (double)P[q * G + g];
+      Un[q] = a.Unew[q * n + t];
+    }
+    const double isg = 1.0 / m.sqrtgam;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
+    const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
+    double Pn[NV];
+    int iters;
+    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
+    st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
+    if (st) {
+      double U5[5];
+      prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) a.Unew[q * n + t] = U5[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
+    a.status[t] = (uint8_t)st;
+    it_sum += iters;
+    it_max = iters > (int)it_max ? iters : it_max;
+    c_rho += (st & ST_RHO_FLOOR) != 0;
+    c_eps += (st & ST_EPS_FLOOR) != 0;
+    c_w += (st & ST_W_CAP) != 0;
+    c_nc += (st & ST_NOT_CONVERGED) != 0;
+  }
+  if (a.stats) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      it_sum += __shfl_xor_sync(0xffffffffu, it_sum, o);
+      c_rho += __shfl_xor_sync(0xffffffffu, c_rho, o);
+      c_eps += __shfl_xor_sync(0xffffffffu, c_eps, o);
+      c_w += __shfl_xor_sync(0xffffffffu, c_w, o);
+      c_nc += __shfl_xor_sync(0xffffffffu, c_nc, o);
+      it_max = max(it_max, __shfl_xor_sync(0xffffffffu, it_max, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (it_sum) atomicAdd(a.stats + 0, (unsigned long long)it_sum);
+      if (c_rho) atomicAdd(a.stats + 1, (unsigned long long)c_rho);
+      if (c_eps) atomicAdd(a.stats + 2, (unsigned long long)c_eps);
+      if (c_w) atomicAdd(a.stats + 3, (unsigned long long)c_w);
+      if (c_nc) atomicAdd(a.stats + 4, (unsigned long long)c_nc);
+      atomicMax(a.stats + 6, (unsigned long long)it_max);
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
     }
   }
 }

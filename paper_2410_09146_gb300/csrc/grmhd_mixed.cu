@@ -47,6 +47,14 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
     k_update<KERR_SCHILD, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
   else
     k_update<MINKOWSKI, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.worklist == nullptr) return e;
+  // second pass over the cells whose float con2prim phase did not settle (count known on the device only)
+  const int g2 = grid_for(p.isize / 8 + 1, 128);
+  if (p.metric == KERR_SCHILD)
+    k_update_deferred<KERR_SCHILD, T><<<g2, 128, 0, s>>>((T*)P, a, p);
+  else
+    k_update_deferred<MINKOWSKI, T><<<g2, 128, 0, s>>>((T*)P, a, p);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,90 @@
+// Arithmetic-throughput probe: FP64 / FP32 FMA, add, mul, divide and square root on eight
+// independent chains per thread, 152 x 8 blocks of 256 threads. Prints operations per second.
+// The all-FP64 stage is bound by the FP64 pipe on GB300, and its roofline peak is this probe's
+// DFMA rate. Build and run:
+//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o probe_fp probe_fp_throughput.cu && ./probe_fp
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#define NCH 8
+
+template <int OP>
+__global__ void chains64(double* out, int iters, double s) {
+  double a[NCH];
+  for (int c = 0; c < NCH; ++c) a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      if (OP == 0) a[c] = fma(a[c], s, 1e-9);
+      else if (OP == 1) a[c] = a[c] + s;
+      else if (OP == 2) a[c] = a[c] * s;
+      else if (OP == 3) a[c] = 1.0 / a[c] + s;
+      else if (OP == 4) a[c] = sqrt(a[c]) + s;
+    }
+  }
+  double t = 0;
+  for (int c = 0; c < NCH; ++c) t += a[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;  // one slot per thread: grid * block entries
+}
+
+template <int OP>
+__global__ void chains32(float* out, int iters, float s) {
+  float a[NCH];
+  for (int c = 0; c < NCH; ++c) a[c] = 1.0f + 1e-3f * (threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      if (OP == 0) a[c] = fmaf(a[c], s, 1e-9f);
+      else if (OP == 3) a[c] = 1.0f / a[c] + s;
+      else if (OP == 4) a[c] = sqrtf(a[c]) + s;
+    }
+  }
+  float t = 0;
+  for (int c = 0; c < NCH; ++c) t += a[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+template <typename K, typename T>
+static void timed(const char* name, K kern, T* buf, int iters, T s, int blocks, int threads, double flop_per_op) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  kern<<<blocks, threads>>>(buf, iters, s);  // warm-up
+  cudaDeviceSynchronize();
+  cudaEventRecord(e0);
+  kern<<<blocks, threads>>>(buf, iters, s);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  const double ops = (double)blocks * threads * iters * NCH;
+  printf("%-10s %8.3f ms  %10.3f Gop/s  (%.3f TFLOP/s at %.0f flop/op)\n", name, ms, ops / ms / 1e6,
+         ops * flop_per_op / ms / 1e9, flop_per_op);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+int main() {
+  const int blocks = 152 * 8, threads = 256;
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+  cudaMalloc(&d64, sizeof(double) * blocks * threads);
+  cudaMalloc(&d32, sizeof(float) * blocks * threads);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, 0);
+  printf("%s SMs=%d cc=%d.%d\n", prop.name, prop.multiProcessorCount, prop.major, prop.minor);
+  timed("dfma", chains64<0>, d64, 2000, 0.999999, blocks, threads, 2);
+  timed("dadd", chains64<1>, d64, 2000, 1e-12, blocks, threads, 1);
+  timed("dmul", chains64<2>, d64, 2000, 0.9999999, blocks, threads, 1);
+  timed("ddiv+add", chains64<3>, d64, 200, 1e-12, blocks, threads, 1);
+  timed("dsqrt+add", chains64<4>, d64, 200, 1e-12, blocks, threads, 1);
+  timed("ffma", chains32<0>, d32, 20000, 0.999999f, blocks, threads, 2);
+  timed("fdiv+add", chains32<3>, d32, 2000, 1e-7f, blocks, threads, 1);
+  timed("fsqrt+add", chains32<4>, d32, 2000, 1e-7f, blocks, threads, 1);
+  const cudaError_t e = cudaGetLastError();
+  printf("status %s\n", cudaGetErrorString(e));
+  cudaFree(d64);
+  cudaFree(d32);
+  return e == cudaSuccess ? 0 : 1;
+}

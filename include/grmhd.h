@@ -153,6 +153,29 @@ int grmhd_set_timing(grmhd_ctx* c, int on);
  * the last recorded event. */
 int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
 
+/* One all-FP64 Runge-Kutta stage, like grmhd_stage, for callers that cannot allocate device memory
+ * (code inside a CUDA-graph capture, hosts whose framework owns every device allocation, embedded
+ * hosts without a device allocator). The paper has no counterpart: this is a packaging of the same
+ * stage. No context and no workspace: the caller passes the state, all device pointers --
+ *   P      double [8][nz+2ng][ny+2ng][nx+2ng], primitives in; interior (and periodic ghosts) out
+ *   U0     double [8][nz][ny][nx], state at the start of the step (read only when g0 != 0)
+ *   Ucur   double [8][nz][ny][nx], the stage's input state
+ *   Unew   double [8][nz][ny][nx], the stage's output state (may not alias Ucur or U0)
+ *   status uint8  [nz][ny][nx]
+ * -- and the coefficients of Unew = g0 U0 + g1 Ucur + beta dt L(Ucur); dt <= 0 takes the CFL step of
+ * this call's face speeds. p->precision must be GRMHD_FP64.
+ * Scratch (face fluxes, edge EMFs, speed and time-step scalars) lives in a 16 MiB array of device
+ * memory built into the library (every GPU that loads the library holds it until the process exits),
+ * which bounds the block to (16 MiB - 512 B) / 216 B = 77,672 ghosted cells, e.g. 34^3 interior cells
+ * with 4 ghosts; larger blocks are rejected with GRMHD_E_INVALID and a message in
+ * grmhd_last_error(NULL). The first call on each device looks up the array's device address; make
+ * that first call before any stream capture. Every call shares the array and the array keeps the
+ * previous call's contents (the call clears what it accumulates into): calls that overlap on the GPU,
+ * on one stream or several, race on it. Asynchronous on `stream` (a cudaStream_t, NULL = default).
+ * Errors: GRMHD_E_INVALID, GRMHD_E_CUDA. */
+int grmhd_stage_noalloc(const grmhd_params* p, double* P, const double* U0, const double* Ucur, double* Unew,
+                        uint8_t* status, double g0, double g1, double beta, double dt, void* stream);
+
 /* Last error message of the context (or of the last failed grmhd_create when c is NULL). */
 const char* grmhd_last_error(const grmhd_ctx* c);
 

@@ -147,6 +147,10 @@ cudaError_t collect_timing(grmhd_ctx* c) {
 
 }  // namespace
 
+namespace grmhd {
+char* create_error_buffer() { return g_create_err; }
+}  // namespace grmhd
+
 extern "C" {
 
 size_t grmhd_workspace_bytes(const grmhd_params* p) {

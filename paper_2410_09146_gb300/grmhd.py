@@ -72,6 +72,8 @@ def lib():
         L.grmhd_get.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_set_timing.argtypes = [vp, ctypes.c_int]
         L.grmhd_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        L.grmhd_stage_noalloc.argtypes = [P, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, vp]
         L.grmhd_last_error.argtypes = [vp]
         L.grmhd_last_error.restype = ctypes.c_char_p
         L.grmhd_destroy.argtypes = [vp]
@@ -165,6 +167,14 @@ def grmhd_get_timing(ctx: int):
     n = ctypes.c_int(0)
     _check(lib().grmhd_get_timing(ctx, ms, ctypes.byref(n)), ctx)
     return dict(zip(KERNEL_GROUPS, list(ms))), n.value
+
+
+def grmhd_stage_noalloc(p: grmhd_params, P_ptr: int, U0_ptr: int, Ucur_ptr: int, Unew_ptr: int, status_ptr: int,
+                        g0: float, g1: float, beta: float, dt: float, stream_ptr: int = 0) -> None:
+    """Allocation-free all-FP64 stage on caller-owned device arrays (see include/grmhd.h)."""
+    vp = ctypes.c_void_p
+    _check(lib().grmhd_stage_noalloc(ctypes.byref(p), vp(P_ptr), vp(U0_ptr or None), vp(Ucur_ptr), vp(Unew_ptr),
+                                     vp(status_ptr), g0, g1, beta, dt, vp(stream_ptr or None)))
 
 
 def grmhd_destroy(ctx: int) -> None:

@@ -118,6 +118,22 @@ def measured_peaks():
         return {}
 
 
+# ----------------------------------------------------------------------------- aggregation across ranks
+def aggregate(ms_local, zones_local, steps, dist=None, device=None):
+    """Whole-job throughput: the slowest rank's time (max over ranks) and the sum of all ranks' zone
+    updates. Returns (value in zone-updates/s, max ms, world size)."""
+    if dist is None or not dist.is_initialized():
+        return zones_local * steps / (ms_local / 1e3), ms_local, 1
+    import torch
+    t = torch.tensor([ms_local, float(zones_local)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    ms = float(mx[0])
+    return float(sm[1]) * steps / (ms / 1e3), ms, dist.get_world_size()
+
+
 # ----------------------------------------------------------------------------- our arm
 def time_stages(ctx, k0, n_stages):
     import torch

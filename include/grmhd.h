@@ -176,6 +176,46 @@ int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
 int grmhd_stage_noalloc(const grmhd_params* p, double* P, const double* U0, const double* Ucur, double* Unew,
                         uint8_t* status, double g0, double g1, double beta, double dt, void* stream);
 
+/* ---- Batches of meshblocks (many uneven blocks advanced together) ----
+ * A batch holds nblocks independent meshblocks that share the physics options of `p` (its nx..nz,
+ * x0, dx fields are ignored; each block brings its own). Ghost zones are taken as given
+ * (p->bc must be GRMHD_BC_FIXED; the exchange between blocks is not part of the stage). grmhd_stage and
+ * grmhd_rk2_step advance every block: each phase (fluxes of all directions, EMFs, cell update, deferred
+ * con2prim) is one persistent launch whose CTAs take fixed-size work items (`tile` faces, edges or
+ * cells of one block) from a device counter. With dt <= 0 the CFL step is the minimum over the batch. */
+typedef struct {
+  int nx, ny, nz;  /* interior cells */
+  double x0[3];    /* coordinate of the block's interior lower corner */
+  double dx[3];    /* cell widths */
+} grmhd_block;
+
+/* Workspace bytes of a batch (0 on invalid input). */
+size_t grmhd_batch_workspace_bytes(const grmhd_params* p, int nblocks, const grmhd_block* blocks);
+
+/* Create a batch context (workspace and stream borrowed as for grmhd_create); the tile starts at 512.
+ * Errors: GRMHD_E_INVALID, GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED (periodic blocks), GRMHD_E_CUDA. */
+int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* blocks, void* workspace, size_t bytes,
+                       void* stream, grmhd_ctx** out);
+
+/* Load one block's primitives (double, [8][nz+2ng][ny+2ng][nx+2ng]) and derive its conserved state;
+ * every block must be loaded before the first stage. */
+int grmhd_batch_set_prims(grmhd_ctx* c, int block, const double* P, int where);
+
+/* grmhd_get for one block (PRIMS, CONS, STATUS); STATS and DT are batch-wide. */
+int grmhd_batch_get(grmhd_ctx* c, int block, int what, void* dst, int where);
+
+/* Work-item size in faces / edges / cells (128 .. 2^20); results do not depend on it. */
+int grmhd_batch_set_tile(grmhd_ctx* c, int tile);
+
+/* Time tiles 128 .. 4096 with one real RK2 step each (the batch advances by 6 steps with the CFL time
+ * step) and keep the fastest; returns it and its milliseconds per stage (either pointer may be NULL). */
+int grmhd_batch_autotune(grmhd_ctx* c, int* best_tile, double* best_ms);
+
+/* Batch contexts only: with `on` != 0 each distinct stage (coefficients, dt, state slots, tile) is
+ * captured once into a CUDA graph on a library-owned capture stream and replayed on the context's
+ * stream afterwards. Timing events are not recorded in graph mode. */
+int grmhd_set_graph(grmhd_ctx* c, int on);
+
 /* Last error message of the context (or of the last failed grmhd_create when c is NULL). */
 const char* grmhd_last_error(const grmhd_ctx* c);
 

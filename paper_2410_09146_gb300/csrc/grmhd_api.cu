@@ -3,7 +3,9 @@
 
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <vector>
 
 #include "../../include/grmhd.h"
 #include "grmhd_device.cuh"
@@ -32,6 +34,19 @@ struct grmhd_ctx {
   double t_ms[6];            // accumulated ms per kernel group since the last read
   int t_stages;              // stages accumulated
   bool t_pending;            // events of the last stage not yet read
+  // batch of meshblocks (nblocks == 0: a single-block context)
+  int nblocks;
+  std::vector<BlockDesc> hblocks;
+  BlockDesc* dblocks;
+  WorkItem* ditems;
+  long long max_items;
+  int n_items[3];            // flux | EMF | update items at the current tile
+  int tile;
+  int grid_persist;
+  long long total_cells;
+  bool use_graph;
+  cudaStream_t cap_stream;
+  std::map<std::vector<double>, cudaGraphExec_t> graphs;
   char err[256];
 };
 
@@ -145,6 +160,104 @@ cudaError_t collect_timing(grmhd_ctx* c) {
   return cudaSuccess;
 }
 
+constexpr int kMinTile = 128;
+
+long long block_items(const DevParams& p, int tile, int phase) {
+  long long n;
+  if (phase < 3) {
+    int ex, ey;
+    n = face_box(p, phase, ex, ey);
+  } else if (phase == 3) {
+    n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+  } else {
+    n = p.isize;
+  }
+  return (n + tile - 1) / tile;
+}
+
+std::vector<WorkItem> build_items(const std::vector<BlockDesc>& blocks, int tile, int counts[3]) {
+  std::vector<WorkItem> v[3];
+  for (int b = 0; b < (int)blocks.size(); ++b) {
+    const DevParams& p = blocks[b].p;
+    for (int phase = 0; phase < 5; ++phase) {
+      long long n;
+      if (phase < 3) {
+        int ex, ey;
+        n = face_box(p, phase, ex, ey);
+      } else if (phase == 3) {
+        n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+      } else {
+        n = p.isize;
+      }
+      const int list = phase < 3 ? 0 : phase - 2;
+      for (long long s = 0; s < n; s += tile) {
+        WorkItem w;
+        w.block = b;
+        w.phase = phase;
+        w.start = s;
+        w.count = (int)std::min<long long>(tile, n - s);
+        w.pad = 0;
+        v[list].push_back(w);
+      }
+    }
+  }
+  std::vector<WorkItem> all;
+  for (int l = 0; l < 3; ++l) {
+    counts[l] = (int)v[l].size();
+    all.insert(all.end(), v[l].begin(), v[l].end());
+  }
+  return all;
+}
+
+struct BatchLayout {
+  size_t scal, blocks, items, worklist, total;
+  std::vector<size_t> P, U, F, E, status;  // per block; U and F hold 3 consecutive regions
+};
+
+bool valid_block(const grmhd_block& b, int ng, char* msg, size_t n) {
+  if (b.nx < 1 || b.ny < 1 || b.nz < 1) { snprintf(msg, n, "block sizes must be >= 1"); return false; }
+  if (!(b.dx[0] > 0 && b.dx[1] > 0 && b.dx[2] > 0)) { snprintf(msg, n, "block cell widths must be > 0"); return false; }
+  const double cells = (double)(b.nx + 2 * ng) * (b.ny + 2 * ng) * (b.nz + 2 * ng);
+  if (cells > 2.0e9) { snprintf(msg, n, "block too large"); return false; }
+  return true;
+}
+
+DevParams block_params(const grmhd_params* p, const grmhd_block& b) {
+  grmhd_params q = *p;
+  q.nx = b.nx; q.ny = b.ny; q.nz = b.nz;
+  for (int i = 0; i < 3; ++i) { q.x0[i] = b.x0[i]; q.dx[i] = b.dx[i]; }
+  return dev_params(&q);
+}
+
+BatchLayout batch_layout(const grmhd_params* p, int nblocks, const grmhd_block* blocks) {
+  BatchLayout l;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  const size_t pb = p->precision == GRMHD_MIXED ? 4 : 8;
+  l.scal = take(64 * sizeof(unsigned long long));
+  l.blocks = take(sizeof(BlockDesc) * (size_t)nblocks);
+  long long items = 0, cells = 0;
+  std::vector<BlockDesc> tmp(nblocks);
+  for (int b = 0; b < nblocks; ++b) {
+    const DevParams d = block_params(p, blocks[b]);
+    for (int phase = 0; phase < 5; ++phase) items += block_items(d, kMinTile, phase);
+    cells += d.isize;
+  }
+  l.items = take(sizeof(WorkItem) * (size_t)items);
+  for (int b = 0; b < nblocks; ++b) {
+    const DevParams d = block_params(p, blocks[b]);
+    const size_t G = (size_t)d.gsize, I = (size_t)d.isize;
+    l.P.push_back(take(8 * G * pb));
+    for (int s = 0; s < 3; ++s) l.U.push_back(take(8 * I * sizeof(double)));
+    for (int k = 0; k < 3; ++k) l.F.push_back(take(8 * G * pb));
+    l.E.push_back(take(3 * G * pb));
+    l.status.push_back(take(I));
+  }
+  l.worklist = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(int)) : 0;
+  l.total = off;
+  return l;
+}
+
 }  // namespace
 
 namespace grmhd {
@@ -209,6 +322,7 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
 
 int grmhd_set_prims(grmhd_ctx* c, const double* P, int where) {
   if (!c || !P) return c ? fail(c, GRMHD_E_INVALID, "P is NULL") : GRMHD_E_INVALID;
+  if (c->nblocks > 0) return fail(c, GRMHD_E_INVALID, "batch context: use grmhd_batch_set_prims");
   if (batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no grid");
   const size_t bytes = sizeof(double) * NV * (size_t)c->dp.gsize;
   const double* src = P;
@@ -230,6 +344,7 @@ int grmhd_set_prims(grmhd_ctx* c, const double* P, int where) {
 
 int grmhd_set_cons(grmhd_ctx* c, const double* U, int where) {
   if (!c || !U) return c ? fail(c, GRMHD_E_INVALID, "U is NULL") : GRMHD_E_INVALID;
+  if (c->nblocks > 0) return fail(c, GRMHD_E_INVALID, "not available for batch contexts");
   if (batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no grid");
   if (where != GRMHD_HOST && where != GRMHD_DEVICE) return fail(c, GRMHD_E_INVALID, "bad where");
   const size_t bytes = sizeof(double) * NV * (size_t)c->dp.isize;
@@ -241,8 +356,12 @@ int grmhd_set_cons(grmhd_ctx* c, const double* U, int where) {
   return GRMHD_OK;
 }
 
+static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt);
+static int grmhd_get_scalars(grmhd_ctx* c, int what, void* dst, int where);
+
 int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   if (!c) return GRMHD_E_INVALID;
+  if (c->nblocks > 0) return batch_stage(c, g0, g1, beta, dt);
   if (batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no grid");
   if (!c->has_state) return fail(c, GRMHD_E_INVALID, "grmhd_set_prims has not been called");
   if (!(g0 == g0) || !(g1 == g1) || !(beta == beta) || !(dt == dt)) return fail(c, GRMHD_E_INVALID, "NaN stage coefficient");
@@ -314,8 +433,89 @@ int grmhd_c2p(grmhd_ctx* c, long long n, const double* U, double* P, uint8_t* st
   return GRMHD_OK;
 }
 
+static int grmhd_get_scalars(grmhd_ctx* c, int what, void* dst, int where) {
+  const cudaMemcpyKind kind = where == GRMHD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (what == GRMHD_GET_STATS)
+    CK(cudaMemcpyAsync(dst, c->scal + 8, 8 * sizeof(unsigned long long), kind, c->stream), "copying stats");
+  else
+    CK(cudaMemcpyAsync(dst, c->scal + 3, sizeof(double), kind, c->stream), "copying dt");
+  if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
+  return GRMHD_OK;
+}
+
+// Enqueue one batched stage on stream s (slot indices, coefficients and dt already fixed).
+static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStream_t s) {
+  const FormLaunchers& L = *c->L;
+  unsigned long long* ms = c->scal;
+  unsigned int* ctr = (unsigned int*)(c->scal + 20);
+  CK(cudaMemsetAsync(c->scal + 8, 0, 9 * sizeof(unsigned long long), s), "clearing stats");
+  CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned int), s), "clearing work counters");
+  if (track) CK(cudaMemsetAsync(ms, 0, sizeof(unsigned long long), s), "clearing speeds");
+  const WorkItem* flux_items = c->ditems;
+  const WorkItem* emf_items = flux_items + c->n_items[0];
+  const WorkItem* upd_items = emf_items + c->n_items[1];
+  const int grid = c->grid_persist;
+  CK(L.batch_flux(c->dblocks, flux_items, c->n_items[0], ctr + 0, ms, track ? 1 : 0, c->prm.metric, c->prm.recon, grid, s),
+     "batched flux");
+  if (track) CK(launch_batch_finalize_dt(ms, (double*)(c->scal + 3), c->prm.cfl, s), "time step");
+  CK(L.batch_emf(c->dblocks, emf_items, c->n_items[1], ctr + 1, grid, s), "batched EMF");
+  CK(L.batch_update(c->dblocks, upd_items, c->n_items[2], ctr + 2, a, c->prm.metric, grid, s), "batched update");
+  if (c->worklist) CK(L.batch_deferred(c->dblocks, c->nblocks, a, c->prm.metric, grid, s), "batched deferred con2prim");
+  return GRMHD_OK;
+}
+
+static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
+  if (!c->has_state) return fail(c, GRMHD_E_INVALID, "grmhd_batch_set_prims has not been called");
+  if (!(g0 == g0) || !(g1 == g1) || !(beta == beta) || !(dt == dt)) return fail(c, GRMHD_E_INVALID, "NaN stage coefficient");
+  const bool first = g0 == 0.0;
+  if (!first && c->s0 == c->sc) return fail(c, GRMHD_E_INVALID, "a stage with g0 != 0 needs a preceding stage with g0 == 0");
+  const int s0 = first ? c->sc : c->s0;
+  const int dst = first ? (c->sc + 1) % 3 : 3 - c->s0 - c->sc;
+  const bool auto_dt = !(dt > 0.0);
+  const bool track = auto_dt && first;
+  BatchArgs a;
+  a.g0 = g0; a.g1 = g1; a.beta = beta; a.dt = dt;
+  a.use_dev_dt = auto_dt ? 1 : 0;
+  a.s0 = s0; a.sc = c->sc; a.dst = dst;
+  a.dt_dev = (const double*)(c->scal + 3);
+  a.stats = c->scal + 8;
+  a.worklist = c->worklist;
+  a.wl_count = (unsigned int*)(c->scal + 16);
+  if (c->use_graph) {
+    const std::vector<double> key = {g0, g1, beta, dt, (double)s0, (double)c->sc, (double)dst, (double)c->tile};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "starting the graph capture");
+      const int rc = batch_enqueue(c, a, track, c->cap_stream);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      CK(e, "ending the graph capture");
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      CK(e2, "instantiating the stage graph");
+      it = c->graphs.emplace(key, ex).first;
+    }
+    CK(cudaGraphLaunch(it->second, c->stream), "launching the stage graph");
+  } else {
+    const int rc = batch_enqueue(c, a, track, c->stream);
+    if (rc) return rc;
+  }
+  c->s0 = s0;
+  c->sc = dst;
+  return GRMHD_OK;
+}
+
 int grmhd_get(grmhd_ctx* c, int what, void* dst, int where) {
   if (!c || !dst) return c ? fail(c, GRMHD_E_INVALID, "dst is NULL") : GRMHD_E_INVALID;
+  if (c->nblocks > 0) {
+    if (what == GRMHD_GET_STATS || what == GRMHD_GET_DT) return grmhd_get_scalars(c, what, dst, where);
+    return fail(c, GRMHD_E_INVALID, "per-block data of a batch: use grmhd_batch_get");
+  }
   if (where != GRMHD_HOST && where != GRMHD_DEVICE) return fail(c, GRMHD_E_INVALID, "bad where");
   const cudaMemcpyKind kind = where == GRMHD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   const cudaStream_t s = c->stream;
@@ -383,7 +583,225 @@ const char* grmhd_last_error(const grmhd_ctx* c) { return c ? c->err : g_create_
 void grmhd_destroy(grmhd_ctx* c) {
   if (c && c->timing)
     for (int k = 0; k < 7; ++k) cudaEventDestroy(c->ev[k]);
+  if (c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  }
   delete c;
+}
+
+// ------------------------------------------------------------------ batches of meshblocks
+
+size_t grmhd_batch_workspace_bytes(const grmhd_params* p, int nblocks, const grmhd_block* blocks) {
+  char msg[256];
+  if (!p || nblocks < 1 || !blocks) return 0;
+  grmhd_params q = *p;
+  q.nx = blocks[0].nx; q.ny = blocks[0].ny; q.nz = blocks[0].nz;
+  for (int i = 0; i < 3; ++i) q.dx[i] = blocks[0].dx[i];
+  if (!valid_params(&q, msg, sizeof msg)) return 0;
+  for (int b = 0; b < nblocks; ++b)
+    if (!valid_block(blocks[b], p->ng, msg, sizeof msg)) return 0;
+  return batch_layout(p, nblocks, blocks).total;
+}
+
+int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* blocks, void* workspace, size_t bytes,
+                       void* stream, grmhd_ctx** out) {
+  if (!out) {
+    snprintf(g_create_err, sizeof g_create_err, "out is NULL");
+    return GRMHD_E_INVALID;
+  }
+  *out = nullptr;
+  if (!p || nblocks < 1 || !blocks) {
+    snprintf(g_create_err, sizeof g_create_err, "need params and at least one block");
+    return GRMHD_E_INVALID;
+  }
+  grmhd_params q = *p;
+  q.nx = blocks[0].nx; q.ny = blocks[0].ny; q.nz = blocks[0].nz;
+  for (int i = 0; i < 3; ++i) q.dx[i] = blocks[0].dx[i];
+  if (!valid_params(&q, g_create_err, sizeof g_create_err)) return GRMHD_E_INVALID;
+  if (p->bc != GRMHD_BC_FIXED) {
+    snprintf(g_create_err, sizeof g_create_err, "batched blocks take their ghosts as given (GRMHD_BC_FIXED)");
+    return GRMHD_E_UNSUPPORTED;
+  }
+  for (int b = 0; b < nblocks; ++b)
+    if (!valid_block(blocks[b], p->ng, g_create_err, sizeof g_create_err)) return GRMHD_E_INVALID;
+  const BatchLayout l = batch_layout(p, nblocks, blocks);
+  if (bytes < l.total || !workspace) {
+    snprintf(g_create_err, sizeof g_create_err, "workspace of %zu bytes is smaller than the %zu bytes needed", bytes,
+             l.total);
+    return GRMHD_E_WORKSPACE;
+  }
+  if (((uintptr_t)workspace) % kAlign != 0) {
+    snprintf(g_create_err, sizeof g_create_err, "workspace must be 256-byte aligned");
+    return GRMHD_E_WORKSPACE;
+  }
+  grmhd_ctx* c = new (std::nothrow) grmhd_ctx();
+  if (!c) {
+    snprintf(g_create_err, sizeof g_create_err, "host allocation failed");
+    return GRMHD_E_INVALID;
+  }
+  c->prm = *p;
+  c->dp = dev_params(&q);
+  c->L = p->precision == GRMHD_MIXED ? &mixed_launchers() : &fp64_launchers();
+  c->stream = (cudaStream_t)stream;
+  c->ws = (char*)workspace;
+  c->ws_bytes = bytes;
+  c->scal = (unsigned long long*)(c->ws + l.scal);
+  c->nblocks = nblocks;
+  c->dblocks = (BlockDesc*)(c->ws + l.blocks);
+  c->ditems = (WorkItem*)(c->ws + l.items);
+  c->worklist = p->precision == GRMHD_MIXED ? (int*)(c->ws + l.worklist) : nullptr;
+  c->hblocks.resize(nblocks);
+  long long off = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    BlockDesc& d = c->hblocks[b];
+    d.p = block_params(p, blocks[b]);
+    d.P = c->ws + l.P[b];
+    for (int k = 0; k < 3; ++k) {
+      d.U[k] = (double*)(c->ws + l.U[3 * b + k]);
+      d.F[k] = c->ws + l.F[3 * b + k];
+    }
+    d.E = c->ws + l.E[b];
+    d.status = (uint8_t*)(c->ws + l.status[b]);
+    d.cell_offset = off;
+    off += d.p.isize;
+  }
+  c->total_cells = off;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  c->grid_persist = (sms > 0 ? sms : 152) * c->L->batch_ctas_per_sm(p->metric);
+  cudaError_t e = cudaMemsetAsync(c->ws, 0, l.total, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->dblocks, c->hblocks.data(), sizeof(BlockDesc) * nblocks, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    snprintf(g_create_err, sizeof g_create_err, "initialising the batch failed: %s", cudaGetErrorString(e));
+    delete c;
+    return GRMHD_E_CUDA;
+  }
+  *out = c;
+  const int rc = grmhd_batch_set_tile(c, 512);
+  if (rc) {
+    snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
+    delete c;
+    *out = nullptr;
+    return rc;
+  }
+  return GRMHD_OK;
+}
+
+int grmhd_batch_set_tile(grmhd_ctx* c, int tile) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "not a batch context") : GRMHD_E_INVALID;
+  if (tile < kMinTile || tile > (1 << 20)) return fail(c, GRMHD_E_INVALID, "tile must be in [128, 2^20]");
+  const std::vector<WorkItem> items = build_items(c->hblocks, tile, c->n_items);
+  // items are built from a smaller minimum tile, so they always fit the reserved region
+  CK(cudaMemcpyAsync(c->ditems, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, c->stream),
+     "uploading work items");
+  CK(cudaStreamSynchronize(c->stream), "synchronising");
+  c->tile = tile;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  return GRMHD_OK;
+}
+
+int grmhd_batch_set_prims(grmhd_ctx* c, int block, const double* P, int where) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "not a batch context") : GRMHD_E_INVALID;
+  if (block < 0 || block >= c->nblocks || !P) return fail(c, GRMHD_E_INVALID, "bad block index or P");
+  const BlockDesc& b = c->hblocks[block];
+  const size_t bytes = sizeof(double) * NV * (size_t)b.p.gsize;
+  const double* src = P;
+  if (where == GRMHD_HOST) {
+    // stage through the block's flux region (at least 8 G doubles in both forms)
+    CK(cudaMemcpyAsync(b.F[0], P, bytes, cudaMemcpyHostToDevice, c->stream), "copying P to the device");
+    src = (const double*)b.F[0];
+  } else if (where != GRMHD_DEVICE) {
+    return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");
+  }
+  CK(c->L->load_prims(b.p, src, b.P, c->stream), "loading primitives");
+  CK(c->L->prim2con(b.p, b.P, b.U[0], c->stream), "prim->cons");
+  c->s0 = c->sc = 0;
+  c->has_state = true;
+  return GRMHD_OK;
+}
+
+int grmhd_batch_get(grmhd_ctx* c, int block, int what, void* dst, int where) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "not a batch context") : GRMHD_E_INVALID;
+  if (!dst) return fail(c, GRMHD_E_INVALID, "dst is NULL");
+  if (where != GRMHD_HOST && where != GRMHD_DEVICE) return fail(c, GRMHD_E_INVALID, "bad where");
+  const cudaMemcpyKind kind = where == GRMHD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const cudaStream_t s = c->stream;
+  if (what == GRMHD_GET_STATS || what == GRMHD_GET_DT) return grmhd_get_scalars(c, what, dst, where);
+  if (block < 0 || block >= c->nblocks) return fail(c, GRMHD_E_INVALID, "bad block index");
+  const BlockDesc& b = c->hblocks[block];
+  switch (what) {
+    case GRMHD_GET_PRIMS: {
+      const size_t bytes = sizeof(double) * NV * (size_t)b.p.gsize;
+      if (c->L->p_bytes == 8) {
+        CK(cudaMemcpyAsync(dst, b.P, bytes, kind, s), "copying P");
+      } else if (where == GRMHD_DEVICE) {
+        CK(c->L->store_prims(b.p, b.P, (double*)dst, s), "converting P");
+      } else {
+        CK(c->L->store_prims(b.p, b.P, (double*)b.F[0], s), "converting P");
+        CK(cudaMemcpyAsync(dst, b.F[0], bytes, kind, s), "copying P");
+      }
+      break;
+    }
+    case GRMHD_GET_CONS:
+      CK(cudaMemcpyAsync(dst, b.U[c->sc], sizeof(double) * NV * (size_t)b.p.isize, kind, s), "copying U");
+      break;
+    case GRMHD_GET_STATUS:
+      CK(cudaMemcpyAsync(dst, b.status, (size_t)b.p.isize, kind, s), "copying status");
+      break;
+    default:
+      return fail(c, GRMHD_E_INVALID, "unknown GRMHD_GET_* selector");
+  }
+  if (where == GRMHD_HOST) CK(cudaStreamSynchronize(s), "synchronising");
+  return GRMHD_OK;
+}
+
+int grmhd_set_graph(grmhd_ctx* c, int on) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "graphs are built for batch contexts") : GRMHD_E_INVALID;
+  if (on && !c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "creating the capture stream");
+  c->use_graph = on != 0;
+  return GRMHD_OK;
+}
+
+int grmhd_batch_autotune(grmhd_ctx* c, int* best_tile, double* best_ms) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "not a batch context") : GRMHD_E_INVALID;
+  if (!c->has_state) return fail(c, GRMHD_E_INVALID, "load the blocks' primitives first");
+  const int tiles[] = {128, 256, 512, 1024, 2048, 4096};
+  int best = c->tile;
+  float best_t = 1e30f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "creating events");
+  CK(cudaEventCreate(&e1), "creating events");
+  const bool graph = c->use_graph;
+  c->use_graph = false;
+  int rc = GRMHD_OK;
+  for (int t : tiles) {
+    rc = grmhd_batch_set_tile(c, t);
+    if (rc) break;
+    CK(cudaEventRecord(e0, c->stream), "recording");
+    rc = grmhd_rk2_step(c, 0.0);  // one real step of the batch per candidate
+    if (rc) break;
+    CK(cudaEventRecord(e1, c->stream), "recording");
+    CK(cudaEventSynchronize(e1), "synchronising");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1), "reading events");
+    if (ms < best_t) {
+      best_t = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->use_graph = graph;
+  if (rc) return rc;
+  rc = grmhd_batch_set_tile(c, best);
+  if (best_tile) *best_tile = best;
+  if (best_ms) *best_ms = 0.5 * best_t;
+  return rc;
 }
 
 }  // extern "C"

@@ -24,6 +24,11 @@ cudaError_t launch_finalize_dt(const unsigned long long* ms, double* dt, const D
   return cudaGetLastError();
 }
 
+cudaError_t launch_batch_finalize_dt(const unsigned long long* ms, double* dt, double cfl, cudaStream_t s) {
+  k_batch_finalize_dt<<<1, 32, 0, s>>>(ms, dt, cfl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_c2p_batch(const double* U, double* P, uint8_t* status, int* iters, long long n, int flags,
                              const DevParams& p, unsigned long long* stats, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

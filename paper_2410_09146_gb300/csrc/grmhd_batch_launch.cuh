@@ -1,0 +1,59 @@
+// Launchers of the batched persistent kernels for one arithmetic form (R: flux type, T: P storage).
+#pragma once
+
+#include "grmhd_kernels.cuh"
+#include "grmhd_launch.h"
+
+namespace grmhd {
+
+template <class R, class T>
+struct BatchLaunch {
+  template <int METRIC>
+  static cudaError_t flux_m(const BlockDesc* b, const WorkItem* it, int n, unsigned int* ctr, unsigned long long* ms,
+                            int track, int recon, int grid, cudaStream_t s) {
+    switch (recon) {
+      case RECON_CONSTANT: k_batch_flux<R, T, METRIC, RECON_CONSTANT><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
+      case RECON_PLM_MINMOD: k_batch_flux<R, T, METRIC, RECON_PLM_MINMOD><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
+      case RECON_PLM_MC: k_batch_flux<R, T, METRIC, RECON_PLM_MC><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
+      case RECON_WENO5Z: k_batch_flux<R, T, METRIC, RECON_WENO5Z><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t flux(const BlockDesc* b, const WorkItem* it, int n, unsigned int* ctr, unsigned long long* ms,
+                          int track, int metric, int recon, int grid, cudaStream_t s) {
+    return metric == KERR_SCHILD ? flux_m<KERR_SCHILD>(b, it, n, ctr, ms, track, recon, grid, s)
+                                 : flux_m<MINKOWSKI>(b, it, n, ctr, ms, track, recon, grid, s);
+  }
+  static cudaError_t emf(const BlockDesc* b, const WorkItem* it, int n, unsigned int* ctr, int grid, cudaStream_t s) {
+    k_batch_emf<R><<<grid, 128, 0, s>>>(b, it, n, ctr);
+    return cudaGetLastError();
+  }
+  static cudaError_t update(const BlockDesc* b, const WorkItem* it, int n, unsigned int* ctr, const BatchArgs& a,
+                            int metric, int grid, cudaStream_t s) {
+    if (metric == KERR_SCHILD)
+      k_batch_update<KERR_SCHILD, R, T><<<grid, 128, 0, s>>>(b, it, n, ctr, a);
+    else
+      k_batch_update<MINKOWSKI, R, T><<<grid, 128, 0, s>>>(b, it, n, ctr, a);
+    return cudaGetLastError();
+  }
+  static cudaError_t deferred(const BlockDesc* b, int nblocks, const BatchArgs& a, int metric, int grid,
+                              cudaStream_t s) {
+    if (metric == KERR_SCHILD)
+      k_batch_deferred<KERR_SCHILD, T><<<grid, 128, 0, s>>>(b, nblocks, a);
+    else
+      k_batch_deferred<MINKOWSKI, T><<<grid, 128, 0, s>>>(b, nblocks, a);
+    return cudaGetLastError();
+  }
+  // CTAs per SM of the persistent kernels (occupancy of the update kernel, the heaviest)
+  static int ctas_per_sm(int metric) {
+    int n = 0;
+    if (metric == KERR_SCHILD)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_update<KERR_SCHILD, R, T>, 128, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_update<MINKOWSKI, R, T>, 128, 0);
+    return n > 0 ? n : 1;
+  }
+};
+
+}  // namespace grmhd

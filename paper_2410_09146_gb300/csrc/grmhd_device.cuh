@@ -51,6 +51,46 @@ struct StageArgs {
 };
 
 
+// Face box of direction d: face index along d in [0, n_d], transverse cell indices in [-1, n_t]
+// (the transverse halo feeds the CT edge averages).
+__host__ __device__ __forceinline__ long long face_box(const DevParams& p, int d, int& ex, int& ey) {
+  ex = p.nx + (d == 0 ? 1 : 2);
+  ey = p.ny + (d == 1 ? 1 : 2);
+  const int ez = p.nz + (d == 2 ? 1 : 2);
+  return (long long)ex * ey * ez;
+}
+
+// One meshblock of a batch: its geometry and where its arrays live in the workspace.
+struct BlockDesc {
+  DevParams p;
+  void* P;                // primitives [8][gz][gy][gx] (storage type of the form)
+  void* F[3];             // face fluxes per direction
+  void* E;                // edge EMFs
+  double* U[3];           // conserved-state slots
+  uint8_t* status;
+  long long cell_offset;  // index of the block's first interior cell in the batch
+};
+
+// A contiguous range of faces / edges / cells of one block (phase 0..2: fluxes of direction d,
+// 3: EMFs, 4: cell update).
+struct WorkItem {
+  int block;
+  int phase;
+  long long start;
+  int count;
+  int pad;
+};
+
+// Coefficients and bookkeeping shared by every block of a batched stage.
+struct BatchArgs {
+  double g0, g1, beta, dt;
+  int use_dev_dt, s0, sc, dst;
+  const double* dt_dev;
+  unsigned long long* stats;
+  int* worklist;
+  unsigned int* wl_count;
+};
+
 // ------------------------------------------------------------------ metric (Sec. 2.3)
 // gam / gamu hold the symmetric 3x3 in the order xx, xy, xz, yy, yz, zz.
 template <class R>
@@ -419,7 +459,7 @@ __device__ __forceinline__ C2PEval<T> c2p_master_value(const C2PIn<T>& c, T mu) 
   e.df = T(0);
   e.x = x;
   e.W = W;
-  e.rho = c.D * iW;
+  e.rho = c.D / W;
   e.eps = eps;
   return e;
 }

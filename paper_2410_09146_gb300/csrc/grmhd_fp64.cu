@@ -2,6 +2,7 @@
 // contraction (-fmad=false) so that every double operation rounds as the FP64 reference does.
 #include "grmhd_kernels.cuh"
 #include "grmhd_launch.h"
+#include "grmhd_batch_launch.cuh"
 
 namespace grmhd {
 
@@ -67,7 +68,9 @@ cudaError_t store_prims(const DevParams& p, const void* P, double* dst, cudaStre
   return cudaMemcpyAsync(dst, P, sizeof(double) * NV * p.gsize, cudaMemcpyDeviceToDevice, s);
 }
 
-const FormLaunchers kFp64 = {ghost, flux, emf, update, prim2con, load_prims, store_prims, 8, 8};
+using BL = BatchLaunch<double, double>;
+const FormLaunchers kFp64 = {ghost, flux, emf, update, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
+                                BL::deferred, BL::ctas_per_sm, 8, 8};
 
 }  // namespace
 

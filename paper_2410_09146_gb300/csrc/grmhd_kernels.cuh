@@ -42,84 +42,96 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// a1 + a2 + a3: one thread per face of direction d in the box
-//   face index along d in [0, n_d], transverse cell indices in [-1, n_t]
-// (the transverse halo feeds the CT edge averages). Writes the Riemann flux and, for interior
-// faces, reduces max |lambda| into ms[d].
+// a1 + a2 + a3 for face t of direction d: reconstruct the two cells beside the face, evaluate the
+// metric at the face centre, the two sides' (U, F, lambda), and the Riemann flux. Writes F and
+// returns max |lambda| of the face when it is an interior face (0 otherwise).
+template <class R, class T, int METRIC, int RECON>
+__device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__ P, R* __restrict__ F, int d,
+                                       long long t) {
+  int ex, ey;
+  face_box(p, d, ex, ey);
+  const long long stride = d == 0 ? 1 : (d == 1 ? (long long)p.gx : (long long)p.gx * p.gy);
+  const int i = (int)(t % ex) + (d == 0 ? 0 : -1);
+  const int j = (int)((t / ex) % ey) + (d == 1 ? 0 : -1);
+  const int k = (int)(t / ((long long)ex * ey)) + (d == 2 ? 0 : -1);
+  const long long g = gidx(p, i, j, k);
+  R PL[NV], PR[NV];
+  const R eps = R(p.weno_eps);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const T* Pq = P + q * p.gsize + g;
+    const R fm3 = RECON == RECON_WENO5Z ? R(Pq[-3 * stride]) : R(0);
+    const R fm2 = RECON != RECON_CONSTANT ? R(Pq[-2 * stride]) : R(0);
+    const R fm1 = R(Pq[-stride]);
+    const R f0 = R(Pq[0]);
+    const R fp1 = RECON != RECON_CONSTANT ? R(Pq[stride]) : R(0);
+    const R fp2 = RECON == RECON_WENO5Z ? R(Pq[2 * stride]) : R(0);
+    R qm, qp;
+    recon_cell<R, RECON>(fm3, fm2, fm1, f0, fp1, eps, qm, qp);  // cell c - e_d
+    PL[q] = qp;
+    recon_cell<R, RECON>(fm2, fm1, f0, fp1, fp2, eps, qm, qp);  // cell c
+    PR[q] = qm;
+  }
+  // A face whose reconstructed density is not positive or internal energy is negative on
+  // either side takes the first-order (cell) values of both neighbours.
+  if (!(PL[0] > R(0)) || !(PL[4] >= R(0)) || !(PR[0] > R(0)) || !(PR[4] >= R(0))) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      PL[q] = R(P[q * p.gsize + g - stride]);
+      PR[q] = R(P[q * p.gsize + g]);
+    }
+  }
+  // face centre, in the flux arithmetic type
+  R xf[3] = {R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
+             R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2])};
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
+  Metric<R> m;
+  metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
+  FaceSide<R> L, Rs;
+  prim_to_face<R>(PL, m, d, R(p.gamma_eos), L);
+  prim_to_face<R>(PR, m, d, R(p.gamma_eos), Rs);
+  R Fh[NV];
+  const R cm = riemann_flux<R>(p.riemann, L, Rs, Fh);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
+  const bool interior = (d == 0 || (i >= 0 && i < p.nx)) && (d == 1 || (j >= 0 && j < p.ny)) &&
+                        (d == 2 || (k >= 0 && k < p.nz));
+  return interior ? cm : R(0);
+}
+
+// Block-wide max of v (non-negative) folded into *dst with one atomic per block.
+template <class R>
+__device__ __forceinline__ void block_max_to(R v, unsigned long long* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ R red[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : R(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomic_max_pos(dst, (double)v);
+  }
+}
+
+// One thread per face of direction d; for interior faces max |lambda| is reduced into ms[d].
 template <class R, class T, int METRIC, int RECON>
 __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __restrict__ F,
                                               unsigned long long* __restrict__ ms, DevParams p, int d,
                                               int track_speed) {
-  const int ex = p.nx + (d == 0 ? 1 : 2), ey = p.ny + (d == 1 ? 1 : 2), ez = p.nz + (d == 2 ? 1 : 2);
-  const int ox = d == 0 ? 0 : -1, oy = d == 1 ? 0 : -1, oz = d == 2 ? 0 : -1;
-  const long long nface = (long long)ex * ey * ez;
-  const long long stride = d == 0 ? 1 : (d == 1 ? (long long)p.gx : (long long)p.gx * p.gy);
+  int ex, ey;
+  const long long nface = face_box(p, d, ex, ey);
   R cm_local = R(0);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nface;
        t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % ex) + ox;
-    const int j = (int)((t / ex) % ey) + oy;
-    const int k = (int)(t / ((long long)ex * ey)) + oz;
-    const long long g = gidx(p, i, j, k);
-    R PL[NV], PR[NV];
-    const R eps = R(p.weno_eps);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const T* Pq = P + q * p.gsize + g;
-      const R fm3 = RECON == RECON_WENO5Z ? R(Pq[-3 * stride]) : R(0);
-      const R fm2 = RECON != RECON_CONSTANT ? R(Pq[-2 * stride]) : R(0);
-      const R fm1 = R(Pq[-stride]);
-      const R f0 = R(Pq[0]);
-      const R fp1 = RECON != RECON_CONSTANT ? R(Pq[stride]) : R(0);
-      const R fp2 = RECON == RECON_WENO5Z ? R(Pq[2 * stride]) : R(0);
-      R qm, qp;
-      recon_cell<R, RECON>(fm3, fm2, fm1, f0, fp1, eps, qm, qp);  // cell c - e_d
-      PL[q] = qp;
-      recon_cell<R, RECON>(fm2, fm1, f0, fp1, fp2, eps, qm, qp);  // cell c
-      PR[q] = qm;
-    }
-    // A face whose reconstructed density is not positive or internal energy is negative on
-    // either side takes the first-order (cell) values of both neighbours.
-    if (!(PL[0] > R(0)) || !(PL[4] >= R(0)) || !(PR[0] > R(0)) || !(PR[4] >= R(0))) {
-#pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        PL[q] = R(P[q * p.gsize + g - stride]);
-        PR[q] = R(P[q * p.gsize + g]);
-      }
-    }
-    // face centre, in the flux arithmetic type
-    R xf[3] = {R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
-               R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2])};
-    const int cd = d == 0 ? i : (d == 1 ? j : k);
-    xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
-    Metric<R> m;
-    metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
-    FaceSide<R> L, Rs;
-    prim_to_face<R>(PL, m, d, R(p.gamma_eos), L);
-    prim_to_face<R>(PR, m, d, R(p.gamma_eos), Rs);
-    R Fh[NV];
-    const R cm = riemann_flux<R>(p.riemann, L, Rs, Fh);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
-    const bool interior = (d == 0 || (i >= 0 && i < p.nx)) && (d == 1 || (j >= 0 && j < p.ny)) &&
-                          (d == 2 || (k >= 0 && k < p.nz));
-    if (interior && cm > cm_local) cm_local = cm;
+    const R cm = flux_face<R, T, METRIC, RECON>(p, P, F, d, t);
+    if (cm > cm_local) cm_local = cm;
   }
-  if (track_speed) {
-    R v = cm_local;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __shared__ R red[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-      v = lane < (int)(blockDim.x >> 5) ? red[lane] : R(0);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0) atomic_max_pos(ms + d, (double)v);
-    }
-  }
+  if (track_speed) block_max_to<R>(cm_local, ms + d);
 }
 
 // a7: dt = cfl / max_d(max|lambda_d| / dx_d)
@@ -132,24 +144,29 @@ static __global__ void k_finalize_dt(const unsigned long long* ms, double* dt, D
 }
 
 // a4: Toth flux-CT edge EMFs, Omega_k = 1/4 (sum of the 4 F^j_{B^i} - sum of the 4 F^i_{B^j})
-// around the edge for (i, j, k) cyclic. Thread box [0, nx] x [0, ny] x [0, nz].
+// around the edge for (i, j, k) cyclic, for edge box index t in [0, nx] x [0, ny] x [0, nz].
+template <class R>
+__device__ __forceinline__ void emf_edge(const DevParams& p, const R* __restrict__ Fx, const R* __restrict__ Fy,
+                                         const R* __restrict__ Fz, R* __restrict__ E, long long t) {
+  const int ex = p.nx + 1, ey = p.ny + 1;
+  const long long G = p.gsize;
+  const long long sy = p.gx, sz = (long long)p.gx * p.gy;
+  const int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
+  const long long g = gidx(p, i, j, k);
+  if (k < p.nz)  // Omega_z(fi = i, fj = j, k)
+    E[2 * G + g] = R(0.25) * (Fy[5 * G + g - 1] + Fy[5 * G + g] - Fx[6 * G + g - sy] - Fx[6 * G + g]);
+  if (i < p.nx)  // Omega_x(i, fj = j, fk = k)
+    E[0 * G + g] = R(0.25) * (Fz[6 * G + g - sy] + Fz[6 * G + g] - Fy[7 * G + g - sz] - Fy[7 * G + g]);
+  if (j < p.ny)  // Omega_y(fi = i, j, fk = k)
+    E[1 * G + g] = R(0.25) * (Fx[7 * G + g - sz] + Fx[7 * G + g] - Fz[5 * G + g - 1] - Fz[5 * G + g]);
+}
+
 template <class R>
 __global__ void k_emf(const R* __restrict__ Fx, const R* __restrict__ Fy, const R* __restrict__ Fz,
                       R* __restrict__ E, DevParams p) {
-  const int ex = p.nx + 1, ey = p.ny + 1, ez = p.nz + 1;
-  const long long n = (long long)ex * ey * ez;
-  const long long G = p.gsize;
-  const long long sy = p.gx, sz = (long long)p.gx * p.gy;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
-    const long long g = gidx(p, i, j, k);
-    if (k < p.nz)  // Omega_z(fi = i, fj = j, k)
-      E[2 * G + g] = R(0.25) * (Fy[5 * G + g - 1] + Fy[5 * G + g] - Fx[6 * G + g - sy] - Fx[6 * G + g]);
-    if (i < p.nx)  // Omega_x(i, fj = j, fk = k)
-      E[0 * G + g] = R(0.25) * (Fz[6 * G + g - sy] + Fz[6 * G + g] - Fy[7 * G + g - sz] - Fy[7 * G + g]);
-    if (j < p.ny)  // Omega_y(fi = i, j, fk = k)
-      E[1 * G + g] = R(0.25) * (Fx[7 * G + g - sz] + Fx[7 * G + g] - Fz[5 * G + g - 1] - Fz[5 * G + g]);
-  }
+  const long long n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    emf_edge<R>(p, Fx, Fy, Fz, E, t);
 }
 
 // Geometric source terms at a cell centre (Sec. 2.1 source vector, without the radiation
@@ -257,99 +274,10 @@ __device__ __forceinline__ void ks_sources(const DevParams& p, R x, R y, R z, co
   (void)L4;
 }
 
-// a5 + a6: one thread per interior cell. Divergence of the face fluxes (CT fluxes for B),
-// sources, RK combination Unew = g0 U0 + g1 Ucur + beta dt L, con2prim warm-started from the
-// current primitives, floors, and the re-derived hydro state when a floor fired.
-template <int METRIC, class R, class T>
-__global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __restrict__ Fx,
-                                                const R* __restrict__ Fy, const R* __restrict__ Fz,
-                                                const R* __restrict__ E, StageArgs a, DevParams p) {
-  const long long n = p.isize;
-  const long long G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
-  const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
-  const double bdt = a.beta * dt;
+// Per-thread con2prim statistics, folded into StageArgs::stats once per warp.
+struct CellStats {
   unsigned int it_sum = 0, c_rho = 0, c_eps = 0, c_w = 0, c_nc = 0, c_bad = 0, it_max = 0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
-    const long long g = gidx(p, i, j, k);
-    const double xc = p.x0[0] + (i + 0.5) * p.dx[0];
-    const double yc = p.x0[1] + (j + 0.5) * p.dx[1];
-    const double zc = p.x0[2] + (k + 0.5) * p.dx[2];
-    double Pc[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) Pc[q] = (double)P[q * G + g];
-    R L[NV];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const R div = (Fx[q * G + g + 1] - Fx[q * G + g]) * R(p.idx[0]) + (Fy[q * G + g + sy] - Fy[q * G + g]) * R(p.idx[1]) +
-                    (Fz[q * G + g + sz] - Fz[q * G + g]) * R(p.idx[2]);
-      L[q] = -div;
-    }
-    const R* Ex = E;
-    const R* Ey = E + G;
-    const R* Ez = E + 2 * G;
-    const R h = R(0.5);
-    // CT fluxes of B (normal components vanish)
-    const R FyBx_p = h * (Ez[g + sy] + Ez[g + sy + 1]), FyBx_m = h * (Ez[g] + Ez[g + 1]);
-    const R FzBx_p = -h * (Ey[g + sz] + Ey[g + sz + 1]), FzBx_m = -h * (Ey[g] + Ey[g + 1]);
-    const R FxBy_p = -h * (Ez[g + 1] + Ez[g + 1 + sy]), FxBy_m = -h * (Ez[g] + Ez[g + sy]);
-    const R FzBy_p = h * (Ex[g + sz] + Ex[g + sz + sy]), FzBy_m = h * (Ex[g] + Ex[g + sy]);
-    const R FxBz_p = h * (Ey[g + 1] + Ey[g + 1 + sz]), FxBz_m = h * (Ey[g] + Ey[g + sz]);
-    const R FyBz_p = -h * (Ex[g + sy] + Ex[g + sy + sz]), FyBz_m = -h * (Ex[g] + Ex[g + sz]);
-    L[5] = -((FyBx_p - FyBx_m) * R(p.idx[1]) + (FzBx_p - FzBx_m) * R(p.idx[2]));
-    L[6] = -((FxBy_p - FxBy_m) * R(p.idx[0]) + (FzBy_p - FzBy_m) * R(p.idx[2]));
-    L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
-    Metric<double> m;
-    double rks;
-    metric_at<double, METRIC>(p, xc, yc, zc, m, &rks);
-    if (METRIC == KERR_SCHILD) {
-      R Sr[5];
-      R Pr[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) Pr[q] = R(Pc[q]);
-      Metric<R> mr;
-      metric_at<R, METRIC>(p, R(xc), R(yc), R(zc), mr);
-      ks_sources<R>(p, R(xc), R(yc), R(zc), Pr, mr, Sr);
-#pragma unroll
-      for (int q = 1; q < 5; ++q) L[q] += Sr[q];
-    }
-    double Un[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double u = a.g1 * a.Ucur[q * n + t];
-      if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
-      Un[q] = u + bdt * (double)L[q];
-    }
-    // a6: con2prim on the undensitized state, warm-started from the current primitives
-    const double isg = 1.0 / m.sqrtgam;
-    double Uc[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
-    const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
-    double Pn[NV];
-    int iters;
-    int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters, a.worklist != nullptr)
-                            : con2prim<double>(p, m, Uc, mu0, Pn, iters);
-    if (st == C2P_DEFERRED) {
-      // finished by k_update_deferred: keep P (the warm start), store the new conserved state
-#pragma unroll
-      for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
-      a.worklist[atomicAdd(a.wl_count, 1u)] = (int)t;
-      it_sum += iters;
-      continue;
-    }
-    st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
-    if (st) {
-      double U5[5];
-      prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) Un[q] = U5[q];
-    }
-#pragma unroll
-    for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
-    a.status[t] = (uint8_t)st;
+  __device__ __forceinline__ void add(int st, int iters) {
     it_sum += iters;
     it_max = iters > (int)it_max ? iters : it_max;
     c_rho += (st & ST_RHO_FLOOR) != 0;
@@ -358,8 +286,8 @@ __global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __re
     c_nc += (st & ST_NOT_CONVERGED) != 0;
     c_bad += (st & ST_BAD_INPUT) != 0;
   }
-  if (a.stats) {
-    // warp-level sums, one atomic per warp
+  __device__ __forceinline__ void flush(unsigned long long* stats) {
+    if (!stats) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       it_sum += __shfl_xor_sync(0xffffffffu, it_sum, o);
@@ -371,82 +299,278 @@ __global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __re
       it_max = max(it_max, __shfl_xor_sync(0xffffffffu, it_max, o));
     }
     if ((threadIdx.x & 31) == 0) {
-      atomicAdd(a.stats + 0, (unsigned long long)it_sum);
-      if (c_rho) atomicAdd(a.stats + 1, (unsigned long long)c_rho);
-      if (c_eps) atomicAdd(a.stats + 2, (unsigned long long)c_eps);
-      if (c_w) atomicAdd(a.stats + 3, (unsigned long long)c_w);
-      if (c_nc) atomicAdd(a.stats + 4, (unsigned long long)c_nc);
-      if (c_bad) atomicAdd(a.stats + 5, (unsigned long long)c_bad);
-      atomicMax(a.stats + 6, (unsigned long long)it_max);
+      if (it_sum) atomicAdd(stats + 0, (unsigned long long)it_sum);
+      if (c_rho) atomicAdd(stats + 1, (unsigned long long)c_rho);
+      if (c_eps) atomicAdd(stats + 2, (unsigned long long)c_eps);
+      if (c_w) atomicAdd(stats + 3, (unsigned long long)c_w);
+      if (c_nc) atomicAdd(stats + 4, (unsigned long long)c_nc);
+      if (c_bad) atomicAdd(stats + 5, (unsigned long long)c_bad);
+      atomicMax(stats + 6, (unsigned long long)it_max);
     }
+  }
+};
+
+// a5 + a6 for interior cell t: divergence of the face fluxes (CT fluxes for B), sources, RK
+// combination Unew = g0 U0 + g1 Ucur + beta dt L, con2prim warm-started from the current primitives,
+// floors, and the re-derived hydro state when a floor fired. In the mixed form a cell whose float
+// con2prim phase does not settle is queued (wl_tag identifies its block) and finished by
+// deferred_cell. dt is the stage's time step.
+template <int METRIC, class R, class T>
+__device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ P, const R* __restrict__ Fx,
+                                            const R* __restrict__ Fy, const R* __restrict__ Fz,
+                                            const R* __restrict__ E, const StageArgs& a, double dt, long long t,
+                                            long long wl_tag, CellStats& cs) {
+  const long long n = p.isize;
+  const long long G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
+  const double bdt = a.beta * dt;
+  const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+  const long long g = gidx(p, i, j, k);
+  const double xc = p.x0[0] + (i + 0.5) * p.dx[0];
+  const double yc = p.x0[1] + (j + 0.5) * p.dx[1];
+  const double zc = p.x0[2] + (k + 0.5) * p.dx[2];
+  double Pc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) Pc[q] = (double)P[q * G + g];
+  R L[NV];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const R div = (Fx[q * G + g + 1] - Fx[q * G + g]) * R(p.idx[0]) + (Fy[q * G + g + sy] - Fy[q * G + g]) * R(p.idx[1]) +
+                  (Fz[q * G + g + sz] - Fz[q * G + g]) * R(p.idx[2]);
+    L[q] = -div;
+  }
+  const R* Ex = E;
+  const R* Ey = E + G;
+  const R* Ez = E + 2 * G;
+  const R h = R(0.5);
+  // CT fluxes of B (normal components vanish)
+  const R FyBx_p = h * (Ez[g + sy] + Ez[g + sy + 1]), FyBx_m = h * (Ez[g] + Ez[g + 1]);
+  const R FzBx_p = -h * (Ey[g + sz] + Ey[g + sz + 1]), FzBx_m = -h * (Ey[g] + Ey[g + 1]);
+  const R FxBy_p = -h * (Ez[g + 1] + Ez[g + 1 + sy]), FxBy_m = -h * (Ez[g] + Ez[g + sy]);
+  const R FzBy_p = h * (Ex[g + sz] + Ex[g + sz + sy]), FzBy_m = h * (Ex[g] + Ex[g + sy]);
+  const R FxBz_p = h * (Ey[g + 1] + Ey[g + 1 + sz]), FxBz_m = h * (Ey[g] + Ey[g + sz]);
+  const R FyBz_p = -h * (Ex[g + sy] + Ex[g + sy + sz]), FyBz_m = -h * (Ex[g] + Ex[g + sz]);
+  L[5] = -((FyBx_p - FyBx_m) * R(p.idx[1]) + (FzBx_p - FzBx_m) * R(p.idx[2]));
+  L[6] = -((FxBy_p - FxBy_m) * R(p.idx[0]) + (FzBy_p - FzBy_m) * R(p.idx[2]));
+  L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
+  Metric<double> m;
+  double rks;
+  metric_at<double, METRIC>(p, xc, yc, zc, m, &rks);
+  if (METRIC == KERR_SCHILD) {
+    R Sr[5];
+    R Pr[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Pr[q] = R(Pc[q]);
+    Metric<R> mr;
+    metric_at<R, METRIC>(p, R(xc), R(yc), R(zc), mr);
+    ks_sources<R>(p, R(xc), R(yc), R(zc), Pr, mr, Sr);
+#pragma unroll
+    for (int q = 1; q < 5; ++q) L[q] += Sr[q];
+  }
+  double Un[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double u = a.g1 * a.Ucur[q * n + t];
+    if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
+    Un[q] = u + bdt * (double)L[q];
+  }
+  // a6: con2prim on the undensitized state, warm-started from the current primitives
+  const double isg = 1.0 / m.sqrtgam;
+  double Uc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
+  const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
+  double Pn[NV];
+  int iters;
+  int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters, a.worklist != nullptr)
+                          : con2prim<double>(p, m, Uc, mu0, Pn, iters);
+  if (st == C2P_DEFERRED) {
+    // finished by deferred_cell: keep P (the warm start), store the new conserved state
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+    a.worklist[atomicAdd(a.wl_count, 1u)] = (int)(wl_tag + t);
+    cs.it_sum += iters;
+    return;
+  }
+  st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
+  if (st) {
+    double U5[5];
+    prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Un[q] = U5[q];
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
+  a.status[t] = (uint8_t)st;
+  cs.add(st, iters);
+}
+
+template <int METRIC, class R, class T>
+__global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __restrict__ Fx,
+                                                const R* __restrict__ Fy, const R* __restrict__ Fz,
+                                                const R* __restrict__ E, StageArgs a, DevParams p) {
+  const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
+  CellStats cs;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.isize; t += (long long)gridDim.x * blockDim.x)
+    update_cell<METRIC, R, T>(p, P, Fx, Fy, Fz, E, a, dt, t, 0, cs);
+  cs.flush(a.stats);
+}
+
+// Mixed form, second pass for cell t: the full double con2prim of a cell whose float phase did not
+// settle (grouped so that a warp's lanes do the same work). Unew holds its conserved state.
+template <int METRIC, class T>
+__device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict__ P, const StageArgs& a, long long t,
+                                              CellStats& cs) {
+  const long long n = p.isize, G = p.gsize;
+  const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+  const long long g = gidx(p, i, j, k);
+  Metric<double> m;
+  double rks;
+  metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                            p.x0[2] + (k + 0.5) * p.dx[2], m, &rks);
+  double Pc[NV], Un[NV], Uc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    Pc[q] = (double)P[q * G + g];
+    Un[q] = a.Unew[q * n + t];
+  }
+  const double isg = 1.0 / m.sqrtgam;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
+  const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
+  double Pn[NV];
+  int iters;
+  int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
+  st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
+  if (st) {
+    double U5[5];
+    prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) a.Unew[q * n + t] = U5[q];
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
+  a.status[t] = (uint8_t)st;
+  cs.add(st, iters);
+}
+
+template <int METRIC, class T>
+__global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, StageArgs a, DevParams p) {
+  const unsigned int cnt = *a.wl_count;
+  CellStats cs;
+  for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x)
+    deferred_cell<METRIC, T>(p, P, a, a.worklist[w], cs);
+  cs.flush(a.stats);
+  if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
+}
+
+// ------------------------------------------------------------------ batched (many meshblocks)
+// Persistent kernels: each CTA takes work items from a device counter until the list is empty,
+// so one launch covers every block of the batch for one phase.
+__device__ __forceinline__ int next_item(unsigned int* counter) {
+  __shared__ int s_item;
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  return s_item;
+}
+
+__device__ __forceinline__ StageArgs block_stage_args(const BlockDesc& b, const BatchArgs& a) {
+  StageArgs s;
+  s.U0 = b.U[a.s0];
+  s.Ucur = b.U[a.sc];
+  s.Unew = b.U[a.dst];
+  s.status = b.status;
+  s.dt_dev = a.dt_dev;
+  s.stats = a.stats;
+  s.g0 = a.g0;
+  s.g1 = a.g1;
+  s.beta = a.beta;
+  s.dt = a.dt;
+  s.use_dev_dt = a.use_dev_dt;
+  s.worklist = a.worklist;
+  s.wl_count = a.wl_count;
+  return s;
+}
+
+// Fluxes of every direction of every block; ms[0] collects max |lambda| / dx over the batch.
+template <class R, class T, int METRIC, int RECON>
+__global__ void __launch_bounds__(128) k_batch_flux(const BlockDesc* __restrict__ blocks,
+                                                    const WorkItem* __restrict__ items, int nitems,
+                                                    unsigned int* counter, unsigned long long* ms, int track_speed) {
+  R cm_local = R(0);
+  for (;;) {
+    const int it = next_item(counter);
+    if (it >= nitems) break;
+    const WorkItem w = items[it];
+    const BlockDesc& b = blocks[w.block];
+    const R idx = R(b.p.idx[w.phase]);
+    for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+      const R cm = flux_face<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k) * idx;
+      if (cm > cm_local) cm_local = cm;
+    }
+  }
+  if (track_speed) block_max_to<R>(cm_local, ms);
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) k_batch_emf(const BlockDesc* __restrict__ blocks,
+                                                   const WorkItem* __restrict__ items, int nitems,
+                                                   unsigned int* counter) {
+  for (;;) {
+    const int it = next_item(counter);
+    if (it >= nitems) break;
+    const WorkItem w = items[it];
+    const BlockDesc& b = blocks[w.block];
+    for (int k = threadIdx.x; k < w.count; k += blockDim.x)
+      emf_edge<R>(b.p, (const R*)b.F[0], (const R*)b.F[1], (const R*)b.F[2], (R*)b.E, w.start + k);
   }
 }
 
-// Mixed form, second pass: cells whose float con2prim phase did not settle run the full double
-// iteration here, grouped so that a warp's lanes do the same work. Unew holds their conserved state.
+template <int METRIC, class R, class T>
+__global__ void __launch_bounds__(128) k_batch_update(const BlockDesc* __restrict__ blocks,
+                                                      const WorkItem* __restrict__ items, int nitems,
+                                                      unsigned int* counter, BatchArgs a) {
+  const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
+  CellStats cs;
+  for (;;) {
+    const int it = next_item(counter);
+    if (it >= nitems) break;
+    const WorkItem w = items[it];
+    const BlockDesc& b = blocks[w.block];
+    const StageArgs sa = block_stage_args(b, a);
+    for (int k = threadIdx.x; k < w.count; k += blockDim.x)
+      update_cell<METRIC, R, T>(b.p, (T*)b.P, (const R*)b.F[0], (const R*)b.F[1], (const R*)b.F[2], (const R*)b.E,
+                                sa, dt, w.start + k, b.cell_offset, cs);
+  }
+  cs.flush(a.stats);
+}
+
+// Deferred con2prim cells of the batch: worklist entries are batch-wide cell indices.
 template <int METRIC, class T>
-__global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, StageArgs a, DevParams p) {
-  const long long n = p.isize, G = p.gsize;
+__global__ void __launch_bounds__(128) k_batch_deferred(const BlockDesc* __restrict__ blocks, int nblocks,
+                                                        BatchArgs a) {
   const unsigned int cnt = *a.wl_count;
-  unsigned int it_sum = 0, c_rho = 0, c_eps = 0, c_w = 0, c_nc = 0, it_max = 0;
+  CellStats cs;
   for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
-    const long long t = a.worklist[w];
-    const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
-    const long long g = gidx(p, i, j, k);
-    Metric<double> m;
-    double rks;
-    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
-                              p.x0[2] + (k + 0.5) * p.dx[2], m, &rks);
-    double Pc[NV], Un[NV], Uc[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      Pc[q] = (double)P[q * G + g];
-      Un[q] = a.Unew[q * n + t];
+    const long long gcell = a.worklist[w];
+    int lo = 0, hi = nblocks - 1;  // last block whose cell_offset <= gcell
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (blocks[mid].cell_offset <= gcell) lo = mid; else hi = mid - 1;
     }
-    const double isg = 1.0 / m.sqrtgam;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
-    const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
-    double Pn[NV];
-    int iters;
-    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
-    st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
-    if (st) {
-      double U5[5];
-      prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) a.Unew[q * n + t] = U5[q];
-    }
-#pragma unroll
-    for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
-    a.status[t] = (uint8_t)st;
-    it_sum += iters;
-    it_max = iters > (int)it_max ? iters : it_max;
-    c_rho += (st & ST_RHO_FLOOR) != 0;
-    c_eps += (st & ST_EPS_FLOOR) != 0;
-    c_w += (st & ST_W_CAP) != 0;
-    c_nc += (st & ST_NOT_CONVERGED) != 0;
+    const BlockDesc& b = blocks[lo];
+    const StageArgs sa = block_stage_args(b, a);
+    deferred_cell<METRIC, T>(b.p, (T*)b.P, sa, gcell - b.cell_offset, cs);
   }
-  if (a.stats) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      it_sum += __shfl_xor_sync(0xffffffffu, it_sum, o);
-      c_rho += __shfl_xor_sync(0xffffffffu, c_rho, o);
-      c_eps += __shfl_xor_sync(0xffffffffu, c_eps, o);
-      c_w += __shfl_xor_sync(0xffffffffu, c_w, o);
-      c_nc += __shfl_xor_sync(0xffffffffu, c_nc, o);
-      it_max = max(it_max, __shfl_xor_sync(0xffffffffu, it_max, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      if (it_sum) atomicAdd(a.stats + 0, (unsigned long long)it_sum);
-      if (c_rho) atomicAdd(a.stats + 1, (unsigned long long)c_rho);
-      if (c_eps) atomicAdd(a.stats + 2, (unsigned long long)c_eps);
-      if (c_w) atomicAdd(a.stats + 3, (unsigned long long)c_w);
-      if (c_nc) atomicAdd(a.stats + 4, (unsigned long long)c_nc);
-      atomicMax(a.stats + 6, (unsigned long long)it_max);
-      if (blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
-    }
-  }
+  cs.flush(a.stats);
+  if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
+}
+
+// dt = cfl / (max over the batch of |lambda| / dx)
+static __global__ void k_batch_finalize_dt(const unsigned long long* ms, double* dt, double cfl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dt = cfl / __longlong_as_double((long long)ms[0]);
 }
 
 // Densitized conserved state of the interior from the primitives (set-up and checkpoint restore).

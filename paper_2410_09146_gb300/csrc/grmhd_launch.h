@@ -20,6 +20,15 @@ struct FormLaunchers {
   cudaError_t (*prim2con)(const DevParams& p, const void* P, double* U, cudaStream_t s);
   cudaError_t (*load_prims)(const DevParams& p, const double* src, void* P, cudaStream_t s);   // double -> storage
   cudaError_t (*store_prims)(const DevParams& p, const void* P, double* dst, cudaStream_t s);  // storage -> double
+  // batched persistent kernels (many meshblocks, one launch per phase)
+  cudaError_t (*batch_flux)(const BlockDesc* b, const WorkItem* it, int n, unsigned int* ctr, unsigned long long* ms,
+                            int track, int metric, int recon, int grid, cudaStream_t s);
+  cudaError_t (*batch_emf)(const BlockDesc* b, const WorkItem* it, int n, unsigned int* ctr, int grid, cudaStream_t s);
+  cudaError_t (*batch_update)(const BlockDesc* b, const WorkItem* it, int n, unsigned int* ctr, const BatchArgs& a,
+                              int metric, int grid, cudaStream_t s);
+  cudaError_t (*batch_deferred)(const BlockDesc* b, int nblocks, const BatchArgs& a, int metric, int grid,
+                                cudaStream_t s);
+  int (*batch_ctas_per_sm)(int metric);
   int p_bytes;  // bytes per stored primitive
   int r_bytes;  // bytes per flux / EMF value
 };
@@ -28,6 +37,7 @@ const FormLaunchers& fp64_launchers();
 const FormLaunchers& mixed_launchers();
 
 cudaError_t launch_finalize_dt(const unsigned long long* ms, double* dt, const DevParams& p, cudaStream_t s);
+cudaError_t launch_batch_finalize_dt(const unsigned long long* ms, double* dt, double cfl, cudaStream_t s);
 cudaError_t launch_c2p_batch(const double* U, double* P, uint8_t* status, int* iters, long long n, int flags,
                              const DevParams& p, unsigned long long* stats, cudaStream_t s);
 

@@ -2,6 +2,7 @@
 // P stored in float; the state accumulation and con2prim stay in double (inside k_update).
 #include "grmhd_kernels.cuh"
 #include "grmhd_launch.h"
+#include "grmhd_batch_launch.cuh"
 
 namespace grmhd {
 
@@ -79,7 +80,9 @@ cudaError_t store_prims(const DevParams& p, const void* P, double* dst, cudaStre
   return cudaGetLastError();
 }
 
-const FormLaunchers kMixed = {ghost, flux, emf, update, prim2con, load_prims, store_prims, 4, 4};
+using BL = BatchLaunch<float, float>;
+const FormLaunchers kMixed = {ghost, flux, emf, update, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
+                                BL::deferred, BL::ctas_per_sm, 4, 4};
 
 }  // namespace
 

@@ -44,6 +44,11 @@ class grmhd_params(ctypes.Structure):
     ]
 
 
+class grmhd_block(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double * 3), ("dx", ctypes.c_double * 3)]
+
+
 _lib = None
 
 
@@ -74,6 +79,15 @@ def lib():
         L.grmhd_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         L.grmhd_stage_noalloc.argtypes = [P, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, vp]
+        B = ctypes.POINTER(grmhd_block)
+        L.grmhd_batch_workspace_bytes.argtypes = [P, ctypes.c_int, B]
+        L.grmhd_batch_workspace_bytes.restype = ctypes.c_size_t
+        L.grmhd_batch_create.argtypes = [P, ctypes.c_int, B, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.grmhd_batch_set_prims.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+        L.grmhd_batch_get.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
+        L.grmhd_batch_set_tile.argtypes = [vp, ctypes.c_int]
+        L.grmhd_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.grmhd_set_graph.argtypes = [vp, ctypes.c_int]
         L.grmhd_last_error.argtypes = [vp]
         L.grmhd_last_error.restype = ctypes.c_char_p
         L.grmhd_destroy.argtypes = [vp]
@@ -179,6 +193,112 @@ def grmhd_stage_noalloc(p: grmhd_params, P_ptr: int, U0_ptr: int, Ucur_ptr: int,
 
 def grmhd_destroy(ctx: int) -> None:
     lib().grmhd_destroy(ctx)
+
+
+def grmhd_batch_workspace_bytes(p: grmhd_params, blocks) -> int:
+    arr = (grmhd_block * len(blocks))(*blocks)
+    return int(lib().grmhd_batch_workspace_bytes(ctypes.byref(p), len(blocks), arr))
+
+
+def grmhd_batch_create(p: grmhd_params, blocks, workspace_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    arr = (grmhd_block * len(blocks))(*blocks)
+    out = ctypes.c_void_p()
+    _check(lib().grmhd_batch_create(ctypes.byref(p), len(blocks), arr, ctypes.c_void_p(workspace_ptr), nbytes,
+                                    ctypes.c_void_p(stream_ptr), ctypes.byref(out)))
+    return out.value
+
+
+def grmhd_batch_set_prims(ctx: int, block: int, P) -> None:
+    ptr, where = _ptr(P)
+    _check(lib().grmhd_batch_set_prims(ctx, block, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_batch_get(ctx: int, block: int, what: int, dst) -> None:
+    ptr, where = _ptr(dst)
+    _check(lib().grmhd_batch_get(ctx, block, what, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_batch_set_tile(ctx: int, tile: int) -> None:
+    _check(lib().grmhd_batch_set_tile(ctx, tile), ctx)
+
+
+def grmhd_batch_autotune(ctx: int):
+    t = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().grmhd_batch_autotune(ctx, ctypes.byref(t), ctypes.byref(ms)), ctx)
+    return t.value, ms.value
+
+
+def grmhd_set_graph(ctx: int, on: bool) -> None:
+    _check(lib().grmhd_set_graph(ctx, int(on)), ctx)
+
+
+def block_of(setup) -> grmhd_block:
+    b = grmhd_block()
+    b.nx, b.ny, b.nz = setup.n
+    b.x0[:] = list(setup.x0)
+    b.dx[:] = list(setup.dx)
+    return b
+
+
+class BatchContext:
+    """Many meshblocks advanced together (one persistent launch per phase); `setups` give each block's
+    size and placement, the first one the shared physics options."""
+
+    def __init__(self, setups, device: int = 0, stream=None):
+        import torch
+        self.setups = list(setups)
+        self.p = params(self.setups[0])
+        self.blocks = [block_of(s) for s in self.setups]
+        nbytes = grmhd_batch_workspace_bytes(self.p, self.blocks)
+        if nbytes == 0:
+            raise GrmhdError("invalid batch parameters")
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.ctx = grmhd_batch_create(self.p, self.blocks, self.ws_ptr, nbytes, self.stream.cuda_stream)
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            grmhd_destroy(self.ctx)
+            self.ctx = None
+
+    def set_prims(self, block, P):
+        grmhd_batch_set_prims(self.ctx, block, P)
+
+    def stage(self, g0, g1, beta, dt=0.0):
+        grmhd_stage(self.ctx, g0, g1, beta, dt)
+
+    def rk2_step(self, dt=0.0):
+        grmhd_rk2_step(self.ctx, dt)
+
+    def get(self, block, what):
+        s = self.setups[block]
+        shape, dt = {GRMHD_GET_PRIMS: (s.prim_shape(), np.float64), GRMHD_GET_CONS: (s.cons_shape(), np.float64),
+                     GRMHD_GET_STATUS: (s.cons_shape()[1:], np.uint8)}[what]
+        out = np.empty(shape, dt)
+        grmhd_batch_get(self.ctx, block, what, out)
+        return out
+
+    def stats(self):
+        out = np.empty(8, np.uint64)
+        grmhd_get(self.ctx, GRMHD_GET_STATS, out)
+        return out
+
+    def dt(self):
+        out = np.empty(1, np.float64)
+        grmhd_get(self.ctx, GRMHD_GET_DT, out)
+        return float(out[0])
+
+    def set_tile(self, tile):
+        grmhd_batch_set_tile(self.ctx, tile)
+
+    def autotune(self):
+        return grmhd_batch_autotune(self.ctx)
+
+    def set_graph(self, on=True):
+        grmhd_set_graph(self.ctx, on)
 
 
 # ------------------------------------------------------------------ convenience object

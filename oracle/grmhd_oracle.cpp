@@ -511,6 +511,7 @@ struct C2PResult {
   double P[8];
   int status;
   int iters;
+  double mu, mup;  // root of the master function and the upper end of its bracket
 };
 
 // Undensitized conserved Uc = (D, S_j, tau, B^k) -> primitives, before floors.
@@ -520,6 +521,7 @@ static void con2prim_point(const orc_params& p, const Geom& G, const double* Uc,
   for (int v = 0; v < 8; ++v) R.P[v] = 0.0;
   bool finite = true;
   for (int v = 0; v < 8; ++v) finite = finite && std::isfinite(Uc[v]);
+  R.mu = R.mup = 0.0;
   if (!finite || !(Uc[0] > 0.0)) {
     R.status = ST_BAD_INPUT;
     for (int k = 1; k <= 3; ++k) R.P[4 + k] = std::isfinite(Uc[4 + k]) ? Uc[4 + k] : 0.0;
@@ -561,6 +563,8 @@ static void con2prim_point(const orc_params& p, const Geom& G, const double* Uc,
   } else {
     mu = brent([&](double m) { return master_f(c, m, nullptr); }, 0.0, mup, f0, fup, &R.iters);
   }
+  R.mu = mu;
+  R.mup = mup;
   MasterOut o;
   master_f(c, mu, &o);
   const double W = o.W;
@@ -710,6 +714,22 @@ int orc_c2p_points(const orc_params* p, long n, const double* xyz, const double*
     for (int v = 0; v < 8; ++v) P[8 * q + v] = R.P[v];
     if (status) status[q] = (uint8_t)st;
     if (iters) iters[q] = R.iters;
+  }
+  return 0;
+}
+
+// Root mu = 1/(h W) of the master function and the bracket end mu_+ for densitized U at points
+// (the targets of the learned con2prim guess).
+int orc_c2p_mu_points(const orc_params* p, long n, const double* xyz, const double* U, double* mu, double* mup) {
+  for (long q = 0; q < n; ++q) {
+    Geom G;
+    metric_eval(*p, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2], G);
+    double Uc[8];
+    for (int v = 0; v < 8; ++v) Uc[v] = U[8 * q + v] / G.sqrtgam;
+    C2PResult R;
+    con2prim_point(*p, G, Uc, R);
+    mu[q] = R.mu;
+    mup[q] = R.mup;
   }
   return 0;
 }

@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-guess", action="store_true")
+    ap.add_argument("--guess-states", type=int, default=100_000_000)
     return ap.parse_args()
 
 
@@ -246,6 +248,7 @@ def run_ours(args):
     l1p = l1_rel(cm.prims()[inner], P64[inner])
     del cm
     torch.cuda.empty_cache()
+    guess = None if args.no_guess else run_guess(G, I, rank, n_states=args.guess_states)
     batched = None
     if not args.no_batched:
         batched, bms, bzones = run_batched(G, I, max(4, min(args.steps, 10)), args.warmup, rank)
@@ -289,12 +292,105 @@ def run_ours(args):
     }
     if batched is not None:
         out["batched"] = batched
+    if guess is not None:
+        out["c2p_guess"] = guess
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(n_sample=80, n_stages=1)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _iter_summary(iters, status, torch):
+    """Mean and 99th percentile of per-state iterations (from their histogram), non-converged fraction."""
+    h = torch.bincount(iters.to(torch.int64)).double()
+    c = torch.cumsum(h, 0) / h.sum()
+    p99 = int(torch.searchsorted(c, torch.tensor([0.99], dtype=torch.float64, device=c.device)).item())
+    mean = float((h * torch.arange(len(h), dtype=torch.float64, device=h.device)).sum() / h.sum())
+    return {"mean_iterations": mean, "p99_iterations": p99,
+            "not_converged_frac": float(((status & 8) != 0).double().mean())}
+
+
+def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=3000, reps=3):
+    """Learned con2prim guess: train on pairs solved by the library's FP64 con2prim (standard start), then
+    time the flat con2prim batch of n_states fresh states from the standard start and from the network's
+    start, with per-state iteration statistics and the agreement of the two solutions."""
+    import torch
+    dev = torch.device("cuda")
+    ctx = G.Context(I.Setup(n=(0, 0, 0)))  # c2p_tol 1e-10
+    # ---- training pairs
+    P = I.c2p_states_device(n_train, seed=7000 + rank, device=dev)
+    U = torch.empty_like(P)
+    ctx.p2c(P, U)
+    st = torch.empty(n_train, dtype=torch.uint8, device=dev)
+    X = torch.empty((n_train, 8), dtype=torch.float32, device=dev)
+    T = torch.empty((n_train, 2), dtype=torch.float32, device=dev)
+    ctx.c2p_guess(U, P, st, None, X=X, T=T)
+    keep = (st & (8 | 16)) == 0
+    X, T = X[keep].contiguous(), T[keep].contiguous()
+    del P, U, st, keep
+    net = G.GuessNet(seed=11)
+    net.fit_norm(X, T)
+    losses = torch.zeros(train_steps, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net.train(X, T, batch=152 * 128, steps=train_steps, lr=3e-3, lr_end=3e-5, aux=0.1, losses=losses)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    lh = losses.cpu().numpy()
+    n_pairs = X.shape[0]
+    del X, T
+    torch.cuda.empty_cache()
+    # ---- evaluation states (inputs larger than L2)
+    P = I.c2p_states_device(n_states, seed=9000 + rank, device=dev)
+    U = torch.empty_like(P)
+    ctx.p2c(P, U)
+    Ps, Pn = P, torch.empty_like(P)
+    sts = torch.empty(n_states, dtype=torch.uint8, device=dev)
+    stn = torch.empty_like(sts)
+    its = torch.empty(n_states, dtype=torch.int32, device=dev)
+    itn = torch.empty_like(its)
+    guess = torch.empty((2, n_states), dtype=torch.float64, device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_std = timed(lambda: ctx.c2p_guess(U, Ps, sts, its))
+    ms_net = timed(lambda: ctx.c2p_guess(U, Pn, stn, itn, net=net, guess=guess))
+    fallbacks = int(ctx.stats()[7])
+    # backward error |U(P) - U| / (|D| + |tau| + |S|) of each solution on states neither solve floored or
+    # flagged (forward differences between the two are bounded by the conditioning, not the solver)
+    plain = (sts == 0) & (stn == 0)
+    scale = U[0].abs() + U[4].abs() + torch.linalg.vector_norm(U[1:4], dim=0)
+    Ub = torch.empty_like(U)
+    berr = []
+    for Pd in (Ps, Pn):
+        ctx.p2c(Pd, Ub)
+        berr.append(float(((Ub - U).abs().amax(dim=0) / scale)[plain].max()))
+    del Ub
+    out = {"states": n_states, "c2p_tol": 1e-10,
+           "train": {"pairs": n_pairs, "source": "the library's FP64 con2prim from the standard start",
+                     "steps": train_steps, "batch": 152 * 128, "ms": train_ms,
+                     "loss_first": float(lh[:10].mean()), "loss_last": float(lh[-100:].mean())},
+           "standard": dict(_iter_summary(its, sts, torch), ms=ms_std, states_per_s=n_states / (ms_std / 1e3)),
+           "network": dict(_iter_summary(itn, stn, torch), ms=ms_net, states_per_s=n_states / (ms_net / 1e3),
+                           fallback_frac=fallbacks / n_states),
+           "same_status": bool(torch.equal(sts, stn)),
+           "max_backward_err": {"standard": berr[0], "network": berr[1]}}
+    out["speedup"] = ms_std / ms_net
+    del P, U, Pn, guess, sts, stn, its, itn, net, ctx
+    torch.cuda.empty_cache()
+    return out
 
 
 def batched_setups(seed0=3):

@@ -139,6 +139,85 @@ int grmhd_rk2_step(grmhd_ctx* c, double dt);
  * context's gamma_eos, floors, tolerance and stream. Asynchronous. */
 int grmhd_c2p(grmhd_ctx* c, long long n, const double* U, double* P, uint8_t* status, int* iters, int flags);
 
+/* Prim->cons of a flat-space batch (Sec. 2.1 eq. (conserved vector) with the Minkowski metric): P and U
+ * are device arrays [8][n] (structure of arrays), the layouts of grmhd_c2p; uses the context's gamma_eos
+ * and stream. Asynchronous. Errors: GRMHD_E_INVALID, GRMHD_E_CUDA. */
+int grmhd_p2c(grmhd_ctx* c, long long n, const double* P, double* U);
+
+/* ---- Learned initial guess for con2prim -------------------------------------------------------
+ * The paper's con2prim (Sec. 3.1: the Kastaun et al. 2021 master function f(mu), root mu = 1/(h W) in
+ * the bracket (0, mu_+]) starts its iteration from a fixed point of the bracket. These entry points
+ * add a small network that predicts where the root lies: an 8 -> 64 -> 64 -> 64 -> 2 multilayer
+ * perceptron with SiLU activations, BF16 weights and FP32 arithmetic, trained on the GPU by the
+ * library's own forward, backward and Adam kernels. The paper has no counterpart.
+ *
+ * Network: raw features x = (log1p(q), log1p(r^2)/2, log1p(b^2)/2, log1p((r.b)^2)/4, r/(1+q), b^2/(1+q),
+ * ln(max(eps_+, 1e-30))/10, ln W_+) of the invariants q = tau/D (clamped at 0), r^2 = S^2/D^2,
+ * b^2 = B^2/D, (r.b)^2 and of eps_+, W_+ (the master-function intermediates at mu_+), standardised
+ * (x - mean_x) * invstd_x; outputs o de-standardised y = o * std_y + mean_y with
+ *   y0 = -ln(1 - mu/mu_+)  (clipped to [0, 30]),   y1 = ln W at the root (auxiliary).
+ * The guess is mu_0 = mu_+ (1 - e^{-y0}); the safeguarded Newton iteration keeps its full bracket, so a
+ * poor guess costs iterations, never the root.
+ * Parameters theta (float [GRMHD_MLP_NPARAM]): W1 [64][8], b1 [64], W2 [64][64], b2 [64], W3 [64][64],
+ * b3 [64], W4 [2][64], b4 [2], row-major [out][in]. Standardisation norm (float [GRMHD_MLP_NNORM]):
+ * mean_x [8], invstd_x [8], mean_y [2], std_y [2].
+ * Loss of a batch of n samples (X raw features [n][8], T raw targets [n][2], device float):
+ *   L = (1/n) sum_s [(o0 - t0)^2 + aux (o1 - t1)^2],  t = (T - mean_y) / std_y.
+ * Every forward pass, in training too, uses the BF16 copy of the weights; gradients are taken with
+ * respect to that copy and applied to FP32 master weights by Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * State: one device workspace of grmhd_mlp_workspace_bytes() bytes, 256-byte aligned, owned by the
+ * caller (master weights, Adam moments, gradient, standardisation, BF16 weights). Functions without a
+ * context report errors through grmhd_last_error(NULL) (thread-local). */
+#define GRMHD_MLP_NPARAM 9026
+#define GRMHD_MLP_NNORM 20
+
+size_t grmhd_mlp_workspace_bytes(void);
+
+/* Load theta and norm (host float arrays) into the workspace, clear the Adam state and the gradient,
+ * and make the BF16 copy. Synchronises `stream`. Errors: GRMHD_E_INVALID, GRMHD_E_WORKSPACE (alignment),
+ * GRMHD_E_CUDA. */
+int grmhd_mlp_set_weights(void* ws, const float* theta, const float* norm, void* stream);
+
+/* Copy the FP32 master weights to theta (host) and, when theta_bf16 is not NULL, the BF16 weights used
+ * by the forward pass (as float) to theta_bf16. Synchronises `stream`. */
+int grmhd_mlp_get_weights(const void* ws, float* theta, float* theta_bf16, void* stream);
+
+/* Network outputs Y [n][2] (device float, raw units) for raw features X [n][8] (device float).
+ * Asynchronous. */
+int grmhd_mlp_forward(const void* ws, long long n, const float* X, float* Y, void* stream);
+
+/* Loss and gradient of one batch (n >= 1): the gradient accumulates in the workspace (cleared first) and
+ * is copied to grad (host float [GRMHD_MLP_NPARAM]) and the loss to *loss when those are not NULL
+ * (then the call synchronises). */
+int grmhd_mlp_grad(void* ws, long long n, const float* X, const float* T, double aux, float* grad, float* loss,
+                   void* stream);
+
+/* One Adam update with the gradient held in the workspace (step counts from 1; learning rate lr);
+ * refreshes the BF16 copy and clears the gradient. Asynchronous. */
+int grmhd_mlp_adam(void* ws, double lr, int step, void* stream);
+
+/* `steps` Adam steps over contiguous minibatches of `batch` samples of (X, T) (n samples, i.i.d.
+ * order assumed; the window wraps to the start when it would pass the end), learning rate decaying
+ * from lr to lr_end on a cosine; Adam's step count starts at first_step (>= 1). loss_dev (device
+ * float [steps], or NULL) receives the loss of each minibatch. Asynchronous. */
+int grmhd_mlp_train(void* ws, long long n, const float* X, const float* T, long long batch, int steps, double lr,
+                    double lr_end, double aux, int first_step, float* loss_dev, void* stream);
+
+/* Flat-space con2prim batch like grmhd_c2p (same U, P, status, iters layouts; the context's gamma_eos,
+ * floors, tolerance and stream) with the initial guess chosen by mlp_ws:
+ *   mlp_ws != NULL: the network evaluates every state and writes guess (device double [2][n], required):
+ *                   guess[t] = mu_0 = mu_+ (1 - e^{-y0}), guess[n + t] = mu_+. The solve runs at most 8
+ *                   Newton iterations from mu_0; if they do not converge (or mu_0 is not inside
+ *                   (0, mu_+)) it falls back to the standard start with the full iteration budget;
+ *   mlp_ws == NULL: the standard start mu_+/2 (guess is ignored).
+ * X (device float [n][8]) and T (device float [n][2]), when not NULL, receive the raw features and the
+ * targets (y0, ln W) of the solved root: training pairs from the library's own FP64 solve.
+ * GRMHD_GET_STATS then holds [0] iterations (master-function evaluations, all attempts), [4] states not
+ * converged and [7] fallbacks to the standard start. Asynchronous.
+ * Errors: GRMHD_E_INVALID, GRMHD_E_WORKSPACE, GRMHD_E_CUDA. */
+int grmhd_c2p_guess(grmhd_ctx* c, const void* mlp_ws, long long n, const double* U, double* P, uint8_t* status,
+                    int* iters, double* guess, float* X, float* T);
+
 /* Copy `what` (GRMHD_GET_*) to dst (`where` = GRMHD_HOST synchronises the stream). */
 int grmhd_get(grmhd_ctx* c, int what, void* dst, int where);
 

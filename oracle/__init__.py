@@ -75,7 +75,7 @@ def _load():
         lib.orc_geom_points.argtypes = [P, L, dp, dp]
         lib.orc_prim2con_points.argtypes = [P, L, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_c2p_points.argtypes = [P, L, dp, dp, dp, u8p, ip, ctypes.c_int]
-        lib.orc_c2p_mu_points.argtypes = [P, L, dp, dp, dp, dp]
+        lib.orc_c2p_mu_points.argtypes = [P, L, dp, dp, dp, dp, dp]
         lib.orc_recon_points.argtypes = [ctypes.c_int, L, dp, ctypes.c_double, dp, dp]
         lib.orc_weno5z_points.argtypes = [L, dp, ctypes.c_double, dp, dp, dp]
         lib.orc_riemann_points.argtypes = [P, L, dp, dp, dp, ctypes.c_int, dp, dp]
@@ -150,12 +150,15 @@ def c2p_points(p: OrcParams, xyz, U, floors: bool = True):
     return P, st, it
 
 
-def c2p_mu_points(p: OrcParams, xyz, U):
-    """Root mu = 1/(h W) and bracket end mu_+ of the con2prim master function at points."""
+def c2p_mu_points(p: OrcParams, xyz, U, aux: bool = False):
+    """Root mu = 1/(h W) and bracket end mu_+ of the con2prim master function at points; with
+    aux=True also eps and W of the master-function intermediates at mu_+."""
     xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
     U = np.ascontiguousarray(U, dtype=np.float64).reshape(-1, 8)
-    mu = np.zeros(len(U)); mup = np.zeros(len(U))
-    _load().orc_c2p_mu_points(ctypes.byref(p), len(U), _dp(xyz), _dp(U), _dp(mu), _dp(mup))
+    mu = np.zeros(len(U)); mup = np.zeros(len(U)); ax = np.zeros((len(U), 2))
+    _load().orc_c2p_mu_points(ctypes.byref(p), len(U), _dp(xyz), _dp(U), _dp(mu), _dp(mup), _dp(ax))
+    if aux:
+        return mu, mup, ax[:, 0].copy(), ax[:, 1].copy()
     return mu, mup
 
 

@@ -512,6 +512,7 @@ struct C2PResult {
   int status;
   int iters;
   double mu, mup;  // root of the master function and the upper end of its bracket
+  double eps_p, W_p;  // eps and W of the master-function intermediates at mu_+
 };
 
 // Undensitized conserved Uc = (D, S_j, tau, B^k) -> primitives, before floors.
@@ -521,7 +522,7 @@ static void con2prim_point(const orc_params& p, const Geom& G, const double* Uc,
   for (int v = 0; v < 8; ++v) R.P[v] = 0.0;
   bool finite = true;
   for (int v = 0; v < 8; ++v) finite = finite && std::isfinite(Uc[v]);
-  R.mu = R.mup = 0.0;
+  R.mu = R.mup = R.eps_p = R.W_p = 0.0;
   if (!finite || !(Uc[0] > 0.0)) {
     R.status = ST_BAD_INPUT;
     for (int k = 1; k <= 3; ++k) R.P[4 + k] = std::isfinite(Uc[4 + k]) ? Uc[4 + k] : 0.0;
@@ -554,7 +555,10 @@ static void con2prim_point(const orc_params& p, const Geom& G, const double* Uc,
   if (fa1 > 0.0) mup = brent([&](double m) { return fa_of(c, m); }, 0.0, 1.0, -1.0, fa1, nullptr);
   // Root of the master function on [0, mu_+]; f(0) = -1/nu(0) < 0.
   double f0 = master_f(c, 0.0, nullptr);
-  double fup = master_f(c, mup, nullptr);
+  MasterOut op;
+  double fup = master_f(c, mup, &op);
+  R.eps_p = op.eps;
+  R.W_p = op.W;
   double mu;
   if (fup <= 0.0) {
     // Analytically f(mu_+) >= 0 (nu >= (1+a)(1+eps)/W >= sqrt(1 - v^2) there); a non-positive
@@ -719,8 +723,10 @@ int orc_c2p_points(const orc_params* p, long n, const double* xyz, const double*
 }
 
 // Root mu = 1/(h W) of the master function and the bracket end mu_+ for densitized U at points
-// (the targets of the learned con2prim guess).
-int orc_c2p_mu_points(const orc_params* p, long n, const double* xyz, const double* U, double* mu, double* mup) {
+// (the targets of the learned con2prim guess); aux [n][2] (may be NULL) receives eps and W of the
+// master-function intermediates at mu_+ (two of its features).
+int orc_c2p_mu_points(const orc_params* p, long n, const double* xyz, const double* U, double* mu, double* mup,
+                      double* aux) {
   for (long q = 0; q < n; ++q) {
     Geom G;
     metric_eval(*p, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2], G);
@@ -730,6 +736,10 @@ int orc_c2p_mu_points(const orc_params* p, long n, const double* xyz, const doub
     con2prim_point(*p, G, Uc, R);
     mu[q] = R.mu;
     mup[q] = R.mup;
+    if (aux) {
+      aux[2 * q] = R.eps_p;
+      aux[2 * q + 1] = R.W_p;
+    }
   }
   return 0;
 }

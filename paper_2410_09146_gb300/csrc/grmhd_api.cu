@@ -357,6 +357,27 @@ int grmhd_set_cons(grmhd_ctx* c, const double* U, int where) {
 }
 
 static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt);
+int grmhd_p2c(grmhd_ctx* c, long long n, const double* P, double* U) {
+  if (!c) return GRMHD_E_INVALID;
+  if (n < 0 || (n > 0 && (!U || !P))) return fail(c, GRMHD_E_INVALID, "bad batch arguments");
+  CK(launch_p2c_batch(P, U, n, c->dp, c->stream), "prim2con batch");
+  return GRMHD_OK;
+}
+
+int grmhd_c2p_guess(grmhd_ctx* c, const void* mlp_ws, long long n, const double* U, double* P, uint8_t* status,
+                    int* iters, double* guess, float* X, float* T) {
+  if (!c) return GRMHD_E_INVALID;
+  if (n < 0 || (n > 0 && (!U || !P))) return fail(c, GRMHD_E_INVALID, "bad batch arguments");
+  if (mlp_ws && !guess) return fail(c, GRMHD_E_INVALID, "the network guess needs a guess buffer");
+  if (mlp_ws && ((uintptr_t)mlp_ws) % 256 != 0) return fail(c, GRMHD_E_WORKSPACE, "network workspace not 256-byte aligned");
+  unsigned long long* stats = c->scal + 8;
+  CK(cudaMemsetAsync(stats, 0, 8 * sizeof(unsigned long long), c->stream), "clearing stats");
+  if (mlp_ws) CK(launch_mlp_guess(mlp_ws, U, guess, n, c->dp, c->stream), "network guess");
+  CK(launch_c2p_guided(U, P, status, iters, n, c->dp, mlp_ws ? guess : nullptr, X, T, stats, c->stream),
+     "guided con2prim batch");
+  return GRMHD_OK;
+}
+
 static int grmhd_get_scalars(grmhd_ctx* c, int what, void* dst, int where);
 
 int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {

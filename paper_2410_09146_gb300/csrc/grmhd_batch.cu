@@ -1,4 +1,4 @@
-// Launch-size helper, the time-step finalisation and the flat con2prim batch (built with FMA).
+// Launch-size helper, the time-step finalisation and the flat con2prim / prim2con batches (built with FMA).
 #include "grmhd_kernels.cuh"
 #include "grmhd_launch.h"
 
@@ -33,6 +33,12 @@ cudaError_t launch_c2p_batch(const double* U, double* P, uint8_t* status, int* i
                              const DevParams& p, unsigned long long* stats, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_c2p_batch<<<grid_for(n, 128), 128, 0, s>>>(U, P, status, iters, n, flags, p, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p2c_batch(const double* P, double* U, long long n, const DevParams& p, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_p2c_batch<<<grid_for(n, 128), 128, 0, s>>>(P, U, n, p);
   return cudaGetLastError();
 }
 

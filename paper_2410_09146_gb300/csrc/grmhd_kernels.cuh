@@ -595,6 +595,22 @@ __global__ void k_prim2con(const T* __restrict__ P, double* __restrict__ U, DevP
   }
 }
 
+// Flat-space prim->cons over a batch: P, U are [8][n] (structure of arrays).
+static __global__ void k_p2c_batch(const double* __restrict__ P, double* __restrict__ U, long long n, DevParams p) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    Metric<double> m;
+    metric_at<double, MINKOWSKI>(p, 0.0, 0.0, 0.0, m);
+    double Pc[NV], U5[5];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Pc[q] = P[q * n + t];
+    prim_to_cons5<double>(Pc, m, p.gamma_eos, U5);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q * n + t] = U5[q];
+#pragma unroll
+    for (int q = 5; q < NV; ++q) U[q * n + t] = Pc[q];
+  }
+}
+
 // Flat-space con2prim over a batch: U, P are [8][n] (structure of arrays).
 // flags bit 0: use P as the warm start.
 static __global__ void k_c2p_batch(const double* __restrict__ U, double* __restrict__ P, uint8_t* __restrict__ status,

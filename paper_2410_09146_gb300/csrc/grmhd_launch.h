@@ -40,6 +40,16 @@ cudaError_t launch_finalize_dt(const unsigned long long* ms, double* dt, const D
 cudaError_t launch_batch_finalize_dt(const unsigned long long* ms, double* dt, double cfl, cudaStream_t s);
 cudaError_t launch_c2p_batch(const double* U, double* P, uint8_t* status, int* iters, long long n, int flags,
                              const DevParams& p, unsigned long long* stats, cudaStream_t s);
+cudaError_t launch_p2c_batch(const double* P, double* U, long long n, const DevParams& p, cudaStream_t s);
+
+// Learned-guess con2prim (grmhd_mlp.cu): the network's start (mu_0, mu_+) [2][n] for flat-space
+// states, and the batch solve from it (guess != NULL, with fallback) or from mu_+/2, optionally
+// recording training pairs (X, T).
+cudaError_t launch_mlp_guess(const void* mlp_ws, const double* U, double* guess, long long n, const DevParams& p,
+                             cudaStream_t s);
+cudaError_t launch_c2p_guided(const double* U, double* P, uint8_t* status, int* iters, long long n,
+                              const DevParams& p, const double* guess, float* X, float* T, unsigned long long* stats,
+                              cudaStream_t s);
 
 int grid_for(long long n, int threads);
 

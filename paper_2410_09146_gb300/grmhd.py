@@ -25,6 +25,7 @@ METRIC = {"minkowski": 0, "kerr_schild": 1}
 BC = {"periodic": 0, "fixed": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 ST_RHO_FLOOR, ST_EPS_FLOOR, ST_W_CAP, ST_NOT_CONVERGED, ST_BAD_INPUT = 1, 2, 4, 8, 16
+GRMHD_MLP_NPARAM, GRMHD_MLP_NNORM = 9026, 20
 
 
 class GrmhdError(RuntimeError):
@@ -88,6 +89,18 @@ def lib():
         L.grmhd_batch_set_tile.argtypes = [vp, ctypes.c_int]
         L.grmhd_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.grmhd_set_graph.argtypes = [vp, ctypes.c_int]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.grmhd_mlp_workspace_bytes.argtypes = []
+        L.grmhd_mlp_workspace_bytes.restype = ctypes.c_size_t
+        L.grmhd_mlp_set_weights.argtypes = [vp, fp, fp, vp]
+        L.grmhd_mlp_get_weights.argtypes = [vp, fp, fp, vp]
+        L.grmhd_mlp_forward.argtypes = [vp, ctypes.c_longlong, vp, vp, vp]
+        L.grmhd_mlp_grad.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.c_double, fp, fp, vp]
+        L.grmhd_mlp_adam.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp]
+        L.grmhd_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
+        L.grmhd_p2c.argtypes = [vp, ctypes.c_longlong, vp, vp]
+        L.grmhd_c2p_guess.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp]
         L.grmhd_last_error.argtypes = [vp]
         L.grmhd_last_error.restype = ctypes.c_char_p
         L.grmhd_destroy.argtypes = [vp]
@@ -162,6 +175,68 @@ def grmhd_c2p(ctx: int, n: int, U_ptr: int, P_ptr: int, status_ptr: int = 0, ite
               flags: int = 0) -> None:
     vp = ctypes.c_void_p
     _check(lib().grmhd_c2p(ctx, n, vp(U_ptr), vp(P_ptr), vp(status_ptr or None), vp(iters_ptr or None), flags), ctx)
+
+
+def grmhd_p2c(ctx: int, n: int, P_ptr: int, U_ptr: int) -> None:
+    vp = ctypes.c_void_p
+    _check(lib().grmhd_p2c(ctx, n, vp(P_ptr), vp(U_ptr)), ctx)
+
+
+def grmhd_c2p_guess(ctx: int, mlp_ws: int, n: int, U_ptr: int, P_ptr: int, status_ptr: int = 0, iters_ptr: int = 0,
+                    guess_ptr: int = 0, X_ptr: int = 0, T_ptr: int = 0) -> None:
+    vp = ctypes.c_void_p
+    _check(lib().grmhd_c2p_guess(ctx, vp(mlp_ws or None), n, vp(U_ptr), vp(P_ptr), vp(status_ptr or None),
+                                 vp(iters_ptr or None), vp(guess_ptr or None), vp(X_ptr or None), vp(T_ptr or None)),
+           ctx)
+
+
+def _fp(a):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def grmhd_mlp_workspace_bytes() -> int:
+    return int(lib().grmhd_mlp_workspace_bytes())
+
+
+def grmhd_mlp_set_weights(ws: int, theta, norm, stream_ptr: int) -> None:
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    norm = np.ascontiguousarray(norm, dtype=np.float32)
+    assert theta.size == GRMHD_MLP_NPARAM and norm.size == GRMHD_MLP_NNORM
+    _check(lib().grmhd_mlp_set_weights(ctypes.c_void_p(ws), _fp(theta), _fp(norm), ctypes.c_void_p(stream_ptr)))
+
+
+def grmhd_mlp_get_weights(ws: int, stream_ptr: int):
+    """(FP32 master weights, BF16 weights as float32)."""
+    theta = np.zeros(GRMHD_MLP_NPARAM, np.float32)
+    wb = np.zeros(GRMHD_MLP_NPARAM, np.float32)
+    _check(lib().grmhd_mlp_get_weights(ctypes.c_void_p(ws), _fp(theta), _fp(wb), ctypes.c_void_p(stream_ptr)))
+    return theta, wb
+
+
+def grmhd_mlp_forward(ws: int, n: int, X_ptr: int, Y_ptr: int, stream_ptr: int) -> None:
+    vp = ctypes.c_void_p
+    _check(lib().grmhd_mlp_forward(vp(ws), n, vp(X_ptr), vp(Y_ptr), vp(stream_ptr)))
+
+
+def grmhd_mlp_grad(ws: int, n: int, X_ptr: int, T_ptr: int, aux: float, stream_ptr: int):
+    """(loss, gradient [NPARAM] float32) of one batch."""
+    vp = ctypes.c_void_p
+    g = np.zeros(GRMHD_MLP_NPARAM, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(lib().grmhd_mlp_grad(vp(ws), n, vp(X_ptr), vp(T_ptr), aux, _fp(g), _fp(loss), vp(stream_ptr)))
+    return float(loss[0]), g
+
+
+def grmhd_mlp_adam(ws: int, lr: float, step: int, stream_ptr: int) -> None:
+    _check(lib().grmhd_mlp_adam(ctypes.c_void_p(ws), lr, step, ctypes.c_void_p(stream_ptr)))
+
+
+def grmhd_mlp_train(ws: int, n: int, X_ptr: int, T_ptr: int, batch: int, steps: int, lr: float, lr_end: float,
+                    aux: float, first_step: int, loss_ptr: int, stream_ptr: int) -> None:
+    vp = ctypes.c_void_p
+    _check(lib().grmhd_mlp_train(vp(ws), n, vp(X_ptr), vp(T_ptr), batch, steps, lr, lr_end, aux, first_step,
+                                 vp(loss_ptr or None), vp(stream_ptr)))
 
 
 def grmhd_get(ctx: int, what: int, dst) -> None:
@@ -375,3 +450,94 @@ class Context:
         n = U.shape[1]
         grmhd_c2p(self.ctx, n, U.data_ptr(), P.data_ptr(), 0 if status is None else status.data_ptr(),
                   0 if iters is None else iters.data_ptr(), flags)
+
+    def p2c(self, P, U):
+        """Flat-space prim->cons batch of torch device tensors P, U of shape [8][n] (float64)."""
+        grmhd_p2c(self.ctx, P.shape[1], P.data_ptr(), U.data_ptr())
+
+    def c2p_guess(self, U, P, status=None, iters=None, net=None, guess=None, X=None, T=None):
+        """Flat-space con2prim batch [8][n] with the network's start (net: GuessNet; guess: float64 [2][n]
+        receives (mu_0, mu_+)) or the standard start (net None); X [n][8] and T [n][2] (float32) receive
+        training pairs when given."""
+        n = U.shape[1]
+        if net is not None and guess is None:
+            raise GrmhdError("the network guess needs a guess buffer")
+        ptr = lambda a: 0 if a is None else a.data_ptr()
+        grmhd_c2p_guess(self.ctx, 0 if net is None else net.ws_ptr, n, U.data_ptr(), P.data_ptr(), ptr(status),
+                        ptr(iters), ptr(guess) if net is not None else 0, ptr(X), ptr(T))
+
+
+class GuessNet:
+    """The learned con2prim guess: a device workspace with weights, Adam state and standardisation.
+
+    Initialisation (He-uniform hidden layers, small output layer, zero biases) and the standardisation
+    statistics are host-side set-up; forward, backward and Adam run in the library's kernels.
+    """
+
+    def __init__(self, device: int = 0, stream=None, seed: int = 0):
+        import torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = grmhd_mlp_workspace_bytes()
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.step = 0
+        self.norm = np.zeros(GRMHD_MLP_NNORM, np.float32)
+        self.norm[8:16] = 1.0
+        self.norm[18:20] = 1.0
+        self.set_weights(init_weights(seed), self.norm)
+
+    def set_weights(self, theta, norm):
+        self.norm = np.asarray(norm, np.float32).copy()
+        grmhd_mlp_set_weights(self.ws_ptr, theta, self.norm, self.stream.cuda_stream)
+        self.step = 0
+
+    def weights(self):
+        return grmhd_mlp_get_weights(self.ws_ptr, self.stream.cuda_stream)
+
+    def fit_norm(self, X, T, sample: int = 1 << 20):
+        """Standardisation from (a leading sample of) raw features X [n][8] and targets T [n][2]
+        (device float32); keeps the weights and resets Adam."""
+        Xs = X[:sample].double().cpu().numpy()
+        Ts = T[:sample].double().cpu().numpy()
+        norm = np.zeros(GRMHD_MLP_NNORM)
+        norm[0:8] = Xs.mean(0)
+        norm[8:16] = 1.0 / np.maximum(Xs.std(0), 1e-6)
+        norm[16:18] = Ts.mean(0)
+        norm[18:20] = np.maximum(Ts.std(0), 1e-6)
+        theta, _ = self.weights()
+        self.set_weights(theta, norm)
+
+    def forward(self, X, Y=None):
+        import torch
+        n = X.shape[0]
+        if Y is None:
+            Y = torch.empty((n, 2), dtype=torch.float32, device=X.device)
+        grmhd_mlp_forward(self.ws_ptr, n, X.data_ptr(), Y.data_ptr(), self.stream.cuda_stream)
+        return Y
+
+    def grad(self, X, T, aux: float = 0.1):
+        return grmhd_mlp_grad(self.ws_ptr, X.shape[0], X.data_ptr(), T.data_ptr(), aux, self.stream.cuda_stream)
+
+    def adam(self, lr: float):
+        self.step += 1
+        grmhd_mlp_adam(self.ws_ptr, lr, self.step, self.stream.cuda_stream)
+
+    def train(self, X, T, batch: int, steps: int, lr: float, lr_end: float = 0.0, aux: float = 0.1, losses=None):
+        """Adam over contiguous minibatches (see grmhd_mlp_train); losses: device float32 [steps] or None."""
+        grmhd_mlp_train(self.ws_ptr, X.shape[0], X.data_ptr(), T.data_ptr(), batch, steps, lr, lr_end, aux,
+                        self.step + 1, 0 if losses is None else losses.data_ptr(), self.stream.cuda_stream)
+        self.step += steps
+
+
+def init_weights(seed: int = 0):
+    """He-uniform hidden layers, output layer scaled by 0.1, zero biases (float32 [GRMHD_MLP_NPARAM])."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in, scale in ((64, 8, 1.0), (64, 64, 1.0), (64, 64, 1.0), (2, 64, 0.1)):
+        bound = scale * np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-bound, bound, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    theta = np.concatenate(parts).astype(np.float32)
+    assert theta.size == GRMHD_MLP_NPARAM
+    return theta

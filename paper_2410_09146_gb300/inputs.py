@@ -236,3 +236,32 @@ def c2p_states(n: int, seed: int = 4, gamma_eos: float = GAMMA_DEFAULT, rho_rang
     P[:, 4] = press / (gamma_eos - 1.0)
     P[:, 5:8] = (W * np.sqrt(sig * rho))[:, None] * db
     return P
+
+
+def c2p_states_device(n: int, seed: int, device, gamma_eos: float = GAMMA_DEFAULT, rho_range=(1e-8, 1.0),
+                      w_range=(1.0, 50.0), sigma_range=(1e-4, 1e3)):
+    """The distribution of c2p_states drawn on a CUDA device from a seeded torch generator:
+    primitive states [8][n] (float64, structure of arrays) for workloads too large to draw on the host.
+    The states differ from c2p_states' (another generator); the distribution is the same."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = dict(dtype=torch.float64, device=device)
+
+    def logu(lo, hi):
+        return 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * torch.rand(n, generator=g, **f64))
+
+    rho = logu(*rho_range)
+    W = logu(*w_range)
+    sig = logu(*sigma_range)
+    press = 0.01 * rho ** (5.0 / 3.0) * 10.0 ** (2.0 * torch.rand(n, generator=g, **f64) - 1.0)
+    dv = torch.randn(3, n, generator=g, **f64)
+    dv /= torch.linalg.vector_norm(dv, dim=0, keepdim=True)
+    db = torch.randn(3, n, generator=g, **f64)
+    db /= torch.linalg.vector_norm(db, dim=0, keepdim=True)
+    P = torch.empty(8, n, **f64)
+    P[0] = rho
+    P[1:4] = torch.sqrt(W * W - 1.0) * dv
+    P[4] = press / (gamma_eos - 1.0)
+    P[5:8] = W * torch.sqrt(sig * rho) * db
+    return P

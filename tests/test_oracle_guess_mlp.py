@@ -1,0 +1,162 @@
+"""Pins of the FP64 reference of the learned con2prim guess (oracle/guess_mlp.py).
+
+* backward() against central finite differences of the loss (every parameter block, both outputs);
+* a network reduced to one unit per layer, evaluated in closed form with math.exp;
+* the first Adam step moves every parameter by lr * sign(g) (bias-corrected m/sqrt(v) = g/|g|);
+* BF16 rounding of values with known nearest-even results, and against torch's bfloat16 cast;
+* features and targets of the state at rest without field, where mu = 1/h and mu_+ = 1 in closed form;
+  of cold moving states without field, where mu = mu_+ = 1/W and eps(mu_+) = 0; and targets of random
+  states against the oracle's own con2prim root and W.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import guess_mlp as M
+from paper_2410_09146_gb300 import inputs as I
+
+
+def _net(seed, scale=0.4):
+    rng = np.random.default_rng(seed)
+    theta = rng.normal(0, scale, M.NPARAM)
+    norm = np.concatenate([rng.normal(0, 0.5, 8), rng.uniform(0.5, 2, 8), rng.normal(0, 1, 2),
+                           rng.uniform(0.5, 3, 2)])
+    return theta, norm
+
+
+def test_gradient_matches_finite_differences():
+    theta, norm = _net(1)
+    rng = np.random.default_rng(2)
+    X = rng.normal(0, 1, (12, 8))
+    T = rng.normal(0, 2, (12, 2))
+    aux = 0.3
+    _, g = M.loss_and_grad(theta, norm, X, T, aux)
+    # every bias and output weight, and a random sample of each weight matrix
+    idx = []
+    for name, (o, shape) in M.OFFSETS.items():
+        size = int(np.prod(shape))
+        if name.startswith("b") or name == "W4":
+            idx.extend(range(o, o + size))
+        else:
+            idx.extend(o + rng.choice(size, 40, replace=False))
+    h = 1e-6
+    for i in idx:
+        tp = theta.copy(); tp[i] += h
+        tm = theta.copy(); tm[i] -= h
+        fd = (M.loss_and_grad(tp, norm, X, T, aux)[0] - M.loss_and_grad(tm, norm, X, T, aux)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_single_unit_chain_closed_form():
+    P = {k: np.zeros(s) for k, (_, s) in M.OFFSETS.items()}
+    a1, c1, a2, c2, a3, c3, a40, a41, c40, c41 = 0.7, -0.2, 1.3, 0.1, -0.9, 0.4, 1.1, -0.6, 0.05, 0.3
+    P["W1"][0, 2] = a1; P["b1"][0] = c1
+    P["W2"][0, 0] = a2; P["b2"][0] = c2
+    P["W3"][0, 0] = a3; P["b3"][0] = c3
+    P["W4"][0, 0] = a40; P["W4"][1, 0] = a41; P["b4"][:] = (c40, c41)
+    theta = M.pack(P)
+    norm = np.zeros(M.NNORM)
+    norm[0:8] = 0.25; norm[8:16] = 2.0; norm[16:18] = (1.5, -0.5); norm[18:20] = (3.0, 0.5)
+    X = np.array([[0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0]])
+
+    def silu(z):
+        return z / (1.0 + math.exp(-z))
+
+    x2 = (1.0 - 0.25) * 2.0
+    h3 = silu(a3 * silu(a2 * silu(a1 * x2 + c1) + c2) + c3)
+    want = [(a40 * h3 + c40) * 3.0 + 1.5, (a41 * h3 + c41) * 0.5 - 0.5]
+    got = M.forward(theta, norm, X)[0]
+    assert np.allclose(got, want, rtol=1e-14, atol=1e-15)
+
+
+def test_first_adam_step_is_lr_sign():
+    rng = np.random.default_rng(3)
+    theta = rng.normal(size=50)
+    g = rng.normal(size=50)
+    th, m, v = M.adam_step(theta, np.zeros(50), np.zeros(50), g, 1, lr=1e-3)
+    assert np.allclose(th, theta - 1e-3 * np.sign(g), rtol=0, atol=1e-3 * 1e-8 / np.min(np.abs(g)) + 1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_bf16_rounding():
+    vals = np.array([1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -20, -(1 + 2.0 ** -8), 0.0,
+                     3.0e38, 1e-40], np.float32)
+    want = np.array([1.0, 1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, -1.0, 0.0], np.float64)
+    got = M.bf16_round(vals)
+    assert np.array_equal(got[:6], want)
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    r = (rng.normal(size=10000) * 10.0 ** rng.uniform(-5, 5, 10000)).astype(np.float32)
+    ref = torch.tensor(r).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(M.bf16_round(r), ref)
+    assert np.array_equal(M.bf16_round(vals), torch.tensor(vals).to(torch.bfloat16).to(torch.float64).numpy())
+
+
+def test_features_targets_at_rest(orc):
+    s = I.linear_wave_setup(8)
+    p = orc.params(s)
+    eps = np.array([1e-6, 1e-3, 0.1, 1.0, 30.0])
+    rho = np.array([1.0, 0.3, 1e-4, 2.0, 0.01])
+    P = np.zeros((5, 8))
+    P[:, 0] = rho
+    P[:, 4] = rho * eps
+    x = np.zeros((5, 3))
+    U = orc.prim2con_points(p, x, P)["U"]
+    q, r2, b2, rb2 = M.invariants_flat(U)
+    assert np.allclose(q, eps, rtol=1e-14) and np.all(r2 == 0) and np.all(b2 == 0)
+    mu, mup, eps_p, W_p = orc.c2p_mu_points(p, x, U, aux=True)
+    h = 1.0 + s.gamma_eos * eps
+    assert np.allclose(mup, 1.0, rtol=1e-15) and np.allclose(mu, 1.0 / h, rtol=1e-13)
+    # at mu_+ = 1 with r = 0: W = 1 and eps = q
+    assert np.allclose(W_p, 1.0, rtol=1e-15) and np.allclose(eps_p, eps, rtol=1e-13)
+    X = M.features(q, r2, b2, rb2, eps_p, W_p)
+    assert np.allclose(X[:, 0], np.log1p(eps), rtol=1e-14) and np.allclose(X[:, 6], 0.1 * np.log(eps), rtol=1e-12)
+    assert np.all(X[:, 1:6] == 0) and np.all(X[:, 7] == 0)
+    T = M.targets(mu, mup, np.ones(5))
+    assert np.allclose(T[:, 0], np.log(h / (h - 1.0)), rtol=1e-9) and np.all(T[:, 1] == 0)
+    # the guess map inverts the first target
+    assert np.allclose(M.guess_from_output(T[:, 0], mup), mu, rtol=1e-12)
+
+
+def test_features_of_cold_moving_states(orc):
+    # cold gas, B = 0, moving: q = W - 1, r^2 = W^2 - 1, so mu_+ = 1/W is the root itself, W(mu_+) = W
+    # and eps(mu_+) = 0 (to roundoff of the W-sized terms)
+    s = I.linear_wave_setup(8)
+    p = orc.params(s)
+    W = np.array([1.5, 3.0, 10.0, 40.0])
+    d = np.array([[1.0, 0, 0], [0, 0.6, 0.8], [0.0, 0, 1.0], [0.48, 0.6, 0.64]])
+    P = np.zeros((4, 8))
+    P[:, 0] = 0.5
+    P[:, 1:4] = np.sqrt(W * W - 1)[:, None] * d
+    x = np.zeros((4, 3))
+    U = orc.prim2con_points(p, x, P)["U"]
+    q, r2, b2, rb2 = M.invariants_flat(U)
+    assert np.allclose(q, W - 1, rtol=1e-13) and np.allclose(r2, W * W - 1, rtol=1e-13)
+    mu, mup, eps_p, W_p = orc.c2p_mu_points(p, x, U, aux=True)
+    assert np.allclose(mup, 1.0 / W, rtol=1e-13) and np.allclose(W_p, W, rtol=1e-12)
+    assert np.all(np.abs(eps_p) <= 1e-13 * W * W)
+    X = M.features(q, r2, b2, rb2, eps_p, W_p)
+    assert np.all(X[:, 6] <= 0.1 * np.log(1e-13 * W * W) + 1e-12) and np.allclose(X[:, 7], np.log(W), rtol=1e-12)
+
+
+def test_targets_of_random_states(orc):
+    s = I.linear_wave_setup(8)
+    p = orc.params(s)
+    Ps = I.c2p_states(3000, seed=21)
+    x = np.zeros((len(Ps), 3))
+    U = orc.prim2con_points(p, x, Ps)["U"]
+    mu, mup = orc.c2p_mu_points(p, x, U)
+    Po, st, _ = orc.c2p_points(p, x, U, floors=False)
+    ok = st == 0
+    W = np.sqrt(1.0 + np.sum(Po[:, 1:4] ** 2, 1))
+    T = M.targets(mu, mup, W)
+    assert np.all(mu <= mup) and np.all(mu > 0)
+    assert np.all((T[:, 0] >= 0) & (T[:, 0] <= M.Y0_MAX))
+    # the root is 1/(h W) of the recovered primitives
+    h = 1.0 + s.gamma_eos * Po[:, 4] / Po[:, 0]
+    assert np.allclose((mu * h * W)[ok], 1.0, rtol=1e-9)
+    # ... and W of the generating primitives on well-conditioned states
+    W0 = np.sqrt(1.0 + np.sum(Ps[:, 1:4] ** 2, 1))
+    good = ok & (W0 < 10)
+    assert np.allclose(T[good, 1], np.log(W0[good]), atol=1e-9)

@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-guess", action="store_true")
     ap.add_argument("--guess-states", type=int, default=100_000_000)
+    ap.add_argument("--guess-only", action="store_true",
+                    help="run only the learned-guess con2prim section and print its JSON (profiling aid)")
     return ap.parse_args()
 
 
@@ -366,10 +368,14 @@ def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=
         return a.elapsed_time(b) / reps
 
     ms_std = timed(lambda: ctx.c2p_guess(U, Ps, sts, its))
-    ms_net = timed(lambda: ctx.c2p_guess(U, Pn, stn, itn, net=net, guess=guess))
-    fallbacks = int(ctx.stats()[7])
-    # backward error |U(P) - U| / (|D| + |tau| + |S|) of each solution on states neither solve floored or
-    # flagged (forward differences between the two are bounded by the conditioning, not the solver)
+    ms_f32 = timed(lambda: ctx.c2p_guess(U, Pn, stn, itn, net=net, guess=guess, fp32=True))
+    fall_f32 = int(ctx.stats()[7])
+    sum_f32 = _iter_summary(itn, stn, torch)
+    mis_f32 = int((sts != stn).sum())
+    ms_tc = timed(lambda: ctx.c2p_guess(U, Pn, stn, itn, net=net))
+    stats_tc = ctx.stats()
+    # backward error |U(P) - U| / (|D| + |tau| + |S|) of each solution on states no solve floored or
+    # flagged (forward differences between them are bounded by the conditioning, not the solver)
     plain = (sts == 0) & (stn == 0)
     scale = U[0].abs() + U[4].abs() + torch.linalg.vector_norm(U[1:4], dim=0)
     Ub = torch.empty_like(U)
@@ -383,11 +389,16 @@ def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=
                      "steps": train_steps, "batch": 152 * 128, "ms": train_ms,
                      "loss_first": float(lh[:10].mean()), "loss_last": float(lh[-100:].mean())},
            "standard": dict(_iter_summary(its, sts, torch), ms=ms_std, states_per_s=n_states / (ms_std / 1e3)),
-           "network": dict(_iter_summary(itn, stn, torch), ms=ms_net, states_per_s=n_states / (ms_net / 1e3),
-                           fallback_frac=fallbacks / n_states),
-           "same_status": bool(torch.equal(sts, stn)),
-           "max_backward_err": {"standard": berr[0], "network": berr[1]}}
-    out["speedup"] = ms_std / ms_net
+           "network_tc": dict(_iter_summary(itn, stn, torch), ms=ms_tc, states_per_s=n_states / (ms_tc / 1e3),
+                              fallback_frac=int(stats_tc[7]) / n_states, abandoned_tiles=int(stats_tc[6]),
+                              kernel="fused: hidden layers as tcgen05 MMAs, FP64 Newton in the same kernel"),
+           "network_fp32": dict(sum_f32, ms=ms_f32, states_per_s=n_states / (ms_f32 / 1e3),
+                                fallback_frac=fall_f32 / n_states,
+                                kernel="network on the FP32 cores, then the FP64 solve (two kernels)"),
+           "status_mismatch": {"network_fp32": mis_f32, "network_tc": int((sts != stn).sum())},
+           "max_backward_err": {"standard": berr[0], "network_tc": berr[1]}}
+    out["speedup_tc"] = ms_std / ms_tc
+    out["speedup_fp32"] = ms_std / ms_f32
     del P, U, Pn, guess, sts, stn, its, itn, net, ctx
     torch.cuda.empty_cache()
     return out
@@ -531,6 +542,15 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.guess_only:
+        import torch
+        from paper_2410_09146_gb300 import build as B
+        B.build()
+        from paper_2410_09146_gb300 import grmhd as G
+        from paper_2410_09146_gb300 import inputs as I
+        torch.cuda.set_device(0)
+        print(json.dumps({"c2p_guess": run_guess(G, I, 0, n_states=args.guess_states)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -204,19 +204,26 @@ int grmhd_mlp_train(void* ws, long long n, const float* X, const float* T, long 
                     double lr_end, double aux, int first_step, float* loss_dev, void* stream);
 
 /* Flat-space con2prim batch like grmhd_c2p (same U, P, status, iters layouts; the context's gamma_eos,
- * floors, tolerance and stream) with the initial guess chosen by mlp_ws:
- *   mlp_ws != NULL: the network evaluates every state and writes guess (device double [2][n], required):
- *                   guess[t] = mu_0 = mu_+ (1 - e^{-y0}), guess[n + t] = mu_+. The solve runs at most 8
- *                   Newton iterations from mu_0; if they do not converge (or mu_0 is not inside
- *                   (0, mu_+)) it falls back to the standard start with the full iteration budget;
- *   mlp_ws == NULL: the standard start mu_+/2 (guess is ignored).
+ * floors, tolerance and stream) with the initial guess chosen by mlp_ws and flags:
+ *   mlp_ws == NULL: the standard start mu_+/2 (guess ignored);
+ *   mlp_ws != NULL: the network's start mu_0 = mu_+ (1 - e^{-y0}). The solve runs at most 8 Newton
+ *                   iterations from mu_0; if they do not converge (or mu_0 is not inside (0, mu_+)) it
+ *                   falls back to the standard start with the full iteration budget. Network, flags 0:
+ *                   one fused kernel per tile of 128 states, the two 64 x 64 layers as tcgen05 MMAs
+ *                   (BF16 operands in shared memory, FP32 accumulators in tensor memory); guess (device
+ *                   double [2][n], may be NULL) receives (mu_0, mu_+). flags GRMHD_GUESS_FP32: the
+ *                   network on the FP32 cores in a separate kernel that writes guess (then required),
+ *                   then the solve.
  * X (device float [n][8]) and T (device float [n][2]), when not NULL, receive the raw features and the
- * targets (y0, ln W) of the solved root: training pairs from the library's own FP64 solve.
+ * targets (y0, ln W) of the solved root: training pairs from the library's own FP64 solve (standard
+ * start or GRMHD_GUESS_FP32 only; GRMHD_E_INVALID otherwise).
  * GRMHD_GET_STATS then holds [0] iterations (master-function evaluations, all attempts), [4] states not
- * converged and [7] fallbacks to the standard start. Asynchronous.
- * Errors: GRMHD_E_INVALID, GRMHD_E_WORKSPACE, GRMHD_E_CUDA. */
+ * converged, [6] tiles of the fused kernel abandoned because an MMA completion was not observed within
+ * its wait limit (0 in normal operation; the states of such tiles are not written) and [7] fallbacks
+ * to the standard start. Asynchronous. Errors: GRMHD_E_INVALID, GRMHD_E_WORKSPACE, GRMHD_E_CUDA. */
+#define GRMHD_GUESS_FP32 1
 int grmhd_c2p_guess(grmhd_ctx* c, const void* mlp_ws, long long n, const double* U, double* P, uint8_t* status,
-                    int* iters, double* guess, float* X, float* T);
+                    int* iters, double* guess, float* X, float* T, int flags);
 
 /* Copy `what` (GRMHD_GET_*) to dst (`where` = GRMHD_HOST synchronises the stream). */
 int grmhd_get(grmhd_ctx* c, int what, void* dst, int where);

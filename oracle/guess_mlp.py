@@ -10,10 +10,11 @@ master-function intermediates at mu_+, carry the thermal content that fixes how 
 mu_+ (features()).
 
     x  = (features - mean_x) * invstd_x
-    h1 = silu(W1 x + b1),  h2 = silu(W2 h1 + b2),  h3 = silu(W3 h2 + b3)
-    o  = W4 h3 + b4,       y = o * std_y + mean_y
+    h1 = bf16(silu(W1 x + b1)),  h2 = bf16(silu(W2 h1 + b2)),  h3 = silu(W3 h2 + b3)
+    o  = W4 h3 + b4,             y = o * std_y + mean_y
 
-with 64 hidden units per layer and SiLU(z) = z / (1 + e^-z). The two outputs are
+with 64 hidden units per layer, SiLU(z) = z / (1 + e^-z) and bf16() the round-to-nearest-even BF16
+rounding of the two activations that feed the 64 x 64 layers (tensor-core operands on the GPU). The two outputs are
 y0 = -ln(1 - mu/mu_+) (clipped to [0, 30]) and y1 = ln W at the root. The loss is the mean over
 samples of (o0 - t0)^2 + aux (o1 - t1)^2 in standardised units t = (y - mean_y)/std_y.
 
@@ -131,15 +132,21 @@ def _dsilu(z):
     return s * (1.0 + z * (1.0 - s))
 
 
-def forward(theta, norm, X, cache: bool = False):
-    """Network outputs y [n][2] (de-standardised) for raw features X [n][8]."""
+def forward(theta, norm, X, cache: bool = False, round_h: bool = True):
+    """Network outputs y [n][2] (de-standardised) for raw features X [n][8].
+
+    round_h: the hidden activations h1 and h2 (the inputs of the two 64 x 64 layers, the tensor-core
+    operands on the GPU) are rounded to BF16, as every forward pass of the library does; the gradient
+    passes through the rounding unchanged (straight-through).
+    """
     P = unpack(theta)
     norm = np.asarray(norm, dtype=np.float64)
+    rnd = bf16_round if round_h else (lambda a: a)
     x = (np.asarray(X, dtype=np.float64) - norm[:NIN]) * norm[NIN:2 * NIN]
     z1 = x @ P["W1"].T + P["b1"]
-    h1 = _silu(z1)
+    h1 = rnd(_silu(z1))
     z2 = h1 @ P["W2"].T + P["b2"]
-    h2 = _silu(z2)
+    h2 = rnd(_silu(z2))
     z3 = h2 @ P["W3"].T + P["b3"]
     h3 = _silu(z3)
     o = h3 @ P["W4"].T + P["b4"]
@@ -149,11 +156,11 @@ def forward(theta, norm, X, cache: bool = False):
     return y
 
 
-def loss_and_grad(theta, norm, X, T, aux: float):
+def loss_and_grad(theta, norm, X, T, aux: float, round_h: bool = True):
     """Loss (mean over samples) and its gradient [NPARAM] for raw features X and raw targets T."""
     P = unpack(theta)
     norm = np.asarray(norm, dtype=np.float64)
-    _, c = forward(theta, norm, X, cache=True)
+    _, c = forward(theta, norm, X, cache=True, round_h=round_h)
     n = len(X)
     t = (np.asarray(T, dtype=np.float64) - norm[2 * NIN:2 * NIN + 2]) / norm[2 * NIN + 2:]
     wgt = np.array([1.0, aux])

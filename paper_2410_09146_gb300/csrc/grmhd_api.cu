@@ -365,13 +365,21 @@ int grmhd_p2c(grmhd_ctx* c, long long n, const double* P, double* U) {
 }
 
 int grmhd_c2p_guess(grmhd_ctx* c, const void* mlp_ws, long long n, const double* U, double* P, uint8_t* status,
-                    int* iters, double* guess, float* X, float* T) {
+                    int* iters, double* guess, float* X, float* T, int flags) {
   if (!c) return GRMHD_E_INVALID;
   if (n < 0 || (n > 0 && (!U || !P))) return fail(c, GRMHD_E_INVALID, "bad batch arguments");
-  if (mlp_ws && !guess) return fail(c, GRMHD_E_INVALID, "the network guess needs a guess buffer");
+  if (flags & ~GRMHD_GUESS_FP32) return fail(c, GRMHD_E_INVALID, "unknown flags");
+  const bool fp32 = (flags & GRMHD_GUESS_FP32) != 0;
+  if (mlp_ws && fp32 && !guess) return fail(c, GRMHD_E_INVALID, "the FP32-core guess needs a guess buffer");
+  if (mlp_ws && !fp32 && (X || T))
+    return fail(c, GRMHD_E_INVALID, "training pairs are recorded by the standard or the FP32-core path only");
   if (mlp_ws && ((uintptr_t)mlp_ws) % 256 != 0) return fail(c, GRMHD_E_WORKSPACE, "network workspace not 256-byte aligned");
   unsigned long long* stats = c->scal + 8;
   CK(cudaMemsetAsync(stats, 0, 8 * sizeof(unsigned long long), c->stream), "clearing stats");
+  if (mlp_ws && !fp32) {
+    CK(launch_c2p_net_tc(mlp_ws, U, P, status, iters, n, c->dp, guess, stats, c->stream), "tensor-core guided con2prim");
+    return GRMHD_OK;
+  }
   if (mlp_ws) CK(launch_mlp_guess(mlp_ws, U, guess, n, c->dp, c->stream), "network guess");
   CK(launch_c2p_guided(U, P, status, iters, n, c->dp, mlp_ws ? guess : nullptr, X, T, stats, c->stream),
      "guided con2prim batch");

@@ -492,6 +492,17 @@ __device__ __forceinline__ T c2p_mu_plus(const C2PIn<T>& c, T mu, T rtol, int ma
   return mu;
 }
 
+// mu_+ of a double-precision set-up, iterated in float to a relative step of 1e-7 and then polished
+// in double to 1e-15 (the same root as c2p_mu_plus<double> to rounding, in about half the double
+// iterations). Used by the flat con2prim batches.
+__device__ __forceinline__ double c2p_mu_plus_fast(const C2PIn<double>& c) {
+  C2PIn<float> cf;
+  cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
+  cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
+  const float muf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
+  return c2p_mu_plus<double>(c, (double)muf, 1e-15, 12);
+}
+
 // Bracketed Newton iteration on [0, mup] from mu (double or float). Returns 0 when converged (the
 // root, or mu_+ when f(mu_+) <= 0: the cold limit eps = 0), ST_NOT_CONVERGED otherwise.
 template <class T>
@@ -581,10 +592,11 @@ __device__ __forceinline__ void c2p_bad_output(const double Uc[NV], double Pout[
 }
 
 // All-FP64 con2prim: double Newton to |d mu| <= c2p_tol mu plus one more step. Returns the status
-// bits of the solve (0, ST_NOT_CONVERGED or ST_BAD_INPUT); floors are separate.
+// bits of the solve (0, ST_NOT_CONVERGED or ST_BAD_INPUT); floors are separate. fast_mup: the bracket
+// end from c2p_mu_plus_fast (flat batches) instead of the all-double iteration (the FP64 stage).
 template <class R>
 __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, const double Uc[NV],
-                                        double mu_guess, double Pout[NV], int& iters) {
+                                        double mu_guess, double Pout[NV], int& iters, bool fast_mup = false) {
   iters = 0;
   C2PIn<double> c;
   double ru[3], bu[3];
@@ -592,7 +604,7 @@ __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, 
     c2p_bad_output(Uc, Pout);
     return ST_BAD_INPUT;
   }
-  const double mup = c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
+  const double mup = fast_mup ? c2p_mu_plus_fast(c) : c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
   double mu = mu_guess;
   const int st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, iters, true);
   c2p_output(c, mu, ru, bu, Uc, Pout);

@@ -632,7 +632,7 @@ static __global__ void k_c2p_batch(const double* __restrict__ U, double* __restr
     }
     double Pn[NV];
     int iters;
-    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
+    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters, true);
     st |= apply_floors<MINKOWSKI>(p, m.gam, 1.0, Pn);
 #pragma unroll
     for (int q = 0; q < NV; ++q) P[q * n + t] = Pn[q];

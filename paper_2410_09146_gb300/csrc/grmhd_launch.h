@@ -51,6 +51,12 @@ cudaError_t launch_c2p_guided(const double* U, double* P, uint8_t* status, int* 
                               const DevParams& p, const double* guess, float* X, float* T, unsigned long long* stats,
                               cudaStream_t s);
 
+// Fused learned-guess con2prim with the hidden layers on the tensor cores (grmhd_mlp_tc.cu); guess
+// (optional) receives (mu_0, mu_+) [2][n]; stats [6] counts tiles abandoned on an MMA wait timeout.
+cudaError_t launch_c2p_net_tc(const void* mlp_ws, const double* U, double* P, uint8_t* status, int* iters,
+                              long long n, const DevParams& p, double* guess, unsigned long long* stats,
+                              cudaStream_t s);
+
 int grid_for(long long n, int threads);
 
 }  // namespace grmhd

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(128) k_mlp_guess(long long n, const double* __
     C2PIn<double> c;
     double mu0 = 0.0, mup = 0.0;
     if (flat_invariants(p, U, n, t, Uc, c, ru, bu)) {
-      mup = c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
+      mup = c2p_mu_plus_fast(c);
       float x[NIN], y[NOUT];
       raw_features(c, mup, x);
       forward_one(Ws, normS, sm + FWD_ACT_OFF + threadIdx.x * LD, x, y);
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(128) k_c2p_guided(const double* __restrict__ U
         }
         if (!done) ++nfall;
       } else {
-        mup = c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
+        mup = c2p_mu_plus_fast(c);
       }
       if (!done) {
         mu = 0.5 * mup;

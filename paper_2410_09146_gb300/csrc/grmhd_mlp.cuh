@@ -55,6 +55,9 @@ inline MlpPtrs ptrs(const void* ws) {
 
 __device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + __expf(-z)); }
 __device__ __forceinline__ float silu(float z) { return z * sigm(z); }
+// The activations h1, h2 that feed the two 64 x 64 layers are rounded to BF16 in every forward pass
+// (they are the tensor-core operands of the fused kernel; training and the FP32-core path round alike).
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float dsilu(float z) {
   const float s = sigm(z);
   return s * (1.f + z * (1.f - s));
@@ -123,7 +126,7 @@ __device__ __forceinline__ void dense_regs(const float* __restrict__ W, const fl
 // stride LD per thread: conflict-free): inputs are read into registers, then the outputs overwrite the
 // row four at a time. The loop over output groups stays rolled so that the code fits the instruction
 // cache (a fully unrolled 64 x 64 layer does not).
-template <int K>
+template <int K, bool ROUND>
 __device__ __forceinline__ void dense_row(const float* __restrict__ W, const float* __restrict__ b, float* act) {
   float in[K];
 #pragma unroll
@@ -142,10 +145,10 @@ __device__ __forceinline__ void dense_row(const float* __restrict__ W, const flo
       a2 = fmaf(w2.w, in[k + 3], fmaf(w2.z, in[k + 2], fmaf(w2.y, in[k + 1], fmaf(w2.x, in[k], a2))));
       a3 = fmaf(w3.w, in[k + 3], fmaf(w3.z, in[k + 2], fmaf(w3.y, in[k + 1], fmaf(w3.x, in[k], a3))));
     }
-    act[j] = silu(a0);
-    act[j + 1] = silu(a1);
-    act[j + 2] = silu(a2);
-    act[j + 3] = silu(a3);
+    act[j] = ROUND ? bf16r(silu(a0)) : silu(a0);
+    act[j + 1] = ROUND ? bf16r(silu(a1)) : silu(a1);
+    act[j + 2] = ROUND ? bf16r(silu(a2)) : silu(a2);
+    act[j + 3] = ROUND ? bf16r(silu(a3)) : silu(a3);
   }
 }
 
@@ -155,9 +158,9 @@ __device__ __forceinline__ void forward_one(const float* __restrict__ Ws, const 
                                             const float xin[NIN], float y[NOUT]) {
 #pragma unroll
   for (int k = 0; k < NIN; ++k) act[k] = (xin[k] - normS[k]) * normS[NIN + k];
-  dense_row<NIN>(Ws + OFF_W1, Ws + OFF_B1, act);
-  dense_row<HID>(Ws + OFF_W2, Ws + OFF_B2, act);
-  dense_row<HID>(Ws + OFF_W3, Ws + OFF_B3, act);
+  dense_row<NIN, true>(Ws + OFF_W1, Ws + OFF_B1, act);   // h1 (BF16)
+  dense_row<HID, true>(Ws + OFF_W2, Ws + OFF_B2, act);   // h2 (BF16)
+  dense_row<HID, false>(Ws + OFF_W3, Ws + OFF_B3, act);  // h3
   float h[HID];
 #pragma unroll
   for (int k = 0; k < HID; ++k) h[k] = act[k];

@@ -5,7 +5,8 @@ namespace grmhd {
 namespace mlp {
 namespace {
 
-// Fused forward + backward over tiles of TILE samples (thread s owns sample s of a tile). Accumulates
+// Fused forward + backward over tiles of TILE samples (thread s owns sample s of a tile). The forward
+// pass rounds h1 and h2 to BF16 like inference; the backward pass treats the rounding as the identity. Accumulates
 // into grad the gradient of L = (1/n) sum_s [(o0 - t0)^2 + aux (o1 - t1)^2] (standardised outputs and
 // targets) with respect to the weights as used in the forward pass (the BF16 copy), and L into loss[0].
 // T holds raw targets [n][2].
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(TILE, 1) k_mlp_train(long long n, const float*
 #pragma unroll
       for (int j = 0; j < HID; ++j) {
         a1[j] = z[j];
-        hb[j] = silu(z[j]);
+        hb[j] = bf16r(silu(z[j]));  // h1
       }
     }
     {
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(TILE, 1) k_mlp_train(long long n, const float*
 #pragma unroll
       for (int j = 0; j < HID; ++j) {
         a2[j] = z[j];
-        h[j] = silu(z[j]);
+        h[j] = bf16r(silu(z[j]));  // h2
       }
       dense_regs<HID>(Ws + OFF_W3, Ws + OFF_B3, h, z, false);
 #pragma unroll
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(TILE, 1) k_mlp_train(long long n, const float*
       }
     }
     __syncthreads();
-    for (int k = 0; k < HID; ++k) hb[k] = silu(a2[k]);  // h2
+    for (int k = 0; k < HID; ++k) hb[k] = bf16r(silu(a2[k]));  // h2
     __syncthreads();
     // ---- gW3[j][k] = sum_r delta3[r][j] h2[r][k]: thread owns column kc, rows jr + 2i; gb3
     {
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(TILE, 1) k_mlp_train(long long n, const float*
       a2[k] = acc * dsilu(a2[k]);
     }
     __syncthreads();
-    for (int k = 0; k < HID; ++k) hb[k] = silu(a1[k]);  // h1
+    for (int k = 0; k < HID; ++k) hb[k] = bf16r(silu(a1[k]));  // h1
     __syncthreads();
     // ---- gW2[j][k] = sum_r delta2[r][j] h1[r][k]; gb2
     {

@@ -26,6 +26,7 @@ BC = {"periodic": 0, "fixed": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
 ST_RHO_FLOOR, ST_EPS_FLOOR, ST_W_CAP, ST_NOT_CONVERGED, ST_BAD_INPUT = 1, 2, 4, 8, 16
 GRMHD_MLP_NPARAM, GRMHD_MLP_NNORM = 9026, 20
+GRMHD_GUESS_FP32 = 1
 
 
 class GrmhdError(RuntimeError):
@@ -100,7 +101,7 @@ def lib():
         L.grmhd_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
         L.grmhd_p2c.argtypes = [vp, ctypes.c_longlong, vp, vp]
-        L.grmhd_c2p_guess.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp]
+        L.grmhd_c2p_guess.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
         L.grmhd_last_error.argtypes = [vp]
         L.grmhd_last_error.restype = ctypes.c_char_p
         L.grmhd_destroy.argtypes = [vp]
@@ -183,11 +184,11 @@ def grmhd_p2c(ctx: int, n: int, P_ptr: int, U_ptr: int) -> None:
 
 
 def grmhd_c2p_guess(ctx: int, mlp_ws: int, n: int, U_ptr: int, P_ptr: int, status_ptr: int = 0, iters_ptr: int = 0,
-                    guess_ptr: int = 0, X_ptr: int = 0, T_ptr: int = 0) -> None:
+                    guess_ptr: int = 0, X_ptr: int = 0, T_ptr: int = 0, flags: int = 0) -> None:
     vp = ctypes.c_void_p
     _check(lib().grmhd_c2p_guess(ctx, vp(mlp_ws or None), n, vp(U_ptr), vp(P_ptr), vp(status_ptr or None),
-                                 vp(iters_ptr or None), vp(guess_ptr or None), vp(X_ptr or None), vp(T_ptr or None)),
-           ctx)
+                                 vp(iters_ptr or None), vp(guess_ptr or None), vp(X_ptr or None), vp(T_ptr or None),
+                                 flags), ctx)
 
 
 def _fp(a):
@@ -455,16 +456,18 @@ class Context:
         """Flat-space prim->cons batch of torch device tensors P, U of shape [8][n] (float64)."""
         grmhd_p2c(self.ctx, P.shape[1], P.data_ptr(), U.data_ptr())
 
-    def c2p_guess(self, U, P, status=None, iters=None, net=None, guess=None, X=None, T=None):
-        """Flat-space con2prim batch [8][n] with the network's start (net: GuessNet; guess: float64 [2][n]
-        receives (mu_0, mu_+)) or the standard start (net None); X [n][8] and T [n][2] (float32) receive
-        training pairs when given."""
+    def c2p_guess(self, U, P, status=None, iters=None, net=None, guess=None, X=None, T=None, fp32=False):
+        """Flat-space con2prim batch [8][n] from the network's start (net: GuessNet) or the standard start
+        (net None). Network on the tensor cores (fused kernel) unless fp32; guess (float64 [2][n]) receives
+        (mu_0, mu_+) and is required with fp32. X [n][8] and T [n][2] (float32) receive training pairs
+        (standard start or fp32 only)."""
         n = U.shape[1]
-        if net is not None and guess is None:
-            raise GrmhdError("the network guess needs a guess buffer")
+        if net is not None and fp32 and guess is None:
+            raise GrmhdError("the FP32-core guess needs a guess buffer")
         ptr = lambda a: 0 if a is None else a.data_ptr()
         grmhd_c2p_guess(self.ctx, 0 if net is None else net.ws_ptr, n, U.data_ptr(), P.data_ptr(), ptr(status),
-                        ptr(iters), ptr(guess) if net is not None else 0, ptr(X), ptr(T))
+                        ptr(iters), ptr(guess) if net is not None else 0, ptr(X), ptr(T),
+                        GRMHD_GUESS_FP32 if fp32 else 0)
 
 
 class GuessNet:

@@ -5,8 +5,10 @@
   tail of 104);
 * the first Adam step: master weights move by lr * sign(g), the BF16 copy is the nearest-even rounding;
 * features and targets recorded by the guided con2prim against the oracle's invariants, root and W;
+* the fused kernel's guess (hidden layers on the tensor cores) against the FP64 reference network;
 * without a guess the guided batch reproduces the plain batch; with a network trained on oracle-solved
-  pairs it needs fewer iterations for the same roots, and rarely falls back to the standard start.
+  pairs both network paths (FP32 cores, tensor cores) need fewer iterations for the same roots and
+  rarely fall back to the standard start.
 """
 import numpy as np
 import pytest
@@ -64,8 +66,10 @@ def test_forward_and_gradient_match_fp64_reference(orc):
     torch.cuda.synchronize()
     Yr = M.forward(wb, norm.astype(np.float64), X32)
     scale = norm[18:20].astype(np.float64)
-    err = np.abs(Yg.cpu().numpy() - Yr) / (scale + np.abs(Yr))  # FP32 sums of 64 terms per layer
-    assert err.max() < 1e-4, err.max()
+    # FP32 sums of 64 terms per layer; h1, h2 are rounded to BF16 on both sides, and a value within an
+    # FP32 rounding error of a BF16 rounding boundary can round the other way (a few samples in 1000)
+    err = np.abs(Yg.cpu().numpy() - Yr) / (scale + np.abs(Yr))
+    assert np.percentile(err, 99) < 1e-4 and err.max() < 2e-2, (np.percentile(err, 99), err.max())
     aux = 0.25
     loss_g, grad_g = net.grad(Xd, Td, aux)
     loss_r, grad_r = M.loss_and_grad(wb, norm.astype(np.float64), X32, T32, aux)
@@ -96,6 +100,47 @@ def test_first_adam_step(orc):
     assert np.allclose(master[nz], want[nz], rtol=0, atol=2e-7)
     assert np.array_equal(master[~nz], theta[~nz])
     assert np.array_equal(wb.astype(np.float64), M.bf16_round(master))
+
+
+def test_tensor_core_network_matches_fp64_reference(orc):
+    # the fused kernel's guess (hidden layers as tcgen05 MMAs) against the FP64 reference network on the
+    # features the library records for the same states (standard path), over 2.5 tiles of 128 plus a
+    # ragged tail
+    torch, G = _setup()
+    rng = np.random.default_rng(12)
+    n = 20000 + 77
+    U, X, T, st_o, _, _ = _oracle_pairs(orc, n, seed=13)
+    net = G.GuessNet(seed=4)
+    theta = (G.init_weights(4) + rng.normal(0, 0.02, M.NPARAM)).astype(np.float32)
+    norm = np.concatenate([X.mean(0), 1.0 / X.std(0), [12.0, 1.0], [3.0, 0.7]]).astype(np.float32)
+    net.set_weights(theta, norm)
+    _, wb = net.weights()
+    ctx = G.Context(I.Setup(n=(0, 0, 0)))
+    Ud = torch.tensor(U.T.copy(), device="cuda")
+    P1, P2 = torch.zeros_like(Ud), torch.zeros_like(Ud)
+    st1 = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    st2 = torch.zeros_like(st1)
+    it2 = torch.zeros(n, dtype=torch.int32, device="cuda")
+    Xg = torch.zeros((n, 8), dtype=torch.float32, device="cuda")
+    guess = torch.full((2, n), -1.0, dtype=torch.float64, device="cuda")
+    ctx.c2p_guess(Ud, P1, st1, None, X=Xg)
+    ctx.c2p_guess(Ud, P2, st2, it2, net=net, guess=guess)
+    stats = ctx.stats()
+    torch.cuda.synchronize()
+    assert int(stats[6]) == 0  # no tile abandoned
+    g = guess.cpu().numpy()
+    ok = st1.cpu().numpy() == 0
+    assert np.all(g[1, ok] > 0) and np.all(g[0, ok] <= g[1, ok])
+    y_tc = -np.log1p(-g[0] / g[1])
+    y_ref = M.forward(wb, norm.astype(np.float64), Xg.cpu().numpy().astype(np.float64))[:, 0]
+    m = ok & (y_ref > 0.5) & (y_ref < 29.5)
+    assert m.mean() > 0.9
+    d = np.abs(y_tc[m] - y_ref[m])
+    assert np.median(d) < 1e-4 and np.percentile(d, 99) < 2e-3 and d.max() < 0.1, (np.median(d), d.max())
+    # same statuses as the standard start, and every state converged
+    assert np.array_equal(st1.cpu().numpy(), st2.cpu().numpy())
+    assert not np.any(st2.cpu().numpy() & 8)
+    assert int(stats[0]) == int(it2.cpu().numpy().sum())
 
 
 def test_features_targets_and_plain_equivalence(orc):
@@ -167,31 +212,38 @@ def test_trained_guess_reduces_iterations(orc):
     its = torch.zeros(n, dtype=torch.int32, device="cuda")
     itn = torch.zeros_like(its)
     guess = torch.zeros((2, n), dtype=torch.float64, device="cuda")
+    Pt = torch.zeros_like(Ud)
+    stt = torch.zeros_like(sts)
+    itt = torch.zeros_like(its)
     ctx.c2p_guess(Ud, Ps, sts, its)
-    ctx.c2p_guess(Ud, Pn, stn, itn, net=net, guess=guess)
+    ctx.c2p_guess(Ud, Pn, stn, itn, net=net, guess=guess, fp32=True)
     fallbacks = int(ctx.stats()[7])
+    ctx.c2p_guess(Ud, Pt, stt, itt, net=net)
+    stats_tc = ctx.stats()
     torch.cuda.synchronize()
-    its, itn = its.cpu().numpy(), itn.cpu().numpy()
-    sts, stn = sts.cpu().numpy(), stn.cpu().numpy()
-    assert np.array_equal(sts, stn)
-    assert np.mean(stn & 8) == 0  # every state converged
+    its, itn, itt = its.cpu().numpy(), itn.cpu().numpy(), itt.cpu().numpy()
+    sts, stn, stt = sts.cpu().numpy(), stn.cpu().numpy(), stt.cpu().numpy()
+    assert np.array_equal(sts, stn) and np.array_equal(sts, stt)
+    assert np.mean(stn & 8) == 0 and np.mean(stt & 8) == 0  # every state converged
+    assert int(stats_tc[6]) == 0
     # the guess: median error of y0 on the held-out states
     g = guess.cpu().numpy()
     y0 = -np.log1p(-g[0] / g[1])
     good = (st_e == 0) & (Te[:, 0] < 25)
     yerr = np.abs(y0[good] - Te[good, 0])
     assert np.median(yerr) < 0.1, np.median(yerr)
-    assert fallbacks <= 0.01 * n
-    # fewer iterations, same roots
-    assert itn.mean() <= its.mean() - 1.0, (its.mean(), itn.mean())
-    assert np.percentile(itn, 99) <= np.percentile(its, 99)
+    assert fallbacks <= 0.01 * n and int(stats_tc[7]) <= 0.01 * n
+    # fewer iterations on both network paths
+    for it in (itn, itt):
+        assert it.mean() <= its.mean() - 1.0, (its.mean(), it.mean())
+        assert np.percentile(it, 99) <= np.percentile(its, 99)
     # both solutions reproduce U to roundoff (the conditioning-free measure) ...
     s = I.linear_wave_setup(8)
     p = orc.params(s)
     x = np.zeros((n, 3))
     plain = sts == 0
     scale = np.abs(Ue[:, 0]) + np.abs(Ue[:, 4]) + np.linalg.norm(Ue[:, 1:4], axis=1)
-    for Pd in (Ps, Pn):
+    for Pd in (Ps, Pn, Pt):
         Ub = orc.prim2con_points(p, x, Pd.cpu().numpy().T.copy())["U"]
         be = (np.max(np.abs(Ub - Ue), axis=1) / scale)[plain]
         assert be.max() < 1e-11 and np.median(be) < 1e-14
@@ -202,5 +254,7 @@ def test_trained_guess_reduces_iterations(orc):
     sig = np.sum(Pg[:, 5:8] ** 2, 1) / (Pg[:, 0] * W * W)
     good = plain & (W <= 10) & (sig <= 10) & (Pg[:, 4] * (s.gamma_eos - 1.0) / Pg[:, 0] >= 1e-4)
     assert good.mean() > 0.05
-    a, b = Ps.cpu().numpy()[:5, good], Pn.cpu().numpy()[:5, good]
-    assert np.max(np.abs(a - b) / (np.abs(a) + np.abs(a[0]))) < 1e-10
+    a = Ps.cpu().numpy()[:5, good]
+    for Pd in (Pn, Pt):
+        b = Pd.cpu().numpy()[:5, good]
+        assert np.max(np.abs(a - b) / (np.abs(a) + np.abs(a[0]))) < 1e-10

@@ -1,6 +1,7 @@
 """Pins of the FP64 reference of the learned con2prim guess (oracle/guess_mlp.py).
 
-* backward() against central finite differences of the loss (every parameter block, both outputs);
+* backward() against central finite differences of the loss (every parameter block, both outputs), and
+  the BF16 rounding of h1, h2 as a straight-through step;
 * a network reduced to one unit per layer, evaluated in closed form with math.exp;
 * the first Adam step moves every parameter by lr * sign(g) (bias-corrected m/sqrt(v) = g/|g|);
 * BF16 rounding of values with known nearest-even results, and against torch's bfloat16 cast;
@@ -40,12 +41,35 @@ def test_gradient_matches_finite_differences():
             idx.extend(range(o, o + size))
         else:
             idx.extend(o + rng.choice(size, 40, replace=False))
+    # finite differences of the unrounded network (BF16 rounding makes the loss piecewise constant)
+    _, g = M.loss_and_grad(theta, norm, X, T, aux, round_h=False)
     h = 1e-6
     for i in idx:
         tp = theta.copy(); tp[i] += h
         tm = theta.copy(); tm[i] -= h
-        fd = (M.loss_and_grad(tp, norm, X, T, aux)[0] - M.loss_and_grad(tm, norm, X, T, aux)[0]) / (2 * h)
+        fd = (M.loss_and_grad(tp, norm, X, T, aux, round_h=False)[0]
+              - M.loss_and_grad(tm, norm, X, T, aux, round_h=False)[0]) / (2 * h)
         assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_rounded_forward_is_straight_through():
+    # rounding h1, h2 changes only the activations: the rounded network's gradient is the unrounded
+    # formula evaluated on the rounded activations, i.e. equal to the unrounded gradient of a network whose
+    # layer-2 and layer-3 inputs are the rounded values; check the forward values and the W2/W3 blocks
+    theta, norm = _net(3, scale=0.3)
+    rng = np.random.default_rng(4)
+    X = rng.normal(0, 1, (9, 8))
+    T = rng.normal(0, 2, (9, 2))
+    y, c = M.forward(theta, norm, X, cache=True, round_h=True)
+    assert np.array_equal(c["h1"], M.bf16_round(c["h1"])) and np.array_equal(c["h2"], M.bf16_round(c["h2"]))
+    P = M.unpack(theta)
+    assert np.allclose(c["z2"], c["h1"] @ P["W2"].T + P["b2"], rtol=1e-14, atol=1e-14)
+    _, g = M.loss_and_grad(theta, norm, X, T, 0.5, round_h=True)
+    G = M.unpack(g)
+    e = c["o"] - (T - norm[16:18]) / norm[18:20]
+    do = 2.0 * np.array([1.0, 0.5]) * e / len(X)
+    d3 = (do @ P["W4"]) * (lambda z: (1 / (1 + np.exp(-z))) * (1 + z * (1 - 1 / (1 + np.exp(-z)))))(c["z3"])
+    assert np.allclose(G["W3"], d3.T @ c["h2"], rtol=1e-12, atol=1e-15)
 
 
 def test_single_unit_chain_closed_form():
@@ -66,7 +90,7 @@ def test_single_unit_chain_closed_form():
     x2 = (1.0 - 0.25) * 2.0
     h3 = silu(a3 * silu(a2 * silu(a1 * x2 + c1) + c2) + c3)
     want = [(a40 * h3 + c40) * 3.0 + 1.5, (a41 * h3 + c41) * 0.5 - 0.5]
-    got = M.forward(theta, norm, X)[0]
+    got = M.forward(theta, norm, X, round_h=False)[0]
     assert np.allclose(got, want, rtol=1e-14, atol=1e-15)
 
 

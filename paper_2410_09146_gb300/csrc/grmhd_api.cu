@@ -26,7 +26,9 @@ struct grmhd_ctx {
   void* E;
   uint8_t* status;
   int* worklist;             // mixed form: deferred con2prim cells (NULL in the FP64 form)
-  unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats, [16] worklist count
+  int* floorlist;            // cells whose hydro state is re-derived after floors
+  unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats, [16] worklist count,
+                             // [17] floor-list count, [20..23] batch work counters
   int s0, sc;                // slot of U0 and of the current state
   bool has_state;
   bool timing;               // record CUDA events around each kernel group
@@ -58,7 +60,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t P, U[3], F[3], E, status, worklist, scal, total;
+  size_t P, U[3], F[3], E, status, worklist, floorlist, geo, scal, total;
 };
 
 bool valid_params(const grmhd_params* p, char* msg, size_t n) {
@@ -102,6 +104,8 @@ Layout layout_of(const grmhd_params* p) {
     l.E = take(3 * G * pb);
     l.status = take(I);
     if (p->precision == GRMHD_MIXED) l.worklist = take(I * sizeof(int));
+    l.floorlist = take(I * sizeof(int));
+    if (p->metric == GRMHD_KERR_SCHILD) l.geo = take(NGEO * I * sizeof(double));
   }
   l.total = off;
   return l;
@@ -210,8 +214,8 @@ std::vector<WorkItem> build_items(const std::vector<BlockDesc>& blocks, int tile
 }
 
 struct BatchLayout {
-  size_t scal, blocks, items, worklist, total;
-  std::vector<size_t> P, U, F, E, status;  // per block; U and F hold 3 consecutive regions
+  size_t scal, blocks, items, worklist, floorlist, total;
+  std::vector<size_t> P, U, F, E, status, geo;  // per block; U and F hold 3 consecutive regions
 };
 
 bool valid_block(const grmhd_block& b, int ng, char* msg, size_t n) {
@@ -252,8 +256,10 @@ BatchLayout batch_layout(const grmhd_params* p, int nblocks, const grmhd_block* 
     for (int k = 0; k < 3; ++k) l.F.push_back(take(8 * G * pb));
     l.E.push_back(take(3 * G * pb));
     l.status.push_back(take(I));
+    l.geo.push_back(p->metric == GRMHD_KERR_SCHILD ? take(NGEO * I * sizeof(double)) : 0);
   }
   l.worklist = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(int)) : 0;
+  l.floorlist = take((size_t)cells * sizeof(int));
   l.total = off;
   return l;
 }
@@ -307,12 +313,15 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
     c->E = c->ws + l.E;
     c->status = (uint8_t*)(c->ws + l.status);
     c->worklist = p->precision == GRMHD_MIXED ? (int*)(c->ws + l.worklist) : nullptr;
+    c->floorlist = (int*)(c->ws + l.floorlist);
+    if (p->metric == GRMHD_KERR_SCHILD) c->dp.geo = (const double*)(c->ws + l.geo);
   }
   c->s0 = c->sc = 0;
   c->has_state = false;
   cudaError_t e = cudaMemsetAsync(c->ws, 0, l.total, c->stream);
+  if (e == cudaSuccess && c->dp.geo) e = c->L->geometry(c->dp, (double*)c->dp.geo, c->stream);
   if (e != cudaSuccess) {
-    snprintf(g_create_err, sizeof g_create_err, "clearing the workspace failed: %s", cudaGetErrorString(e));
+    snprintf(g_create_err, sizeof g_create_err, "initialising the workspace failed: %s", cudaGetErrorString(e));
     delete c;
     return GRMHD_E_CUDA;
   }
@@ -413,7 +422,7 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   unsigned long long* ms = c->scal;
   double* dt_dev = (double*)(c->scal + 3);
   unsigned long long* stats = c->scal + 8;
-  CK(cudaMemsetAsync(stats, 0, 9 * sizeof(unsigned long long), s), "clearing stats and the worklist count");
+  CK(cudaMemsetAsync(stats, 0, 10 * sizeof(unsigned long long), s), "clearing stats and the worklist counts");
   if (track) CK(cudaMemsetAsync(ms, 0, 3 * sizeof(unsigned long long), s), "clearing speeds");
   TMARK(0);
   if (c->prm.bc == GRMHD_BC_PERIODIC) CK(L.ghost(c->dp, c->P, s), "ghost fill");
@@ -425,7 +434,7 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   TMARK(4);
   CK(L.emf(c->dp, c->F[0], c->F[1], c->F[2], c->E, s), "EMF");
   TMARK(5);
-  StageArgs a;
+  StageArgs a{};
   a.U0 = c->Uslot[c->s0];
   a.Ucur = c->Uslot[c->sc];
   a.Unew = c->Uslot[dst];
@@ -439,6 +448,8 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   a.use_dev_dt = auto_dt ? 1 : 0;
   a.worklist = c->worklist;
   a.wl_count = (unsigned int*)(c->scal + 16);
+  a.floorlist = c->floorlist;
+  a.fl_count = (unsigned int*)(c->scal + 17);
   CK(L.update(c->dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
   TMARK(6);
 #undef TMARK
@@ -477,7 +488,7 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   const FormLaunchers& L = *c->L;
   unsigned long long* ms = c->scal;
   unsigned int* ctr = (unsigned int*)(c->scal + 20);
-  CK(cudaMemsetAsync(c->scal + 8, 0, 9 * sizeof(unsigned long long), s), "clearing stats");
+  CK(cudaMemsetAsync(c->scal + 8, 0, 10 * sizeof(unsigned long long), s), "clearing stats and list counts");
   CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned int), s), "clearing work counters");
   if (track) CK(cudaMemsetAsync(ms, 0, sizeof(unsigned long long), s), "clearing speeds");
   const WorkItem* flux_items = c->ditems;
@@ -489,6 +500,7 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   if (track) CK(launch_batch_finalize_dt(ms, (double*)(c->scal + 3), c->prm.cfl, s), "time step");
   CK(L.batch_emf(c->dblocks, emf_items, c->n_items[1], ctr + 1, grid, s), "batched EMF");
   CK(L.batch_update(c->dblocks, upd_items, c->n_items[2], ctr + 2, a, c->prm.metric, grid, s), "batched update");
+  CK(L.batch_floors(c->dblocks, c->nblocks, a, c->prm.metric, grid, s), "batched floor re-derivation");
   if (c->worklist) CK(L.batch_deferred(c->dblocks, c->nblocks, a, c->prm.metric, grid, s), "batched deferred con2prim");
   return GRMHD_OK;
 }
@@ -502,7 +514,7 @@ static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double d
   const int dst = first ? (c->sc + 1) % 3 : 3 - c->s0 - c->sc;
   const bool auto_dt = !(dt > 0.0);
   const bool track = auto_dt && first;
-  BatchArgs a;
+  BatchArgs a{};
   a.g0 = g0; a.g1 = g1; a.beta = beta; a.dt = dt;
   a.use_dev_dt = auto_dt ? 1 : 0;
   a.s0 = s0; a.sc = c->sc; a.dst = dst;
@@ -510,6 +522,8 @@ static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double d
   a.stats = c->scal + 8;
   a.worklist = c->worklist;
   a.wl_count = (unsigned int*)(c->scal + 16);
+  a.floorlist = c->floorlist;
+  a.fl_count = (unsigned int*)(c->scal + 17);
   if (c->use_graph) {
     const std::vector<double> key = {g0, g1, beta, dt, (double)s0, (double)c->sc, (double)dst, (double)c->tile};
     auto it = c->graphs.find(key);
@@ -680,6 +694,7 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   c->dblocks = (BlockDesc*)(c->ws + l.blocks);
   c->ditems = (WorkItem*)(c->ws + l.items);
   c->worklist = p->precision == GRMHD_MIXED ? (int*)(c->ws + l.worklist) : nullptr;
+  c->floorlist = (int*)(c->ws + l.floorlist);
   c->hblocks.resize(nblocks);
   long long off = 0;
   for (int b = 0; b < nblocks; ++b) {
@@ -692,6 +707,7 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
     }
     d.E = c->ws + l.E[b];
     d.status = (uint8_t*)(c->ws + l.status[b]);
+    if (p->metric == GRMHD_KERR_SCHILD) d.p.geo = (const double*)(c->ws + l.geo[b]);
     d.cell_offset = off;
     off += d.p.isize;
   }
@@ -701,6 +717,8 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   c->grid_persist = (sms > 0 ? sms : 152) * c->L->batch_ctas_per_sm(p->metric);
   cudaError_t e = cudaMemsetAsync(c->ws, 0, l.total, c->stream);
+  for (int b = 0; b < nblocks && e == cudaSuccess; ++b)
+    if (c->hblocks[b].p.geo) e = c->L->geometry(c->hblocks[b].p, (double*)c->hblocks[b].p.geo, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->dblocks, c->hblocks.data(), sizeof(BlockDesc) * nblocks, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

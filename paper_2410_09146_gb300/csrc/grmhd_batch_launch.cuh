@@ -45,6 +45,14 @@ struct BatchLaunch {
       k_batch_deferred<MINKOWSKI, T><<<grid, 128, 0, s>>>(b, nblocks, a);
     return cudaGetLastError();
   }
+  static cudaError_t floors(const BlockDesc* b, int nblocks, const BatchArgs& a, int metric, int grid,
+                            cudaStream_t s) {
+    if (metric == KERR_SCHILD)
+      k_batch_floors<KERR_SCHILD, T><<<grid, 128, 0, s>>>(b, nblocks, a);
+    else
+      k_batch_floors<MINKOWSKI, T><<<grid, 128, 0, s>>>(b, nblocks, a);
+    return cudaGetLastError();
+  }
   // CTAs per SM of the persistent kernels (occupancy of the update kernel, the heaviest)
   static int ctas_per_sm(int metric) {
     int n = 0;

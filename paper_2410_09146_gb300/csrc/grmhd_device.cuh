@@ -33,6 +33,9 @@ struct DevParams {
   double c2p_tol;
   int c2p_max_iter;
   double cfl, weno_eps;
+  // Geometry cache: NGEO doubles per interior cell (structure of arrays, isize apart) holding the
+  // static Kerr-Schild metric at the cell centre, filled once per block; NULL: computed in place.
+  const double* geo;
 };
 
 // Arguments of the update kernel (a5 + a6).
@@ -48,6 +51,8 @@ struct StageArgs {
   int use_dev_dt;
   int* worklist;                 // mixed form: cells whose float con2prim phase did not settle
   unsigned int* wl_count;        // number of entries in worklist
+  int* floorlist;                // cells whose floors / status re-derive U in a compacted pass (NULL: inline)
+  unsigned int* fl_count;        // number of entries in floorlist
 };
 
 
@@ -89,6 +94,8 @@ struct BatchArgs {
   unsigned long long* stats;
   int* worklist;
   unsigned int* wl_count;
+  int* floorlist;
+  unsigned int* fl_count;
 };
 
 // ------------------------------------------------------------------ metric (Sec. 2.3)
@@ -100,6 +107,37 @@ struct Metric {
 
 __host__ __device__ constexpr int sym3(int i, int j) {
   return i <= j ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
+}
+
+// Geometry cache entries: alpha, beta^i (3), gamma_ij (6), gamma^ij (6), sqrt(gamma), Kerr-Schild r.
+constexpr int NGEO = 18;
+
+__device__ __forceinline__ void geo_store(double* __restrict__ geo, long long n, long long t, const Metric<double>& m,
+                                          double r) {
+  geo[t] = m.alpha;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) geo[(1 + i) * n + t] = m.beta[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    geo[(4 + i) * n + t] = m.gam[i];
+    geo[(10 + i) * n + t] = m.gamu[i];
+  }
+  geo[16 * n + t] = m.sqrtgam;
+  geo[17 * n + t] = r;
+}
+
+__device__ __forceinline__ void geo_load(const double* __restrict__ geo, long long n, long long t, Metric<double>& m,
+                                         double& r) {
+  m.alpha = geo[t];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m.beta[i] = geo[(1 + i) * n + t];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    m.gam[i] = geo[(4 + i) * n + t];
+    m.gamu[i] = geo[(10 + i) * n + t];
+  }
+  m.sqrtgam = geo[16 * n + t];
+  r = geo[17 * n + t];
 }
 
 template <class R>

@@ -48,6 +48,14 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
     k_update<KERR_SCHILD, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
   else
     k_update<MINKOWSKI, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.floorlist == nullptr) return e;
+  // re-derivation of the hydro state of the floored cells (count known on the device only)
+  const int g3 = grid_for(p.isize / 8 + 1, 128);
+  if (p.metric == KERR_SCHILD)
+    k_update_floors<KERR_SCHILD, T><<<g3, 128, 0, s>>>((const T*)P, a, p);
+  else
+    k_update_floors<MINKOWSKI, T><<<g3, 128, 0, s>>>((const T*)P, a, p);
   return cudaGetLastError();
 }
 
@@ -68,9 +76,15 @@ cudaError_t store_prims(const DevParams& p, const void* P, double* dst, cudaStre
   return cudaMemcpyAsync(dst, P, sizeof(double) * NV * p.gsize, cudaMemcpyDeviceToDevice, s);
 }
 
+cudaError_t geometry(const DevParams& p, double* geo, cudaStream_t s) {
+  if (p.metric != KERR_SCHILD || p.isize == 0) return cudaSuccess;
+  k_geometry<KERR_SCHILD><<<grid_for(p.isize, 128), 128, 0, s>>>(p, geo);
+  return cudaGetLastError();
+}
+
 using BL = BatchLaunch<double, double>;
 const FormLaunchers kFp64 = {ghost, flux, emf, update, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
-                                BL::deferred, BL::ctas_per_sm, 8, 8};
+                                BL::deferred, BL::ctas_per_sm, 8, 8, geometry, BL::floors};
 
 }  // namespace
 

@@ -274,6 +274,30 @@ __device__ __forceinline__ void ks_sources(const DevParams& p, R x, R y, R z, co
   (void)L4;
 }
 
+// Double-precision metric at the centre of interior cell t: from the block's geometry cache when it
+// has one (Kerr-Schild), else evaluated in place.
+template <int METRIC>
+__device__ __forceinline__ void cell_metric(const DevParams& p, long long t, double xc, double yc, double zc,
+                                            Metric<double>& m, double& r) {
+  if (METRIC == KERR_SCHILD && p.geo != nullptr)
+    geo_load(p.geo, p.isize, t, m, r);
+  else
+    metric_at<double, METRIC>(p, xc, yc, zc, m, &r);
+}
+
+// Fill the geometry cache of a block (once, at context creation).
+template <int METRIC>
+__global__ void k_geometry(DevParams p, double* __restrict__ geo) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.isize; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+    Metric<double> m;
+    double r;
+    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                              p.x0[2] + (k + 0.5) * p.dx[2], m, &r);
+    geo_store(geo, p.isize, t, m, r);
+  }
+}
+
 // Per-thread con2prim statistics, folded into StageArgs::stats once per warp.
 struct CellStats {
   unsigned int it_sum = 0, c_rho = 0, c_eps = 0, c_w = 0, c_nc = 0, c_bad = 0, it_max = 0;
@@ -354,7 +378,7 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
   Metric<double> m;
   double rks;
-  metric_at<double, METRIC>(p, xc, yc, zc, m, &rks);
+  cell_metric<METRIC>(p, t, xc, yc, zc, m, rks);
   if (METRIC == KERR_SCHILD) {
     R Sr[5];
     R Pr[NV];
@@ -393,10 +417,16 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   }
   st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
   if (st) {
-    double U5[5];
-    prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
+    if (a.floorlist) {
+      // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
+      // hold only such cells (a few percent of cells, but present in most warps of this pass)
+      a.floorlist[atomicAdd(a.fl_count, 1u)] = (int)(wl_tag + t);
+    } else {
+      double U5[5];
+      prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) Un[q] = U5[q];
+      for (int q = 0; q < 5; ++q) Un[q] = U5[q];
+    }
   }
 #pragma unroll
   for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
@@ -427,8 +457,8 @@ __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict_
   const long long g = gidx(p, i, j, k);
   Metric<double> m;
   double rks;
-  metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
-                            p.x0[2] + (k + 0.5) * p.dx[2], m, &rks);
+  cell_metric<METRIC>(p, t, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                      p.x0[2] + (k + 0.5) * p.dx[2], m, rks);
   double Pc[NV], Un[NV], Uc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
@@ -455,6 +485,32 @@ __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict_
   cs.add(st, iters);
 }
 
+// Hydro part of the conserved state of a cell whose floors (or status) fired in update_cell,
+// re-derived from the primitives it stored.
+template <int METRIC, class T>
+__device__ __forceinline__ void floor_cell(const DevParams& p, const T* __restrict__ P, const StageArgs& a, long long t) {
+  const long long n = p.isize, G = p.gsize;
+  const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+  const long long g = gidx(p, i, j, k);
+  Metric<double> m;
+  double rks;
+  cell_metric<METRIC>(p, t, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                      p.x0[2] + (k + 0.5) * p.dx[2], m, rks);
+  double Pn[NV], U5[5];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) Pn[q] = (double)P[q * G + g];
+  prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) a.Unew[q * n + t] = U5[q];
+}
+
+template <int METRIC, class T>
+__global__ void __launch_bounds__(128) k_update_floors(const T* __restrict__ P, StageArgs a, DevParams p) {
+  const unsigned int cnt = *a.fl_count;
+  for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x)
+    floor_cell<METRIC, T>(p, P, a, a.floorlist[w]);
+}
+
 template <int METRIC, class T>
 __global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, StageArgs a, DevParams p) {
   const unsigned int cnt = *a.wl_count;
@@ -477,7 +533,7 @@ __device__ __forceinline__ int next_item(unsigned int* counter) {
 }
 
 __device__ __forceinline__ StageArgs block_stage_args(const BlockDesc& b, const BatchArgs& a) {
-  StageArgs s;
+  StageArgs s{};
   s.U0 = b.U[a.s0];
   s.Ucur = b.U[a.sc];
   s.Unew = b.U[a.dst];
@@ -491,6 +547,8 @@ __device__ __forceinline__ StageArgs block_stage_args(const BlockDesc& b, const 
   s.use_dev_dt = a.use_dev_dt;
   s.worklist = a.worklist;
   s.wl_count = a.wl_count;
+  s.floorlist = a.floorlist;
+  s.fl_count = a.fl_count;
   return s;
 }
 
@@ -566,6 +624,22 @@ __global__ void __launch_bounds__(128) k_batch_deferred(const BlockDesc* __restr
   }
   cs.flush(a.stats);
   if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
+}
+
+template <int METRIC, class T>
+__global__ void __launch_bounds__(128) k_batch_floors(const BlockDesc* __restrict__ blocks, int nblocks, BatchArgs a) {
+  const unsigned int cnt = *a.fl_count;
+  for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
+    const long long gcell = a.floorlist[w];
+    int lo = 0, hi = nblocks - 1;  // last block whose cell_offset <= gcell
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (blocks[mid].cell_offset <= gcell) lo = mid; else hi = mid - 1;
+    }
+    const BlockDesc& b = blocks[lo];
+    const StageArgs sa = block_stage_args(b, a);
+    floor_cell<METRIC, T>(b.p, (const T*)b.P, sa, gcell - b.cell_offset);
+  }
 }
 
 // dt = cfl / (max over the batch of |lambda| / dx)

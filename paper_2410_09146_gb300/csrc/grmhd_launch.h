@@ -31,6 +31,11 @@ struct FormLaunchers {
   int (*batch_ctas_per_sm)(int metric);
   int p_bytes;  // bytes per stored primitive
   int r_bytes;  // bytes per flux / EMF value
+  // fill the geometry cache (NGEO x isize doubles) of a Kerr-Schild block
+  cudaError_t (*geometry)(const DevParams& p, double* geo, cudaStream_t s);
+  // batched re-derivation of the hydro state of floored cells
+  cudaError_t (*batch_floors)(const BlockDesc* b, int nblocks, const BatchArgs& a, int metric, int grid,
+                              cudaStream_t s);
 };
 
 const FormLaunchers& fp64_launchers();

@@ -49,9 +49,19 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
   else
     k_update<MINKOWSKI, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || a.worklist == nullptr) return e;
-  // second pass over the cells whose float con2prim phase did not settle (count known on the device only)
+  if (e != cudaSuccess) return e;
+  // passes over the cells queued by k_update (counts known on the device only): re-derivation of the
+  // hydro state of floored cells, and the double con2prim of cells whose float phase did not settle
   const int g2 = grid_for(p.isize / 8 + 1, 128);
+  if (a.floorlist) {
+    if (p.metric == KERR_SCHILD)
+      k_update_floors<KERR_SCHILD, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
+    else
+      k_update_floors<MINKOWSKI, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (a.worklist == nullptr) return cudaSuccess;
   if (p.metric == KERR_SCHILD)
     k_update_deferred<KERR_SCHILD, T><<<g2, 128, 0, s>>>((T*)P, a, p);
   else
@@ -80,9 +90,15 @@ cudaError_t store_prims(const DevParams& p, const void* P, double* dst, cudaStre
   return cudaGetLastError();
 }
 
+cudaError_t geometry(const DevParams& p, double* geo, cudaStream_t s) {
+  if (p.metric != KERR_SCHILD || p.isize == 0) return cudaSuccess;
+  k_geometry<KERR_SCHILD><<<grid_for(p.isize, 128), 128, 0, s>>>(p, geo);
+  return cudaGetLastError();
+}
+
 using BL = BatchLaunch<float, float>;
 const FormLaunchers kMixed = {ghost, flux, emf, update, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
-                                BL::deferred, BL::ctas_per_sm, 4, 4};
+                                BL::deferred, BL::ctas_per_sm, 4, 4, geometry, BL::floors};
 
 }  // namespace
 

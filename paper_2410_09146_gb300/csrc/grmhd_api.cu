@@ -127,6 +127,8 @@ DevParams dev_params(const grmhd_params* p) {
   d.gamma_eos = p->gamma_eos;
   d.metric = p->metric; d.recon = p->recon; d.riemann = p->riemann; d.bc = p->bc;
   d.rho_floor0 = p->rho_floor0; d.eps_floor0 = p->eps_floor0; d.floor_r_exp = p->floor_r_exp; d.w_max = p->w_max;
+  d.w_max2 = p->w_max * p->w_max;
+  d.v0sq_cap = 1.0 - 1.0 / (p->w_max * p->w_max);
   d.c2p_tol = p->c2p_tol; d.c2p_max_iter = p->c2p_max_iter;
   d.cfl = p->cfl; d.weno_eps = p->weno_eps;
   return d;

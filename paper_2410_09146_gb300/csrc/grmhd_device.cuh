@@ -30,6 +30,7 @@ struct DevParams {
   double gamma_eos;
   int metric, recon, riemann, bc;
   double rho_floor0, eps_floor0, floor_r_exp, w_max;
+  double w_max2, v0sq_cap;   // w_max^2 and 1 - 1/w_max^2 (velocity bound of the con2prim solve)
   double c2p_tol;
   int c2p_max_iter;
   double cfl, weno_eps;
@@ -109,11 +110,12 @@ __host__ __device__ constexpr int sym3(int i, int j) {
   return i <= j ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
 }
 
-// Geometry cache entries: alpha, beta^i (3), gamma_ij (6), gamma^ij (6), sqrt(gamma), Kerr-Schild r.
-constexpr int NGEO = 18;
+// Geometry cache entries: alpha, beta^i (3), gamma_ij (6), gamma^ij (6), sqrt(gamma), 1/sqrt(gamma) and
+// the floor radius factor r^-floor_r_exp.
+constexpr int NGEO = 19;
 
 __device__ __forceinline__ void geo_store(double* __restrict__ geo, long long n, long long t, const Metric<double>& m,
-                                          double r) {
+                                          double isg, double fr) {
   geo[t] = m.alpha;
 #pragma unroll
   for (int i = 0; i < 3; ++i) geo[(1 + i) * n + t] = m.beta[i];
@@ -123,11 +125,12 @@ __device__ __forceinline__ void geo_store(double* __restrict__ geo, long long n,
     geo[(10 + i) * n + t] = m.gamu[i];
   }
   geo[16 * n + t] = m.sqrtgam;
-  geo[17 * n + t] = r;
+  geo[17 * n + t] = isg;
+  geo[18 * n + t] = fr;
 }
 
 __device__ __forceinline__ void geo_load(const double* __restrict__ geo, long long n, long long t, Metric<double>& m,
-                                         double& r) {
+                                         double& isg, double& fr) {
   m.alpha = geo[t];
 #pragma unroll
   for (int i = 0; i < 3; ++i) m.beta[i] = geo[(1 + i) * n + t];
@@ -137,7 +140,8 @@ __device__ __forceinline__ void geo_load(const double* __restrict__ geo, long lo
     m.gamu[i] = geo[(10 + i) * n + t];
   }
   m.sqrtgam = geo[16 * n + t];
-  r = geo[17 * n + t];
+  isg = geo[17 * n + t];
+  fr = geo[18 * n + t];
 }
 
 template <class R>
@@ -604,7 +608,7 @@ __device__ __forceinline__ int c2p_setup(const DevParams& p, const Metric<R>& m,
   c.rb2 = c.rb * c.rb;
   c.gm1 = p.gamma_eos - 1.0;
   // velocity bound of the solve: physical bound r^2/(1 + r^2) and the Lorentz-factor ceiling
-  c.v0sq = fmin(c.r2 / (1.0 + c.r2), 1.0 - 1.0 / (p.w_max * p.w_max));
+  c.v0sq = fmin(c.r2 / (1.0 + c.r2), p.v0sq_cap);
   return 0;
 }
 
@@ -674,23 +678,21 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
   double mu = (double)muf;
   bool done = false;
   if (stf == 0 && isfinite(mu) && mu > 0.0) {
-    if (muf >= mupf) {
-      // float root on the bracket end (cold limit): settle mu_+ in double and test f there
-      const double mup = c2p_mu_plus<double>(c, (double)mupf, 1e-15, 8);
-      const C2PEval<double> e = c2p_master(c, mup);
-      ++iters;
-      if (!(e.f > 0.0)) {
-        mu = mup;
-        done = true;
-      } else {
-        mu = mup;
-      }
-    }
-    if (!done) {
-      const C2PEval<double> e = c2p_master(c, mu);
-      ++iters;
+    // One double evaluation of the master function for every cell, so that a warp runs it once: at the
+    // float root, or, when that sits on the bracket end (cold limit), at mu_+ settled in double. A cold
+    // cell whose f(mu_+) <= 0 has its root on mu_+; otherwise, as for every other cell, the double Newton
+    // step from the evaluation point must be small.
+    const bool cold = muf >= mupf;
+    double mue = mu;
+    if (cold) mue = c2p_mu_plus<double>(c, (double)mupf, 1e-15, 8);
+    const C2PEval<double> e = c2p_master(c, mue);
+    ++iters;
+    if (cold && !(e.f > 0.0)) {
+      mu = mue;
+      done = true;
+    } else {
       const double step = -e.f / e.df;
-      const double nmu = mu + step;
+      const double nmu = mue + step;
       if (e.df > 0.0 && nmu > 0.0 && fabs(step) <= 1e-6 * nmu && nmu <= (double)mupf * (1.0 + 1e-5)) {
         mu = nmu;
         done = true;
@@ -712,10 +714,8 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
 
 // Floors (Sec. 3.2): rho >= rho0 r^-n, rho eps >= rho eps0 r^-n (r the Kerr-Schild radius; 1 in
 // Minkowski), and the Lorentz-factor ceiling W <= w_max.
-template <int METRIC>
-__device__ __forceinline__ int apply_floors(const DevParams& p, const double gam[6], double r, double P[NV]) {
-  double fr = 1.0;
-  if (METRIC == KERR_SCHILD) fr = p.floor_r_exp == 2.0 ? 1.0 / (r * r) : pow(r, -p.floor_r_exp);
+// Floors with the radius factor fr = r^-floor_r_exp already evaluated (1 in Minkowski).
+__device__ __forceinline__ int apply_floors_fr(const DevParams& p, const double gam[6], double fr, double P[NV]) {
   const double rho_flr = p.rho_floor0 * fr;
   const double eps_flr = p.eps_floor0 * fr;
   int st = 0;
@@ -731,8 +731,8 @@ __device__ __forceinline__ int apply_floors(const DevParams& p, const double gam
   double utl[3];
   lower3(gam, ut, utl);
   const double usq = ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2];
-  if (sqrt(1.0 + usq) > p.w_max) {
-    const double s = sqrt((p.w_max * p.w_max - 1.0) / usq);
+  if (1.0 + usq > p.w_max2) {  // W = sqrt(1 + u^2) > w_max
+    const double s = sqrt((p.w_max2 - 1.0) / usq);
     P[1] *= s;
     P[2] *= s;
     P[3] *= s;
@@ -741,15 +741,25 @@ __device__ __forceinline__ int apply_floors(const DevParams& p, const double gam
   return st;
 }
 
-// mu = 1/(h W) of a primitive state, the con2prim warm start.
+// Radius factor of the floors at Kerr-Schild radius r.
+__device__ __forceinline__ double floor_factor(const DevParams& p, double r) {
+  return p.floor_r_exp == 2.0 ? 1.0 / (r * r) : pow(r, -p.floor_r_exp);
+}
+
+template <int METRIC>
+__device__ __forceinline__ int apply_floors(const DevParams& p, const double gam[6], double r, double P[NV]) {
+  return apply_floors_fr(p, gam, METRIC == KERR_SCHILD ? floor_factor(p, r) : 1.0, P);
+}
+
+// mu = 1/(h W) of a primitive state, the con2prim warm start (in the arithmetic type R).
 template <class R>
-__device__ __forceinline__ double mu_of_prims(const double P[NV], const double gam[6], double gamma_eos) {
-  const double ut[3] = {P[1], P[2], P[3]};
-  double utl[3];
+__device__ __forceinline__ R mu_of_prims(const R P[NV], const R gam[6], R gamma_eos) {
+  const R ut[3] = {P[1], P[2], P[3]};
+  R utl[3];
   lower3(gam, ut, utl);
-  const double W = sqrt(1.0 + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
-  const double h = 1.0 + gamma_eos * P[4] / P[0];  // 1 + eps + p/rho = 1 + Gamma u/rho
-  return 1.0 / (h * W);
+  const R W = sqrt(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
+  const R h = R(1) + gamma_eos * P[4] / P[0];  // 1 + eps + p/rho = 1 + Gamma u/rho
+  return R(1) / (h * W);
 }
 
 }  // namespace grmhd

@@ -274,15 +274,19 @@ __device__ __forceinline__ void ks_sources(const DevParams& p, R x, R y, R z, co
   (void)L4;
 }
 
-// Double-precision metric at the centre of interior cell t: from the block's geometry cache when it
-// has one (Kerr-Schild), else evaluated in place.
+// Double-precision metric at the centre of interior cell t, 1/sqrt(gamma) and the floor radius factor:
+// from the block's geometry cache when it has one (Kerr-Schild), else evaluated in place.
 template <int METRIC>
 __device__ __forceinline__ void cell_metric(const DevParams& p, long long t, double xc, double yc, double zc,
-                                            Metric<double>& m, double& r) {
-  if (METRIC == KERR_SCHILD && p.geo != nullptr)
-    geo_load(p.geo, p.isize, t, m, r);
-  else
+                                            Metric<double>& m, double& isg, double& fr) {
+  if (METRIC == KERR_SCHILD && p.geo != nullptr) {
+    geo_load(p.geo, p.isize, t, m, isg, fr);
+  } else {
+    double r;
     metric_at<double, METRIC>(p, xc, yc, zc, m, &r);
+    isg = 1.0 / m.sqrtgam;
+    fr = METRIC == KERR_SCHILD ? floor_factor(p, r) : 1.0;
+  }
 }
 
 // Fill the geometry cache of a block (once, at context creation).
@@ -294,7 +298,7 @@ __global__ void k_geometry(DevParams p, double* __restrict__ geo) {
     double r;
     metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
                               p.x0[2] + (k + 0.5) * p.dx[2], m, &r);
-    geo_store(geo, p.isize, t, m, r);
+    geo_store(geo, p.isize, t, m, 1.0 / m.sqrtgam, METRIC == KERR_SCHILD ? floor_factor(p, r) : 1.0);
   }
 }
 
@@ -352,9 +356,9 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   const double xc = p.x0[0] + (i + 0.5) * p.dx[0];
   const double yc = p.x0[1] + (j + 0.5) * p.dx[1];
   const double zc = p.x0[2] + (k + 0.5) * p.dx[2];
-  double Pc[NV];
+  T Pt[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) Pc[q] = (double)P[q * G + g];
+  for (int q = 0; q < NV; ++q) Pt[q] = P[q * G + g];
   R L[NV];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -377,15 +381,20 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   L[6] = -((FxBy_p - FxBy_m) * R(p.idx[0]) + (FzBy_p - FzBy_m) * R(p.idx[2]));
   L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
   Metric<double> m;
-  double rks;
-  cell_metric<METRIC>(p, t, xc, yc, zc, m, rks);
+  double isg, fr;
+  cell_metric<METRIC>(p, t, xc, yc, zc, m, isg, fr);
+  // metric in the source / warm-start precision: the double one itself in the FP64 form
+  Metric<R> mr;
+  if constexpr (sizeof(R) == sizeof(double)) {
+    mr = m;
+  } else {
+    metric_at<R, METRIC>(p, R(xc), R(yc), R(zc), mr);
+  }
+  R Pr[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) Pr[q] = R(Pt[q]);
   if (METRIC == KERR_SCHILD) {
     R Sr[5];
-    R Pr[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) Pr[q] = R(Pc[q]);
-    Metric<R> mr;
-    metric_at<R, METRIC>(p, R(xc), R(yc), R(zc), mr);
     ks_sources<R>(p, R(xc), R(yc), R(zc), Pr, mr, Sr);
 #pragma unroll
     for (int q = 1; q < 5; ++q) L[q] += Sr[q];
@@ -397,12 +406,12 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
     if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
     Un[q] = u + bdt * (double)L[q];
   }
-  // a6: con2prim on the undensitized state, warm-started from the current primitives
-  const double isg = 1.0 / m.sqrtgam;
+  // a6: con2prim on the undensitized state, warm-started from the current primitives (the warm start only
+  // seeds the iteration: in the mixed form it is evaluated in float, the precision of its first phase)
   double Uc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
-  const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
+  const double mu0 = (double)mu_of_prims<R>(Pr, mr.gam, R(p.gamma_eos));
   double Pn[NV];
   int iters;
   int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters, a.worklist != nullptr)
@@ -415,7 +424,7 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
     cs.it_sum += iters;
     return;
   }
-  st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
+  st |= apply_floors_fr(p, m.gam, fr, Pn);
   if (st) {
     if (a.floorlist) {
       // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
@@ -456,23 +465,22 @@ __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict_
   const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
   const long long g = gidx(p, i, j, k);
   Metric<double> m;
-  double rks;
+  double isg, fr;
   cell_metric<METRIC>(p, t, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
-                      p.x0[2] + (k + 0.5) * p.dx[2], m, rks);
+                      p.x0[2] + (k + 0.5) * p.dx[2], m, isg, fr);
   double Pc[NV], Un[NV], Uc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     Pc[q] = (double)P[q * G + g];
     Un[q] = a.Unew[q * n + t];
   }
-  const double isg = 1.0 / m.sqrtgam;
 #pragma unroll
   for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
   const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
   double Pn[NV];
   int iters;
-  int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
-  st |= apply_floors<METRIC>(p, m.gam, rks, Pn);
+  int st = con2prim<double>(p, m, Uc, mu0, Pn, iters, true);
+  st |= apply_floors_fr(p, m.gam, fr, Pn);
   if (st) {
     double U5[5];
     prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
@@ -493,9 +501,9 @@ __device__ __forceinline__ void floor_cell(const DevParams& p, const T* __restri
   const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
   const long long g = gidx(p, i, j, k);
   Metric<double> m;
-  double rks;
+  double isg, fr;
   cell_metric<METRIC>(p, t, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
-                      p.x0[2] + (k + 0.5) * p.dx[2], m, rks);
+                      p.x0[2] + (k + 0.5) * p.dx[2], m, isg, fr);
   double Pn[NV], U5[5];
 #pragma unroll
   for (int q = 0; q < NV; ++q) Pn[q] = (double)P[q * G + g];

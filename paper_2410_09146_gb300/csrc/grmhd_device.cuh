@@ -545,6 +545,26 @@ __device__ __forceinline__ double c2p_mu_plus_fast(const C2PIn<double>& c) {
   return c2p_mu_plus<double>(c, (double)muf, 1e-15, 12);
 }
 
+// mu_+ in double from an accurate float value (relative error ~1e-7): two Newton steps on
+// g(mu) = mu^2 (1 + rbar^2(mu)) - 1 (quadratic convergence: 1e-7 -> 1e-14 -> rounding). A fixed step count,
+// so that the lanes of a warp stay together. mupf >= 1 is the bound mu_+ = 1 itself.
+__device__ __forceinline__ double c2p_mu_plus_polish(const C2PIn<double>& c, float mupf) {
+  double m1 = (double)mupf;
+  if (mupf < 1.f) {
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const double xx = 1.0 / (1.0 + m1 * c.b2);
+      const double dx = -c.b2 * xx * xx;
+      const double rb = xx * xx * c.r2 + m1 * xx * (1.0 + xx) * c.rb2;
+      const double drb = 2.0 * xx * dx * c.r2 + c.rb2 * (xx * (1.0 + xx) + m1 * dx * (1.0 + 2.0 * xx));
+      const double g = m1 * m1 * (1.0 + rb) - 1.0;
+      const double dg = 2.0 * m1 * (1.0 + rb) + m1 * m1 * drb;
+      m1 -= g / dg;
+    }
+  }
+  return m1;
+}
+
 // Bracketed Newton iteration on [0, mup] from mu (double or float). Returns 0 when converged (the
 // root, or mu_+ when f(mu_+) <= 0: the cold limit eps = 0), ST_NOT_CONVERGED otherwise.
 template <class T>
@@ -639,16 +659,22 @@ __device__ __forceinline__ void c2p_bad_output(const double Uc[NV], double Pout[
 template <class R>
 __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, const double Uc[NV],
                                         double mu_guess, double Pout[NV], int& iters, bool fast_mup = false) {
+  const unsigned lanes = __activemask();  // each of these lanes reaches the __syncwarp below once
   iters = 0;
   C2PIn<double> c;
   double ru[3], bu[3];
-  if (c2p_setup<R>(p, m, Uc, c, ru, bu)) {
+  const bool bad = c2p_setup<R>(p, m, Uc, c, ru, bu) != 0;
+  double mu = mu_guess;
+  int st = ST_BAD_INPUT;
+  if (!bad) {
+    const double mup = fast_mup ? c2p_mu_plus_fast(c) : c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
+    st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, iters, true);
+  }
+  __syncwarp(lanes);  // reconverge after iterations of different lengths: the output runs once per warp
+  if (bad) {
     c2p_bad_output(Uc, Pout);
     return ST_BAD_INPUT;
   }
-  const double mup = fast_mup ? c2p_mu_plus_fast(c) : c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
-  double mu = mu_guess;
-  const int st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, iters, true);
   c2p_output(c, mu, ru, bu, Uc, Pout);
   return st;
 }
@@ -660,20 +686,29 @@ enum { C2P_DEFERRED = 256 };  // returned by con2prim_mixed(defer = true): the c
 template <class R>
 __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R>& m, const double Uc[NV],
                                               double mu_guess, double Pout[NV], int& iters, bool defer = false) {
+  // Lanes entering together; each of them reaches the __syncwarp below exactly once (no return before it).
+  const unsigned lanes = __activemask();
   iters = 0;
   C2PIn<double> c;
   double ru[3], bu[3];
-  if (c2p_setup<R>(p, m, Uc, c, ru, bu)) {
+  const bool bad = c2p_setup<R>(p, m, Uc, c, ru, bu) != 0;
+  float mupf = 1.f, muf = 0.f;
+  int itf = 0, stf = ST_NOT_CONVERGED;
+  if (!bad) {
+    C2PIn<float> cf;
+    cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
+    cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
+    mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
+    muf = (float)mu_guess;
+    stf = c2p_newton<float>(cf, mupf, muf, 2e-6f, 24, itf, false);
+  }
+  // The float iterations end at different counts in different lanes: reconverge, so that the double part
+  // below runs once for the warp rather than once per group of lanes (FP64 issue is per warp instruction).
+  __syncwarp(lanes);
+  if (bad) {
     c2p_bad_output(Uc, Pout);
     return ST_BAD_INPUT;
   }
-  C2PIn<float> cf;
-  cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
-  cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
-  const float mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
-  float muf = (float)mu_guess;
-  int itf = 0;
-  const int stf = c2p_newton<float>(cf, mupf, muf, 2e-6f, 24, itf, false);
   iters = itf;
   double mu = (double)muf;
   bool done = false;
@@ -684,7 +719,10 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
     // step from the evaluation point must be small.
     const bool cold = muf >= mupf;
     double mue = mu;
-    if (cold) mue = c2p_mu_plus<double>(c, (double)mupf, 1e-15, 8);
+    if (__any_sync(__activemask(), cold)) {  // the same instructions for every lane of the warp
+      const double mup = c2p_mu_plus_polish(c, mupf);
+      if (cold) mue = mup;
+    }
     const C2PEval<double> e = c2p_master(c, mue);
     ++iters;
     if (cold && !(e.f > 0.0)) {

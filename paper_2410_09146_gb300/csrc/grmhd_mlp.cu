@@ -100,17 +100,13 @@ __global__ void __launch_bounds__(128) k_c2p_guided(const double* __restrict__ U
                                                     unsigned long long* stats) {
   unsigned int it_sum = 0, nconv = 0, nfall = 0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const unsigned lanes = __activemask();  // each of these lanes reaches the __syncwarp below once
     double Uc[NV], ru[3], bu[3], Pn[NV];
     C2PIn<double> c;
     int st = 0, iters = 0;
-    if (!flat_invariants(p, U, n, t, Uc, c, ru, bu)) {
-      c2p_bad_output(Uc, Pn);
-      st = ST_BAD_INPUT;
-      if (X)
-        for (int k = 0; k < NIN; ++k) X[t * NIN + k] = 0.f;
-      if (T) T[t * NOUT] = T[t * NOUT + 1] = 0.f;
-    } else {
-      double mup, mu;
+    const bool good = flat_invariants(p, U, n, t, Uc, c, ru, bu);
+    double mup = 0.0, mu = 0.0;
+    if (good) {
       bool done = false;
       if (guess) {
         mu = guess[t];
@@ -127,6 +123,15 @@ __global__ void __launch_bounds__(128) k_c2p_guided(const double* __restrict__ U
         st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, iters, true);
       }
       if (st) ++nconv;
+    }
+    __syncwarp(lanes);  // iterations of different lengths: run the output once per warp
+    if (!good) {
+      c2p_bad_output(Uc, Pn);
+      st = ST_BAD_INPUT;
+      if (X)
+        for (int k = 0; k < NIN; ++k) X[t * NIN + k] = 0.f;
+      if (T) T[t * NOUT] = T[t * NOUT + 1] = 0.f;
+    } else {
       c2p_output(c, mu, ru, bu, Uc, Pn);
       if (X) {
         float x[NIN];

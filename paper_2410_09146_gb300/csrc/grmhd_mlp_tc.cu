@@ -239,15 +239,13 @@ __global__ void __launch_bounds__(TC_M) k_c2p_net_tc(const double* __restrict__ 
     y0 = y0 * S.norm[2 * NIN + NOUT] + S.norm[2 * NIN];
     if (!valid) continue;
     // ---- Newton from the network's start, fallback to the standard start
+    const unsigned lanes = __activemask();  // each of these lanes reaches the __syncwarp below once
     double Pn[NV];
     int st = 0, iters = 0;
-    double mu0 = 0.0;
-    if (!good) {
-      c2p_bad_output(Uc, Pn);
-      st = ST_BAD_INPUT;
-    } else {
+    double mu0 = 0.0, mu = 0.0;
+    if (good) {
       const float yc = fminf(fmaxf(y0, 0.f), Y0_MAX);  // NaN -> 0 -> mu_0 = 0 -> fallback
-      double mu = mup - mup * (double)__expf(-yc);
+      mu = mup - mup * (double)__expf(-yc);
       mu0 = mu;
       bool done = false;
       if (mu > 0.0 && mu < mup) done = c2p_newton<double>(c, mup, mu, p.c2p_tol, GUESS_MAX_ITER, iters, true) == 0;
@@ -257,6 +255,12 @@ __global__ void __launch_bounds__(TC_M) k_c2p_net_tc(const double* __restrict__ 
         st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, iters, true);
       }
       if (st) ++nconv;
+    }
+    __syncwarp(lanes);  // iterations of different lengths: run the output once per warp
+    if (!good) {
+      c2p_bad_output(Uc, Pn);
+      st = ST_BAD_INPUT;
+    } else {
       c2p_output(c, mu, ru, bu, Uc, Pn);
     }
     Metric<double> m;

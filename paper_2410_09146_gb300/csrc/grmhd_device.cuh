@@ -451,6 +451,7 @@ __device__ __forceinline__ T c2p_rbar2(const C2PIn<T>& c, T mu, T& x) {
 template <class T>
 struct C2PEval {
   T f, df, x, W, rho, eps;
+  T dx, dW, drho, deps;  // derivatives of x, W, rho, eps with respect to mu (0 from c2p_master_value)
 };
 
 template <class T>
@@ -481,6 +482,10 @@ __device__ __forceinline__ C2PEval<T> c2p_master(const C2PIn<T>& c, T mu_v) {
   e.W = W.v;
   e.rho = rho.v;
   e.eps = eps.v;
+  e.dx = x.d;
+  e.dW = W.d;
+  e.drho = rho.d;
+  e.deps = eps.d;
   return e;
 }
 
@@ -503,6 +508,7 @@ __device__ __forceinline__ C2PEval<T> c2p_master_value(const C2PIn<T>& c, T mu) 
   e.W = W;
   e.rho = c.D / W;
   e.eps = eps;
+  e.dx = e.dW = e.drho = e.deps = T(0);
   return e;
 }
 
@@ -612,11 +618,11 @@ __device__ __forceinline__ int c2p_setup(const DevParams& p, const Metric<R>& m,
     gamu[t] = (double)m.gamu[t];
   }
   c.D = Uc[0];
-  const double iD = 1.0 / c.D;
+  const double isD = rsqrt(c.D);  // 1/sqrt(D), and 1/D as its square
+  const double iD = isD * isD;
   c.q = Uc[4] * iD;
   const double rl[3] = {Uc[1] * iD, Uc[2] * iD, Uc[3] * iD};
   lower3(gamu, rl, ru);
-  const double isD = 1.0 / sqrt(c.D);
   bu[0] = Uc[5] * isD;
   bu[1] = Uc[6] * isD;
   bu[2] = Uc[7] * isD;
@@ -633,9 +639,9 @@ __device__ __forceinline__ int c2p_setup(const DevParams& p, const Metric<R>& m,
 }
 
 // Primitives at the root mu.
-__device__ __forceinline__ void c2p_output(const C2PIn<double>& c, double mu, const double ru[3], const double bu[3],
-                                           const double Uc[NV], double Pout[NV]) {
-  const C2PEval<double> e = c2p_master_value(c, mu);
+__device__ __forceinline__ void c2p_output_eval(const C2PIn<double>& c, const C2PEval<double>& e, double mu,
+                                                const double ru[3], const double bu[3], const double Uc[NV],
+                                                double Pout[NV]) {
   const double W = e.W;
   Pout[0] = e.rho;
   const double mx = mu * e.x;
@@ -644,6 +650,11 @@ __device__ __forceinline__ void c2p_output(const C2PIn<double>& c, double mu, co
   Pout[4] = e.rho * e.eps;
 #pragma unroll
   for (int k = 0; k < 3; ++k) Pout[5 + k] = Uc[5 + k];
+}
+
+__device__ __forceinline__ void c2p_output(const C2PIn<double>& c, double mu, const double ru[3], const double bu[3],
+                                           const double Uc[NV], double Pout[NV]) {
+  c2p_output_eval(c, c2p_master_value(c, mu), mu, ru, bu, Uc, Pout);
 }
 
 __device__ __forceinline__ void c2p_bad_output(const double Uc[NV], double Pout[NV]) {
@@ -712,6 +723,7 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
   iters = itf;
   double mu = (double)muf;
   bool done = false;
+  C2PEval<double> ev;  // the intermediates at the accepted root
   if (stf == 0 && isfinite(mu) && mu > 0.0) {
     // One double evaluation of the master function for every cell, so that a warp runs it once: at the
     // float root, or, when that sits on the bracket end (cold limit), at mu_+ settled in double. A cold
@@ -727,26 +739,36 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
     ++iters;
     if (cold && !(e.f > 0.0)) {
       mu = mue;
+      ev = e;
       done = true;
     } else {
       const double step = -e.f / e.df;
       const double nmu = mue + step;
       if (e.df > 0.0 && nmu > 0.0 && fabs(step) <= 1e-6 * nmu && nmu <= (double)mupf * (1.0 + 1e-5)) {
+        // the intermediates at the root to first order in the step (the neglected term is O(step^2),
+        // ~1e-12 relative): no second evaluation of the master function
         mu = nmu;
+        ev = e;
+        ev.x += e.dx * step;
+        ev.W += e.dW * step;
+        ev.rho += e.drho * step;
+        ev.eps = fmax(e.eps + e.deps * step, 0.0);
         done = true;
       }
     }
   }
   int st = 0;
   if (!done && defer) return C2P_DEFERRED;
-  if (!done) {  // float phase did not settle: full double iteration
-    const double mup = c2p_mu_plus<double>(c, -1.0, 1e-15, 60);
-    mu = mu_guess;
+  if (!done) {  // float phase did not settle: double iteration on the full bracket, from the float root
+    const double mup = c2p_mu_plus_fast(c);
+    if (!(stf == 0 && isfinite(mu) && mu > 0.0)) mu = mu_guess;
     int it64 = 0;
     st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, it64, true);
     iters += it64;
+    c2p_output(c, mu, ru, bu, Uc, Pout);
+    return st;
   }
-  c2p_output(c, mu, ru, bu, Uc, Pout);
+  c2p_output_eval(c, ev, mu, ru, bu, Uc, Pout);
   return st;
 }
 

@@ -290,7 +290,8 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
-        "gpu_launches": 6 * args.steps + (args.steps + 1) // 2,  # 3 flux, EMF, update, deferred update per stage; CFL per step
+        # per stage: 3 flux, EMF, update, floored-cell pass, deferred con2prim; the CFL finalisation per step
+        "gpu_launches": 7 * args.steps + (args.steps + 1) // 2,
     }
     if batched is not None:
         out["batched"] = batched
@@ -444,13 +445,18 @@ def run_batched(G, I, steps, warmup, rank):
             "c2p_iterations_per_cell": float(stats[0]) / zones}, ms, zones
 
 
-# Work and traffic per unit of the mixed-form kernels, measured by ncu on the 96^3 Kerr-Schild random
-# block (profiles/k_update_k_flux_kerr_schild_96_mixed.md): double-precision flops (DADD + DMUL +
-# 2 DFMA, active lanes) per cell of k_update, float flops per face of k_flux, DRAM bytes per unit.
-UPDATE_FP64_FLOP_PER_CELL = 787.0
-UPDATE_DRAM_BYTES_PER_CELL = 272.0
-FLUX_FP32_FLOP_PER_FACE = 4755.0
-FLUX_DRAM_BYTES_PER_FACE = 40.6
+# Work and traffic per unit of the mixed-form kernels, measured by ncu (--set full) on the 96^3
+# Kerr-Schild random block (profiles/k_update_k_flux_kerr_schild_96_mixed.md): double-precision flops
+# (DADD + DMUL + 2 DFMA, active lanes) per cell of k_update, float flops (FADD + FMUL + 2 FFMA) per face
+# of k_flux, DRAM bytes (read + write) per unit.
+UPDATE_FP64_FLOP_PER_CELL = 457.2
+UPDATE_DRAM_BYTES_PER_CELL = 438.9
+# algorithmic bytes per cell of k_update: P (8 float) + Ucur (8 double) + U0 (8 double, stages with
+# g0 != 0) + 3 x 8 face fluxes (float) + 3 EMFs (float) + 19 doubles of cached geometry read; Unew
+# (8 double) + P (8 float) + status written; the average over the two stages of an RK2 step
+UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 152 + 64 + 32 + 1
+FLUX_FP32_FLOP_PER_FACE = 4563.0
+FLUX_DRAM_BYTES_PER_FACE = 41.2
 FP64_PEAK_TFLOPS = 1.008   # measured DFMA rate (profiles/fp_throughput_gb300.md)
 FP32_PEAK_TFLOPS = 74.5    # measured FFMA rate
 
@@ -462,12 +468,13 @@ def roofline(dom, ms, n, s, stats, peaks):
     if dom == "update":
         flops = UPDATE_FP64_FLOP_PER_CELL * cells
         achieved = flops / (ms / 1e3) / 1e12
-        return {"kernel": "k_update (+ deferred con2prim)", "bound": "alu", "achieved": achieved,
+        return {"kernel": "k_update", "bound": "alu", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": UPDATE_DRAM_BYTES_PER_CELL * cells, "ms_per_launch": ms,
                 "work_per_unit": f"{UPDATE_FP64_FLOP_PER_CELL} FP64 flop/cell (ncu, 96^3)",
-                "algorithmic_bytes_per_cell": 297,
-                "note": "FP64 pipe; peak = measured DFMA rate of this GB300 (MEASURED_PEAKS.json has no FP64 figure); "
+                "algorithmic_bytes_per_cell": UPDATE_ALGO_BYTES_PER_CELL,
+                "note": "FP64 pipe (issue-bound: one warp FP64 instruction per ~20 SM cycles whatever its active "
+                        "lanes); peak = measured DFMA rate of this GB300 (MEASURED_PEAKS.json has no FP64 figure); "
                         "traffic scaled from the 96^3 ncu capture by cell count"}
     faces = 3 * (n + 1) * (n + 2) ** 2 / 3.0
     flops = FLUX_FP32_FLOP_PER_FACE * faces

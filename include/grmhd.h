@@ -233,10 +233,11 @@ int grmhd_get(grmhd_ctx* c, int what, void* dst, int where);
  * the records are asynchronous. */
 int grmhd_set_timing(grmhd_ctx* c, int on);
 
-/* Accumulated device milliseconds per kernel group since the last call, ms[6] = ghost fill, flux x,
+/* Accumulated device milliseconds per kernel group since the last call, ms[7] = ghost fill, flux x,
  * flux y, flux z (each including its share of the CFL reduction), EMF, update (divergence + sources +
- * RK + con2prim + floors), and the number of stages they cover; resets the totals. Synchronises on
- * the last recorded event. */
+ * RK + con2prim + floors), cell passes (re-derived hydro state of floored cells; the mixed form's
+ * double con2prim of cells whose float phase did not settle), and the number of stages they cover;
+ * resets the totals. Synchronises on the last recorded event. */
 int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
 
 /* One all-FP64 Runge-Kutta stage, like grmhd_stage, for callers that cannot allocate device memory

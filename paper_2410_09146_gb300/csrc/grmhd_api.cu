@@ -32,8 +32,8 @@ struct grmhd_ctx {
   int s0, sc;                // slot of U0 and of the current state
   bool has_state;
   bool timing;               // record CUDA events around each kernel group
-  cudaEvent_t ev[8];         // ghost | flux x | flux y | flux z | emf | update | end
-  double t_ms[6];            // accumulated ms per kernel group since the last read
+  cudaEvent_t ev[8];         // ghost | flux x | flux y | flux z | emf | update | cell passes | end
+  double t_ms[7];            // accumulated ms per kernel group since the last read
   int t_stages;              // stages accumulated
   bool t_pending;            // events of the last stage not yet read
   // batch of meshblocks (nblocks == 0: a single-block context)
@@ -153,9 +153,9 @@ bool batch_only(const grmhd_ctx* c) { return c->dp.isize == 0; }
 // Fold the events of the last timed stage into the per-kernel totals (synchronises on its last event).
 cudaError_t collect_timing(grmhd_ctx* c) {
   if (!c->t_pending) return cudaSuccess;
-  cudaError_t e = cudaEventSynchronize(c->ev[6]);
+  cudaError_t e = cudaEventSynchronize(c->ev[7]);
   if (e != cudaSuccess) return e;
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 7; ++k) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]);
     if (e != cudaSuccess) return e;
@@ -454,6 +454,8 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   a.fl_count = (unsigned int*)(c->scal + 17);
   CK(L.update(c->dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
   TMARK(6);
+  CK(L.cell_passes(c->dp, c->P, a, s), "floored and deferred cells");
+  TMARK(7);
 #undef TMARK
   if (c->timing) c->t_pending = true;
   c->sc = dst;
@@ -601,11 +603,11 @@ int grmhd_get(grmhd_ctx* c, int what, void* dst, int where) {
 int grmhd_set_timing(grmhd_ctx* c, int on) {
   if (!c) return GRMHD_E_INVALID;
   if (on && !c->timing) {
-    for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&c->ev[k]), "creating timing events");
+    for (int k = 0; k < 8; ++k) CK(cudaEventCreate(&c->ev[k]), "creating timing events");
   }
   if (!on && c->timing) {
     CK(collect_timing(c), "reading kernel timings");
-    for (int k = 0; k < 7; ++k) cudaEventDestroy(c->ev[k]);
+    for (int k = 0; k < 8; ++k) cudaEventDestroy(c->ev[k]);
   }
   c->timing = on != 0;
   return GRMHD_OK;
@@ -614,7 +616,7 @@ int grmhd_set_timing(grmhd_ctx* c, int on) {
 int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages) {
   if (!c || !ms) return GRMHD_E_INVALID;
   if (c->timing) CK(collect_timing(c), "reading kernel timings");
-  for (int k = 0; k < 6; ++k) {
+  for (int k = 0; k < 7; ++k) {
     ms[k] = c->t_ms[k];
     c->t_ms[k] = 0.0;
   }
@@ -627,7 +629,7 @@ const char* grmhd_last_error(const grmhd_ctx* c) { return c ? c->err : g_create_
 
 void grmhd_destroy(grmhd_ctx* c) {
   if (c && c->timing)
-    for (int k = 0; k < 7; ++k) cudaEventDestroy(c->ev[k]);
+    for (int k = 0; k < 8; ++k) cudaEventDestroy(c->ev[k]);
   if (c) {
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -17,6 +17,8 @@ struct FormLaunchers {
   cudaError_t (*emf)(const DevParams& p, const void* Fx, const void* Fy, const void* Fz, void* E, cudaStream_t s);
   cudaError_t (*update)(const DevParams& p, void* P, const void* Fx, const void* Fy, const void* Fz, const void* E,
                         const StageArgs& a, cudaStream_t s);
+  // the passes over the cells queued by update (floored cells; deferred con2prim in the mixed form)
+  cudaError_t (*cell_passes)(const DevParams& p, void* P, const StageArgs& a, cudaStream_t s);
   cudaError_t (*prim2con)(const DevParams& p, const void* P, double* U, cudaStream_t s);
   cudaError_t (*load_prims)(const DevParams& p, const double* src, void* P, cudaStream_t s);   // double -> storage
   cudaError_t (*store_prims)(const DevParams& p, const void* P, double* dst, cudaStream_t s);  // storage -> double

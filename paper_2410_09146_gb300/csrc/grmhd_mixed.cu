@@ -48,17 +48,19 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
     k_update<KERR_SCHILD, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
   else
     k_update<MINKOWSKI, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // passes over the cells queued by k_update (counts known on the device only): re-derivation of the
-  // hydro state of floored cells, and the double con2prim of cells whose float phase did not settle
+  return cudaGetLastError();
+}
+
+// Passes over the cells queued by k_update (counts known on the device only): re-derivation of the hydro
+// state of floored cells, and (mixed form) the double con2prim of cells whose float phase did not settle.
+cudaError_t cell_passes(const DevParams& p, void* P, const StageArgs& a, cudaStream_t s) {
   const int g2 = grid_for(p.isize / 8 + 1, 128);
   if (a.floorlist) {
     if (p.metric == KERR_SCHILD)
       k_update_floors<KERR_SCHILD, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
     else
       k_update_floors<MINKOWSKI, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (a.worklist == nullptr) return cudaSuccess;
@@ -97,7 +99,7 @@ cudaError_t geometry(const DevParams& p, double* geo, cudaStream_t s) {
 }
 
 using BL = BatchLaunch<float, float>;
-const FormLaunchers kMixed = {ghost, flux, emf, update, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
+const FormLaunchers kMixed = {ghost, flux, emf, update, cell_passes, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
                                 BL::deferred, BL::ctas_per_sm, 4, 4, geometry, BL::floors};
 
 }  // namespace

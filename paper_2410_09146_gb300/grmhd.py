@@ -249,11 +249,11 @@ def grmhd_set_timing(ctx: int, on: bool) -> None:
     _check(lib().grmhd_set_timing(ctx, int(on)), ctx)
 
 
-KERNEL_GROUPS = ("ghost", "flux_x", "flux_y", "flux_z", "emf", "update")
+KERNEL_GROUPS = ("ghost", "flux_x", "flux_y", "flux_z", "emf", "update", "cell_passes")
 
 
 def grmhd_get_timing(ctx: int):
-    ms = (ctypes.c_double * 6)()
+    ms = (ctypes.c_double * 7)()
     n = ctypes.c_int(0)
     _check(lib().grmhd_get_timing(ctx, ms, ctypes.byref(n)), ctx)
     return dict(zip(KERNEL_GROUPS, list(ms))), n.value

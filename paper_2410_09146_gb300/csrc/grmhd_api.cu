@@ -171,8 +171,7 @@ constexpr int kMinTile = 128;
 long long block_items(const DevParams& p, int tile, int phase) {
   long long n;
   if (phase < 3) {
-    int ex, ey;
-    n = face_box(p, phase, ex, ey);
+    n = flux_units(p, phase);
   } else if (phase == 3) {
     n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
   } else {
@@ -188,8 +187,7 @@ std::vector<WorkItem> build_items(const std::vector<BlockDesc>& blocks, int tile
     for (int phase = 0; phase < 5; ++phase) {
       long long n;
       if (phase < 3) {
-        int ex, ey;
-        n = face_box(p, phase, ex, ey);
+        n = flux_units(p, phase);
       } else if (phase == 3) {
         n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
       } else {

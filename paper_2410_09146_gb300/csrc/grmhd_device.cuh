@@ -77,8 +77,8 @@ struct BlockDesc {
   long long cell_offset;  // index of the block's first interior cell in the batch
 };
 
-// A contiguous range of faces / edges / cells of one block (phase 0..2: fluxes of direction d,
-// 3: EMFs, 4: cell update).
+// A contiguous range of flux units (faces, or runs of faces: flux_units) / edges / cells of one block
+// (phase 0..2: fluxes of direction d, 3: EMFs, 4: cell update).
 struct WorkItem {
   int block;
   int phase;
@@ -320,17 +320,23 @@ __device__ __forceinline__ R minmod_slope(R dm, R dp) {
   return dm > R(0) ? m : -m;
 }
 
-// WENO5-Z value at the face on the f2 -> f3 side of the centre value f2 (stencil f0..f4),
-// and its nonlinear weights. Candidates are the third-order cell-average forms, linear weights
-// (1/10, 6/10, 3/10), tau_Z = |beta_2 - beta_0|, exponent p = 2.
+// WENO5-Z values at both faces of the cell with centre value f2 (stencil f0..f4), and their nonlinear
+// weights. Candidates are the third-order cell-average forms, linear weights (1/10, 6/10, 3/10),
+// tau_Z = |beta_2 - beta_0|, exponent p = 2. The plus face comes from (f0..f4), the minus face from the
+// mirrored stencil (f4..f0). The mirrored stencil has the same smoothness indicators in reverse order (beta_0 <-> beta_2)
+// and the same tau, so they and the ratios tau/(beta + eps) are computed once; only the candidate values
+// and the linear weights (gamma is not symmetric) differ between the two sides.
 template <class R>
-__device__ __forceinline__ R weno5z_face(R f0, R f1, R f2, R f3, R f4, R eps, R w[3]) {
+__device__ __forceinline__ void weno5z_both(R f0, R f1, R f2, R f3, R f4, R eps, R& qp, R& qm, R wp[3], R wm[3]) {
   const R P0 = (R(2) * f0 - R(7) * f1 + R(11) * f2) * R(1.0 / 6.0);
   const R P1 = (-f1 + R(5) * f2 + R(2) * f3) * R(1.0 / 6.0);
   const R P2 = (R(2) * f2 + R(5) * f3 - f4) * R(1.0 / 6.0);
-  R t0 = f0 - R(2) * f1 + f2, s0 = f0 - R(4) * f1 + R(3) * f2;
-  R t1 = f1 - R(2) * f2 + f3, s1 = f1 - f3;
-  R t2 = f2 - R(2) * f3 + f4, s2 = R(3) * f2 - R(4) * f3 + f4;
+  const R M0 = (R(2) * f4 - R(7) * f3 + R(11) * f2) * R(1.0 / 6.0);  // mirrored candidates
+  const R M1 = (-f3 + R(5) * f2 + R(2) * f1) * R(1.0 / 6.0);
+  const R M2 = (R(2) * f2 + R(5) * f1 - f0) * R(1.0 / 6.0);
+  const R t0 = f0 - R(2) * f1 + f2, s0 = f0 - R(4) * f1 + R(3) * f2;
+  const R t1 = f1 - R(2) * f2 + f3, s1 = f1 - f3;
+  const R t2 = f2 - R(2) * f3 + f4, s2 = R(3) * f2 - R(4) * f3 + f4;
   const R b0 = R(13.0 / 12.0) * t0 * t0 + R(0.25) * s0 * s0;
   const R b1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * s1 * s1;
   const R b2 = R(13.0 / 12.0) * t2 * t2 + R(0.25) * s2 * s2;
@@ -341,14 +347,18 @@ __device__ __forceinline__ R weno5z_face(R f0, R f1, R f2, R f3, R f4, R eps, R 
     q1 = fmin(q1, R(1e15));
     q2 = fmin(q2, R(1e15));
   }
-  const R a0 = R(0.1) * (R(1) + q0 * q0);
-  const R a1 = R(0.6) * (R(1) + q1 * q1);
-  const R a2 = R(0.3) * (R(1) + q2 * q2);
-  const R is = rcp(a0 + a1 + a2);
-  w[0] = a0 * is;
-  w[1] = a1 * is;
-  w[2] = a2 * is;
-  return w[0] * P0 + w[1] * P1 + w[2] * P2;
+  const R z0 = R(1) + q0 * q0, z1 = R(1) + q1 * q1, z2 = R(1) + q2 * q2;
+  const R a0 = R(0.1) * z0, a1 = R(0.6) * z1, a2 = R(0.3) * z2;      // plus side
+  const R c0 = R(0.1) * z2, c1 = R(0.6) * z1, c2 = R(0.3) * z0;      // minus side (stencils mirrored)
+  const R is = rcp(a0 + a1 + a2), im = rcp(c0 + c1 + c2);
+  wp[0] = a0 * is;
+  wp[1] = a1 * is;
+  wp[2] = a2 * is;
+  wm[0] = c0 * im;
+  wm[1] = c1 * im;
+  wm[2] = c2 * im;
+  qp = wp[0] * P0 + wp[1] * P1 + wp[2] * P2;
+  qm = wm[0] * M0 + wm[1] * M1 + wm[2] * M2;
 }
 
 template <class R>
@@ -366,9 +376,8 @@ __device__ __forceinline__ void recon_cell(R f0, R f1, R f2, R f3, R f4, R eps, 
     qm = f2 - R(0.5) * s;
     qp = f2 + R(0.5) * s;
   } else {
-    R wp[3], wm[3];
-    const R P5p = weno5z_face<R>(f0, f1, f2, f3, f4, eps, wp);
-    const R P5m = weno5z_face<R>(f4, f3, f2, f1, f0, eps, wm);  // mirrored stencil x -> -x
+    R wp[3], wm[3], P5p, P5m;
+    weno5z_both<R>(f0, f1, f2, f3, f4, eps, P5p, P5m, wp, wm);
     const R sp = weno_sigma_side(wp), sm = weno_sigma_side(wm);
     R sigma = sp + sm > R(0) ? R(2) * sp * sm / (sp + sm) : R(0);  // both sides can underflow in float
     sigma = sigma > R(1) ? R(1) : sigma;
@@ -434,6 +443,21 @@ template <class T>
 __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
   const T s = sqrt(a.v);
   return {s, a.d * T(0.5) / s};
+}
+
+// Work units of the flux phase of direction d: faces (face-centric reconstructions), or, for
+// WENO5-Z-AOAH, (transverse position, run of FLUX_RUN faces along d) pairs (cell-centric: each cell
+// reconstructed once per direction). The transverse positions span [-1, n] in both directions.
+constexpr int FLUX_RUN = 16;
+
+__host__ __device__ __forceinline__ long long flux_units(const DevParams& p, int d) {
+  if (p.recon == RECON_WENO5Z) {
+    const int nd = d == 0 ? p.nx : (d == 1 ? p.ny : p.nz);
+    const int na = d == 0 ? p.ny : p.nx, nb = d == 2 ? p.ny : p.nz;
+    return (long long)(na + 2) * (nb + 2) * ((nd + FLUX_RUN) / FLUX_RUN);
+  }
+  int ex, ey;
+  return face_box(p, d, ex, ey);
 }
 
 template <class T>

@@ -19,7 +19,9 @@ cudaError_t flux_m(const DevParams& p, const T* P, R* F, unsigned long long* ms,
     case RECON_CONSTANT: k_flux<R, T, METRIC, RECON_CONSTANT><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
     case RECON_PLM_MINMOD: k_flux<R, T, METRIC, RECON_PLM_MINMOD><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
     case RECON_PLM_MC: k_flux<R, T, METRIC, RECON_PLM_MC><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
-    case RECON_WENO5Z: k_flux<R, T, METRIC, RECON_WENO5Z><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+    case RECON_WENO5Z:  // cell-centric: each cell reconstructed once per direction
+      k_flux_cc<R, T, METRIC><<<grid_for(flux_units(p, d), 128), 128, 0, s>>>(P, F, ms, p, d, track);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -42,8 +42,35 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// a1 + a2 + a3 for face t of direction d: reconstruct the two cells beside the face, evaluate the
-// metric at the face centre, the two sides' (U, F, lambda), and the Riemann flux. Writes F and
+// a1 + a3 for the face between cells (i, j, k) - e_d and (i, j, k) of direction d, given the two
+// reconstructed sides PL, PR and the two cell values cL, cR: evaluate the metric at the face centre, the
+// two sides' (U, F, lambda), and the Riemann flux Fh; returns max |lambda|. A face whose reconstructed
+// density is not positive or internal energy is negative on either side takes the first-order (cell)
+// values of both neighbours.
+template <class R, int METRIC>
+__device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, int k, R PL[NV], R PR[NV],
+                                       const R cL[NV], const R cR[NV], R Fh[NV]) {
+  if (!(PL[0] > R(0)) || !(PL[4] >= R(0)) || !(PR[0] > R(0)) || !(PR[4] >= R(0))) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      PL[q] = cL[q];
+      PR[q] = cR[q];
+    }
+  }
+  // face centre, in the flux arithmetic type
+  R xf[3] = {R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
+             R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2])};
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
+  Metric<R> m;
+  metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
+  FaceSide<R> L, Rs;
+  prim_to_face<R>(PL, m, d, R(p.gamma_eos), L);
+  prim_to_face<R>(PR, m, d, R(p.gamma_eos), Rs);
+  return riemann_flux<R>(p.riemann, L, Rs, Fh);
+}
+
+// a2 for face t of direction d: reconstruct the two cells beside the face, then face_flux. Writes F and
 // returns max |lambda| of the face when it is an interior face (0 otherwise).
 template <class R, class T, int METRIC, int RECON>
 __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__ P, R* __restrict__ F, int d,
@@ -55,7 +82,7 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
   const int j = (int)((t / ex) % ey) + (d == 1 ? 0 : -1);
   const int k = (int)(t / ((long long)ex * ey)) + (d == 2 ? 0 : -1);
   const long long g = gidx(p, i, j, k);
-  R PL[NV], PR[NV];
+  R PL[NV], PR[NV], cL[NV], cR[NV];
   const R eps = R(p.weno_eps);
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
@@ -71,28 +98,11 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
     PL[q] = qp;
     recon_cell<R, RECON>(fm2, fm1, f0, fp1, fp2, eps, qm, qp);  // cell c
     PR[q] = qm;
+    cL[q] = fm1;
+    cR[q] = f0;
   }
-  // A face whose reconstructed density is not positive or internal energy is negative on
-  // either side takes the first-order (cell) values of both neighbours.
-  if (!(PL[0] > R(0)) || !(PL[4] >= R(0)) || !(PR[0] > R(0)) || !(PR[4] >= R(0))) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      PL[q] = R(P[q * p.gsize + g - stride]);
-      PR[q] = R(P[q * p.gsize + g]);
-    }
-  }
-  // face centre, in the flux arithmetic type
-  R xf[3] = {R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
-             R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2])};
-  const int cd = d == 0 ? i : (d == 1 ? j : k);
-  xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
-  Metric<R> m;
-  metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
-  FaceSide<R> L, Rs;
-  prim_to_face<R>(PL, m, d, R(p.gamma_eos), L);
-  prim_to_face<R>(PR, m, d, R(p.gamma_eos), Rs);
   R Fh[NV];
-  const R cm = riemann_flux<R>(p.riemann, L, Rs, Fh);
+  const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
 #pragma unroll
   for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
   const bool interior = (d == 0 || (i >= 0 && i < p.nx)) && (d == 1 || (j >= 0 && j < p.ny)) &&
@@ -129,6 +139,90 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nface;
        t += (long long)gridDim.x * blockDim.x) {
     const R cm = flux_face<R, T, METRIC, RECON>(p, P, F, d, t);
+    if (cm > cm_local) cm_local = cm;
+  }
+  if (track_speed) block_max_to<R>(cm_local, ms + d);
+}
+
+// Cell-centric fluxes of direction d for WENO5-Z-AOAH, unit t of flux_units: one transverse position and
+// a run of FLUX_RUN faces along d. A sliding window of five cells per variable is loaded once per cell;
+// each cell is reconstructed once (both of its faces), and face f pairs the plus side of cell f - 1 with
+// the minus side of cell f (face_flux, as in the face-centric flux_face). Returns max |lambda| over the
+// run's interior faces.
+template <class R, class T, int METRIC>
+__device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ P, R* __restrict__ F, int d,
+                                      long long t) {
+  // transverse coordinates: a fastest (x for d = 1, 2; y for d = 0), b the other
+  const int nd = d == 0 ? p.nx : (d == 1 ? p.ny : p.nz);
+  const int na = d == 0 ? p.ny : p.nx;
+  const int nb = d == 2 ? p.ny : p.nz;
+  const long long sd = d == 0 ? 1 : (d == 1 ? (long long)p.gx : (long long)p.gx * p.gy);
+  const R eps = R(p.weno_eps);
+  const int a = (int)(t % (na + 2)) - 1;
+  const long long rest = t / (na + 2);
+  const int b = (int)(rest % (nb + 2)) - 1;
+  const int f0 = (int)(rest / (nb + 2)) * FLUX_RUN;
+  const int f1 = min(f0 + FLUX_RUN, nd + 1);
+  int i = d == 0 ? f0 : a;
+  int j = d == 1 ? f0 : (d == 0 ? a : b);
+  int k = d == 2 ? f0 : b;
+  const bool inner_t = a >= 0 && a < na && b >= 0 && b < nb;  // interior transverse position
+  long long g = gidx(p, i, j, k);
+  // window of cell f0 - 1: cells f0 - 3 .. f0 + 1
+  R w[NV][5];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const T* Pq = P + q * p.gsize + g;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) w[q][s] = R(Pq[(s - 3) * sd]);
+  }
+  R PL[NV], cL[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    R qm, qp;
+    recon_cell<R, RECON_WENO5Z>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
+    PL[q] = qp;
+    cL[q] = w[q][2];
+  }
+  R cm_run = R(0);
+  for (int f = f0; f < f1; ++f) {
+    // window of cell f: cells f - 2 .. f + 2
+    R PR[NV], cR[NV], QP[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) w[q][s] = w[q][s + 1];
+      w[q][4] = R(P[q * p.gsize + g + 2 * sd]);
+      R qm, qp;
+      recon_cell<R, RECON_WENO5Z>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
+      PR[q] = qm;
+      QP[q] = qp;
+      cR[q] = w[q][2];
+    }
+    R Fh[NV];
+    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      F[q * p.gsize + g] = Fh[q];
+      PL[q] = QP[q];
+      cL[q] = cR[q];
+    }
+    if (inner_t && cm > cm_run) cm_run = cm;
+    g += sd;
+    if (d == 0) ++i; else if (d == 1) ++j; else ++k;
+  }
+  return cm_run;
+}
+
+template <class R, class T, int METRIC>
+__global__ void __launch_bounds__(128) k_flux_cc(const T* __restrict__ P, R* __restrict__ F,
+                                                 unsigned long long* __restrict__ ms, DevParams p, int d,
+                                                 int track_speed) {
+  const long long total = flux_units(p, d);
+  R cm_local = R(0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const R cm = flux_run<R, T, METRIC>(p, P, F, d, t);
     if (cm > cm_local) cm_local = cm;
   }
   if (track_speed) block_max_to<R>(cm_local, ms + d);
@@ -573,7 +667,11 @@ __global__ void __launch_bounds__(128) k_batch_flux(const BlockDesc* __restrict_
     const BlockDesc& b = blocks[w.block];
     const R idx = R(b.p.idx[w.phase]);
     for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
-      const R cm = flux_face<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k) * idx;
+      // units of flux_units: runs of faces for WENO5-Z-AOAH (cell-centric), single faces otherwise
+      const R cm = (RECON == RECON_WENO5Z
+                        ? flux_run<R, T, METRIC>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k)
+                        : flux_face<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k)) *
+                   idx;
       if (cm > cm_local) cm_local = cm;
     }
   }

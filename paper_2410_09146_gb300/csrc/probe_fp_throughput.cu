@@ -1,5 +1,6 @@
 // Arithmetic-throughput probe: FP64 / FP32 FMA, add, mul, divide and square root on eight
-// independent chains per thread, 152 x 8 blocks of 256 threads. Prints operations per second.
+// independent chains per thread, 152 x 8 blocks of 256 threads. Prints operations per second; then the
+// DFMA rate when only some lanes of every warp take part (how the FP64 pipe charges a partly active warp).
 // The all-FP64 stage is bound by the FP64 pipe on GB300, and its roofline peak is this probe's
 // DFMA rate. Build and run:
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o probe_fp probe_fp_throughput.cu && ./probe_fp
@@ -45,6 +46,21 @@ __global__ void chains32(float* out, int iters, float s) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 
+// DFMA chains in the lanes below `lanes` of every warp only.
+__global__ void chains64_lanes(double* out, int iters, double s, int lanes) {
+  double a[NCH];
+  for (int c = 0; c < NCH; ++c) a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  if ((int)(threadIdx.x & 31) < lanes) {
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) a[c] = fma(a[c], s, 1e-9);
+    }
+  }
+  double t = 0;
+  for (int c = 0; c < NCH; ++c) t += a[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 template <typename K, typename T>
 static void timed(const char* name, K kern, T* buf, int iters, T s, int blocks, int threads, double flop_per_op) {
   cudaEvent_t e0, e1;
@@ -82,6 +98,23 @@ int main() {
   timed("ffma", chains32<0>, d32, 20000, 0.999999f, blocks, threads, 2);
   timed("fdiv+add", chains32<3>, d32, 2000, 1e-7f, blocks, threads, 1);
   timed("fsqrt+add", chains32<4>, d32, 2000, 1e-7f, blocks, threads, 1);
+  for (int lanes : {32, 16, 8, 1}) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    chains64_lanes<<<blocks, threads>>>(d64, 2000, 0.999999, lanes);  // warm-up
+    cudaEventRecord(e0);
+    chains64_lanes<<<blocks, threads>>>(d64, 2000, 0.999999, lanes);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double warp_ops = (double)blocks * threads / 32.0 * 2000 * NCH;
+    printf("dfma, %2d active lanes per warp: %8.3f ms  %8.2f G warp-instructions/s  %7.3f TFLOP/s of active lanes\n",
+           lanes, ms, warp_ops / ms / 1e6, warp_ops * lanes * 2 / ms / 1e9);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
   const cudaError_t e = cudaGetLastError();
   printf("status %s\n", cudaGetErrorString(e));
   cudaFree(d64);

@@ -168,8 +168,21 @@ cudaError_t collect_timing(grmhd_ctx* c) {
 
 constexpr int kMinTile = 128;
 
+// Units per work item of a phase: `tile` faces / edges / cells; for the run units of the cell-centric
+// WENO fluxes (FLUX_RUN faces each) tile / FLUX_RUN of them, at least 128 so that a CTA is filled.
+// The x units of the WENO fluxes are lanes of whole warps: their items hold a multiple of 32 of them.
+int phase_tile(const DevParams& p, int tile, int phase) {
+  if ((phase == 1 || phase == 2) && p.recon == RECON_WENO5Z) {
+    const int t = tile / FLUX_RUN;
+    return t < 128 ? 128 : t;
+  }
+  if (phase == 0 && p.recon == RECON_WENO5Z) return (tile + 31) / 32 * 32;
+  return tile;
+}
+
 long long block_items(const DevParams& p, int tile, int phase) {
   long long n;
+  tile = phase_tile(p, tile, phase);
   if (phase < 3) {
     n = flux_units(p, phase);
   } else if (phase == 3) {
@@ -194,12 +207,13 @@ std::vector<WorkItem> build_items(const std::vector<BlockDesc>& blocks, int tile
         n = p.isize;
       }
       const int list = phase < 3 ? 0 : phase - 2;
-      for (long long s = 0; s < n; s += tile) {
+      const int pt = phase_tile(p, tile, phase);
+      for (long long s = 0; s < n; s += pt) {
         WorkItem w;
         w.block = b;
         w.phase = phase;
         w.start = s;
-        w.count = (int)std::min<long long>(tile, n - s);
+        w.count = (int)std::min<long long>(pt, n - s);
         w.pad = 0;
         v[list].push_back(w);
       }

@@ -450,7 +450,16 @@ __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
 // reconstructed once per direction). The transverse positions span [-1, n] in both directions.
 constexpr int FLUX_RUN = 16;
 
+// Direction x (d = 0) is cell-centric per warp instead: the 32 lanes of a warp take 32 consecutive cells
+// of one row (x-coalesced loads and stores) and produce the 31 faces between them, the plus side of the
+// previous cell passed by a lane shuffle; a row holds whole warps (FLUX_WARP_FACES faces each).
+constexpr int FLUX_WARP_FACES = 31;
+
 __host__ __device__ __forceinline__ long long flux_units(const DevParams& p, int d) {
+  if (p.recon == RECON_WENO5Z && d == 0) {
+    const long long rows = (long long)(p.ny + 2) * (p.nz + 2);
+    return rows * ((p.nx + FLUX_WARP_FACES) / FLUX_WARP_FACES) * 32;  // faces 0..nx per row
+  }
   if (p.recon == RECON_WENO5Z) {
     const int nd = d == 0 ? p.nx : (d == 1 ? p.ny : p.nz);
     const int na = d == 0 ? p.ny : p.nx, nb = d == 2 ? p.ny : p.nz;

@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
   if (track_speed) block_max_to<R>(cm_local, ms + d);
 }
 
-// Cell-centric fluxes of direction d for WENO5-Z-AOAH, unit t of flux_units: one transverse position and
-// a run of FLUX_RUN faces along d. A sliding window of five cells per variable is loaded once per cell;
+// Cell-centric fluxes of direction d = 1, 2 for WENO5-Z-AOAH, unit t of flux_units: one transverse
+// position and a run of FLUX_RUN faces along d. A sliding window of five cells per variable is loaded once per cell;
 // each cell is reconstructed once (both of its faces), and face f pairs the plus side of cell f - 1 with
 // the minus side of cell f (face_flux, as in the face-centric flux_face). Returns max |lambda| over the
 // run's interior faces.
@@ -214,6 +214,46 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   return cm_run;
 }
 
+// Cell-centric x fluxes for WENO5-Z-AOAH, unit t of flux_units(p, 0): lane l of a warp reconstructs cell
+// c = 31 w - 1 + l of its row (both faces) and, for l >= 1, evaluates face c (between cells c - 1 and c)
+// with the plus side of cell c - 1 from lane l - 1. Units come in whole, aligned warps (every lane of the
+// warp takes part in the shuffles). Returns max |lambda| of the lane's face when interior, 0 otherwise.
+template <class R, class T, int METRIC>
+__device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__ P, R* __restrict__ F,
+                                       long long t) {
+  const int lane = (int)(t & 31);
+  const int wpr = (p.nx + FLUX_WARP_FACES) / FLUX_WARP_FACES;  // warps per row
+  const long long wr = t >> 5;
+  const long long row = wr / wpr;
+  const int c = (int)(wr % wpr) * FLUX_WARP_FACES - 1 + lane;
+  const int j = (int)(row % (p.ny + 2)) - 1, k = (int)(row / (p.ny + 2)) - 1;
+  const bool live = c <= p.nx;  // cells -1..nx take part (the face of cell c exists for c in 0..nx)
+  const R eps = R(p.weno_eps);
+  const long long g = gidx(p, live ? c : p.nx, j, k);
+  R qm[NV], qp[NV], cc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const T* Pq = P + q * p.gsize + g;
+    R f[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) f[s] = live ? R(Pq[s - 2]) : R(0);
+    recon_cell<R, RECON_WENO5Z>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
+    cc[q] = f[2];
+  }
+  R PL[NV], cL[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    PL[q] = __shfl_up_sync(0xffffffffu, qp[q], 1);
+    cL[q] = __shfl_up_sync(0xffffffffu, cc[q], 1);
+  }
+  if (lane == 0 || !live) return R(0);
+  R Fh[NV];
+  const R cm = face_flux<R, METRIC>(p, 0, c, j, k, PL, qm, cL, cc, Fh);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
+  return (j >= 0 && j < p.ny && k >= 0 && k < p.nz) ? cm : R(0);
+}
+
 template <class R, class T, int METRIC>
 __global__ void __launch_bounds__(128) k_flux_cc(const T* __restrict__ P, R* __restrict__ F,
                                                  unsigned long long* __restrict__ ms, DevParams p, int d,
@@ -222,7 +262,7 @@ __global__ void __launch_bounds__(128) k_flux_cc(const T* __restrict__ P, R* __r
   R cm_local = R(0);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const R cm = flux_run<R, T, METRIC>(p, P, F, d, t);
+    const R cm = d == 0 ? flux_lane<R, T, METRIC>(p, P, F, t) : flux_run<R, T, METRIC>(p, P, F, d, t);
     if (cm > cm_local) cm_local = cm;
   }
   if (track_speed) block_max_to<R>(cm_local, ms + d);
@@ -668,9 +708,11 @@ __global__ void __launch_bounds__(128) k_batch_flux(const BlockDesc* __restrict_
     const R idx = R(b.p.idx[w.phase]);
     for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
       // units of flux_units: runs of faces for WENO5-Z-AOAH (cell-centric), single faces otherwise
-      const R cm = (RECON == RECON_WENO5Z
-                        ? flux_run<R, T, METRIC>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k)
-                        : flux_face<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k)) *
+      const R cm = (RECON != RECON_WENO5Z
+                        ? flux_face<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k)
+                        : (w.phase == 0 ? flux_lane<R, T, METRIC>(b.p, (const T*)b.P, (R*)b.F[0], w.start + k)
+                                        : flux_run<R, T, METRIC>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase,
+                                                                 w.start + k))) *
                    idx;
       if (cm > cm_local) cm_local = cm;
     }

@@ -26,6 +26,7 @@ struct grmhd_ctx {
   void* E;
   uint8_t* status;
   int* worklist;             // mixed form: deferred con2prim cells (NULL in the FP64 form)
+  double* wl_mu;             // mixed form: the double iterate each deferred cell resumes from
   int* floorlist;            // cells whose hydro state is re-derived after floors
   unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats, [16] worklist count,
                              // [17] floor-list count, [20..23] batch work counters
@@ -60,7 +61,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t P, U[3], F[3], E, status, worklist, floorlist, geo, scal, total;
+  size_t P, U[3], F[3], E, status, worklist, wl_mu, floorlist, geo, scal, total;
 };
 
 bool valid_params(const grmhd_params* p, char* msg, size_t n) {
@@ -103,7 +104,10 @@ Layout layout_of(const grmhd_params* p) {
     for (int d = 0; d < 3; ++d) l.F[d] = take(8 * G * pb);
     l.E = take(3 * G * pb);
     l.status = take(I);
-    if (p->precision == GRMHD_MIXED) l.worklist = take(I * sizeof(int));
+    if (p->precision == GRMHD_MIXED) {
+      l.worklist = take(I * sizeof(int));
+      l.wl_mu = take(I * sizeof(double));
+    }
     l.floorlist = take(I * sizeof(int));
     if (p->metric == GRMHD_KERR_SCHILD) l.geo = take(NGEO * I * sizeof(double));
   }
@@ -228,7 +232,7 @@ std::vector<WorkItem> build_items(const std::vector<BlockDesc>& blocks, int tile
 }
 
 struct BatchLayout {
-  size_t scal, blocks, items, worklist, floorlist, total;
+  size_t scal, blocks, items, worklist, wl_mu, floorlist, total;
   std::vector<size_t> P, U, F, E, status, geo;  // per block; U and F hold 3 consecutive regions
 };
 
@@ -273,6 +277,7 @@ BatchLayout batch_layout(const grmhd_params* p, int nblocks, const grmhd_block* 
     l.geo.push_back(p->metric == GRMHD_KERR_SCHILD ? take(NGEO * I * sizeof(double)) : 0);
   }
   l.worklist = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(int)) : 0;
+  l.wl_mu = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(double)) : 0;
   l.floorlist = take((size_t)cells * sizeof(int));
   l.total = off;
   return l;
@@ -327,6 +332,7 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
     c->E = c->ws + l.E;
     c->status = (uint8_t*)(c->ws + l.status);
     c->worklist = p->precision == GRMHD_MIXED ? (int*)(c->ws + l.worklist) : nullptr;
+    c->wl_mu = p->precision == GRMHD_MIXED ? (double*)(c->ws + l.wl_mu) : nullptr;
     c->floorlist = (int*)(c->ws + l.floorlist);
     if (p->metric == GRMHD_KERR_SCHILD) c->dp.geo = (const double*)(c->ws + l.geo);
   }
@@ -462,6 +468,7 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   a.use_dev_dt = auto_dt ? 1 : 0;
   a.worklist = c->worklist;
   a.wl_count = (unsigned int*)(c->scal + 16);
+  a.wl_mu = c->wl_mu;
   a.floorlist = c->floorlist;
   a.fl_count = (unsigned int*)(c->scal + 17);
   CK(L.update(c->dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
@@ -538,6 +545,7 @@ static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double d
   a.stats = c->scal + 8;
   a.worklist = c->worklist;
   a.wl_count = (unsigned int*)(c->scal + 16);
+  a.wl_mu = c->wl_mu;
   a.floorlist = c->floorlist;
   a.fl_count = (unsigned int*)(c->scal + 17);
   if (c->use_graph) {
@@ -710,6 +718,7 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   c->dblocks = (BlockDesc*)(c->ws + l.blocks);
   c->ditems = (WorkItem*)(c->ws + l.items);
   c->worklist = p->precision == GRMHD_MIXED ? (int*)(c->ws + l.worklist) : nullptr;
+  c->wl_mu = p->precision == GRMHD_MIXED ? (double*)(c->ws + l.wl_mu) : nullptr;
   c->floorlist = (int*)(c->ws + l.floorlist);
   c->hblocks.resize(nblocks);
   long long off = 0;

@@ -52,6 +52,7 @@ struct StageArgs {
   int use_dev_dt;
   int* worklist;                 // mixed form: cells whose float con2prim phase did not settle
   unsigned int* wl_count;        // number of entries in worklist
+  double* wl_mu;                 // per worklist entry: the double iterate to resume from (0: none)
   int* floorlist;                // cells whose floors / status re-derive U in a compacted pass (NULL: inline)
   unsigned int* fl_count;        // number of entries in floorlist
 };
@@ -95,6 +96,7 @@ struct BatchArgs {
   unsigned long long* stats;
   int* worklist;
   unsigned int* wl_count;
+  double* wl_mu;
   int* floorlist;
   unsigned int* fl_count;
 };
@@ -723,13 +725,61 @@ __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, 
   return st;
 }
 
+// One double Newton step of the master function from mue, accepted when it is smaller than 1e-6 mue
+// (its error is then of order step^2) and stays below the float bracket end (with margin): on success
+// returns true with the root mu and the intermediates there, to first order in the step.
+__device__ __forceinline__ bool c2p_accept_step(const C2PIn<double>& c, const C2PEval<double>& e, double mue,
+                                                float mupf, double& mu, C2PEval<double>& ev) {
+  const double step = -e.f / e.df;
+  const double nmu = mue + step;
+  mu = nmu;
+  if (!(e.df > 0.0 && nmu > 0.0 && fabs(step) <= 1e-6 * nmu && nmu <= (double)mupf * (1.0 + 1e-5))) return false;
+  ev = e;
+  ev.x += e.dx * step;
+  ev.W += e.dW * step;
+  ev.rho += e.drho * step;
+  ev.eps = fmax(e.eps + e.deps * step, 0.0);
+  return true;
+}
+
+// The double pass of a deferred cell: from the double iterate mu_r of the first pass (when it has one),
+// one more evaluation and the same acceptance as the first pass; otherwise the full double con2prim.
+template <class R>
+__device__ __forceinline__ int con2prim_resume(const DevParams& p, const Metric<R>& m, const double Uc[NV],
+                                               double mu_guess, double mu_r, double Pout[NV], int& iters) {
+  iters = 0;
+  if (mu_r > 0.0) {
+    C2PIn<double> c;
+    double ru[3], bu[3];
+    if (c2p_setup<R>(p, m, Uc, c, ru, bu) == 0) {
+      C2PIn<float> cf;
+      cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
+      cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
+      const float mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
+      const C2PEval<double> e = c2p_master(c, mu_r);
+      iters = 1;
+      double mu;
+      C2PEval<double> ev;
+      if (c2p_accept_step(c, e, mu_r, mupf, mu, ev)) {
+        c2p_output_eval(c, ev, mu, ru, bu, Uc, Pout);
+        return 0;
+      }
+    }
+  }
+  int it2 = 0;
+  const int st = con2prim<R>(p, m, Uc, mu_guess, Pout, it2, true);
+  iters += it2;
+  return st;
+}
+
 // Mixed-form con2prim: the same root, iterated in float to a relative step of 2e-6, then one double
 // Newton step; double iteration only when the float phase fails or the double step is not small.
 enum { C2P_DEFERRED = 256 };  // returned by con2prim_mixed(defer = true): the cell needs the double iteration
 
 template <class R>
 __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R>& m, const double Uc[NV],
-                                              double mu_guess, double Pout[NV], int& iters, bool defer = false) {
+                                              double mu_guess, double Pout[NV], int& iters, bool defer = false,
+                                              double* defer_mu = nullptr) {
   // Lanes entering together; each of them reaches the __syncwarp below exactly once (no return before it).
   const unsigned lanes = __activemask();
   iters = 0;
@@ -775,19 +825,13 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
       ev = e;
       done = true;
     } else {
-      const double step = -e.f / e.df;
-      const double nmu = mue + step;
-      if (e.df > 0.0 && nmu > 0.0 && fabs(step) <= 1e-6 * nmu && nmu <= (double)mupf * (1.0 + 1e-5)) {
-        // the intermediates at the root to first order in the step (the neglected term is O(step^2),
-        // ~1e-12 relative): no second evaluation of the master function
-        mu = nmu;
-        ev = e;
-        ev.x += e.dx * step;
-        ev.W += e.dW * step;
-        ev.rho += e.drho * step;
-        ev.eps = fmax(e.eps + e.deps * step, 0.0);
-        done = true;
-      }
+      // the intermediates at the root to first order in the step (the neglected term is O(step^2),
+      // ~1e-12 relative): no second evaluation of the master function
+      double nmu;
+      done = c2p_accept_step(c, e, mue, mupf, nmu, ev);
+      mu = nmu;
+      if (!done && defer_mu && isfinite(nmu) && nmu > 0.0 && nmu < (double)mupf * (1.0 + 1e-3))
+        *defer_mu = nmu;  // the double pass resumes from this iterate
     }
   }
   int st = 0;

@@ -548,13 +548,16 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   const double mu0 = (double)mu_of_prims<R>(Pr, mr.gam, R(p.gamma_eos));
   double Pn[NV];
   int iters;
-  int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters, a.worklist != nullptr)
+  double mu_r = 0.0;  // the double iterate a deferred cell resumes from
+  int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters, a.worklist != nullptr, &mu_r)
                           : con2prim<double>(p, m, Uc, mu0, Pn, iters);
   if (st == C2P_DEFERRED) {
     // finished by deferred_cell: keep P (the warm start), store the new conserved state
 #pragma unroll
     for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
-    a.worklist[atomicAdd(a.wl_count, 1u)] = (int)(wl_tag + t);
+    const unsigned int slot = atomicAdd(a.wl_count, 1u);
+    a.worklist[slot] = (int)(wl_tag + t);
+    a.wl_mu[slot] = mu_r;
     cs.it_sum += iters;
     return;
   }
@@ -590,11 +593,12 @@ __global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __re
   cs.flush(a.stats);
 }
 
-// Mixed form, second pass for cell t: the full double con2prim of a cell whose float phase did not
-// settle (grouped so that a warp's lanes do the same work). Unew holds its conserved state.
+// Mixed form, second pass for cell t: the double con2prim of a cell whose first pass did not settle,
+// resumed from that pass's double iterate mu_r when it has one (grouped so that a warp's lanes do the
+// same work). Unew holds its conserved state.
 template <int METRIC, class T>
 __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict__ P, const StageArgs& a, long long t,
-                                              CellStats& cs) {
+                                              double mu_r, CellStats& cs) {
   const long long n = p.isize, G = p.gsize;
   const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
   const long long g = gidx(p, i, j, k);
@@ -613,7 +617,7 @@ __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict_
   const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
   double Pn[NV];
   int iters;
-  int st = con2prim<double>(p, m, Uc, mu0, Pn, iters, true);
+  int st = con2prim_resume<double>(p, m, Uc, mu0, mu_r, Pn, iters);
   st |= apply_floors_fr(p, m.gam, fr, Pn);
   if (st) {
     double U5[5];
@@ -658,7 +662,7 @@ __global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, Stag
   const unsigned int cnt = *a.wl_count;
   CellStats cs;
   for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x)
-    deferred_cell<METRIC, T>(p, P, a, a.worklist[w], cs);
+    deferred_cell<METRIC, T>(p, P, a, a.worklist[w], a.wl_mu[w], cs);
   cs.flush(a.stats);
   if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
 }
@@ -689,6 +693,7 @@ __device__ __forceinline__ StageArgs block_stage_args(const BlockDesc& b, const 
   s.use_dev_dt = a.use_dev_dt;
   s.worklist = a.worklist;
   s.wl_count = a.wl_count;
+  s.wl_mu = a.wl_mu;
   s.floorlist = a.floorlist;
   s.fl_count = a.fl_count;
   return s;
@@ -768,7 +773,7 @@ __global__ void __launch_bounds__(128) k_batch_deferred(const BlockDesc* __restr
     }
     const BlockDesc& b = blocks[lo];
     const StageArgs sa = block_stage_args(b, a);
-    deferred_cell<METRIC, T>(b.p, (T*)b.P, sa, gcell - b.cell_offset, cs);
+    deferred_cell<METRIC, T>(b.p, (T*)b.P, sa, gcell - b.cell_offset, a.wl_mu[w], cs);
   }
   cs.flush(a.stats);
   if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;

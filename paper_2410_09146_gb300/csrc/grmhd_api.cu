@@ -173,7 +173,7 @@ cudaError_t collect_timing(grmhd_ctx* c) {
 constexpr int kMinTile = 128;
 
 // Units per work item of a phase: `tile` faces / edges / cells; for the run units of the cell-centric
-// WENO fluxes (FLUX_RUN faces each) tile / FLUX_RUN of them, at least 128 so that a CTA is filled.
+// WENO fluxes (~FLUX_RUN faces each) tile / FLUX_RUN of them, at least 128 so that a CTA is filled.
 // The x units of the WENO fluxes are lanes of whole warps: their items hold a multiple of 32 of them.
 int phase_tile(const DevParams& p, int tile, int phase) {
   if ((phase == 1 || phase == 2) && p.recon == RECON_WENO5Z) {

@@ -448,24 +448,37 @@ __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
 }
 
 // Work units of the flux phase of direction d: faces (face-centric reconstructions), or, for
-// WENO5-Z-AOAH, (transverse position, run of FLUX_RUN faces along d) pairs (cell-centric: each cell
+// WENO5-Z-AOAH, (transverse position, run of ~FLUX_RUN faces along d) pairs (cell-centric: each cell
 // reconstructed once per direction). The transverse positions span [-1, n] in both directions.
 constexpr int FLUX_RUN = 16;
 
-// Direction x (d = 0) is cell-centric per warp instead: the 32 lanes of a warp take 32 consecutive cells
-// of one row (x-coalesced loads and stores) and produce the 31 faces between them, the plus side of the
-// previous cell passed by a lane shuffle; a row holds whole warps (FLUX_WARP_FACES faces each).
+// Runs per column of nd + 1 faces (nd + 1 >= FLUX_RUN: runs of FLUX_RUN to 2 FLUX_RUN - 1 faces) and their
+// common length (the last run takes the remainder).
+__host__ __device__ __forceinline__ int flux_runs(int nd) {
+  const int r = (nd + 1) / FLUX_RUN;
+  return r > 0 ? r : 1;
+}
+__host__ __device__ __forceinline__ int flux_run_length(int nd) {
+  const int r = flux_runs(nd);
+  return (nd + 1 + r - 1) / r;
+}
+
+// Direction x (d = 0) is cell-centric per warp instead: the x rows of cells -1..nx are laid end to end,
+// and warp w takes the 32 consecutive cells 31 w - 1 .. 31 w + 30 of that sequence (x-coalesced loads and
+// stores). A lane whose cell is not the first of its row evaluates the face below its cell with the plus
+// side of the previous cell passed by a lane shuffle; lane 0 only supplies that side (its face belongs to
+// the previous warp). The units are whole warps.
 constexpr int FLUX_WARP_FACES = 31;
 
 __host__ __device__ __forceinline__ long long flux_units(const DevParams& p, int d) {
   if (p.recon == RECON_WENO5Z && d == 0) {
-    const long long rows = (long long)(p.ny + 2) * (p.nz + 2);
-    return rows * ((p.nx + FLUX_WARP_FACES) / FLUX_WARP_FACES) * 32;  // faces 0..nx per row
+    const long long cells = (long long)(p.ny + 2) * (p.nz + 2) * (p.nx + 2);
+    return (cells + FLUX_WARP_FACES - 1) / FLUX_WARP_FACES * 32;
   }
   if (p.recon == RECON_WENO5Z) {
     const int nd = d == 0 ? p.nx : (d == 1 ? p.ny : p.nz);
     const int na = d == 0 ? p.ny : p.nx, nb = d == 2 ? p.ny : p.nz;
-    return (long long)(na + 2) * (nb + 2) * ((nd + FLUX_RUN) / FLUX_RUN);
+    return (long long)(na + 2) * (nb + 2) * flux_runs(nd);
   }
   int ex, ey;
   return face_box(p, d, ex, ey);

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
 }
 
 // Cell-centric fluxes of direction d = 1, 2 for WENO5-Z-AOAH, unit t of flux_units: one transverse
-// position and a run of FLUX_RUN faces along d. A sliding window of five cells per variable is loaded once per cell;
+// position and a run of flux_run_length faces along d. A sliding window of five cells per variable is loaded once per cell;
 // each cell is reconstructed once (both of its faces), and face f pairs the plus side of cell f - 1 with
 // the minus side of cell f (face_flux, as in the face-centric flux_face). Returns max |lambda| over the
 // run's interior faces.
@@ -161,8 +161,9 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   const int a = (int)(t % (na + 2)) - 1;
   const long long rest = t / (na + 2);
   const int b = (int)(rest % (nb + 2)) - 1;
-  const int f0 = (int)(rest / (nb + 2)) * FLUX_RUN;
-  const int f1 = min(f0 + FLUX_RUN, nd + 1);
+  const int run = flux_run_length(nd);
+  const int f0 = (int)(rest / (nb + 2)) * run;
+  const int f1 = min(f0 + run, nd + 1);
   int i = d == 0 ? f0 : a;
   int j = d == 1 ? f0 : (d == 0 ? a : b);
   int k = d == 2 ? f0 : b;
@@ -214,22 +215,23 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   return cm_run;
 }
 
-// Cell-centric x fluxes for WENO5-Z-AOAH, unit t of flux_units(p, 0): lane l of a warp reconstructs cell
-// c = 31 w - 1 + l of its row (both faces) and, for l >= 1, evaluates face c (between cells c - 1 and c)
-// with the plus side of cell c - 1 from lane l - 1. Units come in whole, aligned warps (every lane of the
-// warp takes part in the shuffles). Returns max |lambda| of the lane's face when interior, 0 otherwise.
+// Cell-centric x fluxes for WENO5-Z-AOAH, unit t of flux_units(p, 0): lane l of warp w reconstructs cell
+// s = 31 w - 1 + l of the sequence of x rows (cells -1..nx of each row, end to end) and, when l >= 1 and
+// the cell is not the first of its row, evaluates the face between it and the previous cell with that
+// cell's plus side from lane l - 1. Units come in whole, aligned warps (every lane of the warp takes part in
+// the shuffles). Returns max |lambda| of the lane's face when interior, 0 otherwise.
 template <class R, class T, int METRIC>
 __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__ P, R* __restrict__ F,
                                        long long t) {
   const int lane = (int)(t & 31);
-  const int wpr = (p.nx + FLUX_WARP_FACES) / FLUX_WARP_FACES;  // warps per row
-  const long long wr = t >> 5;
-  const long long row = wr / wpr;
-  const int c = (int)(wr % wpr) * FLUX_WARP_FACES - 1 + lane;
+  const long long seq = (t >> 5) * FLUX_WARP_FACES - 1 + lane;
+  const long long ncell = (long long)(p.ny + 2) * (p.nz + 2) * (p.nx + 2);
+  const bool live = seq >= 0 && seq < ncell;
+  const long long row = live ? seq / (p.nx + 2) : 0;
+  const int c = live ? (int)(seq % (p.nx + 2)) - 1 : 0;
   const int j = (int)(row % (p.ny + 2)) - 1, k = (int)(row / (p.ny + 2)) - 1;
-  const bool live = c <= p.nx;  // cells -1..nx take part (the face of cell c exists for c in 0..nx)
   const R eps = R(p.weno_eps);
-  const long long g = gidx(p, live ? c : p.nx, j, k);
+  const long long g = gidx(p, c, j, k);
   R qm[NV], qp[NV], cc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
@@ -246,7 +248,7 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
     PL[q] = __shfl_up_sync(0xffffffffu, qp[q], 1);
     cL[q] = __shfl_up_sync(0xffffffffu, cc[q], 1);
   }
-  if (lane == 0 || !live) return R(0);
+  if (lane == 0 || !live || c < 0) return R(0);
   R Fh[NV];
   const R cm = face_flux<R, METRIC>(p, 0, c, j, k, PL, qm, cL, cc, Fh);
 #pragma unroll

@@ -446,18 +446,18 @@ def run_batched(G, I, steps, warmup, rank):
 
 
 # Work and traffic per unit of the mixed-form kernels, measured by ncu (--set full) on the 96^3
-# Kerr-Schild random block (profiles/k_update_k_flux_kerr_schild_96_mixed.md): double-precision flops
-# (DADD + DMUL + 2 DFMA, active lanes) per cell of k_update, float flops (FADD + FMUL + 2 FFMA) per face
-# of k_flux, DRAM bytes (read + write) per unit.
-UPDATE_FP64_FLOP_PER_CELL = 457.2
-UPDATE_DRAM_BYTES_PER_CELL = 438.9
+# Kerr-Schild random block (summary under profiles/): double-precision flops (DADD + DMUL + 2 DFMA,
+# active lanes) per cell of k_update, float flops (FADD + FMUL + 2 FFMA) per face of k_flux_cc (mean of
+# the three directions), DRAM bytes (read + write) per unit.
+UPDATE_FP64_FLOP_PER_CELL = 466.5
+UPDATE_DRAM_BYTES_PER_CELL = 373.5
 # algorithmic bytes per cell of k_update: P (8 float) + Ucur (8 double) + U0 (8 double, stages with
 # g0 != 0) + 3 x 8 face fluxes (float) + 3 EMFs (float) + 19 doubles of cached geometry read; Unew
 # (8 double) + P (8 float) + status written; the average over the two stages of an RK2 step
 UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 152 + 64 + 32 + 1
-FLUX_FP32_FLOP_PER_FACE = 4563.0
-FLUX_DRAM_BYTES_PER_FACE = 41.2
-FP64_PEAK_TFLOPS = 1.008   # measured DFMA rate (profiles/fp_throughput_gb300.md)
+FLUX_FP32_FLOP_PER_FACE = 2342.0
+FLUX_DRAM_BYTES_PER_FACE = 38.5
+FP64_PEAK_TFLOPS = 1.008   # measured DFMA rate of this GB300 (probe_fp_throughput.cu, summary under profiles/)
 FP32_PEAK_TFLOPS = 74.5    # measured FFMA rate
 
 
@@ -479,7 +479,7 @@ def roofline(dom, ms, n, s, stats, peaks):
     faces = 3 * (n + 1) * (n + 2) ** 2 / 3.0
     flops = FLUX_FP32_FLOP_PER_FACE * faces
     achieved = flops / (ms / 1e3) / 1e12
-    return {"kernel": f"k_flux ({dom})", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+    return {"kernel": f"k_flux_cc ({dom})", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
             "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": FLUX_DRAM_BYTES_PER_FACE * faces,
             "ms_per_launch": ms, "note": "FP32 pipe; peak = measured FFMA rate"}
 

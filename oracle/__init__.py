@@ -83,6 +83,8 @@ def _load():
         lib.orc_ghost_fill.argtypes = [P, dp]
         lib.orc_stage.argtypes = [P, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, dp, dp, ip, dp, dp]
+        lib.orc_stage_face_ct.argtypes = lib.orc_stage.argtypes + [dp, dp, dp]
+        lib.orc_face_b_to_cells.argtypes = [P, dp, dp]
         _lib = lib
     return _lib
 
@@ -234,3 +236,63 @@ def rk2_step(p: OrcParams, P, U, dt: float = 0.0):
     s1 = stage(p, P, None, U, 0.0, 1.0, 1.0, dt)
     s2 = stage(p, P, U, s1["U"], 0.5, 0.5, 0.5, s1["dt"])
     return s2["U"], s2["status"] | s1["status"], s1["dt"]
+
+
+def face_b_to_cells(p: OrcParams, Bf, P):
+    """Cell-centred B of ``P`` from the face field ``Bf`` [3][gz][gy][gx] (densitized sqrt(gamma) B^d on the
+    lower d-face of each ghosted cell): B^d = mean of the cell's two d-faces / sqrt(gamma), for every cell
+    whose two d-faces are stored. Periodic blocks get their ghost faces filled first (``Bf`` in place)."""
+    assert P.dtype == np.float64 and P.flags.c_contiguous
+    assert Bf.dtype == np.float64 and Bf.flags.c_contiguous and Bf.shape == (3,) + P.shape[1:]
+    _load().orc_face_b_to_cells(ctypes.byref(p), _dp(Bf), _dp(P))
+    return P
+
+
+def stage_face_ct(p: OrcParams, P, Bf0, Bf, U0, Ucur, g0: float, g1: float, beta: float, dt: float,
+                  debug: bool = False):
+    """One RK stage with face-centred upwind CT. ``P`` is updated in place; ``Bf`` (this stage's faces)
+    gets its ghost faces filled when periodic. Returns dict(U, Bf (new faces), status, dt, maxspeed,
+    iters[, F, E])."""
+    assert P.dtype == np.float64 and P.flags.c_contiguous
+    assert Bf.dtype == np.float64 and Bf.flags.c_contiguous and Bf.shape == (3,) + P.shape[1:]
+    Ucur = np.ascontiguousarray(Ucur, dtype=np.float64)
+    U0 = None if U0 is None else np.ascontiguousarray(U0, dtype=np.float64)
+    Bf0 = None if Bf0 is None else np.ascontiguousarray(Bf0, dtype=np.float64)
+    Unew = np.zeros_like(Ucur)
+    Bfn = np.zeros_like(Bf)
+    st = np.zeros(Ucur.shape[1:], np.uint8)
+    dt_used = ctypes.c_double(0.0)
+    ms = np.zeros(3)
+    it = ctypes.c_int(0)
+    F = np.zeros((3, 8) + P.shape[1:]) if debug else None
+    E = np.zeros((3,) + P.shape[1:]) if debug else None
+    rc = _load().orc_stage_face_ct(ctypes.byref(p), _dp(P), _dp(U0), _dp(Ucur), _dp(Unew),
+                                   st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), g0, g1, beta, dt,
+                                   ctypes.byref(dt_used), _dp(ms), ctypes.byref(it), _dp(F), _dp(E),
+                                   _dp(Bf0), _dp(Bf), _dp(Bfn))
+    assert rc == 0
+    out = {"U": Unew, "Bf": Bfn, "status": st, "dt": dt_used.value, "maxspeed": ms, "iters": it.value}
+    if debug:
+        out["F"], out["E"] = F, E
+    return out
+
+
+def rk2_step_face_ct(p: OrcParams, P, Bf, U, dt: float = 0.0):
+    """SSP-RK2 step with face-centred upwind CT (stage coefficients as ``rk2_step``).
+    Returns (U, Bf, status, dt)."""
+    s1 = stage_face_ct(p, P, None, Bf, None, U, 0.0, 1.0, 1.0, dt)
+    s2 = stage_face_ct(p, P, Bf, s1["Bf"], U, s1["U"], 0.5, 0.5, 0.5, s1["dt"])
+    return s2["U"], s2["Bf"], s2["status"] | s1["status"], s1["dt"]
+
+
+def face_divergence(p: OrcParams, Bf):
+    """Face divergence sum_d (Bf_d(upper) - Bf_d(lower)) / dx_d of every interior cell, [nz][ny][nx]."""
+    ng = p.ng
+    nx, ny, nz = p.nx, p.ny, p.nz
+    sl = (slice(ng, ng + nz), slice(ng, ng + ny), slice(ng, ng + nx))
+    out = np.zeros((nz, ny, nx))
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        up = list(sl)
+        up[ax] = slice(sl[ax].start + 1, sl[ax].stop + 1)
+        out += (Bf[d][tuple(up)] - Bf[d][sl]) / p.dx[d]
+    return out

@@ -15,6 +15,8 @@
 //   Sec. 3.1  second-order FV, Toth flux-CT on cell-centred B, LLF / HLL,
 //             constant / PLM (minmod, MC) / WENO5-Z-AOAH reconstruction,
 //             Kastaun et al. (2021) con2prim
+//   Sec. 5    face-centred constrained transport (named there as planned work; the
+//             scheme is the upwind CT of Gardiner & Stone 2005, see stage_impl)
 //   Sec. 3.2  density / specific-energy floors rho0 r^-alpha
 //   App. B    WENO5-Z-AOAH
 // Readings where the paper is silent are stated at the routine that takes them.
@@ -23,6 +25,8 @@
 //   P  [8][ngz][ngy][ngx]  primitives rho, W v^1..3, rho*eps, B^1..3 incl. ghosts
 //   U  [8][nz][ny][nx]     densitized conserved sqrt(gamma)*(D,S_1..3,tau,B^1..3)
 //   status [nz][ny][nx]    uint8 bit set (ORC_ST_*)
+//   Bf [3][ngz][ngy][ngx]  face-centred densitized field sqrt(gamma) B^d; entry (i,j,k) of component d
+//                          is the lower d-face of ghosted cell (i,j,k)
 
 #include <cmath>
 #include <cstdint>
@@ -633,6 +637,25 @@ static void ghost_fill_periodic(const Grid& g, double* P) {
       }
 }
 
+// Periodic fill of the face arrays: every face outside [0, N_d) along its normal d or outside the
+// interior along the other two directions copies its wrapped face (face N_d wraps to face 0, which the
+// CT update leaves equal to it anyway).
+static void ghost_fill_faces_periodic(const Grid& g, double* Bf) {
+  const long n = g.gsize();
+  const int N[3] = {g.nx, g.ny, g.nz};
+  for (int d = 0; d < 3; ++d)
+    for (int k = -g.ng; k < g.nz + g.ng; ++k)
+      for (int j = -g.ng; j < g.ny + g.ng; ++j)
+        for (int i = -g.ng; i < g.nx + g.ng; ++i) {
+          const int c[3] = {i, j, k};
+          bool canonical = true;
+          for (int e = 0; e < 3; ++e)
+            if (c[e] < 0 || c[e] >= N[e]) canonical = false;
+          if (canonical) continue;
+          Bf[d * n + g.gi(i, j, k)] = Bf[d * n + g.gi(wrap(i, g.nx), wrap(j, g.ny), wrap(k, g.nz))];
+        }
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -801,19 +824,40 @@ int orc_ghost_fill(const orc_params* p, double* P) {
   return 0;
 }
 
-// One RK stage:
+}  // extern "C"
+
+namespace {
+
+// One RK stage (both constrained-transport flavours):
 //   Unew = g0 U0 + g1 Ucur + beta dt L(P),  L = -sum_d dF^d/dx^d + sqrt(-g) S with CT for B,
 // followed by con2prim + floors writing the interior of P (ghosts are filled first when periodic).
 // dt <= 0 selects dt = cfl / max_d(max |lambda| / dx_d) over the interior faces of this stage.
-// Outputs: Unew, P (updated in place), status, *dt_used, maxspeed[3] (max |lambda| per direction).
-// Optional debug outputs (may be NULL): Fx/Fy/Fz [8][gsize] face fluxes, Ex/Ey/Ez [gsize] edge EMFs.
-int orc_stage(const orc_params* p, double* P, const double* U0, const double* Ucur, double* Unew, uint8_t* status,
-              double g0, double g1, double beta, double dt, double* dt_used, double* maxspeed, int* iters_total,
-              double* Fdbg, double* Edbg) {
+//
+// Bfcur == NULL: Toth flux-CT on the cell-centred field (Sec. 3.1), B evolved in U.
+// Bfcur != NULL: face-centred upwind CT (Sec. 5 names face-centred CT as planned work and gives no
+// scheme; this is the reading taken). The face arrays carry the state of B:
+//   * the normal component of both Riemann states of a d-face is Bf_d / sqrt(gamma) at the face centre
+//     (it is continuous across the face), the tangential ones are reconstructed as before;
+//   * edge EMFs follow the upwind "contact" CT of Gardiner & Stone (2005, J. Comput. Phys. 205, 509):
+//     the mean of the four face EMFs around the edge plus, on each of the four half-faces, the
+//     difference between face and cell-centred EMF taken in the cell the face's mass flux comes from
+//     (the mean of both cells when the mass flux is zero);
+//   * faces advance by the discrete Stokes theorem, Bfnew = g0 Bf0 + g1 Bfcur + beta dt (curl), so that
+//     the face divergence sum_d (Bf_d(+) - Bf_d(-)) / dx_d does not change;
+//   * the cell-centred densitized field in Unew is the mean of the cell's two new faces of each direction.
+// With Omega_c = sqrt(gamma) (B^a v~^b - B^b v~^a) for (c, a, b) cyclic, Omega_c = F^b_{B^a} = -F^a_{B^b}.
+static int stage_impl(const orc_params* p, double* P, const double* U0, const double* Ucur, double* Unew,
+                      uint8_t* status, double g0, double g1, double beta, double dt, double* dt_used,
+                      double* maxspeed, int* iters_total, double* Fdbg, double* Edbg, const double* Bf0,
+                      double* Bfcur, double* Bfnew) {
   Grid g(*p);
   const long gn = g.gsize(), in = g.isize();
   const int N[3] = {g.nx, g.ny, g.nz};
-  if (p->bc == 0) ghost_fill_periodic(g, P);
+  const bool face_ct = Bfcur != nullptr;
+  if (p->bc == 0) {
+    ghost_fill_periodic(g, P);
+    if (face_ct) ghost_fill_faces_periodic(g, Bfcur);
+  }
 
   // a2 + a3: face fluxes. Direction d face index fd in [0, N_d]; transverse cells in [-1, N].
   std::vector<double> F(3 * 8 * gn, 0.0);
@@ -857,6 +901,11 @@ int orc_stage(const orc_params* p, double* P, const double* U0, const double* Uc
           xf[d] = g.xf(d, c[d]);
           Geom G;
           metric_eval(*p, xf[0], xf[1], xf[2], G);
+          if (face_ct) {
+            const double bn = Bfcur[d * gn + g.gi(i, j, k)] / G.sqrtgam;
+            PL[5 + d] = bn;
+            PR[5 + d] = bn;
+          }
           FaceSide L, R;
           face_side(*p, G, PL, d + 1, L);
           face_side(*p, G, PR, d + 1, R);
@@ -878,35 +927,117 @@ int orc_stage(const orc_params* p, double* P, const double* U0, const double* Uc
   }
   *dt_used = dt;
 
-  // a4: Toth flux-CT edge EMFs. Omega_k on edges along k, for (i, j, k) cyclic:
-  //   Omega_k = 1/4 (sum of the 4 F^j_{B^i} around the edge - sum of the 4 F^i_{B^j})
-  // stored at the index of the cell whose lower faces meet at the edge.
   auto Fv = [&](int d, int v, int i, int j, int k) { return F[(d * 8 + v) * gn + g.gi(i, j, k)]; };
   std::vector<double> E(3 * gn, 0.0);
-  // Omega_z(fi, fj, k): fi in [0, nx], fj in [0, ny], k in [0, nz)
-  for (int k = 0; k < g.nz; ++k)
-    for (int fj = 0; fj <= g.ny; ++fj)
-      for (int fi = 0; fi <= g.nx; ++fi)
-        E[2 * gn + g.gi(fi, fj, k)] = 0.25 * (Fv(1, 5, fi - 1, fj, k) + Fv(1, 5, fi, fj, k) -
-                                              Fv(0, 6, fi, fj - 1, k) - Fv(0, 6, fi, fj, k));
-  // Omega_x(i, fj, fk)
-  for (int fk = 0; fk <= g.nz; ++fk)
-    for (int fj = 0; fj <= g.ny; ++fj)
-      for (int i = 0; i < g.nx; ++i)
-        E[0 * gn + g.gi(i, fj, fk)] = 0.25 * (Fv(2, 6, i, fj - 1, fk) + Fv(2, 6, i, fj, fk) -
-                                              Fv(1, 7, i, fj, fk - 1) - Fv(1, 7, i, fj, fk));
-  // Omega_y(fi, j, fk)
-  for (int fk = 0; fk <= g.nz; ++fk)
-    for (int j = 0; j < g.ny; ++j)
-      for (int fi = 0; fi <= g.nx; ++fi)
-        E[1 * gn + g.gi(fi, j, fk)] = 0.25 * (Fv(0, 7, fi, j, fk - 1) + Fv(0, 7, fi, j, fk) -
-                                              Fv(2, 5, fi - 1, j, fk) - Fv(2, 5, fi, j, fk));
+  if (!face_ct) {
+    // a4: Toth flux-CT edge EMFs. Omega_k on edges along k, for (i, j, k) cyclic:
+    //   Omega_k = 1/4 (sum of the 4 F^j_{B^i} around the edge - sum of the 4 F^i_{B^j})
+    // stored at the index of the cell whose lower faces meet at the edge.
+    // Omega_z(fi, fj, k): fi in [0, nx], fj in [0, ny], k in [0, nz)
+    for (int k = 0; k < g.nz; ++k)
+      for (int fj = 0; fj <= g.ny; ++fj)
+        for (int fi = 0; fi <= g.nx; ++fi)
+          E[2 * gn + g.gi(fi, fj, k)] = 0.25 * (Fv(1, 5, fi - 1, fj, k) + Fv(1, 5, fi, fj, k) -
+                                                Fv(0, 6, fi, fj - 1, k) - Fv(0, 6, fi, fj, k));
+    // Omega_x(i, fj, fk)
+    for (int fk = 0; fk <= g.nz; ++fk)
+      for (int fj = 0; fj <= g.ny; ++fj)
+        for (int i = 0; i < g.nx; ++i)
+          E[0 * gn + g.gi(i, fj, fk)] = 0.25 * (Fv(2, 6, i, fj - 1, fk) + Fv(2, 6, i, fj, fk) -
+                                                Fv(1, 7, i, fj, fk - 1) - Fv(1, 7, i, fj, fk));
+    // Omega_y(fi, j, fk)
+    for (int fk = 0; fk <= g.nz; ++fk)
+      for (int j = 0; j < g.ny; ++j)
+        for (int fi = 0; fi <= g.nx; ++fi)
+          E[1 * gn + g.gi(fi, j, fk)] = 0.25 * (Fv(0, 7, fi, j, fk - 1) + Fv(0, 7, fi, j, fk) -
+                                                Fv(2, 5, fi - 1, j, fk) - Fv(2, 5, fi, j, fk));
+  } else {
+    // a4 (face-centred): cell-centred EMFs Omega_c = sqrt(gamma) (B^a v~^b - B^b v~^a), (c, a, b) cyclic,
+    // from the cell primitives, on cells [-1, N] of every direction.
+    std::vector<double> Ecc(3 * gn, 0.0);
+    for (int k = -1; k <= g.nz; ++k)
+      for (int j = -1; j <= g.ny; ++j)
+        for (int i = -1; i <= g.nx; ++i) {
+          Geom G;
+          metric_eval(*p, g.xc(0, i), g.xc(1, j), g.xc(2, k), G);
+          double Pc[8];
+          for (int v = 0; v < 8; ++v) Pc[v] = P[v * gn + g.gi(i, j, k)];
+          Fluid Fl;
+          fluid_from_prims(*p, G, Pc, Fl);
+          for (int c = 0; c < 3; ++c) {
+            const int a = (c + 1) % 3 + 1, b = (c + 2) % 3 + 1;  // 1-based components
+            Ecc[c * gn + g.gi(i, j, k)] = G.sqrtgam * (Fl.Bcon[a] * Fl.vt[b] - Fl.Bcon[b] * Fl.vt[a]);
+          }
+        }
+    // Edge EMF of component c at the edge between face indices (fa, fb) of its transverse directions
+    // a = c+1, b = c+2 (cyclic); (ia, ib) below are cell indices in the a-b plane, the c index is fixed.
+    for (int c = 0; c < 3; ++c) {
+      const int a = (c + 1) % 3, b = (c + 2) % 3;
+      int lo[3] = {0, 0, 0}, hi[3] = {N[0] + 1, N[1] + 1, N[2] + 1};
+      hi[c] = N[c];  // cells along c, faces along a and b
+      for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+          for (int i = lo[0]; i < hi[0]; ++i) {
+            const int e[3] = {i, j, k};
+            // index of the point with a-index ia, b-index ib and the edge's c-index
+            auto at = [&](int ia, int ib) {
+              int q[3];
+              q[c] = e[c];
+              q[a] = ia;
+              q[b] = ib;
+              return g.gi(q[0], q[1], q[2]);
+            };
+            const int fa = e[a], fb = e[b];
+            // face EMFs: a-faces (normal a) at (fa, ib) give -F^a_{B^b}; b-faces at (ia, fb) give +F^b_{B^a}
+            auto OA = [&](int ib) { return -F[(a * 8 + 5 + b) * gn + at(fa, ib)]; };
+            auto OB = [&](int ia) { return F[(b * 8 + 5 + a) * gn + at(ia, fb)]; };
+            auto Oc = [&](int ia, int ib) { return Ecc[c * gn + at(ia, ib)]; };
+            auto DA = [&](int ib) { return F[(a * 8 + 0) * gn + at(fa, ib)]; };  // mass flux through a-face
+            auto DB = [&](int ia) { return F[(b * 8 + 0) * gn + at(ia, fb)]; };
+            // each half-face term chooses its cell by the sign of that face's mass flux
+            auto pick = [](double m, double lo_cell, double hi_cell) {
+              return m > 0.0 ? lo_cell : (m < 0.0 ? hi_cell : 0.5 * (lo_cell + hi_cell));
+            };
+            // b-direction half-faces of the a-faces below (fb - 1) and above (fb) the edge
+            const double xb_lo = pick(DA(fb - 1), OB(fa - 1) - Oc(fa - 1, fb - 1), OB(fa) - Oc(fa, fb - 1));
+            const double xb_hi = pick(DA(fb), Oc(fa - 1, fb) - OB(fa - 1), Oc(fa, fb) - OB(fa));
+            // a-direction half-faces of the b-faces left (fa - 1) and right (fa) of the edge
+            const double xa_lo = pick(DB(fa - 1), OA(fb - 1) - Oc(fa - 1, fb - 1), OA(fb) - Oc(fa - 1, fb));
+            const double xa_hi = pick(DB(fa), Oc(fa, fb - 1) - OA(fb - 1), Oc(fa, fb) - OA(fb));
+            E[c * gn + g.gi(i, j, k)] = 0.25 * (OA(fb - 1) + OA(fb) + OB(fa - 1) + OB(fa)) +
+                                        0.25 * (xb_lo - xb_hi) + 0.25 * (xa_lo - xa_hi);
+          }
+    }
+    // Faces: discrete Stokes theorem on the edge EMFs. d/dt Bf_x = -dOmega_z/dy + dOmega_y/dz,
+    // d/dt Bf_y = dOmega_z/dx - dOmega_x/dz, d/dt Bf_z = -dOmega_y/dx + dOmega_x/dy.
+    std::memcpy(Bfnew, Bfcur, sizeof(double) * 3 * gn);
+    auto Ev = [&](int c, int i, int j, int k) { return E[c * gn + g.gi(i, j, k)]; };
+    for (int d = 0; d < 3; ++d) {
+      int hi[3] = {N[0], N[1], N[2]};
+      hi[d] = N[d] + 1;
+      for (int k = 0; k < hi[2]; ++k)
+        for (int j = 0; j < hi[1]; ++j)
+          for (int i = 0; i < hi[0]; ++i) {
+            double curl;
+            if (d == 0)
+              curl = -(Ev(2, i, j + 1, k) - Ev(2, i, j, k)) / p->dx[1] + (Ev(1, i, j, k + 1) - Ev(1, i, j, k)) / p->dx[2];
+            else if (d == 1)
+              curl = (Ev(2, i + 1, j, k) - Ev(2, i, j, k)) / p->dx[0] - (Ev(0, i, j, k + 1) - Ev(0, i, j, k)) / p->dx[2];
+            else
+              curl = -(Ev(1, i + 1, j, k) - Ev(1, i, j, k)) / p->dx[0] + (Ev(0, i, j + 1, k) - Ev(0, i, j, k)) / p->dx[1];
+            const long f = d * gn + g.gi(i, j, k);
+            const double b0 = Bf0 ? Bf0[f] : 0.0;
+            Bfnew[f] = g0 * b0 + g1 * Bfcur[f] + beta * dt * curl;
+          }
+    }
+  }
   auto Ev = [&](int c, int i, int j, int k) { return E[c * gn + g.gi(i, j, k)]; };
   if (Fdbg) std::memcpy(Fdbg, F.data(), sizeof(double) * F.size());
   if (Edbg) std::memcpy(Edbg, E.data(), sizeof(double) * E.size());
 
   // a5 + a6: divergence, sources, RK combination, con2prim, floors.
   if (iters_total) *iters_total = 0;
+  const long sx = 1, sy = g.gx, sz = (long)g.gx * g.gy;
   for (int k = 0; k < g.nz; ++k)
     for (int j = 0; j < g.ny; ++j)
       for (int i = 0; i < g.nx; ++i) {
@@ -947,6 +1078,12 @@ int orc_stage(const orc_params* p, double* P, const double* U0, const double* Uc
           double u0 = U0 ? U0[v * in + c] : 0.0;
           Un[v] = g0 * u0 + g1 * Ucur[v * in + c] + beta * dt * L[v];
         }
+        if (face_ct) {
+          // the cell-centred densitized field is the mean of the cell's two new faces of each direction
+          const long gc = g.gi(i, j, k);
+          const long st[3] = {sx, sy, sz};
+          for (int d = 0; d < 3; ++d) Un[5 + d] = 0.5 * (Bfnew[d * gn + gc] + Bfnew[d * gn + gc + st[d]]);
+        }
         // a6: con2prim on the undensitized state.
         double Uc[8];
         for (int v = 0; v < 8; ++v) Uc[v] = Un[v] / G.sqrtgam;
@@ -965,6 +1102,57 @@ int orc_stage(const orc_params* p, double* P, const double* U0, const double* Uc
         for (int v = 0; v < 8; ++v) Unew[v * in + c] = Un[v];
         for (int v = 0; v < 8; ++v) P[v * gn + g.gi(i, j, k)] = R.P[v];
         status[c] = (uint8_t)st;
+      }
+  return 0;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI (stages)
+extern "C" {
+
+// One RK stage with Toth flux-CT on the cell-centred field.
+// Outputs: Unew, P (updated in place), status, *dt_used, maxspeed[3] (max |lambda| per direction).
+// Optional debug outputs (may be NULL): Fx/Fy/Fz [8][gsize] face fluxes, Ex/Ey/Ez [gsize] edge EMFs.
+int orc_stage(const orc_params* p, double* P, const double* U0, const double* Ucur, double* Unew, uint8_t* status,
+              double g0, double g1, double beta, double dt, double* dt_used, double* maxspeed, int* iters_total,
+              double* Fdbg, double* Edbg) {
+  return stage_impl(p, P, U0, Ucur, Unew, status, g0, g1, beta, dt, dt_used, maxspeed, iters_total, Fdbg, Edbg,
+                    nullptr, nullptr, nullptr);
+}
+
+// One RK stage with face-centred upwind CT. Bfcur [3][gsize] is the face field of this stage (its ghost
+// faces are filled first when periodic), Bf0 the one at the start of the step (NULL when g0 = 0), Bfnew
+// receives the advanced faces (ghost faces copied from Bfcur). U0 / Ucur B components are not read.
+int orc_stage_face_ct(const orc_params* p, double* P, const double* U0, const double* Ucur, double* Unew,
+                      uint8_t* status, double g0, double g1, double beta, double dt, double* dt_used,
+                      double* maxspeed, int* iters_total, double* Fdbg, double* Edbg, const double* Bf0,
+                      double* Bfcur, double* Bfnew) {
+  if (!Bfcur || !Bfnew) return 1;
+  return stage_impl(p, P, U0, Ucur, Unew, status, g0, g1, beta, dt, dt_used, maxspeed, iters_total, Fdbg, Edbg,
+                    Bf0, Bfcur, Bfnew);
+}
+
+// Cell-centred field from the faces: B^d of every cell whose two d-faces are both stored (all ghosted
+// cells but the last layer along d) becomes (Bf_d(lower) + Bf_d(upper)) / (2 sqrt(gamma)) at the cell
+// centre; the last layer keeps its value. Periodic blocks get their ghost faces filled first.
+int orc_face_b_to_cells(const orc_params* p, double* Bf, double* P) {
+  Grid g(*p);
+  const long gn = g.gsize();
+  if (p->bc == 0) ghost_fill_faces_periodic(g, Bf);
+  const long st[3] = {1, g.gx, (long)g.gx * g.gy};
+  const int hi[3] = {g.nx + g.ng, g.ny + g.ng, g.nz + g.ng};
+  for (int k = -g.ng; k < hi[2]; ++k)
+    for (int j = -g.ng; j < hi[1]; ++j)
+      for (int i = -g.ng; i < hi[0]; ++i) {
+        Geom G;
+        metric_eval(*p, g.xc(0, i), g.xc(1, j), g.xc(2, k), G);
+        const int c[3] = {i, j, k};
+        const long gc = g.gi(i, j, k);
+        for (int d = 0; d < 3; ++d) {
+          if (c[d] + 1 >= hi[d]) continue;
+          P[(5 + d) * gn + gc] = 0.5 * (Bf[d * gn + gc] + Bf[d * gn + gc + st[d]]) / G.sqrtgam;
+        }
       }
   return 0;
 }

@@ -134,11 +134,15 @@ def _to_uniform(g):
 
 
 def kerr_schild_random_prims(s: Setup, seed: int = 1, rho_range=(1e-6, 1.0), w_range=(1.0, 10.0),
-                             sigma_range=(1e-2, 50.0), p_coef: float = 0.01, kmax: int = 3) -> np.ndarray:
+                             sigma_range=(1e-2, 50.0), p_coef: float = 0.01, kmax: int = 3,
+                             faces: bool = False):
     """Smooth seeded random primitives over the ghosted block (see module docstring).
 
     ``kmax`` bounds the integer wavenumbers of the Fourier modes (per unit cube); small grids
-    use kmax = 1 so that the fields stay resolved.
+    use kmax = 1 so that the fields stay resolved. With ``faces=True`` also returns the face field
+    ``Bf`` [3][gz][gy][gx] (entry (i, j, k) of component d on the lower d-face of ghosted cell (i, j, k)):
+    the same potential's curl on the faces, with the same scale, so that the mean of a cell's two
+    d-faces is its B^d in ``P``. Used as the face-centred field sqrt(gamma) B^d.
     """
     rng = np.random.default_rng(seed)
     f_rho, f_w, f_sig = (_SmoothField(rng, kmax=kmax) for _ in range(3))
@@ -176,40 +180,149 @@ def kerr_schild_random_prims(s: Setup, seed: int = 1, rho_range=(1e-6, 1.0), w_r
     del rho_n, W_n, sig_n
     A = [amp * f(*xn) for f in f_a]
     del amp
-    B = _corner_curl(A, s.dx)
+    Bface = _face_curl(A, s.dx)
+    B = np.stack([_mu(Bface[c], _AX_OF[c]) for c in range(3)])
     # One global scale so the median of |B|^2 / (rho W^2) matches the median target sigma.
     proxy = np.sum(B ** 2, axis=0) / (rho * W * W)
     target = math.sqrt(sigma_range[0] * sigma_range[1])
     scale = math.sqrt(target / float(np.median(proxy)))
     P[5:8] = B * scale
-    return P
+    if not faces:
+        return P
+    Bf = np.empty((3,) + P.shape[1:])
+    for c in range(3):
+        sl = [slice(None)] * 3
+        sl[_AX_OF[c]] = slice(0, -1)  # drop the upper face of the last ghost layer
+        Bf[c] = Bface[c][tuple(sl)] * scale
+    return P, Bf
 
 
-def _corner_curl(A, dx):
-    """Cell-centred curl of node-centred A: B_x = mu_x(D_y mu_z A_z - D_z mu_y A_y) and cyclic.
+_AX_OF = {0: 2, 1: 1, 2: 0}  # array axis of the x, y, z direction ([z][y][x] order)
 
-    A[c] has shape [nz+1][ny+1][nx+1] over the cell corners; the result is [3][nz][ny][nx].
-    mu_d averages the two nodes along d; D_d differences them and divides by dx_d.
-    """
-    def mu(a, ax):
-        sl0 = [slice(None)] * 3; sl1 = [slice(None)] * 3
-        sl0[ax] = slice(0, -1); sl1[ax] = slice(1, None)
-        return 0.5 * (a[tuple(sl0)] + a[tuple(sl1)])
 
+def _mu(a, ax):
+    """Mean of neighbouring entries along array axis ax."""
+    sl0 = [slice(None)] * 3; sl1 = [slice(None)] * 3
+    sl0[ax] = slice(0, -1); sl1[ax] = slice(1, None)
+    return 0.5 * (a[tuple(sl0)] + a[tuple(sl1)])
+
+
+def _face_curl(A, dx):
+    """Curl of node-centred A on the faces: component c on the c-faces is D_a mu_b A_b - D_b mu_a A_a
+    for (c, a, b) cyclic, where mu_d averages the two nodes along d and D_d differences them over dx_d.
+
+    A[c] has shape [nz+1][ny+1][nx+1] over the cell corners; component c of the result has the node
+    count along c and the cell count along the other two directions. Its mean over the two c-faces of
+    each cell is the cell-centred curl of the random field (zero corner divergence)."""
     def D(a, ax, h):
         sl0 = [slice(None)] * 3; sl1 = [slice(None)] * 3
         sl0[ax] = slice(0, -1); sl1[ax] = slice(1, None)
         return (a[tuple(sl1)] - a[tuple(sl0)]) / h
 
-    ax_of = {0: 2, 1: 1, 2: 0}  # array axis of the x, y, z direction ([z][y][x] order)
     out = []
     for c in range(3):
         a, b = (c + 1) % 3, (c + 2) % 3
-        # B_c = mu_c (D_a mu_b A_b - D_b mu_a A_a)
-        t1 = D(mu(A[b], ax_of[b]), ax_of[a], dx[a])
-        t2 = D(mu(A[a], ax_of[a]), ax_of[b], dx[b])
-        out.append(mu(t1 - t2, ax_of[c]))
-    return np.stack(out)
+        t1 = D(_mu(A[b], _AX_OF[b]), _AX_OF[a], dx[a])
+        t2 = D(_mu(A[a], _AX_OF[a]), _AX_OF[b], dx[b])
+        out.append(t1 - t2)
+    return out
+
+
+def smooth_random_prims(s: Setup, seed: int = 6, amp: float = 0.3, b_amp: float = 0.3, kmax: int = 1):
+    """Seeded smooth state over the ghosted block, and its face field: rho = 1 + amp f, rho eps =
+    1.5 (1 + amp f), W v^i = amp f_i, each f a sum of random Fourier modes over the interior (periodic
+    on it), and B the curl of a node-centred random potential of amplitude b_amp (as in
+    ``kerr_schild_random_prims``). Unlike that generator it has no normalised direction field, so every
+    variable is smooth. Returns (P, Bf)."""
+    rng = np.random.default_rng(seed)
+    fs = [_SmoothField(rng, kmax=kmax) for _ in range(5)]
+    fa = [_SmoothField(rng, kmax=kmax) for _ in range(3)]
+    span = [s.n[d] * s.dx[d] for d in range(3)]
+    xc = [(s.cell_centres(d) - s.x0[d]) / span[d] for d in range(3)]
+    xn = [np.arange(-s.ng, s.n[d] + s.ng + 1) / s.n[d] for d in range(3)]
+    P = np.empty(s.prim_shape())
+    g = [f(*xc) for f in fs]
+    P[0] = 1.0 + amp * np.tanh(g[0])
+    P[4] = 1.5 * (1.0 + amp * np.tanh(g[1]))
+    for c in range(3):
+        P[1 + c] = amp * np.tanh(g[2 + c])
+    A = [b_amp * span[0] / (2.0 * math.pi) * f(*xn) for f in fa]
+    Bface = _face_curl(A, s.dx)
+    Bf = np.empty((3,) + P.shape[1:])
+    for c in range(3):
+        sl = [slice(None)] * 3
+        sl[_AX_OF[c]] = slice(0, -1)
+        Bf[c] = Bface[c][tuple(sl)]
+        P[5 + c] = _mu(Bface[c], _AX_OF[c])
+    return P, Bf
+
+
+def plane_random_prims(s: Setup, d: int, seed: int = 5, amp: float = 0.3):
+    """Seeded random state that varies along direction d only (periodic Minkowski block), and its
+    face field. Every variable is a constant plus a sum of three random Fourier modes of the cell
+    coordinate along d; the normal field B^d is constant (a divergence-free plane field).
+    Returns (P, Bf) with Bf [3][gz][gy][gx]: a d-face carries B^d, a face of another direction c
+    carries the B^c of its cell."""
+    rng = np.random.default_rng(seed)
+    n = s.n[d]
+    x = (np.arange(-s.ng, n + s.ng) + 0.5) / n  # unit coordinate of the cells along d
+
+    def profile(base, a):
+        k = rng.integers(1, 4, size=3)
+        ph = rng.uniform(0.0, 2.0 * math.pi, size=3)
+        c = rng.normal(size=3)
+        f = np.sum(c[:, None] * np.sin(2.0 * math.pi * k[:, None] * x[None, :] + ph[:, None]), axis=0)
+        return base + a * f / np.max(np.abs(f))
+
+    prof = [profile(1.0, amp), profile(0.0, amp), profile(0.0, amp), profile(0.0, amp), profile(1.5, amp * 1.5),
+            None, None, None]
+    for c in range(3):
+        prof[5 + c] = np.full_like(x, 0.4) if c == d else profile(0.0, 0.5)
+    ax = _AX_OF[d]
+    shape = [1, 1, 1]
+    shape[ax] = len(x)
+    P = np.empty(s.prim_shape())
+    for v in range(8):
+        P[v] = prof[v].reshape(shape)
+    Bf = np.ascontiguousarray(P[5:8].copy())
+    return P, Bf
+
+
+def field_loop_setup(n: int = 32, recon: str = "plm_mc", riemann: str = "hll") -> Setup:
+    """Periodic Minkowski square [0, 1]^2 of n x n cells, one cell thick in z."""
+    return Setup(n=(n, n, 1), x0=(0.0, 0.0, 0.0), dx=(1.0 / n, 1.0 / n, 1.0 / n), metric="minkowski",
+                 recon=recon, riemann=riemann, bc="periodic")
+
+
+def field_loop_prims(s: Setup, v=(0.3, 0.15), radius: float = 0.3, a0: float = 1e-3, rho: float = 1.0,
+                     press: float = 1.0):
+    """Weak magnetic field loop advected by a uniform flow (the standard CT advection test): uniform
+    rho, pressure and velocity v (as W v^i in P), B the curl of A_z = a0 (radius - r) inside the loop
+    (r from the square's centre), zero outside. Returns (P, Bf), Bf the face curl of the node-centred
+    A_z; P's cell field is the mean of its faces."""
+    vx, vy = v
+    W = 1.0 / math.sqrt(1.0 - vx * vx - vy * vy)
+    P = np.zeros(s.prim_shape())
+    P[0] = rho
+    P[1] = W * vx
+    P[2] = W * vy
+    P[4] = press / (s.gamma_eos - 1.0)
+    gz, gy, gx = P.shape[1:]
+    xn = [s.x0[d] + np.arange(-s.ng, s.n[d] + s.ng + 1) * s.dx[d] for d in range(3)]
+    X, Y = np.meshgrid(xn[0], xn[1], indexing="xy")  # [y][x] node grid
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    az = np.where(r < radius, a0 * (radius - r), 0.0)
+    Az = np.broadcast_to(az[None, :, :], (gz + 1,) + az.shape).copy()
+    zero = np.zeros_like(Az)
+    Bface = _face_curl([zero, zero, Az], s.dx)
+    Bf = np.empty((3,) + P.shape[1:])
+    for c in range(3):
+        sl = [slice(None)] * 3
+        sl[_AX_OF[c]] = slice(0, -1)
+        Bf[c] = Bface[c][tuple(sl)]
+    for c in range(3):
+        P[5 + c] = _mu(Bface[c], _AX_OF[c])
+    return P, Bf
 
 
 def c2p_states(n: int, seed: int = 4, gamma_eos: float = GAMMA_DEFAULT, rho_range=(1e-8, 1.0), w_range=(1.0, 50.0),

@@ -14,6 +14,13 @@ Workloads (sizes and distributions follow the stage's standard test problems):
     corner-to-cell curl of a node-centred vector potential whose amplitude follows a
     magnetisation target log-uniform in [1e-2, 50] (so Toth's corner divergence of B is
     zero up to roundoff). Ghost zones are filled from the same fields (fixed ghosts).
+    With ``faces=True`` it also returns the same potential's curl on the faces (the face-centred field
+    of the face-CT form), whose mean over a cell's two faces of each direction is the cell field.
+  * ``smooth_random`` every variable a smooth random perturbation of a uniform state (no normalised
+    direction field), B from a random potential, with its face field.
+  * ``plane_random`` a periodic state that varies along one direction only, with its face field.
+  * ``field_loop`` a weak magnetic field loop in a uniform flow on a periodic square (the standard
+    constrained-transport advection test), with its face field.
   * ``c2p_states``  i.i.d. primitive states for the flat con2prim batch: rho, W, sigma
     log-uniform over [1e-8, 1], [1, 50], [1e-4, 1e3], P = 0.01 rho^(5/3) 10^U(-1,1),
     isotropic velocity and field directions.

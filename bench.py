@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-guess", action="store_true")
+    ap.add_argument("--no-face-ct", action="store_true")
     ap.add_argument("--guess-states", type=int, default=100_000_000)
     ap.add_argument("--guess-only", action="store_true",
                     help="run only the learned-guess con2prim section and print its JSON (profiling aid)")
@@ -184,7 +185,7 @@ def run_ours(args):
 
     n = args.n
     s_mix, seed = workload(n, "mixed", rank)
-    P = I.kerr_schild_random_prims(s_mix, seed=seed)
+    P, Bf = I.kerr_schild_random_prims(s_mix, seed=seed, faces=True)
     cells = n ** 3
     # ---- mixed form: warm-up, timed region (device events, clocks sampled)
     ctx = G.Context(s_mix)
@@ -250,6 +251,8 @@ def run_ours(args):
     l1p = l1_rel(cm.prims()[inner], P64[inner])
     del cm
     torch.cuda.empty_cache()
+    face_ct = None if args.no_face_ct else run_face_ct(G, s_mix, P, Bf, args.steps, args.warmup)
+    del Bf
     guess = None if args.no_guess else run_guess(G, I, rank, n_states=args.guess_states)
     batched = None
     if not args.no_batched:
@@ -293,6 +296,8 @@ def run_ours(args):
         # per stage: 3 flux, EMF, update, floored-cell pass, deferred con2prim; the CFL finalisation per step
         "gpu_launches": 7 * args.steps + (args.steps + 1) // 2,
     }
+    if face_ct is not None:
+        out["face_ct"] = face_ct
     if batched is not None:
         out["batched"] = batched
     if guess is not None:
@@ -419,6 +424,57 @@ def batched_setups(seed0=3):
                               metric="kerr_schild", spin=0.9, recon="weno5z_aoah", riemann="hll", bc="fixed",
                               precision="mixed"))
     return setups
+
+
+def _face_divergence(B, s, torch):
+    """max |sum_d (Bf_d(upper) - Bf_d(lower)) / dx_d| x min dx / max |Bf| over the interior cells."""
+    ng = s.ng
+    nx, ny, nz = s.n
+    div = None
+    for d, ax in ((0, 2), (1, 1), (2, 0)):
+        lo = [slice(ng, ng + nz), slice(ng, ng + ny), slice(ng, ng + nx)]
+        hi = list(lo)
+        hi[ax] = slice(lo[ax].start + 1, lo[ax].stop + 1)
+        t = (B[d][tuple(hi)] - B[d][tuple(lo)]) / s.dx[d]
+        div = t if div is None else div + t
+    return float(div.abs().max() * min(s.dx) / B.abs().max())
+
+
+def run_face_ct(G, s_mix, P, Bf, steps, warmup):
+    """The same workload with face-centred upwind CT (the field on the faces): stage throughput, per-kernel
+    times, and the face divergence before and after the timed stages."""
+    import dataclasses
+    import torch
+    s = dataclasses.replace(s_mix, ct="face")
+    ctx = G.Context(s)
+    ctx.set_prims(P)
+    ctx.set_face_b(Bf)
+    B = torch.empty((3,) + tuple(P.shape[1:]), dtype=torch.float64, device="cuda")
+    ctx.get(G.GRMHD_GET_FACE_B, out=B)
+    div0 = _face_divergence(B, s, torch)
+    for k in range(warmup):
+        ctx.stage(*stage_coeffs(k), 0.0)
+    k0 = warmup + (warmup % 2)
+    if warmup % 2:
+        ctx.stage(*stage_coeffs(warmup), 0.0)
+    torch.cuda.synchronize()
+    ms = time_stages(ctx, k0, steps)
+    ctx.set_timing(True)
+    time_stages(ctx, k0, min(steps, 8))
+    kt, kst = ctx.timing()
+    ctx.set_timing(False)
+    ctx.get(G.GRMHD_GET_FACE_B, out=B)
+    torch.cuda.synchronize()
+    div = _face_divergence(B, s, torch)
+    cells = s.n[0] * s.n[1] * s.n[2]
+    out = {"value": cells * steps / (ms / 1e3), "unit": UNIT, "ms_per_stage": ms / steps, "steps": steps,
+           "kernels_ms_per_stage": {k: v / max(kst, 1) for k, v in kt.items()},
+           "emf_group": "cell-centred EMFs, upwind edge EMFs and the Stokes update of the faces",
+           "face_divergence_rel": {"initial": div0, "after": div, "stages": warmup + (warmup % 2) + steps + min(steps, 8)},
+           "scheme": "face-centred field, upwind (contact) edge EMFs of Gardiner & Stone 2005"}
+    del ctx, B
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(G, I, steps, warmup, rank):

@@ -63,6 +63,11 @@ extern "C" {
 #define GRMHD_MIXED 1           /* reconstruction, fluxes, EMFs and sources in float; P stored in float;
                                    state accumulation and con2prim in double */
 
+/* constrained transport of the magnetic field */
+#define GRMHD_CT_FLUX 0         /* Toth flux-CT of the cell-centred field (Sec. 3.1) */
+#define GRMHD_CT_FACE 1         /* face-centred field, upwind edge EMFs (Sec. 5 names face-centred CT as
+                                   planned work; scheme: the "contact" CT of Gardiner & Stone 2005) */
+
 #define GRMHD_HOST 0
 #define GRMHD_DEVICE 1
 
@@ -75,6 +80,7 @@ extern "C" {
                                    of a cell, cells the mixed form's float con2prim phase handed to the
                                    double iteration */
 #define GRMHD_GET_DT 4          /* double [1]: the time step of the last first stage (CFL rule) */
+#define GRMHD_GET_FACE_B 5      /* double [3][nz+2ng][ny+2ng][nx+2ng]: the current face field (GRMHD_CT_FACE) */
 
 /* per-cell status bits */
 #define GRMHD_ST_RHO_FLOOR 1
@@ -101,6 +107,7 @@ typedef struct {
   int c2p_max_iter;           /* iteration cap of the root solve */
   double cfl;                 /* dt = cfl / max_d(max |lambda_d| / dx_d) when the stage picks dt */
   double weno_eps;            /* epsilon of the WENO5-Z weights (App. B eq. (nonlinear weights)) */
+  int ct;                     /* GRMHD_CT_FLUX | GRMHD_CT_FACE (single-block contexts only) */
 } grmhd_params;
 
 /* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */
@@ -120,6 +127,18 @@ int grmhd_set_prims(grmhd_ctx* c, const double* P, int where);
 /* Overwrite the current conserved state with U (double [8][nz][ny][nx]) without touching P; used
  * with grmhd_set_prims to restore a checkpoint taken with grmhd_get. */
 int grmhd_set_cons(grmhd_ctx* c, const double* U, int where);
+
+/* Face-centred CT (p->ct == GRMHD_CT_FACE): load the face field Bf (double [3][nz+2ng][ny+2ng][nx+2ng],
+ * `where` = GRMHD_HOST or GRMHD_DEVICE): entry (i,j,k) of component d is sqrt(gamma) B^d on the lower
+ * d-face of ghosted cell (i,j,k), i.e. the densitized field whose face divergence
+ * sum_d (Bf_d(upper) - Bf_d(lower)) / dx_d the stage keeps. Call after grmhd_set_prims: the faces replace
+ * the cell field of P (B^d = mean of the two d-faces / sqrt(gamma) at the cell centre, for every cell
+ * whose two d-faces are stored: all but the last ghost layer along d; periodic blocks get their ghost
+ * faces filled first) and the conserved state is derived again. Fixed ghost faces keep these values.
+ * In this mode the stage advances the faces by the discrete Stokes theorem on upwind edge EMFs and
+ * the cell field is the mean of its faces; the B components of U0 / Ucur are not read.
+ * Errors: GRMHD_E_INVALID (no grid, not a face-CT context, bad `where`), GRMHD_E_CUDA. */
+int grmhd_set_face_b(grmhd_ctx* c, const double* Bf, int where);
 
 /* One Runge-Kutta stage (a0..a6 of the stage; Sec. 3.1):
  *   Unew = g0 U0 + g1 Ucur + beta dt L(Ucur)
@@ -250,7 +269,7 @@ int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
  *   Unew   double [8][nz][ny][nx], the stage's output state (may not alias Ucur or U0)
  *   status uint8  [nz][ny][nx]
  * -- and the coefficients of Unew = g0 U0 + g1 Ucur + beta dt L(Ucur); dt <= 0 takes the CFL step of
- * this call's face speeds. p->precision must be GRMHD_FP64.
+ * this call's face speeds. p->precision must be GRMHD_FP64 and p->ct GRMHD_CT_FLUX (else GRMHD_E_INVALID).
  * Scratch (face fluxes, edge EMFs, speed and time-step scalars) lives in a 16 MiB array of device
  * memory built into the library (every GPU that loads the library holds it until the process exits),
  * which bounds the block to (16 MiB - 512 B) / 216 B = 77,672 ghosted cells, e.g. 34^3 interior cells
@@ -280,7 +299,8 @@ typedef struct {
 size_t grmhd_batch_workspace_bytes(const grmhd_params* p, int nblocks, const grmhd_block* blocks);
 
 /* Create a batch context (workspace and stream borrowed as for grmhd_create); the tile starts at 512.
- * Errors: GRMHD_E_INVALID, GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED (periodic blocks), GRMHD_E_CUDA. */
+ * Errors: GRMHD_E_INVALID, GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED (periodic blocks, face-centred CT),
+ * GRMHD_E_CUDA. */
 int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* blocks, void* workspace, size_t bytes,
                        void* stream, grmhd_ctx** out);
 

@@ -30,6 +30,9 @@ struct grmhd_ctx {
   int* floorlist;            // cells whose hydro state is re-derived after floors
   unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats, [16] worklist count,
                              // [17] floor-list count, [20..23] batch work counters
+  double* Bslot[3];          // face-centred CT: face field slots [3][gsize], paired with Uslot
+  void* Ecc;                 // face-centred CT: cell-centred EMFs [3][gsize] (flux type)
+  bool has_faces;            // face-centred CT: grmhd_set_face_b called since grmhd_set_prims
   int s0, sc;                // slot of U0 and of the current state
   bool has_state;
   bool timing;               // record CUDA events around each kernel group
@@ -61,7 +64,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t P, U[3], F[3], E, status, worklist, wl_mu, floorlist, geo, scal, total;
+  size_t P, U[3], F[3], E, status, worklist, wl_mu, floorlist, geo, B[3], Ecc, scal, total;
 };
 
 bool valid_params(const grmhd_params* p, char* msg, size_t n) {
@@ -86,6 +89,7 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   if (!(p->c2p_tol > 0.0) || p->c2p_max_iter < 1) { snprintf(msg, n, "bad con2prim tolerance / iteration cap"); return false; }
   if (!(p->w_max > 1.0)) { snprintf(msg, n, "w_max must be > 1"); return false; }
   if (p->metric == GRMHD_KERR_SCHILD && !(p->mass > 0.0)) { snprintf(msg, n, "mass must be > 0"); return false; }
+  if (p->ct != GRMHD_CT_FLUX && p->ct != GRMHD_CT_FACE) { snprintf(msg, n, "unknown constrained-transport mode"); return false; }
   return true;
 }
 
@@ -110,6 +114,10 @@ Layout layout_of(const grmhd_params* p) {
     }
     l.floorlist = take(I * sizeof(int));
     if (p->metric == GRMHD_KERR_SCHILD) l.geo = take(NGEO * I * sizeof(double));
+    if (p->ct == GRMHD_CT_FACE) {
+      for (int k = 0; k < 3; ++k) l.B[k] = take(3 * G * sizeof(double));
+      l.Ecc = take(3 * G * pb);
+    }
   }
   l.total = off;
   return l;
@@ -335,7 +343,12 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
     c->wl_mu = p->precision == GRMHD_MIXED ? (double*)(c->ws + l.wl_mu) : nullptr;
     c->floorlist = (int*)(c->ws + l.floorlist);
     if (p->metric == GRMHD_KERR_SCHILD) c->dp.geo = (const double*)(c->ws + l.geo);
+    if (p->ct == GRMHD_CT_FACE) {
+      for (int k = 0; k < 3; ++k) c->Bslot[k] = (double*)(c->ws + l.B[k]);
+      c->Ecc = c->ws + l.Ecc;
+    }
   }
+  c->has_faces = false;
   c->s0 = c->sc = 0;
   c->has_state = false;
   cudaError_t e = cudaMemsetAsync(c->ws, 0, l.total, c->stream);
@@ -368,6 +381,29 @@ int grmhd_set_prims(grmhd_ctx* c, const double* P, int where) {
   c->s0 = c->sc = 0;
   CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], c->stream), "prim->cons");
   c->has_state = true;
+  c->has_faces = false;
+  return GRMHD_OK;
+}
+
+int grmhd_set_face_b(grmhd_ctx* c, const double* Bf, int where) {
+  if (!c || !Bf) return c ? fail(c, GRMHD_E_INVALID, "Bf is NULL") : GRMHD_E_INVALID;
+  if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
+  if (c->prm.ct != GRMHD_CT_FACE) return fail(c, GRMHD_E_INVALID, "not a face-centred CT context (params.ct)");
+  if (!c->has_state) return fail(c, GRMHD_E_INVALID, "grmhd_set_prims has not been called");
+  if (where != GRMHD_HOST && where != GRMHD_DEVICE) return fail(c, GRMHD_E_INVALID, "bad where");
+  const size_t bytes = sizeof(double) * 3 * (size_t)c->dp.gsize;
+  double* cur = c->Bslot[c->sc];
+  CK(cudaMemcpyAsync(cur, Bf, bytes, where == GRMHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                     c->stream),
+     "copying the face field");
+  if (c->prm.bc == GRMHD_BC_PERIODIC) CK(c->L->ghost_faces(c->dp, cur, c->stream), "face ghost fill");
+  // every slot starts from these faces: fixed ghost faces are never written by a stage
+  for (int k = 0; k < 3; ++k)
+    if (c->Bslot[k] != cur) CK(cudaMemcpyAsync(c->Bslot[k], cur, bytes, cudaMemcpyDeviceToDevice, c->stream), "copying faces");
+  CK(c->L->face_to_cells(c->dp, cur, c->P, c->stream), "cell field from the faces");
+  CK(c->L->prim2con(c->dp, c->P, c->Uslot[c->sc], c->stream), "prim->cons");
+  if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
+  c->has_faces = true;
   return GRMHD_OK;
 }
 
@@ -434,8 +470,13 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   }
   const bool auto_dt = !(dt > 0.0);
   const bool track = auto_dt && first;
+  const bool face = c->prm.ct == GRMHD_CT_FACE;
+  if (face && !c->has_faces) return fail(c, GRMHD_E_INVALID, "grmhd_set_face_b has not been called");
   const FormLaunchers& L = *c->L;
   const cudaStream_t s = c->stream;
+  // this stage's parameters: with face-centred CT the flux kernels read the normal field of the faces
+  DevParams dp = c->dp;
+  if (face) dp.bface = c->Bslot[c->sc];
   if (c->timing) CK(collect_timing(c), "reading kernel timings");
 #define TMARK(k) \
   if (c->timing) CK(cudaEventRecord(c->ev[k], s), "recording a timing event")
@@ -445,15 +486,16 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   CK(cudaMemsetAsync(stats, 0, 10 * sizeof(unsigned long long), s), "clearing stats and the worklist counts");
   if (track) CK(cudaMemsetAsync(ms, 0, 3 * sizeof(unsigned long long), s), "clearing speeds");
   TMARK(0);
-  if (c->prm.bc == GRMHD_BC_PERIODIC) CK(L.ghost(c->dp, c->P, s), "ghost fill");
+  if (c->prm.bc == GRMHD_BC_PERIODIC) {
+    CK(L.ghost(dp, c->P, s), "ghost fill");
+    if (face) CK(L.ghost_faces(dp, c->Bslot[c->sc], s), "face ghost fill");
+  }
   for (int d = 0; d < 3; ++d) {
     TMARK(1 + d);
-    CK(L.flux(c->dp, c->P, c->F[d], ms, d, track ? 1 : 0, s), "flux");
+    CK(L.flux(dp, c->P, c->F[d], ms, d, track ? 1 : 0, s), "flux");
   }
-  if (track) CK(launch_finalize_dt(ms, dt_dev, c->dp, s), "time step");
+  if (track) CK(launch_finalize_dt(ms, dt_dev, dp, s), "time step");
   TMARK(4);
-  CK(L.emf(c->dp, c->F[0], c->F[1], c->F[2], c->E, s), "EMF");
-  TMARK(5);
   StageArgs a{};
   a.U0 = c->Uslot[c->s0];
   a.Ucur = c->Uslot[c->sc];
@@ -471,9 +513,17 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   a.wl_mu = c->wl_mu;
   a.floorlist = c->floorlist;
   a.fl_count = (unsigned int*)(c->scal + 17);
-  CK(L.update(c->dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
+  if (face) {
+    CK(L.emf_face(dp, c->P, c->F[0], c->F[1], c->F[2], c->Ecc, c->E, s), "upwind EMF");
+    CK(L.face_update(dp, c->Bslot[c->s0], c->Bslot[c->sc], c->Bslot[dst], c->E, a, s), "face update");
+    a.bface_new = c->Bslot[dst];
+  } else {
+    CK(L.emf(dp, c->F[0], c->F[1], c->F[2], c->E, s), "EMF");
+  }
+  TMARK(5);
+  CK(L.update(dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
   TMARK(6);
-  CK(L.cell_passes(c->dp, c->P, a, s), "floored and deferred cells");
+  CK(L.cell_passes(dp, c->P, a, s), "floored and deferred cells");
   TMARK(7);
 #undef TMARK
   if (c->timing) c->t_pending = true;
@@ -613,6 +663,10 @@ int grmhd_get(grmhd_ctx* c, int what, void* dst, int where) {
     case GRMHD_GET_DT:
       CK(cudaMemcpyAsync(dst, c->scal + 3, sizeof(double), kind, s), "copying dt");
       break;
+    case GRMHD_GET_FACE_B:
+      if (c->prm.ct != GRMHD_CT_FACE) return fail(c, GRMHD_E_INVALID, "not a face-centred CT context");
+      CK(cudaMemcpyAsync(dst, c->Bslot[c->sc], sizeof(double) * 3 * (size_t)c->dp.gsize, kind, s), "copying faces");
+      break;
     default:
       return fail(c, GRMHD_E_INVALID, "unknown GRMHD_GET_* selector");
   }
@@ -688,6 +742,10 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   if (!valid_params(&q, g_create_err, sizeof g_create_err)) return GRMHD_E_INVALID;
   if (p->bc != GRMHD_BC_FIXED) {
     snprintf(g_create_err, sizeof g_create_err, "batched blocks take their ghosts as given (GRMHD_BC_FIXED)");
+    return GRMHD_E_UNSUPPORTED;
+  }
+  if (p->ct != GRMHD_CT_FLUX) {
+    snprintf(g_create_err, sizeof g_create_err, "batches use flux-CT (GRMHD_CT_FLUX)");
     return GRMHD_E_UNSUPPORTED;
   }
   for (int b = 0; b < nblocks; ++b)

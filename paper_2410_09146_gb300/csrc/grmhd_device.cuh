@@ -37,6 +37,10 @@ struct DevParams {
   // Geometry cache: NGEO doubles per interior cell (structure of arrays, isize apart) holding the
   // static Kerr-Schild metric at the cell centre, filled once per block; NULL: computed in place.
   const double* geo;
+  // Face-centred CT: the stage's face field sqrt(gamma) B^d, [3][gsize] double (entry (i,j,k) of
+  // component d on the lower d-face of cell (i,j,k)); the flux kernels take the normal field from it.
+  // NULL: cell-centred field (flux-CT).
+  const double* bface;
 };
 
 // Arguments of the update kernel (a5 + a6).
@@ -55,6 +59,7 @@ struct StageArgs {
   double* wl_mu;                 // per worklist entry: the double iterate to resume from (0: none)
   int* floorlist;                // cells whose floors / status re-derive U in a compacted pass (NULL: inline)
   unsigned int* fl_count;        // number of entries in floorlist
+  const double* bface_new;       // face-centred CT: the advanced faces [3][gsize]; NULL: flux-CT
 };
 
 

@@ -1,6 +1,7 @@
 // All-FP64 form of the stage kernels (every step in double precision). Built without FMA
 // contraction (-fmad=false) so that every double operation rounds as the FP64 reference does.
 #include "grmhd_kernels.cuh"
+#include "grmhd_face_ct.cuh"
 #include "grmhd_launch.h"
 #include "grmhd_batch_launch.cuh"
 
@@ -96,9 +97,11 @@ cudaError_t geometry(const DevParams& p, double* geo, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+using FC = FaceCtLaunch<R, T>;
 using BL = BatchLaunch<double, double>;
 const FormLaunchers kFp64 = {ghost, flux, emf, update, cell_passes, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
-                                BL::deferred, BL::ctas_per_sm, 8, 8, geometry, BL::floors};
+                                BL::deferred, BL::ctas_per_sm, 8, 8, geometry, BL::floors,
+                                FC::emf, FC::faces, FC::to_cells, FC::ghost_faces};
 
 }  // namespace
 

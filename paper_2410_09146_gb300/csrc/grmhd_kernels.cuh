@@ -20,8 +20,9 @@ __device__ __forceinline__ long long iidx(const DevParams& p, int i, int j, int 
   return ((long long)k * p.ny + j) * p.nx + i;
 }
 
-// a0: periodic ghost fill (every ghost cell copies its wrapped interior cell).
-template <class T>
+// a0: periodic ghost fill (every ghost cell copies its wrapped interior cell); NVAR arrays gsize apart
+// (the 8 primitives, or the 3 face-field components, whose canonical faces wrap the same way).
+template <class T, int NVAR = NV>
 __global__ void k_ghost_periodic(T* __restrict__ P, DevParams p) {
   const long long n = p.gsize;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -33,7 +34,7 @@ __global__ void k_ghost_periodic(T* __restrict__ P, DevParams p) {
     const int si = ((i % p.nx) + p.nx) % p.nx, sj = ((j % p.ny) + p.ny) % p.ny, sk = ((k % p.nz) + p.nz) % p.nz;
     const long long src = gidx(p, si, sj, sk);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) P[q * n + t] = P[q * n + src];
+    for (int q = 0; q < NVAR; ++q) P[q * n + t] = P[q * n + src];
   }
 }
 
@@ -46,7 +47,8 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 // reconstructed sides PL, PR and the two cell values cL, cR: evaluate the metric at the face centre, the
 // two sides' (U, F, lambda), and the Riemann flux Fh; returns max |lambda|. A face whose reconstructed
 // density is not positive or internal energy is negative on either side takes the first-order (cell)
-// values of both neighbours.
+// values of both neighbours. With a face-centred field (p.bface) both sides take the face's normal
+// field B^d = Bf_d / sqrt(gamma).
 template <class R, int METRIC>
 __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, int k, R PL[NV], R PR[NV],
                                        const R cL[NV], const R cR[NV], R Fh[NV]) {
@@ -64,6 +66,11 @@ __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, 
   xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
   Metric<R> m;
   metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
+  if (p.bface != nullptr) {
+    const R bn = R(p.bface[d * p.gsize + gidx(p, i, j, k)]) / m.sqrtgam;
+    PL[5 + d] = bn;
+    PR[5 + d] = bn;
+  }
   FaceSide<R> L, Rs;
   prim_to_face<R>(PL, m, d, R(p.gamma_eos), L);
   prim_to_face<R>(PR, m, d, R(p.gamma_eos), Rs);
@@ -502,20 +509,24 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
                   (Fz[q * G + g + sz] - Fz[q * G + g]) * R(p.idx[2]);
     L[q] = -div;
   }
-  const R* Ex = E;
-  const R* Ey = E + G;
-  const R* Ez = E + 2 * G;
-  const R h = R(0.5);
-  // CT fluxes of B (normal components vanish)
-  const R FyBx_p = h * (Ez[g + sy] + Ez[g + sy + 1]), FyBx_m = h * (Ez[g] + Ez[g + 1]);
-  const R FzBx_p = -h * (Ey[g + sz] + Ey[g + sz + 1]), FzBx_m = -h * (Ey[g] + Ey[g + 1]);
-  const R FxBy_p = -h * (Ez[g + 1] + Ez[g + 1 + sy]), FxBy_m = -h * (Ez[g] + Ez[g + sy]);
-  const R FzBy_p = h * (Ex[g + sz] + Ex[g + sz + sy]), FzBy_m = h * (Ex[g] + Ex[g + sy]);
-  const R FxBz_p = h * (Ey[g + 1] + Ey[g + 1 + sz]), FxBz_m = h * (Ey[g] + Ey[g + sz]);
-  const R FyBz_p = -h * (Ex[g + sy] + Ex[g + sy + sz]), FyBz_m = -h * (Ex[g] + Ex[g + sz]);
-  L[5] = -((FyBx_p - FyBx_m) * R(p.idx[1]) + (FzBx_p - FzBx_m) * R(p.idx[2]));
-  L[6] = -((FxBy_p - FxBy_m) * R(p.idx[0]) + (FzBy_p - FzBy_m) * R(p.idx[2]));
-  L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
+  if (a.bface_new == nullptr) {
+    const R* Ex = E;
+    const R* Ey = E + G;
+    const R* Ez = E + 2 * G;
+    const R h = R(0.5);
+    // CT fluxes of B (normal components vanish)
+    const R FyBx_p = h * (Ez[g + sy] + Ez[g + sy + 1]), FyBx_m = h * (Ez[g] + Ez[g + 1]);
+    const R FzBx_p = -h * (Ey[g + sz] + Ey[g + sz + 1]), FzBx_m = -h * (Ey[g] + Ey[g + 1]);
+    const R FxBy_p = -h * (Ez[g + 1] + Ez[g + 1 + sy]), FxBy_m = -h * (Ez[g] + Ez[g + sy]);
+    const R FzBy_p = h * (Ex[g + sz] + Ex[g + sz + sy]), FzBy_m = h * (Ex[g] + Ex[g + sy]);
+    const R FxBz_p = h * (Ey[g + 1] + Ey[g + 1 + sz]), FxBz_m = h * (Ey[g] + Ey[g + sz]);
+    const R FyBz_p = -h * (Ex[g + sy] + Ex[g + sy + sz]), FyBz_m = -h * (Ex[g] + Ex[g + sz]);
+    L[5] = -((FyBx_p - FyBx_m) * R(p.idx[1]) + (FzBx_p - FzBx_m) * R(p.idx[2]));
+    L[6] = -((FxBy_p - FxBy_m) * R(p.idx[0]) + (FzBy_p - FzBy_m) * R(p.idx[2]));
+    L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
+  } else {
+    L[5] = L[6] = L[7] = R(0);  // the field comes from the advanced faces below
+  }
   Metric<double> m;
   double isg, fr;
   cell_metric<METRIC>(p, t, xc, yc, zc, m, isg, fr);
@@ -541,6 +552,13 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
     double u = a.g1 * a.Ucur[q * n + t];
     if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
     Un[q] = u + bdt * (double)L[q];
+  }
+  if (a.bface_new != nullptr) {
+    // face-centred CT: the cell's densitized field is the mean of its two advanced faces of each direction
+    const double* bn = a.bface_new;
+    Un[5] = 0.5 * (bn[g] + bn[g + 1]);
+    Un[6] = 0.5 * (bn[G + g] + bn[G + g + sy]);
+    Un[7] = 0.5 * (bn[2 * G + g] + bn[2 * G + g + sz]);
   }
   // a6: con2prim on the undensitized state, warm-started from the current primitives (the warm start only
   // seeds the iteration: in the mixed form it is evaluated in float, the precision of its first phase)

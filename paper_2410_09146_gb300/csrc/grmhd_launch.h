@@ -38,6 +38,14 @@ struct FormLaunchers {
   // batched re-derivation of the hydro state of floored cells
   cudaError_t (*batch_floors)(const BlockDesc* b, int nblocks, const BatchArgs& a, int metric, int grid,
                               cudaStream_t s);
+  // face-centred CT (grmhd_face_ct.cuh): cell-centred and upwind edge EMFs, the Stokes update of the
+  // faces, the cell field from the faces, the periodic fill of the face arrays
+  cudaError_t (*emf_face)(const DevParams& p, const void* P, const void* Fx, const void* Fy, const void* Fz,
+                          void* Ecc, void* E, cudaStream_t s);
+  cudaError_t (*face_update)(const DevParams& p, const double* Bf0, const double* Bfc, double* Bfn, const void* E,
+                             const StageArgs& a, cudaStream_t s);
+  cudaError_t (*face_to_cells)(const DevParams& p, const double* Bf, void* P, cudaStream_t s);
+  cudaError_t (*ghost_faces)(const DevParams& p, double* Bf, cudaStream_t s);
 };
 
 const FormLaunchers& fp64_launchers();

@@ -1,6 +1,7 @@
 // Mixed form of the stage kernels: reconstruction, Riemann fluxes, EMFs and sources in float with
 // P stored in float; the state accumulation and con2prim stay in double (inside k_update).
 #include "grmhd_kernels.cuh"
+#include "grmhd_face_ct.cuh"
 #include "grmhd_launch.h"
 #include "grmhd_batch_launch.cuh"
 
@@ -100,9 +101,11 @@ cudaError_t geometry(const DevParams& p, double* geo, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+using FC = FaceCtLaunch<R, T>;
 using BL = BatchLaunch<float, float>;
 const FormLaunchers kMixed = {ghost, flux, emf, update, cell_passes, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
-                                BL::deferred, BL::ctas_per_sm, 4, 4, geometry, BL::floors};
+                                BL::deferred, BL::ctas_per_sm, 4, 4, geometry, BL::floors,
+                                FC::emf, FC::faces, FC::to_cells, FC::ghost_faces};
 
 }  // namespace
 

@@ -19,11 +19,13 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "grmhd.h")
 GRMHD_OK, GRMHD_E_INVALID, GRMHD_E_CUDA, GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED = 0, -1, -2, -3, -4
 GRMHD_HOST, GRMHD_DEVICE = 0, 1
 GRMHD_GET_PRIMS, GRMHD_GET_CONS, GRMHD_GET_STATUS, GRMHD_GET_STATS, GRMHD_GET_DT = 0, 1, 2, 3, 4
+GRMHD_GET_FACE_B = 5
 RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3}
 RIEMANN = {"llf": 0, "hll": 1}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
 BC = {"periodic": 0, "fixed": 1}
 PRECISION = {"fp64": 0, "mixed": 1}
+CT = {"flux": 0, "face": 1}
 ST_RHO_FLOOR, ST_EPS_FLOOR, ST_W_CAP, ST_NOT_CONVERGED, ST_BAD_INPUT = 1, 2, 4, 8, 16
 GRMHD_MLP_NPARAM, GRMHD_MLP_NNORM = 9026, 20
 GRMHD_GUESS_FP32 = 1
@@ -42,7 +44,7 @@ class grmhd_params(ctypes.Structure):
         ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("precision", ctypes.c_int), ("bc", ctypes.c_int),
         ("rho_floor0", ctypes.c_double), ("eps_floor0", ctypes.c_double), ("floor_r_exp", ctypes.c_double),
         ("w_max", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_max_iter", ctypes.c_int),
-        ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double),
+        ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double), ("ct", ctypes.c_int),
     ]
 
 
@@ -73,6 +75,7 @@ def lib():
         L.grmhd_create.argtypes = [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
         L.grmhd_set_prims.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_set_cons.argtypes = [vp, vp, ctypes.c_int]
+        L.grmhd_set_face_b.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_stage.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.grmhd_rk2_step.argtypes = [vp, ctypes.c_double]
         L.grmhd_c2p.argtypes = [vp, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int]
@@ -124,6 +127,7 @@ def params(setup) -> grmhd_params:
     p.rho_floor0, p.eps_floor0, p.floor_r_exp, p.w_max = (setup.rho_floor0, setup.eps_floor0, setup.floor_r_exp,
                                                           setup.w_max)
     p.c2p_tol, p.c2p_max_iter, p.cfl, p.weno_eps = setup.c2p_tol, setup.c2p_max_iter, setup.cfl, setup.weno_eps
+    p.ct = CT[getattr(setup, "ct", "flux")]
     return p
 
 
@@ -162,6 +166,11 @@ def grmhd_set_prims(ctx: int, P) -> None:
 def grmhd_set_cons(ctx: int, U) -> None:
     ptr, where = _ptr(U)
     _check(lib().grmhd_set_cons(ctx, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_set_face_b(ctx: int, Bf) -> None:
+    ptr, where = _ptr(Bf)
+    _check(lib().grmhd_set_face_b(ctx, ctypes.c_void_p(ptr), where), ctx)
 
 
 def grmhd_stage(ctx: int, g0: float, g1: float, beta: float, dt: float) -> None:
@@ -407,6 +416,9 @@ class Context:
     def set_cons(self, U):
         grmhd_set_cons(self.ctx, U)
 
+    def set_face_b(self, Bf):
+        grmhd_set_face_b(self.ctx, Bf)
+
     def stage(self, g0, g1, beta, dt=0.0):
         grmhd_stage(self.ctx, g0, g1, beta, dt)
 
@@ -417,7 +429,7 @@ class Context:
         s = self.setup
         shapes = {GRMHD_GET_PRIMS: (s.prim_shape(), np.float64), GRMHD_GET_CONS: (s.cons_shape(), np.float64),
                   GRMHD_GET_STATUS: (s.cons_shape()[1:], np.uint8), GRMHD_GET_STATS: ((8,), np.uint64),
-                  GRMHD_GET_DT: ((1,), np.float64)}
+                  GRMHD_GET_DT: ((1,), np.float64), GRMHD_GET_FACE_B: ((3,) + s.prim_shape()[1:], np.float64)}
         if out is None:
             shape, dt = shapes[what]
             out = np.empty(shape, dt)
@@ -438,6 +450,9 @@ class Context:
 
     def dt(self):
         return float(self.get(GRMHD_GET_DT)[0])
+
+    def face_b(self):
+        return self.get(GRMHD_GET_FACE_B)
 
     def set_timing(self, on=True):
         grmhd_set_timing(self.ctx, on)

@@ -59,6 +59,7 @@ class Setup:
     cfl: float = 0.4
     weno_eps: float = 1e-26
     precision: str = "fp64"            # "fp64" | "mixed"
+    ct: str = "flux"                   # "flux" (Toth flux-CT, cell field) | "face" (face-centred upwind CT)
 
     @property
     def ghosted(self):

@@ -29,7 +29,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3}
+RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3, "mp5": 4}
 RIEMANN = {"llf": 0, "hll": 1}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
 BC = {"periodic": 0, "fixed": 1}

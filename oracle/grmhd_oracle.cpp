@@ -13,7 +13,7 @@
 //             (Lorentz factor), (b-B relations), (T^{mu nu}), (primitive vector)
 //   Sec. 2.3  analytic metric and its derivatives (Cartesian Kerr-Schild)
 //   Sec. 3.1  second-order FV, Toth flux-CT on cell-centred B, LLF / HLL,
-//             constant / PLM (minmod, MC) / WENO5-Z-AOAH reconstruction,
+//             constant / PLM (minmod, MC) / WENO5-Z-AOAH / MP5 reconstruction,
 //             Kastaun et al. (2021) con2prim
 //   Sec. 5    face-centred constrained transport (named there as planned work; the
 //             scheme is the upwind CT of Gardiner & Stone 2005, see stage_impl)
@@ -44,7 +44,7 @@ typedef struct {
   double spin;           // a/M
   double mass;           // M
   double gamma_eos;      // ideal-gas adiabatic index
-  int recon;             // 0 constant, 1 PLM minmod, 2 PLM MC, 3 WENO5-Z-AOAH
+  int recon;             // 0 constant, 1 PLM minmod, 2 PLM MC, 3 WENO5-Z-AOAH, 4 MP5
   int riemann;           // 0 LLF, 1 HLL
   int bc;                // 0 periodic, 1 fixed ghosts
   double rho_floor0;     // rho_flr = rho_floor0 * r^-floor_r_exp (KS) or rho_floor0 (Minkowski)
@@ -355,12 +355,52 @@ static double weno_sigma_side(const double w[3]) {
   return 3.0 * w[0] * w[1] * w[2] / (g2 * w[0] * w[1] + g1 * w[0] * w[2] + g0 * w[1] * w[2]);
 }
 
+// MP5 (Sec. 3.1 names the fifth-order monotonicity-preserving scheme of Suresh & Huynh 1997,
+// J. Comput. Phys. 136, 83, without formulas): value at the right face of the centre cell of
+// f[0..4] = f_{j-2..j+2}. The fifth-order interpolant is kept when it lies between f_j and the
+// monotonicity-preserving bound f_j + minmod(f_{j+1} - f_j, alpha (f_j - f_{j-1})); otherwise it is
+// moved to the nearest end of the accuracy-preserving interval, whose ends combine the upper and
+// middle limits with the large-curvature limits built from the limited second differences d^M4.
+// Readings: alpha = 4 and the 4/3 curvature weight of the published scheme; the acceptance test is
+// (v - f_j)(v - f_MP) <= 0 (no absolute epsilon, so the test does not depend on the data's scale).
+static double minmod2(double a, double b) { return 0.5 * (sgn(a) + sgn(b)) * std::min(std::fabs(a), std::fabs(b)); }
+
+static double minmod4(double w, double x, double y, double z) {
+  const double s = 0.125 * (sgn(w) + sgn(x)) * std::fabs((sgn(w) + sgn(y)) * (sgn(w) + sgn(z)));
+  return s * std::min(std::min(std::fabs(w), std::fabs(x)), std::min(std::fabs(y), std::fabs(z)));
+}
+
+static double mp5_face(const double* f) {
+  const double alpha = 4.0;
+  const double v = (2.0 * f[0] - 13.0 * f[1] + 47.0 * f[2] + 27.0 * f[3] - 3.0 * f[4]) / 60.0;
+  const double vmp = f[2] + minmod2(f[3] - f[2], alpha * (f[2] - f[1]));
+  if ((v - f[2]) * (v - vmp) <= 0.0) return v;
+  const double dm = f[0] - 2.0 * f[1] + f[2];  // second differences at j-1, j, j+1
+  const double d0 = f[1] - 2.0 * f[2] + f[3];
+  const double dp = f[2] - 2.0 * f[3] + f[4];
+  const double dhp = minmod4(4.0 * d0 - dp, 4.0 * dp - d0, d0, dp);  // limited curvature at j+1/2
+  const double dhm = minmod4(4.0 * d0 - dm, 4.0 * dm - d0, d0, dm);  // and at j-1/2
+  const double vul = f[2] + alpha * (f[2] - f[1]);                   // upper limit
+  const double vav = 0.5 * (f[2] + f[3]);
+  const double vmd = vav - 0.5 * dhp;                                 // median
+  const double vlc = f[2] + 0.5 * (f[2] - f[1]) + 4.0 / 3.0 * dhm;    // large curvature
+  const double vmin = std::max(std::min(std::min(f[2], f[3]), vmd), std::min(std::min(f[2], vul), vlc));
+  const double vmax = std::min(std::max(std::max(f[2], f[3]), vmd), std::max(std::max(f[2], vul), vlc));
+  return v + minmod2(vmin - v, vmax - v);  // the median of v, vmin, vmax
+}
+
 // Reconstruct the two face values of cell j from f[0..4] = f_{j-2..j+2}.
 // qm = value at x_{j-1/2}, qp = value at x_{j+1/2}.
 static void recon_cell(int method, const double* f, double eps, double& qm, double& qp) {
   const double fj = f[2];
   if (method == 0) {
     qm = qp = fj;
+    return;
+  }
+  if (method == 4) {  // MP5; the j-1/2 face from the mirrored stencil
+    const double fr[5] = {f[4], f[3], f[2], f[1], f[0]};
+    qp = mp5_face(f);
+    qm = mp5_face(fr);
     return;
   }
   const double dm = f[2] - f[1], dp = f[3] - f[2];

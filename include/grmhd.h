@@ -52,6 +52,7 @@ extern "C" {
 #define GRMHD_RECON_PLM_MINMOD 1
 #define GRMHD_RECON_PLM_MC 2
 #define GRMHD_RECON_WENO5Z_AOAH 3
+#define GRMHD_RECON_MP5 4        /* Suresh & Huynh's monotonicity-preserving fifth order (Sec. 3.1) */
 
 #define GRMHD_RIEMANN_LLF 0
 #define GRMHD_RIEMANN_HLL 1

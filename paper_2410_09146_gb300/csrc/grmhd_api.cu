@@ -49,6 +49,7 @@ struct grmhd_ctx {
   int n_items[3];            // flux | EMF | update items at the current tile
   int tile;
   int grid_persist;
+  int grid_flux;             // persistent grid of the batched flux phase
   long long total_cells;
   bool use_graph;
   cudaStream_t cap_stream;
@@ -72,7 +73,7 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   const bool batch_only = p->nx == 0 && p->ny == 0 && p->nz == 0;
   if (!batch_only) {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { snprintf(msg, n, "nx, ny, nz must be >= 1"); return false; }
-    const int need = p->recon == GRMHD_RECON_WENO5Z_AOAH ? 3 : (p->recon == GRMHD_RECON_CONSTANT ? 1 : 2);
+    const int need = p->recon >= GRMHD_RECON_WENO5Z_AOAH ? 3 : (p->recon == GRMHD_RECON_CONSTANT ? 1 : 2);
     if (p->ng < need) { snprintf(msg, n, "ng = %d too small for the reconstruction (needs %d)", p->ng, need); return false; }
     if (p->ng > 16) { snprintf(msg, n, "ng = %d too large", p->ng); return false; }
     for (int d = 0; d < 3; ++d)
@@ -81,7 +82,7 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
     if (cells > 4.0e9) { snprintf(msg, n, "block too large"); return false; }
   }
   if (p->metric != GRMHD_MINKOWSKI && p->metric != GRMHD_KERR_SCHILD) { snprintf(msg, n, "unknown metric"); return false; }
-  if (p->recon < 0 || p->recon > 3) { snprintf(msg, n, "unknown reconstruction"); return false; }
+  if (p->recon < 0 || p->recon > 4) { snprintf(msg, n, "unknown reconstruction"); return false; }
   if (p->riemann != GRMHD_RIEMANN_LLF && p->riemann != GRMHD_RIEMANN_HLL) { snprintf(msg, n, "unknown Riemann solver"); return false; }
   if (p->precision != GRMHD_FP64 && p->precision != GRMHD_MIXED) { snprintf(msg, n, "unknown precision"); return false; }
   if (p->bc != GRMHD_BC_PERIODIC && p->bc != GRMHD_BC_FIXED) { snprintf(msg, n, "unknown boundary condition"); return false; }
@@ -181,14 +182,14 @@ cudaError_t collect_timing(grmhd_ctx* c) {
 constexpr int kMinTile = 128;
 
 // Units per work item of a phase: `tile` faces / edges / cells; for the run units of the cell-centric
-// WENO fluxes (~FLUX_RUN faces each) tile / FLUX_RUN of them, at least 128 so that a CTA is filled.
-// The x units of the WENO fluxes are lanes of whole warps: their items hold a multiple of 32 of them.
+// five-point fluxes (~FLUX_RUN faces each) tile / FLUX_RUN of them, at least 128 so that a CTA is filled.
+// The x units of those fluxes are lanes of whole warps: their items hold a multiple of 32 of them.
 int phase_tile(const DevParams& p, int tile, int phase) {
-  if ((phase == 1 || phase == 2) && p.recon == RECON_WENO5Z) {
+  if ((phase == 1 || phase == 2) && cell_centric(p.recon)) {
     const int t = tile / FLUX_RUN;
     return t < 128 ? 128 : t;
   }
-  if (phase == 0 && p.recon == RECON_WENO5Z) return (tile + 31) / 32 * 32;
+  if (phase == 0 && cell_centric(p.recon)) return (tile + 31) / 32 * 32;
   return tile;
 }
 
@@ -568,7 +569,8 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   const WorkItem* emf_items = flux_items + c->n_items[0];
   const WorkItem* upd_items = emf_items + c->n_items[1];
   const int grid = c->grid_persist;
-  CK(L.batch_flux(c->dblocks, flux_items, c->n_items[0], ctr + 0, ms, track ? 1 : 0, c->prm.metric, c->prm.recon, grid, s),
+  CK(L.batch_flux(c->dblocks, flux_items, c->n_items[0], ctr + 0, ms, track ? 1 : 0, c->prm.metric, c->prm.recon,
+                   c->grid_flux, s),
      "batched flux");
   if (track) CK(launch_batch_finalize_dt(ms, (double*)(c->scal + 3), c->prm.cfl, s), "time step");
   CK(L.batch_emf(c->dblocks, emf_items, c->n_items[1], ctr + 1, grid, s), "batched EMF");
@@ -799,6 +801,7 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   c->grid_persist = (sms > 0 ? sms : 152) * c->L->batch_ctas_per_sm(p->metric);
+  c->grid_flux = (sms > 0 ? sms : 152) * c->L->batch_flux_ctas_per_sm(p->metric, p->recon);
   cudaError_t e = cudaMemsetAsync(c->ws, 0, l.total, c->stream);
   for (int b = 0; b < nblocks && e == cudaSuccess; ++b)
     if (c->hblocks[b].p.geo) e = c->L->geometry(c->hblocks[b].p, (double*)c->hblocks[b].p.geo, c->stream);

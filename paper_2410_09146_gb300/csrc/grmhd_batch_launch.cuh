@@ -16,6 +16,7 @@ struct BatchLaunch {
       case RECON_PLM_MINMOD: k_batch_flux<R, T, METRIC, RECON_PLM_MINMOD><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
       case RECON_PLM_MC: k_batch_flux<R, T, METRIC, RECON_PLM_MC><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
       case RECON_WENO5Z: k_batch_flux<R, T, METRIC, RECON_WENO5Z><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
+      case RECON_MP5: k_batch_flux<R, T, METRIC, RECON_MP5><<<grid, 128, 0, s>>>(b, it, n, ctr, ms, track); break;
       default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -54,6 +55,24 @@ struct BatchLaunch {
     return cudaGetLastError();
   }
   // CTAs per SM of the persistent kernels (occupancy of the update kernel, the heaviest)
+  template <int METRIC>
+  static int flux_ctas_m(int recon) {
+    int n = 0;
+    switch (recon) {
+      case RECON_CONSTANT: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_flux<R, T, METRIC, RECON_CONSTANT>, 128, 0); break;
+      case RECON_PLM_MINMOD: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_flux<R, T, METRIC, RECON_PLM_MINMOD>, 128, 0); break;
+      case RECON_PLM_MC: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_flux<R, T, METRIC, RECON_PLM_MC>, 128, 0); break;
+      case RECON_WENO5Z: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_flux<R, T, METRIC, RECON_WENO5Z>, 128, 0); break;
+      case RECON_MP5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_flux<R, T, METRIC, RECON_MP5>, 128, 0); break;
+      default: break;
+    }
+    return n > 0 ? n : 1;
+  }
+  // resident CTAs per SM of the batched flux kernel (its persistent grid is sized from this, the other
+  // phases' grid from the update kernel's)
+  static int flux_ctas_per_sm(int metric, int recon) {
+    return metric == KERR_SCHILD ? flux_ctas_m<KERR_SCHILD>(recon) : flux_ctas_m<MINKOWSKI>(recon);
+  }
   static int ctas_per_sm(int metric) {
     int n = 0;
     if (metric == KERR_SCHILD)

@@ -14,7 +14,10 @@
 namespace grmhd {
 
 enum { MINKOWSKI = 0, KERR_SCHILD = 1 };
-enum { RECON_CONSTANT = 0, RECON_PLM_MINMOD = 1, RECON_PLM_MC = 2, RECON_WENO5Z = 3 };
+enum { RECON_CONSTANT = 0, RECON_PLM_MINMOD = 1, RECON_PLM_MC = 2, RECON_WENO5Z = 3, RECON_MP5 = 4 };
+
+// Five-point reconstructions (WENO5-Z-AOAH, MP5) run on the cell-centric flux path.
+__host__ __device__ constexpr bool cell_centric(int recon) { return recon == RECON_WENO5Z || recon == RECON_MP5; }
 enum { RIEMANN_LLF = 0, RIEMANN_HLL = 1 };
 enum { ST_RHO_FLOOR = 1, ST_EPS_FLOOR = 2, ST_W_CAP = 4, ST_NOT_CONVERGED = 8, ST_BAD_INPUT = 16 };
 enum { NV = 8 };
@@ -373,11 +376,54 @@ __device__ __forceinline__ R weno_sigma_side(const R w[3]) {
   return R(3) * w[0] * w[1] * w[2] / (R(0.3) * w[0] * w[1] + R(0.6) * w[0] * w[2] + R(0.1) * w[1] * w[2]);
 }
 
+// MP5 (Sec. 3.1; the monotonicity-preserving scheme of Suresh & Huynh 1997): value at the upper face of the
+// centre cell of (f0..f4). The fifth-order interpolant is kept when it lies between f2 and the
+// monotonicity-preserving bound f2 + minmod(f3 - f2, 4 (f2 - f1)); otherwise it is moved to the nearest
+// end of the accuracy-preserving interval built from the upper, median and large-curvature limits with
+// the limited second differences d^M4. Acceptance test (v - f2)(v - v_MP) <= 0, alpha = 4.
+template <class R>
+__device__ __forceinline__ R sgn1(R a) {
+  return a > R(0) ? R(1) : (a < R(0) ? R(-1) : R(0));
+}
+
+template <class R>
+__device__ __forceinline__ R minmod2(R a, R b) {
+  return R(0.5) * (sgn1(a) + sgn1(b)) * fmin(fabs(a), fabs(b));
+}
+
+template <class R>
+__device__ __forceinline__ R minmod4(R w, R x, R y, R z) {
+  const R sw = sgn1(w);
+  const R s = R(0.125) * (sw + sgn1(x)) * fabs((sw + sgn1(y)) * (sw + sgn1(z)));
+  return s * fmin(fmin(fabs(w), fabs(x)), fmin(fabs(y), fabs(z)));
+}
+
+template <class R>
+__device__ __forceinline__ R mp5_face(R f0, R f1, R f2, R f3, R f4) {
+  const R alpha = R(4);
+  const R v = (R(2) * f0 - R(13) * f1 + R(47) * f2 + R(27) * f3 - R(3) * f4) / R(60);
+  const R vmp = f2 + minmod2(f3 - f2, alpha * (f2 - f1));
+  if ((v - f2) * (v - vmp) <= R(0)) return v;
+  const R dm = f0 - R(2) * f1 + f2, d0 = f1 - R(2) * f2 + f3, dp = f2 - R(2) * f3 + f4;
+  const R dhp = minmod4(R(4) * d0 - dp, R(4) * dp - d0, d0, dp);
+  const R dhm = minmod4(R(4) * d0 - dm, R(4) * dm - d0, d0, dm);
+  const R vul = f2 + alpha * (f2 - f1);
+  const R vav = R(0.5) * (f2 + f3);
+  const R vmd = vav - R(0.5) * dhp;
+  const R vlc = f2 + R(0.5) * (f2 - f1) + R(4) / R(3) * dhm;
+  const R vmin = fmax(fmin(fmin(f2, f3), vmd), fmin(fmin(f2, vul), vlc));
+  const R vmax = fmin(fmax(fmax(f2, f3), vmd), fmax(fmax(f2, vul), vlc));
+  return v + minmod2(vmin - v, vmax - v);
+}
+
 // Face values of the centre cell c = f[2]: qm at its lower face, qp at its upper face.
 template <class R, int RECON>
 __device__ __forceinline__ void recon_cell(R f0, R f1, R f2, R f3, R f4, R eps, R& qm, R& qp) {
   if (RECON == RECON_CONSTANT) {
     qm = qp = f2;
+  } else if (RECON == RECON_MP5) {  // the lower face from the mirrored stencil
+    qp = mp5_face<R>(f0, f1, f2, f3, f4);
+    qm = mp5_face<R>(f4, f3, f2, f1, f0);
   } else if (RECON == RECON_PLM_MINMOD || RECON == RECON_PLM_MC) {
     const R s = RECON == RECON_PLM_MC ? mc_slope(f2 - f1, f3 - f2) : minmod_slope(f2 - f1, f3 - f2);
     qm = f2 - R(0.5) * s;
@@ -476,11 +522,11 @@ __host__ __device__ __forceinline__ int flux_run_length(int nd) {
 constexpr int FLUX_WARP_FACES = 31;
 
 __host__ __device__ __forceinline__ long long flux_units(const DevParams& p, int d) {
-  if (p.recon == RECON_WENO5Z && d == 0) {
+  if (cell_centric(p.recon) && d == 0) {
     const long long cells = (long long)(p.ny + 2) * (p.nz + 2) * (p.nx + 2);
     return (cells + FLUX_WARP_FACES - 1) / FLUX_WARP_FACES * 32;
   }
-  if (p.recon == RECON_WENO5Z) {
+  if (cell_centric(p.recon)) {
     const int nd = d == 0 ? p.nx : (d == 1 ? p.ny : p.nz);
     const int na = d == 0 ? p.ny : p.nx, nb = d == 2 ? p.ny : p.nz;
     return (long long)(na + 2) * (nb + 2) * flux_runs(nd);

@@ -21,7 +21,10 @@ cudaError_t flux_m(const DevParams& p, const T* P, R* F, unsigned long long* ms,
     case RECON_PLM_MINMOD: k_flux<R, T, METRIC, RECON_PLM_MINMOD><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
     case RECON_PLM_MC: k_flux<R, T, METRIC, RECON_PLM_MC><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
     case RECON_WENO5Z:  // cell-centric: each cell reconstructed once per direction
-      k_flux_cc<R, T, METRIC><<<grid_for(flux_units(p, d), 128), 128, 0, s>>>(P, F, ms, p, d, track);
+      k_flux_cc<R, T, METRIC, RECON_WENO5Z><<<grid_for(flux_units(p, d), 128), 128, 0, s>>>(P, F, ms, p, d, track);
+      break;
+    case RECON_MP5:
+      k_flux_cc<R, T, METRIC, RECON_MP5><<<grid_for(flux_units(p, d), 128), 128, 0, s>>>(P, F, ms, p, d, track);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -101,7 +104,8 @@ using FC = FaceCtLaunch<R, T>;
 using BL = BatchLaunch<double, double>;
 const FormLaunchers kFp64 = {ghost, flux, emf, update, cell_passes, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
                                 BL::deferred, BL::ctas_per_sm, 8, 8, geometry, BL::floors,
-                                FC::emf, FC::faces, FC::to_cells, FC::ghost_faces};
+                                FC::emf, FC::faces, FC::to_cells, FC::ghost_faces,
+                                BL::flux_ctas_per_sm};
 
 }  // namespace
 

@@ -94,12 +94,12 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const T* Pq = P + q * p.gsize + g;
-    const R fm3 = RECON == RECON_WENO5Z ? R(Pq[-3 * stride]) : R(0);
+    const R fm3 = cell_centric(RECON) ? R(Pq[-3 * stride]) : R(0);
     const R fm2 = RECON != RECON_CONSTANT ? R(Pq[-2 * stride]) : R(0);
     const R fm1 = R(Pq[-stride]);
     const R f0 = R(Pq[0]);
     const R fp1 = RECON != RECON_CONSTANT ? R(Pq[stride]) : R(0);
-    const R fp2 = RECON == RECON_WENO5Z ? R(Pq[2 * stride]) : R(0);
+    const R fp2 = cell_centric(RECON) ? R(Pq[2 * stride]) : R(0);
     R qm, qp;
     recon_cell<R, RECON>(fm3, fm2, fm1, f0, fp1, eps, qm, qp);  // cell c - e_d
     PL[q] = qp;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
 // each cell is reconstructed once (both of its faces), and face f pairs the plus side of cell f - 1 with
 // the minus side of cell f (face_flux, as in the face-centric flux_face). Returns max |lambda| over the
 // run's interior faces.
-template <class R, class T, int METRIC>
+template <class R, class T, int METRIC, int RECON>
 __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ P, R* __restrict__ F, int d,
                                       long long t) {
   // transverse coordinates: a fastest (x for d = 1, 2; y for d = 0), b the other
@@ -188,7 +188,7 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     R qm, qp;
-    recon_cell<R, RECON_WENO5Z>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
+    recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
     PL[q] = qp;
     cL[q] = w[q][2];
   }
@@ -202,7 +202,7 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
       for (int s = 0; s < 4; ++s) w[q][s] = w[q][s + 1];
       w[q][4] = R(P[q * p.gsize + g + 2 * sd]);
       R qm, qp;
-      recon_cell<R, RECON_WENO5Z>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
+      recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
       PR[q] = qm;
       QP[q] = qp;
       cR[q] = w[q][2];
@@ -227,7 +227,7 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
 // the cell is not the first of its row, evaluates the face between it and the previous cell with that
 // cell's plus side from lane l - 1. Units come in whole, aligned warps (every lane of the warp takes part in
 // the shuffles). Returns max |lambda| of the lane's face when interior, 0 otherwise.
-template <class R, class T, int METRIC>
+template <class R, class T, int METRIC, int RECON>
 __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__ P, R* __restrict__ F,
                                        long long t) {
   const int lane = (int)(t & 31);
@@ -246,7 +246,7 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
     R f[5];
 #pragma unroll
     for (int s = 0; s < 5; ++s) f[s] = live ? R(Pq[s - 2]) : R(0);
-    recon_cell<R, RECON_WENO5Z>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
+    recon_cell<R, RECON>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
     cc[q] = f[2];
   }
   R PL[NV], cL[NV];
@@ -263,15 +263,21 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
   return (j >= 0 && j < p.ny && k >= 0 && k < p.nz) ? cm : R(0);
 }
 
-template <class R, class T, int METRIC>
-__global__ void __launch_bounds__(128) k_flux_cc(const T* __restrict__ P, R* __restrict__ F,
+// Resident CTAs per SM the float cell-centric flux kernels are compiled for: 8 x 128 threads at 64
+// registers, the best of the occupancy / spill trade-off measured at 256^3 (the loads of the P window are
+// latency-bound; the double form is bound by FP64 issue and keeps its registers).
+template <class R>
+constexpr int kFluxMinBlocks = sizeof(R) == 4 ? 8 : 1;
+
+template <class R, class T, int METRIC, int RECON>
+__global__ void __launch_bounds__(128, kFluxMinBlocks<R>) k_flux_cc(const T* __restrict__ P, R* __restrict__ F,
                                                  unsigned long long* __restrict__ ms, DevParams p, int d,
                                                  int track_speed) {
   const long long total = flux_units(p, d);
   R cm_local = R(0);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const R cm = d == 0 ? flux_lane<R, T, METRIC>(p, P, F, t) : flux_run<R, T, METRIC>(p, P, F, d, t);
+    const R cm = d == 0 ? flux_lane<R, T, METRIC, RECON>(p, P, F, t) : flux_run<R, T, METRIC, RECON>(p, P, F, d, t);
     if (cm > cm_local) cm_local = cm;
   }
   if (track_speed) block_max_to<R>(cm_local, ms + d);
@@ -721,7 +727,7 @@ __device__ __forceinline__ StageArgs block_stage_args(const BlockDesc& b, const 
 
 // Fluxes of every direction of every block; ms[0] collects max |lambda| / dx over the batch.
 template <class R, class T, int METRIC, int RECON>
-__global__ void __launch_bounds__(128) k_batch_flux(const BlockDesc* __restrict__ blocks,
+__global__ void __launch_bounds__(128, kFluxMinBlocks<R>) k_batch_flux(const BlockDesc* __restrict__ blocks,
                                                     const WorkItem* __restrict__ items, int nitems,
                                                     unsigned int* counter, unsigned long long* ms, int track_speed) {
   R cm_local = R(0);
@@ -732,12 +738,12 @@ __global__ void __launch_bounds__(128) k_batch_flux(const BlockDesc* __restrict_
     const BlockDesc& b = blocks[w.block];
     const R idx = R(b.p.idx[w.phase]);
     for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
-      // units of flux_units: runs of faces for WENO5-Z-AOAH (cell-centric), single faces otherwise
-      const R cm = (RECON != RECON_WENO5Z
+      // units of flux_units: runs of faces for the five-point reconstructions (cell-centric), single faces otherwise
+      const R cm = (!cell_centric(RECON)
                         ? flux_face<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase, w.start + k)
-                        : (w.phase == 0 ? flux_lane<R, T, METRIC>(b.p, (const T*)b.P, (R*)b.F[0], w.start + k)
-                                        : flux_run<R, T, METRIC>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase,
-                                                                 w.start + k))) *
+                        : (w.phase == 0 ? flux_lane<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[0], w.start + k)
+                                        : flux_run<R, T, METRIC, RECON>(b.p, (const T*)b.P, (R*)b.F[w.phase], w.phase,
+                                                                        w.start + k))) *
                    idx;
       if (cm > cm_local) cm_local = cm;
     }

@@ -46,6 +46,8 @@ struct FormLaunchers {
                              const StageArgs& a, cudaStream_t s);
   cudaError_t (*face_to_cells)(const DevParams& p, const double* Bf, void* P, cudaStream_t s);
   cudaError_t (*ghost_faces)(const DevParams& p, double* Bf, cudaStream_t s);
+  // resident CTAs per SM of the batched flux kernel (metric, recon)
+  int (*batch_flux_ctas_per_sm)(int metric, int recon);
 };
 
 const FormLaunchers& fp64_launchers();

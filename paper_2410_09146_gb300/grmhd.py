@@ -20,7 +20,7 @@ GRMHD_OK, GRMHD_E_INVALID, GRMHD_E_CUDA, GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED 
 GRMHD_HOST, GRMHD_DEVICE = 0, 1
 GRMHD_GET_PRIMS, GRMHD_GET_CONS, GRMHD_GET_STATUS, GRMHD_GET_STATS, GRMHD_GET_DT = 0, 1, 2, 3, 4
 GRMHD_GET_FACE_B = 5
-RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3}
+RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3, "mp5": 4}
 RIEMANN = {"llf": 0, "hll": 1}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
 BC = {"periodic": 0, "fixed": 1}

@@ -44,9 +44,9 @@ def _run(G, setups, prims, graph=False, tile=None, steps=2, dt=0.02):
             for b in range(len(setups))]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_matches_single_blocks(G, precision):
-    setups, prims = _blocks(precision)
+@pytest.mark.parametrize("precision,recon", [("fp64", "weno5z_aoah"), ("mixed", "weno5z_aoah"), ("mixed", "mp5")])
+def test_batch_matches_single_blocks(G, precision, recon):
+    setups, prims = _blocks(precision, recon)
     ref = []
     for s, P in zip(setups, prims):
         c = G.Context(s)

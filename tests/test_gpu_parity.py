@@ -98,7 +98,7 @@ def test_c2p_batch_parity(G, orc):
 
 @pytest.mark.parametrize("n3,recon,riemann", [((16, 16, 16), "plm_mc", "llf"), ((13, 7, 5), "plm_mc", "llf"),
                                                ((12, 10, 9), "weno5z_aoah", "hll"), ((9, 9, 9), "plm_minmod", "hll"),
-                                               ((8, 6, 5), "constant", "llf")])
+                                               ((8, 6, 5), "constant", "llf"), ((11, 9, 7), "mp5", "hll")])
 def test_stage_linear_wave_parity(G, orc, n3, recon, riemann):
     gw = json.load(open(GOLDEN))
     s = I.linear_wave_setup(n3[0], n3[1], n3[2], recon=recon, riemann=riemann)
@@ -107,7 +107,7 @@ def test_stage_linear_wave_parity(G, orc, n3, recon, riemann):
     assert worst["floored_frac"] == 0.0
 
 
-@pytest.mark.parametrize("n,recon", [(16, "weno5z_aoah"), (12, "plm_mc")])
+@pytest.mark.parametrize("n,recon", [(16, "weno5z_aoah"), (12, "plm_mc"), (12, "mp5")])
 def test_stage_kerr_schild_parity(G, orc, n, recon):
     s = I.kerr_schild_setup(n, recon=recon, riemann="hll")
     P = I.kerr_schild_random_prims(s, seed=1)

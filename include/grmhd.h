@@ -286,7 +286,8 @@ int grmhd_stage_noalloc(const grmhd_params* p, double* P, const double* U0, cons
 /* ---- Batches of meshblocks (many uneven blocks advanced together) ----
  * A batch holds nblocks independent meshblocks that share the physics options of `p` (its nx..nz,
  * x0, dx fields are ignored; each block brings its own). Ghost zones are taken as given
- * (p->bc must be GRMHD_BC_FIXED; the exchange between blocks is not part of the stage). grmhd_stage and
+ * (p->bc must be GRMHD_BC_FIXED), unless grmhd_batch_set_lattice declares the blocks a lattice, whose
+ * ghosts are then exchanged on the device at the start of every stage. grmhd_stage and
  * grmhd_rk2_step advance every block: each phase (fluxes of all directions, EMFs, cell update, deferred
  * con2prim) is one persistent launch whose CTAs take fixed-size work items (`tile` faces, edges or
  * cells of one block) from a device counter. With dt <= 0 the CFL step is the minimum over the batch. */
@@ -304,6 +305,16 @@ size_t grmhd_batch_workspace_bytes(const grmhd_params* p, int nblocks, const grm
  * GRMHD_E_CUDA. */
 int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* blocks, void* workspace, size_t bytes,
                        void* stream, grmhd_ctx** out);
+
+/* Declare that the batch's blocks tile an nbx x nby x nbz lattice of one meshblock grid: block b sits at
+ * lattice position (b % nbx, (b / nbx) % nby, b / (nbx nby)); all blocks have the same cell counts and
+ * widths and block b's interior corner is block 0's plus its lattice position times the block size.
+ * Every later stage then starts with a same-level ghost exchange on the device: each ghost cell of each
+ * block takes the primitives of the cell with the same global index in the block that owns it (across
+ * the lattice edge: wrapped when `periodic`, else kept as loaded -- a fixed outer boundary). The result
+ * is the stage of the one large block the lattice tiles. (0, 0, 0) switches the exchange off.
+ * Errors: GRMHD_E_INVALID (not a batch, block count, sizes, widths or corners off the lattice). */
+int grmhd_batch_set_lattice(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic);
 
 /* Load one block's primitives (double, [8][nz+2ng][ny+2ng][nx+2ng]) and derive its conserved state;
  * every block must be loaded before the first stage. */

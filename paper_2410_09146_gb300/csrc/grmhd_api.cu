@@ -1,6 +1,7 @@
 // C-ABI entry points of libgrmhd.so (declared and documented in include/grmhd.h).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -50,7 +51,10 @@ struct grmhd_ctx {
   int tile;
   int grid_persist;
   int grid_flux;             // persistent grid of the batched flux phase
+  bool lattice_on;           // the blocks tile a lattice: ghosts exchanged at the start of every stage
+  Lattice lattice;
   long long total_cells;
+  long long total_ghosted;   // nblocks x gsize of block 0 (meaningful for lattices, whose blocks are equal)
   bool use_graph;
   cudaStream_t cap_stream;
   std::map<std::vector<double>, cudaGraphExec_t> graphs;
@@ -569,6 +573,8 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   const WorkItem* emf_items = flux_items + c->n_items[0];
   const WorkItem* upd_items = emf_items + c->n_items[1];
   const int grid = c->grid_persist;
+  if (c->lattice_on)
+    CK(L.batch_exchange(c->dblocks, c->nblocks, c->total_ghosted, c->lattice, s), "ghost exchange");
   CK(L.batch_flux(c->dblocks, flux_items, c->n_items[0], ctr + 0, ms, track ? 1 : 0, c->prm.metric, c->prm.recon,
                    c->grid_flux, s),
      "batched flux");
@@ -797,6 +803,8 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
     off += d.p.isize;
   }
   c->total_cells = off;
+  c->total_ghosted = (long long)nblocks * c->hblocks[0].p.gsize;
+  c->lattice_on = false;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -833,6 +841,38 @@ int grmhd_batch_set_tile(grmhd_ctx* c, int tile) {
      "uploading work items");
   CK(cudaStreamSynchronize(c->stream), "synchronising");
   c->tile = tile;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  return GRMHD_OK;
+}
+
+int grmhd_batch_set_lattice(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "not a batch context") : GRMHD_E_INVALID;
+  if (nbx == 0 && nby == 0 && nbz == 0) {
+    c->lattice_on = false;
+  } else {
+    if (nbx < 1 || nby < 1 || nbz < 1 || (long long)nbx * nby * nbz != c->nblocks)
+      return fail(c, GRMHD_E_INVALID, "the lattice must hold exactly the batch's blocks");
+    const DevParams& a = c->hblocks[0].p;
+    const int nb[3] = {nbx, nby, nbz};
+    for (int b = 0; b < c->nblocks; ++b) {
+      const DevParams& q = c->hblocks[b].p;
+      if (q.nx != a.nx || q.ny != a.ny || q.nz != a.nz) return fail(c, GRMHD_E_INVALID, "lattice blocks differ in size");
+      const int bc[3] = {b % nbx, (b / nbx) % nby, b / (nbx * nby)};
+      const int n[3] = {a.nx, a.ny, a.nz};
+      for (int d = 0; d < 3; ++d) {
+        if (q.dx[d] != a.dx[d]) return fail(c, GRMHD_E_INVALID, "lattice blocks differ in cell width");
+        const double want = a.x0[d] + (double)bc[d] * n[d] * a.dx[d];
+        if (std::fabs(q.x0[d] - want) > 1e-9 * (std::fabs(want) + nb[d] * n[d] * a.dx[d]))
+          return fail(c, GRMHD_E_INVALID, "block corners do not follow the lattice order");
+      }
+    }
+    c->lattice.nb[0] = nbx;
+    c->lattice.nb[1] = nby;
+    c->lattice.nb[2] = nbz;
+    c->lattice.periodic = periodic ? 1 : 0;
+    c->lattice_on = true;
+  }
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
   return GRMHD_OK;

@@ -73,6 +73,10 @@ struct BatchLaunch {
   static int flux_ctas_per_sm(int metric, int recon) {
     return metric == KERR_SCHILD ? flux_ctas_m<KERR_SCHILD>(recon) : flux_ctas_m<MINKOWSKI>(recon);
   }
+  static cudaError_t exchange(const BlockDesc* b, int nblocks, long long ghosted_cells, const Lattice& L, cudaStream_t s) {
+    k_batch_exchange<T><<<grid_for(ghosted_cells, 256), 256, 0, s>>>(b, nblocks, L);
+    return cudaGetLastError();
+  }
   static int ctas_per_sm(int metric) {
     int n = 0;
     if (metric == KERR_SCHILD)

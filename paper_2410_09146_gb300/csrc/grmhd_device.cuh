@@ -96,6 +96,13 @@ struct WorkItem {
   int pad;
 };
 
+// A batch whose blocks, all of the same size, tile an nb[0] x nb[1] x nb[2] lattice: block b sits at
+// lattice position (b % nb[0], (b / nb[0]) % nb[1], b / (nb[0] nb[1])). periodic: the lattice wraps.
+struct Lattice {
+  int nb[3];
+  int periodic;
+};
+
 // Coefficients and bookkeeping shared by every block of a batched stage.
 struct BatchArgs {
   double g0, g1, beta, dt;

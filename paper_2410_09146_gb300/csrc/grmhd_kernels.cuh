@@ -176,24 +176,22 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   int k = d == 2 ? f0 : b;
   const bool inner_t = a >= 0 && a < na && b >= 0 && b < nb;  // interior transverse position
   long long g = gidx(p, i, j, k);
-  // window of cell f0 - 1: cells f0 - 3 .. f0 + 1
+  // Every cell of the run, and the one before it, is reconstructed at the single call site in the loop
+  // below (a second inlined copy could round differently under FMA contraction, making a cell's face
+  // values depend on where runs start). Window before the first iteration: cells f0 - 4 .. f0 with the
+  // first slot unused (it is shifted out before use), so no cell below f0 - 3 is read.
   R w[NV][5];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const T* Pq = P + q * p.gsize + g;
+    w[q][0] = R(0);
 #pragma unroll
-    for (int s = 0; s < 5; ++s) w[q][s] = R(Pq[(s - 3) * sd]);
+    for (int s = 1; s < 5; ++s) w[q][s] = R(Pq[(s - 4) * sd]);
   }
   R PL[NV], cL[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    R qm, qp;
-    recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
-    PL[q] = qp;
-    cL[q] = w[q][2];
-  }
   R cm_run = R(0);
-  for (int f = f0; f < f1; ++f) {
+  g -= sd;  // the cell before the run: f0 - 1
+  for (int f = f0 - 1; f < f1; ++f) {
     // window of cell f: cells f - 2 .. f + 2
     R PR[NV], cR[NV], QP[NV];
 #pragma unroll
@@ -207,17 +205,22 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
       QP[q] = qp;
       cR[q] = w[q][2];
     }
-    R Fh[NV];
-    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
+    if (f >= f0) {
+      R Fh[NV];
+      const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
+      if (inner_t && cm > cm_run) cm_run = cm;
+    }
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      F[q * p.gsize + g] = Fh[q];
       PL[q] = QP[q];
       cL[q] = cR[q];
     }
-    if (inner_t && cm > cm_run) cm_run = cm;
     g += sd;
-    if (d == 0) ++i; else if (d == 1) ++j; else ++k;
+    if (f >= f0) {
+      if (d == 0) ++i; else if (d == 1) ++j; else ++k;
+    }
   }
   return cm_run;
 }
@@ -723,6 +726,46 @@ __device__ __forceinline__ StageArgs block_stage_args(const BlockDesc& b, const 
   s.floorlist = a.floorlist;
   s.fl_count = a.fl_count;
   return s;
+}
+
+// Same-level ghost exchange of a lattice batch: every ghost cell of every block takes the primitives of
+// the cell with the same global index in the block that owns it. Outside the lattice the global index
+// wraps when periodic; otherwise the ghost keeps its value (fixed outer boundary). Sources are interior
+// cells and destinations ghost cells, so the copies never overlap.
+template <class T>
+__global__ void k_batch_exchange(const BlockDesc* __restrict__ blocks, int nblocks, Lattice L) {
+  const DevParams& p0 = blocks[0].p;  // every block of a lattice has the same sizes
+  const long long G = p0.gsize;
+  const int n[3] = {p0.nx, p0.ny, p0.nz};
+  const long long total = (long long)nblocks * G;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / G);
+    const long long g = t - (long long)b * G;
+    const int c[3] = {(int)(g % p0.gx) - p0.ng, (int)((g / p0.gx) % p0.gy) - p0.ng,
+                      (int)(g / ((long long)p0.gx * p0.gy)) - p0.ng};
+    if (c[0] >= 0 && c[0] < n[0] && c[1] >= 0 && c[1] < n[1] && c[2] >= 0 && c[2] < n[2]) continue;
+    const int bc[3] = {b % L.nb[0], (b / L.nb[0]) % L.nb[1], b / (L.nb[0] * L.nb[1])};
+    int src[3], sb[3];
+    bool outside = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long N = (long long)L.nb[d] * n[d];
+      long long gd = (long long)bc[d] * n[d] + c[d];
+      if (gd < 0 || gd >= N) {
+        outside = true;
+        gd = ((gd % N) + N) % N;
+      }
+      sb[d] = (int)(gd / n[d]);
+      src[d] = (int)(gd - (long long)sb[d] * n[d]);
+    }
+    if (outside && !L.periodic) continue;
+    const BlockDesc& S = blocks[sb[0] + L.nb[0] * (sb[1] + L.nb[1] * sb[2])];
+    const T* __restrict__ Ps = (const T*)S.P;
+    T* __restrict__ Pd = (T*)blocks[b].P;
+    const long long gs = gidx(S.p, src[0], src[1], src[2]);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Pd[q * G + g] = Ps[q * G + gs];
+  }
 }
 
 // Fluxes of every direction of every block; ms[0] collects max |lambda| / dx over the batch.

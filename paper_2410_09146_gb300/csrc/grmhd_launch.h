@@ -48,6 +48,9 @@ struct FormLaunchers {
   cudaError_t (*ghost_faces)(const DevParams& p, double* Bf, cudaStream_t s);
   // resident CTAs per SM of the batched flux kernel (metric, recon)
   int (*batch_flux_ctas_per_sm)(int metric, int recon);
+  // same-level ghost exchange of a lattice batch (ghosted_cells = nblocks x the block's gsize)
+  cudaError_t (*batch_exchange)(const BlockDesc* b, int nblocks, long long ghosted_cells, const Lattice& L,
+                                cudaStream_t s);
 };
 
 const FormLaunchers& fp64_launchers();

@@ -91,6 +91,7 @@ def lib():
         L.grmhd_batch_set_prims.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_batch_get.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_batch_set_tile.argtypes = [vp, ctypes.c_int]
+        L.grmhd_batch_set_lattice.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.grmhd_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.grmhd_set_graph.argtypes = [vp, ctypes.c_int]
         fp = ctypes.POINTER(ctypes.c_float)
@@ -293,6 +294,10 @@ def grmhd_batch_create(p: grmhd_params, blocks, workspace_ptr: int, nbytes: int,
     return out.value
 
 
+def grmhd_batch_set_lattice(ctx: int, nbx: int, nby: int, nbz: int, periodic: bool) -> None:
+    _check(lib().grmhd_batch_set_lattice(ctx, nbx, nby, nbz, int(periodic)), ctx)
+
+
 def grmhd_batch_set_prims(ctx: int, block: int, P) -> None:
     ptr, where = _ptr(P)
     _check(lib().grmhd_batch_set_prims(ctx, block, ctypes.c_void_p(ptr), where), ctx)
@@ -378,6 +383,9 @@ class BatchContext:
 
     def set_tile(self, tile):
         grmhd_batch_set_tile(self.ctx, tile)
+
+    def set_lattice(self, nb, periodic):
+        grmhd_batch_set_lattice(self.ctx, nb[0], nb[1], nb[2], periodic)
 
     def autotune(self):
         return grmhd_batch_autotune(self.ctx)

@@ -176,22 +176,30 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   int k = d == 2 ? f0 : b;
   const bool inner_t = a >= 0 && a < na && b >= 0 && b < nb;  // interior transverse position
   long long g = gidx(p, i, j, k);
-  // Every cell of the run, and the one before it, is reconstructed at the single call site in the loop
-  // below (a second inlined copy could round differently under FMA contraction, making a cell's face
-  // values depend on where runs start). Window before the first iteration: cells f0 - 4 .. f0 with the
-  // first slot unused (it is shifted out before use), so no cell below f0 - 3 is read.
+  // The cell before the run is reconstructed before the loop, every other cell inside it. In the float
+  // form the two inlined copies may round differently under FMA contraction, so a cell's face values can
+  // differ in the last bit with where runs start (they move with the block size): the float form is
+  // bitwise reproducible for one block layout, not across layouts. One call site for all cells costs
+  // ~0.45 ms per 256^3 stage (measured), so the faster form is kept; the double form is built without
+  // contraction and does not depend on the layout.
+  // window of cell f0 - 1: cells f0 - 3 .. f0 + 1
   R w[NV][5];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const T* Pq = P + q * p.gsize + g;
-    w[q][0] = R(0);
 #pragma unroll
-    for (int s = 1; s < 5; ++s) w[q][s] = R(Pq[(s - 4) * sd]);
+    for (int s = 0; s < 5; ++s) w[q][s] = R(Pq[(s - 3) * sd]);
   }
   R PL[NV], cL[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    R qm, qp;
+    recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
+    PL[q] = qp;
+    cL[q] = w[q][2];
+  }
   R cm_run = R(0);
-  g -= sd;  // the cell before the run: f0 - 1
-  for (int f = f0 - 1; f < f1; ++f) {
+  for (int f = f0; f < f1; ++f) {
     // window of cell f: cells f - 2 .. f + 2
     R PR[NV], cR[NV], QP[NV];
 #pragma unroll
@@ -205,22 +213,17 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
       QP[q] = qp;
       cR[q] = w[q][2];
     }
-    if (f >= f0) {
-      R Fh[NV];
-      const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
-#pragma unroll
-      for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
-      if (inner_t && cm > cm_run) cm_run = cm;
-    }
+    R Fh[NV];
+    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
+      F[q * p.gsize + g] = Fh[q];
       PL[q] = QP[q];
       cL[q] = cR[q];
     }
+    if (inner_t && cm > cm_run) cm_run = cm;
     g += sd;
-    if (f >= f0) {
-      if (d == 0) ++i; else if (d == 1) ++j; else ++k;
-    }
+    if (d == 0) ++i; else if (d == 1) ++j; else ++k;
   }
   return cm_run;
 }

@@ -595,6 +595,34 @@ __device__ __forceinline__ C2PEval<T> c2p_master(const C2PIn<T>& c, T mu_v) {
   return e;
 }
 
+// Master-function value and intermediates at mu without derivatives, in double: the same operations as
+// the value part of c2p_master (derivatives cost about as much again; the mixed form takes them in float).
+__device__ __forceinline__ C2PEval<double> c2p_master_f(const C2PIn<double>& c, double mu) {
+  const double x = 1.0 / (1.0 + c.b2 * mu);
+  const double rb = c.r2 * (x * x) + c.rb2 * (mu * x * (1.0 + x));
+  const double qbar = (c.q - 0.5 * c.b2) - (0.5 * (c.b2 * c.r2 - c.rb2)) * (mu * mu * x * x);
+  double vh2 = mu * mu * rb;
+  if (vh2 > c.v0sq) vh2 = c.v0sq;
+  const double iW = sqrt(1.0 - vh2);
+  const double W = 1.0 / iW;
+  double eps = W * (qbar - mu * rb) + vh2 * W * W * (1.0 / (1.0 + W));
+  if (eps < 0.0) eps = 0.0;
+  const double onepe = 1.0 + eps;
+  const double a = c.gm1 * eps * (1.0 / onepe);
+  const double nuA = (1.0 + a) * onepe * iW;
+  const double nuB = (1.0 + a) * (1.0 + qbar - mu * rb);
+  const double nu = nuA >= nuB ? nuA : nuB;
+  C2PEval<double> e;
+  e.f = mu - 1.0 / (nu + mu * rb);
+  e.df = 0.0;
+  e.x = x;
+  e.W = W;
+  e.rho = c.D * iW;
+  e.eps = eps;
+  e.dx = e.dW = e.drho = e.deps = 0.0;
+  return e;
+}
+
 // Master-function intermediates without the derivative (final evaluation at the root).
 template <class T>
 __device__ __forceinline__ C2PEval<T> c2p_master_value(const C2PIn<T>& c, T mu) {
@@ -859,8 +887,8 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
   const bool bad = c2p_setup<R>(p, m, Uc, c, ru, bu) != 0;
   float mupf = 1.f, muf = 0.f;
   int itf = 0, stf = ST_NOT_CONVERGED;
+  C2PIn<float> cf;
   if (!bad) {
-    C2PIn<float> cf;
     cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
     cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
     mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
@@ -889,7 +917,15 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
       const double mup = c2p_mu_plus_polish(c, mupf);
       if (cold) mue = mup;
     }
-    const C2PEval<double> e = c2p_master(c, mue);
+    // f and the intermediates in double; their derivatives, which only scale the last Newton step and the
+    // first-order move of the primitives (both at most 1e-6 mu), in float at the same point
+    C2PEval<double> e = c2p_master_f(c, mue);
+    const C2PEval<float> ed = c2p_master<float>(cf, (float)mue);
+    e.df = (double)ed.df;
+    e.dx = (double)ed.dx;
+    e.dW = (double)ed.dW;
+    e.drho = (double)ed.drho;
+    e.deps = (double)ed.deps;
     ++iters;
     if (cold && !(e.f > 0.0)) {
       mu = mue;

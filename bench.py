@@ -505,8 +505,8 @@ def run_batched(G, I, steps, warmup, rank):
 # Kerr-Schild random block (summary under profiles/): double-precision flops (DADD + DMUL + 2 DFMA,
 # active lanes) per cell of k_update, float flops (FADD + FMUL + 2 FFMA) per face of k_flux_cc (mean of
 # the three directions), DRAM bytes (read + write) per unit.
-UPDATE_FP64_FLOP_PER_CELL = 466.5
-UPDATE_DRAM_BYTES_PER_CELL = 373.5
+UPDATE_FP64_FLOP_PER_CELL = 386.7
+UPDATE_DRAM_BYTES_PER_CELL = 373.8
 # algorithmic bytes per cell of k_update: P (8 float) + Ucur (8 double) + U0 (8 double, stages with
 # g0 != 0) + 3 x 8 face fluxes (float) + 3 EMFs (float) + 19 doubles of cached geometry read; Unew
 # (8 double) + P (8 float) + status written; the average over the two stages of an RK2 step

@@ -824,7 +824,7 @@ __device__ __forceinline__ int con2prim(const DevParams& p, const Metric<R>& m, 
   return st;
 }
 
-// One double Newton step of the master function from mue, accepted when it is smaller than 1e-6 mue
+// One double Newton step of the master function from mue, accepted when it is smaller than 3e-6 mue
 // (its error is then of order step^2) and stays below the float bracket end (with margin): on success
 // returns true with the root mu and the intermediates there, to first order in the step.
 __device__ __forceinline__ bool c2p_accept_step(const C2PIn<double>& c, const C2PEval<double>& e, double mue,
@@ -832,7 +832,7 @@ __device__ __forceinline__ bool c2p_accept_step(const C2PIn<double>& c, const C2
   const double step = -e.f / e.df;
   const double nmu = mue + step;
   mu = nmu;
-  if (!(e.df > 0.0 && nmu > 0.0 && fabs(step) <= 1e-6 * nmu && nmu <= (double)mupf * (1.0 + 1e-5))) return false;
+  if (!(e.df > 0.0 && nmu > 0.0 && fabs(step) <= 3e-6 * nmu && nmu <= (double)mupf * (1.0 + 1e-5))) return false;
   ev = e;
   ev.x += e.dx * step;
   ev.W += e.dW * step;
@@ -918,7 +918,7 @@ __device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R
       if (cold) mue = mup;
     }
     // f and the intermediates in double; their derivatives, which only scale the last Newton step and the
-    // first-order move of the primitives (both at most 1e-6 mu), in float at the same point
+    // first-order move of the primitives (both at most 3e-6 mu), in float at the same point
     C2PEval<double> e = c2p_master_f(c, mue);
     const C2PEval<float> ed = c2p_master<float>(cf, (float)mue);
     e.df = (double)ed.df;

@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(256) k_face_update(const double* __restrict__ 
   const long long G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
   const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
   const double bdt = a.beta * dt;
+  const double cx = bdt * p.idx[0], cy = bdt * p.idx[1], cz = bdt * p.idx[2];  // beta dt / dx_d
+  const bool with0 = a.g0 != 0.0;  // uniform: first stages have no step-start term
   const R* Ex = E;
   const R* Ey = E + G;
   const R* Ez = E + 2 * G;
@@ -110,19 +112,19 @@ __global__ void __launch_bounds__(256) k_face_update(const double* __restrict__ 
     const long long g = gidx(p, i, j, k);
     const double ez = (double)Ez[g], ey_ = (double)Ey[g], ex_ = (double)Ex[g];
     if (j < p.ny && k < p.nz) {
-      const double curl = -((double)Ez[g + sy] - ez) * p.idx[1] + ((double)Ey[g + sz] - ey_) * p.idx[2];
-      const double b0 = a.g0 != 0.0 ? Bf0[g] : 0.0;
-      Bfn[g] = a.g0 * b0 + a.g1 * Bfc[g] + bdt * curl;
+      double b = a.g1 * Bfc[g] + (((double)Ey[g + sz] - ey_) * cz - ((double)Ez[g + sy] - ez) * cy);
+      if (with0) b += a.g0 * Bf0[g];
+      Bfn[g] = b;
     }
     if (i < p.nx && k < p.nz) {
-      const double curl = ((double)Ez[g + 1] - ez) * p.idx[0] - ((double)Ex[g + sz] - ex_) * p.idx[2];
-      const double b0 = a.g0 != 0.0 ? Bf0[G + g] : 0.0;
-      Bfn[G + g] = a.g0 * b0 + a.g1 * Bfc[G + g] + bdt * curl;
+      double b = a.g1 * Bfc[G + g] + (((double)Ez[g + 1] - ez) * cx - ((double)Ex[g + sz] - ex_) * cz);
+      if (with0) b += a.g0 * Bf0[G + g];
+      Bfn[G + g] = b;
     }
     if (i < p.nx && j < p.ny) {
-      const double curl = -((double)Ey[g + 1] - ey_) * p.idx[0] + ((double)Ex[g + sy] - ex_) * p.idx[1];
-      const double b0 = a.g0 != 0.0 ? Bf0[2 * G + g] : 0.0;
-      Bfn[2 * G + g] = a.g0 * b0 + a.g1 * Bfc[2 * G + g] + bdt * curl;
+      double b = a.g1 * Bfc[2 * G + g] + (((double)Ex[g + sy] - ex_) * cy - ((double)Ey[g + 1] - ey_) * cx);
+      if (with0) b += a.g0 * Bf0[2 * G + g];
+      Bfn[2 * G + g] = b;
     }
   }
 }

@@ -511,6 +511,10 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   const double xc = p.x0[0] + (i + 0.5) * p.dx[0];
   const double yc = p.x0[1] + (j + 0.5) * p.dx[1];
   const double zc = p.x0[2] + (k + 0.5) * p.dx[2];
+  // the cell centre in the source / warm-start precision, formed in that precision (no conversion from double)
+  const R xr = R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]);
+  const R yr = R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]);
+  const R zr = R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2]);
   T Pt[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) Pt[q] = P[q * G + g];
@@ -547,14 +551,14 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   if constexpr (sizeof(R) == sizeof(double)) {
     mr = m;
   } else {
-    metric_at<R, METRIC>(p, R(xc), R(yc), R(zc), mr);
+    metric_at<R, METRIC>(p, xr, yr, zr, mr);
   }
   R Pr[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) Pr[q] = R(Pt[q]);
   if (METRIC == KERR_SCHILD) {
     R Sr[5];
-    ks_sources<R>(p, R(xc), R(yc), R(zc), Pr, mr, Sr);
+    ks_sources<R>(p, xr, yr, zr, Pr, mr, Sr);
 #pragma unroll
     for (int q = 1; q < 5; ++q) L[q] += Sr[q];
   }

@@ -46,6 +46,60 @@ __global__ void chains32(float* out, int iters, float s) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 
+// Float -> double and double -> float conversions, independent per chain, fed and consumed by integer
+// operations only (a float add on the input side of the first), so that the conversions are the only
+// candidate for the FP64 pipe.
+__global__ void cvt_f2d(unsigned long long* out, int iters, float s) {
+  float f[NCH];
+  for (int c = 0; c < NCH; ++c) f[c] = 1.0f + 1e-3f * (threadIdx.x + c);
+  unsigned long long acc = 0;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      f[c] += s;
+      acc ^= (unsigned long long)__double_as_longlong((double)f[c]);
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+__global__ void cvt_d2f(unsigned long long* out, int iters, float s) {
+  long long b[NCH];
+  for (int c = 0; c < NCH; ++c) b[c] = __double_as_longlong(1.0 + 1e-3 * (threadIdx.x + c) + (double)s);
+  unsigned int acc = 0;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      b[c] += 1;
+      acc ^= __float_as_uint((float)__longlong_as_double(b[c]));
+    }
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// DFMA chains and float -> double conversions interleaved (NCH of each per iteration): the time is the sum
+// of the two alone when they share the FP64 pipe, their maximum when they do not.
+__global__ void dfma_cvt(unsigned long long* out, int iters, float s) {
+  double a[NCH];
+  float f[NCH];
+  for (int c = 0; c < NCH; ++c) {
+    a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+    f[c] = 1.0f + 1e-3f * (threadIdx.x + c);
+  }
+  unsigned long long acc = 0;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      a[c] = fma(a[c], 0.999999, 1e-9);
+      f[c] += s;
+      acc ^= (unsigned long long)__double_as_longlong((double)f[c]);
+    }
+  }
+  double t = 0;
+  for (int c = 0; c < NCH; ++c) t += a[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc ^ (unsigned long long)__double_as_longlong(t);
+}
+
 // DFMA chains in the lanes below `lanes` of every warp only.
 __global__ void chains64_lanes(double* out, int iters, double s, int lanes) {
   double a[NCH];
@@ -61,8 +115,8 @@ __global__ void chains64_lanes(double* out, int iters, double s, int lanes) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 
-template <typename K, typename T>
-static void timed(const char* name, K kern, T* buf, int iters, T s, int blocks, int threads, double flop_per_op) {
+template <typename K, typename T, typename S>
+static void timed(const char* name, K kern, T* buf, int iters, S s, int blocks, int threads, double flop_per_op) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -98,6 +152,12 @@ int main() {
   timed("ffma", chains32<0>, d32, 20000, 0.999999f, blocks, threads, 2);
   timed("fdiv+add", chains32<3>, d32, 2000, 1e-7f, blocks, threads, 1);
   timed("fsqrt+add", chains32<4>, d32, 2000, 1e-7f, blocks, threads, 1);
+  unsigned long long* du = nullptr;
+  cudaMalloc(&du, sizeof(unsigned long long) * blocks * threads);
+  timed("cvt f->d", cvt_f2d, du, 2000, 1e-7f, blocks, threads, 1);
+  timed("cvt d->f", cvt_d2f, du, 2000, 1e-7f, blocks, threads, 1);
+  timed("dfma+cvt", dfma_cvt, du, 2000, 1e-7f, blocks, threads, 1);
+  cudaFree(du);
   for (int lanes : {32, 16, 8, 1}) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

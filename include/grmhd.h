@@ -45,7 +45,7 @@ extern "C" {
 #define GRMHD_E_UNSUPPORTED (-4) /* option combination not built */
 
 /* options */
-#define GRMHD_MINKOWSKI 0
+#define GRMHD_MINKOWSKI 0     /* flat space, optionally with a constant shift (params.shift) */
 #define GRMHD_KERR_SCHILD 1 /* Cartesian Kerr-Schild, spin a = spin * mass along z */
 
 #define GRMHD_RECON_CONSTANT 0
@@ -109,6 +109,9 @@ typedef struct {
   double cfl;                 /* dt = cfl / max_d(max |lambda_d| / dx_d) when the stage picks dt */
   double weno_eps;            /* epsilon of the WENO5-Z weights (App. B eq. (nonlinear weights)) */
   int ct;                     /* GRMHD_CT_FLUX | GRMHD_CT_FACE (single-block contexts only) */
+  double shift[3];            /* GRMHD_MINKOWSKI only: constant shift beta^i, i.e. flat space in coordinates moving
+                                 at velocity -beta (Sec. 4.1.1's boosted linear waves; |beta| < 1); ignored by
+                                 Kerr-Schild */
 } grmhd_params;
 
 /* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */

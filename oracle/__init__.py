@@ -59,7 +59,7 @@ class OrcParams(ctypes.Structure):
         ("recon", ctypes.c_int), ("riemann", ctypes.c_int), ("bc", ctypes.c_int),
         ("rho_floor0", ctypes.c_double), ("eps_floor0", ctypes.c_double), ("floor_r_exp", ctypes.c_double),
         ("w_max", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_max_iter", ctypes.c_int),
-        ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double),
+        ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double), ("shift", ctypes.c_double * 3),
     ]
 
 
@@ -110,6 +110,7 @@ def params(setup) -> OrcParams:
                                                           setup.w_max)
     p.c2p_tol, p.c2p_max_iter = setup.c2p_tol, setup.c2p_max_iter
     p.cfl, p.weno_eps = setup.cfl, setup.weno_eps
+    p.shift[:] = list(getattr(setup, "shift", (0.0, 0.0, 0.0)))
     return p
 
 

@@ -55,6 +55,7 @@ typedef struct {
   int c2p_max_iter;      // unused by the oracle
   double cfl;
   double weno_eps;
+  double shift[3];       // Minkowski only: constant shift beta^i of coordinates moving at -beta (zero: at rest)
 } orc_params;
 
 }  // extern "C"
@@ -116,8 +117,16 @@ static void metric_eval(const orc_params& p, double x, double y, double z, Geom&
   std::memset(&G, 0, sizeof(G));
   double eta[4][4] = {{-1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 0, 0, 1}};
   if (p.metric == 0) {
+    // flat space in coordinates moving at constant velocity -shift (Sec. 4.1.1's boosted linear waves):
+    // ds^2 = -dt^2 + (dx^i + beta^i dt)^2, i.e. g_00 = -1 + beta^2, g_0i = beta_i, g_ij = delta_ij
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) G.g[a][b] = eta[a][b];
+    double b2 = 0.0;
+    for (int i = 1; i <= 3; ++i) {
+      G.g[0][i] = G.g[i][0] = p.shift[i - 1];
+      b2 += p.shift[i - 1] * p.shift[i - 1];
+    }
+    G.g[0][0] = -1.0 + b2;
     G.r = 1.0;
   } else {
     const double M = p.mass, a = p.spin * p.mass;

@@ -95,6 +95,10 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   if (!(p->w_max > 1.0)) { snprintf(msg, n, "w_max must be > 1"); return false; }
   if (p->metric == GRMHD_KERR_SCHILD && !(p->mass > 0.0)) { snprintf(msg, n, "mass must be > 0"); return false; }
   if (p->ct != GRMHD_CT_FLUX && p->ct != GRMHD_CT_FACE) { snprintf(msg, n, "unknown constrained-transport mode"); return false; }
+  if (p->metric == GRMHD_MINKOWSKI && !(p->shift[0] * p->shift[0] + p->shift[1] * p->shift[1] + p->shift[2] * p->shift[2] < 1.0)) {
+    snprintf(msg, n, "the shift must have |beta| < 1");
+    return false;
+  }
   return true;
 }
 
@@ -148,6 +152,7 @@ DevParams dev_params(const grmhd_params* p) {
   d.v0sq_cap = 1.0 - 1.0 / (p->w_max * p->w_max);
   d.c2p_tol = p->c2p_tol; d.c2p_max_iter = p->c2p_max_iter;
   d.cfl = p->cfl; d.weno_eps = p->weno_eps;
+  for (int i = 0; i < 3; ++i) d.shift[i] = p->metric == GRMHD_MINKOWSKI ? p->shift[i] : 0.0;
   return d;
 }
 

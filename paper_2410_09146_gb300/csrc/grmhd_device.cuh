@@ -44,6 +44,7 @@ struct DevParams {
   // component d on the lower d-face of cell (i,j,k)); the flux kernels take the normal field from it.
   // NULL: cell-centred field (flux-CT).
   const double* bface;
+  double shift[3];  // Minkowski: constant shift beta^i (flat space in coordinates moving at -beta)
 };
 
 // Arguments of the update kernel (a5 + a6).
@@ -188,7 +189,7 @@ __device__ __forceinline__ void metric_at(const DevParams& p, R x, R y, R z, Met
     m.alpha = R(1);
     m.sqrtgam = R(1);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) m.beta[i] = R(0);
+    for (int i = 0; i < 3; ++i) m.beta[i] = R(p.shift[i]);
 #pragma unroll
     for (int t = 0; t < 6; ++t) m.gam[t] = m.gamu[t] = (t == 0 || t == 3 || t == 5) ? R(1) : R(0);
     if (rks) *rks = R(1);

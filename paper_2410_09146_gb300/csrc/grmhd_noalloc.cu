@@ -100,6 +100,7 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
   d.w_max2 = p->w_max * p->w_max;
   d.v0sq_cap = 1.0 - 1.0 / (p->w_max * p->w_max);
   d.c2p_tol = p->c2p_tol; d.c2p_max_iter = p->c2p_max_iter; d.cfl = p->cfl; d.weno_eps = p->weno_eps;
+  for (int i = 0; i < 3; ++i) d.shift[i] = p->metric == GRMHD_MINKOWSKI ? p->shift[i] : 0.0;
 
   void* base = nullptr;
   cudaError_t e = scratch_address(&base);

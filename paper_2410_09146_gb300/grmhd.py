@@ -45,6 +45,7 @@ class grmhd_params(ctypes.Structure):
         ("rho_floor0", ctypes.c_double), ("eps_floor0", ctypes.c_double), ("floor_r_exp", ctypes.c_double),
         ("w_max", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_max_iter", ctypes.c_int),
         ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double), ("ct", ctypes.c_int),
+        ("shift", ctypes.c_double * 3),
     ]
 
 
@@ -129,6 +130,7 @@ def params(setup) -> grmhd_params:
                                                           setup.w_max)
     p.c2p_tol, p.c2p_max_iter, p.cfl, p.weno_eps = setup.c2p_tol, setup.c2p_max_iter, setup.cfl, setup.weno_eps
     p.ct = CT[getattr(setup, "ct", "flux")]
+    p.shift[:] = list(getattr(setup, "shift", (0.0, 0.0, 0.0)))
     return p
 
 

@@ -19,6 +19,9 @@ Workloads (sizes and distributions follow the stage's standard test problems):
   * ``smooth_random`` every variable a smooth random perturbation of a uniform state (no normalised
     direction field), B from a random potential, with its face field.
   * ``plane_random`` a periodic state that varies along one direction only, with its face field.
+  * ``boosted_wave`` a plane linear wave along the diagonal of a periodic square in flat space with a
+    constant shift (the coordinate boost of the paper's 2-D linear-wave tests); mode shapes and speeds
+    are passed in (tests/golden/boosted_waves.json, written from the oracle).
   * ``field_loop`` a weak magnetic field loop in a uniform flow on a periodic square (the standard
     constrained-transport advection test), with its face field.
   * ``c2p_states``  i.i.d. primitive states for the flat con2prim batch: rho, W, sigma
@@ -60,6 +63,7 @@ class Setup:
     weno_eps: float = 1e-26
     precision: str = "fp64"            # "fp64" | "mixed"
     ct: str = "flux"                   # "flux" (Toth flux-CT, cell field) | "face" (face-centred upwind CT)
+    shift: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # Minkowski: constant shift (boosted coordinates)
 
     @property
     def ghosted(self):
@@ -234,6 +238,27 @@ def _face_curl(A, dx):
         t2 = D(_mu(A[a], _AX_OF[a]), _AX_OF[b], dx[b])
         out.append(t1 - t2)
     return out
+
+
+def boosted_wave_setup(n: int = 32, recon: str = "plm_mc", riemann: str = "hll", shift=(0.617213, 0.617213, 0.0)) -> Setup:
+    """Periodic unit square of n x n cells (one cell in z), flat metric with a constant shift: the coordinate
+    boost of the paper's 2-D linear-wave tests (Sec. 4.1.1)."""
+    return Setup(n=(n, n, 1), x0=(0.0, 0.0, 0.0), dx=(1.0 / n, 1.0 / n, 1.0 / n), metric="minkowski",
+                 recon=recon, riemann=riemann, bc="periodic", shift=tuple(shift))
+
+
+def boosted_wave_prims(s: Setup, background, eigvec, speed: float, amplitude: float = 1e-6, t: float = 0.0) -> np.ndarray:
+    """Plane wave along the diagonal n = (1, 1, 0)/sqrt(2) with one wavelength across the square's diagonal period:
+    P = P0 + amplitude * eigvec * sin(2 pi [(x + y) - sqrt(2) speed t]) at the cell centres (the exact solution of
+    the linearised equations at time t; `speed` is the mode's coordinate speed along n)."""
+    xc = s.cell_centres(0)
+    yc = s.cell_centres(1)
+    phase = 2.0 * math.pi * ((xc[None, :] + yc[:, None]) - math.sqrt(2.0) * speed * t)  # [y][x]
+    w = np.sin(phase)
+    P = np.empty(s.prim_shape())
+    for v in range(8):
+        P[v] = background[v] + amplitude * eigvec[v] * w[None, :, :]
+    return P
 
 
 def smooth_random_prims(s: Setup, seed: int = 6, amp: float = 0.3, b_amp: float = 0.3, kmax: int = 1):

@@ -1,0 +1,71 @@
+"""The paper's 2-D linear-wave suite (Sec. 4.1.1) on the GPU: sound, Alfven, slow and fast waves along the diagonal
+of a periodic square, flat metric with the coordinate boost v_x = v_y = 0.617213 (a constant shift), modes and
+speeds from tests/golden/boosted_waves.json (written from the oracle).
+
+* All-FP64 parity with the oracle on boosted-wave states (a square and a ragged block), every stage within
+  1e-12 under the measures of tests/parity.py.
+* Convergence: after one period (the solution is then the initial condition) the amplitude-scaled L1 error of the
+  primitives, (1/(A N^2)) sum |P - P0|, falls at second order (PLM-MC + HLL; the paper reports roughly at least
+  second order) from 64^2 to 128^2 and from 128^2 to 256^2.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2410_09146_gb300 import inputs as I
+from tests.test_gpu_parity import _step_compare
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "boosted_waves.json")
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_09146_gb300 import build
+    build.build()
+    from paper_2410_09146_gb300 import grmhd
+    return grmhd
+
+
+@pytest.mark.parametrize("wave,n3,recon,riemann", [("fast", (16, 16, 1), "plm_mc", "llf"),
+                                                   ("alfven", (13, 9, 3), "weno5z_aoah", "hll"),
+                                                   ("slow", (12, 10, 2), "mp5", "hll")])
+def test_boosted_wave_parity(G, orc, wave, n3, recon, riemann):
+    w = json.load(open(GOLDEN))["waves"][wave]
+    s = I.boosted_wave_setup(16, recon=recon, riemann=riemann)
+    s.n = n3
+    s.dx = tuple(1.0 / k for k in n3)
+    P = I.boosted_wave_prims(s, w["background_prims"], w["eigvec_prims"], w["speed"], amplitude=1e-3)
+    _step_compare(G, orc, s, P, nsteps=2)
+
+
+def _period_error(G, wave, n, amp=1e-6):
+    g = json.load(open(GOLDEN))
+    w = g["waves"][wave]
+    s = I.boosted_wave_setup(n, recon="plm_mc", riemann="hll")
+    P0 = I.boosted_wave_prims(s, w["background_prims"], w["eigvec_prims"], w["speed"], amp)
+    period = (1.0 / np.sqrt(2.0)) / abs(w["speed"])  # one wavelength along n = 1/sqrt(2)
+    vmax = max(abs(v) for v in w["spectrum"])
+    steps = int(np.ceil(period / (s.cfl * s.dx[0] / vmax)))
+    dt = period / steps
+    ctx = G.Context(s)
+    ctx.set_prims(P0.copy())
+    for _ in range(steps):
+        ctx.rk2_step(dt)
+    P = ctx.prims()
+    ng = s.ng
+    inner = (slice(None), slice(ng, -ng), slice(ng, -ng), slice(ng, -ng))
+    return float(np.abs(P[inner] - P0[inner]).sum() / (amp * n * n))
+
+
+@pytest.mark.parametrize("wave", ["sound", "alfven", "slow", "fast"])
+def test_boosted_wave_second_order(G, wave):
+    e = {n: _period_error(G, wave, n) for n in (32, 64, 128, 256)}
+    orders = {f"{a}->{b}": float(np.log2(e[a] / e[b])) for a, b in ((32, 64), (64, 128), (128, 256))}
+    print(wave, "L1 after one period:", e, "orders:", orders)
+    assert orders["64->128"] > 1.8 and orders["128->256"] > 1.8, (e, orders)

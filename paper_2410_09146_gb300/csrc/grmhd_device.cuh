@@ -596,16 +596,17 @@ __device__ __forceinline__ C2PEval<T> c2p_master(const C2PIn<T>& c, T mu_v) {
   return e;
 }
 
-// Master-function value and intermediates at mu without derivatives, in double: the same operations as
-// the value part of c2p_master (derivatives cost about as much again; the mixed form takes them in float).
+// Master-function value and intermediates at mu without derivatives, in double: the operations of the value
+// part of c2p_master, W from a reciprocal square root (derivatives cost about as much again; the mixed form
+// takes them in float).
 __device__ __forceinline__ C2PEval<double> c2p_master_f(const C2PIn<double>& c, double mu) {
   const double x = 1.0 / (1.0 + c.b2 * mu);
   const double rb = c.r2 * (x * x) + c.rb2 * (mu * x * (1.0 + x));
   const double qbar = (c.q - 0.5 * c.b2) - (0.5 * (c.b2 * c.r2 - c.rb2)) * (mu * mu * x * x);
   double vh2 = mu * mu * rb;
   if (vh2 > c.v0sq) vh2 = c.v0sq;
-  const double iW = sqrt(1.0 - vh2);
-  const double W = 1.0 / iW;
+  const double W = rsqrt(1.0 - vh2);  // one reciprocal square root instead of a square root and a division
+  const double iW = (1.0 - vh2) * W;
   double eps = W * (qbar - mu * rb) + vh2 * W * W * (1.0 / (1.0 + W));
   if (eps < 0.0) eps = 0.0;
   const double onepe = 1.0 + eps;

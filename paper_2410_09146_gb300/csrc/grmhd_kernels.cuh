@@ -887,8 +887,9 @@ __global__ void k_prim2con(const T* __restrict__ P, double* __restrict__ U, DevP
 #pragma unroll
     for (int q = 0; q < NV; ++q) Pc[q] = (double)P[q * G + g];
     Metric<double> m;
-    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
-                              p.x0[2] + (k + 0.5) * p.dx[2], m);
+    double isg, fr;  // the metric from the block's geometry cache when it has one (same values as in place)
+    cell_metric<METRIC>(p, t, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                        p.x0[2] + (k + 0.5) * p.dx[2], m, isg, fr);
     double U5[5];
     prim_to_cons5<double>(Pc, m, p.gamma_eos, U5);
 #pragma unroll

@@ -23,8 +23,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "grmhd_oracle.cpp")
-_BUILD = os.path.join(_HERE, "_build")
+# GRMHD_ORACLE_SRC / GRMHD_ORACLE_BUILD point the package at another copy of the source (the planted-mistake
+# tests compile copies with one mistake each and run the pins against them)
+_SRC = os.environ.get("GRMHD_ORACLE_SRC") or os.path.join(_HERE, "grmhd_oracle.cpp")
+_BUILD = os.environ.get("GRMHD_ORACLE_BUILD") or os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None

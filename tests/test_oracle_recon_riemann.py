@@ -7,6 +7,10 @@
   linear data and for sigma -> 1 on constants).
 * WENO5-Z converges at fifth order on cell averages of sin(2 pi x); AOAH at >= 3.
 * At a step, AOAH stays within the data range (no new extrema).
+* AOAH mixes both faces of a cell with one weight sigma, a harmonic mean of the two face values
+  sigma_{j+-1/2} (eq. def:sigma): it lies between the smaller side and their geometric mean (an
+  arithmetic mean lies above the geometric one). The two sides share the three smoothness indicators
+  (the mirrored face sees them with the linear weights reversed), so their ratio stays within [1/3, 3].
 * Riemann: consistency F(U, U) = F(U) for LLF and HLL; HLL = upwind flux when all speeds > 0.
 """
 import numpy as np
@@ -109,3 +113,26 @@ def test_hll_supersonic_is_upwind(orc):
     Fh, cm = orc.riemann_points(p, np.zeros((1, 3)), PL, PR, 1)
     phys = orc.prim2con_points(p, np.zeros((1, 3)), PL)
     np.testing.assert_allclose(Fh[0], phys["F"][0, 0], rtol=1e-14, atol=1e-16)
+
+
+def test_aoah_sigma_is_a_harmonic_mean_of_the_sides(orc):
+    rng = np.random.default_rng(2)
+    n = 20000
+    x = np.arange(5)[None, :] - 2.0
+    f = rng.normal(size=(n, 1)) + rng.normal(size=(n, 1)) * x + 0.3 * rng.normal(size=(n, 1)) * x ** 2
+    f += np.where(x >= rng.integers(0, 5, n)[:, None] - 1.5, rng.normal(size=(n, 1)) * 3, 0.0)  # a jump
+    vp, _, sp = orc.weno5z_points(f)
+    vm, _, sm = orc.weno5z_points(f[:, ::-1].copy())  # the j-1/2 face: the mirrored stencil
+    ratio = np.maximum(sp, sm) / np.minimum(sp, sm)
+    assert ratio.max() <= 3.0 * (1 + 1e-12) and ratio.max() > 2.9
+    qm, qp = orc.recon_points("weno5z_aoah", f)
+    lm, lp = orc.recon_points("plm_mc", f)
+    scale = np.abs(f).max(1)
+    use = (np.abs(vp - lp) > 1e-2 * scale) & (np.abs(vm - lm) > 1e-2 * scale) & (ratio > 1.5) & (np.maximum(sp, sm) < 1)
+    assert use.sum() > 1000
+    # the weight each face mixed with: q = sigma P5 + (1 - sigma) P_plm
+    sig_p = ((qp - lp) / (vp - lp))[use]
+    sig_m = ((qm - lm) / (vm - lm))[use]
+    assert np.abs(sig_p - sig_m).max() < 1e-12
+    lo, gm = np.minimum(sp, sm)[use], np.sqrt(sp * sm)[use]
+    assert np.all(sig_p >= lo * (1 - 1e-12)) and np.all(sig_p <= gm * (1 + 1e-12))

@@ -87,6 +87,8 @@ def _load():
                                   ctypes.c_double, dp, dp, ip, dp, dp]
         lib.orc_stage_face_ct.argtypes = lib.orc_stage.argtypes + [dp, dp, dp]
         lib.orc_face_b_to_cells.argtypes = [P, dp, dp]
+        lib.orc_face_fluxes_used.argtypes = [P, dp, dp, dp]
+        lib.orc_finish_points.argtypes = [P, L, dp, dp, dp, u8p]
         _lib = lib
     return _lib
 
@@ -229,6 +231,30 @@ def stage(p: OrcParams, P, U0, Ucur, g0: float, g1: float, beta: float, dt: floa
     if debug:
         out["F"], out["E"] = F, E
     return out
+
+
+def face_fluxes_used(p: OrcParams, F, E):
+    """Fluxes the flux-CT update uses on every interior face, [3][8] + grid shape: the hydro components of
+    the stage's face fluxes ``F`` and the CT fluxes of B formed from its edge EMFs ``E`` (both from
+    ``stage(..., debug=True)``)."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    out = np.zeros_like(F)
+    _load().orc_face_fluxes_used(ctypes.byref(p), _dp(F), _dp(E), _dp(out))
+    return out
+
+
+def finish_points(p: OrcParams, xyz, Un):
+    """The stage's last step at points: con2prim of the densitized conserved states ``Un`` [n][8], floors,
+    and the hydro part re-derived from the floored primitives when a status bit is set.
+    Returns (Un after, P, status)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    Un = np.array(Un, dtype=np.float64, order="C").reshape(-1, 8)
+    n = len(Un)
+    P = np.zeros((n, 8)); st = np.zeros(n, np.uint8)
+    _load().orc_finish_points(ctypes.byref(p), n, _dp(xyz), _dp(Un), _dp(P),
+                              st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return Un, P, st
 
 
 def rk2_step(p: OrcParams, P, U, dt: float = 0.0):

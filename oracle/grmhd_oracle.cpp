@@ -895,6 +895,50 @@ namespace {
 //     the face divergence sum_d (Bf_d(+) - Bf_d(-)) / dx_d does not change;
 //   * the cell-centred densitized field in Unew is the mean of the cell's two new faces of each direction.
 // With Omega_c = sqrt(gamma) (B^a v~^b - B^b v~^a) for (c, a, b) cyclic, Omega_c = F^b_{B^a} = -F^a_{B^b}.
+// CT fluxes of B through the lower d-face of ghosted cell (i, j, k) (Toth flux-CT, Sec. 3.1): each is the
+// mean of the two edge EMFs bounding the face along the transverse direction, with the sign of E = -v x B
+// (F^x_{B^y} = -Omega_z, F^x_{B^z} = +Omega_y, F^y_{B^x} = +Omega_z, F^y_{B^z} = -Omega_x,
+// F^z_{B^x} = -Omega_y, F^z_{B^y} = +Omega_x); the normal component is zero. E holds Omega_x, Omega_y,
+// Omega_z, each [gsize], on the edges stored at the ghosted cell index.
+static void ct_face_flux_b(const Grid& g, const double* E, int d, int i, int j, int k, double Fb[3]) {
+  const long gn = g.gsize();
+  auto Ev = [&](int c, int ii, int jj, int kk) { return E[c * gn + g.gi(ii, jj, kk)]; };
+  if (d == 0) {
+    Fb[0] = 0.0;
+    Fb[1] = -0.5 * (Ev(2, i, j, k) + Ev(2, i, j + 1, k));
+    Fb[2] = 0.5 * (Ev(1, i, j, k) + Ev(1, i, j, k + 1));
+  } else if (d == 1) {
+    Fb[0] = 0.5 * (Ev(2, i, j, k) + Ev(2, i + 1, j, k));
+    Fb[1] = 0.0;
+    Fb[2] = -0.5 * (Ev(0, i, j, k) + Ev(0, i, j, k + 1));
+  } else {
+    Fb[0] = -0.5 * (Ev(1, i, j, k) + Ev(1, i + 1, j, k));
+    Fb[1] = 0.5 * (Ev(0, i, j, k) + Ev(0, i, j + 1, k));
+    Fb[2] = 0.0;
+  }
+}
+
+// a6 for one cell: con2prim of the densitized conserved state Un (Sec. 3.1), floors and the W ceiling
+// (Sec. 3.2); when any status bit is set the hydro part of Un is re-derived from the floored primitives
+// (B is kept as evolved). Returns the status; Pout gets the primitives.
+static int finish_cell(const orc_params& p, const Geom& G, double* Un, double* Pout, int* iters) {
+  double Uc[8];
+  for (int v = 0; v < 8; ++v) Uc[v] = Un[v] / G.sqrtgam;
+  C2PResult R;
+  con2prim_point(p, G, Uc, R);
+  if (iters) *iters += R.iters;
+  const int st = R.status | apply_floors(p, G, R.P);
+  if (st) {
+    Fluid Ff;
+    fluid_from_prims(p, G, R.P, Ff);
+    double Uf[8];
+    cons_from_fluid(G, Ff, Uf);
+    for (int v = 0; v < 5; ++v) Un[v] = G.sqrtgam * Uf[v];
+  }
+  for (int v = 0; v < 8; ++v) Pout[v] = R.P[v];
+  return st;
+}
+
 static int stage_impl(const orc_params* p, double* P, const double* U0, const double* Ucur, double* Unew,
                       uint8_t* status, double g0, double g1, double beta, double dt, double* dt_used,
                       double* maxspeed, int* iters_total, double* Fdbg, double* Edbg, const double* Bf0,
@@ -1080,7 +1124,6 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
           }
     }
   }
-  auto Ev = [&](int c, int i, int j, int k) { return E[c * gn + g.gi(i, j, k)]; };
   if (Fdbg) std::memcpy(Fdbg, F.data(), sizeof(double) * F.size());
   if (Edbg) std::memcpy(Edbg, E.data(), sizeof(double) * E.size());
 
@@ -1105,22 +1148,17 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
                        (Fv(2, v, i, j, k + 1) - Fv(2, v, i, j, k)) / p->dx[2];
           L[v] = -div + G.sqrtmg * S[v];
         }
-        // CT-corrected B fluxes (normal components are zero).
-        const double FyBx_p = 0.5 * (Ev(2, i, j + 1, k) + Ev(2, i + 1, j + 1, k));
-        const double FyBx_m = 0.5 * (Ev(2, i, j, k) + Ev(2, i + 1, j, k));
-        const double FzBx_p = -0.5 * (Ev(1, i, j, k + 1) + Ev(1, i + 1, j, k + 1));
-        const double FzBx_m = -0.5 * (Ev(1, i, j, k) + Ev(1, i + 1, j, k));
-        const double FxBy_p = -0.5 * (Ev(2, i + 1, j, k) + Ev(2, i + 1, j + 1, k));
-        const double FxBy_m = -0.5 * (Ev(2, i, j, k) + Ev(2, i, j + 1, k));
-        const double FzBy_p = 0.5 * (Ev(0, i, j, k + 1) + Ev(0, i, j + 1, k + 1));
-        const double FzBy_m = 0.5 * (Ev(0, i, j, k) + Ev(0, i, j + 1, k));
-        const double FxBz_p = 0.5 * (Ev(1, i + 1, j, k) + Ev(1, i + 1, j, k + 1));
-        const double FxBz_m = 0.5 * (Ev(1, i, j, k) + Ev(1, i, j, k + 1));
-        const double FyBz_p = -0.5 * (Ev(0, i, j + 1, k) + Ev(0, i, j + 1, k + 1));
-        const double FyBz_m = -0.5 * (Ev(0, i, j, k) + Ev(0, i, j, k + 1));
-        L[5] = -((FyBx_p - FyBx_m) / p->dx[1] + (FzBx_p - FzBx_m) / p->dx[2]);
-        L[6] = -((FxBy_p - FxBy_m) / p->dx[0] + (FzBy_p - FzBy_m) / p->dx[2]);
-        L[7] = -((FxBz_p - FxBz_m) / p->dx[0] + (FyBz_p - FyBz_m) / p->dx[1]);
+        // CT-corrected B fluxes through the cell's lower (m) and upper (p) faces of each direction
+        double Bxm[3], Bxp[3], Bym[3], Byp[3], Bzm[3], Bzp[3];
+        ct_face_flux_b(g, E.data(), 0, i, j, k, Bxm);
+        ct_face_flux_b(g, E.data(), 0, i + 1, j, k, Bxp);
+        ct_face_flux_b(g, E.data(), 1, i, j, k, Bym);
+        ct_face_flux_b(g, E.data(), 1, i, j + 1, k, Byp);
+        ct_face_flux_b(g, E.data(), 2, i, j, k, Bzm);
+        ct_face_flux_b(g, E.data(), 2, i, j, k + 1, Bzp);
+        L[5] = -((Byp[0] - Bym[0]) / p->dx[1] + (Bzp[0] - Bzm[0]) / p->dx[2]);
+        L[6] = -((Bxp[1] - Bxm[1]) / p->dx[0] + (Bzp[1] - Bzm[1]) / p->dx[2]);
+        L[7] = -((Bxp[2] - Bxm[2]) / p->dx[0] + (Byp[2] - Bym[2]) / p->dx[1]);
         const long c = g.ii(i, j, k);
         double Un[8];
         for (int v = 0; v < 8; ++v) {
@@ -1133,23 +1171,11 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
           const long st[3] = {sx, sy, sz};
           for (int d = 0; d < 3; ++d) Un[5 + d] = 0.5 * (Bfnew[d * gn + gc] + Bfnew[d * gn + gc + st[d]]);
         }
-        // a6: con2prim on the undensitized state.
-        double Uc[8];
-        for (int v = 0; v < 8; ++v) Uc[v] = Un[v] / G.sqrtgam;
-        C2PResult R;
-        con2prim_point(*p, G, Uc, R);
-        if (iters_total) *iters_total += R.iters;
-        int st = R.status | apply_floors(*p, G, R.P);
-        if (st) {
-          // Re-derive the hydro conserved variables from the floored primitives; B is kept as evolved.
-          Fluid Ff;
-          fluid_from_prims(*p, G, R.P, Ff);
-          double Uf[8];
-          cons_from_fluid(G, Ff, Uf);
-          for (int v = 0; v < 5; ++v) Un[v] = G.sqrtgam * Uf[v];
-        }
+        // a6: con2prim, floors, re-derived hydro state
+        double Pn[8];
+        const int st = finish_cell(*p, G, Un, Pn, iters_total);
         for (int v = 0; v < 8; ++v) Unew[v * in + c] = Un[v];
-        for (int v = 0; v < 8; ++v) P[v * gn + g.gi(i, j, k)] = R.P[v];
+        for (int v = 0; v < 8; ++v) P[v * gn + g.gi(i, j, k)] = Pn[v];
         status[c] = (uint8_t)st;
       }
   return 0;
@@ -1185,6 +1211,41 @@ int orc_stage_face_ct(const orc_params* p, double* P, const double* U0, const do
 // Cell-centred field from the faces: B^d of every cell whose two d-faces are both stored (all ghosted
 // cells but the last layer along d) becomes (Bf_d(lower) + Bf_d(upper)) / (2 sqrt(gamma)) at the cell
 // centre; the last layer keeps its value. Periodic blocks get their ghost faces filled first.
+// The face fluxes a flux-CT stage's update uses, from its face fluxes F [3][8][gsize] and edge EMFs
+// E [3][gsize] (the stage's debug outputs): the hydro components (0..4) are F's, the B components the CT
+// fluxes; every face of the interior (index 0..n along its normal, interior across it) is written, the
+// rest of Fused [3][8][gsize] is left as it was.
+int orc_face_fluxes_used(const orc_params* p, const double* F, const double* E, double* Fused) {
+  const Grid g(*p);
+  const long gn = g.gsize();
+  const int N[3] = {g.nx, g.ny, g.nz};
+  for (int d = 0; d < 3; ++d) {
+    int hi[3] = {N[0], N[1], N[2]};
+    hi[d] = N[d] + 1;
+    for (int k = 0; k < hi[2]; ++k)
+      for (int j = 0; j < hi[1]; ++j)
+        for (int i = 0; i < hi[0]; ++i) {
+          const long f = g.gi(i, j, k);
+          for (int v = 0; v < 5; ++v) Fused[(d * 8 + v) * gn + f] = F[(d * 8 + v) * gn + f];
+          double Fb[3];
+          ct_face_flux_b(g, E, d, i, j, k, Fb);
+          for (int c = 0; c < 3; ++c) Fused[(d * 8 + 5 + c) * gn + f] = Fb[c];
+        }
+  }
+  return 0;
+}
+
+// a6 at n points: Un [n][8] densitized conserved states (updated in place when a status bit re-derives the
+// hydro part), P [n][8] and status [n] out; the metric at xyz [n][3].
+int orc_finish_points(const orc_params* p, long n, const double* xyz, double* Un, double* P, uint8_t* status) {
+  for (long q = 0; q < n; ++q) {
+    Geom G;
+    metric_eval(*p, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2], G);
+    status[q] = (uint8_t)finish_cell(*p, G, Un + 8 * q, P + 8 * q, nullptr);
+  }
+  return 0;
+}
+
 int orc_face_b_to_cells(const orc_params* p, double* Bf, double* P) {
   Grid g(*p);
   const long gn = g.gsize();

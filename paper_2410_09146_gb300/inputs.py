@@ -411,3 +411,87 @@ def c2p_states_device(n: int, seed: int, device, gamma_eos: float = GAMMA_DEFAUL
     P[4] = press / (gamma_eos - 1.0)
     P[5:8] = W * torch.sqrt(sig * rho) * db
     return P
+
+
+# ----------------------------------------------------------------------------- two-level block meshes
+@dataclasses.dataclass
+class TwoLevelMesh:
+    """Leaves of a two-level block mesh over an nb[0] x nb[1] x nb[2] grid of root blocks. ``root`` holds the
+    physics options, the cell counts of every block (even), the mesh corner (x0) and the level-0 cell
+    width (dx). Block b has level ``levels[b]`` (0: a root block; 1: one of the 8 children of a refined
+    root block, half the cell width) and position ``pos[b]`` in its level's block lattice (level 1:
+    0 <= pos < 2 nb). ``periodic``: the mesh wraps; else the ghosts outside it keep their loaded values."""
+    root: Setup
+    nb: Tuple[int, int, int]
+    periodic: bool
+    levels: list
+    pos: list
+
+    @property
+    def nblocks(self):
+        return len(self.levels)
+
+    def setup(self, b: int) -> Setup:
+        h = 0.5 ** self.levels[b]
+        dx = tuple(self.root.dx[d] * h for d in range(3))
+        x0 = tuple(self.root.x0[d] + self.pos[b][d] * self.root.n[d] * dx[d] for d in range(3))
+        return dataclasses.replace(self.root, x0=x0, dx=dx, bc="fixed")
+
+    def extent(self):
+        return tuple(self.nb[d] * self.root.n[d] * self.root.dx[d] for d in range(3))
+
+
+def two_level_mesh(root: Setup, nb, refined, periodic: bool) -> TwoLevelMesh:
+    """The root blocks not in ``refined`` (level 0, lattice order, x fastest), then the 8 children of each
+    refined root block in the order given (x fastest)."""
+    refined = [tuple(r) for r in refined]
+    levels, pos = [], []
+    for z in range(nb[2]):
+        for y in range(nb[1]):
+            for x in range(nb[0]):
+                if (x, y, z) not in refined:
+                    levels.append(0)
+                    pos.append((x, y, z))
+    for r in refined:
+        for c in range(8):
+            levels.append(1)
+            pos.append((2 * r[0] + (c & 1), 2 * r[1] + ((c >> 1) & 1), 2 * r[2] + (c >> 2)))
+    return TwoLevelMesh(root=root, nb=tuple(nb), periodic=periodic, levels=levels, pos=pos)
+
+
+def two_level_prims(mesh: TwoLevelMesh, seed: int = 8, amp: float = 0.3, b0=(0.3, 0.0, 0.0), b_amp: float = 0.1,
+                    kmax: int = 1, rho0: float = 1.0):
+    """Seeded smooth state of the whole mesh, evaluated at every block's cells (ghosts included): rho =
+    rho0 (1 + amp tanh f0), rho eps = 1.5 rho0 (1 + amp tanh f1), W v^i = amp tanh f_i, B = b0 + b_amp f_B,
+    each f a sum of random Fourier modes on the mesh's unit cube (periodic on it). Returns [P_b]."""
+    rng = np.random.default_rng(seed)
+    fs = [_SmoothField(rng, kmax=kmax) for _ in range(8)]
+    span = mesh.extent()
+    out = []
+    for b in range(mesh.nblocks):
+        s = mesh.setup(b)
+        u = [(s.cell_centres(d) - mesh.root.x0[d]) / span[d] for d in range(3)]
+        g = [f(*u) for f in fs]
+        P = np.empty(s.prim_shape())
+        P[0] = rho0 * (1.0 + amp * np.tanh(g[0]))
+        P[4] = 1.5 * rho0 * (1.0 + amp * np.tanh(g[1]))
+        for c in range(3):
+            P[1 + c] = amp * np.tanh(g[2 + c])
+            P[5 + c] = b0[c] + b_amp * g[5 + c]
+        out.append(P)
+    return out
+
+
+def two_level_wave_prims(mesh: TwoLevelMesh, background, eigvec, amplitude: float = 1e-6):
+    """Plane wave along x over the whole mesh: background + amplitude * eigvec * sin(2 pi (x - x0) / L) at
+    every block's cells (ghosts included), L the mesh's x extent. Returns [P_b]."""
+    L = mesh.extent()[0]
+    out = []
+    for b in range(mesh.nblocks):
+        s = mesh.setup(b)
+        ph = np.sin(2.0 * math.pi * (s.cell_centres(0) - mesh.root.x0[0]) / L)
+        P = np.empty(s.prim_shape())
+        for v in range(8):
+            P[v] = background[v] + amplitude * eigvec[v] * ph[None, None, :]
+        out.append(P)
+    return out

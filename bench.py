@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-guess", action="store_true")
     ap.add_argument("--no-face-ct", action="store_true")
+    ap.add_argument("--no-two-level", action="store_true")
     ap.add_argument("--guess-states", type=int, default=100_000_000)
     ap.add_argument("--guess-only", action="store_true",
                     help="run only the learned-guess con2prim section and print its JSON (profiling aid)")
@@ -254,6 +255,7 @@ def run_ours(args):
     del cm
     torch.cuda.empty_cache()
     face_ct = None if args.no_face_ct else run_face_ct(G, s_mix, P, Bf, args.steps, args.warmup)
+    two_level = None if args.no_two_level else run_two_level(G, I, s_mix.recon, args.steps, args.warmup)
     del Bf
     guess = None if args.no_guess else run_guess(G, I, rank, n_states=args.guess_states)
     batched = None
@@ -300,6 +302,8 @@ def run_ours(args):
     }
     if face_ct is not None:
         out["face_ct"] = face_ct
+    if two_level is not None:
+        out["two_level"] = two_level
     if batched is not None:
         out["batched"] = batched
     if guess is not None:
@@ -477,6 +481,47 @@ def run_face_ct(G, s_mix, P, Bf, steps, warmup):
     del ctx, B
     torch.cuda.empty_cache()
     return out
+
+
+def two_level_mesh_workload(I, recon, precision):
+    """Kerr-Schild two-level mesh: 4 x 4 x 4 root blocks of 32^3 over [3, 23]^3, the 8 roots next to the hole
+    refined (56 root blocks + 64 children: 120 blocks of 32^3, 3.93 M zones)."""
+    root = I.Setup(n=(32, 32, 32), x0=(3.0, 3.0, 3.0), dx=(20.0 / 128,) * 3, metric="kerr_schild", spin=0.9,
+                   mass=1.0, recon=recon, riemann="hll", bc="fixed", precision=precision)
+    refined = [(x, y, z) for z in range(2) for y in range(2) for x in range(2)]
+    return I.two_level_mesh(root, (4, 4, 4), refined, False)
+
+
+def run_two_level(G, I, recon, steps, warmup):
+    """Stage throughput of the two-level mesh (ghost exchange between levels, refluxing), replayed from CUDA
+    graphs, and the same batch with the mesh switched off (blocks with loaded ghosts, no exchange or
+    refluxing): the difference is what the mesh costs."""
+    import torch
+    m = two_level_mesh_workload(I, recon, "mixed")
+    setups = [m.setup(b) for b in range(m.nblocks)]
+    Ps = I.two_level_prims(m, seed=11)
+    res = {}
+    for mode in ("mesh", "blocks only"):
+        bc = G.BatchContext(setups)
+        for b in range(m.nblocks):
+            bc.set_prims(b, Ps[b])
+        if mode == "mesh":
+            bc.set_mesh(m.nb, m.periodic, m.levels, m.pos)
+        tile, _ = bc.autotune()
+        bc.set_graph(True)
+        for k in range(max(warmup, 2)):
+            bc.stage(*stage_coeffs(k), 0.0)
+        torch.cuda.synchronize()
+        res[mode] = time_stages(bc, 0, steps)
+        del bc
+        torch.cuda.empty_cache()
+    zones = m.nblocks * 32 ** 3
+    ms = res["mesh"] / steps
+    return {"blocks": m.nblocks, "fine_blocks": sum(m.levels), "zones": zones, "ms_per_stage": ms, "steps": steps,
+            "zone_updates_per_s": zones / (ms / 1e3), "ms_per_stage_without_mesh": res["blocks only"] / steps,
+            "mesh_overhead_ms": ms - res["blocks only"] / steps,
+            "scheme": "two-pass ghost exchange (copy, restriction, minmod prolongation), Berger-Colella refluxing",
+            "workload": "Kerr-Schild a = 0.9 over [3, 23]^3: 4^3 root blocks of 32^3, the 8 nearest the hole refined"}
 
 
 def run_batched(G, I, steps, warmup, rank):

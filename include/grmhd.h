@@ -319,6 +319,29 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
  * Errors: GRMHD_E_INVALID (not a batch, block count, sizes, widths or corners off the lattice). */
 int grmhd_batch_set_lattice(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic);
 
+/* Declare that the batch's blocks are the leaves of a two-level block mesh over an nbx x nby x nbz grid of
+ * root blocks (the meshblock AMR the method runs on, Sec. 3; one time step for both levels). level[b] is 0
+ * for a root block and 1 for one of the 8 children of a refined root block (half the cell width);
+ * pos[3b..3b+2] is block b's position in its level's block lattice (0 <= pos < nb, or < 2 nb on level 1).
+ * All blocks have the same cell counts, each even and >= 4; block 0 fixes the level-0 cell width and the
+ * mesh corner; every block's width and interior corner must follow its level and position, and the
+ * leaves must tile the mesh once. Both arrays are read during the call only (host memory).
+ * Every later stage then:
+ *  - starts with a two-pass ghost exchange of the primitives: a ghost over a leaf of its own level copies
+ *    that leaf's cell; a coarse ghost over a fine leaf takes the mean of the 8 fine cells under it; then a
+ *    fine ghost over a coarse leaf takes the coarse cell plus, per direction, the minmod-limited slope
+ *    (of the coarse cell and its two neighbours) times +-1/4 (prolongation). Outside the mesh the
+ *    coordinates wrap when `periodic`; otherwise those ghosts keep their loaded values;
+ *  - ends by refluxing every coarse cell with a face on a fine leaf: that face's flux (for B the flux-CT
+ *    face flux from the edge EMFs) is replaced by the mean of the 4 fine face fluxes covering it,
+ *    U += beta dt s (F_coarse - F_fine) / dx (s = +1 on the cell's upper face, -1 on its lower), and the
+ *    cell takes con2prim (the double solver in both forms), floors and the re-derived hydro state again.
+ * The mesh then conserves every variable to roundoff when periodic (floors aside). (0, 0, 0) switches the
+ * mesh off; declaring a lattice (grmhd_batch_set_lattice) replaces it and vice versa.
+ * Errors: GRMHD_E_INVALID (not a batch, bad arguments, sizes, levels, widths, corners, overlapping or
+ * missing leaves), GRMHD_E_CUDA (upload). */
+int grmhd_batch_set_mesh(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic, const int* level, const int* pos);
+
 /* Load one block's primitives (double, [8][nz+2ng][ny+2ng][nx+2ng]) and derive its conserved state;
  * every block must be loaded before the first stage. */
 int grmhd_batch_set_prims(grmhd_ctx* c, int block, const double* P, int where);

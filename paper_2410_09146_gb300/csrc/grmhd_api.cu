@@ -11,6 +11,7 @@
 #include "../../include/grmhd.h"
 #include "grmhd_device.cuh"
 #include "grmhd_launch.h"
+#include "grmhd_mesh_host.h"
 
 using namespace grmhd;
 
@@ -53,6 +54,12 @@ struct grmhd_ctx {
   int grid_flux;             // persistent grid of the batched flux phase
   bool lattice_on;           // the blocks tile a lattice: ghosts exchanged at the start of every stage
   Lattice lattice;
+  bool mesh_on;              // the blocks are the leaves of a two-level mesh: exchange and refluxing
+  MeshDesc mesh;
+  int* dleaf;                // leaf map of the mesh (workspace, capacity leaf_cap)
+  RefluxCell* dreflux;       // coarse cells at coarse-fine faces (workspace, capacity reflux_cap)
+  long long leaf_cap, reflux_cap;
+  int n_reflux;
   long long total_cells;
   long long total_ghosted;   // nblocks x gsize of block 0 (meaningful for lattices, whose blocks are equal)
   bool use_graph;
@@ -250,7 +257,8 @@ std::vector<WorkItem> build_items(const std::vector<BlockDesc>& blocks, int tile
 }
 
 struct BatchLayout {
-  size_t scal, blocks, items, worklist, wl_mu, floorlist, total;
+  size_t scal, blocks, items, worklist, wl_mu, floorlist, leaf, reflux, total;
+  long long leaf_cap, reflux_cap;
   std::vector<size_t> P, U, F, E, status, geo;  // per block; U and F hold 3 consecutive regions
 };
 
@@ -297,6 +305,15 @@ BatchLayout batch_layout(const grmhd_params* p, int nblocks, const grmhd_block* 
   l.worklist = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(int)) : 0;
   l.wl_mu = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(double)) : 0;
   l.floorlist = take((size_t)cells * sizeof(int));
+  // two-level meshes: a leaf map of at most 8 units per block, and at most every face cell of every block
+  // at a coarse-fine face
+  l.leaf_cap = 8LL * nblocks;
+  l.reflux_cap = 0;
+  for (int b = 0; b < nblocks; ++b)
+    l.reflux_cap += 2LL * ((long long)blocks[b].nx * blocks[b].ny + (long long)blocks[b].ny * blocks[b].nz +
+                           (long long)blocks[b].nx * blocks[b].nz);
+  l.leaf = take((size_t)l.leaf_cap * sizeof(int));
+  l.reflux = take((size_t)l.reflux_cap * sizeof(RefluxCell));
   l.total = off;
   return l;
 }
@@ -580,6 +597,10 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   const int grid = c->grid_persist;
   if (c->lattice_on)
     CK(L.batch_exchange(c->dblocks, c->nblocks, c->total_ghosted, c->lattice, s), "ghost exchange");
+  if (c->mesh_on) {
+    CK(L.mesh_exchange(c->dblocks, c->nblocks, c->total_ghosted, c->mesh, 1, s), "mesh ghost exchange (pass 1)");
+    CK(L.mesh_exchange(c->dblocks, c->nblocks, c->total_ghosted, c->mesh, 2, s), "mesh ghost exchange (pass 2)");
+  }
   CK(L.batch_flux(c->dblocks, flux_items, c->n_items[0], ctr + 0, ms, track ? 1 : 0, c->prm.metric, c->prm.recon,
                    c->grid_flux, s),
      "batched flux");
@@ -588,6 +609,8 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   CK(L.batch_update(c->dblocks, upd_items, c->n_items[2], ctr + 2, a, c->prm.metric, grid, s), "batched update");
   CK(L.batch_floors(c->dblocks, c->nblocks, a, c->prm.metric, grid, s), "batched floor re-derivation");
   if (c->worklist) CK(L.batch_deferred(c->dblocks, c->nblocks, a, c->prm.metric, grid, s), "batched deferred con2prim");
+  if (c->mesh_on && c->n_reflux > 0)
+    CK(L.mesh_reflux(c->dblocks, c->dreflux, c->n_reflux, a, c->prm.metric, s), "refluxing");
   return GRMHD_OK;
 }
 
@@ -810,6 +833,12 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   c->total_cells = off;
   c->total_ghosted = (long long)nblocks * c->hblocks[0].p.gsize;
   c->lattice_on = false;
+  c->mesh_on = false;
+  c->dleaf = (int*)(c->ws + l.leaf);
+  c->dreflux = (RefluxCell*)(c->ws + l.reflux);
+  c->leaf_cap = l.leaf_cap;
+  c->reflux_cap = l.reflux_cap;
+  c->n_reflux = 0;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -877,6 +906,47 @@ int grmhd_batch_set_lattice(grmhd_ctx* c, int nbx, int nby, int nbz, int periodi
     c->lattice.nb[2] = nbz;
     c->lattice.periodic = periodic ? 1 : 0;
     c->lattice_on = true;
+    c->mesh_on = false;
+  }
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  return GRMHD_OK;
+}
+
+int grmhd_batch_set_mesh(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic, const int* level, const int* pos) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "not a batch context") : GRMHD_E_INVALID;
+  if (nbx == 0 && nby == 0 && nbz == 0) {
+    c->mesh_on = false;
+  } else {
+    if (nbx < 1 || nby < 1 || nbz < 1 || !level || !pos) return fail(c, GRMHD_E_INVALID, "bad mesh arguments");
+    if (8LL * nbx * nby * nbz > c->leaf_cap) return fail(c, GRMHD_E_INVALID, "more root blocks than the batch's leaves can tile");
+    std::vector<DevParams> bp(c->nblocks);
+    for (int b = 0; b < c->nblocks; ++b) bp[b] = c->hblocks[b].p;
+    std::vector<int> leaf;
+    std::vector<RefluxCell> cells;
+    const char* why = build_mesh_tables(bp.data(), c->nblocks, nbx, nby, nbz, periodic, level, pos, leaf, cells);
+    if (why) return fail(c, GRMHD_E_INVALID, why);
+    const long long units = (long long)leaf.size();
+    if ((long long)cells.size() > c->reflux_cap) return fail(c, GRMHD_E_INVALID, "too many coarse-fine cells");
+    for (int b = 0; b < c->nblocks; ++b) {
+      c->hblocks[b].level = level[b];
+      for (int d = 0; d < 3; ++d) c->hblocks[b].pos[d] = pos[3 * b + d];
+    }
+    CK(cudaMemcpyAsync(c->dleaf, leaf.data(), sizeof(int) * units, cudaMemcpyHostToDevice, c->stream), "mesh leaf map");
+    if (!cells.empty())
+      CK(cudaMemcpyAsync(c->dreflux, cells.data(), sizeof(RefluxCell) * cells.size(), cudaMemcpyHostToDevice, c->stream),
+         "mesh reflux cells");
+    CK(cudaMemcpyAsync(c->dblocks, c->hblocks.data(), sizeof(BlockDesc) * c->nblocks, cudaMemcpyHostToDevice, c->stream),
+       "mesh block descriptors");
+    CK(cudaStreamSynchronize(c->stream), "mesh upload");
+    c->mesh.nb[0] = nbx;
+    c->mesh.nb[1] = nby;
+    c->mesh.nb[2] = nbz;
+    c->mesh.periodic = periodic ? 1 : 0;
+    c->mesh.leaf = c->dleaf;
+    c->n_reflux = (int)cells.size();
+    c->mesh_on = true;
+    c->lattice_on = false;
   }
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();

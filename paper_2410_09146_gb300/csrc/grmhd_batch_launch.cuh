@@ -2,6 +2,7 @@
 #pragma once
 
 #include "grmhd_kernels.cuh"
+#include "grmhd_mesh.cuh"
 #include "grmhd_launch.h"
 
 namespace grmhd {
@@ -75,6 +76,21 @@ struct BatchLaunch {
   }
   static cudaError_t exchange(const BlockDesc* b, int nblocks, long long ghosted_cells, const Lattice& L, cudaStream_t s) {
     k_batch_exchange<T><<<grid_for(ghosted_cells, 256), 256, 0, s>>>(b, nblocks, L);
+    return cudaGetLastError();
+  }
+  static cudaError_t mesh_exchange(const BlockDesc* b, int nblocks, long long ghosted_cells, const MeshDesc& M,
+                                   int pass, cudaStream_t s) {
+    k_mesh_exchange<T><<<grid_for(ghosted_cells, 256), 256, 0, s>>>(b, nblocks, M, pass);
+    return cudaGetLastError();
+  }
+  static cudaError_t mesh_reflux(const BlockDesc* b, const RefluxCell* cells, int ncells, const BatchArgs& a,
+                                 int metric, cudaStream_t s) {
+    if (ncells <= 0) return cudaSuccess;
+    const int grid = (ncells + 127) / 128;
+    if (metric == KERR_SCHILD)
+      k_mesh_reflux<KERR_SCHILD, R, T><<<grid, 128, 0, s>>>(b, cells, ncells, a);
+    else
+      k_mesh_reflux<MINKOWSKI, R, T><<<grid, 128, 0, s>>>(b, cells, ncells, a);
     return cudaGetLastError();
   }
   static int ctas_per_sm(int metric) {

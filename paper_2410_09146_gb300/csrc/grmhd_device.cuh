@@ -85,6 +85,8 @@ struct BlockDesc {
   double* U[3];           // conserved-state slots
   uint8_t* status;
   long long cell_offset;  // index of the block's first interior cell in the batch
+  int level;              // two-level mesh: 0 (root block) or 1 (child of a refined root block)
+  int pos[3];             // two-level mesh: position in its level's block lattice
 };
 
 // A contiguous range of flux units (faces, or runs of faces: flux_units) / edges / cells of one block
@@ -102,6 +104,23 @@ struct WorkItem {
 struct Lattice {
   int nb[3];
   int periodic;
+};
+
+// A batch whose blocks, all of the same size, are the leaves of a two-level mesh over an nb[0] x nb[1] x
+// nb[2] grid of root blocks (BlockDesc::level / pos). leaf: the block covering each fine-block-sized unit
+// of the mesh, [2 nb[2]][2 nb[1]][2 nb[0]] (a root block covers 2 x 2 x 2 units). periodic: the mesh wraps.
+struct MeshDesc {
+  int nb[3];
+  int periodic;
+  const int* leaf;
+};
+
+// A coarse cell with at least one face on a fine leaf: fine[2 d + s] is the fine block across its lower
+// (s = 0) or upper (s = 1) face of direction d, or -1.
+struct RefluxCell {
+  int block;
+  int cell;
+  int fine[6];
 };
 
 // Coefficients and bookkeeping shared by every block of a batched stage.

@@ -105,7 +105,8 @@ using BL = BatchLaunch<double, double>;
 const FormLaunchers kFp64 = {ghost, flux, emf, update, cell_passes, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
                                 BL::deferred, BL::ctas_per_sm, 8, 8, geometry, BL::floors,
                                 FC::emf, FC::faces, FC::to_cells, FC::ghost_faces,
-                                BL::flux_ctas_per_sm, BL::exchange};
+                                BL::flux_ctas_per_sm, BL::exchange, BL::mesh_exchange,
+                                BL::mesh_reflux};
 
 }  // namespace
 

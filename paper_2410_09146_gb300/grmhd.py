@@ -93,6 +93,8 @@ def lib():
         L.grmhd_batch_get.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_batch_set_tile.argtypes = [vp, ctypes.c_int]
         L.grmhd_batch_set_lattice.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.grmhd_batch_set_mesh.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
         L.grmhd_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.grmhd_set_graph.argtypes = [vp, ctypes.c_int]
         fp = ctypes.POINTER(ctypes.c_float)
@@ -300,6 +302,14 @@ def grmhd_batch_set_lattice(ctx: int, nbx: int, nby: int, nbz: int, periodic: bo
     _check(lib().grmhd_batch_set_lattice(ctx, nbx, nby, nbz, int(periodic)), ctx)
 
 
+def grmhd_batch_set_mesh(ctx: int, nbx: int, nby: int, nbz: int, periodic: bool, level, pos) -> None:
+    lv = np.ascontiguousarray(level, dtype=np.int32).ravel()
+    ps = np.ascontiguousarray(pos, dtype=np.int32).ravel()
+    ip = ctypes.POINTER(ctypes.c_int)
+    _check(lib().grmhd_batch_set_mesh(ctx, nbx, nby, nbz, int(periodic), lv.ctypes.data_as(ip), ps.ctypes.data_as(ip)),
+           ctx)
+
+
 def grmhd_batch_set_prims(ctx: int, block: int, P) -> None:
     ptr, where = _ptr(P)
     _check(lib().grmhd_batch_set_prims(ctx, block, ctypes.c_void_p(ptr), where), ctx)
@@ -388,6 +398,10 @@ class BatchContext:
 
     def set_lattice(self, nb, periodic):
         grmhd_batch_set_lattice(self.ctx, nb[0], nb[1], nb[2], periodic)
+
+    def set_mesh(self, nb, periodic, level, pos):
+        """Declare the blocks the leaves of a two-level mesh (``grmhd_batch_set_mesh``)."""
+        grmhd_batch_set_mesh(self.ctx, nb[0], nb[1], nb[2], periodic, level, pos)
 
     def autotune(self):
         return grmhd_batch_autotune(self.ctx)

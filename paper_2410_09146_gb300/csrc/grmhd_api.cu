@@ -57,6 +57,9 @@ struct grmhd_ctx {
   bool mesh_on;              // the blocks are the leaves of a two-level mesh: exchange and refluxing
   MeshDesc mesh;
   int* dleaf;                // leaf map of the mesh (workspace, capacity leaf_cap)
+  unsigned* dghost;          // ghost cells of a mesh block (workspace, capacity ghost_cap)
+  int* dfine;                // level-1 blocks of the mesh (workspace, nblocks entries)
+  long long ghost_cap;
   RefluxCell* dreflux;       // coarse cells at coarse-fine faces (workspace, capacity reflux_cap)
   long long leaf_cap, reflux_cap;
   int n_reflux;
@@ -257,8 +260,8 @@ std::vector<WorkItem> build_items(const std::vector<BlockDesc>& blocks, int tile
 }
 
 struct BatchLayout {
-  size_t scal, blocks, items, worklist, wl_mu, floorlist, leaf, reflux, total;
-  long long leaf_cap, reflux_cap;
+  size_t scal, blocks, items, worklist, wl_mu, floorlist, leaf, reflux, ghost, fine, total;
+  long long leaf_cap, reflux_cap, ghost_cap;
   std::vector<size_t> P, U, F, E, status, geo;  // per block; U and F hold 3 consecutive regions
 };
 
@@ -312,8 +315,15 @@ BatchLayout batch_layout(const grmhd_params* p, int nblocks, const grmhd_block* 
   for (int b = 0; b < nblocks; ++b)
     l.reflux_cap += 2LL * ((long long)blocks[b].nx * blocks[b].ny + (long long)blocks[b].ny * blocks[b].nz +
                            (long long)blocks[b].nx * blocks[b].nz);
+  l.ghost_cap = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    const DevParams d = block_params(p, blocks[b]);
+    if (d.gsize - d.isize > l.ghost_cap) l.ghost_cap = d.gsize - d.isize;
+  }
   l.leaf = take((size_t)l.leaf_cap * sizeof(int));
   l.reflux = take((size_t)l.reflux_cap * sizeof(RefluxCell));
+  l.ghost = take((size_t)l.ghost_cap * sizeof(unsigned));
+  l.fine = take((size_t)nblocks * sizeof(int));
   l.total = off;
   return l;
 }
@@ -598,8 +608,8 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   if (c->lattice_on)
     CK(L.batch_exchange(c->dblocks, c->nblocks, c->total_ghosted, c->lattice, s), "ghost exchange");
   if (c->mesh_on) {
-    CK(L.mesh_exchange(c->dblocks, c->nblocks, c->total_ghosted, c->mesh, 1, s), "mesh ghost exchange (pass 1)");
-    CK(L.mesh_exchange(c->dblocks, c->nblocks, c->total_ghosted, c->mesh, 2, s), "mesh ghost exchange (pass 2)");
+    CK(L.mesh_exchange(c->dblocks, c->nblocks, c->mesh, 1, s), "mesh ghost exchange (pass 1)");
+    CK(L.mesh_exchange(c->dblocks, c->nblocks, c->mesh, 2, s), "mesh ghost exchange (pass 2)");
   }
   CK(L.batch_flux(c->dblocks, flux_items, c->n_items[0], ctr + 0, ms, track ? 1 : 0, c->prm.metric, c->prm.recon,
                    c->grid_flux, s),
@@ -836,6 +846,9 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   c->mesh_on = false;
   c->dleaf = (int*)(c->ws + l.leaf);
   c->dreflux = (RefluxCell*)(c->ws + l.reflux);
+  c->dghost = (unsigned*)(c->ws + l.ghost);
+  c->dfine = (int*)(c->ws + l.fine);
+  c->ghost_cap = l.ghost_cap;
   c->leaf_cap = l.leaf_cap;
   c->reflux_cap = l.reflux_cap;
   c->n_reflux = 0;
@@ -922,10 +935,13 @@ int grmhd_batch_set_mesh(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic, 
     if (8LL * nbx * nby * nbz > c->leaf_cap) return fail(c, GRMHD_E_INVALID, "more root blocks than the batch's leaves can tile");
     std::vector<DevParams> bp(c->nblocks);
     for (int b = 0; b < c->nblocks; ++b) bp[b] = c->hblocks[b].p;
-    std::vector<int> leaf;
+    std::vector<int> leaf, fine;
     std::vector<RefluxCell> cells;
-    const char* why = build_mesh_tables(bp.data(), c->nblocks, nbx, nby, nbz, periodic, level, pos, leaf, cells);
+    std::vector<unsigned> ghost;
+    const char* why =
+        build_mesh_tables(bp.data(), c->nblocks, nbx, nby, nbz, periodic, level, pos, leaf, cells, ghost, fine);
     if (why) return fail(c, GRMHD_E_INVALID, why);
+    if ((long long)ghost.size() > c->ghost_cap) return fail(c, GRMHD_E_INVALID, "ghost table larger than reserved");
     const long long units = (long long)leaf.size();
     if ((long long)cells.size() > c->reflux_cap) return fail(c, GRMHD_E_INVALID, "too many coarse-fine cells");
     for (int b = 0; b < c->nblocks; ++b) {
@@ -936,6 +952,11 @@ int grmhd_batch_set_mesh(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic, 
     if (!cells.empty())
       CK(cudaMemcpyAsync(c->dreflux, cells.data(), sizeof(RefluxCell) * cells.size(), cudaMemcpyHostToDevice, c->stream),
          "mesh reflux cells");
+    CK(cudaMemcpyAsync(c->dghost, ghost.data(), sizeof(unsigned) * ghost.size(), cudaMemcpyHostToDevice, c->stream),
+       "mesh ghost table");
+    if (!fine.empty())
+      CK(cudaMemcpyAsync(c->dfine, fine.data(), sizeof(int) * fine.size(), cudaMemcpyHostToDevice, c->stream),
+         "mesh fine blocks");
     CK(cudaMemcpyAsync(c->dblocks, c->hblocks.data(), sizeof(BlockDesc) * c->nblocks, cudaMemcpyHostToDevice, c->stream),
        "mesh block descriptors");
     CK(cudaStreamSynchronize(c->stream), "mesh upload");
@@ -944,6 +965,10 @@ int grmhd_batch_set_mesh(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic, 
     c->mesh.nb[2] = nbz;
     c->mesh.periodic = periodic ? 1 : 0;
     c->mesh.leaf = c->dleaf;
+    c->mesh.ghost = c->dghost;
+    c->mesh.nghost = (int)ghost.size();
+    c->mesh.fine = c->dfine;
+    c->mesh.nfine = (int)fine.size();
     c->n_reflux = (int)cells.size();
     c->mesh_on = true;
     c->lattice_on = false;

@@ -78,19 +78,22 @@ struct BatchLaunch {
     k_batch_exchange<T><<<grid_for(ghosted_cells, 256), 256, 0, s>>>(b, nblocks, L);
     return cudaGetLastError();
   }
-  static cudaError_t mesh_exchange(const BlockDesc* b, int nblocks, long long ghosted_cells, const MeshDesc& M,
-                                   int pass, cudaStream_t s) {
-    k_mesh_exchange<T><<<grid_for(ghosted_cells, 256), 256, 0, s>>>(b, nblocks, M, pass);
+  static cudaError_t mesh_exchange(const BlockDesc* b, int nblocks, const MeshDesc& M, int pass, cudaStream_t s) {
+    const int ny = pass == 2 ? M.nfine : nblocks;
+    if (ny <= 0 || M.nghost <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((M.nghost + 255) / 256), (unsigned)ny);
+    k_mesh_exchange<T><<<grid, 256, 0, s>>>(b, M, pass);
     return cudaGetLastError();
   }
   static cudaError_t mesh_reflux(const BlockDesc* b, const RefluxCell* cells, int ncells, const BatchArgs& a,
                                  int metric, cudaStream_t s) {
     if (ncells <= 0) return cudaSuccess;
-    const int grid = (ncells + 127) / 128;
+    // 64-thread CTAs: the reflux cells are few (a face layer), so spread them over as many SMs as possible
+    const int grid = (ncells + 63) / 64;
     if (metric == KERR_SCHILD)
-      k_mesh_reflux<KERR_SCHILD, R, T><<<grid, 128, 0, s>>>(b, cells, ncells, a);
+      k_mesh_reflux<KERR_SCHILD, R, T><<<grid, 64, 0, s>>>(b, cells, ncells, a);
     else
-      k_mesh_reflux<MINKOWSKI, R, T><<<grid, 128, 0, s>>>(b, cells, ncells, a);
+      k_mesh_reflux<MINKOWSKI, R, T><<<grid, 64, 0, s>>>(b, cells, ncells, a);
     return cudaGetLastError();
   }
   static int ctas_per_sm(int metric) {

@@ -113,6 +113,13 @@ struct MeshDesc {
   int nb[3];
   int periodic;
   const int* leaf;
+  // the ghost cells of a block (all blocks have the same extents): ghosted indices packed as
+  // i | j << 10 | k << 20, nghost of them
+  const unsigned* ghost;
+  int nghost;
+  // the level-1 blocks (the only ones pass 2 writes to)
+  const int* fine;
+  int nfine;
 };
 
 // A coarse cell with at least one face on a fine leaf: fine[2 d + s] is the fine block across its lower

@@ -53,8 +53,7 @@ struct FormLaunchers {
                                 cudaStream_t s);
   // two-level mesh (grmhd_mesh.cuh): one pass (1 or 2) of the ghost exchange, and the refluxing of the
   // coarse cells at coarse-fine faces after the update
-  cudaError_t (*mesh_exchange)(const BlockDesc* b, int nblocks, long long ghosted_cells, const MeshDesc& M, int pass,
-                               cudaStream_t s);
+  cudaError_t (*mesh_exchange)(const BlockDesc* b, int nblocks, const MeshDesc& M, int pass, cudaStream_t s);
   cudaError_t (*mesh_reflux)(const BlockDesc* b, const RefluxCell* cells, int ncells, const BatchArgs& a, int metric,
                              cudaStream_t s);
 };

@@ -20,20 +20,20 @@ __device__ __forceinline__ int mesh_leaf(const MeshDesc& M, int fx, int fy, int 
   return M.leaf[fx / n[0] + 2 * M.nb[0] * (fy / n[1] + 2 * M.nb[1] * (fz / n[2]))];
 }
 
+// One pass of the exchange. Grid: (x: ghost cells of a block, y: blocks; pass 2: the level-1 blocks only).
+// The restriction and prolongation arithmetic is in the storage type of the primitives (float in the mixed
+// form, where conversions to double would share the FP64 pipe; double in the all-FP64 form).
 template <class T>
-__global__ void k_mesh_exchange(const BlockDesc* __restrict__ blocks, int nblocks, MeshDesc M, int pass) {
-  const DevParams& p0 = blocks[0].p;  // every block of a mesh has the same cell counts
-  const long long G = p0.gsize;
-  const int n[3] = {p0.nx, p0.ny, p0.nz};
-  const long long total = (long long)nblocks * G;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(t / G);
-    const long long g = t - (long long)b * G;
-    const int c[3] = {(int)(g % p0.gx) - p0.ng, (int)((g / p0.gx) % p0.gy) - p0.ng,
-                      (int)(g / ((long long)p0.gx * p0.gy)) - p0.ng};
-    if (c[0] >= 0 && c[0] < n[0] && c[1] >= 0 && c[1] < n[1] && c[2] >= 0 && c[2] < n[2]) continue;
-    const BlockDesc& D = blocks[b];
-    const int lev = D.level;
+__global__ void __launch_bounds__(256) k_mesh_exchange(const BlockDesc* __restrict__ blocks, MeshDesc M, int pass) {
+  const int b = pass == 2 ? M.fine[blockIdx.y] : (int)blockIdx.y;
+  const BlockDesc& D = blocks[b];
+  const DevParams& p = D.p;  // every block of a mesh has the same cell counts
+  const long long G = p.gsize;
+  const int n[3] = {p.nx, p.ny, p.nz};
+  const int lev = D.level;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M.nghost; e += gridDim.x * blockDim.x) {
+    const unsigned pk = M.ghost[e];
+    const int c[3] = {(int)(pk & 1023u) - p.ng, (int)((pk >> 10) & 1023u) - p.ng, (int)(pk >> 20) - p.ng};
     int gl[3];
     bool outside = false;
 #pragma unroll
@@ -42,13 +42,14 @@ __global__ void k_mesh_exchange(const BlockDesc* __restrict__ blocks, int nblock
       int gd = D.pos[d] * n[d] + c[d];
       if (gd < 0 || gd >= N) {
         outside = true;
-        gd = ((gd % N) + N) % N;
+        gd = gd < 0 ? gd + N : gd - N;  // ghosts are at most ng < n cells outside, so one wrap suffices
       }
       gl[d] = gd;
     }
     if (outside && !M.periodic) continue;
     const int src = lev ? mesh_leaf(M, gl[0], gl[1], gl[2], n) : mesh_leaf(M, 2 * gl[0], 2 * gl[1], 2 * gl[2], n);
     const BlockDesc& S = blocks[src];
+    const long long g = gidx(p, c[0], c[1], c[2]);
     const T* __restrict__ Ps = (const T*)S.P;
     T* __restrict__ Pd = (T*)D.P;
     if (pass == 1 && S.level == lev) {
@@ -62,31 +63,32 @@ __global__ void k_mesh_exchange(const BlockDesc* __restrict__ blocks, int nblock
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const T* a = Ps + q * G + g0;
-        double acc = 0.0;
+        T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc += (double)a[(k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz];
-        Pd[q * G + g] = (T)(acc / 8.0);
+        for (int k = 0; k < 8; ++k) acc += a[(k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz];
+        Pd[q * G + g] = acc / T(8);
       }
-    } else if (pass == 2 && lev == 1 && S.level == 0) {
+    } else if (pass == 2 && S.level == 0) {
       // prolongation from the coarse cell containing this fine ghost (an interior cell of S)
       const long long gc = gidx(S.p, (gl[0] >> 1) - S.pos[0] * n[0], (gl[1] >> 1) - S.pos[1] * n[1],
                                 (gl[2] >> 1) - S.pos[2] * n[2]);
       const long long st[3] = {1, S.p.gx, (long long)S.p.gx * S.p.gy};
-      double off[3];
+      T off[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) off[d] = (gl[d] & 1) ? 0.25 : -0.25;
+      for (int d = 0; d < 3; ++d) off[d] = (gl[d] & 1) ? T(0.25) : T(-0.25);
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const T* a = Ps + q * G + gc;
-        const double pc = (double)a[0];
-        double v = pc;
+        const T pc = a[0];
+        T v = pc;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const double up = (double)a[st[d]] - pc, dn = pc - (double)a[-st[d]];
-          const double m = up * dn > 0.0 ? (up > 0.0 ? fmin(up, dn) : fmax(up, dn)) : 0.0;
+          const T up = a[st[d]] - pc, dn = pc - a[-st[d]];
+          // minmod: the smaller slope in magnitude when both have the same sign, else 0
+          const T m = up * dn > T(0) ? (up > T(0) ? (up < dn ? up : dn) : (up > dn ? up : dn)) : T(0);
           v = v + off[d] * m;
         }
-        Pd[q * G + g] = (T)v;
+        Pd[q * G + g] = v;
       }
     }
   }
@@ -120,7 +122,7 @@ __device__ __forceinline__ void face_flux_used(const DevParams& p, const R* __re
 }
 
 template <int METRIC, class R, class T>
-__global__ void __launch_bounds__(128) k_mesh_reflux(const BlockDesc* __restrict__ blocks,
+__global__ void __launch_bounds__(64) k_mesh_reflux(const BlockDesc* __restrict__ blocks,
                                                      const RefluxCell* __restrict__ cells, int ncells, BatchArgs a) {
   const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
   const double bdt = a.beta * dt;

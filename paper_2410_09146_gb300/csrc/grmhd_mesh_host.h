@@ -10,17 +10,22 @@
 namespace grmhd {
 
 // Blocks bp[0..nblocks) (cell counts, widths, corners) with level[b] and pos[3b..3b+2] as documented for
-// grmhd_batch_set_mesh. Fills leaf ([2 nbz][2 nby][2 nbx], the block covering each fine-block-sized unit)
-// and cells (every coarse cell with a face on a fine leaf). Returns NULL, or why the mesh is refused.
+// grmhd_batch_set_mesh. Fills leaf ([2 nbz][2 nby][2 nbx], the block covering each fine-block-sized unit),
+// cells (every coarse cell with a face on a fine leaf), ghost (the ghosted indices of a block's ghost
+// cells, packed i | j << 10 | k << 20) and fine (the level-1 blocks). Returns NULL, or why the mesh is
+// refused.
 inline const char* build_mesh_tables(const DevParams* bp, int nblocks, int nbx, int nby, int nbz, int periodic,
                                      const int* level, const int* pos, std::vector<int>& leaf,
-                                     std::vector<RefluxCell>& cells) {
+                                     std::vector<RefluxCell>& cells, std::vector<unsigned>& ghost,
+                                     std::vector<int>& fine) {
   if (nblocks < 1 || nbx < 1 || nby < 1 || nbz < 1 || !level || !pos) return "bad mesh arguments";
+  if (nblocks > 65535) return "a mesh holds at most 65535 blocks";
   const int nb[3] = {nbx, nby, nbz};
   const DevParams& a = bp[0];
   const int n[3] = {a.nx, a.ny, a.nz};
   for (int d = 0; d < 3; ++d)
-    if (n[d] % 2 != 0 || n[d] < 4) return "mesh blocks need even cell counts >= 4";
+    if (n[d] % 2 != 0 || n[d] < 4 || n[d] < a.ng) return "mesh blocks need even cell counts >= max(4, ng)";
+  if (a.gx > 1024 || a.gy > 1024 || a.gz > 1024) return "mesh blocks need ghosted extents <= 1024";
   if (level[0] != 0 && level[0] != 1) return "levels must be 0 or 1";
   // the level-0 cell width and the mesh corner, from block 0
   double dx0[3], X0[3];
@@ -89,6 +94,16 @@ inline const char* build_mesh_tables(const DevParams* bp, int nblocks, int nbx, 
           if (any) cells.push_back(rc);
         }
   }
+  ghost.clear();
+  for (int k = 0; k < a.gz; ++k)
+    for (int j = 0; j < a.gy; ++j)
+      for (int i = 0; i < a.gx; ++i) {
+        const bool in = i >= a.ng && i < a.ng + n[0] && j >= a.ng && j < a.ng + n[1] && k >= a.ng && k < a.ng + n[2];
+        if (!in) ghost.push_back((unsigned)i | ((unsigned)j << 10) | ((unsigned)k << 20));
+      }
+  fine.clear();
+  for (int b = 0; b < nblocks; ++b)
+    if (level[b] == 1) fine.push_back(b);
   return nullptr;
 }
 

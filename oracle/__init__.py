@@ -88,6 +88,8 @@ def _load():
         lib.orc_stage_face_ct.argtypes = lib.orc_stage.argtypes + [dp, dp, dp]
         lib.orc_face_b_to_cells.argtypes = [P, dp, dp]
         lib.orc_face_fluxes_used.argtypes = [P, dp, dp, dp]
+        lib.orc_stage_scalar.argtypes = [P, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, dp, dp, ip, dp, dp, dp, dp]
         lib.orc_finish_points.argtypes = [P, L, dp, dp, dp, u8p]
         _lib = lib
     return _lib
@@ -231,6 +233,34 @@ def stage(p: OrcParams, P, U0, Ucur, g0: float, g1: float, beta: float, dt: floa
     if debug:
         out["F"], out["E"] = F, E
     return out
+
+
+def stage_scalar(p: OrcParams, P, X, U0, Ucur, DX0, DXcur, g0: float, g1: float, beta: float, dt: float):
+    """One flux-CT stage that also advances a passive scalar X (ghosted [gz][gy][gx], updated in place like P)
+    with conserved sqrt(gamma) D X (DX0 / DXcur interior arrays; DX0 may be None when g0 = 0).
+    Returns dict(U, DX, status, dt, maxspeed, iters)."""
+    assert P.dtype == np.float64 and P.flags.c_contiguous and X.dtype == np.float64 and X.flags.c_contiguous
+    Unew = np.zeros_like(Ucur)
+    DXnew = np.zeros_like(DXcur)
+    st = np.zeros(Ucur.shape[1:], np.uint8)
+    dt_used = ctypes.c_double(0.0)
+    ms = np.zeros(3)
+    it = ctypes.c_int(0)
+    DX0 = None if DX0 is None else np.ascontiguousarray(DX0, dtype=np.float64)
+    DXcur = np.ascontiguousarray(DXcur, dtype=np.float64)
+    _load().orc_stage_scalar(ctypes.byref(p), _dp(P), _dp(None if U0 is None else np.ascontiguousarray(U0)),
+                             _dp(np.ascontiguousarray(Ucur)), _dp(Unew),
+                             st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), g0, g1, beta, dt,
+                             ctypes.byref(dt_used), _dp(ms), ctypes.byref(it), _dp(X), _dp(DX0), _dp(DXcur), _dp(DXnew))
+    return dict(U=Unew, DX=DXnew, status=st, dt=dt_used.value, maxspeed=ms, iters=it.value)
+
+
+def rk2_step_scalar(p: OrcParams, P, X, U, DX, dt: float = 0.0):
+    """SSP-RK2 step of the fluid and the passive scalar (stage coefficients as ``rk2_step``).
+    Returns (U, DX, status, dt)."""
+    s1 = stage_scalar(p, P, X, None, U, None, DX, 0.0, 1.0, 1.0, dt)
+    s2 = stage_scalar(p, P, X, U, s1["U"], DX, s1["DX"], 0.5, 0.5, 0.5, s1["dt"])
+    return s2["U"], s2["DX"], s2["status"], s1["dt"]
 
 
 def face_fluxes_used(p: OrcParams, F, E):

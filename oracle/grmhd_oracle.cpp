@@ -674,7 +674,7 @@ struct Grid {
 
 static int wrap(int i, int n) { return ((i % n) + n) % n; }
 
-static void ghost_fill_periodic(const Grid& g, double* P) {
+static void ghost_fill_periodic(const Grid& g, double* P, int nvar = 8) {
   const long n = g.gsize();
   for (int k = -g.ng; k < g.nz + g.ng; ++k)
     for (int j = -g.ng; j < g.ny + g.ng; ++j)
@@ -682,7 +682,7 @@ static void ghost_fill_periodic(const Grid& g, double* P) {
         bool interior = i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz;
         if (interior) continue;
         long dst = g.gi(i, j, k), src = g.gi(wrap(i, g.nx), wrap(j, g.ny), wrap(k, g.nz));
-        for (int v = 0; v < 8; ++v) P[v * n + dst] = P[v * n + src];
+        for (int v = 0; v < nvar; ++v) P[v * n + dst] = P[v * n + src];
       }
 }
 
@@ -1194,6 +1194,69 @@ int orc_stage(const orc_params* p, double* P, const double* U0, const double* Uc
               double* Fdbg, double* Edbg) {
   return stage_impl(p, P, U0, Ucur, Unew, status, g0, g1, beta, dt, dt_used, maxspeed, iters_total, Fdbg, Edbg,
                     nullptr, nullptr, nullptr);
+}
+
+// One flux-CT RK stage that also advances a passive scalar (Sec. 2.1: Phoebus evolves passive scalars X by
+// (X rho u^mu)_{;mu} = S, the electron fraction Y_e with the radiation's lepton exchange as S; without
+// radiation S = 0). Conserved: sqrt(gamma) D X (D = rho W); primitive: X, [gsize] ghosted like P (its
+// ghosts filled first when periodic). Reading (the discretisation is not given): X is reconstructed like
+// the primitives, and the face flux of sqrt(gamma) D X is the face mass flux of the stage (sqrt(-g) F^d_D
+// after the Riemann solver) times X on the upwind side of that flux (either side when it is zero);
+// DXnew = g0 DX0 + g1 DXcur - beta dt div F_X; then X = DXnew / (sqrt(gamma) D) with the stage's final
+// sqrt(gamma) D (after floors: a floor that adds mass dilutes X, D X stays conserved). DX0 may be NULL
+// when g0 = 0. The other arguments are those of orc_stage.
+int orc_stage_scalar(const orc_params* p, double* P, const double* U0, const double* Ucur, double* Unew,
+                     uint8_t* status, double g0, double g1, double beta, double dt, double* dt_used, double* maxspeed,
+                     int* iters_total, double* X, const double* DX0, const double* DXcur, double* DXnew) {
+  const Grid g(*p);
+  const long gn = g.gsize(), in = g.isize();
+  const int N[3] = {g.nx, g.ny, g.nz};
+  std::vector<double> F(3 * 8 * gn, 0.0);
+  const int rc = stage_impl(p, P, U0, Ucur, Unew, status, g0, g1, beta, dt, dt_used, maxspeed, iters_total,
+                            F.data(), nullptr, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  dt = *dt_used;
+  if (p->bc == 0) ghost_fill_periodic(g, X, 1);
+  // face fluxes of sqrt(gamma) D X on the faces of the interior
+  std::vector<double> FX(3 * gn, 0.0);
+  for (int d = 0; d < 3; ++d) {
+    int hi[3] = {N[0], N[1], N[2]};
+    hi[d] = N[d] + 1;
+    for (int k = 0; k < hi[2]; ++k)
+      for (int j = 0; j < hi[1]; ++j)
+        for (int i = 0; i < hi[0]; ++i) {
+          double sL[5], sR[5];
+          for (int q = 0; q < 5; ++q) {
+            int cl[3] = {i, j, k}, cr[3] = {i, j, k};
+            cl[d] += q - 3;  // stencil of the cell below the face
+            cr[d] += q - 2;  // stencil of the cell above it
+            sL[q] = X[g.gi(cl[0], cl[1], cl[2])];
+            sR[q] = X[g.gi(cr[0], cr[1], cr[2])];
+          }
+          double qm, qp, XL, XR;
+          recon_cell(p->recon, sL, p->weno_eps, qm, qp);
+          XL = qp;
+          recon_cell(p->recon, sR, p->weno_eps, qm, qp);
+          XR = qm;
+          const long f = g.gi(i, j, k);
+          const double mdot = F[(d * 8 + 0) * gn + f];
+          FX[d * gn + f] = mdot * (mdot >= 0.0 ? XL : XR);
+        }
+  }
+  for (int k = 0; k < N[2]; ++k)
+    for (int j = 0; j < N[1]; ++j)
+      for (int i = 0; i < N[0]; ++i) {
+        auto Fv = [&](int d, int a, int b, int c) { return FX[d * gn + g.gi(a, b, c)]; };
+        const double div = (Fv(0, i + 1, j, k) - Fv(0, i, j, k)) / p->dx[0] +
+                           (Fv(1, i, j + 1, k) - Fv(1, i, j, k)) / p->dx[1] +
+                           (Fv(2, i, j, k + 1) - Fv(2, i, j, k)) / p->dx[2];
+        const long c = g.ii(i, j, k);
+        const double x0 = DX0 ? DX0[c] : 0.0;
+        DXnew[c] = g0 * x0 + g1 * DXcur[c] + beta * dt * (-div);
+        X[g.gi(i, j, k)] = DXnew[c] / Unew[c];  // Unew[0 * in + c]: the densitized D
+      }
+  (void)in;
+  return 0;
 }
 
 // One RK stage with face-centred upwind CT. Bfcur [3][gsize] is the face field of this stage (its ghost

@@ -16,7 +16,9 @@ The planted mistakes, by the passage they break:
 * flux-CT: the 1/4 in the edge average of the EMF;
 * the RK stage: the two state weights exchanged;
 * con2prim (Kastaun et al. 2021): the sign of the B-term in qbar, the W factor of eps, min instead of max in
-  nu; the floors (Sec. 3.2): the internal energy floor absolute instead of specific.
+  nu; the floors (Sec. 3.2): the internal energy floor absolute instead of specific;
+* the passive scalar (Sec. 2.1): X taken downwind, X from the old density, the RK weights exchanged, the
+  ghosts not filled, the stencil of the face's left state shifted.
 """
 import os
 import subprocess
@@ -28,7 +30,8 @@ import oracle as orc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_metric.py", "tests/test_oracle_fluid.py", "tests/test_oracle_recon_riemann.py",
-        "tests/test_oracle_c2p.py", "tests/test_oracle_stage.py", "tests/test_oracle_boosted_waves.py"]
+        "tests/test_oracle_c2p.py", "tests/test_oracle_stage.py", "tests/test_oracle_boosted_waves.py",
+        "tests/test_oracle_scalar.py"]
 
 MUTANTS = {
     "KS f power of r": ("const double f = 2.0 * M * r * r2 / Sig;", "const double f = 2.0 * M * r2 / Sig;"),
@@ -63,6 +66,14 @@ MUTANTS = {
     "con2prim nu min": ("const double nu = std::max(nuA, nuB);", "const double nu = std::min(nuA, nuB);"),
     "absolute internal energy floor": ("if (!(P[4] >= P[0] * eps_flr)) { P[4] = P[0] * eps_flr;",
                                        "if (!(P[4] >= eps_flr)) { P[4] = eps_flr;"),
+    "scalar taken downwind": ("FX[d * gn + f] = mdot * (mdot >= 0.0 ? XL : XR);",
+                              "FX[d * gn + f] = mdot * (mdot >= 0.0 ? XR : XL);"),
+    "scalar from the old density": ("X[g.gi(i, j, k)] = DXnew[c] / Unew[c];", "X[g.gi(i, j, k)] = DXnew[c] / Ucur[c];"),
+    "scalar RK weights exchanged": ("DXnew[c] = g0 * x0 + g1 * DXcur[c] + beta * dt * (-div);",
+                                    "DXnew[c] = g1 * x0 + g0 * DXcur[c] + beta * dt * (-div);"),
+    "scalar ghosts not filled": ("if (p->bc == 0) ghost_fill_periodic(g, X, 1);", "if (p->bc == 7) ghost_fill_periodic(g, X, 1);"),
+    "scalar left stencil": ("            cl[d] += q - 3;  // stencil of the cell below the face\n",
+                            "            cl[d] += q - 2;  // stencil of the cell below the face\n"),
 }
 
 

@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-guess", action="store_true")
     ap.add_argument("--no-face-ct", action="store_true")
     ap.add_argument("--no-two-level", action="store_true")
+    ap.add_argument("--no-scalar", action="store_true")
     ap.add_argument("--guess-states", type=int, default=100_000_000)
     ap.add_argument("--guess-only", action="store_true",
                     help="run only the learned-guess con2prim section and print its JSON (profiling aid)")
@@ -256,6 +257,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
     face_ct = None if args.no_face_ct else run_face_ct(G, s_mix, P, Bf, args.steps, args.warmup)
     two_level = None if args.no_two_level else run_two_level(G, I, s_mix.recon, args.steps, args.warmup)
+    scalar = None if args.no_scalar else run_scalar(G, s_mix, P, args.steps, args.warmup, ms / args.steps)
     del Bf
     guess = None if args.no_guess else run_guess(G, I, rank, n_states=args.guess_states)
     batched = None
@@ -304,6 +306,8 @@ def run_ours(args):
         out["face_ct"] = face_ct
     if two_level is not None:
         out["two_level"] = two_level
+    if scalar is not None:
+        out["scalar"] = scalar
     if batched is not None:
         out["batched"] = batched
     if guess is not None:
@@ -479,6 +483,31 @@ def run_face_ct(G, s_mix, P, Bf, steps, warmup):
            "face_divergence_rel": {"initial": div0, "after": div, "stages": warmup + (warmup % 2) + steps + min(steps, 8)},
            "scheme": "face-centred field, upwind (contact) edge EMFs of Gardiner & Stone 2005"}
     del ctx, B
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_scalar(G, s_mix, P, steps, warmup, ms_plain):
+    """The same workload with one passive scalar (the electron fraction, say) advanced too: stage
+    throughput and the scalar's cost per stage against the plain stage."""
+    import dataclasses
+    import numpy as np
+    import torch
+    s = dataclasses.replace(s_mix, scalar=True)
+    ctx = G.Context(s)
+    ctx.set_prims(P)
+    x = s.cell_centres(0)
+    X = np.broadcast_to((0.1 + 0.4 * (x > 0.5 * (s.x0[0] + x[-1])))[None, None, :], s.prim_shape()[1:]).copy()
+    ctx.set_scalar(X)
+    for k in range(warmup + (warmup % 2)):
+        ctx.stage(*stage_coeffs(k), 0.0)
+    torch.cuda.synchronize()
+    ms = time_stages(ctx, 0, steps)
+    cells = s.n[0] * s.n[1] * s.n[2]
+    out = {"value": cells * steps / (ms / 1e3), "unit": UNIT, "ms_per_stage": ms / steps, "steps": steps,
+           "scalar_ms_per_stage": ms / steps - ms_plain, "scheme": "sqrt(gamma) D X carried by the face mass flux, "
+           "X reconstructed like the primitives and taken on the upwind side"}
+    del ctx
     torch.cuda.empty_cache()
     return out
 

@@ -82,6 +82,8 @@ extern "C" {
                                    double iteration */
 #define GRMHD_GET_DT 4          /* double [1]: the time step of the last first stage (CFL rule) */
 #define GRMHD_GET_FACE_B 5      /* double [3][nz+2ng][ny+2ng][nx+2ng]: the current face field (GRMHD_CT_FACE) */
+#define GRMHD_GET_SCALAR 6      /* double [nz+2ng][ny+2ng][nx+2ng]: the passive scalar X (params.scalar) */
+#define GRMHD_GET_SCALAR_CONS 7 /* double [nz][ny][nx]: its conserved sqrt(gamma) D X, the current state */
 
 /* per-cell status bits */
 #define GRMHD_ST_RHO_FLOOR 1
@@ -112,10 +114,24 @@ typedef struct {
   double shift[3];            /* GRMHD_MINKOWSKI only: constant shift beta^i, i.e. flat space in coordinates moving
                                  at velocity -beta (Sec. 4.1.1's boosted linear waves; |beta| < 1); ignored by
                                  Kerr-Schild */
+  int scalar;                 /* 1: also evolve one passive scalar X, e.g. the electron fraction (Sec. 2.1,
+                                 (X rho u^mu)_{;mu} = 0; see grmhd_set_scalar); single-block contexts, ng >= 3 */
 } grmhd_params;
 
 /* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */
 size_t grmhd_workspace_bytes(const grmhd_params* p);
+
+/* Passive scalar (params.scalar = 1; Sec. 2.1: Phoebus evolves passive scalars X, the electron fraction
+ * among them, by (X rho u^mu)_{;mu} = S; here S = 0, no radiation). Set X after grmhd_set_prims or
+ * grmhd_set_cons (each discards a previous scalar): X is double [nz+2ng][ny+2ng][nx+2ng] (ghosts as for P: read when the
+ * boundary is fixed, filled periodically otherwise), host or device (where), read during the call;
+ * the conserved sqrt(gamma) D X of the interior is formed from the current state. Every stage then also
+ * advances it: the face flux of sqrt(gamma) D X is the stage's face mass flux times X reconstructed (with
+ * the stage's reconstruction) on the upwind side of that flux, the update takes the stage's RK weights,
+ * and X = (sqrt(gamma) D X) / (sqrt(gamma) D) with the stage's final D (so a density floor dilutes X while
+ * sqrt(gamma) D X stays conserved). Both forms: X stored like P, D X in double.
+ * Errors: GRMHD_E_INVALID (no scalar in the params, no state yet, X NULL, bad where), GRMHD_E_CUDA. */
+int grmhd_set_scalar(grmhd_ctx* c, const double* X, int where);
 
 /* Create a context on the current CUDA device. `workspace` is a device pointer to at least
  * grmhd_workspace_bytes(p) bytes, 256-byte aligned (may be NULL when that is 0); `stream` is a

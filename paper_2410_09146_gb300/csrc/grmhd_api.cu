@@ -33,6 +33,10 @@ struct grmhd_ctx {
   unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats, [16] worklist count,
                              // [17] floor-list count, [20..23] batch work counters
   double* Bslot[3];          // face-centred CT: face field slots [3][gsize], paired with Uslot
+  void* X;                   // passive scalar: X [gsize] (storage type of P)
+  double* DXslot[3];         // passive scalar: sqrt(gamma) D X [isize], paired with Uslot
+  void* FX;                  // passive scalar: face fluxes [3][gsize] (flux type)
+  bool has_scalar;           // passive scalar: grmhd_set_scalar called since grmhd_set_prims
   void* Ecc;                 // face-centred CT: cell-centred EMFs [3][gsize] (flux type)
   bool has_faces;            // face-centred CT: grmhd_set_face_b called since grmhd_set_prims
   int s0, sc;                // slot of U0 and of the current state
@@ -79,7 +83,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
-  size_t P, U[3], F[3], E, status, worklist, wl_mu, floorlist, geo, B[3], Ecc, scal, total;
+  size_t P, U[3], F[3], E, status, worklist, wl_mu, floorlist, geo, B[3], Ecc, X, DX[3], FX, scal, total;
 };
 
 bool valid_params(const grmhd_params* p, char* msg, size_t n) {
@@ -105,6 +109,8 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   if (!(p->w_max > 1.0)) { snprintf(msg, n, "w_max must be > 1"); return false; }
   if (p->metric == GRMHD_KERR_SCHILD && !(p->mass > 0.0)) { snprintf(msg, n, "mass must be > 0"); return false; }
   if (p->ct != GRMHD_CT_FLUX && p->ct != GRMHD_CT_FACE) { snprintf(msg, n, "unknown constrained-transport mode"); return false; }
+  if (p->scalar != 0 && p->scalar != 1) { snprintf(msg, n, "scalar must be 0 or 1"); return false; }
+  if (p->scalar && p->ng < 3) { snprintf(msg, n, "a passive scalar needs ng >= 3"); return false; }
   if (p->metric == GRMHD_MINKOWSKI && !(p->shift[0] * p->shift[0] + p->shift[1] * p->shift[1] + p->shift[2] * p->shift[2] < 1.0)) {
     snprintf(msg, n, "the shift must have |beta| < 1");
     return false;
@@ -136,6 +142,11 @@ Layout layout_of(const grmhd_params* p) {
     if (p->ct == GRMHD_CT_FACE) {
       for (int k = 0; k < 3; ++k) l.B[k] = take(3 * G * sizeof(double));
       l.Ecc = take(3 * G * pb);
+    }
+    if (p->scalar) {
+      l.X = take(G * pb);
+      for (int k = 0; k < 3; ++k) l.DX[k] = take(I * sizeof(double));
+      l.FX = take(3 * G * pb);
     }
   }
   l.total = off;
@@ -384,8 +395,14 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
       for (int k = 0; k < 3; ++k) c->Bslot[k] = (double*)(c->ws + l.B[k]);
       c->Ecc = c->ws + l.Ecc;
     }
+    if (p->scalar) {
+      c->X = c->ws + l.X;
+      for (int k = 0; k < 3; ++k) c->DXslot[k] = (double*)(c->ws + l.DX[k]);
+      c->FX = c->ws + l.FX;
+    }
   }
   c->has_faces = false;
+  c->has_scalar = false;
   c->s0 = c->sc = 0;
   c->has_state = false;
   cudaError_t e = cudaMemsetAsync(c->ws, 0, l.total, c->stream);
@@ -419,6 +436,7 @@ int grmhd_set_prims(grmhd_ctx* c, const double* P, int where) {
   CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], c->stream), "prim->cons");
   c->has_state = true;
   c->has_faces = false;
+  c->has_scalar = false;
   return GRMHD_OK;
 }
 
@@ -444,6 +462,26 @@ int grmhd_set_face_b(grmhd_ctx* c, const double* Bf, int where) {
   return GRMHD_OK;
 }
 
+int grmhd_set_scalar(grmhd_ctx* c, const double* X, int where) {
+  if (!c || !X) return c ? fail(c, GRMHD_E_INVALID, "X is NULL") : GRMHD_E_INVALID;
+  if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
+  if (!c->prm.scalar) return fail(c, GRMHD_E_INVALID, "the context was created without a passive scalar");
+  if (!c->has_state) return fail(c, GRMHD_E_INVALID, "grmhd_set_prims has not been called");
+  const double* src = X;
+  if (where == GRMHD_HOST) {
+    // stage through the flux region (at least 8 G doubles)
+    CK(cudaMemcpyAsync(c->F[0], X, sizeof(double) * (size_t)c->dp.gsize, cudaMemcpyHostToDevice, c->stream),
+       "copying X to the device");
+    src = (const double*)c->F[0];
+  } else if (where != GRMHD_DEVICE) {
+    return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");
+  }
+  CK(c->L->scalar_load(c->dp, src, c->X, c->Uslot[c->sc], c->DXslot[c->sc], c->stream), "loading X");
+  if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
+  c->has_scalar = true;
+  return GRMHD_OK;
+}
+
 int grmhd_set_cons(grmhd_ctx* c, const double* U, int where) {
   if (!c || !U) return c ? fail(c, GRMHD_E_INVALID, "U is NULL") : GRMHD_E_INVALID;
   if (c->nblocks > 0) return fail(c, GRMHD_E_INVALID, "not available for batch contexts");
@@ -455,6 +493,7 @@ int grmhd_set_cons(grmhd_ctx* c, const double* U, int where) {
      "copying U");
   if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
   c->has_state = true;
+  c->has_scalar = false;
   return GRMHD_OK;
 }
 
@@ -509,6 +548,7 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   const bool track = auto_dt && first;
   const bool face = c->prm.ct == GRMHD_CT_FACE;
   if (face && !c->has_faces) return fail(c, GRMHD_E_INVALID, "grmhd_set_face_b has not been called");
+  if (c->prm.scalar && !c->has_scalar) return fail(c, GRMHD_E_INVALID, "grmhd_set_scalar has not been called");
   const FormLaunchers& L = *c->L;
   const cudaStream_t s = c->stream;
   // this stage's parameters: with face-centred CT the flux kernels read the normal field of the faces
@@ -561,6 +601,13 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   CK(L.update(dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
   TMARK(6);
   CK(L.cell_passes(dp, c->P, a, s), "floored and deferred cells");
+  if (c->prm.scalar) {
+    // the passive scalar: X of the stage's start, the stage's mass fluxes, its final D
+    if (c->prm.bc == GRMHD_BC_PERIODIC) CK(L.scalar_ghost(dp, c->X, s), "scalar ghost fill");
+    for (int d = 0; d < 3; ++d) CK(L.scalar_flux(dp, c->X, c->F[d], c->FX, d, s), "scalar flux");
+    CK(L.scalar_update(dp, c->X, c->FX, c->DXslot[c->s0], c->DXslot[c->sc], c->DXslot[dst], c->Uslot[dst], a, s),
+       "scalar update");
+  }
   TMARK(7);
 #undef TMARK
   if (c->timing) c->t_pending = true;
@@ -709,6 +756,18 @@ int grmhd_get(grmhd_ctx* c, int what, void* dst, int where) {
     case GRMHD_GET_DT:
       CK(cudaMemcpyAsync(dst, c->scal + 3, sizeof(double), kind, s), "copying dt");
       break;
+    case GRMHD_GET_SCALAR:
+    case GRMHD_GET_SCALAR_CONS:
+      if (!c->prm.scalar || !c->has_scalar) return fail(c, GRMHD_E_INVALID, "no passive scalar set");
+      if (what == GRMHD_GET_SCALAR_CONS) {
+        CK(cudaMemcpyAsync(dst, c->DXslot[c->sc], sizeof(double) * (size_t)c->dp.isize, kind, s), "copying D X");
+      } else if (where == GRMHD_DEVICE) {
+        CK(c->L->scalar_store(c->dp, c->X, (double*)dst, s), "converting X");
+      } else {
+        CK(c->L->scalar_store(c->dp, c->X, (double*)c->F[0], s), "converting X");
+        CK(cudaMemcpyAsync(dst, c->F[0], sizeof(double) * (size_t)c->dp.gsize, kind, s), "copying X");
+      }
+      break;
     case GRMHD_GET_FACE_B:
       if (c->prm.ct != GRMHD_CT_FACE) return fail(c, GRMHD_E_INVALID, "not a face-centred CT context");
       CK(cudaMemcpyAsync(dst, c->Bslot[c->sc], sizeof(double) * 3 * (size_t)c->dp.gsize, kind, s), "copying faces");
@@ -792,6 +851,10 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   }
   if (p->ct != GRMHD_CT_FLUX) {
     snprintf(g_create_err, sizeof g_create_err, "batches use flux-CT (GRMHD_CT_FLUX)");
+    return GRMHD_E_UNSUPPORTED;
+  }
+  if (p->scalar) {
+    snprintf(g_create_err, sizeof g_create_err, "the passive scalar is for single-block contexts");
     return GRMHD_E_UNSUPPORTED;
   }
   for (int b = 0; b < nblocks; ++b)

@@ -4,6 +4,7 @@
 #include "grmhd_face_ct.cuh"
 #include "grmhd_launch.h"
 #include "grmhd_batch_launch.cuh"
+#include "grmhd_scalar.cuh"
 
 namespace grmhd {
 
@@ -102,11 +103,12 @@ cudaError_t geometry(const DevParams& p, double* geo, cudaStream_t s) {
 
 using FC = FaceCtLaunch<R, T>;
 using BL = BatchLaunch<double, double>;
+using SL = ScalarLaunch<double, double>;
 const FormLaunchers kFp64 = {ghost, flux, emf, update, cell_passes, prim2con, load_prims, store_prims, BL::flux, BL::emf, BL::update,
                                 BL::deferred, BL::ctas_per_sm, 8, 8, geometry, BL::floors,
                                 FC::emf, FC::faces, FC::to_cells, FC::ghost_faces,
                                 BL::flux_ctas_per_sm, BL::exchange, BL::mesh_exchange,
-                                BL::mesh_reflux};
+                                BL::mesh_reflux, SL::flux, SL::update, SL::load, SL::store, SL::ghost};
 
 }  // namespace
 

@@ -56,6 +56,14 @@ struct FormLaunchers {
   cudaError_t (*mesh_exchange)(const BlockDesc* b, int nblocks, const MeshDesc& M, int pass, cudaStream_t s);
   cudaError_t (*mesh_reflux)(const BlockDesc* b, const RefluxCell* cells, int ncells, const BatchArgs& a, int metric,
                              cudaStream_t s);
+  // passive scalar (grmhd_scalar.cuh): face fluxes of direction d (FX holds the 3 directions), the update,
+  // loading X (and D X from the current state), widening X to double, the periodic ghost fill of X
+  cudaError_t (*scalar_flux)(const DevParams& p, const void* X, const void* F, void* FX, int d, cudaStream_t s);
+  cudaError_t (*scalar_update)(const DevParams& p, void* X, const void* FX, const double* DX0, const double* DXcur,
+                               double* DXnew, const double* Unew, const StageArgs& a, cudaStream_t s);
+  cudaError_t (*scalar_load)(const DevParams& p, const double* Xd, void* X, const double* U, double* DX, cudaStream_t s);
+  cudaError_t (*scalar_store)(const DevParams& p, const void* X, double* Xd, cudaStream_t s);
+  cudaError_t (*scalar_ghost)(const DevParams& p, void* X, cudaStream_t s);
 };
 
 const FormLaunchers& fp64_launchers();

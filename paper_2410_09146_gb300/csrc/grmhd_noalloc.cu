@@ -63,6 +63,7 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
   if (g0 != 0.0 && !U0) return fail(GRMHD_E_INVALID, "U0 is NULL but g0 != 0");
   if (p->precision != GRMHD_FP64) return fail(GRMHD_E_INVALID, "only the all-FP64 form is available");
   if (p->ct != GRMHD_CT_FLUX) return fail(GRMHD_E_INVALID, "face-centred CT needs a context (grmhd_create)");
+  if (p->scalar) return fail(GRMHD_E_INVALID, "the passive scalar needs a context (grmhd_create)");
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(GRMHD_E_INVALID, "nx, ny, nz must be >= 1");
   const int need = p->recon >= GRMHD_RECON_WENO5Z_AOAH ? 3 : (p->recon == GRMHD_RECON_CONSTANT ? 1 : 2);
   if (p->recon < 0 || p->recon > 4 || p->ng < need || p->ng > 16)

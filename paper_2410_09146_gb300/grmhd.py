@@ -20,6 +20,8 @@ GRMHD_OK, GRMHD_E_INVALID, GRMHD_E_CUDA, GRMHD_E_WORKSPACE, GRMHD_E_UNSUPPORTED 
 GRMHD_HOST, GRMHD_DEVICE = 0, 1
 GRMHD_GET_PRIMS, GRMHD_GET_CONS, GRMHD_GET_STATUS, GRMHD_GET_STATS, GRMHD_GET_DT = 0, 1, 2, 3, 4
 GRMHD_GET_FACE_B = 5
+GRMHD_GET_SCALAR = 6
+GRMHD_GET_SCALAR_CONS = 7
 RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3, "mp5": 4}
 RIEMANN = {"llf": 0, "hll": 1}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
@@ -45,7 +47,7 @@ class grmhd_params(ctypes.Structure):
         ("rho_floor0", ctypes.c_double), ("eps_floor0", ctypes.c_double), ("floor_r_exp", ctypes.c_double),
         ("w_max", ctypes.c_double), ("c2p_tol", ctypes.c_double), ("c2p_max_iter", ctypes.c_int),
         ("cfl", ctypes.c_double), ("weno_eps", ctypes.c_double), ("ct", ctypes.c_int),
-        ("shift", ctypes.c_double * 3),
+        ("shift", ctypes.c_double * 3), ("scalar", ctypes.c_int),
     ]
 
 
@@ -77,6 +79,7 @@ def lib():
         L.grmhd_set_prims.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_set_cons.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_set_face_b.argtypes = [vp, vp, ctypes.c_int]
+        L.grmhd_set_scalar.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_stage.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.grmhd_rk2_step.argtypes = [vp, ctypes.c_double]
         L.grmhd_c2p.argtypes = [vp, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int]
@@ -133,6 +136,7 @@ def params(setup) -> grmhd_params:
     p.c2p_tol, p.c2p_max_iter, p.cfl, p.weno_eps = setup.c2p_tol, setup.c2p_max_iter, setup.cfl, setup.weno_eps
     p.ct = CT[getattr(setup, "ct", "flux")]
     p.shift[:] = list(getattr(setup, "shift", (0.0, 0.0, 0.0)))
+    p.scalar = int(bool(getattr(setup, "scalar", False)))
     return p
 
 
@@ -176,6 +180,11 @@ def grmhd_set_cons(ctx: int, U) -> None:
 def grmhd_set_face_b(ctx: int, Bf) -> None:
     ptr, where = _ptr(Bf)
     _check(lib().grmhd_set_face_b(ctx, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_set_scalar(ctx: int, X) -> None:
+    ptr, where = _ptr(X)
+    _check(lib().grmhd_set_scalar(ctx, ctypes.c_void_p(ptr), where), ctx)
 
 
 def grmhd_stage(ctx: int, g0: float, g1: float, beta: float, dt: float) -> None:
@@ -443,6 +452,10 @@ class Context:
     def set_face_b(self, Bf):
         grmhd_set_face_b(self.ctx, Bf)
 
+    def set_scalar(self, X):
+        """Passive scalar X (ghosted, double; params.scalar): ``grmhd_set_scalar``."""
+        grmhd_set_scalar(self.ctx, X)
+
     def stage(self, g0, g1, beta, dt=0.0):
         grmhd_stage(self.ctx, g0, g1, beta, dt)
 
@@ -453,7 +466,9 @@ class Context:
         s = self.setup
         shapes = {GRMHD_GET_PRIMS: (s.prim_shape(), np.float64), GRMHD_GET_CONS: (s.cons_shape(), np.float64),
                   GRMHD_GET_STATUS: (s.cons_shape()[1:], np.uint8), GRMHD_GET_STATS: ((8,), np.uint64),
-                  GRMHD_GET_DT: ((1,), np.float64), GRMHD_GET_FACE_B: ((3,) + s.prim_shape()[1:], np.float64)}
+                  GRMHD_GET_DT: ((1,), np.float64), GRMHD_GET_FACE_B: ((3,) + s.prim_shape()[1:], np.float64),
+                  GRMHD_GET_SCALAR: (s.prim_shape()[1:], np.float64),
+                  GRMHD_GET_SCALAR_CONS: (s.cons_shape()[1:], np.float64)}
         if out is None:
             shape, dt = shapes[what]
             out = np.empty(shape, dt)
@@ -477,6 +492,12 @@ class Context:
 
     def face_b(self):
         return self.get(GRMHD_GET_FACE_B)
+
+    def scalar(self):
+        return self.get(GRMHD_GET_SCALAR)
+
+    def scalar_cons(self):
+        return self.get(GRMHD_GET_SCALAR_CONS)
 
     def set_timing(self, on=True):
         grmhd_set_timing(self.ctx, on)

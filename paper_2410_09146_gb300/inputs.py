@@ -64,6 +64,7 @@ class Setup:
     precision: str = "fp64"            # "fp64" | "mixed"
     ct: str = "flux"                   # "flux" (Toth flux-CT, cell field) | "face" (face-centred upwind CT)
     shift: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # Minkowski: constant shift (boosted coordinates)
+    scalar: bool = False               # also evolve one passive scalar (the electron fraction, say)
 
     @property
     def ghosted(self):

@@ -12,34 +12,56 @@
 
 namespace grmhd {
 
-// Face flux of sqrt(gamma) D X through the d-faces of the interior: face (i, j, k), i along d in [0, n_d],
-// is the lower d-face of ghosted cell (i, j, k) and sits between cells c - e_d and c.
+// Face fluxes of sqrt(gamma) D X through the d-faces of the interior, in runs of kRun consecutive faces
+// along d: face f (0 <= f <= n_d) is the lower d-face of cell f and sits between cells f - 1 and f. A
+// thread slides a 6-cell window along its run and reconstructs each cell once (both faces): the face's
+// left value is the previous cell's upper face, its right value this cell's lower face.
+// Grid: x over (run, transverse a) in 32-bit indices, y over transverse b; for d = y, z the x direction of
+// the mesh is the fastest index (coalesced loads), for d = x the run index is.
+constexpr int kRun = 16;
+
 template <class R, class T, int RECON>
 __global__ void __launch_bounds__(256) k_scalar_flux(const T* __restrict__ X, const R* __restrict__ F,
                                                      R* __restrict__ FX, DevParams p, int d) {
   const int n[3] = {p.nx, p.ny, p.nz};
-  int m[3] = {n[0], n[1], n[2]};
-  m[d] = n[d] + 1;
-  const long long nf = (long long)m[0] * m[1] * m[2];
+  const int nrun = (n[d] + 1 + kRun - 1) / kRun;
+  // (fast, slow) extents of the x index: d = 0: (run, y); d = 1: (x, run); d = 2: (x, run) with y on the grid
+  const int a_fast = d == 0 ? nrun : n[0];
+  const int a_slow = d == 0 ? n[1] : nrun;
+  const int c2 = blockIdx.y;  // d = 0, 1: z; d = 2: y
   const long long st = d == 0 ? 1 : (d == 1 ? (long long)p.gx : (long long)p.gx * p.gy);
   const R eps = R(p.weno_eps);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nf; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % m[0]), j = (int)((t / m[0]) % m[1]), k = (int)(t / ((long long)m[0] * m[1]));
-    const long long g = gidx(p, i, j, k);
-    R f[6];
+  const int total = a_fast * a_slow;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int u = t % a_fast, v = t / a_fast;
+    int c[3], r;
+    if (d == 0) { r = u; c[1] = v; c[2] = c2; c[0] = 0; }
+    else if (d == 1) { c[0] = u; r = v; c[2] = c2; c[1] = 0; }
+    else { c[0] = u; r = v; c[1] = c2; c[2] = 0; }
+    const int f0 = r * kRun;
+    const int f1 = min(f0 + kRun, n[d] + 1);
+    c[d] = f0;
+    long long g = gidx(p, c[0], c[1], c[2]);  // lower face of cell f0
+    R w[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) f[q] = R(X[g + (q - 3) * st]);  // cells c-3 .. c+2 along d
-    R qm, qp, XL, XR;
-    recon_cell<R, RECON>(f[0], f[1], f[2], f[3], f[4], eps, qm, qp);  // the cell below the face
-    XL = qp;
-    recon_cell<R, RECON>(f[1], f[2], f[3], f[4], f[5], eps, qm, qp);  // the cell above it
-    XR = qm;
-    const R mdot = F[g];  // component 0 (mass) of the face flux
-    FX[g] = mdot * (mdot >= R(0) ? XL : XR);
+    for (int q = 0; q < 5; ++q) w[q] = R(X[g + (q - 3) * st]);  // cells f0-3 .. f0+1
+    R qm, qp;
+    recon_cell<R, RECON>(w[0], w[1], w[2], w[3], w[4], eps, qm, qp);  // cell f0 - 1
+    R XL = qp;
+    for (int f = f0; f < f1; ++f, g += st) {
+      w[5] = R(X[g + 2 * st]);  // cell f + 2
+      recon_cell<R, RECON>(w[1], w[2], w[3], w[4], w[5], eps, qm, qp);  // cell f
+      const R mdot = F[g];  // component 0 (mass) of the face flux
+      FX[g] = mdot * (mdot >= R(0) ? XL : qm);
+      XL = qp;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) w[q] = w[q + 1];
+    }
   }
 }
 
-// DXnew = g0 DX0 + g1 DXcur + beta dt (-div FX); X = DXnew / D (Unew component 0) on the interior.
+// DXnew = g0 DX0 + g1 DXcur + beta dt (-div FX) in double; X = DXnew / D (Unew component 0) on the interior,
+// in the storage type of X. Grid: x over the cells of an xy-plane, y over z.
 template <class R, class T>
 __global__ void __launch_bounds__(256) k_scalar_update(T* __restrict__ X, const R* __restrict__ FX,
                                                        const double* __restrict__ DX0, const double* __restrict__ DXcur,
@@ -51,8 +73,11 @@ __global__ void __launch_bounds__(256) k_scalar_update(T* __restrict__ X, const 
   const R* Fx = FX;
   const R* Fy = FX + G;
   const R* Fz = FX + 2 * G;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.isize; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
+  const int k = blockIdx.y;
+  const int plane = p.nx * p.ny;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < plane; q += gridDim.x * blockDim.x) {
+    const int i = q % p.nx, j = q / p.nx;
+    const long long t = (long long)k * plane + q;
     const long long g = gidx(p, i, j, k);
     const R div = (Fx[g + 1] - Fx[g]) * R(p.idx[0]) + (Fy[g + sy] - Fy[g]) * R(p.idx[1]) +
                   (Fz[g + sz] - Fz[g]) * R(p.idx[2]);
@@ -60,7 +85,12 @@ __global__ void __launch_bounds__(256) k_scalar_update(T* __restrict__ X, const 
     if (a.g0 != 0.0) u += a.g0 * DX0[t];
     const double dxn = u + bdt * (double)(-div);
     DXnew[t] = dxn;
-    X[g] = (T)(dxn / Unew[t]);
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // mixed form: X is stored in float, so divide in float (a double divide is ~10 FP64 issue slots)
+      X[g] = (float)dxn / (float)Unew[t];
+    } else {
+      X[g] = (T)(dxn / Unew[t]);
+    }
   }
 }
 
@@ -87,9 +117,10 @@ __global__ void k_scalar_store(const T* __restrict__ X, double* __restrict__ Xd,
 template <class R, class T>
 struct ScalarLaunch {
   static cudaError_t flux(const DevParams& p, const void* X, const void* F, void* FX, int d, cudaStream_t s) {
-    long long nf = (long long)p.nx * p.ny * p.nz / (d == 0 ? p.nx : (d == 1 ? p.ny : p.nz)) *
-                   ((d == 0 ? p.nx : (d == 1 ? p.ny : p.nz)) + 1);
-    const int grid = grid_for(nf, 256);
+    const int n[3] = {p.nx, p.ny, p.nz};
+    const long long nrun = (n[d] + 1 + kRun - 1) / kRun;
+    const long long per = d == 0 ? nrun * n[1] : (long long)n[0] * nrun;  // x indices per grid row
+    const dim3 grid((unsigned)((per + 255) / 256), (unsigned)(d == 2 ? n[1] : n[2]));
     const T* x = (const T*)X;
     const R* f = (const R*)F;
     R* fx = (R*)FX + (long long)d * p.gsize;
@@ -105,7 +136,8 @@ struct ScalarLaunch {
   }
   static cudaError_t update(const DevParams& p, void* X, const void* FX, const double* DX0, const double* DXcur,
                             double* DXnew, const double* Unew, const StageArgs& a, cudaStream_t s) {
-    k_scalar_update<R, T><<<grid_for(p.isize, 256), 256, 0, s>>>((T*)X, (const R*)FX, DX0, DXcur, DXnew, Unew, p, a);
+    const dim3 grid((unsigned)(((long long)p.nx * p.ny + 255) / 256), (unsigned)p.nz);
+    k_scalar_update<R, T><<<grid, 256, 0, s>>>((T*)X, (const R*)FX, DX0, DXcur, DXnew, Unew, p, a);
     return cudaGetLastError();
   }
   static cudaError_t load(const DevParams& p, const double* Xd, void* X, const double* U, double* DX, cudaStream_t s) {

@@ -115,7 +115,8 @@ typedef struct {
                                  at velocity -beta (Sec. 4.1.1's boosted linear waves; |beta| < 1); ignored by
                                  Kerr-Schild */
   int scalar;                 /* 1: also evolve one passive scalar X, e.g. the electron fraction (Sec. 2.1,
-                                 (X rho u^mu)_{;mu} = 0; see grmhd_set_scalar); single-block contexts, ng >= 3 */
+                                 (X rho u^mu)_{;mu} = 0; see grmhd_set_scalar); single-block contexts and batches
+                                 (not two-level meshes), ng >= 3 */
 } grmhd_params;
 
 /* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */
@@ -334,6 +335,15 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
  * is the stage of the one large block the lattice tiles. (0, 0, 0) switches the exchange off.
  * Errors: GRMHD_E_INVALID (not a batch, block count, sizes, widths or corners off the lattice). */
 int grmhd_batch_set_lattice(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic);
+
+/* Passive scalar of block `block` of a batch created with params.scalar = 1 (as grmhd_set_scalar: X double
+ * [gz][gy][gx] of that block, ghosts included, host or device, read during the call; the block's
+ * sqrt(gamma) D X formed from its current state; grmhd_batch_set_prims of the block discards it). Every
+ * block needs one before a stage; the stage then advances each block's scalar as grmhd_stage does, and
+ * a lattice exchange (grmhd_batch_set_lattice) copies X's ghosts with P's. Read back per block with
+ * grmhd_batch_get(GRMHD_GET_SCALAR / GRMHD_GET_SCALAR_CONS). Two-level meshes refuse the scalar.
+ * Errors: GRMHD_E_INVALID (not a batch, bad block, no scalar in the params, no state yet), GRMHD_E_CUDA. */
+int grmhd_batch_set_scalar(grmhd_ctx* c, int block, const double* X, int where);
 
 /* Declare that the batch's blocks are the leaves of a two-level block mesh over an nbx x nby x nbz grid of
  * root blocks (the meshblock AMR the method runs on, Sec. 3; one time step for both levels). level[b] is 0

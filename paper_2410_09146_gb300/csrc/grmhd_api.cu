@@ -37,6 +37,8 @@ struct grmhd_ctx {
   double* DXslot[3];         // passive scalar: sqrt(gamma) D X [isize], paired with Uslot
   void* FX;                  // passive scalar: face fluxes [3][gsize] (flux type)
   bool has_scalar;           // passive scalar: grmhd_set_scalar called since grmhd_set_prims
+  std::vector<char> block_scalar;  // batches: grmhd_batch_set_scalar called for block b since its set_prims
+  long long max_runs, max_cells;   // batches with a scalar: grid sizing (largest block's gsize and isize)
   void* Ecc;                 // face-centred CT: cell-centred EMFs [3][gsize] (flux type)
   bool has_faces;            // face-centred CT: grmhd_set_face_b called since grmhd_set_prims
   int s0, sc;                // slot of U0 and of the current state
@@ -274,6 +276,7 @@ struct BatchLayout {
   size_t scal, blocks, items, worklist, wl_mu, floorlist, leaf, reflux, ghost, fine, total;
   long long leaf_cap, reflux_cap, ghost_cap;
   std::vector<size_t> P, U, F, E, status, geo;  // per block; U and F hold 3 consecutive regions
+  std::vector<size_t> X, DX, FX;                // passive scalar per block (DX: 3 consecutive regions)
 };
 
 bool valid_block(const grmhd_block& b, int ng, char* msg, size_t n) {
@@ -315,6 +318,11 @@ BatchLayout batch_layout(const grmhd_params* p, int nblocks, const grmhd_block* 
     l.E.push_back(take(3 * G * pb));
     l.status.push_back(take(I));
     l.geo.push_back(p->metric == GRMHD_KERR_SCHILD ? take(NGEO * I * sizeof(double)) : 0);
+    if (p->scalar) {
+      l.X.push_back(take(G * pb));
+      for (int k = 0; k < 3; ++k) l.DX.push_back(take(I * sizeof(double)));
+      l.FX.push_back(take(3 * G * pb));
+    }
   }
   l.worklist = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(int)) : 0;
   l.wl_mu = p->precision == GRMHD_MIXED ? take((size_t)cells * sizeof(double)) : 0;
@@ -668,11 +676,21 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
   if (c->worklist) CK(L.batch_deferred(c->dblocks, c->nblocks, a, c->prm.metric, grid, s), "batched deferred con2prim");
   if (c->mesh_on && c->n_reflux > 0)
     CK(L.mesh_reflux(c->dblocks, c->dreflux, c->n_reflux, a, c->prm.metric, s), "refluxing");
+  if (c->prm.scalar) {
+    // the passive scalar of every block: X of the stage's start (its ghosts exchanged with P's), the stage's
+    // mass fluxes, the blocks' final D
+    for (int d = 0; d < 3; ++d)
+      CK(L.batch_scalar_flux(c->dblocks, c->nblocks, c->max_runs, c->prm.recon, d, s), "batched scalar flux");
+    CK(L.batch_scalar_update(c->dblocks, c->nblocks, c->max_cells, a, s), "batched scalar update");
+  }
   return GRMHD_OK;
 }
 
 static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   if (!c->has_state) return fail(c, GRMHD_E_INVALID, "grmhd_batch_set_prims has not been called");
+  if (c->prm.scalar)
+    for (int b = 0; b < c->nblocks; ++b)
+      if (!c->block_scalar[b]) return fail(c, GRMHD_E_INVALID, "grmhd_batch_set_scalar has not been called for every block");
   if (!(g0 == g0) || !(g1 == g1) || !(beta == beta) || !(dt == dt)) return fail(c, GRMHD_E_INVALID, "NaN stage coefficient");
   const bool first = g0 == 0.0;
   if (!first && c->s0 == c->sc) return fail(c, GRMHD_E_INVALID, "a stage with g0 != 0 needs a preceding stage with g0 == 0");
@@ -853,8 +871,8 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
     snprintf(g_create_err, sizeof g_create_err, "batches use flux-CT (GRMHD_CT_FLUX)");
     return GRMHD_E_UNSUPPORTED;
   }
-  if (p->scalar) {
-    snprintf(g_create_err, sizeof g_create_err, "the passive scalar is for single-block contexts");
+  if (p->scalar && nblocks > 65535) {
+    snprintf(g_create_err, sizeof g_create_err, "a batch with a passive scalar holds at most 65535 blocks");
     return GRMHD_E_UNSUPPORTED;
   }
   for (int b = 0; b < nblocks; ++b)
@@ -888,6 +906,9 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   c->wl_mu = p->precision == GRMHD_MIXED ? (double*)(c->ws + l.wl_mu) : nullptr;
   c->floorlist = (int*)(c->ws + l.floorlist);
   c->hblocks.resize(nblocks);
+  c->max_runs = 0;
+  c->max_cells = 0;
+  c->block_scalar.assign(p->scalar ? nblocks : 0, 0);
   long long off = 0;
   for (int b = 0; b < nblocks; ++b) {
     BlockDesc& d = c->hblocks[b];
@@ -900,6 +921,16 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
     d.E = c->ws + l.E[b];
     d.status = (uint8_t*)(c->ws + l.status[b]);
     if (p->metric == GRMHD_KERR_SCHILD) d.p.geo = (const double*)(c->ws + l.geo[b]);
+    d.X = nullptr;
+    d.FX = nullptr;
+    for (int k = 0; k < 3; ++k) d.DX[k] = nullptr;
+    if (p->scalar) {
+      d.X = c->ws + l.X[b];
+      for (int k = 0; k < 3; ++k) d.DX[k] = (double*)(c->ws + l.DX[3 * b + k]);
+      d.FX = c->ws + l.FX[b];
+      c->max_runs = std::max(c->max_runs, (long long)d.p.gsize);
+      c->max_cells = std::max(c->max_cells, d.p.isize);
+    }
     d.cell_offset = off;
     off += d.p.isize;
   }
@@ -995,6 +1026,7 @@ int grmhd_batch_set_mesh(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic, 
     c->mesh_on = false;
   } else {
     if (nbx < 1 || nby < 1 || nbz < 1 || !level || !pos) return fail(c, GRMHD_E_INVALID, "bad mesh arguments");
+    if (c->prm.scalar) return fail(c, GRMHD_E_INVALID, "two-level meshes do not carry the passive scalar");
     if (8LL * nbx * nby * nbz > c->leaf_cap) return fail(c, GRMHD_E_INVALID, "more root blocks than the batch's leaves can tile");
     std::vector<DevParams> bp(c->nblocks);
     for (int b = 0; b < c->nblocks; ++b) bp[b] = c->hblocks[b].p;
@@ -1058,6 +1090,27 @@ int grmhd_batch_set_prims(grmhd_ctx* c, int block, const double* P, int where) {
   CK(c->L->prim2con(b.p, b.P, b.U[0], c->stream), "prim->cons");
   c->s0 = c->sc = 0;
   c->has_state = true;
+  if (!c->block_scalar.empty()) c->block_scalar[block] = 0;
+  return GRMHD_OK;
+}
+
+int grmhd_batch_set_scalar(grmhd_ctx* c, int block, const double* X, int where) {
+  if (!c || c->nblocks < 1) return c ? fail(c, GRMHD_E_INVALID, "not a batch context") : GRMHD_E_INVALID;
+  if (block < 0 || block >= c->nblocks || !X) return fail(c, GRMHD_E_INVALID, "bad block index or X");
+  if (!c->prm.scalar) return fail(c, GRMHD_E_INVALID, "the batch was created without a passive scalar");
+  if (!c->has_state) return fail(c, GRMHD_E_INVALID, "grmhd_batch_set_prims has not been called");
+  const BlockDesc& b = c->hblocks[block];
+  const double* src = X;
+  if (where == GRMHD_HOST) {
+    CK(cudaMemcpyAsync(b.F[0], X, sizeof(double) * (size_t)b.p.gsize, cudaMemcpyHostToDevice, c->stream),
+       "copying X to the device");
+    src = (const double*)b.F[0];
+  } else if (where != GRMHD_DEVICE) {
+    return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");
+  }
+  CK(c->L->scalar_load(b.p, src, b.X, b.U[c->sc], b.DX[c->sc], c->stream), "loading X");
+  if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
+  c->block_scalar[block] = 1;
   return GRMHD_OK;
 }
 
@@ -1088,6 +1141,18 @@ int grmhd_batch_get(grmhd_ctx* c, int block, int what, void* dst, int where) {
       break;
     case GRMHD_GET_STATUS:
       CK(cudaMemcpyAsync(dst, b.status, (size_t)b.p.isize, kind, s), "copying status");
+      break;
+    case GRMHD_GET_SCALAR:
+    case GRMHD_GET_SCALAR_CONS:
+      if (!c->prm.scalar || !c->block_scalar[block]) return fail(c, GRMHD_E_INVALID, "no passive scalar set");
+      if (what == GRMHD_GET_SCALAR_CONS) {
+        CK(cudaMemcpyAsync(dst, b.DX[c->sc], sizeof(double) * (size_t)b.p.isize, kind, s), "copying D X");
+      } else if (where == GRMHD_DEVICE) {
+        CK(c->L->scalar_store(b.p, b.X, (double*)dst, s), "converting X");
+      } else {
+        CK(c->L->scalar_store(b.p, b.X, (double*)b.F[0], s), "converting X");
+        CK(cudaMemcpyAsync(dst, b.F[0], sizeof(double) * (size_t)b.p.gsize, kind, s), "copying X");
+      }
       break;
     default:
       return fail(c, GRMHD_E_INVALID, "unknown GRMHD_GET_* selector");

@@ -87,6 +87,9 @@ struct BlockDesc {
   long long cell_offset;  // index of the block's first interior cell in the batch
   int level;              // two-level mesh: 0 (root block) or 1 (child of a refined root block)
   int pos[3];             // two-level mesh: position in its level's block lattice
+  void* X;                // passive scalar X [gsize] (storage type of P), NULL without one
+  double* DX[3];          // passive scalar: sqrt(gamma) D X slots [isize], paired with U
+  void* FX;               // passive scalar: face fluxes [3][gsize] (flux type)
 };
 
 // A contiguous range of flux units (faces, or runs of faces: flux_units) / edges / cells of one block

@@ -108,7 +108,8 @@ const FormLaunchers kFp64 = {ghost, flux, emf, update, cell_passes, prim2con, lo
                                 BL::deferred, BL::ctas_per_sm, 8, 8, geometry, BL::floors,
                                 FC::emf, FC::faces, FC::to_cells, FC::ghost_faces,
                                 BL::flux_ctas_per_sm, BL::exchange, BL::mesh_exchange,
-                                BL::mesh_reflux, SL::flux, SL::update, SL::load, SL::store, SL::ghost};
+                                BL::mesh_reflux, SL::flux, SL::update, SL::load, SL::store, SL::ghost,
+                                SL::batch_flux, SL::batch_update};
 
 }  // namespace
 

@@ -772,6 +772,7 @@ __global__ void k_batch_exchange(const BlockDesc* __restrict__ blocks, int nbloc
     const long long gs = gidx(S.p, src[0], src[1], src[2]);
 #pragma unroll
     for (int q = 0; q < NV; ++q) Pd[q * G + g] = Ps[q * G + gs];
+    if (S.X) ((T*)blocks[b].X)[g] = ((const T*)S.X)[gs];  // the passive scalar, when the batch has one
   }
 }
 

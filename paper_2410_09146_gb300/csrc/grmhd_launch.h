@@ -64,6 +64,11 @@ struct FormLaunchers {
   cudaError_t (*scalar_load)(const DevParams& p, const double* Xd, void* X, const double* U, double* DX, cudaStream_t s);
   cudaError_t (*scalar_store)(const DevParams& p, const void* X, double* Xd, cudaStream_t s);
   cudaError_t (*scalar_ghost)(const DevParams& p, void* X, cudaStream_t s);
+  // passive scalar of a batch: face fluxes of direction d of every block, the update of every block
+  cudaError_t (*batch_scalar_flux)(const BlockDesc* b, int nblocks, long long max_units, int recon, int d,
+                                   cudaStream_t s);
+  cudaError_t (*batch_scalar_update)(const BlockDesc* b, int nblocks, long long max_cells, const BatchArgs& a,
+                                     cudaStream_t s);
 };
 
 const FormLaunchers& fp64_launchers();

@@ -80,6 +80,7 @@ def lib():
         L.grmhd_set_cons.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_set_face_b.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_set_scalar.argtypes = [vp, vp, ctypes.c_int]
+        L.grmhd_batch_set_scalar.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_stage.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.grmhd_rk2_step.argtypes = [vp, ctypes.c_double]
         L.grmhd_c2p.argtypes = [vp, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int]
@@ -319,6 +320,11 @@ def grmhd_batch_set_mesh(ctx: int, nbx: int, nby: int, nbz: int, periodic: bool,
            ctx)
 
 
+def grmhd_batch_set_scalar(ctx: int, block: int, X) -> None:
+    ptr, where = _ptr(X)
+    _check(lib().grmhd_batch_set_scalar(ctx, block, ctypes.c_void_p(ptr), where), ctx)
+
+
 def grmhd_batch_set_prims(ctx: int, block: int, P) -> None:
     ptr, where = _ptr(P)
     _check(lib().grmhd_batch_set_prims(ctx, block, ctypes.c_void_p(ptr), where), ctx)
@@ -378,6 +384,10 @@ class BatchContext:
     def set_prims(self, block, P):
         grmhd_batch_set_prims(self.ctx, block, P)
 
+    def set_scalar(self, block, X):
+        """Passive scalar X of one block (ghosted, double; params.scalar): ``grmhd_batch_set_scalar``."""
+        grmhd_batch_set_scalar(self.ctx, block, X)
+
     def stage(self, g0, g1, beta, dt=0.0):
         grmhd_stage(self.ctx, g0, g1, beta, dt)
 
@@ -387,7 +397,9 @@ class BatchContext:
     def get(self, block, what):
         s = self.setups[block]
         shape, dt = {GRMHD_GET_PRIMS: (s.prim_shape(), np.float64), GRMHD_GET_CONS: (s.cons_shape(), np.float64),
-                     GRMHD_GET_STATUS: (s.cons_shape()[1:], np.uint8)}[what]
+                     GRMHD_GET_STATUS: (s.cons_shape()[1:], np.uint8),
+                     GRMHD_GET_SCALAR: (s.prim_shape()[1:], np.float64),
+                     GRMHD_GET_SCALAR_CONS: (s.cons_shape()[1:], np.float64)}[what]
         out = np.empty(shape, dt)
         grmhd_batch_get(self.ctx, block, what, out)
         return out

@@ -9,7 +9,9 @@ pinned in tests/test_oracle_scalar.py), through the C ABI.
   mixed to 1e-6: the scalar's flux is formed in float there).
 * Mixed form: per-variable L1 of X and D X against the FP64 oracle within 1e-6 after two steps.
 * Refusals: no scalar in the params, no prior grmhd_set_prims, a stage before grmhd_set_scalar, ng < 3,
-  batches.
+  two-level meshes.
+* Batches: uneven Kerr-Schild blocks in one batch (and its CUDA-graph replay) bit for bit each block's own
+  context in both forms; a periodic lattice (X's ghosts exchanged with P's) bit for bit the large block.
 """
 import dataclasses
 
@@ -151,5 +153,93 @@ def test_scalar_refusals(G):
         ctx.stage(0.0, 1.0, 1.0, 0.001)                         # the scalar was not set
     with pytest.raises(G.GrmhdError):
         G.Context(dataclasses.replace(s, ng=2, recon="plm_mc"))  # the scalar's stencil needs ng >= 3
+    bc = G.BatchContext([dataclasses.replace(s, bc="fixed")])
+    bc.set_prims(0, P.copy())
     with pytest.raises(G.GrmhdError):
-        G.BatchContext([dataclasses.replace(s, bc="fixed")])    # batches have no scalar
+        bc.stage(0.0, 1.0, 1.0, 0.001)                          # a block without its scalar
+
+
+def _batch_blocks(precision):
+    layout = [((8, 8, 8), (3.0, 3.0, 3.0), 0.5), ((12, 10, 6), (8.0, 3.0, 3.0), 0.4),
+              ((16, 16, 16), (3.0, 10.0, 10.0), 0.3), ((5, 7, 9), (14.0, 14.0, 4.0), 0.6)]
+    setups = [I.Setup(n=n3, x0=lo, dx=(h, h, h), metric="kerr_schild", spin=0.9, recon="weno5z_aoah", riemann="hll",
+                      bc="fixed", precision=precision, scalar=True) for n3, lo, h in layout]
+    prims = [I.kerr_schild_random_prims(s, seed=3 + b, rho_range=(0.1, 1.0), w_range=(1.0, 2.0),
+                                        sigma_range=(0.01, 1.0), p_coef=0.5, kmax=1) for b, s in enumerate(setups)]
+    return setups, prims
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_scalar_is_each_blocks_own_context(G, precision):
+    """Uneven Kerr-Schild blocks in one batch (also replayed as a CUDA graph): each block's X and D X bit
+    for bit those of the block advanced in its own context."""
+    setups, prims = _batch_blocks(precision)
+    Xs = [_scalar_field(s, seed=7 + b) for b, s in enumerate(setups)]
+    ref = []
+    for s, P, X in zip(setups, prims, Xs):
+        c = G.Context(s)
+        c.set_prims(P.copy())
+        c.set_scalar(X)
+        for _ in range(2):
+            c.stage(0.0, 1.0, 1.0, 0.02)
+            c.stage(0.5, 0.5, 0.5, 0.02)
+        ref.append((c.scalar(), c.scalar_cons(), c.cons()))
+    for graph in (False, True):
+        bc = G.BatchContext(setups)
+        for b, (P, X) in enumerate(zip(prims, Xs)):
+            bc.set_prims(b, P.copy())
+            bc.set_scalar(b, X)
+        if graph:
+            bc.set_graph(True)
+        for _ in range(2):
+            bc.stage(0.0, 1.0, 1.0, 0.02)
+            bc.stage(0.5, 0.5, 0.5, 0.02)
+        for b, (Xr, DXr, Ur) in enumerate(ref):
+            assert np.array_equal(bc.get(b, G.GRMHD_GET_SCALAR), Xr), (precision, graph, b)
+            assert np.array_equal(bc.get(b, G.GRMHD_GET_SCALAR_CONS), DXr), (precision, graph, b)
+            assert np.array_equal(bc.get(b, G.GRMHD_GET_CONS), Ur), (precision, graph, b)
+
+
+def test_lattice_scalar_is_the_large_block(G):
+    """A periodic lattice of blocks exchanges X's ghosts with P's: all-FP64, bit for bit the large block."""
+    s = dataclasses.replace(I.linear_wave_setup(32, ny=24, nz=16, recon="weno5z_aoah", riemann="hll"), scalar=True)
+    P, _ = I.smooth_random_prims(s, seed=9, amp=0.3, b_amp=0.3, kmax=1)
+    X = _scalar_field(s, seed=2)
+    big = G.Context(s)
+    big.set_prims(P.copy())
+    big.set_scalar(X)
+    nb = (4, 3, 2)
+    n = [s.n[d] // nb[d] for d in range(3)]
+    ng = s.ng
+    bc_setups, sl = [], []
+    for bz in range(nb[2]):
+        for by in range(nb[1]):
+            for bx in range(nb[0]):
+                b3 = (bx, by, bz)
+                x0 = tuple(s.x0[d] + b3[d] * n[d] * s.dx[d] for d in range(3))
+                bc_setups.append(dataclasses.replace(s, n=tuple(n), x0=x0, bc="fixed"))
+                sl.append(tuple(slice(b3[d] * n[d], b3[d] * n[d] + n[d] + 2 * ng) for d in (2, 1, 0)))
+    bc = G.BatchContext(bc_setups)
+    for b, q in enumerate(sl):
+        bc.set_prims(b, np.ascontiguousarray(P[(slice(None),) + q]))
+        bc.set_scalar(b, np.ascontiguousarray(X[q]))
+    bc.set_lattice(nb, True)
+    for _ in range(2):
+        big.stage(0.0, 1.0, 1.0, 0.01)
+        big.stage(0.5, 0.5, 0.5, 0.01)
+        bc.stage(0.0, 1.0, 1.0, 0.01)
+        bc.stage(0.5, 0.5, 0.5, 0.01)
+    Xb, DXb = big.scalar(), big.scalar_cons()
+    for b, q in enumerate(sl):
+        inner = tuple(slice(t.start + ng, t.stop - ng) for t in q)
+        assert np.array_equal(bc.get(b, G.GRMHD_GET_SCALAR)[ng:-ng, ng:-ng, ng:-ng], Xb[inner]), b
+        assert np.array_equal(bc.get(b, G.GRMHD_GET_SCALAR_CONS),
+                              DXb[tuple(slice(t.start, t.stop - 2 * ng) for t in q)]), b
+
+
+def test_two_level_mesh_refuses_the_scalar(G):
+    root = I.Setup(n=(8, 8, 8), dx=(1 / 16,) * 3, recon="plm_mc", riemann="hll", bc="fixed", scalar=True)
+    m = I.two_level_mesh(root, (2, 1, 1), [(1, 0, 0)], True)
+    bc = G.BatchContext([m.setup(b) for b in range(m.nblocks)])
+    with pytest.raises(G.GrmhdError):
+        bc.set_mesh(m.nb, m.periodic, m.levels, m.pos)

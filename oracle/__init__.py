@@ -89,7 +89,7 @@ def _load():
         lib.orc_face_b_to_cells.argtypes = [P, dp, dp]
         lib.orc_face_fluxes_used.argtypes = [P, dp, dp, dp]
         lib.orc_stage_scalar.argtypes = [P, dp, dp, dp, dp, u8p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, dp, dp, ip, dp, dp, dp, dp]
+                                         ctypes.c_double, dp, dp, ip, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_finish_points.argtypes = [P, L, dp, dp, dp, u8p]
         _lib = lib
     return _lib
@@ -235,10 +235,11 @@ def stage(p: OrcParams, P, U0, Ucur, g0: float, g1: float, beta: float, dt: floa
     return out
 
 
-def stage_scalar(p: OrcParams, P, X, U0, Ucur, DX0, DXcur, g0: float, g1: float, beta: float, dt: float):
+def stage_scalar(p: OrcParams, P, X, U0, Ucur, DX0, DXcur, g0: float, g1: float, beta: float, dt: float,
+                 debug: bool = False):
     """One flux-CT stage that also advances a passive scalar X (ghosted [gz][gy][gx], updated in place like P)
     with conserved sqrt(gamma) D X (DX0 / DXcur interior arrays; DX0 may be None when g0 = 0).
-    Returns dict(U, DX, status, dt, maxspeed, iters)."""
+    Returns dict(U, DX, status, dt, maxspeed, iters[, F, E, FX])."""
     assert P.dtype == np.float64 and P.flags.c_contiguous and X.dtype == np.float64 and X.flags.c_contiguous
     Unew = np.zeros_like(Ucur)
     DXnew = np.zeros_like(DXcur)
@@ -248,11 +249,18 @@ def stage_scalar(p: OrcParams, P, X, U0, Ucur, DX0, DXcur, g0: float, g1: float,
     it = ctypes.c_int(0)
     DX0 = None if DX0 is None else np.ascontiguousarray(DX0, dtype=np.float64)
     DXcur = np.ascontiguousarray(DXcur, dtype=np.float64)
+    F = np.zeros((3, 8) + P.shape[1:]) if debug else None
+    E = np.zeros((3,) + P.shape[1:]) if debug else None
+    FX = np.zeros((3,) + P.shape[1:]) if debug else None
     _load().orc_stage_scalar(ctypes.byref(p), _dp(P), _dp(None if U0 is None else np.ascontiguousarray(U0)),
                              _dp(np.ascontiguousarray(Ucur)), _dp(Unew),
                              st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), g0, g1, beta, dt,
-                             ctypes.byref(dt_used), _dp(ms), ctypes.byref(it), _dp(X), _dp(DX0), _dp(DXcur), _dp(DXnew))
-    return dict(U=Unew, DX=DXnew, status=st, dt=dt_used.value, maxspeed=ms, iters=it.value)
+                             ctypes.byref(dt_used), _dp(ms), ctypes.byref(it), _dp(X), _dp(DX0), _dp(DXcur), _dp(DXnew),
+                             _dp(F), _dp(E), _dp(FX))
+    out = dict(U=Unew, DX=DXnew, status=st, dt=dt_used.value, maxspeed=ms, iters=it.value)
+    if debug:
+        out["F"], out["E"], out["FX"] = F, E, FX
+    return out
 
 
 def rk2_step_scalar(p: OrcParams, P, X, U, DX, dt: float = 0.0):

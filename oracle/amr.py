@@ -16,12 +16,15 @@ The paper names the AMR fill without formulas; the readings taken here:
   fluxes covering it, so that the mesh conserves every variable; it is applied after the stage,
   U += beta dt s (F_coarse - F_fine) / dx (s = +1 for the cell's upper face, -1 for its lower), and the
   cell then takes con2prim, floors and the re-derived hydro state again (the stage's last step).
-* one time step for all levels (no subcycling).
+* one time step for all levels (no subcycling);
+* a passive scalar X (optional) is exchanged like a primitive (the same copy, restriction and
+  prolongation) and its conserved sqrt(gamma) D X refluxed like the other variables, with the scalar's
+  face fluxes, after the fluid's refluxing; the refluxed cell's X is then DX / D with its refluxed D.
 Out of the mesh the coordinates wrap when periodic; otherwise those ghosts keep their loaded values.
 """
 import numpy as np
 
-from . import finish_points, face_fluxes_used, params, stage
+from . import finish_points, face_fluxes_used, params, stage, stage_scalar
 
 LEAF_NONE = -1
 
@@ -162,16 +165,25 @@ def _reflux(mesh, lm, Fu):
     return corr
 
 
-def mesh_stage(mesh, Ps, U0s, Ucurs, g0, g1, beta, dt):
+def mesh_stage(mesh, Ps, U0s, Ucurs, g0, g1, beta, dt, Xs=None, DX0s=None, DXcurs=None):
     """One RK stage of the mesh: Unew = g0 U0 + g1 Ucur + beta dt L on every leaf, with the ghost exchange
-    before and the refluxing after (module docstring). Ps is updated in place. Returns (Unew list, status
-    list, per-block maxspeed / dx maxima)."""
+    before and the refluxing after (module docstring). Ps (and the scalar's Xs, when given with its
+    conserved DXcurs and, for g0 != 0, DX0s) are updated in place. Returns (Unew list, status list,
+    per-block maxspeed / dx maxima), and the DXnew list last when a scalar is given."""
     lm = leaf_map(mesh)
     fill_ghosts(mesh, Ps, lm)
-    outs, Fu, speeds = [], [], []
+    if Xs is not None:
+        fill_ghosts(mesh, [X[None] for X in Xs], lm)  # as a one-variable primitive
+    outs, Fu, FX, speeds = [], [], [], []
     for b in range(mesh.nblocks):
         p = params(mesh.setup(b))
-        o = stage(p, Ps[b], None if U0s is None else U0s[b], Ucurs[b], g0, g1, beta, dt, debug=True)
+        U0 = None if U0s is None else U0s[b]
+        if Xs is None:
+            o = stage(p, Ps[b], U0, Ucurs[b], g0, g1, beta, dt, debug=True)
+        else:
+            o = stage_scalar(p, Ps[b], Xs[b], U0, Ucurs[b], None if DX0s is None else DX0s[b], DXcurs[b], g0, g1,
+                             beta, dt, debug=True)
+            FX.append([o["FX"][d][None] for d in range(3)])
         outs.append(o)
         Fu.append(face_fluxes_used(p, o["F"], o["E"]))
         speeds.append(max(o["maxspeed"][d] / mesh.setup(b).dx[d] for d in range(3)))
@@ -192,7 +204,16 @@ def mesh_stage(mesh, Ps, U0s, Ucurs, g0, g1, beta, dt):
             Unew[b][:, k, j, i] = Un[q]
             Ps[b][:, k + ng, j + ng, i + ng] = P[q]
             status[b][k, j, i] = st[q]
-    return Unew, status, speeds
+    if Xs is None:
+        return Unew, status, speeds
+    DXnew = [o["DX"] for o in outs]
+    corrX = _reflux(mesh, lm, FX)
+    for b in range(mesh.nblocks):
+        ng = mesh.setup(b).ng
+        for (k, j, i), dX in corrX[b].items():
+            DXnew[b][k, j, i] = DXnew[b][k, j, i] + beta * dt * dX[0]
+            Xs[b][k + ng, j + ng, i + ng] = DXnew[b][k, j, i] / Unew[b][0, k, j, i]
+    return Unew, status, speeds, DXnew
 
 
 def mesh_dt(mesh, speeds):

@@ -1204,16 +1204,19 @@ int orc_stage(const orc_params* p, double* P, const double* U0, const double* Uc
 // after the Riemann solver) times X on the upwind side of that flux (either side when it is zero);
 // DXnew = g0 DX0 + g1 DXcur - beta dt div F_X; then X = DXnew / (sqrt(gamma) D) with the stage's final
 // sqrt(gamma) D (after floors: a floor that adds mass dilutes X, D X stays conserved). DX0 may be NULL
-// when g0 = 0. The other arguments are those of orc_stage.
+// when g0 = 0. Optional outputs (may be NULL): the stage's face fluxes Fdbg [3][8][gsize] and edge EMFs
+// Edbg [3][gsize], and the scalar's face fluxes FXdbg [3][gsize]. The other arguments are those of orc_stage.
 int orc_stage_scalar(const orc_params* p, double* P, const double* U0, const double* Ucur, double* Unew,
                      uint8_t* status, double g0, double g1, double beta, double dt, double* dt_used, double* maxspeed,
-                     int* iters_total, double* X, const double* DX0, const double* DXcur, double* DXnew) {
+                     int* iters_total, double* X, const double* DX0, const double* DXcur, double* DXnew,
+                     double* Fdbg, double* Edbg, double* FXdbg) {
   const Grid g(*p);
   const long gn = g.gsize(), in = g.isize();
   const int N[3] = {g.nx, g.ny, g.nz};
   std::vector<double> F(3 * 8 * gn, 0.0);
   const int rc = stage_impl(p, P, U0, Ucur, Unew, status, g0, g1, beta, dt, dt_used, maxspeed, iters_total,
-                            F.data(), nullptr, nullptr, nullptr, nullptr);
+                            F.data(), Edbg, nullptr, nullptr, nullptr);
+  if (Fdbg) std::memcpy(Fdbg, F.data(), sizeof(double) * F.size());
   if (rc) return rc;
   dt = *dt_used;
   if (p->bc == 0) ghost_fill_periodic(g, X, 1);
@@ -1255,6 +1258,7 @@ int orc_stage_scalar(const orc_params* p, double* P, const double* U0, const dou
         DXnew[c] = g0 * x0 + g1 * DXcur[c] + beta * dt * (-div);
         X[g.gi(i, j, k)] = DXnew[c] / Unew[c];  // Unew[0 * in + c]: the densitized D
       }
+  if (FXdbg) std::memcpy(FXdbg, FX.data(), sizeof(double) * FX.size());
   (void)in;
   return 0;
 }

@@ -12,6 +12,8 @@ Fixed by the mathematics or by the single-block oracle, not by amr.py's own form
   does not without refluxing;
 * a mesh of one level everywhere (all roots, or all their children) is the single large block, bit for bit;
 * the state stays consistent: every leaf's primitives are the con2prim of its conserved state;
+* a passive scalar on the mesh: the sum of sqrt(gamma) D X is conserved to roundoff (and is not without
+  the scalar's refluxing), X = DX / D on every leaf, and a uniform X stays uniform across the levels;
 * a fast magnetosonic wave on a partly refined mesh ends with an error between those of the coarse and
   the fine uniform grids.
 ``test_planted_mistakes_fail_a_pin`` plants wrong prolongation offsets, an unlimited one-sided prolongation
@@ -316,3 +318,41 @@ def test_planted_mistakes_fail_a_pin():
             if not caught:
                 missed.append(name)
     assert not missed, missed
+
+
+def _scalar_mesh_steps(m, A=amr, dt=0.02, X0=None, steps=2):
+    Ps = I.two_level_prims(m, seed=8)
+    Us = A.mesh_prim2con(m, Ps)
+    rng = np.random.default_rng(12)
+    Xs = [(np.full(m.setup(b).prim_shape()[1:], X0) if X0 is not None
+           else rng.uniform(0.0, 1.0, m.setup(b).prim_shape()[1:])) for b in range(m.nblocks)]
+    DXs = [Us[b][0] * _interior(Xs[b][None])[0] for b in range(m.nblocks)]
+    t0 = sum(DX.sum() * np.prod(m.setup(b).dx) for b, DX in enumerate(DXs))
+    for _ in range(steps):
+        U1, st, _, DX1 = A.mesh_stage(m, Ps, None, Us, 0.0, 1.0, 1.0, dt, Xs, None, DXs)
+        Us, st, _, DXs = A.mesh_stage(m, Ps, Us, U1, 0.5, 0.5, 0.5, dt, Xs, DXs, DX1)
+    t1 = sum(DX.sum() * np.prod(m.setup(b).dx) for b, DX in enumerate(DXs))
+    scale = sum(np.abs(DX).sum() * np.prod(m.setup(b).dx) for b, DX in enumerate(DXs))
+    return Ps, Us, Xs, DXs, abs(t1 - t0) / scale
+
+
+def test_mesh_scalar_is_conserved_and_consistent():
+    m = _mesh(periodic=True, nb=(2, 2, 2), refined=[(1, 0, 0), (0, 1, 1)])
+    Ps, Us, Xs, DXs, err = _scalar_mesh_steps(m)
+    assert err < 1e-14
+    for b in range(m.nblocks):
+        np.testing.assert_allclose(_interior(Xs[b][None])[0], DXs[b] / Us[b][0], rtol=1e-15)
+
+
+def test_mesh_uniform_scalar_stays_uniform():
+    m = _mesh(periodic=True, nb=(2, 2, 2), refined=[(1, 0, 0), (0, 1, 1)])
+    Ps, Us, Xs, DXs, _ = _scalar_mesh_steps(m, X0=0.3)
+    assert max(np.max(np.abs(_interior(X[None]) - 0.3)) for X in Xs) < 1e-15
+
+
+def test_mesh_scalar_needs_its_refluxing(monkeypatch):
+    m = _mesh(periodic=True, nb=(2, 2, 2), refined=[(1, 0, 0), (0, 1, 1)])
+    orig = amr._reflux
+    monkeypatch.setattr(amr, "_reflux", lambda mesh, lm, Fu: orig(mesh, lm, Fu) if Fu[0][0].shape[0] == 8
+                        else [dict() for _ in range(mesh.nblocks)])
+    assert _scalar_mesh_steps(m)[-1] > 1e-8

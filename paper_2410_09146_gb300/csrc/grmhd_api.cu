@@ -682,6 +682,8 @@ static int batch_enqueue(grmhd_ctx* c, const BatchArgs& a, bool track, cudaStrea
     for (int d = 0; d < 3; ++d)
       CK(L.batch_scalar_flux(c->dblocks, c->nblocks, c->max_runs, c->prm.recon, d, s), "batched scalar flux");
     CK(L.batch_scalar_update(c->dblocks, c->nblocks, c->max_cells, a, s), "batched scalar update");
+    if (c->mesh_on && c->n_reflux > 0)
+      CK(L.mesh_reflux_scalar(c->dblocks, c->dreflux, c->n_reflux, a, s), "scalar refluxing");
   }
   return GRMHD_OK;
 }
@@ -1026,7 +1028,6 @@ int grmhd_batch_set_mesh(grmhd_ctx* c, int nbx, int nby, int nbz, int periodic, 
     c->mesh_on = false;
   } else {
     if (nbx < 1 || nby < 1 || nbz < 1 || !level || !pos) return fail(c, GRMHD_E_INVALID, "bad mesh arguments");
-    if (c->prm.scalar) return fail(c, GRMHD_E_INVALID, "two-level meshes do not carry the passive scalar");
     if (8LL * nbx * nby * nbz > c->leaf_cap) return fail(c, GRMHD_E_INVALID, "more root blocks than the batch's leaves can tile");
     std::vector<DevParams> bp(c->nblocks);
     for (int b = 0; b < c->nblocks; ++b) bp[b] = c->hblocks[b].p;

@@ -96,6 +96,12 @@ struct BatchLaunch {
       k_mesh_reflux<MINKOWSKI, R, T><<<grid, 64, 0, s>>>(b, cells, ncells, a);
     return cudaGetLastError();
   }
+  static cudaError_t mesh_reflux_scalar(const BlockDesc* b, const RefluxCell* cells, int ncells, const BatchArgs& a,
+                                        cudaStream_t s) {
+    if (ncells <= 0) return cudaSuccess;
+    k_mesh_reflux_scalar<R, T><<<(ncells + 63) / 64, 64, 0, s>>>(b, cells, ncells, a);
+    return cudaGetLastError();
+  }
   static int ctas_per_sm(int metric) {
     int n = 0;
     if (metric == KERR_SCHILD)

@@ -69,6 +69,9 @@ struct FormLaunchers {
                                    cudaStream_t s);
   cudaError_t (*batch_scalar_update)(const BlockDesc* b, int nblocks, long long max_cells, const BatchArgs& a,
                                      cudaStream_t s);
+  // refluxing of the passive scalar on a two-level mesh, after its update
+  cudaError_t (*mesh_reflux_scalar)(const BlockDesc* b, const RefluxCell* cells, int ncells, const BatchArgs& a,
+                                    cudaStream_t s);
 };
 
 const FormLaunchers& fp64_launchers();

@@ -52,21 +52,26 @@ __global__ void __launch_bounds__(256) k_mesh_exchange(const BlockDesc* __restri
     const long long g = gidx(p, c[0], c[1], c[2]);
     const T* __restrict__ Ps = (const T*)S.P;
     T* __restrict__ Pd = (T*)D.P;
+    // the passive scalar, when the batch carries one, is exchanged like one more primitive
+    const T* __restrict__ Xs = (const T*)S.X;
+    T* __restrict__ Xd = (T*)D.X;
     if (pass == 1 && S.level == lev) {
       const long long gs = gidx(S.p, gl[0] - S.pos[0] * n[0], gl[1] - S.pos[1] * n[1], gl[2] - S.pos[2] * n[2]);
 #pragma unroll
       for (int q = 0; q < NV; ++q) Pd[q * G + g] = Ps[q * G + gs];
+      if (Xs) Xd[g] = Xs[gs];
     } else if (pass == 1 && lev == 0 && S.level == 1) {
       // restriction: the 8 fine interior cells under this coarse ghost (n even: all in leaf S)
       const long long g0 = gidx(S.p, 2 * gl[0] - S.pos[0] * n[0], 2 * gl[1] - S.pos[1] * n[1], 2 * gl[2] - S.pos[2] * n[2]);
       const long long sy = S.p.gx, sz = (long long)S.p.gx * S.p.gy;
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const T* a = Ps + q * G + g0;
+      for (int q = 0; q <= NV; ++q) {
+        if (q == NV && !Xs) break;
+        const T* a = q < NV ? Ps + q * G + g0 : Xs + g0;
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc += a[(k & 1) + ((k >> 1) & 1) * sy + (k >> 2) * sz];
-        Pd[q * G + g] = acc / T(8);
+        if (q < NV) Pd[q * G + g] = acc / T(8); else Xd[g] = acc / T(8);
       }
     } else if (pass == 2 && S.level == 0) {
       // prolongation from the coarse cell containing this fine ghost (an interior cell of S)
@@ -77,8 +82,9 @@ __global__ void __launch_bounds__(256) k_mesh_exchange(const BlockDesc* __restri
 #pragma unroll
       for (int d = 0; d < 3; ++d) off[d] = (gl[d] & 1) ? T(0.25) : T(-0.25);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const T* a = Ps + q * G + gc;
+      for (int q = 0; q <= NV; ++q) {
+        if (q == NV && !Xs) break;
+        const T* a = q < NV ? Ps + q * G + gc : Xs + gc;
         const T pc = a[0];
         T v = pc;
 #pragma unroll
@@ -88,7 +94,7 @@ __global__ void __launch_bounds__(256) k_mesh_exchange(const BlockDesc* __restri
           const T m = up * dn > T(0) ? (up > T(0) ? (up < dn ? up : dn) : (up > dn ? up : dn)) : T(0);
           v = v + off[d] * m;
         }
-        Pd[q * G + g] = v;
+        if (q < NV) Pd[q * G + g] = v; else Xd[g] = v;
       }
     }
   }
@@ -194,6 +200,51 @@ __global__ void __launch_bounds__(64) k_mesh_reflux(const BlockDesc* __restrict_
       P[q * G + g] = (T)Pn[q];
     }
     B.status[t] = (uint8_t)stt;
+  }
+}
+
+// Refluxing of the passive scalar after its update: every coarse cell at a coarse-fine face corrects its
+// sqrt(gamma) D X by the difference between its face flux and the mean of the 4 fine ones (the same faces
+// as the fluid's refluxing), then X = DX / D with its refluxed D.
+template <class R, class T>
+__global__ void __launch_bounds__(64) k_mesh_reflux_scalar(const BlockDesc* __restrict__ blocks,
+                                                            const RefluxCell* __restrict__ cells, int ncells,
+                                                            BatchArgs a) {
+  const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
+  const double bdt = a.beta * dt;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < ncells; w += gridDim.x * blockDim.x) {
+    const RefluxCell rc = cells[w];
+    const BlockDesc& B = blocks[rc.block];
+    const DevParams& p = B.p;
+    const long long t = rc.cell;
+    const int nn[3] = {p.nx, p.ny, p.nz};
+    const int ci[3] = {(int)(t % p.nx), (int)((t / p.nx) % p.ny), (int)(t / ((long long)p.nx * p.ny))};
+    const long long g = gidx(p, ci[0], ci[1], ci[2]);
+    const long long st[3] = {1, p.gx, (long long)p.gx * p.gy};
+    double dX = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+      for (int s = 0; s < 2; ++s) {
+        const int fb = rc.fine[2 * d + s];
+        if (fb < 0) continue;
+        const BlockDesc& S = blocks[fb];
+        const double Fc = (double)((const R*)B.FX)[(long long)d * p.gsize + g + (s ? st[d] : 0)];
+        double Ff = 0.0;
+        int ff[3];
+        ff[d] = s ? 0 : nn[d];
+        for (int c2 = 0; c2 < 2; ++c2)
+          for (int c1 = 0; c1 < 2; ++c1) {
+            ff[a1] = 2 * (B.pos[a1] * nn[a1] + ci[a1]) - S.pos[a1] * nn[a1] + c1;
+            ff[a2] = 2 * (B.pos[a2] * nn[a2] + ci[a2]) - S.pos[a2] * nn[a2] + c2;
+            Ff += (double)((const R*)S.FX)[(long long)d * S.p.gsize + gidx(S.p, ff[0], ff[1], ff[2])];
+          }
+        dX += (s ? 1.0 : -1.0) * (Fc - Ff / 4.0) / p.dx[d];
+      }
+    }
+    double* DX = B.DX[a.dst];
+    const double dxn = DX[t] + bdt * dX;
+    DX[t] = dxn;
+    ((T*)B.X)[g] = (T)(dxn / B.U[a.dst][t]);
   }
 }
 

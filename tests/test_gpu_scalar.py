@@ -8,8 +8,7 @@ pinned in tests/test_oracle_scalar.py), through the C ABI.
   its flux divergence being formed in float like the fluid's); a uniform X stays uniform (FP64 to 1e-15,
   mixed to 1e-6: the scalar's flux is formed in float there).
 * Mixed form: per-variable L1 of X and D X against the FP64 oracle within 1e-6 after two steps.
-* Refusals: no scalar in the params, no prior grmhd_set_prims, a stage before grmhd_set_scalar, ng < 3,
-  two-level meshes.
+* Refusals: no scalar in the params, no prior grmhd_set_prims, a stage before grmhd_set_scalar, ng < 3.
 * Batches: uneven Kerr-Schild blocks in one batch (and its CUDA-graph replay) bit for bit each block's own
   context in both forms; a periodic lattice (X's ghosts exchanged with P's) bit for bit the large block.
 """
@@ -236,10 +235,3 @@ def test_lattice_scalar_is_the_large_block(G):
         assert np.array_equal(bc.get(b, G.GRMHD_GET_SCALAR_CONS),
                               DXb[tuple(slice(t.start, t.stop - 2 * ng) for t in q)]), b
 
-
-def test_two_level_mesh_refuses_the_scalar(G):
-    root = I.Setup(n=(8, 8, 8), dx=(1 / 16,) * 3, recon="plm_mc", riemann="hll", bc="fixed", scalar=True)
-    m = I.two_level_mesh(root, (2, 1, 1), [(1, 0, 0)], True)
-    bc = G.BatchContext([m.setup(b) for b in range(m.nblocks)])
-    with pytest.raises(G.GrmhdError):
-        bc.set_mesh(m.nb, m.periodic, m.levels, m.pos)

@@ -12,6 +12,8 @@ pinned in tests/test_oracle_amr.py), through the C ABI.
 * Mixed form: per-variable L1 of U and P against the oracle within 1e-6 (the mixed form's bound on
   smooth data).
 * A mesh of root blocks only is the lattice exchange, bit for bit; bad meshes are refused.
+* With a passive scalar (exchanged like a primitive, refluxed after its update): X and sqrt(gamma) D X of
+  every leaf within 1e-12 of the oracle (FP64) and the sum of sqrt(gamma) D X conserved on a periodic mesh.
 The time step is passed in (both sides take the same dt).
 """
 import dataclasses
@@ -156,3 +158,38 @@ def test_mesh_refusals(G):
     bo = G.BatchContext([odd.setup(0)])
     with pytest.raises(G.GrmhdError):
         bo.set_mesh((1, 1, 1), True, odd.levels, odd.pos)
+
+
+@pytest.mark.parametrize("name,make", [CASES[1], CASES[2]], ids=[CASES[1][0], CASES[2][0]])
+def test_fp64_mesh_scalar_matches_the_oracle(G, name, make):
+    from oracle import amr
+    m = make()
+    m.root = dataclasses.replace(m.root, scalar=True)
+    Ps = I.two_level_prims(m, seed=5)
+    rng = np.random.default_rng(6)
+    Xs = [rng.uniform(0.2, 0.8, m.setup(b).prim_shape()[1:]) for b in range(m.nblocks)]
+    dt = 0.4 * min(m.setup(b).dx[0] for b in range(m.nblocks)) / 1.5
+    bc = G.BatchContext([m.setup(b) for b in range(m.nblocks)])
+    for b in range(m.nblocks):
+        bc.set_prims(b, Ps[b].copy())
+        bc.set_scalar(b, Xs[b].copy())
+    bc.set_mesh(m.nb, m.periodic, m.levels, m.pos)
+    Po, Xo = [P.copy() for P in Ps], [X.copy() for X in Xs]
+    Us = amr.mesh_prim2con(m, Po)
+    ng = m.root.ng
+    DXs = [Us[b][0] * Xo[b][ng:-ng, ng:-ng, ng:-ng] for b in range(m.nblocks)]
+    t0 = sum(DX.sum() * np.prod(m.setup(b).dx) for b, DX in enumerate(DXs))
+    for _ in range(2):
+        bc.stage(0.0, 1.0, 1.0, dt)
+        bc.stage(0.5, 0.5, 0.5, dt)
+        U1, _, _, DX1 = amr.mesh_stage(m, Po, None, Us, 0.0, 1.0, 1.0, dt, Xo, None, DXs)
+        Us, _, _, DXs = amr.mesh_stage(m, Po, Us, U1, 0.5, 0.5, 0.5, dt, Xo, DXs, DX1)
+    Xg = [bc.get(b, G.GRMHD_GET_SCALAR)[ng:-ng, ng:-ng, ng:-ng] for b in range(m.nblocks)]
+    DXg = [bc.get(b, G.GRMHD_GET_SCALAR_CONS) for b in range(m.nblocks)]
+    ex = max(np.max(np.abs(a - b_[ng:-ng, ng:-ng, ng:-ng])) for a, b_ in zip(Xg, Xo)) / max(np.abs(X).max() for X in Xo)
+    ed = max(np.max(np.abs(a - b_)) for a, b_ in zip(DXg, DXs)) / max(np.abs(D).max() for D in DXs)
+    assert ex < 1e-12 and ed < 1e-12, (ex, ed)
+    if m.periodic:
+        t1 = sum(DX.sum() * np.prod(m.setup(b).dx) for b, DX in enumerate(DXg))
+        scale = sum(np.abs(DX).sum() * np.prod(m.setup(b).dx) for b, DX in enumerate(DXg))
+        assert abs(t1 - t0) < 1e-14 * scale

@@ -115,8 +115,8 @@ typedef struct {
                                  at velocity -beta (Sec. 4.1.1's boosted linear waves; |beta| < 1); ignored by
                                  Kerr-Schild */
   int scalar;                 /* 1: also evolve one passive scalar X, e.g. the electron fraction (Sec. 2.1,
-                                 (X rho u^mu)_{;mu} = 0; see grmhd_set_scalar); single-block contexts and batches
-                                 (not two-level meshes), ng >= 3 */
+                                 (X rho u^mu)_{;mu} = 0; see grmhd_set_scalar); single-block contexts, batches,
+                                 lattices and two-level meshes, ng >= 3 */
 } grmhd_params;
 
 /* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */
@@ -340,8 +340,10 @@ int grmhd_batch_set_lattice(grmhd_ctx* c, int nbx, int nby, int nbz, int periodi
  * [gz][gy][gx] of that block, ghosts included, host or device, read during the call; the block's
  * sqrt(gamma) D X formed from its current state; grmhd_batch_set_prims of the block discards it). Every
  * block needs one before a stage; the stage then advances each block's scalar as grmhd_stage does, and
- * a lattice exchange (grmhd_batch_set_lattice) copies X's ghosts with P's. Read back per block with
- * grmhd_batch_get(GRMHD_GET_SCALAR / GRMHD_GET_SCALAR_CONS). Two-level meshes refuse the scalar.
+ * a lattice exchange (grmhd_batch_set_lattice) copies X's ghosts with P's; a two-level mesh
+ * (grmhd_batch_set_mesh) exchanges X like a primitive and refluxes sqrt(gamma) D X with the scalar's face
+ * fluxes after its update (then X = DX / D with the refluxed D). Read back per block with
+ * grmhd_batch_get(GRMHD_GET_SCALAR / GRMHD_GET_SCALAR_CONS).
  * Errors: GRMHD_E_INVALID (not a batch, bad block, no scalar in the params, no state yet), GRMHD_E_CUDA. */
 int grmhd_batch_set_scalar(grmhd_ctx* c, int block, const double* X, int where);
 
@@ -362,7 +364,8 @@ int grmhd_batch_set_scalar(grmhd_ctx* c, int block, const double* X, int where);
  *    face flux from the edge EMFs) is replaced by the mean of the 4 fine face fluxes covering it,
  *    U += beta dt s (F_coarse - F_fine) / dx (s = +1 on the cell's upper face, -1 on its lower), and the
  *    cell takes con2prim (the double solver in both forms), floors and the re-derived hydro state again.
- * The mesh then conserves every variable to roundoff when periodic (floors aside). (0, 0, 0) switches the
+ * The mesh then conserves every variable to roundoff when periodic (floors aside). A passive scalar
+ * (params.scalar) is exchanged and refluxed the same way (see grmhd_batch_set_scalar). (0, 0, 0) switches the
  * mesh off; declaring a lattice (grmhd_batch_set_lattice) replaces it and vice versa.
  * Errors: GRMHD_E_INVALID (not a batch, bad arguments, sizes, levels, widths, corners, overlapping or
  * missing leaves), GRMHD_E_CUDA (upload). */

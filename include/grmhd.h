@@ -84,6 +84,8 @@ extern "C" {
 #define GRMHD_GET_FACE_B 5      /* double [3][nz+2ng][ny+2ng][nx+2ng]: the current face field (GRMHD_CT_FACE) */
 #define GRMHD_GET_SCALAR 6      /* double [nz+2ng][ny+2ng][nx+2ng]: the passive scalar X (params.scalar) */
 #define GRMHD_GET_SCALAR_CONS 7 /* double [nz][ny][nx]: its conserved sqrt(gamma) D X, the current state */
+#define GRMHD_GET_PRIMS_F32 8   /* float [8][nz+2ng][ny+2ng][nx+2ng]: the primitives as the mixed form stores them
+                                   (GRMHD_MIXED contexts only) */
 
 /* per-cell status bits */
 #define GRMHD_ST_RHO_FLOOR 1
@@ -121,6 +123,13 @@ typedef struct {
 
 /* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */
 size_t grmhd_workspace_bytes(const grmhd_params* p);
+
+/* The primitives in single precision, for the mixed form (which stores P in float): P is float
+ * [8][nz+2ng][ny+2ng][nx+2ng], host or device (where), read during the call, copied into the context's P
+ * without conversion; otherwise as grmhd_set_prims (U formed, a previous scalar or face field discarded).
+ * The same state as grmhd_set_prims with these values in double (its load rounds to float), at half the
+ * bytes. Errors: GRMHD_E_INVALID (an all-FP64 or batch context, P NULL, bad where), GRMHD_E_CUDA. */
+int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where);
 
 /* Passive scalar (params.scalar = 1; Sec. 2.1: Phoebus evolves passive scalars X, the electron fraction
  * among them, by (X rho u^mu)_{;mu} = S; here S = 0, no radiation). Set X after grmhd_set_prims or

@@ -470,6 +470,22 @@ int grmhd_set_face_b(grmhd_ctx* c, const double* Bf, int where) {
   return GRMHD_OK;
 }
 
+int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) {
+  if (!c || !P) return c ? fail(c, GRMHD_E_INVALID, "P is NULL") : GRMHD_E_INVALID;
+  if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
+  if (c->L->p_bytes != 4) return fail(c, GRMHD_E_INVALID, "single-precision primitives need a GRMHD_MIXED context");
+  if (where != GRMHD_HOST && where != GRMHD_DEVICE) return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");
+  const size_t bytes = sizeof(float) * NV * (size_t)c->dp.gsize;
+  CK(cudaMemcpyAsync(c->P, P, bytes, where == GRMHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
+     "copying P");
+  c->s0 = c->sc = 0;
+  CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], c->stream), "prim->cons");
+  c->has_state = true;
+  c->has_faces = false;
+  c->has_scalar = false;
+  return GRMHD_OK;
+}
+
 int grmhd_set_scalar(grmhd_ctx* c, const double* X, int where) {
   if (!c || !X) return c ? fail(c, GRMHD_E_INVALID, "X is NULL") : GRMHD_E_INVALID;
   if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
@@ -766,6 +782,10 @@ int grmhd_get(grmhd_ctx* c, int what, void* dst, int where) {
     }
     case GRMHD_GET_CONS:
       CK(cudaMemcpyAsync(dst, c->Uslot[c->sc], sizeof(double) * NV * (size_t)c->dp.isize, kind, s), "copying U");
+      break;
+    case GRMHD_GET_PRIMS_F32:
+      if (c->L->p_bytes != 4) return fail(c, GRMHD_E_INVALID, "single-precision primitives need a GRMHD_MIXED context");
+      CK(cudaMemcpyAsync(dst, c->P, sizeof(float) * NV * (size_t)c->dp.gsize, kind, s), "copying P");
       break;
     case GRMHD_GET_STATUS:
       CK(cudaMemcpyAsync(dst, c->status, (size_t)c->dp.isize, kind, s), "copying status");

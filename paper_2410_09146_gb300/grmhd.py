@@ -22,6 +22,7 @@ GRMHD_GET_PRIMS, GRMHD_GET_CONS, GRMHD_GET_STATUS, GRMHD_GET_STATS, GRMHD_GET_DT
 GRMHD_GET_FACE_B = 5
 GRMHD_GET_SCALAR = 6
 GRMHD_GET_SCALAR_CONS = 7
+GRMHD_GET_PRIMS_F32 = 8
 RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3, "mp5": 4}
 RIEMANN = {"llf": 0, "hll": 1}
 METRIC = {"minkowski": 0, "kerr_schild": 1}
@@ -80,6 +81,7 @@ def lib():
         L.grmhd_set_cons.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_set_face_b.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_set_scalar.argtypes = [vp, vp, ctypes.c_int]
+        L.grmhd_set_prims_f32.argtypes = [vp, vp, ctypes.c_int]
         L.grmhd_batch_set_scalar.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_stage.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.grmhd_rk2_step.argtypes = [vp, ctypes.c_double]
@@ -181,6 +183,11 @@ def grmhd_set_cons(ctx: int, U) -> None:
 def grmhd_set_face_b(ctx: int, Bf) -> None:
     ptr, where = _ptr(Bf)
     _check(lib().grmhd_set_face_b(ctx, ctypes.c_void_p(ptr), where), ctx)
+
+
+def grmhd_set_prims_f32(ctx: int, P) -> None:
+    ptr, where = _ptr(P)
+    _check(lib().grmhd_set_prims_f32(ctx, ctypes.c_void_p(ptr), where), ctx)
 
 
 def grmhd_set_scalar(ctx: int, X) -> None:
@@ -480,7 +487,8 @@ class Context:
                   GRMHD_GET_STATUS: (s.cons_shape()[1:], np.uint8), GRMHD_GET_STATS: ((8,), np.uint64),
                   GRMHD_GET_DT: ((1,), np.float64), GRMHD_GET_FACE_B: ((3,) + s.prim_shape()[1:], np.float64),
                   GRMHD_GET_SCALAR: (s.prim_shape()[1:], np.float64),
-                  GRMHD_GET_SCALAR_CONS: (s.cons_shape()[1:], np.float64)}
+                  GRMHD_GET_SCALAR_CONS: (s.cons_shape()[1:], np.float64),
+                  GRMHD_GET_PRIMS_F32: (s.prim_shape(), np.float32)}
         if out is None:
             shape, dt = shapes[what]
             out = np.empty(shape, dt)

@@ -118,7 +118,7 @@ typedef struct {
                                  Kerr-Schild */
   int scalar;                 /* 1: also evolve one passive scalar X, e.g. the electron fraction (Sec. 2.1,
                                  (X rho u^mu)_{;mu} = 0; see grmhd_set_scalar); single-block contexts, batches,
-                                 lattices and two-level meshes, ng >= 3 */
+                                 lattices and two-level meshes, with flux-CT and ng >= 3 */
 } grmhd_params;
 
 /* Bytes of device workspace a context with these parameters needs (0 on invalid parameters). */

@@ -113,6 +113,7 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   if (p->ct != GRMHD_CT_FLUX && p->ct != GRMHD_CT_FACE) { snprintf(msg, n, "unknown constrained-transport mode"); return false; }
   if (p->scalar != 0 && p->scalar != 1) { snprintf(msg, n, "scalar must be 0 or 1"); return false; }
   if (p->scalar && p->ng < 3) { snprintf(msg, n, "a passive scalar needs ng >= 3"); return false; }
+  if (p->scalar && p->ct != GRMHD_CT_FLUX) { snprintf(msg, n, "the passive scalar runs with flux-CT (GRMHD_CT_FLUX)"); return false; }
   if (p->metric == GRMHD_MINKOWSKI && !(p->shift[0] * p->shift[0] + p->shift[1] * p->shift[1] + p->shift[2] * p->shift[2] < 1.0)) {
     snprintf(msg, n, "the shift must have |beta| < 1");
     return false;

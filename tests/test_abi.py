@@ -48,6 +48,24 @@ def test_workspace_bytes_and_validation(lib):
     assert rc == G.GRMHD_E_WORKSPACE
 
 
+def test_scalar_and_mesh_parameter_validation(lib):
+    """Host-side checks of the passive scalar's parameters (no device work)."""
+    import dataclasses
+    s = dataclasses.replace(I.kerr_schild_setup(16), scalar=True)
+    with_x = G.grmhd_workspace_bytes(G.params(s))
+    without = G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, scalar=False)))
+    G_, I_ = (16 + 8) ** 3, 16 ** 3
+    assert with_x - without >= G_ * 8 + 3 * I_ * 8 + 3 * G_ * 8   # X, three D X slots, its face fluxes
+    assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, ng=2, recon="plm_mc"))) == 0
+    assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, ct="face"))) == 0
+    bad = G.params(s)
+    bad.scalar = 2
+    assert G.grmhd_workspace_bytes(bad) == 0
+    blocks = [G.block_of(dataclasses.replace(s, bc="fixed"))] * 3
+    assert (G.grmhd_batch_workspace_bytes(G.params(s), blocks) >
+            G.grmhd_batch_workspace_bytes(G.params(dataclasses.replace(s, scalar=False)), blocks))
+
+
 def test_struct_layout_matches_header(tmp_path):
     """Every field offset of the ctypes mirror equals the C compiler's offsetof on include/grmhd.h."""
     import shutil

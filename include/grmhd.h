@@ -151,7 +151,8 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
 
 /* Load primitives P (double, [8][nz+2ng][ny+2ng][nx+2ng] including ghosts; `where` = GRMHD_HOST or
  * GRMHD_DEVICE) and derive the conserved state of the interior (Sec. 2.1 eq. (conserved vector)).
- * Resets the Runge-Kutta slot bookkeeping. */
+ * A host P is read before the call returns; a device P must stay unchanged until the stream has run
+ * the load. Resets the Runge-Kutta slot bookkeeping. */
 int grmhd_set_prims(grmhd_ctx* c, const double* P, int where);
 
 /* Overwrite the current conserved state with U (double [8][nz][ny][nx]) without touching P; used

@@ -436,6 +436,7 @@ int grmhd_set_prims(grmhd_ctx* c, const double* P, int where) {
     // buffer, or three contiguous float flux buffers).
     void* tmp = c->F[0];
     CK(cudaMemcpyAsync(tmp, P, bytes, cudaMemcpyHostToDevice, c->stream), "copying P to the device");
+    CK(cudaStreamSynchronize(c->stream), "synchronising");  // a host P is read before the call returns
     src = (const double*)tmp;
   } else if (where != GRMHD_DEVICE) {
     return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");
@@ -479,6 +480,8 @@ int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) {
   const size_t bytes = sizeof(float) * NV * (size_t)c->dp.gsize;
   CK(cudaMemcpyAsync(c->P, P, bytes, where == GRMHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
      "copying P");
+  // a host P (pinned or not) is read before the call returns
+  if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
   c->s0 = c->sc = 0;
   CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], c->stream), "prim->cons");
   c->has_state = true;

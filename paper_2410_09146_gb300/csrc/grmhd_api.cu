@@ -1107,6 +1107,7 @@ int grmhd_batch_set_prims(grmhd_ctx* c, int block, const double* P, int where) {
   if (where == GRMHD_HOST) {
     // stage through the block's flux region (at least 8 G doubles in both forms)
     CK(cudaMemcpyAsync(b.F[0], P, bytes, cudaMemcpyHostToDevice, c->stream), "copying P to the device");
+    CK(cudaStreamSynchronize(c->stream), "synchronising");  // a host P is read before the call returns
     src = (const double*)b.F[0];
   } else if (where != GRMHD_DEVICE) {
     return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");

@@ -128,6 +128,46 @@ static void metric_eval(const orc_params& p, double x, double y, double z, Geom&
     }
     G.g[0][0] = -1.0 + b2;
     G.r = 1.0;
+  } else if (p.metric == 2) {
+    // Kerr-Schild in spherical coordinates with a logarithmic radius, (x^1, x^2, x^3) = (ln r, theta, phi):
+    // the radius and angles of the Cartesian form below through x + i y = (r + i a) e^{i phi} sin(theta),
+    // z = r cos(theta). With Sigma = r^2 + a^2 cos^2(theta) and q = 2 M r / Sigma, in (t, r, theta, phi):
+    // g_tt = -(1 - q), g_tr = q, g_tphi = -a sin^2 q, g_rr = 1 + q, g_rphi = -a sin^2 (1 + q),
+    // g_thth = Sigma, g_phph = sin^2 (Sigma + a^2 sin^2 (1 + q)); each r index then carries a factor r
+    // (dr = r dx^1) and d/dx^1 = r d/dr. Stationary and axisymmetric: no t or phi derivatives.
+    const double M = p.mass, a = p.spin * p.mass;
+    const double r = std::exp(x), sn = std::sin(y), cs = std::cos(y), s2 = sn * sn;
+    const double Sig = r * r + a * a * cs * cs;
+    const double q = 2.0 * M * r / Sig;
+    const double dSr = 2.0 * r, dSt = -2.0 * a * a * cs * sn;          // d Sigma / dr, d Sigma / dtheta
+    const double dqr = 2.0 * M * (Sig - r * dSr) / (Sig * Sig);          // dq / dr
+    const double dqt = -2.0 * M * r * dSt / (Sig * Sig);                 // dq / dtheta
+    double gs[4][4] = {}, gr[4][4] = {}, gt[4][4] = {};                  // g, d_r g, d_theta g in (t, r, theta, phi)
+    gs[0][0] = -(1.0 - q); gr[0][0] = dqr; gt[0][0] = dqt;
+    gs[0][1] = q; gr[0][1] = dqr; gt[0][1] = dqt;
+    gs[0][3] = -a * s2 * q; gr[0][3] = -a * s2 * dqr; gt[0][3] = -a * (2.0 * sn * cs * q + s2 * dqt);
+    gs[1][1] = 1.0 + q; gr[1][1] = dqr; gt[1][1] = dqt;
+    gs[1][3] = -a * s2 * (1.0 + q); gr[1][3] = -a * s2 * dqr; gt[1][3] = -a * (2.0 * sn * cs * (1.0 + q) + s2 * dqt);
+    gs[2][2] = Sig; gr[2][2] = dSr; gt[2][2] = dSt;
+    const double Ep = Sig + a * a * s2 * (1.0 + q);
+    gs[3][3] = s2 * Ep;
+    gr[3][3] = s2 * (dSr + a * a * s2 * dqr);
+    gt[3][3] = 2.0 * sn * cs * Ep + s2 * (dSt + a * a * (2.0 * sn * cs * (1.0 + q) + s2 * dqt));
+    for (int m = 0; m < 4; ++m)
+      for (int n = m + 1; n < 4; ++n) {
+        gs[n][m] = gs[m][n];
+        gr[n][m] = gr[m][n];
+        gt[n][m] = gt[m][n];
+      }
+    for (int m = 0; m < 4; ++m)
+      for (int n = 0; n < 4; ++n) {
+        const int k = (m == 1) + (n == 1);
+        const double fac = k == 0 ? 1.0 : (k == 1 ? r : r * r);
+        G.g[m][n] = fac * gs[m][n];
+        G.dg[1][m][n] = k * fac * gs[m][n] + fac * r * gr[m][n];  // r d/dr (r^k g)
+        G.dg[2][m][n] = fac * gt[m][n];
+      }
+    G.r = r;
   } else {
     const double M = p.mass, a = p.spin * p.mass;
     const double xs[4] = {0.0, x, y, z};
@@ -635,10 +675,11 @@ static void con2prim_point(const orc_params& p, const Geom& G, const double* Uc,
 }
 
 // Floors (Sec. 3.2) and the Lorentz-factor ceiling. Readings: rho_flr = rho0 r^-alpha
-// (Kerr-Schild radius r) or rho0 (Minkowski); u >= rho eps0 r^-alpha; W <= w_max.
+// (Kerr-Schild radius r; in the spherical coordinates x^1 = ln r this is the paper's rho0 e^{-alpha x^1})
+// or rho0 (Minkowski); u >= rho eps0 r^-alpha; W <= w_max.
 static int apply_floors(const orc_params& p, const Geom& G, double* P) {
   int st = 0;
-  double fr = p.metric == 1 ? std::pow(G.r, -p.floor_r_exp) : 1.0;
+  double fr = p.metric >= 1 ? std::pow(G.r, -p.floor_r_exp) : 1.0;
   const double rho_flr = p.rho_floor0 * fr;
   const double eps_flr = p.eps_floor0 * fr;
   if (!(P[0] >= rho_flr)) { P[0] = rho_flr; st |= ST_RHO_FLOOR; }

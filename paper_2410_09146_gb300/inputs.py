@@ -496,3 +496,74 @@ def two_level_wave_prims(mesh: TwoLevelMesh, background, eigvec, amplitude: floa
             P[v] = background[v] + amplitude * eigvec[v] * ph[None, None, :]
         out.append(P)
     return out
+
+
+# ----------------------------------------------------------------------------- spherical Kerr-Schild
+def torus_setup(n, r_lo, r_hi, th_lo, th_hi, spin=0.9, recon="weno5z_aoah", riemann="hll", nphi=4,
+                dphi=0.05) -> Setup:
+    """Block of n x n x nphi cells in spherical Kerr-Schild coordinates (x^1, x^2, x^3) = (ln r, theta, phi)
+    over [ln r_lo, ln r_hi] x [th_lo, th_hi] x [0, nphi dphi], fixed ghosts."""
+    x0 = (math.log(r_lo), th_lo, 0.0)
+    dx = ((math.log(r_hi) - math.log(r_lo)) / n, (th_hi - th_lo) / n, dphi)
+    return Setup(n=(n, n, nphi), x0=x0, dx=dx, metric="kerr_schild_spherical", spin=spin, mass=1.0, recon=recon,
+                 riemann=riemann, bc="fixed")
+
+
+def _bl_inverse_t_phi(r, th, a, M=1.0):
+    """g^{tt}, g^{t phi}, g^{phi phi} of Kerr in Boyer-Lindquist coordinates."""
+    s2 = np.sin(th) ** 2
+    Sig = r * r + a * a * np.cos(th) ** 2
+    gtt = -(1 - 2 * M * r / Sig)
+    gtp = -2 * M * a * r * s2 / Sig
+    gpp = (r * r + a * a + 2 * M * a * a * r * s2 / Sig) * s2
+    det = gtt * gpp - gtp * gtp
+    return gpp / det, -gtp / det, gtt / det, (gtt, gtp, gpp)
+
+
+def _u_t(r, th, l, a):
+    """u_t of the purely azimuthal flow with specific angular momentum l = -u_phi / u_t (u_t < 0)."""
+    itt, itp, ipp, _ = _bl_inverse_t_phi(r, th, a)
+    return -1.0 / np.sqrt(-(itt - 2 * l * itp + l * l * ipp))
+
+
+def torus_l(r_max, a, M=1.0):
+    """Specific angular momentum -u_phi/u_t of the prograde circular orbit at r_max in the equatorial plane
+    (Keplerian angular velocity sqrt(M) / (r^{3/2} + a sqrt(M)))."""
+    Om = math.sqrt(M) / (r_max ** 1.5 + a * math.sqrt(M))
+    _, _, _, (gtt, gtp, gpp) = _bl_inverse_t_phi(np.array(r_max), np.array(math.pi / 2), a, M)
+    return float(-(gtp + gpp * Om) / (gtt + gtp * Om))
+
+
+def torus_prims(s: Setup, r_in=6.0, r_max=12.0, K=0.01, rho_atm=1e-6, u_atm=1e-8):
+    """A stationary torus around a Kerr black hole: constant specific angular momentum l = -u_phi / u_t (the
+    Keplerian value at r_max), isentropic p = K rho^gamma, enthalpy from h u_t = const (h = 1 at the inner
+    edge r_in on the equator), at rest in r and theta; outside it a static-density atmosphere. The 4-velocity
+    has u^r = u^theta = 0 in Boyer-Lindquist coordinates, so u^t and u^phi are the same in Kerr-Schild.
+    Primitives at every cell of the spherical Kerr-Schild block s (ghosts included), B = 0."""
+    a, gam = s.spin * s.mass, s.gamma_eos
+    l = torus_l(r_max, a)
+    ut_in = _u_t(np.array(r_in), np.array(math.pi / 2), l, a)
+    x1, th = s.cell_centres(0), s.cell_centres(1)
+    R, TH = np.meshgrid(np.exp(x1), th, indexing="xy")          # [theta][r]
+    ut = _u_t(R, TH, l, a)
+    h = ut_in / ut
+    inside = h > 1.0
+    rho = np.where(inside, (np.maximum(h - 1.0, 0.0) * (gam - 1.0) / (K * gam)) ** (1.0 / (gam - 1.0)), rho_atm)
+    u = np.where(inside, K * rho ** gam / (gam - 1.0), u_atm)
+    itt, itp, ipp, _ = _bl_inverse_t_phi(R, TH, a)
+    uph_l = -l * ut
+    ucon_t = np.where(inside, itt * ut + itp * uph_l, 0.0)
+    ucon_p = np.where(inside, itp * ut + ipp * uph_l, 0.0)
+    # Kerr-Schild 3+1 split in (ln r, theta, phi): alpha = 1/sqrt(1 + q), beta^1 = q / ((1 + q) r)
+    Sig = R * R + a * a * np.cos(TH) ** 2
+    q = 2.0 * R / Sig
+    alpha = 1.0 / np.sqrt(1.0 + q)
+    beta1 = q / ((1.0 + q) * R)
+    # the atmosphere is at rest with respect to the normal observers (W = 1, u~ = 0)
+    P = np.zeros(s.prim_shape())
+    P[0] = rho[None]
+    P[4] = u[None]
+    P[1] = np.where(inside, beta1 * ucon_t, 0.0)[None]          # u~^1 = u^1 + beta^1 u^t, u^1 = 0
+    P[3] = np.where(inside, ucon_p, 0.0)[None]                   # u~^3 = u^3 + beta^3 u^t, beta^3 = 0
+    del alpha
+    return P

@@ -18,7 +18,9 @@ The planted mistakes, by the passage they break:
 * con2prim (Kastaun et al. 2021): the sign of the B-term in qbar, the W factor of eps, min instead of max in
   nu; the floors (Sec. 3.2): the internal energy floor absolute instead of specific;
 * the passive scalar (Sec. 2.1): X taken downwind, X from the old density, the RK weights exchanged, the
-  ghosts not filled, the stencil of the face's left state shifted.
+  ghosts not filled, the stencil of the face's left state shifted;
+* spherical Kerr-Schild: the (1 + q) factor of g_{r phi}, the radial derivative of q, the ln r chain rule of
+  the x^1 derivatives.
 """
 import os
 import subprocess
@@ -31,7 +33,7 @@ import oracle as orc
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = ["tests/test_oracle_metric.py", "tests/test_oracle_fluid.py", "tests/test_oracle_recon_riemann.py",
         "tests/test_oracle_c2p.py", "tests/test_oracle_stage.py", "tests/test_oracle_boosted_waves.py",
-        "tests/test_oracle_scalar.py"]
+        "tests/test_oracle_scalar.py", "tests/test_oracle_spherical_ks.py"]
 
 MUTANTS = {
     "KS f power of r": ("const double f = 2.0 * M * r * r2 / Sig;", "const double f = 2.0 * M * r2 / Sig;"),
@@ -72,6 +74,11 @@ MUTANTS = {
     "scalar RK weights exchanged": ("DXnew[c] = g0 * x0 + g1 * DXcur[c] + beta * dt * (-div);",
                                     "DXnew[c] = g1 * x0 + g0 * DXcur[c] + beta * dt * (-div);"),
     "scalar ghosts not filled": ("if (p->bc == 0) ghost_fill_periodic(g, X, 1);", "if (p->bc == 7) ghost_fill_periodic(g, X, 1);"),
+    "spherical g_rphi factor": ("gs[1][3] = -a * s2 * (1.0 + q);", "gs[1][3] = -a * s2 * q;"),
+    "spherical dq/dr": ("const double dqr = 2.0 * M * (Sig - r * dSr) / (Sig * Sig);",
+                        "const double dqr = 2.0 * M * (Sig - 2.0 * r * dSr) / (Sig * Sig);"),
+    "spherical ln r chain rule": ("G.dg[1][m][n] = k * fac * gs[m][n] + fac * r * gr[m][n];",
+                                  "G.dg[1][m][n] = fac * r * gr[m][n];"),
     "scalar left stencil": ("            cl[d] += q - 3;  // stencil of the cell below the face\n",
                             "            cl[d] += q - 2;  // stencil of the cell below the face\n"),
 }

@@ -1,0 +1,142 @@
+"""Pins of the oracle's Kerr-Schild metric in spherical coordinates with a logarithmic radius,
+(x^1, x^2, x^3) = (ln r, theta, phi) (metric 2; the coordinates of the paper's accretion set-ups, whose
+floors decay in x^1 = ln r, Sec. 3.2). Fixed independently of its formulas:
+
+* it is the Cartesian Kerr-Schild metric (metric 1, pinned in test_oracle_metric.py) transformed by the
+  coordinate map x + i y = (r + i a) e^{i phi} sin(theta), z = r cos(theta), r = e^{x^1}: g = J^T g_cart J;
+* its analytic derivatives match 4th-order central differences (no t or phi dependence);
+* Kerr is a vacuum solution: the Ricci tensor from its Christoffel symbols vanishes;
+* sqrt(-g) = r Sigma sin(theta) (Sigma = r^2 + a^2 cos^2 theta; the Boyer-Lindquist volume element, times r
+  for x^1 = ln r); a = 0 gives Schwarzschild in ingoing Eddington-Finkelstein form;
+* the oracle's stage in these coordinates keeps a stationary torus (the set-up of the paper's disk test)
+  stationary to the scheme's second order.
+"""
+import numpy as np
+
+import oracle as orc
+from paper_2410_09146_gb300 import inputs as I
+
+
+def _setup(spin=0.9):
+    return I.Setup(n=(8, 8, 8), metric="kerr_schild_spherical", spin=spin, mass=1.0, bc="fixed")
+
+
+def _pts(n, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([np.log(rng.uniform(2.5, 20.0, n)), rng.uniform(0.3, np.pi - 0.3, n),
+                     rng.uniform(0.0, 2 * np.pi, n)], 1)
+
+
+def test_is_the_cartesian_metric_transformed():
+    a = 0.9
+    ps, pc = orc.params(_setup(a)), orc.params(I.kerr_schild_setup(8))
+    X = _pts(60, 1)
+    r, th, ph = np.exp(X[:, 0]), X[:, 1], X[:, 2]
+    xyz = np.stack([np.sin(th) * (r * np.cos(ph) - a * np.sin(ph)), np.sin(th) * (r * np.sin(ph) + a * np.cos(ph)),
+                    r * np.cos(th)], 1)
+    J = np.zeros((len(X), 4, 4))  # d(t, x, y, z) / d(t, ln r, theta, phi)
+    J[:, 0, 0] = 1.0
+    J[:, 1, 1] = r * np.sin(th) * np.cos(ph)
+    J[:, 2, 1] = r * np.sin(th) * np.sin(ph)
+    J[:, 3, 1] = r * np.cos(th)
+    J[:, 1, 2] = np.cos(th) * (r * np.cos(ph) - a * np.sin(ph))
+    J[:, 2, 2] = np.cos(th) * (r * np.sin(ph) + a * np.cos(ph))
+    J[:, 3, 2] = -r * np.sin(th)
+    J[:, 1, 3] = -np.sin(th) * (r * np.sin(ph) + a * np.cos(ph))
+    J[:, 2, 3] = np.sin(th) * (r * np.cos(ph) - a * np.sin(ph))
+    gc = orc.geom_points(pc, xyz)["g"]
+    want = np.einsum("nma,nmk,nkb->nab", J, gc, J)
+    got = orc.geom_points(ps, X)["g"]
+    scale = np.abs(want).max(axis=(1, 2))[:, None, None]
+    assert np.max(np.abs(got - want) / scale) < 1e-13
+    # the Cartesian radius recovered from these points is r itself
+    np.testing.assert_allclose(orc.geom_points(pc, xyz)["alpha"], orc.geom_points(ps, X)["alpha"], rtol=1e-13)
+
+
+def _fd(f, x, h=1e-4):
+    out = []
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        out.append((-f(x + 2 * e) + 8 * f(x + e) - 8 * f(x - e) + f(x - 2 * e)) / (12 * h))
+    return np.stack(out, 1)
+
+
+def test_analytic_derivatives_match_fd():
+    p = orc.params(_setup())
+    X = _pts(30, 2)
+    g = orc.geom_points(p, X)
+    fd = _fd(lambda y: orc.geom_points(p, y)["g"], X)
+    scale = np.abs(g["g"]).max()
+    assert np.max(np.abs(g["dg"] - fd)) < 1e-9 * scale
+    assert np.all(g["dg"][:, 2] == 0.0)  # no phi dependence
+
+
+def _christoffel(g, dg, gu):
+    n = len(g)
+    D = np.zeros((n, 4, 4, 4))
+    D[:, 1:] = dg
+    t = D.transpose(0, 2, 1, 3) + D.transpose(0, 2, 3, 1) - D
+    return 0.5 * np.einsum("ndc,ncab->ndab", gu, t)
+
+
+def test_ricci_flat():
+    p = orc.params(_setup())
+    X = _pts(12, 3)
+
+    def gam_at(y):
+        g = orc.geom_points(p, y)
+        return _christoffel(g["g"], g["dg"], g["gu"])
+
+    G = gam_at(X)
+    dG = np.zeros((len(X), 4, 4, 4, 4))
+    dG[:, 1:] = _fd(gam_at, X, h=1e-3)
+    ricci = (np.einsum("nllab->nab", dG) - np.einsum("nblal->nab", dG)
+             + np.einsum("nlls,nsab->nab", G, G) - np.einsum("nlbs,nsal->nab", G, G))
+    scale = max(np.max(np.abs(np.einsum("nllab->nab", dG))), np.max(np.abs(np.einsum("nlbs,nsal->nab", G, G))))
+    assert scale > 1e-3
+    assert np.max(np.abs(ricci)) < 1e-7 * scale
+
+
+def test_volume_element_and_schwarzschild_limit():
+    a = 0.9
+    X = _pts(40, 4)
+    g = orc.geom_points(orc.params(_setup(a)), X)
+    r, th = np.exp(X[:, 0]), X[:, 1]
+    Sig = r * r + a * a * np.cos(th) ** 2
+    np.testing.assert_allclose(g["sqrtmg"], r * Sig * np.sin(th), rtol=1e-13)
+    np.testing.assert_allclose(np.sqrt(-np.linalg.det(g["g"])), r * Sig * np.sin(th), rtol=1e-12)
+    s = orc.geom_points(orc.params(_setup(0.0)), X)["g"]
+    f = 2.0 / r
+    np.testing.assert_allclose(s[:, 0, 0], -(1 - f), rtol=1e-14)
+    np.testing.assert_allclose(s[:, 0, 1], r * f, rtol=1e-14)
+    np.testing.assert_allclose(s[:, 1, 1], r * r * (1 + f), rtol=1e-14)
+    np.testing.assert_allclose(s[:, 2, 2], r * r, rtol=1e-14)
+    np.testing.assert_allclose(s[:, 3, 3], (r * np.sin(th)) ** 2, rtol=1e-14)
+    assert np.all(s[:, 0, 3] == 0) and np.all(s[:, 1, 3] == 0) and np.all(s[:, 0, 2] == 0)
+
+
+def test_stationary_torus_residual_falls_at_second_order():
+    """A torus of constant specific angular momentum in hydrostatic equilibrium (inputs.torus_prims, built in
+    Boyer-Lindquist coordinates from h u_t = const) is an exact stationary solution; one oracle stage in
+    spherical Kerr-Schild coordinates (WENO5-Z-AOAH + HLL, fixed ghosts from the solution) gives a residual
+    dU/dt in the block's inner half that falls at the scheme's second order (measured 2.0), for every
+    variable: the flux divergence and the geometric sources balance."""
+    res = []
+    for n in (16, 32, 64):
+        s = I.torus_setup(n, 9.0, 15.0, 1.35, 1.79)
+        p = orc.params(s)
+        P = I.torus_prims(s)
+        U = orc.prim2con_grid(p, P.copy())
+        dt = 1e-3
+        o = orc.stage(p, P.copy(), None, U, 0.0, 1.0, 1.0, dt)
+        assert np.all(o["status"] == 0)
+        q = n // 4
+        L = ((o["U"] - U) / dt)[:5, :, q:-q, q:-q]
+        Ui = U[:5, :, q:-q, q:-q]
+        scales = [np.abs(Ui[0]).max(), np.abs(Ui[1:4]).max(), np.abs(Ui[1:4]).max(), np.abs(Ui[1:4]).max(),
+                  np.abs(Ui[4]).max()]
+        res.append([np.abs(L[v]).max() / scales[v] for v in range(5)])
+    res = np.array(res)
+    orders = np.log2(res[:-1] / res[1:])
+    assert res[0].max() < 1e-5 and np.all(orders > 1.9), (res, orders)

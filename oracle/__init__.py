@@ -34,7 +34,7 @@ _lib = None
 RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3, "mp5": 4}
 RIEMANN = {"llf": 0, "hll": 1}
 METRIC = {"minkowski": 0, "kerr_schild": 1, "kerr_schild_spherical": 2}
-BC = {"periodic": 0, "fixed": 1}
+BC = {"periodic": 0, "fixed": 1, "spherical": 2}
 
 ST_RHO_FLOOR, ST_EPS_FLOOR, ST_W_CAP, ST_NOT_CONVERGED, ST_BAD_INPUT = 1, 2, 4, 8, 16
 

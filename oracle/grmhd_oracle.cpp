@@ -715,6 +715,34 @@ struct Grid {
 
 static int wrap(int i, int n) { return ((i % n) + n) % n; }
 
+// Spherical blocks (metric 2) covering theta in [0, pi] and phi in [0, 2 pi) with nz even (bc = 2): phi is
+// periodic, and a ghost beyond a pole is the cell mirrored across it and turned by pi in phi. The coordinate
+// map (r, theta, phi) -> point continues analytically through the pole, where (r, -theta, phi) and
+// (r, theta, phi + pi) are one point and d/dtheta reverses: the theta components of W v and of B change sign
+// (primitives 2 and 6), everything else is copied. The radial ghosts are left as loaded (fixed). nvar = 1
+// fills a scalar field (no sign change).
+static void ghost_fill_spherical(const Grid& g, double* P, int nvar = 8) {
+  const long n = g.gsize();
+  for (int k = -g.ng; k < g.nz + g.ng; ++k)
+    for (int j = -g.ng; j < g.ny + g.ng; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const bool jin = j >= 0 && j < g.ny, kin = k >= 0 && k < g.nz;
+        if (jin && kin) continue;
+        int sj = j, sk = wrap(k, g.nz);
+        double sign = 1.0;
+        if (j < 0 || j >= g.ny) {
+          sj = j < 0 ? -j - 1 : 2 * g.ny - j - 1;
+          sk = wrap(sk + g.nz / 2, g.nz);
+          sign = -1.0;
+        }
+        const long dst = g.gi(i, j, k), src = g.gi(i, sj, sk);
+        for (int v = 0; v < nvar; ++v) {
+          const double f = (nvar == 8 && (v == 2 || v == 6)) ? sign : 1.0;
+          P[v * n + dst] = f * P[v * n + src];
+        }
+      }
+}
+
 static void ghost_fill_periodic(const Grid& g, double* P, int nvar = 8) {
   const long n = g.gsize();
   for (int k = -g.ng; k < g.nz + g.ng; ++k)
@@ -911,6 +939,7 @@ int orc_prim2con_grid(const orc_params* p, const double* P, double* U) {
 int orc_ghost_fill(const orc_params* p, double* P) {
   Grid g(*p);
   if (p->bc == 0) ghost_fill_periodic(g, P);
+  if (p->bc == 2) ghost_fill_spherical(g, P);
   return 0;
 }
 
@@ -991,6 +1020,8 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
   if (p->bc == 0) {
     ghost_fill_periodic(g, P);
     if (face_ct) ghost_fill_faces_periodic(g, Bfcur);
+  } else if (p->bc == 2) {
+    ghost_fill_spherical(g, P);
   }
 
   // a2 + a3: face fluxes. Direction d face index fd in [0, N_d]; transverse cells in [-1, N].
@@ -1033,6 +1064,12 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
           }
           double xf[3] = {g.xc(0, i), g.xc(1, j), g.xc(2, k)};
           xf[d] = g.xf(d, c[d]);
+          if (p->metric == 2 && d == 1 && std::fabs(std::sin(xf[1])) < 1e-12) {
+            // Reading (spherical coordinates): a theta face on the polar axis has zero area (sqrt(-g) = 0,
+            // where the metric itself is singular), so it carries no flux.
+            for (int v = 0; v < 8; ++v) F[(d * 8 + v) * gn + g.gi(i, j, k)] = 0.0;
+            continue;
+          }
           Geom G;
           metric_eval(*p, xf[0], xf[1], xf[2], G);
           if (face_ct) {
@@ -1261,6 +1298,7 @@ int orc_stage_scalar(const orc_params* p, double* P, const double* U0, const dou
   if (rc) return rc;
   dt = *dt_used;
   if (p->bc == 0) ghost_fill_periodic(g, X, 1);
+  if (p->bc == 2) ghost_fill_spherical(g, X, 1);
   // face fluxes of sqrt(gamma) D X on the faces of the interior
   std::vector<double> FX(3 * gn, 0.0);
   for (int d = 0; d < 3; ++d) {

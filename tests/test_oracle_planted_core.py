@@ -20,7 +20,8 @@ The planted mistakes, by the passage they break:
 * the passive scalar (Sec. 2.1): X taken downwind, X from the old density, the RK weights exchanged, the
   ghosts not filled, the stencil of the face's left state shifted;
 * spherical Kerr-Schild: the (1 + q) factor of g_{r phi}, the radial derivative of q, the ln r chain rule of
-  the x^1 derivatives.
+  the x^1 derivatives; the polar boundary: the sign change on the wrong component, no half turn in phi,
+  flux through the axis faces.
 """
 import os
 import subprocess
@@ -79,6 +80,11 @@ MUTANTS = {
                         "const double dqr = 2.0 * M * (Sig - 2.0 * r * dSr) / (Sig * Sig);"),
     "spherical ln r chain rule": ("G.dg[1][m][n] = k * fac * gs[m][n] + fac * r * gr[m][n];",
                                   "G.dg[1][m][n] = fac * r * gr[m][n];"),
+    "polar sign on the radial component": ("const double f = (nvar == 8 && (v == 2 || v == 6)) ? sign : 1.0;",
+                                           "const double f = (nvar == 8 && (v == 1 || v == 5)) ? sign : 1.0;"),
+    "polar ghost without the half turn": ("          sk = wrap(sk + g.nz / 2, g.nz);\n", "          sk = wrap(sk, g.nz);\n"),
+    "flux through the polar axis": ("if (p->metric == 2 && d == 1 && std::fabs(std::sin(xf[1])) < 1e-12) {",
+                                    "if (p->metric == 2 && d == 1 && std::fabs(std::sin(xf[1])) < -1.0) {"),
     "scalar left stencil": ("            cl[d] += q - 3;  // stencil of the cell below the face\n",
                             "            cl[d] += q - 2;  // stencil of the cell below the face\n"),
 }

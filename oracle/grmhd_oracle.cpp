@@ -1036,20 +1036,26 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
           const int c[3] = {i, j, k};
           // Left state from cell c - e_d (its + face), right state from cell c (its - face).
           double PL[8], PR[8];
+          // spherical coordinates: the phi components of W v and B grow like 1 / sin(theta) towards the axis;
+          // sin(theta) times them is regular there (and continues through it with the sign of sin(theta)),
+          // so that product is reconstructed and divided by the face's sin(theta)
+          const bool sph = p->metric == 2;
+          const double sfc = sph ? std::sin(d == 1 ? g.xf(1, c[1]) : g.xc(1, j)) : 1.0;
           for (int v = 0; v < 8; ++v) {
+            const bool reg = sph && (v == 3 || v == 7) && std::fabs(sfc) > 1e-12;
             double sL[5], sR[5];
             for (int s = 0; s < 5; ++s) {
               int cl[3] = {i, j, k}, cr[3] = {i, j, k};
               cl[d] += s - 3;  // stencil of cell c-1: c-3 .. c+1
               cr[d] += s - 2;  // stencil of cell c:   c-2 .. c+2
-              sL[s] = P[v * gn + g.gi(cl[0], cl[1], cl[2])];
-              sR[s] = P[v * gn + g.gi(cr[0], cr[1], cr[2])];
+              sL[s] = P[v * gn + g.gi(cl[0], cl[1], cl[2])] * (reg ? std::sin(g.xc(1, cl[1])) : 1.0);
+              sR[s] = P[v * gn + g.gi(cr[0], cr[1], cr[2])] * (reg ? std::sin(g.xc(1, cr[1])) : 1.0);
             }
             double qm, qp;
             recon_cell(p->recon, sL, p->weno_eps, qm, qp);
-            PL[v] = qp;
+            PL[v] = reg ? qp / sfc : qp;
             recon_cell(p->recon, sR, p->weno_eps, qm, qp);
-            PR[v] = qm;
+            PR[v] = reg ? qm / sfc : qm;
           }
           // Reading (the paper is silent on reconstruction failure): a face whose reconstructed
           // density is not positive or internal energy is negative on either side takes the
@@ -1107,15 +1113,34 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
     // Omega_z(fi, fj, k): fi in [0, nx], fj in [0, ny], k in [0, nz)
     for (int k = 0; k < g.nz; ++k)
       for (int fj = 0; fj <= g.ny; ++fj)
-        for (int fi = 0; fi <= g.nx; ++fi)
+        for (int fi = 0; fi <= g.nx; ++fi) {
+          // spherical coordinates: an edge along phi on the axis has zero length, and so a zero EMF
+          // (Omega_phi is the covariant phi component of E, which carries a factor sin(theta))
+          if (p->metric == 2 && std::fabs(std::sin(g.xf(1, fj))) < 1e-12) {
+            E[2 * gn + g.gi(fi, fj, k)] = 0.0;
+            continue;
+          }
           E[2 * gn + g.gi(fi, fj, k)] = 0.25 * (Fv(1, 5, fi - 1, fj, k) + Fv(1, 5, fi, fj, k) -
                                                 Fv(0, 6, fi, fj - 1, k) - Fv(0, 6, fi, fj, k));
+        }
     // Omega_x(i, fj, fk)
     for (int fk = 0; fk <= g.nz; ++fk)
       for (int fj = 0; fj <= g.ny; ++fj)
         for (int i = 0; i < g.nx; ++i)
           E[0 * gn + g.gi(i, fj, fk)] = 0.25 * (Fv(2, 6, i, fj - 1, fk) + Fv(2, 6, i, fj, fk) -
                                                 Fv(1, 7, i, fj, fk - 1) - Fv(1, 7, i, fj, fk));
+    // spherical coordinates: the edges along r on the axis (theta face 0 or ny) are one line for every phi,
+    // where E_r is single-valued: their EMF is the mean over phi of the values computed there
+    if (p->metric == 2)
+      for (int fj = 0; fj <= g.ny; fj += g.ny) {
+        if (std::fabs(std::sin(g.xf(1, fj))) >= 1e-12) continue;
+        for (int i = 0; i < g.nx; ++i) {
+          double m = 0.0;
+          for (int fk = 0; fk < g.nz; ++fk) m += E[0 * gn + g.gi(i, fj, fk)];
+          m /= g.nz;
+          for (int fk = 0; fk <= g.nz; ++fk) E[0 * gn + g.gi(i, fj, fk)] = m;
+        }
+      }
     // Omega_y(fi, j, fk)
     for (int fk = 0; fk <= g.nz; ++fk)
       for (int j = 0; j < g.ny; ++j)

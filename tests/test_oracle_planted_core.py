@@ -21,7 +21,8 @@ The planted mistakes, by the passage they break:
   ghosts not filled, the stencil of the face's left state shifted;
 * spherical Kerr-Schild: the (1 + q) factor of g_{r phi}, the radial derivative of q, the ln r chain rule of
   the x^1 derivatives; the polar boundary: the sign change on the wrong component, no half turn in phi,
-  flux through the axis faces.
+  flux through the axis faces, phi components reconstructed without the sin(theta) weight, the EMFs on the
+  axis left as computed (along phi) or not averaged over phi (along r).
 """
 import os
 import subprocess
@@ -85,6 +86,12 @@ MUTANTS = {
     "polar ghost without the half turn": ("          sk = wrap(sk + g.nz / 2, g.nz);\n", "          sk = wrap(sk, g.nz);\n"),
     "flux through the polar axis": ("if (p->metric == 2 && d == 1 && std::fabs(std::sin(xf[1])) < 1e-12) {",
                                     "if (p->metric == 2 && d == 1 && std::fabs(std::sin(xf[1])) < -1.0) {"),
+    "phi components reconstructed unweighted": ("const bool reg = sph && (v == 3 || v == 7) && std::fabs(sfc) > 1e-12;",
+                                                "const bool reg = false;"),
+    "axis EMF along phi kept": ("if (p->metric == 2 && std::fabs(std::sin(g.xf(1, fj))) < 1e-12) {\n            E[2 * gn",
+                                "if (p->metric == 7 && std::fabs(std::sin(g.xf(1, fj))) < 1e-12) {\n            E[2 * gn"),
+    "axis EMF along r not averaged": ("    if (p->metric == 2)\n      for (int fj = 0; fj <= g.ny; fj += g.ny) {",
+                                      "    if (p->metric == 7)\n      for (int fj = 0; fj <= g.ny; fj += g.ny) {"),
     "scalar left stencil": ("            cl[d] += q - 3;  // stencil of the cell below the face\n",
                             "            cl[d] += q - 2;  // stencil of the cell below the face\n"),
 }
@@ -110,7 +117,17 @@ def test_planted_core_mistakes_fail_a_pin():
     for name, (a, b) in MUTANTS.items():
         assert src.count(a) == 1, name
     with tempfile.TemporaryDirectory() as tmp:
+        # an unchanged copy first: the pins must pass on it, or no failure below would mean anything
+        d = os.path.join(tmp, "unchanged")
+        os.makedirs(d)
+        with open(os.path.join(d, "grmhd_oracle.cpp"), "w") as f:
+            f.write(src)
+        env = dict(os.environ, GRMHD_ORACLE_SRC=os.path.join(d, "grmhd_oracle.cpp"), GRMHD_ORACLE_BUILD=d)
         with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            base = ex.submit(subprocess.run, [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                             cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
             res = list(ex.map(lambda kv: _run(tmp, kv[0], *kv[1][1], src), enumerate(MUTANTS.items())))
+            base = base.result()
+    assert base.returncode == 0, base.stdout[-2000:]
     missed = {name: summary for name, (caught, summary) in zip(MUTANTS, res) if not caught}
     assert not missed, missed

@@ -11,8 +11,9 @@ floors decay in x^1 = ln r, Sec. 3.2). Fixed independently of its formulas:
 * the oracle's stage in these coordinates keeps a stationary torus (the set-up of the paper's disk test)
   stationary to the scheme's second order;
 * the polar boundary (bc "spherical") continues smooth scalar and vector fields through the pole exactly,
-  and a uniform flow along the axis with an axial field stays stationary at second order or better, next
-  to the axis too (axis faces carry no flux: their area vanishes).
+  and a uniform flow along the axis with a field across it stays stationary at second order or better in
+  every variable, next to the axis too (axis faces carry no flux; sin(theta) times the phi components is
+  reconstructed, being regular on the axis; EMFs on the axis are zero along phi and single-valued along r).
 """
 import numpy as np
 
@@ -192,17 +193,19 @@ def test_polar_ghosts_continue_smooth_fields():
 
 
 def test_uniform_flow_across_the_poles():
-    """Flat space in spherical coordinates (M = 0): a uniform flow along the axis with an axial field is
-    stationary; one oracle stage (WENO5-Z-AOAH + HLL, polar and periodic ghosts, axis faces without flux)
-    gives residuals that fall at order > 1.9 both in the rows next to the axis and elsewhere (measured
-    about 3 and 2.1)."""
+    """Flat space in spherical coordinates (M = 0): a uniform flow along the axis with a field that has
+    components across it is stationary. One oracle stage (WENO5-Z-AOAH + HLL, polar and periodic ghosts, axis
+    faces without flux, sin(theta)-weighted phi components reconstructed, axis EMFs: zero along phi and the
+    phi mean along r) gives, for every variable on its own scale, residuals that fall at order > 1.8 in the
+    rows next to the axis and elsewhere on the finest pair of grids (measured 1.9 to 3.0), and on average
+    > 1.6 over both pairs."""
     res = []
     for m in (1, 2, 4):
         s = _full_sphere(4 * m, 8 * m, 16 * m, spin=0.0, mass=0.0)
         p = orc.params(s)
         W = 1 / np.sqrt(1 - 0.09)
         uc, _ = _cart_to_sph(s, 0.0, lambda x, y, z: np.stack([0 * x, 0 * x, 0 * x + 0.3 * W]))
-        Bc, _ = _cart_to_sph(s, 0.0, lambda x, y, z: np.stack([0 * x, 0 * x, 0 * x + 0.2]))
+        Bc, _ = _cart_to_sph(s, 0.0, lambda x, y, z: np.stack([0 * x + 0.15, 0 * x + 0.1, 0 * x + 0.2]))
         P = np.zeros(s.prim_shape())
         P[0], P[4] = 1.0, 1.5
         P[1:4], P[5:8] = uc, Bc
@@ -212,8 +215,10 @@ def test_uniform_flow_across_the_poles():
         assert np.all(o["status"] == 0)
         q = s.n[0] // 4
         L = ((o["U"] - U) / dt)[:, :, :, q:-q]
-        sc = np.abs(U[:, :, :, q:-q]).max()
-        res.append((np.abs(L[:, :, [0, -1], :]).max() / sc, np.abs(L[:, :, 2:-2, :]).max() / sc))
-    res = np.array(res)
+        sc = np.abs(U[:, :, :, q:-q]).reshape(8, -1).max(1)[:, None]
+        res.append(np.concatenate([np.abs(L[:, :, [0, 1, -2, -1], :]).reshape(8, -1).max(1)[:, None] / sc,
+                                   np.abs(L[:, :, 2:-2, :]).reshape(8, -1).max(1)[:, None] / sc], 1))
+    res = np.array(res)  # [resolution][variable][axis rows, elsewhere]
     orders = np.log2(res[:-1] / res[1:])
-    assert np.all(orders > 1.9), (res, orders)
+    # the finest pair is asymptotic (1.9 to 3.0); on the coarsest B^phi away from the axis is at 1.44
+    assert np.all(orders[-1] > 1.8) and np.all(np.log2(res[0] / res[-1]) / 2 > 1.6), (res, orders)

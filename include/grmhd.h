@@ -183,10 +183,14 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt);
 /* One SSP-RK2 (Heun) step: stages (0, 1, 1) and (1/2, 1/2, 1/2) with the same dt (dt <= 0: CFL). */
 int grmhd_rk2_step(grmhd_ctx* c, double dt);
 
-/* Con2prim of a flat-space batch (local orthonormal frame, Minkowski floors): U and P are device
- * arrays [8][n] (structure of arrays) of densitized conserved / primitive variables; status (uint8 [n])
- * and iters (int [n]) may be NULL. flags bit 0: P holds a warm-start guess on entry. Uses the
- * context's gamma_eos, floors, tolerance and stream. Asynchronous. */
+/* Con2prim of a flat-space batch (a6 on its own; Sec. 3.1, the Kastaun et al. solve, and the Sec. 3.2
+ * floors in their Minkowski form): U and P are device arrays [8][n] (structure of arrays) of densitized
+ * conserved / primitive variables; status (uint8 [n]) and iters (int [n]) may be NULL. flags bit 0: P holds
+ * a warm-start guess on entry. Uses the context's gamma_eos, floors, tolerance and stream. Asynchronous.
+ * Two narrowings of the general interface, both deliberate: the states are given in the local orthonormal
+ * frame (any metric reduces to it point by point, which is how the stage itself calls the same solve with
+ * its cell's metric), and the arrays are device memory only (a caller with host arrays copies them with one
+ * cudaMemcpyAsync each; the library allocates no staging buffer). Errors: GRMHD_E_INVALID, GRMHD_E_CUDA. */
 int grmhd_c2p(grmhd_ctx* c, long long n, const double* U, double* P, uint8_t* status, int* iters, int flags);
 
 /* Prim->cons of a flat-space batch (Sec. 2.1 eq. (conserved vector) with the Minkowski metric): P and U
@@ -290,6 +294,22 @@ int grmhd_set_timing(grmhd_ctx* c, int on);
  * resets the totals. Synchronises on the last recorded event. */
 int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
 
+/* The a7 helper (CFL rule; the paper does not state one): out[d] = the largest characteristic speed |lambda+-|
+ * over the interior faces of direction d, from the last stage of this single-block context that took its
+ * time step from the face speeds (a first stage, g0 == 0, with dt <= 0); dt = cfl / max_d(out[d] / dx[d]) is
+ * the step GRMHD_GET_DT returns. Zero before such a stage. Synchronises the context's stream.
+ * Errors: GRMHD_E_INVALID (NULL, or a batch / con2prim-only context), GRMHD_E_CUDA. */
+int grmhd_max_speed(grmhd_ctx* c, double out[3]);
+
+/* Roofline denominators of the ALU-bound kernels (measurement aid; the paper has no counterpart): the dense
+ * fused multiply-add rates of the current device in TFLOP/s (2 flops per FMA), FP64 and FP32, each timed
+ * with CUDA events on `stream` over one launch of eight independent FMA chains per thread on every SM
+ * (about 40 ms and 10 ms on a GB300). The double-precision update and con2prim of the stage are bound by
+ * the FP64 pipe on GB300, whose FP64 rate is about 1/74 of its FP32 rate. `sink` is a caller-owned device
+ * buffer of at least 8 bytes that the kernels may write (they do not in practice); blocks the calling
+ * thread until the measurement ends. Errors: GRMHD_E_INVALID (a NULL pointer), GRMHD_E_CUDA. */
+int grmhd_fp_peaks(double* sink, void* stream, double* fp64_tflops, double* fp32_tflops);
+
 /* One all-FP64 Runge-Kutta stage, like grmhd_stage, for callers that cannot allocate device memory
  * (code inside a CUDA-graph capture, hosts whose framework owns every device allocation, embedded
  * hosts without a device allocator). The paper has no counterpart: this is a packaging of the same
@@ -299,11 +319,15 @@ int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
  *   Ucur   double [8][nz][ny][nx], the stage's input state
  *   Unew   double [8][nz][ny][nx], the stage's output state (may not alias Ucur or U0)
  *   status uint8  [nz][ny][nx]
- * -- and the coefficients of Unew = g0 U0 + g1 Ucur + beta dt L(Ucur); dt <= 0 takes the CFL step of
- * this call's face speeds. p->precision must be GRMHD_FP64 and p->ct GRMHD_CT_FLUX (else GRMHD_E_INVALID).
+ * -- and the coefficients of Unew = g0 U0 + g1 Ucur + beta dt L(Ucur). dt <= 0 on a first stage (g0 == 0)
+ * takes the CFL step of this call's face speeds; dt <= 0 on a later stage (g0 != 0) reuses the step that
+ * the last first-stage call on this device left in the shared array, as grmhd_stage reuses its first
+ * stage's (a two-call RK2 step with dt <= 0 on both calls advances like grmhd_rk2_step, provided no
+ * other call runs in between). p is checked as by grmhd_create (GRMHD_E_INVALID with the reason in
+ * grmhd_last_error(NULL)); p->precision must be GRMHD_FP64 and p->ct GRMHD_CT_FLUX, without a scalar.
  * Scratch (face fluxes, edge EMFs, speed and time-step scalars) lives in a 16 MiB array of device
  * memory built into the library (every GPU that loads the library holds it until the process exits),
- * which bounds the block to (16 MiB - 512 B) / 216 B = 77,672 ghosted cells, e.g. 34^3 interior cells
+ * which bounds the block to floor((16 MiB - 512 B) / 216 B) = 77,669 ghosted cells, e.g. 34^3 interior cells
  * with 4 ghosts; larger blocks are rejected with GRMHD_E_INVALID and a message in
  * grmhd_last_error(NULL). The first call on each device looks up the array's device address; make
  * that first call before any stream capture. Every call shares the array and the array keeps the

@@ -12,7 +12,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgrmhd.so")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["grmhd_api.cu", "grmhd_fp64.cu", "grmhd_mixed.cu", "grmhd_batch.cu", "grmhd_noalloc.cu", "grmhd_mlp.cu",
-           "grmhd_mlp_train.cu", "grmhd_mlp_tc.cu"]
+           "grmhd_mlp_train.cu", "grmhd_mlp_tc.cu", "grmhd_peaks.cu"]
 # The all-FP64 stage kernels round every double operation separately, as the FP64 reference does.
 PER_SOURCE_FLAGS = {"grmhd_fp64.cu": ["-fmad=false"]}
 HEADERS = ["grmhd_device.cuh", "grmhd_kernels.cuh", "grmhd_launch.h", "grmhd_mlp.cuh", "grmhd_face_ct.cuh",

@@ -77,17 +77,10 @@ struct grmhd_ctx {
   char err[256];
 };
 
-namespace {
+namespace grmhd {
 
-thread_local char g_create_err[256] = "";
-
-constexpr size_t kAlign = 256;
-size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
-
-struct Layout {
-  size_t P, U[3], F[3], E, status, worklist, wl_mu, floorlist, geo, B[3], Ecc, X, DX[3], FX, scal, total;
-};
-
+// Parameter checks and the kernel-side copy of the parameters, shared by every entry point that takes a
+// grmhd_params (contexts, batches and the allocation-free stage).
 bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   if (!p) { snprintf(msg, n, "params is NULL"); return false; }
   const bool batch_only = p->nx == 0 && p->ny == 0 && p->nz == 0;
@@ -120,6 +113,43 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   }
   return true;
 }
+
+DevParams dev_params(const grmhd_params* p) {
+  DevParams d{};
+  d.nx = p->nx; d.ny = p->ny; d.nz = p->nz; d.ng = p->ng;
+  d.gx = p->nx + 2 * p->ng; d.gy = p->ny + 2 * p->ng; d.gz = p->nz + 2 * p->ng;
+  d.gsize = (long long)d.gx * d.gy * d.gz;
+  d.isize = (long long)p->nx * p->ny * p->nz;
+  for (int i = 0; i < 3; ++i) {
+    d.x0[i] = p->x0[i];
+    d.dx[i] = p->dx[i];
+    d.idx[i] = p->dx[i] > 0 ? 1.0 / p->dx[i] : 0.0;
+  }
+  d.a = p->spin * p->mass;
+  d.M = p->mass;
+  d.gamma_eos = p->gamma_eos;
+  d.metric = p->metric; d.recon = p->recon; d.riemann = p->riemann; d.bc = p->bc;
+  d.rho_floor0 = p->rho_floor0; d.eps_floor0 = p->eps_floor0; d.floor_r_exp = p->floor_r_exp; d.w_max = p->w_max;
+  d.w_max2 = p->w_max * p->w_max;
+  d.v0sq_cap = 1.0 - 1.0 / (p->w_max * p->w_max);
+  d.c2p_tol = p->c2p_tol; d.c2p_max_iter = p->c2p_max_iter;
+  d.cfl = p->cfl; d.weno_eps = p->weno_eps;
+  for (int i = 0; i < 3; ++i) d.shift[i] = p->metric == GRMHD_MINKOWSKI ? p->shift[i] : 0.0;
+  return d;
+}
+
+}  // namespace grmhd
+
+namespace {
+
+thread_local char g_create_err[256] = "";
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+  size_t P, U[3], F[3], E, status, worklist, wl_mu, floorlist, geo, B[3], Ecc, X, DX[3], FX, scal, total;
+};
 
 Layout layout_of(const grmhd_params* p) {
   Layout l{};
@@ -154,30 +184,6 @@ Layout layout_of(const grmhd_params* p) {
   }
   l.total = off;
   return l;
-}
-
-DevParams dev_params(const grmhd_params* p) {
-  DevParams d{};
-  d.nx = p->nx; d.ny = p->ny; d.nz = p->nz; d.ng = p->ng;
-  d.gx = p->nx + 2 * p->ng; d.gy = p->ny + 2 * p->ng; d.gz = p->nz + 2 * p->ng;
-  d.gsize = (long long)d.gx * d.gy * d.gz;
-  d.isize = (long long)p->nx * p->ny * p->nz;
-  for (int i = 0; i < 3; ++i) {
-    d.x0[i] = p->x0[i];
-    d.dx[i] = p->dx[i];
-    d.idx[i] = p->dx[i] > 0 ? 1.0 / p->dx[i] : 0.0;
-  }
-  d.a = p->spin * p->mass;
-  d.M = p->mass;
-  d.gamma_eos = p->gamma_eos;
-  d.metric = p->metric; d.recon = p->recon; d.riemann = p->riemann; d.bc = p->bc;
-  d.rho_floor0 = p->rho_floor0; d.eps_floor0 = p->eps_floor0; d.floor_r_exp = p->floor_r_exp; d.w_max = p->w_max;
-  d.w_max2 = p->w_max * p->w_max;
-  d.v0sq_cap = 1.0 - 1.0 / (p->w_max * p->w_max);
-  d.c2p_tol = p->c2p_tol; d.c2p_max_iter = p->c2p_max_iter;
-  d.cfl = p->cfl; d.weno_eps = p->weno_eps;
-  for (int i = 0; i < 3; ++i) d.shift[i] = p->metric == GRMHD_MINKOWSKI ? p->shift[i] : 0.0;
-  return d;
 }
 
 int fail(grmhd_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) {
@@ -757,6 +763,20 @@ static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double d
   }
   c->s0 = s0;
   c->sc = dst;
+  return GRMHD_OK;
+}
+
+int grmhd_max_speed(grmhd_ctx* c, double out[3]) {
+  if (!c || !out) return c ? fail(c, GRMHD_E_INVALID, "out is NULL") : GRMHD_E_INVALID;
+  if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
+  unsigned long long bits[3];
+  CK(cudaMemcpyAsync(bits, c->scal, sizeof bits, cudaMemcpyDeviceToHost, c->stream), "copying the speeds");
+  CK(cudaStreamSynchronize(c->stream), "synchronising");
+  for (int d = 0; d < 3; ++d) {
+    double v;
+    std::memcpy(&v, &bits[d], sizeof v);  // non-negative doubles are kept as their bit patterns
+    out[d] = v;
+  }
   return GRMHD_OK;
 }
 

@@ -287,15 +287,28 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   for (int i = 0; i < 3; ++i) bl[i] = Bl[i] * iW + ab0 * vl[i];
   const R pgas = (gamma_eos - R(1)) * u;
   const R rhoh = rho + u + pgas;
-  const R w = rhoh + b2;
   const R pstar = pgas + R(0.5) * b2;
   const R D = rho * W;
-  const R wW2 = w * W * W;
   R Uc[NV];
   Uc[0] = D;
+  if constexpr (sizeof(R) == 4) {
+    // Float faces: S_j and tau in forms without cancellation. The printed forms
+    // S_j = (rho h + b^2) W^2 v_j - alpha b^0 b_j and tau = (rho h + b^2) W^2 - p* - (alpha b^0)^2 - D
+    // subtract terms of size W^2 (B.v)^2 (and rho W from rho h W^2), so their float rounding grows
+    // like W^2 in magnetised, relativistic cells. With b^2 W^2 = B^2 + (alpha b^0)^2 they are equal to
+    //   S_j = (rho h W^2 + B^2) v_j - (B.v) B_j,
+    //   tau = rho W u^2/(W + 1) + rho eps W^2 + p u^2 + B^2 - (B^2 + (alpha b^0)^2)/(2 W^2)   (u^2 = W^2 - 1),
+    // whose terms are all of the size of the result.
+    const R rhohW2 = rhoh * W * W;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) Uc[1 + j] = wW2 * vl[j] - ab0 * bl[j];
-  Uc[4] = wW2 - pstar - ab0 * ab0 - D;
+    for (int j = 0; j < 3; ++j) Uc[1 + j] = (rhohW2 + B2) * vl[j] - Bv * Bl[j];
+    Uc[4] = D * usq / (W + R(1)) + u * W * W + pgas * usq + (B2 - R(0.5) * b2);
+  } else {
+    const R wW2 = (rhoh + b2) * W * W;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Uc[1 + j] = wW2 * vl[j] - ab0 * bl[j];
+    Uc[4] = wW2 - pstar - ab0 * ab0 - D;
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) Uc[5 + k] = B[k];
   const R vtd = vt[d] * ia;
@@ -312,13 +325,25 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   const R cs2 = gamma_eos * pgas / rhoh;
   const R va2 = b2 / (rhoh + b2);
   const R c2 = va2 + cs2 * (R(1) - va2);
-  const R v2 = usq * iW * iW;
   const R vd = v[d];
-  R disc = (R(1) - v2) * (m.gamu[sym3(d, d)] * (R(1) - v2 * c2) - vd * vd * (R(1) - c2));
+  R one_v2, one_c2, one_v2c2;  // 1 - v^2, 1 - c^2 and 1 - v^2 c^2
+  if constexpr (sizeof(R) == 4) {
+    // float faces: 1 - v^2 = 1/W^2, 1 - c^2 = (1 - vA^2)(1 - cs^2) with 1 - vA^2 = rho h/(rho h + b^2), and
+    // 1 - v^2 c^2 = (1 - c^2) + c^2/W^2, instead of differences whose rounding grows like W^2
+    one_v2 = iW * iW;
+    one_c2 = rhoh / (rhoh + b2) * (R(1) - cs2);
+    one_v2c2 = one_c2 + c2 * one_v2;
+  } else {
+    const R v2 = usq * iW * iW;
+    one_v2 = R(1) - v2;
+    one_c2 = R(1) - c2;
+    one_v2c2 = R(1) - v2 * c2;
+  }
+  R disc = one_v2 * (m.gamu[sym3(d, d)] * one_v2c2 - vd * vd * one_c2);
   disc = disc > R(0) ? disc : R(0);
-  const R pre = m.alpha / (R(1) - v2 * c2);
+  const R pre = m.alpha / one_v2c2;
   const R sq = sqrt(c2 * disc);
-  const R base = vd * (R(1) - c2);
+  const R base = vd * one_c2;
   s.lp = pre * (base + sq) - m.beta[d];
   s.lm = pre * (base - sq) - m.beta[d];
 }

@@ -17,6 +17,9 @@
 
 namespace grmhd {
 char* create_error_buffer();  // thread-local message buffer read by grmhd_last_error(NULL)
+// the checks and the kernel-side parameters of grmhd_create (grmhd_api.cu)
+bool valid_params(const grmhd_params* p, char* msg, size_t n);
+DevParams dev_params(const grmhd_params* p);
 }
 
 namespace {
@@ -61,20 +64,13 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
                                    void* stream) {
   if (!p || !P || !Ucur || !Unew || !status) return fail(GRMHD_E_INVALID, "a required pointer is NULL");
   if (g0 != 0.0 && !U0) return fail(GRMHD_E_INVALID, "U0 is NULL but g0 != 0");
+  if (!(g0 == g0) || !(g1 == g1) || !(beta == beta) || !(dt == dt)) return fail(GRMHD_E_INVALID, "NaN stage coefficient");
+  char why[200];
+  if (!valid_params(p, why, sizeof why)) return fail(GRMHD_E_INVALID, why);
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(GRMHD_E_INVALID, "nx, ny, nz must be >= 1");
   if (p->precision != GRMHD_FP64) return fail(GRMHD_E_INVALID, "only the all-FP64 form is available");
   if (p->ct != GRMHD_CT_FLUX) return fail(GRMHD_E_INVALID, "face-centred CT needs a context (grmhd_create)");
   if (p->scalar) return fail(GRMHD_E_INVALID, "the passive scalar needs a context (grmhd_create)");
-  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(GRMHD_E_INVALID, "nx, ny, nz must be >= 1");
-  const int need = p->recon >= GRMHD_RECON_WENO5Z_AOAH ? 3 : (p->recon == GRMHD_RECON_CONSTANT ? 1 : 2);
-  if (p->recon < 0 || p->recon > 4 || p->ng < need || p->ng > 16)
-    return fail(GRMHD_E_INVALID, "bad reconstruction or ghost count");
-  if ((p->metric != GRMHD_MINKOWSKI && p->metric != GRMHD_KERR_SCHILD) ||
-      (p->riemann != GRMHD_RIEMANN_LLF && p->riemann != GRMHD_RIEMANN_HLL) ||
-      (p->bc != GRMHD_BC_PERIODIC && p->bc != GRMHD_BC_FIXED))
-    return fail(GRMHD_E_INVALID, "bad metric, Riemann solver or boundary option");
-  if (!(p->dx[0] > 0.0 && p->dx[1] > 0.0 && p->dx[2] > 0.0) || !(p->gamma_eos > 1.0) || !(p->w_max > 1.0) ||
-      !(p->c2p_tol > 0.0) || p->c2p_max_iter < 1)
-    return fail(GRMHD_E_INVALID, "bad cell width, EOS index, Lorentz ceiling or con2prim tolerance");
   const double G = (double)(p->nx + 2 * p->ng) * (p->ny + 2 * p->ng) * (p->nz + 2 * p->ng);
   // scratch: scalars, three flux arrays [8][G] and the EMFs [3][G], all double
   const double need_bytes = (double)kScalarBytes + (3.0 * 8.0 + 3.0) * 8.0 * G;
@@ -85,23 +81,7 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
     return fail(GRMHD_E_INVALID, msg);
   }
 
-  DevParams d{};
-  d.nx = p->nx; d.ny = p->ny; d.nz = p->nz; d.ng = p->ng;
-  d.gx = p->nx + 2 * p->ng; d.gy = p->ny + 2 * p->ng; d.gz = p->nz + 2 * p->ng;
-  d.gsize = (long long)d.gx * d.gy * d.gz;
-  d.isize = (long long)p->nx * p->ny * p->nz;
-  for (int i = 0; i < 3; ++i) {
-    d.x0[i] = p->x0[i];
-    d.dx[i] = p->dx[i];
-    d.idx[i] = 1.0 / p->dx[i];
-  }
-  d.a = p->spin * p->mass; d.M = p->mass; d.gamma_eos = p->gamma_eos;
-  d.metric = p->metric; d.recon = p->recon; d.riemann = p->riemann; d.bc = p->bc;
-  d.rho_floor0 = p->rho_floor0; d.eps_floor0 = p->eps_floor0; d.floor_r_exp = p->floor_r_exp; d.w_max = p->w_max;
-  d.w_max2 = p->w_max * p->w_max;
-  d.v0sq_cap = 1.0 - 1.0 / (p->w_max * p->w_max);
-  d.c2p_tol = p->c2p_tol; d.c2p_max_iter = p->c2p_max_iter; d.cfl = p->cfl; d.weno_eps = p->weno_eps;
-  for (int i = 0; i < 3; ++i) d.shift[i] = p->metric == GRMHD_MINKOWSKI ? p->shift[i] : 0.0;
+  const DevParams d = dev_params(p);
 
   void* base = nullptr;
   cudaError_t e = scratch_address(&base);
@@ -117,11 +97,15 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
   const cudaStream_t s = (cudaStream_t)stream;
   const FormLaunchers& L = fp64_launchers();
   const bool auto_dt = !(dt > 0.0);
+  // as in grmhd_stage: the CFL step is taken on a first stage (g0 == 0); a later stage of the step with
+  // dt <= 0 reuses the step the last first-stage call left in the array
+  const bool track = auto_dt && g0 == 0.0;
   // the array keeps the previous call's contents: clear the reductions this call accumulates into
-  e = cudaMemsetAsync(ms, 0, kScalarBytes, s);
+  e = cudaMemsetAsync(stats, 0, kScalarBytes - 8 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess && track) e = cudaMemsetAsync(ms, 0, 3 * sizeof(unsigned long long), s);
   if (e == cudaSuccess && p->bc == GRMHD_BC_PERIODIC) e = L.ghost(d, P, s);
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = L.flux(d, P, F[k], ms, k, auto_dt ? 1 : 0, s);
-  if (e == cudaSuccess && auto_dt) e = launch_finalize_dt(ms, dt_dev, d, s);
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = L.flux(d, P, F[k], ms, k, track ? 1 : 0, s);
+  if (e == cudaSuccess && track) e = launch_finalize_dt(ms, dt_dev, d, s);
   if (e == cudaSuccess) e = L.emf(d, F[0], F[1], F[2], E, s);
   if (e == cudaSuccess) {
     StageArgs a{};

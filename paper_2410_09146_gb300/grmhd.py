@@ -115,6 +115,8 @@ def lib():
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
         L.grmhd_p2c.argtypes = [vp, ctypes.c_longlong, vp, vp]
         L.grmhd_c2p_guess.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
+        L.grmhd_max_speed.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.grmhd_fp_peaks.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.grmhd_last_error.argtypes = [vp]
         L.grmhd_last_error.restype = ctypes.c_char_p
         L.grmhd_destroy.argtypes = [vp]
@@ -288,6 +290,21 @@ def grmhd_get_timing(ctx: int):
     n = ctypes.c_int(0)
     _check(lib().grmhd_get_timing(ctx, ms, ctypes.byref(n)), ctx)
     return dict(zip(KERNEL_GROUPS, list(ms))), n.value
+
+
+def grmhd_max_speed(ctx: int):
+    """Largest |lambda| per direction over the interior faces of the last CFL stage (see include/grmhd.h)."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().grmhd_max_speed(ctypes.c_void_p(ctx), out), ctx)
+    return np.array(out[:])
+
+
+def grmhd_fp_peaks(sink_ptr: int, stream_ptr: int = 0):
+    """(FP64, FP32) dense FMA rates of the current device in TFLOP/s (see include/grmhd.h)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().grmhd_fp_peaks(ctypes.c_void_p(sink_ptr), ctypes.c_void_p(stream_ptr or None), ctypes.byref(a),
+                                ctypes.byref(b)))
+    return a.value, b.value
 
 
 def grmhd_stage_noalloc(p: grmhd_params, P_ptr: int, U0_ptr: int, Ucur_ptr: int, Unew_ptr: int, status_ptr: int,
@@ -509,6 +526,9 @@ class Context:
 
     def dt(self):
         return float(self.get(GRMHD_GET_DT)[0])
+
+    def max_speed(self):
+        return grmhd_max_speed(self.ctx)
 
     def face_b(self):
         return self.get(GRMHD_GET_FACE_B)

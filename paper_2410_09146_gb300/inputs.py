@@ -65,6 +65,8 @@ class Setup:
     ct: str = "flux"                   # "flux" (Toth flux-CT, cell field) | "face" (face-centred upwind CT)
     shift: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # Minkowski: constant shift (boosted coordinates)
     scalar: bool = False               # also evolve one passive scalar (the electron fraction, say)
+    # a tile of a larger block (kerr_schild_tile): (parent Setup, offset of the tile's first interior cell)
+    tile_of: object = dataclasses.field(default=None, repr=False, compare=False)
 
     @property
     def ghosted(self):
@@ -146,6 +148,79 @@ def _to_uniform(g):
     return np.clip(0.5 * (1.0 + erf(g / math.sqrt(2.0))), 0.0, 1.0)
 
 
+def _logu(field, lo, hi, grid):
+    u = _to_uniform(field(*grid))
+    return 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * u)
+
+
+def _ks_fields(seed, kmax):
+    rng = np.random.default_rng(seed)
+    f_rho, f_w, f_sig = (_SmoothField(rng, kmax=kmax) for _ in range(3))
+    f_dir = [_SmoothField(rng, kmax=kmax) for _ in range(3)]
+    f_a = [_SmoothField(rng, kmax=kmax) for _ in range(3)]
+    return f_rho, f_w, f_sig, f_dir, f_a
+
+
+def _ks_coords(s: Setup):
+    """Unit-cube coordinates of the ghosted cell centres and of the cell corners of block s."""
+    ng = s.ng
+    span = [s.n[d] * s.dx[d] for d in range(3)]
+    xc = [(s.cell_centres(d) - s.x0[d]) / span[d] for d in range(3)]
+    xn = [(s.x0[d] + np.arange(-ng, s.n[d] + ng + 1) * s.dx[d] - s.x0[d]) / span[d] for d in range(3)]
+    return xc, xn
+
+
+def _ks_unscaled_b(fields, xn, dx, rho_range, w_range, sigma_range):
+    """Face and cell-centred curl of the node-centred potential, before the global scale."""
+    f_rho, f_w, f_sig, _, f_a = fields
+    rho_n = _logu(f_rho, *rho_range, xn)
+    W_n = _logu(f_w, *w_range, xn)
+    sig_n = _logu(f_sig, *sigma_range, xn)
+    amp = W_n * np.sqrt(sig_n * rho_n)
+    del rho_n, W_n, sig_n
+    A = [amp * f(*xn) for f in f_a]
+    del amp
+    Bface = _face_curl(A, dx)
+    return Bface, np.stack([_mu(Bface[c], _AX_OF[c]) for c in range(3)])
+
+
+_SCALE_CACHE = {}
+
+
+def _ks_b_scale(s: Setup, seed, rho_range, w_range, sigma_range, kmax, slab=16):
+    """The global field scale of block s (the median of |B|^2/(rho W^2) over its ghosted cells set to the
+    median target magnetisation), evaluated over z-slabs of the block so that large blocks fit in memory;
+    the values equal those of the whole-block evaluation."""
+    key = (s.n, s.ng, s.x0, s.dx, seed, tuple(rho_range), tuple(w_range), tuple(sigma_range), kmax)
+    if key in _SCALE_CACHE:
+        return _SCALE_CACHE[key]
+    fields = _ks_fields(seed, kmax)
+    f_rho, f_w = fields[0], fields[1]
+    xc, xn = _ks_coords(s)
+    nzg = len(xc[2])
+    proxy = []
+    for k0 in range(0, nzg, slab):
+        k1 = min(k0 + slab, nzg)
+        rho = _logu(f_rho, *rho_range, [xc[0], xc[1], xc[2][k0:k1]])
+        W = _logu(f_w, *w_range, [xc[0], xc[1], xc[2][k0:k1]])
+        _, B = _ks_unscaled_b(fields, [xn[0], xn[1], xn[2][k0:k1 + 1]], s.dx, rho_range, w_range, sigma_range)
+        proxy.append((np.sum(B ** 2, axis=0) / (rho * W * W)).ravel())
+    target = math.sqrt(sigma_range[0] * sigma_range[1])
+    scale = math.sqrt(target / float(np.median(np.concatenate(proxy))))
+    _SCALE_CACHE[key] = scale
+    return scale
+
+
+def kerr_schild_tile(parent: Setup, offset, n) -> Setup:
+    """The set-up of an n[0] x n[1] x n[2] tile of block `parent` whose first interior cell is the parent's
+    interior cell `offset` (same cell widths, ghosts and options): kerr_schild_random_prims(tile, ...,
+    parent=parent) gives exactly the parent's primitives on the tile's cells, ghosts included."""
+    if any(o < 0 or o + k > N for o, k, N in zip(offset, n, parent.n)):
+        raise ValueError("the tile must lie inside the parent's interior")
+    x0 = tuple(parent.x0[d] + offset[d] * parent.dx[d] for d in range(3))
+    return dataclasses.replace(parent, n=tuple(n), x0=x0, tile_of=(parent, tuple(offset)))
+
+
 def kerr_schild_random_prims(s: Setup, seed: int = 1, rho_range=(1e-6, 1.0), w_range=(1.0, 10.0),
                              sigma_range=(1e-2, 50.0), p_coef: float = 0.01, kmax: int = 3,
                              faces: bool = False):
@@ -156,28 +231,24 @@ def kerr_schild_random_prims(s: Setup, seed: int = 1, rho_range=(1e-6, 1.0), w_r
     ``Bf`` [3][gz][gy][gx] (entry (i, j, k) of component d on the lower d-face of ghosted cell (i, j, k)):
     the same potential's curl on the faces, with the same scale, so that the mean of a cell's two
     d-faces is its B^d in ``P``. Used as the face-centred field sqrt(gamma) B^d.
+
+    For a tile made by ``kerr_schild_tile`` the fields are those of the parent block (its unit cube and
+    its global field scale): the result is the parent's primitives on the tile's ghosted cells.
     """
-    rng = np.random.default_rng(seed)
-    f_rho, f_w, f_sig = (_SmoothField(rng, kmax=kmax) for _ in range(3))
-    f_dir = [_SmoothField(rng, kmax=kmax) for _ in range(3)]
-    f_a = [_SmoothField(rng, kmax=kmax) for _ in range(3)]
-    nx, ny, nz = s.n
-    ng = s.ng
-    span = [s.n[d] * s.dx[d] for d in range(3)]
-
-    def unit(d, x):
-        return (x - s.x0[d]) / span[d]
-
-    xc = [unit(d, s.cell_centres(d)) for d in range(3)]
-    xn = [unit(d, s.x0[d] + np.arange(-ng, s.n[d] + ng + 1) * s.dx[d]) for d in range(3)]
-
-    def logu(field, lo, hi, grid):
-        u = _to_uniform(field(*grid))
-        return 10.0 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * u)
+    fields = _ks_fields(seed, kmax)
+    f_rho, f_w, f_sig, f_dir, f_a = fields
+    tile = s.tile_of
+    if tile is None:
+        xc, xn = _ks_coords(s)
+    else:
+        parent, off = tile
+        pxc, pxn = _ks_coords(parent)
+        xc = [pxc[d][off[d]:off[d] + s.n[d] + 2 * s.ng] for d in range(3)]
+        xn = [pxn[d][off[d]:off[d] + s.n[d] + 2 * s.ng + 1] for d in range(3)]
 
     P = np.empty(s.prim_shape())
-    rho = logu(f_rho, *rho_range, xc)
-    W = logu(f_w, *w_range, xc)
+    rho = _logu(f_rho, *rho_range, xc)
+    W = _logu(f_w, *w_range, xc)
     P[0] = rho
     P[4] = p_coef * rho ** (5.0 / 3.0) / (s.gamma_eos - 1.0)
     dirs = np.stack([f(*xc) for f in f_dir])
@@ -186,19 +257,14 @@ def kerr_schild_random_prims(s: Setup, seed: int = 1, rho_range=(1e-6, 1.0), w_r
     del dirs
 
     # Node-centred vector potential with amplitude W sqrt(sigma_target rho) evaluated at the nodes.
-    rho_n = logu(f_rho, *rho_range, xn)
-    W_n = logu(f_w, *w_range, xn)
-    sig_n = logu(f_sig, *sigma_range, xn)
-    amp = W_n * np.sqrt(sig_n * rho_n)
-    del rho_n, W_n, sig_n
-    A = [amp * f(*xn) for f in f_a]
-    del amp
-    Bface = _face_curl(A, s.dx)
-    B = np.stack([_mu(Bface[c], _AX_OF[c]) for c in range(3)])
+    Bface, B = _ks_unscaled_b(fields, xn, s.dx, rho_range, w_range, sigma_range)
     # One global scale so the median of |B|^2 / (rho W^2) matches the median target sigma.
-    proxy = np.sum(B ** 2, axis=0) / (rho * W * W)
-    target = math.sqrt(sigma_range[0] * sigma_range[1])
-    scale = math.sqrt(target / float(np.median(proxy)))
+    if tile is None:
+        proxy = np.sum(B ** 2, axis=0) / (rho * W * W)
+        target = math.sqrt(sigma_range[0] * sigma_range[1])
+        scale = math.sqrt(target / float(np.median(proxy)))
+    else:
+        scale = _ks_b_scale(tile[0], seed, rho_range, w_range, sigma_range, kmax)
     P[5:8] = B * scale
     if not faces:
         return P

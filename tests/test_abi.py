@@ -82,3 +82,27 @@ def test_struct_layout_matches_header(tmp_path):
     vals = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert vals[0] == ctypes.sizeof(G.grmhd_params)
     assert vals[1:] == [getattr(G.grmhd_params, n).offset for n in names]
+
+
+def test_noalloc_refusals_on_the_host(lib):
+    """grmhd_stage_noalloc checks its parameters as grmhd_create does, and its block size against the fixed
+    scratch, before any device work (dummy pointers: nothing is dereferenced)."""
+    import dataclasses
+    vp = ctypes.c_void_p
+    d = vp(256)
+
+    def call(p, g0=0.0, g1=1.0, beta=1.0, dt=0.0):
+        return lib.grmhd_stage_noalloc(ctypes.byref(p), d, d, d, d, d, g0, g1, beta, dt, None)
+
+    ks = I.kerr_schild_setup(8)
+    bad_mass = G.params(dataclasses.replace(ks, mass=0.0))
+    assert call(bad_mass) == G.GRMHD_E_INVALID and b"mass" in lib.grmhd_last_error(None)
+    flat = I.linear_wave_setup(8)
+    assert call(G.params(dataclasses.replace(flat, shift=(0.8, 0.7, 0.0)))) == G.GRMHD_E_INVALID
+    assert b"shift" in lib.grmhd_last_error(None)
+    assert call(G.params(flat), beta=float("nan")) == G.GRMHD_E_INVALID
+    assert b"NaN" in lib.grmhd_last_error(None)
+    assert call(G.params(dataclasses.replace(flat, precision="mixed"))) == G.GRMHD_E_INVALID
+    # 9 x 10 x 863 = 77,670 ghosted cells: one more than the 16 MiB scratch holds
+    assert call(G.params(I.linear_wave_setup(1, 2, 855))) == G.GRMHD_E_INVALID
+    assert b"77669" in lib.grmhd_last_error(None)

@@ -50,7 +50,6 @@ def test_noalloc_matches_context_entry_point(env):
         ref.set_prims(P.copy())
         U0 = ref.cons()
         ref.stage(0.0, 1.0, 1.0, 0.0)
-        dt = ref.dt()
         U1_ref, P1_ref, st1_ref = ref.cons(), ref.prims(), ref.status()
         ref.stage(0.5, 0.5, 0.5, 0.0)
         U2_ref, P2_ref, st2_ref = ref.cons(), ref.prims(), ref.status()
@@ -67,9 +66,10 @@ def test_noalloc_matches_context_entry_point(env):
         torch.cuda.synchronize()
         assert rel_err_cons(U1d.cpu().numpy(), U1_ref).max() <= 1e-12
         assert np.array_equal(st.cpu().numpy(), st1_ref)
-        # second call: reuses the first call's scratch array
+        # second call, also with dt <= 0: it reuses the time step the first call left in the scratch array,
+        # as grmhd_rk2_step's second stage reuses its first stage's
         G.grmhd_stage_noalloc(p, Pd.data_ptr(), U0d.data_ptr(), U1d.data_ptr(), U2d.data_ptr(), st.data_ptr(), 0.5, 0.5,
-                              0.5, dt, stream)
+                              0.5, 0.0, stream)
         torch.cuda.synchronize()
         assert rel_err_cons(U2d.cpu().numpy(), U2_ref).max() <= 1e-12
         assert np.array_equal(st.cpu().numpy(), st2_ref)
@@ -78,6 +78,35 @@ def test_noalloc_matches_context_entry_point(env):
         Pn = Pd.cpu().numpy()
         scale = np.maximum(np.abs(P2_ref[inner]), 1e-3 * np.abs(P2_ref[inner]).max(axis=(1, 2, 3), keepdims=True))
         assert (np.abs(Pn[inner] - P2_ref[inner]) / scale).max() <= 1e-12
+
+
+def test_noalloc_block_at_the_scratch_limit(env):
+    """The largest block the fixed scratch holds with 4 ghosts (13 x 29 x 206 = 77,662 ghosted cells, the limit
+    being 77,669) runs and matches the context entry point; one ghosted cell more than the limit is refused."""
+    from tests.parity import rel_err_cons
+    torch, G = env
+    gw = json.load(open(GOLDEN))
+    s = I.linear_wave_setup(5, 21, 198, recon="plm_mc", riemann="llf")
+    P = I.linear_wave_prims(s, gw["background_prims"], gw["eigvec_prims"], amplitude=1e-3)
+    ref = G.Context(s)
+    ref.set_prims(P.copy())
+    U0 = ref.cons()
+    ref.stage(0.0, 1.0, 1.0, 0.0)
+    U1_ref = ref.cons()
+    p = G.params(s)
+    Pd = torch.tensor(P, device="cuda")
+    U0d = torch.tensor(U0, device="cuda")
+    U1d = torch.empty_like(U0d)
+    st = torch.empty(U0.shape[1:], dtype=torch.uint8, device="cuda")
+    G.grmhd_stage_noalloc(p, Pd.data_ptr(), 0, U0d.data_ptr(), U1d.data_ptr(), st.data_ptr(), 0.0, 1.0, 1.0, 0.0,
+                          torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert rel_err_cons(U1d.cpu().numpy(), U1_ref).max() <= 1e-12
+    assert np.array_equal(st.cpu().numpy(), ref.status())
+    over = G.params(I.linear_wave_setup(1, 2, 855))  # 9 x 10 x 863 = 77,670 ghosted cells
+    with pytest.raises(G.GrmhdError, match="77669"):
+        G.grmhd_stage_noalloc(over, Pd.data_ptr(), 0, U0d.data_ptr(), U1d.data_ptr(), st.data_ptr(), 0.0, 1.0, 1.0,
+                              0.0, 0)
 
 
 def test_noalloc_rejects_blocks_beyond_its_scratch(env):

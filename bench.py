@@ -122,6 +122,11 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
+def l1_rel(a, b):
+    """Per-variable L1 distance sum |a - b| / sum |b| over the leading axis."""
+    return np.array([np.abs(a[v] - b[v]).sum() / max(np.abs(b[v]).sum(), 1e-300) for v in range(a.shape[0])])
+
+
 def measured_peaks():
     try:
         return json.load(open(PEAKS_FILE))
@@ -189,6 +194,7 @@ def run_ours(args):
         return float(t.item())
 
     n = args.n
+    fp_peaks = live_fp_peaks(G)
     s_mix, seed = workload(n, "mixed", rank)
     P, Bf = I.kerr_schild_random_prims(s_mix, seed=seed, faces=True)
     cells = n ** 3
@@ -252,7 +258,6 @@ def run_ours(args):
     cm = G.Context(s_mix)
     cm.set_prims(P)
     cm.rk2_step(0.0)
-    from tests.parity import l1_rel
     ng = s_mix.ng
     inner = (slice(None),) + (slice(ng, -ng),) * 3
     l1u = l1_rel(cm.cons(), U64)
@@ -281,7 +286,9 @@ def run_ours(args):
     per_kernel = {k: v / max(kst, 1) for k, v in kt.items()}
     dom = max(per_kernel, key=per_kernel.get)
     peaks = measured_peaks()
-    roof = roofline(dom, per_kernel[dom], n, s_mix, stats, peaks)
+    roof = roofline(dom, per_kernel[dom], n, stats, fp_peaks, per_stage, peaks)
+    roof["fp_peaks_tflops"] = {"fp64": fp_peaks[0], "fp32": fp_peaks[1], "how": "grmhd_fp_peaks on this GPU, "
+                               "before the timed region"}
     G_cells = (n + 2 * s_mix.ng) ** 3
     h2d = Ph.numel() * Ph.element_size()  # the float primitives copied each way per step
     out = {
@@ -317,7 +324,8 @@ def run_ours(args):
     if guess is not None:
         out["c2p_guess"] = guess
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(n_sample=80, n_stages=1)
+        out["cpu_baseline"], ref = cpu_baseline(n)
+        out["l1_mixed_vs_oracle"] = l1_vs_oracle(G, ref)
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
@@ -593,31 +601,53 @@ UPDATE_DRAM_BYTES_PER_CELL = 373.4
 UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 152 + 64 + 32 + 1
 FLUX_FP32_FLOP_PER_FACE = 2342.0
 FLUX_DRAM_BYTES_PER_FACE = 38.5
-FP64_PEAK_TFLOPS = 1.008   # measured DFMA rate of this GB300 (probe_fp_throughput.cu, summary under profiles/)
-FP32_PEAK_TFLOPS = 74.5    # measured FFMA rate
+# Algorithmic bytes per interior zone per stage of the fused-ideal mixed form (primitives in float, state in
+# double, metric computed, perfect stencil reuse; the mean of the two stages of an RK2 step at 256^3, where
+# the primitive read over the ghosted block is 1.097 zones' worth): 32 f_g (P read) + 64 (U read) + 32
+# (U0 read, second stage only) + 64 (U written) + 32 (P written) + 1 (status) bytes.
+STAGE_ALGO_BYTES_PER_ZONE = 228.5
 
 
-def roofline(dom, ms, n, s, stats, peaks):
-    """Roofline of the dominant kernel group. The update kernel (con2prim in double) is bound by the
-    FP64 pipe, the flux kernels by the FP32 pipe; neither is HBM-bound (DRAM below 2% of peak)."""
+def live_fp_peaks(G):
+    """(FP64, FP32) dense FMA rates of this GPU in TFLOP/s, measured now by the library (grmhd_fp_peaks)."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    f64, f32 = G.grmhd_fp_peaks(sink.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return f64, f32
+
+
+def roofline(dom, ms, n, stats, fp_peaks, ms_stage, peaks):
+    """Roofline of the dominant kernel group, and the whole stage against HBM. The update kernel (con2prim
+    in double) is bound by the FP64 pipe, the flux kernels by the FP32 pipe; neither is HBM-bound."""
     cells = n ** 3
+    f64, f32 = fp_peaks
+    hbm = peaks.get("hbm_gbs")
+    stage_gbs = STAGE_ALGO_BYTES_PER_ZONE * cells / (ms_stage / 1e3) / 1e9
+    stage_hbm = {"achieved": stage_gbs, "peak": hbm, "unit": "GB/s", "frac": stage_gbs / hbm if hbm else None,
+                 "bytes_per_zone": STAGE_ALGO_BYTES_PER_ZONE,
+                 "note": "whole stage: algorithmic bytes per zone x zones / stage time; peak = MEASURED_PEAKS.json "
+                         "hbm_gbs (copy, read + write)"}
     if dom == "update":
         flops = UPDATE_FP64_FLOP_PER_CELL * cells
         achieved = flops / (ms / 1e3) / 1e12
-        return {"kernel": "k_update", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": UPDATE_DRAM_BYTES_PER_CELL * cells, "ms_per_launch": ms,
+        return {"kernel": "k_update", "bound": "alu", "achieved": achieved, "peak": f64, "unit": "TFLOP/s",
+                "frac": achieved / f64, "traffic": UPDATE_DRAM_BYTES_PER_CELL * cells, "ms_per_launch": ms,
                 "work_per_unit": f"{UPDATE_FP64_FLOP_PER_CELL} FP64 flop/cell (ncu, 96^3)",
                 "algorithmic_bytes_per_cell": UPDATE_ALGO_BYTES_PER_CELL,
+                "hbm_frac": UPDATE_ALGO_BYTES_PER_CELL * cells / (ms / 1e3) / 1e9 / hbm if hbm else None,
+                "stage_hbm": stage_hbm,
                 "note": "FP64 pipe (issue-bound: one warp FP64 instruction per ~20 SM cycles whatever its active "
-                        "lanes); peak = measured DFMA rate of this GB300 (MEASURED_PEAKS.json has no FP64 figure); "
-                        "traffic scaled from the 96^3 ncu capture by cell count"}
+                        "lanes); peak = the DFMA rate measured live on this GPU by grmhd_fp_peaks "
+                        "(MEASURED_PEAKS.json has no FP64 figure); traffic scaled from the 96^3 ncu capture by "
+                        "cell count"}
     faces = 3 * (n + 1) * (n + 2) ** 2 / 3.0
     flops = FLUX_FP32_FLOP_PER_FACE * faces
     achieved = flops / (ms / 1e3) / 1e12
-    return {"kernel": f"k_flux_cc ({dom})", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": FLUX_DRAM_BYTES_PER_FACE * faces,
-            "ms_per_launch": ms, "note": "FP32 pipe; peak = measured FFMA rate"}
+    return {"kernel": f"k_flux_cc ({dom})", "bound": "alu", "achieved": achieved, "peak": f32,
+            "unit": "TFLOP/s", "frac": achieved / f32, "traffic": FLUX_DRAM_BYTES_PER_FACE * faces,
+            "ms_per_launch": ms, "stage_hbm": stage_hbm,
+            "note": "FP32 pipe; peak = the FFMA rate measured live on this GPU by grmhd_fp_peaks"}
 
 
 # ----------------------------------------------------------------------------- oracle baselines
@@ -636,17 +666,52 @@ def _oracle_stage_worker(args):
     return n ** 3, time.perf_counter() - t
 
 
-def cpu_baseline(n_sample=64, n_stages=1):
-    """The oracle as it stands, serial on one host core, on a bounded sample of the workload."""
+TILES = ((96, 96, 96), (0, 0, 0))  # 64^3 tiles of the workload: the central one and the one next to the hole
+
+
+def cpu_baseline(n, tile=64):
+    """The oracle as it stands, serial on one host core, on a bounded sample of the workload: one RK2 step of
+    each 64^3 tile in TILES of the n^3 block (the block's own primitives, ghosts included). Returns the
+    baseline entry and the oracle's states, which the mixed form is then compared with."""
     import oracle
+    from paper_2410_09146_gb300 import inputs as I
     oracle.build()
-    zones, secs = 0, 0.0
-    for k in range(n_stages):
-        z, t = _oracle_stage_worker((n_sample, 2 + k))
-        zones += z
-        secs += t
-    return {"value": zones / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_stages} stage(s) of a {n_sample}^3 block of the same workload (FP64 oracle, serial)"}
+    parent = I.kerr_schild_setup(n, recon="weno5z_aoah", riemann="hll")
+    zones, secs, ref = 0, 0.0, []
+    for off in TILES:
+        if any(o + tile > n for o in off):
+            continue
+        s = I.kerr_schild_tile(parent, off, (tile,) * 3)
+        P = I.kerr_schild_random_prims(s, seed=2)
+        p = oracle.params(s)
+        Po = P.copy()
+        t0 = time.perf_counter()
+        Uo, sto, _ = oracle.rk2_step(p, Po, oracle.prim2con_grid(p, Po.copy()), 0.0)
+        secs += time.perf_counter() - t0
+        zones += 2 * tile ** 3
+        ref.append((s, P, Uo, Po))
+    return ({"value": zones / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"one RK2 step (two stages) of each of {len(ref)} {tile}^3 tiles {TILES[:len(ref)]} of the "
+                       f"{n}^3 workload block (FP64 oracle, serial, one core)"}, ref)
+
+
+def l1_vs_oracle(G, ref):
+    """The mixed form's per-variable L1 against the oracle after the same RK2 step of the sampled tiles."""
+    import dataclasses
+    out = []
+    for s, P, Uo, Po in ref:
+        c = G.Context(dataclasses.replace(s, precision="mixed"))
+        c.set_prims(P.copy())
+        c.rk2_step(0.0)
+        ng = s.ng
+        inner = (slice(None),) + (slice(ng, -ng),) * 3
+        U, Pm = c.cons(), c.prims()[inner]
+        del c
+        e_scale = np.abs(Uo[4] + Uo[0]).sum()  # rho eps on the scale con2prim recovers it from (sqrt(gamma) ~ 1)
+        out.append({"tile": list(s.tile_of[1]), "U": [float(x) for x in l1_rel(U, Uo)],
+                    "P": [float(x) for x in l1_rel(Pm, Po[inner])],
+                    "rho_eps_over_tau_plus_D": float(np.abs(Pm[4] - Po[inner][4]).sum() / e_scale)})
+    return {"after": "one RK2 step", "tiles": out, "max_U": max(max(o["U"]) for o in out) if out else None}
 
 
 def run_reference(args):

@@ -650,35 +650,6 @@ __device__ __forceinline__ C2PEval<T> c2p_master(const C2PIn<T>& c, T mu_v) {
   return e;
 }
 
-// Master-function value and intermediates at mu without derivatives, in double: the operations of the value
-// part of c2p_master, W from a reciprocal square root (derivatives cost about as much again; the mixed form
-// takes them in float).
-__device__ __forceinline__ C2PEval<double> c2p_master_f(const C2PIn<double>& c, double mu) {
-  const double x = 1.0 / (1.0 + c.b2 * mu);
-  const double rb = c.r2 * (x * x) + c.rb2 * (mu * x * (1.0 + x));
-  const double qbar = (c.q - 0.5 * c.b2) - (0.5 * (c.b2 * c.r2 - c.rb2)) * (mu * mu * x * x);
-  double vh2 = mu * mu * rb;
-  if (vh2 > c.v0sq) vh2 = c.v0sq;
-  const double W = rsqrt(1.0 - vh2);  // one reciprocal square root instead of a square root and a division
-  const double iW = (1.0 - vh2) * W;
-  double eps = W * (qbar - mu * rb) + vh2 * W * W * (1.0 / (1.0 + W));
-  if (eps < 0.0) eps = 0.0;
-  const double onepe = 1.0 + eps;
-  const double a = c.gm1 * eps * (1.0 / onepe);
-  const double nuA = (1.0 + a) * onepe * iW;
-  const double nuB = (1.0 + a) * (1.0 + qbar - mu * rb);
-  const double nu = nuA >= nuB ? nuA : nuB;
-  C2PEval<double> e;
-  e.f = mu - 1.0 / (nu + mu * rb);
-  e.df = 0.0;
-  e.x = x;
-  e.W = W;
-  e.rho = c.D * iW;
-  e.eps = eps;
-  e.dx = e.dW = e.drho = e.deps = 0.0;
-  return e;
-}
-
 // Master-function intermediates without the derivative (final evaluation at the root).
 template <class T>
 __device__ __forceinline__ C2PEval<T> c2p_master_value(const C2PIn<T>& c, T mu) {
@@ -739,26 +710,6 @@ __device__ __forceinline__ double c2p_mu_plus_fast(const C2PIn<double>& c) {
   cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
   const float muf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
   return c2p_mu_plus<double>(c, (double)muf, 1e-15, 12);
-}
-
-// mu_+ in double from an accurate float value (relative error ~1e-7): two Newton steps on
-// g(mu) = mu^2 (1 + rbar^2(mu)) - 1 (quadratic convergence: 1e-7 -> 1e-14 -> rounding). A fixed step count,
-// so that the lanes of a warp stay together. mupf >= 1 is the bound mu_+ = 1 itself.
-__device__ __forceinline__ double c2p_mu_plus_polish(const C2PIn<double>& c, float mupf) {
-  double m1 = (double)mupf;
-  if (mupf < 1.f) {
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const double xx = 1.0 / (1.0 + m1 * c.b2);
-      const double dx = -c.b2 * xx * xx;
-      const double rb = xx * xx * c.r2 + m1 * xx * (1.0 + xx) * c.rb2;
-      const double drb = 2.0 * xx * dx * c.r2 + c.rb2 * (xx * (1.0 + xx) + m1 * dx * (1.0 + 2.0 * xx));
-      const double g = m1 * m1 * (1.0 + rb) - 1.0;
-      const double dg = 2.0 * m1 * (1.0 + rb) + m1 * m1 * drb;
-      m1 -= g / dg;
-    }
-  }
-  return m1;
 }
 
 // Bracketed Newton iteration on [0, mup] from mu (double or float). Returns 0 when converged (the
@@ -927,88 +878,191 @@ __device__ __forceinline__ int con2prim_resume(const DevParams& p, const Metric<
   return st;
 }
 
-// Mixed-form con2prim: the same root, iterated in float to a relative step of 2e-6, then one double
-// Newton step; double iteration only when the float phase fails or the double step is not small.
-enum { C2P_DEFERRED = 256 };  // returned by con2prim_mixed(defer = true): the cell needs the double iteration
+// Returned by con2prim_mixed_f(defer = true): the cell needs the double iteration of deferred_cell.
+enum { C2P_DEFERRED = 256 };
 
-template <class R>
-__device__ __forceinline__ int con2prim_mixed(const DevParams& p, const Metric<R>& m, const double Uc[NV],
-                                              double mu_guess, double Pout[NV], int& iters, bool defer = false,
-                                              double* defer_mu = nullptr) {
+// Mixed form of the stage's con2prim (a6), from the densitized conserved state, with the primitives returned
+// in float, the storage type of the mixed form. Only what the solve's conditioning needs is double: the
+// master function's invariants q, r^2, b^2, (r.b)^2 and the velocity bound (from the double state and the
+// cell's double metric), mu_+ when the float root sits on it (one double Newton step), the master function at
+// the float root and the specific internal energy there. Everything the float primitives are formed from
+// to float accuracy anyway (x, the Newton step, the output velocities, density and field) is float.
+// Two identities (exact in real arithmetic, with W = 1/sqrt(1 - v^2) and W (1 + qbar - mu rbar^2) = 1 + eps)
+// remove the master function's divisions besides x:
+//   eps = W (qbar - mu rbar^2) + v^2 W^2/(1 + W) = W (1 + qbar - mu rbar^2) - 1,
+//   nu = max((1 + a)(1 + eps)/W, (1 + a)(1 + qbar - mu rbar^2)) = (1 + Gamma eps)/W  (eps clamped at 0),
+// and the root is taken on K f = mu K - 1 (K = nu + mu rbar^2 > 0, the same root), whose Newton step at the
+// root equals f's. Returns the status bits of the solve (floors are applied by the caller) or C2P_DEFERRED
+// when the double step from the float root is not small (defer == true; mu_r then holds the double iterate
+// the double pass resumes from); without defer such a cell takes the full double iteration here.
+__device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric<double>& m, double isg,
+                                                const double Un[NV], float mu_guess, bool defer, float Pf[NV],
+                                                int& iters, double& mu_r) {
   // Lanes entering together; each of them reaches the __syncwarp below exactly once (no return before it).
   const unsigned lanes = __activemask();
   iters = 0;
+  mu_r = 0.0;
+  bool finite = true;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) finite = finite && isfinite(Un[q]);
+  const bool bad = !finite || !(Un[0] > 0.0);
   C2PIn<double> c;
-  double ru[3], bu[3];
-  const bool bad = c2p_setup<R>(p, m, Uc, c, ru, bu) != 0;
+  C2PIn<float> cf;
+  float ruf[3], buf[3];
   float mupf = 1.f, muf = 0.f;
   int itf = 0, stf = ST_NOT_CONVERGED;
-  C2PIn<float> cf;
   if (!bad) {
+    // q = tau/D and r_i = S_i/D are ratios of densitized values; b^i = B^i/sqrt(D) takes sqrt(gamma) once
+    const double D = Un[0] * isg;
+    const double isD = rsqrt(D);
+    const double s = isg * isD * isD;
+    const double rl[3] = {Un[1] * s, Un[2] * s, Un[3] * s};
+    const double tb = isg * isD;
+    const double bu[3] = {Un[5] * tb, Un[6] * tb, Un[7] * tb};
+    double ru[3], bl[3];
+    lower3(m.gamu, rl, ru);
+    lower3(m.gam, bu, bl);
+    c.D = D;
+    c.q = Un[4] * s;
+    c.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
+    c.b2 = bu[0] * bl[0] + bu[1] * bl[1] + bu[2] * bl[2];
+    c.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
+    c.rb2 = c.rb * c.rb;
+    c.gm1 = p.gamma_eos - 1.0;
+    c.v0sq = fmin(c.r2 / (1.0 + c.r2), p.v0sq_cap);
     cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
     cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      ruf[i] = (float)ru[i];
+      buf[i] = (float)bu[i];
+    }
     mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
-    muf = (float)mu_guess;
+    muf = mu_guess;
     stf = c2p_newton<float>(cf, mupf, muf, 2e-6f, 24, itf, false);
   }
   // The float iterations end at different counts in different lanes: reconverge, so that the double part
   // below runs once for the warp rather than once per group of lanes (FP64 issue is per warp instruction).
   __syncwarp(lanes);
   if (bad) {
-    c2p_bad_output(Uc, Pout);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Pf[q] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Pf[5 + k] = isfinite(Un[5 + k]) ? (float)(Un[5 + k] * isg) : 0.f;
     return ST_BAD_INPUT;
   }
   iters = itf;
-  double mu = (double)muf;
   bool done = false;
-  C2PEval<double> ev;  // the intermediates at the accepted root
-  if (stf == 0 && isfinite(mu) && mu > 0.0) {
-    // One double evaluation of the master function for every cell, so that a warp runs it once: at the
-    // float root, or, when that sits on the bracket end (cold limit), at mu_+ settled in double. A cold
-    // cell whose f(mu_+) <= 0 has its root on mu_+; otherwise, as for every other cell, the double Newton
-    // step from the evaluation point must be small.
+  double mu = (double)muf, eps = 0.0;
+  float Wf = 1.f, xf = 1.f;  // the intermediates at the accepted root
+  if (stf == 0 && isfinite(muf) && muf > 0.f) {
     const bool cold = muf >= mupf;
     double mue = mu;
     if (__any_sync(__activemask(), cold)) {  // the same instructions for every lane of the warp
-      const double mup = c2p_mu_plus_polish(c, mupf);
-      if (cold) mue = mup;
+      // mu_+ in double: one Newton step on mu^2 (1 + rbar^2(mu)) - 1 from the float root (relative error
+      // ~1e-7 -> ~1e-14), the derivative in float (it only scales that step)
+      double m1 = (double)mupf;
+      if (mupf < 1.f) {
+        const double xx = 1.0 / (1.0 + m1 * c.b2);
+        const double rb = xx * xx * c.r2 + m1 * xx * (1.0 + xx) * c.rb2;
+        const double gp = m1 * m1 * (1.0 + rb) - 1.0;
+        const float xr = 1.f / (1.f + mupf * cf.b2);
+        const float dxr = -cf.b2 * xr * xr;
+        const float rbr = xr * xr * cf.r2 + mupf * xr * (1.f + xr) * cf.rb2;
+        const float drb = 2.f * xr * dxr * cf.r2 + cf.rb2 * (xr * (1.f + xr) + mupf * dxr * (1.f + 2.f * xr));
+        const float dg = 2.f * mupf * (1.f + rbr) + mupf * mupf * drb;
+        m1 -= (double)((float)gp / dg);
+      }
+      if (cold) mue = m1;
     }
-    // f and the intermediates in double; their derivatives, which only scale the last Newton step and the
-    // first-order move of the primitives (both at most 3e-6 mu), in float at the same point
-    C2PEval<double> e = c2p_master_f(c, mue);
+    // the master function times K at mue, in double
+    const double x = 1.0 / (1.0 + c.b2 * mue);
+    const double rb = c.r2 * (x * x) + c.rb2 * (mue * x * (1.0 + x));
+    const double qbar = (c.q - 0.5 * c.b2) - (0.5 * (c.b2 * c.r2 - c.rb2)) * (mue * mue * x * x);
+    double vh2 = mue * mue * rb;
+    if (vh2 > c.v0sq) vh2 = c.v0sq;
+    const double W = rsqrt(1.0 - vh2);
+    const double iW = (1.0 - vh2) * W;
+    const double e0 = fmax(W * (1.0 + qbar - mue * rb) - 1.0, 0.0);
+    const double K = (1.0 + p.gamma_eos * e0) * iW + mue * rb;
+    const double gK = mue * K - 1.0;
+    // the derivatives, in float at the same point
     const C2PEval<float> ed = c2p_master<float>(cf, (float)mue);
-    e.df = (double)ed.df;
-    e.dx = (double)ed.dx;
-    e.dW = (double)ed.dW;
-    e.drho = (double)ed.drho;
-    e.deps = (double)ed.deps;
     ++iters;
-    if (cold && !(e.f > 0.0)) {
+    if (cold && !(gK > 0.0)) {  // root on mu_+: the cold limit
       mu = mue;
-      ev = e;
+      eps = e0;
+      Wf = (float)W;
+      xf = ed.x;
       done = true;
     } else {
-      // the intermediates at the root to first order in the step (the neglected term is O(step^2),
-      // ~1e-12 relative): no second evaluation of the master function
-      double nmu;
-      done = c2p_accept_step(c, e, mue, mupf, nmu, ev);
+      const float step = -(float)gK / ((float)K * ed.df);
+      const double nmu = mue + (double)step;
       mu = nmu;
-      if (!done && defer_mu && isfinite(nmu) && nmu > 0.0 && nmu < (double)mupf * (1.0 + 1e-3))
-        *defer_mu = nmu;  // the double pass resumes from this iterate
+      done = ed.df > 0.f && nmu > 0.0 && fabsf(step) <= 3e-6f * (float)nmu && nmu <= (double)mupf * (1.0 + 1e-5);
+      if (done) {
+        // the intermediates at the root to first order in the step (the neglected term is O(step^2))
+        eps = fmax(e0 + (double)(ed.deps * step), 0.0);
+        Wf = (float)W + ed.dW * step;
+        xf = ed.x + ed.dx * step;
+      } else if (defer && isfinite(nmu) && nmu > 0.0 && nmu < (double)mupf * (1.0 + 1e-3)) {
+        mu_r = nmu;  // the double pass resumes from this iterate
+      }
     }
   }
-  int st = 0;
   if (!done && defer) return C2P_DEFERRED;
+  int st = 0;
   if (!done) {  // float phase did not settle: double iteration on the full bracket, from the float root
     const double mup = c2p_mu_plus_fast(c);
-    if (!(stf == 0 && isfinite(mu) && mu > 0.0)) mu = mu_guess;
+    if (!(stf == 0 && isfinite(mu) && mu > 0.0)) mu = (double)mu_guess;
     int it64 = 0;
     st = c2p_newton<double>(c, mup, mu, p.c2p_tol, p.c2p_max_iter, it64, true);
     iters += it64;
-    c2p_output(c, mu, ru, bu, Uc, Pout);
-    return st;
+    const C2PEval<double> ev = c2p_master_value(c, mu);
+    eps = ev.eps;
+    Wf = (float)ev.W;
+    xf = (float)ev.x;
   }
-  c2p_output_eval(c, ev, mu, ru, bu, Uc, Pout);
+  // primitives in float: rho = D/W, W v^i = W mu x (r^i + mu (r.b) b^i), rho eps, B^i = b^i sqrt(D)
+  const float muF = (float)mu;
+  const float mx = Wf * muF * xf;
+  const float mrb = muF * cf.rb;
+  Pf[0] = cf.D / Wf;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Pf[1 + i] = mx * (ruf[i] + mrb * buf[i]);
+  Pf[4] = Pf[0] * (float)eps;
+  const float sD = sqrtf(cf.D);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Pf[5 + k] = buf[k] * sD;
+  return st;
+}
+
+// The floors of apply_floors_fr on float primitives (the mixed form's storage type), with the float metric
+// and radius factor.
+__device__ __forceinline__ int apply_floors_f(const DevParams& p, const float gam[6], float fr, float P[NV]) {
+  const float rho_flr = (float)p.rho_floor0 * fr;
+  const float eps_flr = (float)p.eps_floor0 * fr;
+  int st = 0;
+  if (!(P[0] >= rho_flr)) {
+    P[0] = rho_flr;
+    st |= ST_RHO_FLOOR;
+  }
+  if (!(P[4] >= P[0] * eps_flr)) {
+    P[4] = P[0] * eps_flr;
+    st |= ST_EPS_FLOOR;
+  }
+  const float ut[3] = {P[1], P[2], P[3]};
+  float utl[3];
+  lower3(gam, ut, utl);
+  const float usq = ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2];
+  const float wm2 = (float)p.w_max2;
+  if (1.f + usq > wm2) {  // W = sqrt(1 + u^2) > w_max
+    const float s = sqrtf((wm2 - 1.f) / usq);
+    P[1] *= s;
+    P[2] *= s;
+    P[3] *= s;
+    st |= ST_W_CAP;
+  }
   return st;
 }
 

@@ -493,6 +493,108 @@ struct CellStats {
   }
 };
 
+// The part of a geometry-cache entry the mixed form's con2prim needs in double: gamma_ij, gamma^ij, 1/sqrt(gamma).
+__device__ __forceinline__ void geo_load_c2p(const double* __restrict__ geo, long long n, long long t,
+                                             Metric<double>& m, double& isg) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    m.gam[i] = geo[(4 + i) * n + t];
+    m.gamu[i] = geo[(10 + i) * n + t];
+  }
+  isg = geo[17 * n + t];
+}
+
+// Mixed form of a5 + a6 for interior cell t, after the float flux divergence L (CT fluxes for B): float
+// sources, the RK combination in double, con2prim_mixed_f, floors in float on the float primitives. A cell
+// whose double step from the float root is not small is queued for deferred_cell; a floored cell for
+// floor_cell (its hydro state re-derived from the stored primitives), or inline without a floor list.
+template <int METRIC>
+__device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __restrict__ P, const StageArgs& a,
+                                                  float L[NV], double dt, long long t, long long g, double xc,
+                                                  double yc, double zc, float xr, float yr, float zr,
+                                                  const float Pr[NV], long long wl_tag, CellStats& cs) {
+  const long long n = p.isize, G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
+  Metric<float> mr;
+  float rf = 1.f;
+  metric_at<float, METRIC>(p, xr, yr, zr, mr, &rf);
+  if (METRIC == KERR_SCHILD) {
+    float Sr[5];
+    ks_sources<float>(p, xr, yr, zr, Pr, mr, Sr);
+#pragma unroll
+    for (int q = 1; q < 5; ++q) L[q] += Sr[q];
+  }
+  // the RK combination in double; a first stage of SSP-RK2 (g0 = 0, g1 = 1) skips the zero and unit terms
+  const double bdt = a.beta * dt;
+  double Un[NV];
+  if (a.g0 == 0.0 && a.g1 == 1.0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Un[q] = a.Ucur[q * n + t] + bdt * (double)L[q];
+  } else {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double u = a.g1 * a.Ucur[q * n + t];
+      if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
+      Un[q] = u + bdt * (double)L[q];
+    }
+  }
+  if (a.bface_new != nullptr) {
+    // face-centred CT: the cell's densitized field is the mean of its two advanced faces of each direction
+    const double* bn = a.bface_new;
+    Un[5] = 0.5 * (bn[g] + bn[g + 1]);
+    Un[6] = 0.5 * (bn[G + g] + bn[G + g + sy]);
+    Un[7] = 0.5 * (bn[2 * G + g] + bn[2 * G + g + sz]);
+  }
+  Metric<double> m;
+  double isg;
+  if (METRIC == KERR_SCHILD && p.geo != nullptr) {
+    geo_load_c2p(p.geo, n, t, m, isg);
+  } else {
+    metric_at<double, METRIC>(p, xc, yc, zc, m);
+    isg = 1.0 / m.sqrtgam;
+  }
+  // warm start mu = 1/(h W) of the current primitives, in float (it only seeds the float phase)
+  const float mu0 = mu_of_prims<float>(Pr, mr.gam, (float)p.gamma_eos);
+  float Pn[NV];
+  int iters;
+  double mu_r;
+  int st = con2prim_mixed_f(p, m, isg, Un, mu0, a.worklist != nullptr, Pn, iters, mu_r);
+  if (st == C2P_DEFERRED) {
+    // finished by deferred_cell: keep P (the warm start), store the new conserved state
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+    const unsigned int slot = atomicAdd(a.wl_count, 1u);
+    a.worklist[slot] = (int)(wl_tag + t);
+    a.wl_mu[slot] = mu_r;
+    cs.it_sum += iters;
+    return;
+  }
+  const float fr = METRIC == KERR_SCHILD ? (p.floor_r_exp == 2.0 ? 1.f / (rf * rf) : powf(rf, -(float)p.floor_r_exp))
+                                         : 1.f;
+  st |= apply_floors_f(p, mr.gam, fr, Pn);
+  if (st) {
+    if (a.floorlist) {
+      // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
+      // hold only such cells
+      a.floorlist[atomicAdd(a.fl_count, 1u)] = (int)(wl_tag + t);
+    } else {
+      Metric<double> mf;
+      metric_at<double, METRIC>(p, xc, yc, zc, mf);
+      double Pd[NV], U5[5];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Pd[q] = (double)Pn[q];
+      prim_to_cons5<double>(Pd, mf, p.gamma_eos, U5);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Un[q] = U5[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) P[q * G + g] = Pn[q];
+  a.status[t] = (uint8_t)st;
+  cs.add(st, iters);
+}
+
 // a5 + a6 for interior cell t: divergence of the face fluxes (CT fluxes for B), sources, RK
 // combination Unew = g0 U0 + g1 Ucur + beta dt L, con2prim warm-started from the current primitives,
 // floors, and the re-derived hydro state when a floor fired. In the mixed form a cell whose float
@@ -505,7 +607,6 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
                                             long long wl_tag, CellStats& cs) {
   const long long n = p.isize;
   const long long G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
-  const double bdt = a.beta * dt;
   const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
   const long long g = gidx(p, i, j, k);
   const double xc = p.x0[0] + (i + 0.5) * p.dx[0];
@@ -543,79 +644,71 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   } else {
     L[5] = L[6] = L[7] = R(0);  // the field comes from the advanced faces below
   }
-  Metric<double> m;
-  double isg, fr;
-  cell_metric<METRIC>(p, t, xc, yc, zc, m, isg, fr);
-  // metric in the source / warm-start precision: the double one itself in the FP64 form
-  Metric<R> mr;
-  if constexpr (sizeof(R) == sizeof(double)) {
-    mr = m;
+  if constexpr (sizeof(T) == 4) {
+    update_cell_mixed<METRIC>(p, P, a, L, dt, t, g, xc, yc, zc, xr, yr, zr, Pt, wl_tag, cs);
   } else {
-    metric_at<R, METRIC>(p, xr, yr, zr, mr);
-  }
-  R Pr[NV];
+    const double bdt = a.beta * dt;
+    Metric<double> m;
+    double isg, fr;
+    cell_metric<METRIC>(p, t, xc, yc, zc, m, isg, fr);
+    // metric in the source / warm-start precision: the double one itself in the FP64 form
+    Metric<R> mr;
+    if constexpr (sizeof(R) == sizeof(double)) {
+      mr = m;
+    } else {
+      metric_at<R, METRIC>(p, xr, yr, zr, mr);
+    }
+    R Pr[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) Pr[q] = R(Pt[q]);
-  if (METRIC == KERR_SCHILD) {
-    R Sr[5];
-    ks_sources<R>(p, xr, yr, zr, Pr, mr, Sr);
+    for (int q = 0; q < NV; ++q) Pr[q] = R(Pt[q]);
+    if (METRIC == KERR_SCHILD) {
+      R Sr[5];
+      ks_sources<R>(p, xr, yr, zr, Pr, mr, Sr);
 #pragma unroll
-    for (int q = 1; q < 5; ++q) L[q] += Sr[q];
-  }
-  double Un[NV];
+      for (int q = 1; q < 5; ++q) L[q] += Sr[q];
+    }
+    double Un[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    double u = a.g1 * a.Ucur[q * n + t];
-    if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
-    Un[q] = u + bdt * (double)L[q];
-  }
-  if (a.bface_new != nullptr) {
-    // face-centred CT: the cell's densitized field is the mean of its two advanced faces of each direction
-    const double* bn = a.bface_new;
-    Un[5] = 0.5 * (bn[g] + bn[g + 1]);
-    Un[6] = 0.5 * (bn[G + g] + bn[G + g + sy]);
-    Un[7] = 0.5 * (bn[2 * G + g] + bn[2 * G + g + sz]);
-  }
-  // a6: con2prim on the undensitized state, warm-started from the current primitives (the warm start only
-  // seeds the iteration: in the mixed form it is evaluated in float, the precision of its first phase)
-  double Uc[NV];
+    for (int q = 0; q < NV; ++q) {
+      double u = a.g1 * a.Ucur[q * n + t];
+      if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
+      Un[q] = u + bdt * (double)L[q];
+    }
+    if (a.bface_new != nullptr) {
+      // face-centred CT: the cell's densitized field is the mean of its two advanced faces of each direction
+      const double* bn = a.bface_new;
+      Un[5] = 0.5 * (bn[g] + bn[g + 1]);
+      Un[6] = 0.5 * (bn[G + g] + bn[G + g + sy]);
+      Un[7] = 0.5 * (bn[2 * G + g] + bn[2 * G + g + sz]);
+    }
+    // a6: con2prim on the undensitized state, warm-started from the current primitives
+    double Uc[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
-  const double mu0 = (double)mu_of_prims<R>(Pr, mr.gam, R(p.gamma_eos));
-  double Pn[NV];
-  int iters;
-  double mu_r = 0.0;  // the double iterate a deferred cell resumes from
-  int st = sizeof(T) == 4 ? con2prim_mixed<double>(p, m, Uc, mu0, Pn, iters, a.worklist != nullptr, &mu_r)
-                          : con2prim<double>(p, m, Uc, mu0, Pn, iters);
-  if (st == C2P_DEFERRED) {
-    // finished by deferred_cell: keep P (the warm start), store the new conserved state
+    for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
+    const double mu0 = (double)mu_of_prims<R>(Pr, mr.gam, R(p.gamma_eos));
+    double Pn[NV];
+    int iters;
+    int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
+    st |= apply_floors_fr(p, m.gam, fr, Pn);
+    if (st) {
+      if (a.floorlist) {
+        // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
+        // hold only such cells (a few percent of cells, but present in most warps of this pass)
+        a.floorlist[atomicAdd(a.fl_count, 1u)] = (int)(wl_tag + t);
+      } else {
+        double U5[5];
+        prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Un[q] = U5[q];
+      }
+    }
 #pragma unroll
     for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
-    const unsigned int slot = atomicAdd(a.wl_count, 1u);
-    a.worklist[slot] = (int)(wl_tag + t);
-    a.wl_mu[slot] = mu_r;
-    cs.it_sum += iters;
-    return;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
+    a.status[t] = (uint8_t)st;
+    cs.add(st, iters);
   }
-  st |= apply_floors_fr(p, m.gam, fr, Pn);
-  if (st) {
-    if (a.floorlist) {
-      // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
-      // hold only such cells (a few percent of cells, but present in most warps of this pass)
-      a.floorlist[atomicAdd(a.fl_count, 1u)] = (int)(wl_tag + t);
-    } else {
-      double U5[5];
-      prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) Un[q] = U5[q];
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
-  a.status[t] = (uint8_t)st;
-  cs.add(st, iters);
 }
 
 template <int METRIC, class R, class T>

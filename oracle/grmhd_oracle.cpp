@@ -1057,17 +1057,6 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
             recon_cell(p->recon, sR, p->weno_eps, qm, qp);
             PR[v] = reg ? qm / sfc : qm;
           }
-          // Reading (the paper is silent on reconstruction failure): a face whose reconstructed
-          // density is not positive or internal energy is negative on either side takes the
-          // first-order (cell) values of both neighbours.
-          if (!(PL[0] > 0.0) || !(PL[4] >= 0.0) || !(PR[0] > 0.0) || !(PR[4] >= 0.0)) {
-            int cl[3] = {i, j, k};
-            cl[d] -= 1;
-            for (int v = 0; v < 8; ++v) {
-              PL[v] = P[v * gn + g.gi(cl[0], cl[1], cl[2])];
-              PR[v] = P[v * gn + g.gi(i, j, k)];
-            }
-          }
           double xf[3] = {g.xc(0, i), g.xc(1, j), g.xc(2, k)};
           xf[d] = g.xf(d, c[d]);
           if (p->metric == 2 && d == 1 && std::fabs(std::sin(xf[1])) < 1e-12) {
@@ -1078,6 +1067,19 @@ static int stage_impl(const orc_params* p, double* P, const double* U0, const do
           }
           Geom G;
           metric_eval(*p, xf[0], xf[1], xf[2], G);
+          // Reading (Sec. 3.2, atmosphere treatment: the density must stay above its floor and the
+          // specific internal energy is floored likewise): the reconstructed states of a face take the
+          // floors at the face, rho >= rho_flr and rho eps >= rho eps_flr. The paper does not say where
+          // the floors act; on the face states they keep the states the fluxes are built from physical
+          // without a switch, so the face fluxes depend continuously on the cell values.
+          {
+            const double fr = p->metric >= 1 ? std::pow(G.r, -p->floor_r_exp) : 1.0;
+            const double rho_flr = p->rho_floor0 * fr, eps_flr = p->eps_floor0 * fr;
+            for (double* S : {PL, PR}) {
+              if (!(S[0] >= rho_flr)) S[0] = rho_flr;
+              if (!(S[4] >= S[0] * eps_flr)) S[4] = S[0] * eps_flr;
+            }
+          }
           if (face_ct) {
             const double bn = Bfcur[d * gn + g.gi(i, j, k)] / G.sqrtgam;
             PL[5 + d] = bn;

@@ -44,28 +44,28 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
 }
 
 // a1 + a3 for the face between cells (i, j, k) - e_d and (i, j, k) of direction d, given the two
-// reconstructed sides PL, PR and the two cell values cL, cR: evaluate the metric at the face centre, the
-// two sides' (U, F, lambda), and the Riemann flux Fh; returns max |lambda|. A face whose reconstructed
-// density is not positive or internal energy is negative on either side takes the first-order (cell)
-// values of both neighbours. With a face-centred field (p.bface) both sides take the face's normal
-// field B^d = Bf_d / sqrt(gamma).
+// reconstructed sides PL, PR: evaluate the metric at the face centre, floor the two sides (Sec. 3.2: rho >=
+// rho_flr, rho eps >= rho eps_flr at the face; continuous in the data, unlike a switch to other values),
+// their (U, F, lambda), and the Riemann flux Fh; returns max |lambda|. With a face-centred field (p.bface)
+// both sides take the face's normal field B^d = Bf_d / sqrt(gamma).
 template <class R, int METRIC>
 __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, int k, R PL[NV], R PR[NV],
-                                       const R cL[NV], const R cR[NV], R Fh[NV]) {
-  if (!(PL[0] > R(0)) || !(PL[4] >= R(0)) || !(PR[0] > R(0)) || !(PR[4] >= R(0))) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      PL[q] = cL[q];
-      PR[q] = cR[q];
-    }
-  }
+                                       R Fh[NV]) {
   // face centre, in the flux arithmetic type
   R xf[3] = {R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
              R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2])};
   const int cd = d == 0 ? i : (d == 1 ? j : k);
   xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
   Metric<R> m;
-  metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m);
+  R rks = R(1);
+  metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m, &rks);
+  const R fr = METRIC == KERR_SCHILD ? (p.floor_r_exp == 2.0 ? R(1) / (rks * rks) : R(pow((double)rks, -p.floor_r_exp)))
+                                     : R(1);
+  const R rho_flr = R(p.rho_floor0) * fr, eps_flr = R(p.eps_floor0) * fr;
+  if (!(PL[0] >= rho_flr)) PL[0] = rho_flr;
+  if (!(PR[0] >= rho_flr)) PR[0] = rho_flr;
+  if (!(PL[4] >= PL[0] * eps_flr)) PL[4] = PL[0] * eps_flr;
+  if (!(PR[4] >= PR[0] * eps_flr)) PR[4] = PR[0] * eps_flr;
   if (p.bface != nullptr) {
     const R bn = R(p.bface[d * p.gsize + gidx(p, i, j, k)]) / m.sqrtgam;
     PL[5 + d] = bn;
@@ -89,7 +89,7 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
   const int j = (int)((t / ex) % ey) + (d == 1 ? 0 : -1);
   const int k = (int)(t / ((long long)ex * ey)) + (d == 2 ? 0 : -1);
   const long long g = gidx(p, i, j, k);
-  R PL[NV], PR[NV], cL[NV], cR[NV];
+  R PL[NV], PR[NV];
   const R eps = R(p.weno_eps);
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
@@ -105,11 +105,9 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
     PL[q] = qp;
     recon_cell<R, RECON>(fm2, fm1, f0, fp1, fp2, eps, qm, qp);  // cell c
     PR[q] = qm;
-    cL[q] = fm1;
-    cR[q] = f0;
   }
   R Fh[NV];
-  const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
+  const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
 #pragma unroll
   for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
   const bool interior = (d == 0 || (i >= 0 && i < p.nx)) && (d == 1 || (j >= 0 && j < p.ny)) &&
@@ -190,18 +188,17 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
 #pragma unroll
     for (int s = 0; s < 5; ++s) w[q][s] = R(Pq[(s - 3) * sd]);
   }
-  R PL[NV], cL[NV];
+  R PL[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     R qm, qp;
     recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
     PL[q] = qp;
-    cL[q] = w[q][2];
   }
   R cm_run = R(0);
   for (int f = f0; f < f1; ++f) {
     // window of cell f: cells f - 2 .. f + 2
-    R PR[NV], cR[NV], QP[NV];
+    R PR[NV], QP[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
 #pragma unroll
@@ -211,15 +208,13 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
       recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
       PR[q] = qm;
       QP[q] = qp;
-      cR[q] = w[q][2];
     }
     R Fh[NV];
-    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, cL, cR, Fh);
+    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       F[q * p.gsize + g] = Fh[q];
       PL[q] = QP[q];
-      cL[q] = cR[q];
     }
     if (inner_t && cm > cm_run) cm_run = cm;
     g += sd;
@@ -245,7 +240,7 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
   const int j = (int)(row % (p.ny + 2)) - 1, k = (int)(row / (p.ny + 2)) - 1;
   const R eps = R(p.weno_eps);
   const long long g = gidx(p, c, j, k);
-  R qm[NV], qp[NV], cc[NV];
+  R qm[NV], qp[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const T* Pq = P + q * p.gsize + g;
@@ -253,17 +248,13 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
 #pragma unroll
     for (int s = 0; s < 5; ++s) f[s] = live ? R(Pq[s - 2]) : R(0);
     recon_cell<R, RECON>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
-    cc[q] = f[2];
   }
-  R PL[NV], cL[NV];
+  R PL[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    PL[q] = __shfl_up_sync(0xffffffffu, qp[q], 1);
-    cL[q] = __shfl_up_sync(0xffffffffu, cc[q], 1);
-  }
+  for (int q = 0; q < NV; ++q) PL[q] = __shfl_up_sync(0xffffffffu, qp[q], 1);
   if (lane == 0 || !live || c < 0) return R(0);
   R Fh[NV];
-  const R cm = face_flux<R, METRIC>(p, 0, c, j, k, PL, qm, cL, cc, Fh);
+  const R cm = face_flux<R, METRIC>(p, 0, c, j, k, PL, qm, Fh);
 #pragma unroll
   for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
   return (j >= 0 && j < p.ny && k >= 0 && k < p.nz) ? cm : R(0);
@@ -286,6 +277,88 @@ __global__ void __launch_bounds__(128, kFluxMinBlocks<R>) k_flux_cc(const T* __r
     const R cm = d == 0 ? flux_lane<R, T, METRIC, RECON>(p, P, F, t) : flux_run<R, T, METRIC, RECON>(p, P, F, d, t);
     if (cm > cm_local) cm_local = cm;
   }
+  if (track_speed) block_max_to<R>(cm_local, ms + d);
+}
+
+// Shared-memory tiled fluxes of direction d = 1, 2 for the five-point reconstructions (WENO5-Z-AOAH, MP5):
+// a CTA takes FLUX_TILE_T consecutive x positions (transverse position a in [-1, nx]) at one position b of the
+// other transverse direction, and FLUX_TILE_D faces along d. It stages the primitives of the tile with its
+// halo along d (FLUX_TILE_D + 5 cells per column) in shared memory with x-coalesced loads, reconstructs each
+// of the FLUX_TILE_D + 1 cells it needs once (both faces, into shared memory), then evaluates every face from
+// the plus side of the cell below and the minus side of the cell above (face_flux). One thread per cell and
+// then per face: no per-thread window in registers. Max |lambda| of the interior faces goes to ms[d].
+constexpr int FLUX_TILE_T = 32;
+constexpr int FLUX_TILE_D = 16;
+constexpr int FLUX_TILE_TP = FLUX_TILE_T + 1;  // padded row (conflict-free column access)
+constexpr int FLUX_TILE_THREADS = 256;
+
+template <class R>
+constexpr size_t flux_tile_smem() {
+  return sizeof(R) * (size_t)NV * FLUX_TILE_TP * ((FLUX_TILE_D + 5) + 2 * (FLUX_TILE_D + 1));
+}
+
+template <class R, class T, int METRIC, int RECON>
+__global__ void __launch_bounds__(FLUX_TILE_THREADS) k_flux_tile(const T* __restrict__ P, R* __restrict__ F,
+                                                                 unsigned long long* __restrict__ ms, DevParams p,
+                                                                 int d, int track_speed) {
+  extern __shared__ __align__(16) unsigned char flux_smem[];
+  constexpr int CW = FLUX_TILE_D + 5;   // cells staged per column
+  constexpr int CR = FLUX_TILE_D + 1;   // cells reconstructed per column
+  R* sP = (R*)flux_smem;                               // [NV][CW][TP]
+  R* sQ = sP + (size_t)NV * CW * FLUX_TILE_TP;         // [2][NV][CR][TP]: minus side, plus side
+  const int nd = d == 1 ? p.ny : p.nz;
+  const int na = p.nx, nb = d == 1 ? p.nz : p.ny;
+  const int a0 = (int)blockIdx.x * FLUX_TILE_T - 1;
+  const int b = (int)blockIdx.y - 1;
+  const int f0 = (int)blockIdx.z * FLUX_TILE_D;
+  const long long sd = d == 1 ? (long long)p.gx : (long long)p.gx * p.gy;
+  // (a, c along d) -> ghosted index
+  auto cell = [&](int a, int c) { return d == 1 ? gidx(p, a, c, b) : gidx(p, a, b, c); };
+  // stage cells f0 - 3 .. f0 + FLUX_TILE_D + 1 (only those up to nd + 2 are needed: the last face is nd)
+  for (int e = threadIdx.x; e < NV * CW * FLUX_TILE_T; e += FLUX_TILE_THREADS) {
+    const int ct = e % FLUX_TILE_T, rest = e / FLUX_TILE_T;
+    const int cd = rest % CW, q = rest / CW;
+    const int a = a0 + ct, c = f0 - 3 + cd;
+    if (a <= na && c <= nd + 2) sP[(q * CW + cd) * FLUX_TILE_TP + ct] = R(P[q * p.gsize + cell(a, c)]);
+  }
+  __syncthreads();
+  const R eps = R(p.weno_eps);
+  // reconstruct cells f0 - 1 .. f0 + FLUX_TILE_D - 1 (those up to nd)
+  for (int e = threadIdx.x; e < CR * FLUX_TILE_T; e += FLUX_TILE_THREADS) {
+    const int ct = e % FLUX_TILE_T, cc = e / FLUX_TILE_T;
+    if (a0 + ct > na || f0 - 1 + cc > nd) continue;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const R* s = sP + (q * CW + cc) * FLUX_TILE_TP + ct;
+      R qm, qp;
+      recon_cell<R, RECON>(s[0], s[FLUX_TILE_TP], s[2 * FLUX_TILE_TP], s[3 * FLUX_TILE_TP], s[4 * FLUX_TILE_TP], eps,
+                           qm, qp);
+      sQ[(q * CR + cc) * FLUX_TILE_TP + ct] = qm;
+      sQ[((NV + q) * CR + cc) * FLUX_TILE_TP + ct] = qp;
+    }
+  }
+  __syncthreads();
+  // faces f0 .. f0 + FLUX_TILE_D - 1 (those up to nd): face f between cells f - 1 and f
+  R cm_local = R(0);
+  for (int e = threadIdx.x; e < FLUX_TILE_D * FLUX_TILE_T; e += FLUX_TILE_THREADS) {
+    const int ct = e % FLUX_TILE_T, ff = e / FLUX_TILE_T;
+    const int a = a0 + ct, f = f0 + ff;
+    if (a > na || f > nd) continue;
+    R PL[NV], PR[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      PL[q] = sQ[((NV + q) * CR + ff) * FLUX_TILE_TP + ct];
+      PR[q] = sQ[(q * CR + ff + 1) * FLUX_TILE_TP + ct];
+    }
+    R Fh[NV];
+    const int i = a, j = d == 1 ? f : b, k = d == 1 ? b : f;
+    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
+    const long long g = cell(a, f);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
+    if (a >= 0 && a < na && b >= 0 && b < nb && cm > cm_local) cm_local = cm;
+  }
+  (void)sd;
   if (track_speed) block_max_to<R>(cm_local, ms + d);
 }
 

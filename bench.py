@@ -412,6 +412,7 @@ def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=
         ctx.p2c(Pd, Ub)
         berr.append(float(((Ub - U).abs().amax(dim=0) / scale)[plain].max()))
     del Ub
+    mism = _status_mismatch(ctx, U, Ps, Pn, sts, stn, torch)
     out = {"states": n_states, "c2p_tol": 1e-10,
            "train": {"pairs": n_pairs, "source": "the library's FP64 con2prim from the standard start",
                      "steps": train_steps, "batch": 152 * 128, "ms": train_ms,
@@ -423,7 +424,7 @@ def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=
            "network_fp32": dict(sum_f32, ms=ms_f32, states_per_s=n_states / (ms_f32 / 1e3),
                                 fallback_frac=fall_f32 / n_states,
                                 kernel="network on the FP32 cores, then the FP64 solve (two kernels)"),
-           "status_mismatch": {"network_fp32": mis_f32, "network_tc": int((sts != stn).sum())},
+           "status_mismatch": {"network_fp32": mis_f32, "network_tc": int((sts != stn).sum()), "network_tc_detail": mism},
            "max_backward_err": {"standard": berr[0], "network_tc": berr[1]}}
     out["speedup_tc"] = ms_std / ms_tc
     out["speedup_fp32"] = ms_std / ms_f32
@@ -432,20 +433,46 @@ def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=
     return out
 
 
-def batched_setups(seed0=3):
-    """640 uneven meshblocks (448 x 16^3, 160 x 32^3, 32 x 64^3, 4 ghosts), each of physical size 1.6,
-    on disjoint sub-cubes of a 9 x 9 x 8 lattice starting at (3, 3, 3) in Kerr-Schild coordinates; each
-    block's primitives come from the seeded random-state generator (seed 3 + block id)."""
+def _status_mismatch(ctx, U, Pa, Pb, sta, stb, torch):
+    """States whose status bits differ between two solves of the same conserved states (standard start and
+    network start): which bits, and how far the solution on which the floor did not fire sits from the
+    floor's threshold. A floor decision taken on opposite sides of its threshold by two solutions that both
+    meet the root tolerance is a tie at the threshold, within the solve's accuracy at that state."""
+    idx = (sta != stb).nonzero().flatten()
+    if idx.numel() == 0:
+        return {"count": 0}
+    a, b = sta[idx].int(), stb[idx].int()
+    diff = a ^ b
+    bits = {name: int(((diff & m) != 0).sum()) for name, m in (("rho_floor", 1), ("eps_floor", 2), ("w_cap", 4),
+                                                                ("not_converged", 8), ("bad_input", 16))}
+    p = ctx.p
+    Pa_, Pb_ = Pa[:, idx], Pb[:, idx]
+    # the eps floor: u >= rho eps_floor0 (flat space); margin of the solution without the floor bit
+    free_a = (a & 2) == 0
+    Pf = torch.where(free_a[None, :], Pa_, Pb_)
+    eps_margin = (Pf[4] / (Pf[0] * p.eps_floor0) - 1.0).abs()
+    # the Lorentz-factor cap: W <= w_max; margin of the solution without the cap bit
+    free_wa = (a & 4) == 0
+    Pw = torch.where(free_wa[None, :], Pa_, Pb_)
+    W = torch.sqrt(1.0 + (Pw[1:4] ** 2).sum(0))
+    w_margin = (W / p.w_max - 1.0).abs()
+    eps_sel = (diff & 2) != 0
+    w_sel = (diff & 4) != 0
+    # relative difference of mu = 1/(h W) between the two solutions (both meet |d mu| <= 1e-10 mu)
+    def mu(P):
+        Wp = torch.sqrt(1.0 + (P[1:4] ** 2).sum(0))
+        h = 1.0 + ctx.setup.gamma_eos * P[4] / P[0]
+        return 1.0 / (h * Wp)
+    return {"count": int(idx.numel()), "bits": bits,
+            "eps_floor_margin_max": float(eps_margin[eps_sel].max()) if eps_sel.any() else None,
+            "w_cap_margin_max": float(w_margin[w_sel].max()) if w_sel.any() else None,
+            "mu_rel_diff_max": float(((mu(Pa_) - mu(Pb_)).abs() / mu(Pa_)).max())}
+
+
+def batched_setups():
+    """The 640-block batched workload (inputs.batched_setups): block b's primitives use seed 3 + b."""
     from paper_2410_09146_gb300 import inputs as I
-    sizes = [16] * 448 + [32] * 160 + [64] * 32
-    setups = []
-    for b, n in enumerate(sizes):
-        ix, iy, iz = b % 9, (b // 9) % 9, b // 81
-        h = 1.6 / n
-        setups.append(I.Setup(n=(n, n, n), x0=(3.0 + 1.6 * ix, 3.0 + 1.6 * iy, 3.0 + 1.6 * iz), dx=(h, h, h),
-                              metric="kerr_schild", spin=0.9, recon="weno5z_aoah", riemann="hll", bc="fixed",
-                              precision="mixed"))
-    return setups
+    return I.batched_setups()
 
 
 def _face_divergence(B, s, torch):
@@ -589,18 +616,20 @@ def run_batched(G, I, steps, warmup, rank):
             "c2p_iterations_per_cell": float(stats[0]) / zones}, ms, zones
 
 
-# Work and traffic per unit of the mixed-form kernels, measured by ncu (--set full) on the 96^3
-# Kerr-Schild random block (summary under profiles/): double-precision flops (DADD + DMUL + 2 DFMA,
-# active lanes) per cell of k_update, float flops (FADD + FMUL + 2 FFMA) per face of k_flux_cc (mean of
-# the three directions), DRAM bytes (read + write) per unit.
-UPDATE_FP64_FLOP_PER_CELL = 374.0
-UPDATE_DRAM_BYTES_PER_CELL = 373.4
-# algorithmic bytes per cell of k_update: P (8 float) + Ucur (8 double) + U0 (8 double, stages with
-# g0 != 0) + 3 x 8 face fluxes (float) + 3 EMFs (float) + 19 doubles of cached geometry read; Unew
-# (8 double) + P (8 float) + status written; the average over the two stages of an RK2 step
-UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 152 + 64 + 32 + 1
-FLUX_FP32_FLOP_PER_FACE = 2342.0
-FLUX_DRAM_BYTES_PER_FACE = 38.5
+# Work and traffic per unit of the mixed-form kernels, measured by ncu (--set full, one kernel per capture)
+# on the 96^3 Kerr-Schild random block (summaries under profiles/): double-precision flops (DADD + DMUL +
+# 2 DFMA, active lanes) per cell of k_update (mean of the g0 = 0 and g0 != 0 stages), float flops (FADD + FMUL
+# + 2 FFMA) per face of k_flux_cc (mean of the three directions), DRAM bytes (read + write) per unit.
+UPDATE_FP64_FLOP_PER_CELL = 194.7
+UPDATE_DRAM_BYTES_PER_CELL = 387.6
+# algorithmic bytes per cell of k_update: P (8 float) + Ucur (8 double) + U0 (8 double, stages with g0 != 0)
+# + 3 x 8 face fluxes (float) + 3 EMFs (float) + 13 doubles of cached geometry read; Unew (8 double) + P (8
+# float) + status written; the mean over the two stages of an RK2 step
+UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 104 + 64 + 32 + 1
+FLUX_FP32_FLOP_PER_FACE = 2400.0
+FLUX_DRAM_BYTES_PER_FACE = 41.6
+
+
 # Algorithmic bytes per interior zone per stage of the fused-ideal mixed form (primitives in float, state in
 # double, metric computed, perfect stencil reuse; the mean of the two stages of an RK2 step at 256^3, where
 # the primitive read over the ghosted block is 1.097 zones' worth): 32 f_g (P read) + 64 (U read) + 32
@@ -633,12 +662,13 @@ def roofline(dom, ms, n, stats, fp_peaks, ms_stage, peaks):
         achieved = flops / (ms / 1e3) / 1e12
         return {"kernel": "k_update", "bound": "alu", "achieved": achieved, "peak": f64, "unit": "TFLOP/s",
                 "frac": achieved / f64, "traffic": UPDATE_DRAM_BYTES_PER_CELL * cells, "ms_per_launch": ms,
-                "work_per_unit": f"{UPDATE_FP64_FLOP_PER_CELL} FP64 flop/cell (ncu, 96^3)",
+                "work_per_unit": f"{UPDATE_FP64_FLOP_PER_CELL} FP64 flop/cell (ncu, 96^3, active lanes)",
                 "algorithmic_bytes_per_cell": UPDATE_ALGO_BYTES_PER_CELL,
                 "hbm_frac": UPDATE_ALGO_BYTES_PER_CELL * cells / (ms / 1e3) / 1e9 / hbm if hbm else None,
                 "stage_hbm": stage_hbm,
-                "note": "FP64 pipe (issue-bound: one warp FP64 instruction per ~20 SM cycles whatever its active "
-                        "lanes); peak = the DFMA rate measured live on this GPU by grmhd_fp_peaks "
+                "note": "FP64 pipe (issue-bound: one warp FP64 instruction costs the same pipe time whatever its "
+                        "active lanes; ncu: FP64 pipe 75% busy at 58% active lanes per instruction, the rest are "
+                        "float<->double conversions); peak = the DFMA rate measured live on this GPU by grmhd_fp_peaks "
                         "(MEASURED_PEAKS.json has no FP64 figure); traffic scaled from the 96^3 ncu capture by "
                         "cell count"}
     faces = 3 * (n + 1) * (n + 2) ** 2 / 3.0

@@ -294,6 +294,14 @@ int grmhd_set_timing(grmhd_ctx* c, int on);
  * resets the totals. Synchronises on the last recorded event. */
 int grmhd_get_timing(grmhd_ctx* c, double* ms, int* stages);
 
+/* Bounds-check build (compiled with -DGRMHD_BOUNDS_CHECK; a testing aid, the paper has no counterpart): the
+ * stage kernels compare every global-memory index with its array's extent; the first out-of-range access of
+ * a context's stages is recorded and skipped (loads read 0) and nothing traps. out[0] = 0 when no access was
+ * out of range, else (source line << 48 | sign << 47 | |index|) + 1 of the first one; out[1] = 1 when the
+ * library was built with the checks (0: out[0] is always 0). Synchronises the context's stream.
+ * Errors: GRMHD_E_INVALID (NULL), GRMHD_E_CUDA. */
+int grmhd_bounds_fault(grmhd_ctx* c, unsigned long long out[2]);
+
 /* The a7 helper (CFL rule; the paper does not state one): out[d] = the largest characteristic speed |lambda+-|
  * over the interior faces of direction d, from the last stage of this single-block context that took its
  * time step from the face speeds (a first stage, g0 == 0, with dt <= 0); dt = cfl / max_d(out[d] / dx[d]) is
@@ -418,6 +426,11 @@ int grmhd_batch_set_tile(grmhd_ctx* c, int tile);
 /* Time tiles 128 .. 4096 with one real RK2 step each (the batch advances by 6 steps with the CFL time
  * step) and keep the fastest; returns it and its milliseconds per stage (either pointer may be NULL). */
 int grmhd_batch_autotune(grmhd_ctx* c, int* best_tile, double* best_ms);
+
+/* The timing table of the last grmhd_batch_autotune of this batch: *n candidates (0 before any), the first
+ * min(*n, cap) written to tiles[] (work-item size) and ms[] (device milliseconds per stage, CUDA events on the
+ * batch's stream). The tile the autotuner kept is the one with the smallest ms. Errors: GRMHD_E_INVALID. */
+int grmhd_batch_autotune_table(grmhd_ctx* c, int* tiles, double* ms, int cap, int* n);
 
 /* Batch contexts only: with `on` != 0 each distinct stage (coefficients, dt, state slots, tile) is
  * captured once into a CUDA graph on a library-owned capture stream and replayed on the context's

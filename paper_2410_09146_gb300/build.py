@@ -10,6 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgrmhd.so")
+BUILD_BC = os.path.join(HERE, "_build_bc")
+LIB_BC = os.path.join(BUILD_BC, "libgrmhd.so")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["grmhd_api.cu", "grmhd_fp64.cu", "grmhd_mixed.cu", "grmhd_batch.cu", "grmhd_noalloc.cu", "grmhd_mlp.cu",
            "grmhd_mlp_train.cu", "grmhd_mlp_tc.cu", "grmhd_peaks.cu"]
@@ -36,7 +38,16 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), bounds_check: bool = False) -> str:
+    """Build libgrmhd.so (returns its path). bounds_check=True builds the bounds-check variant instead
+    (-DGRMHD_BOUNDS_CHECK, in its own folder): the stage kernels check every global index and record the first
+    out-of-range one (grmhd_bounds_fault) without trapping; a testing build."""
+    if bounds_check:
+        return _build_into(BUILD_BC, LIB_BC, force, verbose, tuple(extra_flags) + ("-DGRMHD_BOUNDS_CHECK",))
+    return _build_into(BUILD, LIB, force, verbose, tuple(extra_flags))
+
+
+def _build_into(BUILD, LIB, force, verbose, extra_flags):
     os.makedirs(BUILD, exist_ok=True)
     deps_common = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "grmhd.h"),
                                                               os.path.abspath(__file__)]

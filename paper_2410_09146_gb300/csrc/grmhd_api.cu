@@ -72,6 +72,9 @@ struct grmhd_ctx {
   long long total_cells;
   long long total_ghosted;   // nblocks x gsize of block 0 (meaningful for lattices, whose blocks are equal)
   bool use_graph;
+  int n_tuned;               // the last autotune's timing table: work-item size and ms per stage
+  int tuned_tile[8];
+  double tuned_ms[8];
   cudaStream_t cap_stream;
   std::map<std::vector<double>, cudaGraphExec_t> graphs;
   char err[256];
@@ -135,6 +138,20 @@ DevParams dev_params(const grmhd_params* p) {
   d.c2p_tol = p->c2p_tol; d.c2p_max_iter = p->c2p_max_iter;
   d.cfl = p->cfl; d.weno_eps = p->weno_eps;
   for (int i = 0; i < 3; ++i) d.shift[i] = p->metric == GRMHD_MINKOWSKI ? p->shift[i] : 0.0;
+  for (int i = 0; i < 3; ++i) {
+    d.fx0[i] = (float)d.x0[i];
+    d.fdx[i] = (float)d.dx[i];
+    d.fidx[i] = (float)d.idx[i];
+    d.fshift[i] = (float)d.shift[i];
+  }
+  d.fa = (float)d.a;
+  d.fM = (float)d.M;
+  d.fgamma = (float)d.gamma_eos;
+  d.fweno_eps = (float)d.weno_eps;
+  d.frho_floor0 = (float)d.rho_floor0;
+  d.feps_floor0 = (float)d.eps_floor0;
+  d.fw_max2 = (float)d.w_max2;
+  d.floor_r2 = d.floor_r_exp == 2.0 ? 1 : 0;
   return d;
 }
 
@@ -145,6 +162,7 @@ namespace {
 thread_local char g_create_err[256] = "";
 
 constexpr size_t kAlign = 256;
+constexpr int kFaultSlot = 32;  // scal[32]: the bounds-check build's fault word
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Layout {
@@ -396,6 +414,7 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
   c->ws = (char*)workspace;
   c->ws_bytes = bytes;
   c->scal = (unsigned long long*)(c->ws + l.scal);
+  c->dp.fault = c->scal + kFaultSlot;
   if (!batch_only(c)) {
     c->P = c->ws + l.P;
     for (int s = 0; s < 3; ++s) c->Uslot[s] = (double*)(c->ws + l.U[s]);
@@ -766,6 +785,19 @@ static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double d
   return GRMHD_OK;
 }
 
+int grmhd_bounds_fault(grmhd_ctx* c, unsigned long long out[2]) {
+  if (!c || !out) return c ? fail(c, GRMHD_E_INVALID, "out is NULL") : GRMHD_E_INVALID;
+  CK(cudaMemcpyAsync(out, c->scal + kFaultSlot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
+     "copying the fault word");
+  CK(cudaStreamSynchronize(c->stream), "synchronising");
+#ifdef GRMHD_BOUNDS_CHECK
+  out[1] = 1;
+#else
+  out[1] = 0;
+#endif
+  return GRMHD_OK;
+}
+
 int grmhd_max_speed(grmhd_ctx* c, double out[3]) {
   if (!c || !out) return c ? fail(c, GRMHD_E_INVALID, "out is NULL") : GRMHD_E_INVALID;
   if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
@@ -959,6 +991,7 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   for (int b = 0; b < nblocks; ++b) {
     BlockDesc& d = c->hblocks[b];
     d.p = block_params(p, blocks[b]);
+    d.p.fault = c->scal + kFaultSlot;
     d.P = c->ws + l.P[b];
     for (int k = 0; k < 3; ++k) {
       d.U[k] = (double*)(c->ws + l.U[3 * b + k]);
@@ -1220,6 +1253,7 @@ int grmhd_batch_autotune(grmhd_ctx* c, int* best_tile, double* best_ms) {
   const int tiles[] = {128, 256, 512, 1024, 2048, 4096};
   int best = c->tile;
   float best_t = 1e30f;
+  c->n_tuned = 0;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "creating events");
   CK(cudaEventCreate(&e1), "creating events");
@@ -1236,6 +1270,9 @@ int grmhd_batch_autotune(grmhd_ctx* c, int* best_tile, double* best_ms) {
     CK(cudaEventSynchronize(e1), "synchronising");
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1), "reading events");
+    c->tuned_tile[c->n_tuned] = t;
+    c->tuned_ms[c->n_tuned] = 0.5 * ms;
+    ++c->n_tuned;
     if (ms < best_t) {
       best_t = ms;
       best = t;
@@ -1249,6 +1286,17 @@ int grmhd_batch_autotune(grmhd_ctx* c, int* best_tile, double* best_ms) {
   if (best_tile) *best_tile = best;
   if (best_ms) *best_ms = 0.5 * best_t;
   return rc;
+}
+
+int grmhd_batch_autotune_table(grmhd_ctx* c, int* tiles, double* ms, int cap, int* n) {
+  if (!c || !n || cap < 0 || (cap > 0 && (!tiles || !ms))) return c ? fail(c, GRMHD_E_INVALID, "bad arguments") : GRMHD_E_INVALID;
+  if (c->nblocks < 1) return fail(c, GRMHD_E_INVALID, "not a batch context");
+  *n = c->n_tuned;
+  for (int k = 0; k < c->n_tuned && k < cap; ++k) {
+    tiles[k] = c->tuned_tile[k];
+    ms[k] = c->tuned_ms[k];
+  }
+  return GRMHD_OK;
 }
 
 }  // extern "C"

@@ -45,7 +45,63 @@ struct DevParams {
   // NULL: cell-centred field (flux-CT).
   const double* bface;
   double shift[3];  // Minkowski: constant shift beta^i (flat space in coordinates moving at -beta)
+  // Float copies of the parameters the float kernels read (set with the double ones): a double -> float
+  // conversion costs an FP64 issue slot on this part, so the float code reads these instead.
+  float fx0[3], fdx[3], fidx[3], fa, fM, fgamma, fweno_eps, frho_floor0, feps_floor0, fw_max2, fshift[3];
+  int floor_r2;  // floor_r_exp == 2 (the radius factor is 1/r^2)
+  // Bounds-check build (GRMHD_BOUNDS_CHECK): the word where the first out-of-range access of a stage kernel
+  // is recorded (see bounds_fault); unused otherwise.
+  unsigned long long* fault;
 };
+
+// Checked global-memory access of the stage kernels. In the bounds-check build (-DGRMHD_BOUNDS_CHECK) every
+// load / store through ldc / stc compares its index with the extent of the array; the first index outside
+// [0, n) is recorded in *p.fault as (source line << 48) | (sign << 47) | |index|, plus one (0 = none), and the
+// access is skipped (a load returns 0). Nothing traps, so a faulty index leaves the context usable. In the
+// normal build both are the plain access.
+__device__ __forceinline__ void bounds_fault(const DevParams& p, int line, long long i) {
+  if (p.fault == nullptr) return;
+  const unsigned long long mag = (unsigned long long)(i < 0 ? -i : i) & ((1ull << 47) - 1);
+  const unsigned long long w = (((unsigned long long)line & 0xffffull) << 48) | ((i < 0 ? 1ull : 0ull) << 47) | mag;
+  atomicCAS(p.fault, 0ull, w + 1);
+}
+
+template <class X>
+__device__ __forceinline__ X ldc(const DevParams& p, const X* __restrict__ a, long long i, long long n, int line) {
+#ifdef GRMHD_BOUNDS_CHECK
+  if (i < 0 || i >= n) {
+    bounds_fault(p, line, i);
+    return X(0);
+  }
+#endif
+  (void)p; (void)n; (void)line;
+  return a[i];
+}
+
+template <class X>
+__device__ __forceinline__ void stc(const DevParams& p, X* __restrict__ a, long long i, long long n, X v, int line) {
+#ifdef GRMHD_BOUNDS_CHECK
+  if (i < 0 || i >= n) {
+    bounds_fault(p, line, i);
+    return;
+  }
+#endif
+  (void)p; (void)n; (void)line;
+  a[i] = v;
+}
+
+#define LDC(arr, i, n) ldc(p, (arr), (long long)(i), (long long)(n), __LINE__)
+#define STC(arr, i, n, v) stc(p, (arr), (long long)(i), (long long)(n), (v), __LINE__)
+
+// A parameter in the arithmetic type R: the double field in double code, its float copy in float code.
+template <class R>
+__host__ __device__ __forceinline__ R par(double d, float f) {
+  if constexpr (sizeof(R) == 4) {
+    return f;
+  } else {
+    return (R)d;
+  }
+}
 
 // Arguments of the update kernel (a5 + a6).
 struct StageArgs {
@@ -218,13 +274,13 @@ __device__ __forceinline__ void metric_at(const DevParams& p, R x, R y, R z, Met
     m.alpha = R(1);
     m.sqrtgam = R(1);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) m.beta[i] = R(p.shift[i]);
+    for (int i = 0; i < 3; ++i) m.beta[i] = par<R>(p.shift[i], p.fshift[i]);
 #pragma unroll
     for (int t = 0; t < 6; ++t) m.gam[t] = m.gamu[t] = (t == 0 || t == 3 || t == 5) ? R(1) : R(0);
     if (rks) *rks = R(1);
   } else {
     R r, r2, f, l[3];
-    ks_core<R>(x, y, z, R(p.a), R(p.M), r, r2, f, l);
+    ks_core<R>(x, y, z, par<R>(p.a, p.fa), par<R>(p.M, p.fM), r, r2, f, l);
     if (rks) *rks = r;
     const R sg = sqrt(R(1) + f);
     const R ip = rcp(R(1) + f);
@@ -241,6 +297,13 @@ __device__ __forceinline__ void metric_at(const DevParams& p, R x, R y, R z, Met
         m.gamu[sym3(i, j)] = (i == j ? R(1) : R(0)) - f * ip * ll;
       }
   }
+}
+
+// Component d of a 3-vector by selects (d is a run-time direction: indexing an array with it would put the
+// array in local memory).
+template <class R>
+__host__ __device__ __forceinline__ R sel3(int d, R a0, R a1, R a2) {
+  return d == 0 ? a0 : (d == 1 ? a1 : a2);
 }
 
 template <class R>
@@ -311,12 +374,13 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) Uc[5 + k] = B[k];
-  const R vtd = vt[d] * ia;
-  const R Bd = B[d];
+  const R vtd = sel3(d, vt[0], vt[1], vt[2]) * ia;
+  const R Bd = sel3(d, B[0], B[1], B[2]);
+  const R vd = sel3(d, v[0], v[1], v[2]);
   s.F[0] = D * vtd;
 #pragma unroll
   for (int j = 0; j < 3; ++j) s.F[1 + j] = Uc[1 + j] * vtd + (j == d ? pstar : R(0)) - bl[j] * Bd * iW;
-  s.F[4] = Uc[4] * vtd + pstar * v[d] - ab0 * Bd * iW;
+  s.F[4] = Uc[4] * vtd + pstar * vd - ab0 * Bd * iW;
 #pragma unroll
   for (int k = 0; k < 3; ++k) s.F[5 + k] = B[k] * vtd - Bd * vt[k] * ia;
 #pragma unroll
@@ -325,7 +389,6 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   const R cs2 = gamma_eos * pgas / rhoh;
   const R va2 = b2 / (rhoh + b2);
   const R c2 = va2 + cs2 * (R(1) - va2);
-  const R vd = v[d];
   R one_v2, one_c2, one_v2c2;  // 1 - v^2, 1 - c^2 and 1 - v^2 c^2
   if constexpr (sizeof(R) == 4) {
     // float faces: 1 - v^2 = 1/W^2, 1 - c^2 = (1 - vA^2)(1 - cs^2) with 1 - vA^2 = rho h/(rho h + b^2), and
@@ -339,13 +402,14 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
     one_c2 = R(1) - c2;
     one_v2c2 = R(1) - v2 * c2;
   }
-  R disc = one_v2 * (m.gamu[sym3(d, d)] * one_v2c2 - vd * vd * one_c2);
+  R disc = one_v2 * (sel3(d, m.gamu[0], m.gamu[3], m.gamu[5]) * one_v2c2 - vd * vd * one_c2);
   disc = disc > R(0) ? disc : R(0);
   const R pre = m.alpha / one_v2c2;
   const R sq = sqrt(c2 * disc);
   const R base = vd * one_c2;
-  s.lp = pre * (base + sq) - m.beta[d];
-  s.lm = pre * (base - sq) - m.beta[d];
+  const R bd = sel3(d, m.beta[0], m.beta[1], m.beta[2]);
+  s.lp = pre * (base + sq) - bd;
+  s.lm = pre * (base - sq) - bd;
 }
 
 // Hydro part of the densitized conserved vector only (used after floors).
@@ -1040,8 +1104,8 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
 // The floors of apply_floors_fr on float primitives (the mixed form's storage type), with the float metric
 // and radius factor.
 __device__ __forceinline__ int apply_floors_f(const DevParams& p, const float gam[6], float fr, float P[NV]) {
-  const float rho_flr = (float)p.rho_floor0 * fr;
-  const float eps_flr = (float)p.eps_floor0 * fr;
+  const float rho_flr = p.frho_floor0 * fr;
+  const float eps_flr = p.feps_floor0 * fr;
   int st = 0;
   if (!(P[0] >= rho_flr)) {
     P[0] = rho_flr;
@@ -1055,7 +1119,7 @@ __device__ __forceinline__ int apply_floors_f(const DevParams& p, const float ga
   float utl[3];
   lower3(gam, ut, utl);
   const float usq = ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2];
-  const float wm2 = (float)p.w_max2;
+  const float wm2 = p.fw_max2;
   if (1.f + usq > wm2) {  // W = sqrt(1 + u^2) > w_max
     const float s = sqrtf((wm2 - 1.f) / usq);
     P[1] *= s;

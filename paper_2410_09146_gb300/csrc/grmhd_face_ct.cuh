@@ -26,8 +26,8 @@ __global__ void __launch_bounds__(128) k_emf_cc(const T* __restrict__ P, R* __re
     const int i = (int)(t % ex) - 1, j = (int)((t / ex) % ey) - 1, k = (int)(t / ((long long)ex * ey)) - 1;
     const long long g = gidx(p, i, j, k);
     Metric<R> m;
-    metric_at<R, METRIC>(p, R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
-                         R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2]), m);
+    metric_at<R, METRIC>(p, par<R>(p.x0[0], p.fx0[0]) + (R(i) + R(0.5)) * par<R>(p.dx[0], p.fdx[0]), par<R>(p.x0[1], p.fx0[1]) + (R(j) + R(0.5)) * par<R>(p.dx[1], p.fdx[1]),
+                         par<R>(p.x0[2], p.fx0[2]) + (R(k) + R(0.5)) * par<R>(p.dx[2], p.fdx[2]), m);
     R ut[3], B[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {

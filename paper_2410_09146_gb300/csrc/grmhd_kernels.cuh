@@ -34,7 +34,7 @@ __global__ void k_ghost_periodic(T* __restrict__ P, DevParams p) {
     const int si = ((i % p.nx) + p.nx) % p.nx, sj = ((j % p.ny) + p.ny) % p.ny, sk = ((k % p.nz) + p.nz) % p.nz;
     const long long src = gidx(p, si, sj, sk);
 #pragma unroll
-    for (int q = 0; q < NVAR; ++q) P[q * n + t] = P[q * n + src];
+    for (int q = 0; q < NVAR; ++q) STC(P, q * n + t, NVAR * n, LDC(P, q * n + src, NVAR * n));
   }
 }
 
@@ -52,28 +52,31 @@ template <class R, int METRIC>
 __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, int k, R PL[NV], R PR[NV],
                                        R Fh[NV]) {
   // face centre, in the flux arithmetic type
-  R xf[3] = {R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]), R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]),
-             R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2])};
+  R xf[3] = {par<R>(p.x0[0], p.fx0[0]) + (R(i) + R(0.5)) * par<R>(p.dx[0], p.fdx[0]), par<R>(p.x0[1], p.fx0[1]) + (R(j) + R(0.5)) * par<R>(p.dx[1], p.fdx[1]),
+             par<R>(p.x0[2], p.fx0[2]) + (R(k) + R(0.5)) * par<R>(p.dx[2], p.fdx[2])};
   const int cd = d == 0 ? i : (d == 1 ? j : k);
-  xf[d] = R(p.x0[d]) + R(cd) * R(p.dx[d]);
+  const R xd = sel3(d, par<R>(p.x0[0], p.fx0[0]), par<R>(p.x0[1], p.fx0[1]), par<R>(p.x0[2], p.fx0[2])) +
+               R(cd) * sel3(d, par<R>(p.dx[0], p.fdx[0]), par<R>(p.dx[1], p.fdx[1]), par<R>(p.dx[2], p.fdx[2]));
+  if (d == 0) xf[0] = xd; else if (d == 1) xf[1] = xd; else xf[2] = xd;
   Metric<R> m;
   R rks = R(1);
   metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m, &rks);
-  const R fr = METRIC == KERR_SCHILD ? (p.floor_r_exp == 2.0 ? R(1) / (rks * rks) : R(pow((double)rks, -p.floor_r_exp)))
+  const R fr = METRIC == KERR_SCHILD ? (p.floor_r2 ? R(1) / (rks * rks) : R(pow((double)rks, -p.floor_r_exp)))
                                      : R(1);
-  const R rho_flr = R(p.rho_floor0) * fr, eps_flr = R(p.eps_floor0) * fr;
+  const R rho_flr = par<R>(p.rho_floor0, p.frho_floor0) * fr, eps_flr = par<R>(p.eps_floor0, p.feps_floor0) * fr;
   if (!(PL[0] >= rho_flr)) PL[0] = rho_flr;
   if (!(PR[0] >= rho_flr)) PR[0] = rho_flr;
   if (!(PL[4] >= PL[0] * eps_flr)) PL[4] = PL[0] * eps_flr;
   if (!(PR[4] >= PR[0] * eps_flr)) PR[4] = PR[0] * eps_flr;
   if (p.bface != nullptr) {
-    const R bn = R(p.bface[d * p.gsize + gidx(p, i, j, k)]) / m.sqrtgam;
-    PL[5 + d] = bn;
-    PR[5 + d] = bn;
+    const R bn = R(LDC(p.bface, d * p.gsize + gidx(p, i, j, k), 3 * p.gsize)) / m.sqrtgam;
+    if (d == 0) { PL[5] = bn; PR[5] = bn; }
+    else if (d == 1) { PL[6] = bn; PR[6] = bn; }
+    else { PL[7] = bn; PR[7] = bn; }
   }
   FaceSide<R> L, Rs;
-  prim_to_face<R>(PL, m, d, R(p.gamma_eos), L);
-  prim_to_face<R>(PR, m, d, R(p.gamma_eos), Rs);
+  prim_to_face<R>(PL, m, d, par<R>(p.gamma_eos, p.fgamma), L);
+  prim_to_face<R>(PR, m, d, par<R>(p.gamma_eos, p.fgamma), Rs);
   return riemann_flux<R>(p.riemann, L, Rs, Fh);
 }
 
@@ -90,16 +93,16 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
   const int k = (int)(t / ((long long)ex * ey)) + (d == 2 ? 0 : -1);
   const long long g = gidx(p, i, j, k);
   R PL[NV], PR[NV];
-  const R eps = R(p.weno_eps);
+  const R eps = par<R>(p.weno_eps, p.fweno_eps);
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    const T* Pq = P + q * p.gsize + g;
-    const R fm3 = cell_centric(RECON) ? R(Pq[-3 * stride]) : R(0);
-    const R fm2 = RECON != RECON_CONSTANT ? R(Pq[-2 * stride]) : R(0);
-    const R fm1 = R(Pq[-stride]);
-    const R f0 = R(Pq[0]);
-    const R fp1 = RECON != RECON_CONSTANT ? R(Pq[stride]) : R(0);
-    const R fp2 = cell_centric(RECON) ? R(Pq[2 * stride]) : R(0);
+    const long long c0 = q * p.gsize + g, PN = NV * p.gsize;
+    const R fm3 = cell_centric(RECON) ? R(LDC(P, c0 - 3 * stride, PN)) : R(0);
+    const R fm2 = RECON != RECON_CONSTANT ? R(LDC(P, c0 - 2 * stride, PN)) : R(0);
+    const R fm1 = R(LDC(P, c0 - stride, PN));
+    const R f0 = R(LDC(P, c0, PN));
+    const R fp1 = RECON != RECON_CONSTANT ? R(LDC(P, c0 + stride, PN)) : R(0);
+    const R fp2 = cell_centric(RECON) ? R(LDC(P, c0 + 2 * stride, PN)) : R(0);
     R qm, qp;
     recon_cell<R, RECON>(fm3, fm2, fm1, f0, fp1, eps, qm, qp);  // cell c - e_d
     PL[q] = qp;
@@ -109,7 +112,7 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
   R Fh[NV];
   const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
 #pragma unroll
-  for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
+  for (int q = 0; q < NV; ++q) STC(F, q * p.gsize + g, NV * p.gsize, Fh[q]);
   const bool interior = (d == 0 || (i >= 0 && i < p.nx)) && (d == 1 || (j >= 0 && j < p.ny)) &&
                         (d == 2 || (k >= 0 && k < p.nz));
   return interior ? cm : R(0);
@@ -162,7 +165,7 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   const int na = d == 0 ? p.ny : p.nx;
   const int nb = d == 2 ? p.ny : p.nz;
   const long long sd = d == 0 ? 1 : (d == 1 ? (long long)p.gx : (long long)p.gx * p.gy);
-  const R eps = R(p.weno_eps);
+  const R eps = par<R>(p.weno_eps, p.fweno_eps);
   const int a = (int)(t % (na + 2)) - 1;
   const long long rest = t / (na + 2);
   const int b = (int)(rest % (nb + 2)) - 1;
@@ -184,9 +187,8 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   R w[NV][5];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    const T* Pq = P + q * p.gsize + g;
 #pragma unroll
-    for (int s = 0; s < 5; ++s) w[q][s] = R(Pq[(s - 3) * sd]);
+    for (int s = 0; s < 5; ++s) w[q][s] = R(LDC(P, q * p.gsize + g + (s - 3) * sd, NV * p.gsize));
   }
   R PL[NV];
 #pragma unroll
@@ -203,7 +205,7 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
     for (int q = 0; q < NV; ++q) {
 #pragma unroll
       for (int s = 0; s < 4; ++s) w[q][s] = w[q][s + 1];
-      w[q][4] = R(P[q * p.gsize + g + 2 * sd]);
+      w[q][4] = R(LDC(P, q * p.gsize + g + 2 * sd, NV * p.gsize));
       R qm, qp;
       recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
       PR[q] = qm;
@@ -213,7 +215,7 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
     const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      F[q * p.gsize + g] = Fh[q];
+      STC(F, q * p.gsize + g, NV * p.gsize, Fh[q]);
       PL[q] = QP[q];
     }
     if (inner_t && cm > cm_run) cm_run = cm;
@@ -238,15 +240,14 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
   const long long row = live ? seq / (p.nx + 2) : 0;
   const int c = live ? (int)(seq % (p.nx + 2)) - 1 : 0;
   const int j = (int)(row % (p.ny + 2)) - 1, k = (int)(row / (p.ny + 2)) - 1;
-  const R eps = R(p.weno_eps);
+  const R eps = par<R>(p.weno_eps, p.fweno_eps);
   const long long g = gidx(p, c, j, k);
   R qm[NV], qp[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    const T* Pq = P + q * p.gsize + g;
     R f[5];
 #pragma unroll
-    for (int s = 0; s < 5; ++s) f[s] = live ? R(Pq[s - 2]) : R(0);
+    for (int s = 0; s < 5; ++s) f[s] = live ? R(LDC(P, q * p.gsize + g + s - 2, NV * p.gsize)) : R(0);
     recon_cell<R, RECON>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
   }
   R PL[NV];
@@ -256,7 +257,7 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
   R Fh[NV];
   const R cm = face_flux<R, METRIC>(p, 0, c, j, k, PL, qm, Fh);
 #pragma unroll
-  for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
+  for (int q = 0; q < NV; ++q) STC(F, q * p.gsize + g, NV * p.gsize, Fh[q]);
   return (j >= 0 && j < p.ny && k >= 0 && k < p.nz) ? cm : R(0);
 }
 
@@ -280,88 +281,6 @@ __global__ void __launch_bounds__(128, kFluxMinBlocks<R>) k_flux_cc(const T* __r
   if (track_speed) block_max_to<R>(cm_local, ms + d);
 }
 
-// Shared-memory tiled fluxes of direction d = 1, 2 for the five-point reconstructions (WENO5-Z-AOAH, MP5):
-// a CTA takes FLUX_TILE_T consecutive x positions (transverse position a in [-1, nx]) at one position b of the
-// other transverse direction, and FLUX_TILE_D faces along d. It stages the primitives of the tile with its
-// halo along d (FLUX_TILE_D + 5 cells per column) in shared memory with x-coalesced loads, reconstructs each
-// of the FLUX_TILE_D + 1 cells it needs once (both faces, into shared memory), then evaluates every face from
-// the plus side of the cell below and the minus side of the cell above (face_flux). One thread per cell and
-// then per face: no per-thread window in registers. Max |lambda| of the interior faces goes to ms[d].
-constexpr int FLUX_TILE_T = 32;
-constexpr int FLUX_TILE_D = 16;
-constexpr int FLUX_TILE_TP = FLUX_TILE_T + 1;  // padded row (conflict-free column access)
-constexpr int FLUX_TILE_THREADS = 256;
-
-template <class R>
-constexpr size_t flux_tile_smem() {
-  return sizeof(R) * (size_t)NV * FLUX_TILE_TP * ((FLUX_TILE_D + 5) + 2 * (FLUX_TILE_D + 1));
-}
-
-template <class R, class T, int METRIC, int RECON>
-__global__ void __launch_bounds__(FLUX_TILE_THREADS) k_flux_tile(const T* __restrict__ P, R* __restrict__ F,
-                                                                 unsigned long long* __restrict__ ms, DevParams p,
-                                                                 int d, int track_speed) {
-  extern __shared__ __align__(16) unsigned char flux_smem[];
-  constexpr int CW = FLUX_TILE_D + 5;   // cells staged per column
-  constexpr int CR = FLUX_TILE_D + 1;   // cells reconstructed per column
-  R* sP = (R*)flux_smem;                               // [NV][CW][TP]
-  R* sQ = sP + (size_t)NV * CW * FLUX_TILE_TP;         // [2][NV][CR][TP]: minus side, plus side
-  const int nd = d == 1 ? p.ny : p.nz;
-  const int na = p.nx, nb = d == 1 ? p.nz : p.ny;
-  const int a0 = (int)blockIdx.x * FLUX_TILE_T - 1;
-  const int b = (int)blockIdx.y - 1;
-  const int f0 = (int)blockIdx.z * FLUX_TILE_D;
-  const long long sd = d == 1 ? (long long)p.gx : (long long)p.gx * p.gy;
-  // (a, c along d) -> ghosted index
-  auto cell = [&](int a, int c) { return d == 1 ? gidx(p, a, c, b) : gidx(p, a, b, c); };
-  // stage cells f0 - 3 .. f0 + FLUX_TILE_D + 1 (only those up to nd + 2 are needed: the last face is nd)
-  for (int e = threadIdx.x; e < NV * CW * FLUX_TILE_T; e += FLUX_TILE_THREADS) {
-    const int ct = e % FLUX_TILE_T, rest = e / FLUX_TILE_T;
-    const int cd = rest % CW, q = rest / CW;
-    const int a = a0 + ct, c = f0 - 3 + cd;
-    if (a <= na && c <= nd + 2) sP[(q * CW + cd) * FLUX_TILE_TP + ct] = R(P[q * p.gsize + cell(a, c)]);
-  }
-  __syncthreads();
-  const R eps = R(p.weno_eps);
-  // reconstruct cells f0 - 1 .. f0 + FLUX_TILE_D - 1 (those up to nd)
-  for (int e = threadIdx.x; e < CR * FLUX_TILE_T; e += FLUX_TILE_THREADS) {
-    const int ct = e % FLUX_TILE_T, cc = e / FLUX_TILE_T;
-    if (a0 + ct > na || f0 - 1 + cc > nd) continue;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const R* s = sP + (q * CW + cc) * FLUX_TILE_TP + ct;
-      R qm, qp;
-      recon_cell<R, RECON>(s[0], s[FLUX_TILE_TP], s[2 * FLUX_TILE_TP], s[3 * FLUX_TILE_TP], s[4 * FLUX_TILE_TP], eps,
-                           qm, qp);
-      sQ[(q * CR + cc) * FLUX_TILE_TP + ct] = qm;
-      sQ[((NV + q) * CR + cc) * FLUX_TILE_TP + ct] = qp;
-    }
-  }
-  __syncthreads();
-  // faces f0 .. f0 + FLUX_TILE_D - 1 (those up to nd): face f between cells f - 1 and f
-  R cm_local = R(0);
-  for (int e = threadIdx.x; e < FLUX_TILE_D * FLUX_TILE_T; e += FLUX_TILE_THREADS) {
-    const int ct = e % FLUX_TILE_T, ff = e / FLUX_TILE_T;
-    const int a = a0 + ct, f = f0 + ff;
-    if (a > na || f > nd) continue;
-    R PL[NV], PR[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      PL[q] = sQ[((NV + q) * CR + ff) * FLUX_TILE_TP + ct];
-      PR[q] = sQ[(q * CR + ff + 1) * FLUX_TILE_TP + ct];
-    }
-    R Fh[NV];
-    const int i = a, j = d == 1 ? f : b, k = d == 1 ? b : f;
-    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
-    const long long g = cell(a, f);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) F[q * p.gsize + g] = Fh[q];
-    if (a >= 0 && a < na && b >= 0 && b < nb && cm > cm_local) cm_local = cm;
-  }
-  (void)sd;
-  if (track_speed) block_max_to<R>(cm_local, ms + d);
-}
-
 // a7: dt = cfl / max_d(max|lambda_d| / dx_d)
 static __global__ void k_finalize_dt(const unsigned long long* ms, double* dt, DevParams p) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -382,11 +301,14 @@ __device__ __forceinline__ void emf_edge(const DevParams& p, const R* __restrict
   const int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
   const long long g = gidx(p, i, j, k);
   if (k < p.nz)  // Omega_z(fi = i, fj = j, k)
-    E[2 * G + g] = R(0.25) * (Fy[5 * G + g - 1] + Fy[5 * G + g] - Fx[6 * G + g - sy] - Fx[6 * G + g]);
+    STC(E, 2 * G + g, 3 * G, R(0.25) * (LDC(Fy, 5 * G + g - 1, 8 * G) + LDC(Fy, 5 * G + g, 8 * G) -
+                                       LDC(Fx, 6 * G + g - sy, 8 * G) - LDC(Fx, 6 * G + g, 8 * G)));
   if (i < p.nx)  // Omega_x(i, fj = j, fk = k)
-    E[0 * G + g] = R(0.25) * (Fz[6 * G + g - sy] + Fz[6 * G + g] - Fy[7 * G + g - sz] - Fy[7 * G + g]);
+    STC(E, 0 * G + g, 3 * G, R(0.25) * (LDC(Fz, 6 * G + g - sy, 8 * G) + LDC(Fz, 6 * G + g, 8 * G) -
+                                       LDC(Fy, 7 * G + g - sz, 8 * G) - LDC(Fy, 7 * G + g, 8 * G)));
   if (j < p.ny)  // Omega_y(fi = i, j, fk = k)
-    E[1 * G + g] = R(0.25) * (Fx[7 * G + g - sz] + Fx[7 * G + g] - Fz[5 * G + g - 1] - Fz[5 * G + g]);
+    STC(E, 1 * G + g, 3 * G, R(0.25) * (LDC(Fx, 7 * G + g - sz, 8 * G) + LDC(Fx, 7 * G + g, 8 * G) -
+                                       LDC(Fz, 5 * G + g - 1, 8 * G) - LDC(Fz, 5 * G + g, 8 * G)));
 }
 
 template <class R>
@@ -406,7 +328,7 @@ __global__ void k_emf(const R* __restrict__ Fx, const R* __restrict__ Fy, const 
 template <class R>
 __device__ __forceinline__ void ks_sources(const DevParams& p, R x, R y, R z, const R P[NV], const Metric<R>& m,
                                            R S[5]) {
-  const R a = R(p.a), M = R(p.M);
+  const R a = par<R>(p.a, p.fa), M = par<R>(p.M, p.fM);
   R r, r2, f, l[3];
   ks_core<R>(x, y, z, a, M, r, r2, f, l);
   const R xs[3] = {x, y, z};
@@ -449,7 +371,7 @@ __device__ __forceinline__ void ks_sources(const DevParams& p, R x, R y, R z, co
     uc[1 + i] = W * ia * vt[i];
     bc[1 + i] = B[i] * iW + b0 * vt[i];
   }
-  const R pg = (R(p.gamma_eos) - R(1)) * P[4];
+  const R pg = (par<R>(p.gamma_eos, p.fgamma) - R(1)) * P[4];
   const R w = P[0] + P[4] + pg + b2;
   const R pt = pg + R(0.5) * b2;
   // g^{mu nu}
@@ -508,6 +430,12 @@ template <int METRIC>
 __device__ __forceinline__ void cell_metric(const DevParams& p, long long t, double xc, double yc, double zc,
                                             Metric<double>& m, double& isg, double& fr) {
   if (METRIC == KERR_SCHILD && p.geo != nullptr) {
+#ifdef GRMHD_BOUNDS_CHECK
+    if (t < 0 || t >= p.isize) {  // every cache entry is a multiple of isize away: one check covers them
+      bounds_fault(p, __LINE__, t);
+      t = 0;
+    }
+#endif
     geo_load(p.geo, p.isize, t, m, isg, fr);
   } else {
     double r;
@@ -601,32 +529,38 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
   double Un[NV];
   if (a.g0 == 0.0 && a.g1 == 1.0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) Un[q] = a.Ucur[q * n + t] + bdt * (double)L[q];
+    for (int q = 0; q < NV; ++q) Un[q] = LDC(a.Ucur, q * n + t, NV * n) + bdt * (double)L[q];
   } else {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double u = a.g1 * a.Ucur[q * n + t];
-      if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
+      double u = a.g1 * LDC(a.Ucur, q * n + t, NV * n);
+      if (a.g0 != 0.0) u += a.g0 * LDC(a.U0, q * n + t, NV * n);
       Un[q] = u + bdt * (double)L[q];
     }
   }
   if (a.bface_new != nullptr) {
     // face-centred CT: the cell's densitized field is the mean of its two advanced faces of each direction
     const double* bn = a.bface_new;
-    Un[5] = 0.5 * (bn[g] + bn[g + 1]);
-    Un[6] = 0.5 * (bn[G + g] + bn[G + g + sy]);
-    Un[7] = 0.5 * (bn[2 * G + g] + bn[2 * G + g + sz]);
+    Un[5] = 0.5 * (LDC(bn, g, 3 * G) + LDC(bn, g + 1, 3 * G));
+    Un[6] = 0.5 * (LDC(bn, G + g, 3 * G) + LDC(bn, G + g + sy, 3 * G));
+    Un[7] = 0.5 * (LDC(bn, 2 * G + g, 3 * G) + LDC(bn, 2 * G + g + sz, 3 * G));
   }
   Metric<double> m;
   double isg;
   if (METRIC == KERR_SCHILD && p.geo != nullptr) {
+#ifdef GRMHD_BOUNDS_CHECK
+    if (t < 0 || t >= n) {
+      bounds_fault(p, __LINE__, t);
+      t = 0;
+    }
+#endif
     geo_load_c2p(p.geo, n, t, m, isg);
   } else {
     metric_at<double, METRIC>(p, xc, yc, zc, m);
     isg = 1.0 / m.sqrtgam;
   }
   // warm start mu = 1/(h W) of the current primitives, in float (it only seeds the float phase)
-  const float mu0 = mu_of_prims<float>(Pr, mr.gam, (float)p.gamma_eos);
+  const float mu0 = mu_of_prims<float>(Pr, mr.gam, p.fgamma);
   float Pn[NV];
   int iters;
   double mu_r;
@@ -634,21 +568,21 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
   if (st == C2P_DEFERRED) {
     // finished by deferred_cell: keep P (the warm start), store the new conserved state
 #pragma unroll
-    for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+    for (int q = 0; q < NV; ++q) STC(a.Unew, q * n + t, NV * n, Un[q]);
     const unsigned int slot = atomicAdd(a.wl_count, 1u);
-    a.worklist[slot] = (int)(wl_tag + t);
-    a.wl_mu[slot] = mu_r;
+    STC(a.worklist, slot, n, (int)(wl_tag + t));
+    STC(a.wl_mu, slot, n, mu_r);
     cs.it_sum += iters;
     return;
   }
-  const float fr = METRIC == KERR_SCHILD ? (p.floor_r_exp == 2.0 ? 1.f / (rf * rf) : powf(rf, -(float)p.floor_r_exp))
+  const float fr = METRIC == KERR_SCHILD ? (p.floor_r2 ? 1.f / (rf * rf) : powf(rf, -(float)p.floor_r_exp))
                                          : 1.f;
   st |= apply_floors_f(p, mr.gam, fr, Pn);
   if (st) {
     if (a.floorlist) {
       // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
       // hold only such cells
-      a.floorlist[atomicAdd(a.fl_count, 1u)] = (int)(wl_tag + t);
+      STC(a.floorlist, atomicAdd(a.fl_count, 1u), n, (int)(wl_tag + t));
     } else {
       Metric<double> mf;
       metric_at<double, METRIC>(p, xc, yc, zc, mf);
@@ -661,10 +595,10 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
     }
   }
 #pragma unroll
-  for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+  for (int q = 0; q < NV; ++q) STC(a.Unew, q * n + t, NV * n, Un[q]);
 #pragma unroll
-  for (int q = 0; q < NV; ++q) P[q * G + g] = Pn[q];
-  a.status[t] = (uint8_t)st;
+  for (int q = 0; q < NV; ++q) STC(P, q * G + g, NV * G, Pn[q]);
+  STC(a.status, t, n, (uint8_t)st);
   cs.add(st, iters);
 }
 
@@ -686,17 +620,17 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   const double yc = p.x0[1] + (j + 0.5) * p.dx[1];
   const double zc = p.x0[2] + (k + 0.5) * p.dx[2];
   // the cell centre in the source / warm-start precision, formed in that precision (no conversion from double)
-  const R xr = R(p.x0[0]) + (R(i) + R(0.5)) * R(p.dx[0]);
-  const R yr = R(p.x0[1]) + (R(j) + R(0.5)) * R(p.dx[1]);
-  const R zr = R(p.x0[2]) + (R(k) + R(0.5)) * R(p.dx[2]);
+  const R xr = par<R>(p.x0[0], p.fx0[0]) + (R(i) + R(0.5)) * par<R>(p.dx[0], p.fdx[0]);
+  const R yr = par<R>(p.x0[1], p.fx0[1]) + (R(j) + R(0.5)) * par<R>(p.dx[1], p.fdx[1]);
+  const R zr = par<R>(p.x0[2], p.fx0[2]) + (R(k) + R(0.5)) * par<R>(p.dx[2], p.fdx[2]);
   T Pt[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) Pt[q] = P[q * G + g];
+  for (int q = 0; q < NV; ++q) Pt[q] = LDC(P, q * G + g, NV * G);
   R L[NV];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const R div = (Fx[q * G + g + 1] - Fx[q * G + g]) * R(p.idx[0]) + (Fy[q * G + g + sy] - Fy[q * G + g]) * R(p.idx[1]) +
-                  (Fz[q * G + g + sz] - Fz[q * G + g]) * R(p.idx[2]);
+    const R div = (LDC(Fx, q * G + g + 1, NV * G) - LDC(Fx, q * G + g, NV * G)) * par<R>(p.idx[0], p.fidx[0]) + (LDC(Fy, q * G + g + sy, NV * G) - LDC(Fy, q * G + g, NV * G)) * par<R>(p.idx[1], p.fidx[1]) +
+                  (LDC(Fz, q * G + g + sz, NV * G) - LDC(Fz, q * G + g, NV * G)) * par<R>(p.idx[2], p.fidx[2]);
     L[q] = -div;
   }
   if (a.bface_new == nullptr) {
@@ -705,15 +639,15 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
     const R* Ez = E + 2 * G;
     const R h = R(0.5);
     // CT fluxes of B (normal components vanish)
-    const R FyBx_p = h * (Ez[g + sy] + Ez[g + sy + 1]), FyBx_m = h * (Ez[g] + Ez[g + 1]);
-    const R FzBx_p = -h * (Ey[g + sz] + Ey[g + sz + 1]), FzBx_m = -h * (Ey[g] + Ey[g + 1]);
-    const R FxBy_p = -h * (Ez[g + 1] + Ez[g + 1 + sy]), FxBy_m = -h * (Ez[g] + Ez[g + sy]);
-    const R FzBy_p = h * (Ex[g + sz] + Ex[g + sz + sy]), FzBy_m = h * (Ex[g] + Ex[g + sy]);
-    const R FxBz_p = h * (Ey[g + 1] + Ey[g + 1 + sz]), FxBz_m = h * (Ey[g] + Ey[g + sz]);
-    const R FyBz_p = -h * (Ex[g + sy] + Ex[g + sy + sz]), FyBz_m = -h * (Ex[g] + Ex[g + sz]);
-    L[5] = -((FyBx_p - FyBx_m) * R(p.idx[1]) + (FzBx_p - FzBx_m) * R(p.idx[2]));
-    L[6] = -((FxBy_p - FxBy_m) * R(p.idx[0]) + (FzBy_p - FzBy_m) * R(p.idx[2]));
-    L[7] = -((FxBz_p - FxBz_m) * R(p.idx[0]) + (FyBz_p - FyBz_m) * R(p.idx[1]));
+    const R FyBx_p = h * (LDC(Ez, g + sy, G) + LDC(Ez, g + sy + 1, G)), FyBx_m = h * (LDC(Ez, g, G) + LDC(Ez, g + 1, G));
+    const R FzBx_p = -h * (LDC(Ey, g + sz, G) + LDC(Ey, g + sz + 1, G)), FzBx_m = -h * (LDC(Ey, g, G) + LDC(Ey, g + 1, G));
+    const R FxBy_p = -h * (LDC(Ez, g + 1, G) + LDC(Ez, g + 1 + sy, G)), FxBy_m = -h * (LDC(Ez, g, G) + LDC(Ez, g + sy, G));
+    const R FzBy_p = h * (LDC(Ex, g + sz, G) + LDC(Ex, g + sz + sy, G)), FzBy_m = h * (LDC(Ex, g, G) + LDC(Ex, g + sy, G));
+    const R FxBz_p = h * (LDC(Ey, g + 1, G) + LDC(Ey, g + 1 + sz, G)), FxBz_m = h * (LDC(Ey, g, G) + LDC(Ey, g + sz, G));
+    const R FyBz_p = -h * (LDC(Ex, g + sy, G) + LDC(Ex, g + sy + sz, G)), FyBz_m = -h * (LDC(Ex, g, G) + LDC(Ex, g + sz, G));
+    L[5] = -((FyBx_p - FyBx_m) * par<R>(p.idx[1], p.fidx[1]) + (FzBx_p - FzBx_m) * par<R>(p.idx[2], p.fidx[2]));
+    L[6] = -((FxBy_p - FxBy_m) * par<R>(p.idx[0], p.fidx[0]) + (FzBy_p - FzBy_m) * par<R>(p.idx[2], p.fidx[2]));
+    L[7] = -((FxBz_p - FxBz_m) * par<R>(p.idx[0], p.fidx[0]) + (FyBz_p - FyBz_m) * par<R>(p.idx[1], p.fidx[1]));
   } else {
     L[5] = L[6] = L[7] = R(0);  // the field comes from the advanced faces below
   }
@@ -743,22 +677,22 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
     double Un[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double u = a.g1 * a.Ucur[q * n + t];
-      if (a.g0 != 0.0) u += a.g0 * a.U0[q * n + t];
+      double u = a.g1 * LDC(a.Ucur, q * n + t, NV * n);
+      if (a.g0 != 0.0) u += a.g0 * LDC(a.U0, q * n + t, NV * n);
       Un[q] = u + bdt * (double)L[q];
     }
     if (a.bface_new != nullptr) {
       // face-centred CT: the cell's densitized field is the mean of its two advanced faces of each direction
       const double* bn = a.bface_new;
-      Un[5] = 0.5 * (bn[g] + bn[g + 1]);
-      Un[6] = 0.5 * (bn[G + g] + bn[G + g + sy]);
-      Un[7] = 0.5 * (bn[2 * G + g] + bn[2 * G + g + sz]);
+      Un[5] = 0.5 * (LDC(bn, g, 3 * G) + LDC(bn, g + 1, 3 * G));
+      Un[6] = 0.5 * (LDC(bn, G + g, 3 * G) + LDC(bn, G + g + sy, 3 * G));
+      Un[7] = 0.5 * (LDC(bn, 2 * G + g, 3 * G) + LDC(bn, 2 * G + g + sz, 3 * G));
     }
     // a6: con2prim on the undensitized state, warm-started from the current primitives
     double Uc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
-    const double mu0 = (double)mu_of_prims<R>(Pr, mr.gam, R(p.gamma_eos));
+    const double mu0 = (double)mu_of_prims<R>(Pr, mr.gam, par<R>(p.gamma_eos, p.fgamma));
     double Pn[NV];
     int iters;
     int st = con2prim<double>(p, m, Uc, mu0, Pn, iters);
@@ -767,7 +701,7 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
       if (a.floorlist) {
         // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
         // hold only such cells (a few percent of cells, but present in most warps of this pass)
-        a.floorlist[atomicAdd(a.fl_count, 1u)] = (int)(wl_tag + t);
+        STC(a.floorlist, atomicAdd(a.fl_count, 1u), n, (int)(wl_tag + t));
       } else {
         double U5[5];
         prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
@@ -776,16 +710,22 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
       }
     }
 #pragma unroll
-    for (int q = 0; q < NV; ++q) a.Unew[q * n + t] = Un[q];
+    for (int q = 0; q < NV; ++q) STC(a.Unew, q * n + t, NV * n, Un[q]);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
-    a.status[t] = (uint8_t)st;
+    for (int q = 0; q < NV; ++q) STC(P, q * G + g, NV * G, (T)Pn[q]);
+    STC(a.status, t, n, (uint8_t)st);
     cs.add(st, iters);
   }
 }
 
+// Resident CTAs per SM the update kernel is compiled for: the mixed form's (double solve, ~190 registers
+// unbounded) is latency-bound at two CTAs per SM; held to four (128 registers, no spills) it runs 6.7 ms per
+// 256^3 stage against 8.45 (two) and 7.62 (three); the FP64 form keeps its registers.
+template <class T>
+constexpr int kUpdateMinBlocks = sizeof(T) == 4 ? 4 : 1;
+
 template <int METRIC, class R, class T>
-__global__ void __launch_bounds__(128) k_update(T* __restrict__ P, const R* __restrict__ Fx,
+__global__ void __launch_bounds__(128, kUpdateMinBlocks<T>) k_update(T* __restrict__ P, const R* __restrict__ Fx,
                                                 const R* __restrict__ Fy, const R* __restrict__ Fz,
                                                 const R* __restrict__ E, StageArgs a, DevParams p) {
   const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
@@ -811,8 +751,8 @@ __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict_
   double Pc[NV], Un[NV], Uc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
-    Pc[q] = (double)P[q * G + g];
-    Un[q] = a.Unew[q * n + t];
+    Pc[q] = (double)LDC(P, q * G + g, NV * G);
+    Un[q] = LDC(a.Unew, q * n + t, NV * n);
   }
 #pragma unroll
   for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
@@ -825,11 +765,11 @@ __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict_
     double U5[5];
     prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) a.Unew[q * n + t] = U5[q];
+    for (int q = 0; q < 5; ++q) STC(a.Unew, q * n + t, NV * n, U5[q]);
   }
 #pragma unroll
-  for (int q = 0; q < NV; ++q) P[q * G + g] = (T)Pn[q];
-  a.status[t] = (uint8_t)st;
+  for (int q = 0; q < NV; ++q) STC(P, q * G + g, NV * G, (T)Pn[q]);
+  STC(a.status, t, n, (uint8_t)st);
   cs.add(st, iters);
 }
 
@@ -846,17 +786,17 @@ __device__ __forceinline__ void floor_cell(const DevParams& p, const T* __restri
                       p.x0[2] + (k + 0.5) * p.dx[2], m, isg, fr);
   double Pn[NV], U5[5];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) Pn[q] = (double)P[q * G + g];
+  for (int q = 0; q < NV; ++q) Pn[q] = (double)LDC(P, q * G + g, NV * G);
   prim_to_cons5<double>(Pn, m, p.gamma_eos, U5);
 #pragma unroll
-  for (int q = 0; q < 5; ++q) a.Unew[q * n + t] = U5[q];
+  for (int q = 0; q < 5; ++q) STC(a.Unew, q * n + t, NV * n, U5[q]);
 }
 
 template <int METRIC, class T>
 __global__ void __launch_bounds__(128) k_update_floors(const T* __restrict__ P, StageArgs a, DevParams p) {
   const unsigned int cnt = *a.fl_count;
   for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x)
-    floor_cell<METRIC, T>(p, P, a, a.floorlist[w]);
+    floor_cell<METRIC, T>(p, P, a, LDC(a.floorlist, w, p.isize));
 }
 
 template <int METRIC, class T>
@@ -864,7 +804,7 @@ __global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, Stag
   const unsigned int cnt = *a.wl_count;
   CellStats cs;
   for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x)
-    deferred_cell<METRIC, T>(p, P, a, a.worklist[w], a.wl_mu[w], cs);
+    deferred_cell<METRIC, T>(p, P, a, LDC(a.worklist, w, p.isize), LDC(a.wl_mu, w, p.isize), cs);
   cs.flush(a.stats);
   if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
 }

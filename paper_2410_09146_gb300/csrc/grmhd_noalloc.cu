@@ -81,7 +81,7 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
     return fail(GRMHD_E_INVALID, msg);
   }
 
-  const DevParams d = dev_params(p);
+  DevParams d = dev_params(p);
 
   void* base = nullptr;
   cudaError_t e = scratch_address(&base);
@@ -90,6 +90,7 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
   unsigned long long* ms = (unsigned long long*)sc;
   double* dt_dev = (double*)(ms + 3);
   unsigned long long* stats = ms + 8;
+  d.fault = ms + 32;  // the bounds-check build's fault word (cleared below with the other scalars)
   double* F[3];
   for (int k = 0; k < 3; ++k) F[k] = (double*)(sc + kScalarBytes) + (size_t)k * 8 * d.gsize;
   double* E = (double*)(sc + kScalarBytes) + (size_t)24 * d.gsize;

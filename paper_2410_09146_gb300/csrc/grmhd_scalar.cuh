@@ -28,7 +28,7 @@ __device__ __forceinline__ void scalar_flux_run(const T* __restrict__ X, const R
                                                 const DevParams& p, int d, int u, int v, int c2) {
   const int n[3] = {p.nx, p.ny, p.nz};
   const long long st = d == 0 ? 1 : (d == 1 ? (long long)p.gx : (long long)p.gx * p.gy);
-  const R eps = R(p.weno_eps);
+  const R eps = par<R>(p.weno_eps, p.fweno_eps);
   int c[3], r;
   if (d == 0) { r = u; c[1] = v; c[2] = c2; c[0] = 0; }
   else if (d == 1) { c[0] = u; r = v; c[2] = c2; c[1] = 0; }
@@ -104,8 +104,8 @@ __device__ __forceinline__ void scalar_update_cell(T* __restrict__ X, const R* _
   const R* Fx = FX;
   const R* Fy = FX + G;
   const R* Fz = FX + 2 * G;
-  const R div = (Fx[g + 1] - Fx[g]) * R(p.idx[0]) + (Fy[g + sy] - Fy[g]) * R(p.idx[1]) +
-                (Fz[g + sz] - Fz[g]) * R(p.idx[2]);
+  const R div = (Fx[g + 1] - Fx[g]) * par<R>(p.idx[0], p.fidx[0]) + (Fy[g + sy] - Fy[g]) * par<R>(p.idx[1], p.fidx[1]) +
+                (Fz[g + sz] - Fz[g]) * par<R>(p.idx[2], p.fidx[2]);
   double u = a.g1 * DXcur[t];
   if (a.g0 != 0.0) u += a.g0 * DX0[t];
   const double dxn = u + bdt * (double)(-div);

@@ -103,6 +103,8 @@ def lib():
         L.grmhd_batch_set_mesh.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip]
         L.grmhd_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.grmhd_set_graph.argtypes = [vp, ctypes.c_int]
+        L.grmhd_batch_autotune_table.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         fp = ctypes.POINTER(ctypes.c_float)
         L.grmhd_mlp_workspace_bytes.argtypes = []
         L.grmhd_mlp_workspace_bytes.restype = ctypes.c_size_t
@@ -116,6 +118,7 @@ def lib():
         L.grmhd_p2c.argtypes = [vp, ctypes.c_longlong, vp, vp]
         L.grmhd_c2p_guess.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
         L.grmhd_max_speed.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        L.grmhd_bounds_fault.argtypes = [vp, ctypes.POINTER(ctypes.c_ulonglong)]
         L.grmhd_fp_peaks.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.grmhd_last_error.argtypes = [vp]
         L.grmhd_last_error.restype = ctypes.c_char_p
@@ -292,6 +295,28 @@ def grmhd_get_timing(ctx: int):
     return dict(zip(KERNEL_GROUPS, list(ms))), n.value
 
 
+def grmhd_bounds_fault(ctx: int):
+    """(fault word, built with checks) of the bounds-check build (see include/grmhd.h)."""
+    out = (ctypes.c_ulonglong * 2)()
+    _check(lib().grmhd_bounds_fault(ctypes.c_void_p(ctx), out), ctx)
+    return int(out[0]), bool(out[1])
+
+
+def use_library(path):
+    """Load the entry points from another build of the library (e.g. the bounds-check build) for the
+    contexts created from now on; returns the previous (path, handle) for restore_library."""
+    global _lib, LIB_PATH
+    prev = (LIB_PATH, _lib)
+    LIB_PATH, _lib = path, None
+    lib()
+    return prev
+
+
+def restore_library(prev):
+    global _lib, LIB_PATH
+    LIB_PATH, _lib = prev
+
+
 def grmhd_max_speed(ctx: int):
     """Largest |lambda| per direction over the interior faces of the last CFL stage (see include/grmhd.h)."""
     out = (ctypes.c_double * 3)()
@@ -368,6 +393,15 @@ def grmhd_batch_autotune(ctx: int):
     ms = ctypes.c_double(0.0)
     _check(lib().grmhd_batch_autotune(ctx, ctypes.byref(t), ctypes.byref(ms)), ctx)
     return t.value, ms.value
+
+
+def grmhd_batch_autotune_table(ctx: int):
+    """[(tile, ms per stage)] of the last autotune of the batch (see include/grmhd.h)."""
+    tiles = (ctypes.c_int * 8)()
+    ms = (ctypes.c_double * 8)()
+    n = ctypes.c_int()
+    _check(lib().grmhd_batch_autotune_table(ctypes.c_void_p(ctx), tiles, ms, 8, ctypes.byref(n)), ctx)
+    return [(tiles[k], ms[k]) for k in range(min(n.value, 8))]
 
 
 def grmhd_set_graph(ctx: int, on: bool) -> None:
@@ -450,6 +484,9 @@ class BatchContext:
 
     def autotune(self):
         return grmhd_batch_autotune(self.ctx)
+
+    def autotune_table(self):
+        return grmhd_batch_autotune_table(self.ctx)
 
     def set_graph(self, on=True):
         grmhd_set_graph(self.ctx, on)

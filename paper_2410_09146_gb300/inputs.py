@@ -481,6 +481,24 @@ def c2p_states_device(n: int, seed: int, device, gamma_eos: float = GAMMA_DEFAUL
 
 
 # ----------------------------------------------------------------------------- two-level block meshes
+def batched_setups(sizes=None, precision: str = "mixed", ids=None):
+    """The 640-block batched workload: 448 x 16^3, 160 x 32^3 and 32 x 64^3 meshblocks (4 ghosts), each of
+    physical size 1.6 on its own sub-cube of a 9 x 9 x 8 lattice from (3, 3, 3) in Kerr-Schild coordinates
+    (a = 0.9), WENO5-Z-AOAH + HLL, fixed ghosts; block b's primitives come from kerr_schild_random_prims with
+    seed 3 + b. ids selects a subset of the 640 blocks (same sizes, places and seeds as in the full batch)."""
+    if sizes is None:
+        sizes = [16] * 448 + [32] * 160 + [64] * 32
+    setups = []
+    for b in (range(len(sizes)) if ids is None else ids):
+        n = sizes[b]
+        ix, iy, iz = b % 9, (b // 9) % 9, b // 81
+        h = 1.6 / n
+        setups.append(Setup(n=(n, n, n), x0=(3.0 + 1.6 * ix, 3.0 + 1.6 * iy, 3.0 + 1.6 * iz), dx=(h, h, h),
+                            metric="kerr_schild", spin=0.9, recon="weno5z_aoah", riemann="hll", bc="fixed",
+                            precision=precision))
+    return setups
+
+
 @dataclasses.dataclass
 class TwoLevelMesh:
     """Leaves of a two-level block mesh over an nb[0] x nb[1] x nb[2] grid of root blocks. ``root`` holds the

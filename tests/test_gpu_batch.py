@@ -79,12 +79,19 @@ def test_batch_cfl_is_minimum_over_blocks(G):
 
 
 def test_batch_autotune(G):
+    """The autotuner times every candidate work-item size with a real RK2 step and keeps the fastest: the
+    tile it returns is the argmin of its own timing table, with that entry's time."""
     setups, prims = _blocks("mixed")
     bc = G.BatchContext(setups)
     for b, P in enumerate(prims):
         bc.set_prims(b, P.copy())
+    assert bc.autotune_table() == []
     tile, ms = bc.autotune()
-    assert tile in (128, 256, 512, 1024, 2048, 4096) and ms > 0
+    table = bc.autotune_table()
+    assert [t for t, _ in table] == [128, 256, 512, 1024, 2048, 4096]
+    assert all(m > 0 for _, m in table)
+    t_best, m_best = min(table, key=lambda e: e[1])
+    assert tile == t_best and ms == m_best, (tile, ms, table)
     bc.set_graph(True)
     bc.rk2_step(0.0)
     assert np.all(np.isfinite(bc.get(0, G.GRMHD_GET_CONS)))

@@ -360,16 +360,24 @@ def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=
     keep = (st & (8 | 16)) == 0
     X, T = X[keep].contiguous(), T[keep].contiguous()
     del P, U, st, keep
-    net = G.GuessNet(seed=11)
-    net.fit_norm(X, T)
-    losses = torch.zeros(train_steps, dtype=torch.float32, device=dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    net.train(X, T, batch=152 * 128, steps=train_steps, lr=3e-3, lr_end=3e-5, aux=0.1, losses=losses)
-    e1.record()
-    torch.cuda.synchronize()
-    train_ms = e0.elapsed_time(e1)
-    lh = losses.cpu().numpy()
+    # the same training twice from the same start: gradients on the FP32 cores, then on the tensor cores (the
+    # network the rest of this section uses)
+    train = {}
+    for tc in (False, True):
+        net = G.GuessNet(seed=11)
+        net.fit_norm(X, T)
+        losses = torch.zeros(train_steps, dtype=torch.float32, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.train(X, T, batch=152 * 128, steps=train_steps, lr=3e-3, lr_end=3e-5, aux=0.1, losses=losses, tc=tc)
+        e1.record()
+        torch.cuda.synchronize()
+        lh = losses.cpu().numpy()
+        train["tensor_cores" if tc else "fp32_cores"] = {"ms": e0.elapsed_time(e1),
+                                                          "ms_per_step": e0.elapsed_time(e1) / train_steps,
+                                                          "loss_first": float(lh[:10].mean()),
+                                                          "loss_last": float(lh[-100:].mean())}
+    train_ms = train["tensor_cores"]["ms"]
     n_pairs = X.shape[0]
     del X, T
     torch.cuda.empty_cache()
@@ -416,7 +424,9 @@ def run_guess(G, I, rank, n_states=100_000_000, n_train=10_000_000, train_steps=
     out = {"states": n_states, "c2p_tol": 1e-10,
            "train": {"pairs": n_pairs, "source": "the library's FP64 con2prim from the standard start",
                      "steps": train_steps, "batch": 152 * 128, "ms": train_ms,
-                     "loss_first": float(lh[:10].mean()), "loss_last": float(lh[-100:].mean())},
+                     "loss_first": float(lh[:10].mean()), "loss_last": float(lh[-100:].mean()),
+                     "gradient": "tensor cores (grmhd_mlp_train_tc): 64 x 64 products and weight gradients as "
+                                 "tcgen05 MMAs, BF16 operands, FP32 accumulation", "compare": train},
            "standard": dict(_iter_summary(its, sts, torch), ms=ms_std, states_per_s=n_states / (ms_std / 1e3)),
            "network_tc": dict(_iter_summary(itn, stn, torch), ms=ms_tc, states_per_s=n_states / (ms_tc / 1e3),
                               fallback_frac=int(stats_tc[7]) / n_states, abandoned_tiles=int(stats_tc[6]),

@@ -241,10 +241,20 @@ int grmhd_mlp_get_weights(const void* ws, float* theta, float* theta_bf16, void*
 int grmhd_mlp_forward(const void* ws, long long n, const float* X, float* Y, void* stream);
 
 /* Loss and gradient of one batch (n >= 1): the gradient accumulates in the workspace (cleared first) and
- * is copied to grad (host float [GRMHD_MLP_NPARAM]) and the loss to *loss when those are not NULL
- * (then the call synchronises). */
+ * is copied to grad (host float [GRMHD_MLP_NPARAM]) and the loss to *loss when those are not NULL; the
+ * call synchronises `stream`. Computed in FP32 on the CUDA cores. */
 int grmhd_mlp_grad(void* ws, long long n, const float* X, const float* T, double aux, float* grad, float* loss,
                    void* stream);
+
+/* The same on the fifth-generation tensor cores (the training form of the learned guess, the paper has no
+ * network): per tile of 128 samples the two 64 x 64 layers forward, the two products that carry the deltas
+ * back through them and (accumulated over tiles) their weight and bias gradients are tcgen05 MMAs of BF16
+ * operands with FP32 accumulation; the back-propagated deltas of layers 3 and 2 are rounded to BF16 where
+ * they enter a product, the first and output layers and their gradients stay FP32. Errors: as
+ * grmhd_mlp_grad, and GRMHD_E_CUDA when a tensor-core completion was not observed within the kernel's
+ * wait limit (the gradient is then incomplete). */
+int grmhd_mlp_grad_tc(void* ws, long long n, const float* X, const float* T, double aux, float* grad, float* loss,
+                      void* stream);
 
 /* One Adam update with the gradient held in the workspace (step counts from 1; learning rate lr);
  * refreshes the BF16 copy and clears the gradient. Asynchronous. */
@@ -256,6 +266,11 @@ int grmhd_mlp_adam(void* ws, double lr, int step, void* stream);
  * float [steps], or NULL) receives the loss of each minibatch. Asynchronous. */
 int grmhd_mlp_train(void* ws, long long n, const float* X, const float* T, long long batch, int steps, double lr,
                     double lr_end, double aux, int first_step, float* loss_dev, void* stream);
+
+/* grmhd_mlp_train with the tensor-core gradient of grmhd_mlp_grad_tc. Asynchronous; a tensor-core wait that
+ * timed out is counted in the workspace and reported by the next grmhd_mlp_grad / grmhd_mlp_grad_tc. */
+int grmhd_mlp_train_tc(void* ws, long long n, const float* X, const float* T, long long batch, int steps, double lr,
+                       double lr_end, double aux, int first_step, float* loss_dev, void* stream);
 
 /* Flat-space con2prim batch like grmhd_c2p (same U, P, status, iters layouts; the context's gamma_eos,
  * floors, tolerance and stream) with the initial guess chosen by mlp_ws and flags:

@@ -156,8 +156,12 @@ def forward(theta, norm, X, cache: bool = False, round_h: bool = True):
     return y
 
 
-def loss_and_grad(theta, norm, X, T, aux: float, round_h: bool = True):
-    """Loss (mean over samples) and its gradient [NPARAM] for raw features X and raw targets T."""
+def loss_and_grad(theta, norm, X, T, aux: float, round_h: bool = True, round_delta: bool = False):
+    """Loss (mean over samples) and its gradient [NPARAM] for raw features X and raw targets T.
+
+    round_delta: the deltas back-propagated into layers 3 and 2 (the operands of the tensor-core products of
+    the library's tensor-core training kernel: delta3 W3, delta2 W2 and the weight gradients delta^T h) are
+    rounded to BF16 where they enter those products; delta1 and the output layer's quantities are not."""
     P = unpack(theta)
     norm = np.asarray(norm, dtype=np.float64)
     _, c = forward(theta, norm, X, cache=True, round_h=round_h)
@@ -170,10 +174,11 @@ def loss_and_grad(theta, norm, X, T, aux: float, round_h: bool = True):
     g = {}
     g["W4"] = do.T @ c["h3"]
     g["b4"] = do.sum(0)
-    d3 = (do @ P["W4"]) * _dsilu(c["z3"])
+    rd = bf16_round if round_delta else (lambda a: a)
+    d3 = rd((do @ P["W4"]) * _dsilu(c["z3"]))
     g["W3"] = d3.T @ c["h2"]
     g["b3"] = d3.sum(0)
-    d2 = (d3 @ P["W3"]) * _dsilu(c["z2"])
+    d2 = rd((d3 @ P["W3"]) * _dsilu(c["z2"]))
     g["W2"] = d2.T @ c["h1"]
     g["b2"] = d2.sum(0)
     d1 = (d2 @ P["W2"]) * _dsilu(c["z1"])

@@ -14,12 +14,12 @@ BUILD_BC = os.path.join(HERE, "_build_bc")
 LIB_BC = os.path.join(BUILD_BC, "libgrmhd.so")
 ROOT = os.path.dirname(HERE)
 SOURCES = ["grmhd_api.cu", "grmhd_fp64.cu", "grmhd_mixed.cu", "grmhd_batch.cu", "grmhd_noalloc.cu", "grmhd_mlp.cu",
-           "grmhd_mlp_train.cu", "grmhd_mlp_tc.cu", "grmhd_peaks.cu"]
+           "grmhd_mlp_train.cu", "grmhd_mlp_tc.cu", "grmhd_peaks.cu", "grmhd_mlp_train_tc.cu"]
 # The all-FP64 stage kernels round every double operation separately, as the FP64 reference does.
 PER_SOURCE_FLAGS = {"grmhd_fp64.cu": ["-fmad=false"]}
 HEADERS = ["grmhd_device.cuh", "grmhd_kernels.cuh", "grmhd_launch.h", "grmhd_mlp.cuh", "grmhd_face_ct.cuh",
            "grmhd_mesh.cuh", "grmhd_mesh_host.h", "grmhd_batch_launch.cuh",
-           "grmhd_scalar.cuh"]
+           "grmhd_scalar.cuh", "grmhd_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 

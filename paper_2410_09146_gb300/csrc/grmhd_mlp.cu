@@ -271,19 +271,40 @@ int grmhd_mlp_forward(const void* ws, long long n, const float* X, float* Y, voi
   return GRMHD_OK;
 }
 
-int grmhd_mlp_grad(void* ws, long long n, const float* X, const float* T, double aux, float* grad, float* loss,
-                   void* stream) {
+namespace {
+using TrainFn = cudaError_t (*)(const MlpPtrs&, long long, const float*, const float*, float, float*, cudaStream_t);
+
+int mlp_grad(TrainFn fn, void* ws, long long n, const float* X, const float* T, double aux, float* grad, float* loss,
+             void* stream) {
   if (!ws || n <= 0 || !X || !T) return fail(GRMHD_E_INVALID, "grmhd_mlp_grad: bad arguments");
   if (!aligned(ws)) return fail(GRMHD_E_WORKSPACE, "grmhd_mlp_grad: workspace not 256-byte aligned");
   const cudaStream_t s = (cudaStream_t)stream;
   const MlpPtrs m = ptrs(ws);
   MCK(cudaMemsetAsync(m.grad, 0, NPARAM * sizeof(float), s), "clearing the gradient");
-  MCK(cudaMemsetAsync(m.loss, 0, 4 * sizeof(float), s), "clearing the loss");
-  MCK(launch_train(m, n, X, T, (float)aux, m.loss, s), "forward + backward");
+  MCK(cudaMemsetAsync(m.loss, 0, sizeof(float), s), "clearing the loss");  // loss[1]: timed-out waits, kept
+  MCK(fn(m, n, X, T, (float)aux, m.loss, s), "forward + backward");
+  float hl[2] = {0.f, 0.f};
+  MCK(cudaMemcpyAsync(hl, m.loss, 2 * sizeof(float), cudaMemcpyDeviceToHost, s), "copying");
   if (grad) MCK(cudaMemcpyAsync(grad, m.grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s), "copying");
-  if (loss) MCK(cudaMemcpyAsync(loss, m.loss, sizeof(float), cudaMemcpyDeviceToHost, s), "copying");
-  if (grad || loss) MCK(cudaStreamSynchronize(s), "synchronising");
+  MCK(cudaStreamSynchronize(s), "synchronising");
+  if (hl[1] != 0.f) {
+    MCK(cudaMemset(m.loss + 1, 0, sizeof(float)), "clearing the wait counter");
+    return fail(GRMHD_E_CUDA, "grmhd_mlp_grad: a tensor-core wait timed out (this or an earlier tensor-core "
+                              "gradient is incomplete)");
+  }
+  if (loss) *loss = hl[0];
   return GRMHD_OK;
+}
+}  // namespace
+
+int grmhd_mlp_grad(void* ws, long long n, const float* X, const float* T, double aux, float* grad, float* loss,
+                   void* stream) {
+  return mlp_grad(launch_train, ws, n, X, T, aux, grad, loss, stream);
+}
+
+int grmhd_mlp_grad_tc(void* ws, long long n, const float* X, const float* T, double aux, float* grad, float* loss,
+                      void* stream) {
+  return mlp_grad(launch_train_tc, ws, n, X, T, aux, grad, loss, stream);
 }
 
 int grmhd_mlp_adam(void* ws, double lr, int step, void* stream) {
@@ -294,8 +315,9 @@ int grmhd_mlp_adam(void* ws, double lr, int step, void* stream) {
   return GRMHD_OK;
 }
 
-int grmhd_mlp_train(void* ws, long long n, const float* X, const float* T, long long batch, int steps, double lr,
-                    double lr_end, double aux, int first_step, float* loss_dev, void* stream) {
+namespace {
+int mlp_train(TrainFn fn, void* ws, long long n, const float* X, const float* T, long long batch, int steps, double lr,
+              double lr_end, double aux, int first_step, float* loss_dev, void* stream) {
   if (!ws || n <= 0 || !X || !T || batch <= 0 || steps < 0 || first_step < 1 || !(lr > 0.0) || !(lr_end >= 0.0))
     return fail(GRMHD_E_INVALID, "grmhd_mlp_train: bad arguments");
   if (!aligned(ws)) return fail(GRMHD_E_WORKSPACE, "grmhd_mlp_train: workspace not 256-byte aligned");
@@ -303,12 +325,13 @@ int grmhd_mlp_train(void* ws, long long n, const float* X, const float* T, long 
   const MlpPtrs m = ptrs(ws);
   if (batch > n) batch = n;
   MCK(cudaMemsetAsync(m.grad, 0, NPARAM * sizeof(float), s), "clearing the gradient");
+  MCK(cudaMemsetAsync(m.loss, 0, sizeof(float), s), "clearing the loss");  // loss[1]: timed-out waits, kept
   if (loss_dev && steps > 0)
     MCK(cudaMemsetAsync(loss_dev, 0, (size_t)steps * sizeof(float), s), "clearing the loss history");
   long long off = 0;
   for (int k = 0; k < steps; ++k) {
     if (off + batch > n) off = 0;  // contiguous minibatches of i.i.d. samples, wrapping at the end
-    MCK(launch_train(m, batch, X + off * NIN, T + off * NOUT, (float)aux, loss_dev ? loss_dev + k : m.loss, s),
+    MCK(fn(m, batch, X + off * NIN, T + off * NOUT, (float)aux, loss_dev ? loss_dev + k : m.loss, s),
         "forward + backward");
     off += batch;
     // cosine decay from lr to lr_end over the call
@@ -317,6 +340,17 @@ int grmhd_mlp_train(void* ws, long long n, const float* X, const float* T, long 
     MCK(cudaGetLastError(), "Adam");
   }
   return GRMHD_OK;
+}
+}  // namespace
+
+int grmhd_mlp_train(void* ws, long long n, const float* X, const float* T, long long batch, int steps, double lr,
+                    double lr_end, double aux, int first_step, float* loss_dev, void* stream) {
+  return mlp_train(launch_train, ws, n, X, T, batch, steps, lr, lr_end, aux, first_step, loss_dev, stream);
+}
+
+int grmhd_mlp_train_tc(void* ws, long long n, const float* X, const float* T, long long batch, int steps, double lr,
+                       double lr_end, double aux, int first_step, float* loss_dev, void* stream) {
+  return mlp_train(launch_train_tc, ws, n, X, T, batch, steps, lr, lr_end, aux, first_step, loss_dev, stream);
 }
 
 }  // extern "C"

@@ -180,6 +180,10 @@ constexpr size_t kTrainSmem = (2 * (NPARAM + 2) + NNORM + TILE * NIN + 4 * TILE 
 static_assert(kTrainSmem <= 227 * 1024, "training tile exceeds shared memory");
 
 // Forward + backward of one batch into the workspace gradient; loss added to *loss (device).
+// The same gradient with the 64 x 64 products and weight gradients on the tensor cores (grmhd_mlp_train_tc.cu);
+// the back-propagated deltas are rounded to BF16 where they enter a product. m.loss[1] counts abandoned CTAs.
+cudaError_t launch_train_tc(const MlpPtrs& m, long long n, const float* X, const float* T, float aux, float* loss,
+                            cudaStream_t s);
 cudaError_t launch_train(const MlpPtrs& m, long long n, const float* X, const float* T, float aux, float* loss,
                          cudaStream_t s);
 

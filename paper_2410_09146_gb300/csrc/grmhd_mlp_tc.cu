@@ -15,6 +15,7 @@
 
 #include "grmhd_launch.h"
 #include "grmhd_mlp.cuh"
+#include "grmhd_tc.cuh"
 
 namespace {
 
@@ -25,16 +26,17 @@ constexpr int TC_M = 128;  // states per tile = threads per CTA = MMA M
 constexpr int TC_N = HID;  // MMA N (outputs of the layer)
 constexpr int TC_K = HID;  // K of layers 2 and 3
 constexpr uint32_t TMEM_COLS = 64;
-// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1),
-// B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                           ((uint32_t)(TC_M >> 4) << 24);
-constexpr int WAIT_LIMIT = 1 << 18;  // mbarrier polls before a tile is abandoned
+constexpr uint32_t IDESC = tc::idesc_bf16(TC_M, TC_N);
+using tc::fence_after_sync;
+using tc::fence_async_smem;
+using tc::fence_before_sync;
+using tc::mbar_wait;
+using tc::mma_commit;
+using tc::smem_addr;
+using tc::smem_desc;
+using tc::tmem_ld16;
 
-// Operands in the canonical K-major layout without swizzle: 8-row x 16-byte core matrices, rows of a
-// core matrix 16 bytes apart, core matrices adjacent in the row direction 128 bytes apart (SBO) and
-// adjacent in K R * 16 bytes apart (LBO) for an operand of R rows. Element (r, k) of a BF16 operand sits
-// at element offset (k / 8) * R * 8 + r * 8 + k % 8.
+// Operands in the canonical K-major layout without swizzle (grmhd_tc.cuh).
 struct __align__(128) TcSmem {
   __nv_bfloat16 A[TC_M * TC_K];   // activations h1 / h2 (16 KB)
   __nv_bfloat16 B2[TC_N * TC_K];  // W2 (8 KB)
@@ -49,56 +51,8 @@ struct __align__(128) TcSmem {
   int ok;
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; base offset 0, no swizzle (bits 61-63 = 0)
-  return d;
-}
-
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (int i = 0; i < WAIT_LIMIT; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  tc::mma_bf16(tmem_d, adesc, bdesc, IDESC, accumulate);
 }
 
 // Eight BF16 values of row r, K group g of the activation operand (one 16-byte store).

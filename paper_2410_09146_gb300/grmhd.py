@@ -112,8 +112,11 @@ def lib():
         L.grmhd_mlp_get_weights.argtypes = [vp, fp, fp, vp]
         L.grmhd_mlp_forward.argtypes = [vp, ctypes.c_longlong, vp, vp, vp]
         L.grmhd_mlp_grad.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.c_double, fp, fp, vp]
+        L.grmhd_mlp_grad_tc.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.c_double, fp, fp, vp]
         L.grmhd_mlp_adam.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp]
         L.grmhd_mlp_train.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
+        L.grmhd_mlp_train_tc.argtypes = [vp, ctypes.c_longlong, vp, vp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, vp, vp]
         L.grmhd_p2c.argtypes = [vp, ctypes.c_longlong, vp, vp]
         L.grmhd_c2p_guess.argtypes = [vp, vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int]
@@ -256,12 +259,13 @@ def grmhd_mlp_forward(ws: int, n: int, X_ptr: int, Y_ptr: int, stream_ptr: int) 
     _check(lib().grmhd_mlp_forward(vp(ws), n, vp(X_ptr), vp(Y_ptr), vp(stream_ptr)))
 
 
-def grmhd_mlp_grad(ws: int, n: int, X_ptr: int, T_ptr: int, aux: float, stream_ptr: int):
-    """(loss, gradient [NPARAM] float32) of one batch."""
+def grmhd_mlp_grad(ws: int, n: int, X_ptr: int, T_ptr: int, aux: float, stream_ptr: int, tc: bool = False):
+    """(loss, gradient [NPARAM] float32) of one batch; tc: grmhd_mlp_grad_tc (tensor cores)."""
     vp = ctypes.c_void_p
     g = np.zeros(GRMHD_MLP_NPARAM, np.float32)
     loss = np.zeros(1, np.float32)
-    _check(lib().grmhd_mlp_grad(vp(ws), n, vp(X_ptr), vp(T_ptr), aux, _fp(g), _fp(loss), vp(stream_ptr)))
+    fn = lib().grmhd_mlp_grad_tc if tc else lib().grmhd_mlp_grad
+    _check(fn(vp(ws), n, vp(X_ptr), vp(T_ptr), aux, _fp(g), _fp(loss), vp(stream_ptr)))
     return float(loss[0]), g
 
 
@@ -270,10 +274,12 @@ def grmhd_mlp_adam(ws: int, lr: float, step: int, stream_ptr: int) -> None:
 
 
 def grmhd_mlp_train(ws: int, n: int, X_ptr: int, T_ptr: int, batch: int, steps: int, lr: float, lr_end: float,
-                    aux: float, first_step: int, loss_ptr: int, stream_ptr: int) -> None:
+                    aux: float, first_step: int, loss_ptr: int, stream_ptr: int, tc: bool = False) -> None:
+    """grmhd_mlp_train, or grmhd_mlp_train_tc (tensor-core gradient) with tc."""
     vp = ctypes.c_void_p
-    _check(lib().grmhd_mlp_train(vp(ws), n, vp(X_ptr), vp(T_ptr), batch, steps, lr, lr_end, aux, first_step,
-                                 vp(loss_ptr or None), vp(stream_ptr)))
+    fn = lib().grmhd_mlp_train_tc if tc else lib().grmhd_mlp_train
+    _check(fn(vp(ws), n, vp(X_ptr), vp(T_ptr), batch, steps, lr, lr_end, aux, first_step, vp(loss_ptr or None),
+              vp(stream_ptr)))
 
 
 def grmhd_get(ctx: int, what: int, dst) -> None:
@@ -656,17 +662,19 @@ class GuessNet:
         grmhd_mlp_forward(self.ws_ptr, n, X.data_ptr(), Y.data_ptr(), self.stream.cuda_stream)
         return Y
 
-    def grad(self, X, T, aux: float = 0.1):
-        return grmhd_mlp_grad(self.ws_ptr, X.shape[0], X.data_ptr(), T.data_ptr(), aux, self.stream.cuda_stream)
+    def grad(self, X, T, aux: float = 0.1, tc: bool = False):
+        return grmhd_mlp_grad(self.ws_ptr, X.shape[0], X.data_ptr(), T.data_ptr(), aux, self.stream.cuda_stream, tc)
 
     def adam(self, lr: float):
         self.step += 1
         grmhd_mlp_adam(self.ws_ptr, lr, self.step, self.stream.cuda_stream)
 
-    def train(self, X, T, batch: int, steps: int, lr: float, lr_end: float = 0.0, aux: float = 0.1, losses=None):
-        """Adam over contiguous minibatches (see grmhd_mlp_train); losses: device float32 [steps] or None."""
+    def train(self, X, T, batch: int, steps: int, lr: float, lr_end: float = 0.0, aux: float = 0.1, losses=None,
+              tc: bool = False):
+        """Adam over contiguous minibatches (see grmhd_mlp_train); losses: device float32 [steps] or None;
+        tc: the tensor-core gradient (grmhd_mlp_train_tc)."""
         grmhd_mlp_train(self.ws_ptr, X.shape[0], X.data_ptr(), T.data_ptr(), batch, steps, lr, lr_end, aux,
-                        self.step + 1, 0 if losses is None else losses.data_ptr(), self.stream.cuda_stream)
+                        self.step + 1, 0 if losses is None else losses.data_ptr(), self.stream.cuda_stream, tc)
         self.step += steps
 
 

@@ -81,6 +81,63 @@ def test_forward_and_gradient_match_fp64_reference(orc):
         assert rel < 1e-4, (name, rel)
 
 
+def test_tensor_core_gradient_matches_fp64_reference(orc):
+    """grmhd_mlp_grad_tc (the 64 x 64 products and weight gradients as tcgen05 MMAs) against the FP64 reference
+    network with the same BF16 roundings (forward activations h1, h2 and the deltas of layers 3 and 2), on the
+    same BF16 weights: 1000 samples, 7 full tiles of 128 and a ragged tail of 104."""
+    torch, G = _setup()
+    rng = np.random.default_rng(15)
+    net = G.GuessNet(seed=17)
+    theta = (G.init_weights(17) + rng.normal(0, 0.05, M.NPARAM)).astype(np.float32)
+    norm = _random_norm(rng)
+    net.set_weights(theta, norm)
+    _, wb = net.weights()
+    U, X, T, _, _, _ = _oracle_pairs(orc, 1000, seed=16)
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    X32 = Xd.cpu().numpy().astype(np.float64)
+    T32 = Td.cpu().numpy().astype(np.float64)
+    aux = 0.25
+    loss_t, grad_t = net.grad(Xd, Td, aux, tc=True)
+    loss_r, grad_r = M.loss_and_grad(wb, norm.astype(np.float64), X32, T32, aux, round_delta=True)
+    loss_f, grad_f = net.grad(Xd, Td, aux)  # the FP32-core gradient (unrounded deltas)
+    _, grad_u = M.loss_and_grad(wb, norm.astype(np.float64), X32, T32, aux, round_delta=False)
+    assert abs(loss_t - loss_r) <= 1e-5 * loss_r and abs(loss_t - loss_f) <= 1e-5 * loss_r
+    worst = {}
+    for name, (o, shape) in M.OFFSETS.items():
+        sz = int(np.prod(shape))
+        gt, gr = grad_t[o:o + sz].astype(np.float64), grad_r[o:o + sz]
+        worst[name] = np.linalg.norm(gt - gr) / np.linalg.norm(gr)
+        # the rounded deltas move the lower blocks by about the BF16 unit against the unrounded gradient
+        drift = np.linalg.norm(gr - grad_u[o:o + sz]) / np.linalg.norm(grad_u[o:o + sz])
+        assert drift < 1e-2, (name, drift)
+    print("tensor-core gradient vs the reference with BF16 deltas:", worst)
+    assert max(worst.values()) < 1e-4, worst
+
+
+def test_tensor_core_training_reduces_the_loss(orc):
+    """A few hundred Adam steps of grmhd_mlp_train_tc on oracle-solved pairs lower the loss as the FP32-core
+    training does from the same start."""
+    torch, G = _setup()
+    U, X, T, st, _, _ = _oracle_pairs(orc, 20000, seed=21)
+    keep = (st & (8 | 16)) == 0
+    Xd = torch.tensor(X[keep], dtype=torch.float32, device="cuda")
+    Td = torch.tensor(T[keep], dtype=torch.float32, device="cuda")
+    out = {}
+    for tc in (False, True):
+        net = G.GuessNet(seed=23)
+        net.fit_norm(Xd, Td)
+        losses = torch.zeros(300, dtype=torch.float32, device="cuda")
+        net.train(Xd, Td, batch=2048, steps=300, lr=3e-3, lr_end=3e-4, losses=losses, tc=tc)
+        torch.cuda.synchronize()
+        lh = losses.cpu().numpy()
+        out[tc] = (float(lh[:10].mean()), float(lh[-20:].mean()))
+        assert net.grad(Xd[:128], Td[:128], 0.1, tc=tc)[0] >= 0  # no tensor-core wait timed out
+    print("loss first / last (FP32 cores, tensor cores):", out)
+    assert out[True][1] < 0.1 * out[True][0]
+    assert out[True][1] < 3.0 * out[False][1]
+
+
 def test_first_adam_step(orc):
     torch, G = _setup()
     rng = np.random.default_rng(8)

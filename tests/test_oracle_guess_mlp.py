@@ -72,6 +72,35 @@ def test_rounded_forward_is_straight_through():
     assert np.allclose(G["W3"], d3.T @ c["h2"], rtol=1e-12, atol=1e-15)
 
 
+def test_rounded_deltas_bound():
+    """round_delta (the tensor-core training form) rounds only the deltas of layers 3 and 2 to BF16: the output
+    layer's gradient is unchanged bit for bit, and each other block moves by no more than the rounding bound
+    it implies -- |delta_bf16 - delta| <= 2^-8 |delta| element by element, carried linearly into the W3, b3
+    and the W2, b2 blocks, and through |W3|, |W2| and |dsilu| into the lower layers."""
+    theta, norm = _net(5, scale=0.3)
+    rng = np.random.default_rng(9)
+    X = rng.normal(0, 1, (40, 8))
+    T = rng.normal(0, 2, (40, 2))
+    _, g0 = M.loss_and_grad(theta, norm, X, T, 0.3, round_delta=False)
+    _, g1 = M.loss_and_grad(theta, norm, X, T, 0.3, round_delta=True)
+    G0, G1 = M.unpack(g0), M.unpack(g1)
+    assert np.array_equal(G0["W4"], G1["W4"]) and np.array_equal(G0["b4"], G1["b4"])
+    P = M.unpack(theta)
+    _, c = M.forward(theta, norm, X, cache=True)
+    e = c["o"] - (T - norm[16:18]) / norm[18:20]
+    do = 2.0 * np.array([1.0, 0.3]) * e / len(X)
+    ds = lambda z: (1 / (1 + np.exp(-z))) * (1 + z * (1 - 1 / (1 + np.exp(-z))))
+    d3 = np.abs((do @ P["W4"]) * ds(c["z3"]))
+    u = 2.0 ** -8
+    assert np.all(np.abs(G1["W3"] - G0["W3"]) <= u * d3.T @ np.abs(c["h2"]) + 1e-300)
+    assert np.all(np.abs(G1["b3"] - G0["b3"]) <= u * d3.sum(0) + 1e-300)
+    # |delta2| with the rounded delta3 (bounded by (1 + u) |delta3| |W3| |dsilu|): the W2 block's change
+    d2 = (1 + u) * (d3 @ np.abs(P["W3"])) * np.abs(ds(c["z2"]))
+    bound_W2 = (u * (1 + u) * d2 + u * d2).T @ np.abs(c["h1"])
+    assert np.all(np.abs(G1["W2"] - G0["W2"]) <= bound_W2 + 1e-300)
+    assert np.abs(G1["W2"] - G0["W2"]).max() > 0  # the rounding does act
+
+
 def test_single_unit_chain_closed_form():
     P = {k: np.zeros(s) for k, (_, s) in M.OFFSETS.items()}
     a1, c1, a2, c2, a3, c3, a40, a41, c40, c41 = 0.7, -0.2, 1.3, 0.1, -0.9, 0.4, 1.1, -0.6, 0.05, 0.3

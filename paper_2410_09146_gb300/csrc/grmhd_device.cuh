@@ -626,8 +626,10 @@ __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
 
 // Work units of the flux phase of direction d: faces (face-centric reconstructions), or, for
 // WENO5-Z-AOAH, (transverse position, run of ~FLUX_RUN faces along d) pairs (cell-centric: each cell
-// reconstructed once per direction). The transverse positions span [-1, n] in both directions.
-constexpr int FLUX_RUN = 16;
+// reconstructed once per direction). The transverse positions span [-1, n] in both directions. Runs of 32
+// faces: at 256^3 the y / z sweeps take 1.95 ms against 2.08 with runs of 16 and 2.23 with runs of 8 (each
+// run reloads and reconstructs the window of the cell before it).
+constexpr int FLUX_RUN = 32;
 
 // Runs per column of nd + 1 faces (nd + 1 >= FLUX_RUN: runs of FLUX_RUN to 2 FLUX_RUN - 1 faces) and their
 // common length (the last run takes the remainder).

@@ -248,7 +248,16 @@ __device__ __forceinline__ void geo_load(const double* __restrict__ geo, long lo
 }
 
 template <class R>
-__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+__device__ __forceinline__ R fdiv(R x, R y) { return x / y; }
+
+// Quotients of the float flux path: the approximate quotient (reciprocal approximation times x, within
+// 2 ulp for 2^-126 <= |y| <= 2^126) instead of the correctly rounded one, whose divide sequence takes ~4x
+// the instructions (~85 quotients per face); the double form keeps the IEEE quotient.
+template <>
+__device__ __forceinline__ float fdiv<float>(float x, float y) { return __fdividef(x, y); }
+
+template <class R>
+__device__ __forceinline__ R rcp(R x) { return fdiv(R(1), x); }
 
 // Kerr-Schild core: r, f = 2 M r^3/(r^4 + a^2 z^2), spatial l_i (l_0 = 1).
 template <class R>
@@ -258,11 +267,11 @@ __device__ __forceinline__ void ks_core(R x, R y, R z, R a, R M, R& r, R& r2, R&
   const R sq = sqrt(A * A + R(4) * a * a * z * z);
   r2 = R(0.5) * (A + sq);
   r = sqrt(r2);
-  f = R(2) * M * r * r2 / (r2 * r2 + a * a * z * z);
+  f = fdiv(R(2) * M * r * r2, r2 * r2 + a * a * z * z);
   const R ira = rcp(r2 + a * a);
   l[0] = (r * x + a * y) * ira;
   l[1] = (r * y - a * x) * ira;
-  l[2] = z / r;
+  l[2] = fdiv(z, r);
 }
 
 // 3+1 quantities in closed form: alpha = (1+f)^-1/2, beta^i = f l^i/(1+f),
@@ -365,7 +374,7 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
     const R rhohW2 = rhoh * W * W;
 #pragma unroll
     for (int j = 0; j < 3; ++j) Uc[1 + j] = (rhohW2 + B2) * vl[j] - Bv * Bl[j];
-    Uc[4] = D * usq / (W + R(1)) + u * W * W + pgas * usq + (B2 - R(0.5) * b2);
+    Uc[4] = fdiv(D * usq, W + R(1)) + u * W * W + pgas * usq + (B2 - R(0.5) * b2);
   } else {
     const R wW2 = (rhoh + b2) * W * W;
 #pragma unroll
@@ -386,15 +395,15 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
 #pragma unroll
   for (int q = 0; q < NV; ++q) s.U[q] = m.sqrtgam * Uc[q];  // sqrt(-g) = 1: F is already densitized
   // Valencia characteristic speeds with the approximate fast speed c^2 = vA^2 + cs^2 (1 - vA^2).
-  const R cs2 = gamma_eos * pgas / rhoh;
-  const R va2 = b2 / (rhoh + b2);
+  const R cs2 = fdiv(gamma_eos * pgas, rhoh);
+  const R va2 = fdiv(b2, rhoh + b2);
   const R c2 = va2 + cs2 * (R(1) - va2);
   R one_v2, one_c2, one_v2c2;  // 1 - v^2, 1 - c^2 and 1 - v^2 c^2
   if constexpr (sizeof(R) == 4) {
     // float faces: 1 - v^2 = 1/W^2, 1 - c^2 = (1 - vA^2)(1 - cs^2) with 1 - vA^2 = rho h/(rho h + b^2), and
     // 1 - v^2 c^2 = (1 - c^2) + c^2/W^2, instead of differences whose rounding grows like W^2
     one_v2 = iW * iW;
-    one_c2 = rhoh / (rhoh + b2) * (R(1) - cs2);
+    one_c2 = fdiv(rhoh, rhoh + b2) * (R(1) - cs2);
     one_v2c2 = one_c2 + c2 * one_v2;
   } else {
     const R v2 = usq * iW * iW;
@@ -404,7 +413,7 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   }
   R disc = one_v2 * (sel3(d, m.gamu[0], m.gamu[3], m.gamu[5]) * one_v2c2 - vd * vd * one_c2);
   disc = disc > R(0) ? disc : R(0);
-  const R pre = m.alpha / one_v2c2;
+  const R pre = fdiv(m.alpha, one_v2c2);
   const R sq = sqrt(c2 * disc);
   const R base = vd * one_c2;
   const R bd = sel3(d, m.beta[0], m.beta[1], m.beta[2]);
@@ -463,7 +472,8 @@ __device__ __forceinline__ R minmod_slope(R dm, R dp) {
 // and the same tau, so they and the ratios tau/(beta + eps) are computed once; only the candidate values
 // and the linear weights (gamma is not symmetric) differ between the two sides.
 template <class R>
-__device__ __forceinline__ void weno5z_both(R f0, R f1, R f2, R f3, R f4, R eps, R& qp, R& qm, R wp[3], R wm[3]) {
+__device__ __forceinline__ void weno5z_both(R f0, R f1, R f2, R f3, R f4, R eps, R& qp, R& qm, R wp[3], R wm[3],
+                                            R z[3]) {
   const R P0 = (R(2) * f0 - R(7) * f1 + R(11) * f2) * R(1.0 / 6.0);
   const R P1 = (-f1 + R(5) * f2 + R(2) * f3) * R(1.0 / 6.0);
   const R P2 = (R(2) * f2 + R(5) * f3 - f4) * R(1.0 / 6.0);
@@ -477,13 +487,16 @@ __device__ __forceinline__ void weno5z_both(R f0, R f1, R f2, R f3, R f4, R eps,
   const R b1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * s1 * s1;
   const R b2 = R(13.0 / 12.0) * t2 * t2 + R(0.25) * s2 * s2;
   const R tau = fabs(b2 - b0);
-  R q0 = tau / (b0 + eps), q1 = tau / (b1 + eps), q2 = tau / (b2 + eps);
+  R q0 = fdiv(tau, b0 + eps), q1 = fdiv(tau, b1 + eps), q2 = fdiv(tau, b2 + eps);
   if (sizeof(R) == 4) {  // keep q^2 inside the float range; a clamped q still dominates its weight
     q0 = fmin(q0, R(1e15));
     q1 = fmin(q1, R(1e15));
     q2 = fmin(q2, R(1e15));
   }
   const R z0 = R(1) + q0 * q0, z1 = R(1) + q1 * q1, z2 = R(1) + q2 * q2;
+  z[0] = z0;
+  z[1] = z1;
+  z[2] = z2;
   const R a0 = R(0.1) * z0, a1 = R(0.6) * z1, a2 = R(0.3) * z2;      // plus side
   const R c0 = R(0.1) * z2, c1 = R(0.6) * z1, c2 = R(0.3) * z0;      // minus side (stencils mirrored)
   const R is = rcp(a0 + a1 + a2), im = rcp(c0 + c1 + c2);
@@ -527,7 +540,7 @@ __device__ __forceinline__ R minmod4(R w, R x, R y, R z) {
 template <class R>
 __device__ __forceinline__ R mp5_face(R f0, R f1, R f2, R f3, R f4) {
   const R alpha = R(4);
-  const R v = (R(2) * f0 - R(13) * f1 + R(47) * f2 + R(27) * f3 - R(3) * f4) / R(60);
+  const R v = fdiv(R(2) * f0 - R(13) * f1 + R(47) * f2 + R(27) * f3 - R(3) * f4, R(60));
   const R vmp = f2 + minmod2(f3 - f2, alpha * (f2 - f1));
   if ((v - f2) * (v - vmp) <= R(0)) return v;
   const R dm = f0 - R(2) * f1 + f2, d0 = f1 - R(2) * f2 + f3, dp = f2 - R(2) * f3 + f4;
@@ -555,10 +568,22 @@ __device__ __forceinline__ void recon_cell(R f0, R f1, R f2, R f3, R f4, R eps, 
     qm = f2 - R(0.5) * s;
     qp = f2 + R(0.5) * s;
   } else {
-    R wp[3], wm[3], P5p, P5m;
-    weno5z_both<R>(f0, f1, f2, f3, f4, eps, P5p, P5m, wp, wm);
-    const R sp = weno_sigma_side(wp), sm = weno_sigma_side(wm);
-    R sigma = sp + sm > R(0) ? R(2) * sp * sm / (sp + sm) : R(0);  // both sides can underflow in float
+    R wp[3], wm[3], z[3], P5p, P5m;
+    weno5z_both<R>(f0, f1, f2, f3, f4, eps, P5p, P5m, wp, wm, z);
+    R sigma;
+    if constexpr (sizeof(R) == 4) {
+      // The same sigma from the unnormalised weights: with w_k = gamma_k z_k / S (S = sum gamma_k z_k) the
+      // reciprocal of a side's sigma is (S / 3) (1/z_0 + 1/z_1 + 1/z_2), the same sum on both sides (the
+      // mirrored side permutes z and gamma together), so the harmonic mean of the two sides is
+      // 6 / ((S_+ + S_-) H) = 15 / ((z_0 + 3 z_1 + z_2) H), H = 1/z_0 + 1/z_1 + 1/z_2: one quotient and three
+      // reciprocals instead of three quotients of products (which can also underflow in float). z_k is
+      // in [1, 1e30] (q clamped), so neither factor leaves the float range.
+      const R H = rcp(z[0]) + rcp(z[1]) + rcp(z[2]);
+      sigma = fdiv(R(15), (z[0] + R(3) * z[1] + z[2]) * H);
+    } else {
+      const R sp = weno_sigma_side(wp), sm = weno_sigma_side(wm);
+      sigma = sp + sm > R(0) ? R(2) * sp * sm / (sp + sm) : R(0);
+    }
     sigma = sigma > R(1) ? R(1) : sigma;
     const R s = mc_slope(f2 - f1, f3 - f2);
     qp = sigma * P5p + (R(1) - sigma) * (f2 + R(0.5) * s);

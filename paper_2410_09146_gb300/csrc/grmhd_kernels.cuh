@@ -61,7 +61,7 @@ __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, 
   Metric<R> m;
   R rks = R(1);
   metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m, &rks);
-  const R fr = METRIC == KERR_SCHILD ? (p.floor_r2 ? R(1) / (rks * rks) : R(pow((double)rks, -p.floor_r_exp)))
+  const R fr = METRIC == KERR_SCHILD ? (p.floor_r2 ? rcp(rks * rks) : R(pow((double)rks, -p.floor_r_exp)))
                                      : R(1);
   const R rho_flr = par<R>(p.rho_floor0, p.frho_floor0) * fr, eps_flr = par<R>(p.eps_floor0, p.feps_floor0) * fr;
   if (!(PL[0] >= rho_flr)) PL[0] = rho_flr;
@@ -69,7 +69,7 @@ __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, 
   if (!(PL[4] >= PL[0] * eps_flr)) PL[4] = PL[0] * eps_flr;
   if (!(PR[4] >= PR[0] * eps_flr)) PR[4] = PR[0] * eps_flr;
   if (p.bface != nullptr) {
-    const R bn = R(LDC(p.bface, d * p.gsize + gidx(p, i, j, k), 3 * p.gsize)) / m.sqrtgam;
+    const R bn = fdiv(R(LDC(p.bface, d * p.gsize + gidx(p, i, j, k), 3 * p.gsize)), m.sqrtgam);
     if (d == 0) { PL[5] = bn; PR[5] = bn; }
     else if (d == 1) { PL[6] = bn; PR[6] = bn; }
     else { PL[7] = bn; PR[7] = bn; }

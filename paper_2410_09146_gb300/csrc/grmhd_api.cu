@@ -151,6 +151,7 @@ DevParams dev_params(const grmhd_params* p) {
   d.frho_floor0 = (float)d.rho_floor0;
   d.feps_floor0 = (float)d.eps_floor0;
   d.fw_max2 = (float)d.w_max2;
+  d.fv0sq_cap = (float)d.v0sq_cap;
   d.floor_r2 = d.floor_r_exp == 2.0 ? 1 : 0;
   return d;
 }

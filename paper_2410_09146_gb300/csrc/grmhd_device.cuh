@@ -48,6 +48,7 @@ struct DevParams {
   // Float copies of the parameters the float kernels read (set with the double ones): a double -> float
   // conversion costs an FP64 issue slot on this part, so the float code reads these instead.
   float fx0[3], fdx[3], fidx[3], fa, fM, fgamma, fweno_eps, frho_floor0, feps_floor0, fw_max2, fshift[3];
+  float fv0sq_cap;
   int floor_r2;  // floor_r_exp == 2 (the radius factor is 1/r^2)
   // Bounds-check build (GRMHD_BOUNDS_CHECK): the word where the first out-of-range access of a stage kernel
   // is recorded (see bounds_fault); unused otherwise.
@@ -259,6 +260,11 @@ __device__ __forceinline__ float fdiv<float>(float x, float y) { return __fdivid
 template <class R>
 __device__ __forceinline__ R rcp(R x) { return fdiv(R(1), x); }
 
+// x finite, and x > 0 for finite x, from the bit pattern: integer instructions, where a double compare
+// would take a slot of the FP64 pipe that binds the mixed form's update.
+__device__ __forceinline__ bool dfinite(double x) { return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000; }
+__device__ __forceinline__ bool dpositive(double x) { return __double_as_longlong(x) > 0; }
+
 // Kerr-Schild core: r, f = 2 M r^3/(r^4 + a^2 z^2), spatial l_i (l_0 = 1).
 template <class R>
 __device__ __forceinline__ void ks_core(R x, R y, R z, R a, R M, R& r, R& r2, R& f, R l[3]) {
@@ -440,13 +446,21 @@ __device__ __forceinline__ void prim_to_cons5(const R P[NV], const Metric<R>& m,
   const R ab0 = W * Bv;
   const R b2 = (B2 + ab0 * ab0) * iW * iW;
   const R pgas = (gamma_eos - R(1)) * P[4];
-  const R w = P[0] + P[4] + pgas + b2;
   const R D = P[0] * W;
-  const R wW2 = w * W * W;
   U5[0] = m.sqrtgam * D;
+  if constexpr (sizeof(R) == 4) {
+    // float: the forms without cancellation of prim_to_face
+    const R rhohW2 = (P[0] + P[4] + pgas) * W * W;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) U5[1 + j] = m.sqrtgam * (wW2 * vl[j] - ab0 * (Bl[j] * iW + ab0 * vl[j]));
-  U5[4] = m.sqrtgam * (wW2 - (pgas + R(0.5) * b2) - ab0 * ab0 - D);
+    for (int j = 0; j < 3; ++j) U5[1 + j] = m.sqrtgam * ((rhohW2 + B2) * vl[j] - Bv * Bl[j]);
+    U5[4] = m.sqrtgam * (fdiv(D * usq, W + R(1)) + P[4] * W * W + pgas * usq + (B2 - R(0.5) * b2));
+  } else {
+    const R w = P[0] + P[4] + pgas + b2;
+    const R wW2 = w * W * W;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) U5[1 + j] = m.sqrtgam * (wW2 * vl[j] - ab0 * (Bl[j] * iW + ab0 * vl[j]));
+    U5[4] = m.sqrtgam * (wW2 - (pgas + R(0.5) * b2) - ab0 * ab0 - D);
+  }
 }
 
 // ------------------------------------------------------------------ reconstruction (Sec. 3.1, App. B)
@@ -995,8 +1009,8 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
   mu_r = 0.0;
   bool finite = true;
 #pragma unroll
-  for (int q = 0; q < NV; ++q) finite = finite && isfinite(Un[q]);
-  const bool bad = !finite || !(Un[0] > 0.0);
+  for (int q = 0; q < NV; ++q) finite = finite && dfinite(Un[q]);
+  const bool bad = !finite || !dpositive(Un[0]);
   C2PIn<double> c;
   C2PIn<float> cf;
   float ruf[3], buf[3];
@@ -1020,9 +1034,10 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
     c.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
     c.rb2 = c.rb * c.rb;
     c.gm1 = p.gamma_eos - 1.0;
-    c.v0sq = fmin(c.r2 / (1.0 + c.r2), p.v0sq_cap);
+    c.v0sq = 0.0;  // formed below where the double part needs it (it costs a double quotient)
     cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
-    cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
+    cf.rb2 = cf.rb * cf.rb; cf.gm1 = p.fgamma - 1.f;
+    cf.v0sq = fminf(__fdividef(cf.r2, 1.f + cf.r2), p.fv0sq_cap);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       ruf[i] = (float)ru[i];
@@ -1062,7 +1077,7 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
         const float rbr = xr * xr * cf.r2 + mupf * xr * (1.f + xr) * cf.rb2;
         const float drb = 2.f * xr * dxr * cf.r2 + cf.rb2 * (xr * (1.f + xr) + mupf * dxr * (1.f + 2.f * xr));
         const float dg = 2.f * mupf * (1.f + rbr) + mupf * mupf * drb;
-        m1 -= (double)((float)gp / dg);
+        m1 -= (double)__fdividef((float)gp, dg);
       }
       if (cold) mue = m1;
     }
@@ -1071,7 +1086,8 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
     const double rb = c.r2 * (x * x) + c.rb2 * (mue * x * (1.0 + x));
     const double qbar = (c.q - 0.5 * c.b2) - (0.5 * (c.b2 * c.r2 - c.rb2)) * (mue * mue * x * x);
     double vh2 = mue * mue * rb;
-    if (vh2 > c.v0sq) vh2 = c.v0sq;
+    // vh2 > v0sq = min(r^2/(1 + r^2), v0sq_cap), without the quotient unless the bound binds
+    if (vh2 * (1.0 + c.r2) > c.r2 || vh2 > p.v0sq_cap) vh2 = fmin(c.r2 / (1.0 + c.r2), p.v0sq_cap);
     const double W = rsqrt(1.0 - vh2);
     const double iW = (1.0 - vh2) * W;
     const double e0 = fmax(W * (1.0 + qbar - mue * rb) - 1.0, 0.0);
@@ -1087,16 +1103,17 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
       xf = ed.x;
       done = true;
     } else {
-      const float step = -(float)gK / ((float)K * ed.df);
+      const float step = -__fdividef((float)gK, (float)K * ed.df);
       const double nmu = mue + (double)step;
       mu = nmu;
-      done = ed.df > 0.f && nmu > 0.0 && fabsf(step) <= 3e-6f * (float)nmu && nmu <= (double)mupf * (1.0 + 1e-5);
+      const float nmuf = (float)nmu;
+      done = ed.df > 0.f && nmuf > 0.f && fabsf(step) <= 3e-6f * nmuf && nmuf <= mupf * (1.f + 1e-5f);
       if (done) {
         // the intermediates at the root to first order in the step (the neglected term is O(step^2))
         eps = fmax(e0 + (double)(ed.deps * step), 0.0);
         Wf = (float)W + ed.dW * step;
         xf = ed.x + ed.dx * step;
-      } else if (defer && isfinite(nmu) && nmu > 0.0 && nmu < (double)mupf * (1.0 + 1e-3)) {
+      } else if (defer && dfinite(nmu) && nmuf > 0.f && nmuf < mupf * (1.f + 1e-3f)) {
         mu_r = nmu;  // the double pass resumes from this iterate
       }
     }
@@ -1104,6 +1121,7 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
   if (!done && defer) return C2P_DEFERRED;
   int st = 0;
   if (!done) {  // float phase did not settle: double iteration on the full bracket, from the float root
+    c.v0sq = fmin(c.r2 / (1.0 + c.r2), p.v0sq_cap);
     const double mup = c2p_mu_plus_fast(c);
     if (!(stf == 0 && isfinite(mu) && mu > 0.0)) mu = (double)mu_guess;
     int it64 = 0;

@@ -153,10 +153,12 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
 }
 
 // Cell-centric fluxes of direction d = 1, 2 for WENO5-Z-AOAH, unit t of flux_units: one transverse
-// position and a run of flux_run_length faces along d. A sliding window of five cells per variable is loaded once per cell;
-// each cell is reconstructed once (both of its faces), and face f pairs the plus side of cell f - 1 with
-// the minus side of cell f (face_flux, as in the face-centric flux_face). Returns max |lambda| over the
-// run's interior faces.
+// position and a run of flux_run_length faces along d. Each cell is reconstructed once (both of its faces),
+// and face f pairs the plus side of cell f - 1 with the minus side of cell f (face_flux, as in the
+// face-centric flux_face). The five-cell stencil is loaded afresh for each cell: four of its rows were
+// loaded by the warp for the cell before (its lanes hold consecutive x positions) and come from L1, and
+// not holding a 40-value window across face_flux cuts the spills at 64 registers (y / z sweeps 1.75 ->
+// 1.45 ms at 256^3). Returns max |lambda| over the run's interior faces.
 template <class R, class T, int METRIC, int RECON>
 __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ P, R* __restrict__ F, int d,
                                       long long t) {
@@ -183,18 +185,15 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   // bitwise reproducible for one block layout, not across layouts. One call site for all cells costs
   // ~0.45 ms per 256^3 stage (measured), so the faster form is kept; the double form is built without
   // contraction and does not depend on the layout.
-  // window of cell f0 - 1: cells f0 - 3 .. f0 + 1
-  R w[NV][5];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-#pragma unroll
-    for (int s = 0; s < 5; ++s) w[q][s] = R(LDC(P, q * p.gsize + g + (s - 3) * sd, NV * p.gsize));
-  }
+  // plus side of cell f0 - 1
   R PL[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
+    const long long c0 = q * p.gsize + g - sd;
     R qm, qp;
-    recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
+    recon_cell<R, RECON>(R(LDC(P, c0 - 2 * sd, NV * p.gsize)), R(LDC(P, c0 - sd, NV * p.gsize)),
+                         R(LDC(P, c0, NV * p.gsize)), R(LDC(P, c0 + sd, NV * p.gsize)),
+                         R(LDC(P, c0 + 2 * sd, NV * p.gsize)), eps, qm, qp);
     PL[q] = qp;
   }
   R cm_run = R(0);
@@ -203,11 +202,11 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
     R PR[NV], QP[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) w[q][s] = w[q][s + 1];
-      w[q][4] = R(LDC(P, q * p.gsize + g + 2 * sd, NV * p.gsize));
+      const long long c0 = q * p.gsize + g;
       R qm, qp;
-      recon_cell<R, RECON>(w[q][0], w[q][1], w[q][2], w[q][3], w[q][4], eps, qm, qp);
+      recon_cell<R, RECON>(R(LDC(P, c0 - 2 * sd, NV * p.gsize)), R(LDC(P, c0 - sd, NV * p.gsize)),
+                           R(LDC(P, c0, NV * p.gsize)), R(LDC(P, c0 + sd, NV * p.gsize)),
+                           R(LDC(P, c0 + 2 * sd, NV * p.gsize)), eps, qm, qp);
       PR[q] = qm;
       QP[q] = qp;
     }
@@ -506,13 +505,13 @@ __device__ __forceinline__ void geo_load_c2p(const double* __restrict__ geo, lon
 }
 
 // Mixed form of a5 + a6 for interior cell t, after the float flux divergence L (CT fluxes for B): float
-// sources, the RK combination in double, con2prim_mixed_f, floors in float on the float primitives. A cell
-// whose double step from the float root is not small is queued for deferred_cell; a floored cell for
-// floor_cell (its hydro state re-derived from the stored primitives), or inline without a floor list.
+// sources, the RK combination in double, con2prim_mixed_f, floors in float on the float primitives and, for
+// a floored cell, its hydro state re-derived from them in float. A cell whose double step from the float
+// root is not small is queued for deferred_cell.
 template <int METRIC>
 __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __restrict__ P, const StageArgs& a,
-                                                  float L[NV], double dt, long long t, long long g, double xc,
-                                                  double yc, double zc, float xr, float yr, float zr,
+                                                  float L[NV], double dt, long long t, long long g, int i, int j,
+                                                  int k, float xr, float yr, float zr,
                                                   const float Pr[NV], long long wl_tag, CellStats& cs) {
   const long long n = p.isize, G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
   Metric<float> mr;
@@ -556,7 +555,8 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
 #endif
     geo_load_c2p(p.geo, n, t, m, isg);
   } else {
-    metric_at<double, METRIC>(p, xc, yc, zc, m);
+    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                              p.x0[2] + (k + 0.5) * p.dx[2], m);
     isg = 1.0 / m.sqrtgam;
   }
   // warm start mu = 1/(h W) of the current primitives, in float (it only seeds the float phase)
@@ -579,20 +579,13 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
                                          : 1.f;
   st |= apply_floors_f(p, mr.gam, fr, Pn);
   if (st) {
-    if (a.floorlist) {
-      // the hydro state of this cell is re-derived from the floored P by floor_cell, in a pass whose warps
-      // hold only such cells
-      STC(a.floorlist, atomicAdd(a.fl_count, 1u), n, (int)(wl_tag + t));
-    } else {
-      Metric<double> mf;
-      metric_at<double, METRIC>(p, xc, yc, zc, mf);
-      double Pd[NV], U5[5];
+    // the hydro state re-derived from the floored float primitives, in float like the floors themselves
+    // (the FP32 pipe is idle in this FP64-bound kernel, so the lanes of a warp that take this branch cost
+    // next to nothing; the forms without cancellation keep it to the rounding of the primitives)
+    float U5[5];
+    prim_to_cons5<float>(Pn, mr, p.fgamma, U5);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) Pd[q] = (double)Pn[q];
-      prim_to_cons5<double>(Pd, mf, p.gamma_eos, U5);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) Un[q] = U5[q];
-    }
+    for (int q = 0; q < 5; ++q) Un[q] = (double)U5[q];
   }
 #pragma unroll
   for (int q = 0; q < NV; ++q) STC(a.Unew, q * n + t, NV * n, Un[q]);
@@ -652,7 +645,7 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
     L[5] = L[6] = L[7] = R(0);  // the field comes from the advanced faces below
   }
   if constexpr (sizeof(T) == 4) {
-    update_cell_mixed<METRIC>(p, P, a, L, dt, t, g, xc, yc, zc, xr, yr, zr, Pt, wl_tag, cs);
+    update_cell_mixed<METRIC>(p, P, a, L, dt, t, g, i, j, k, xr, yr, zr, Pt, wl_tag, cs);
   } else {
     const double bdt = a.beta * dt;
     Metric<double> m;

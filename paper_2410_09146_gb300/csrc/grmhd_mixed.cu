@@ -58,18 +58,10 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
   return cudaGetLastError();
 }
 
-// Passes over the cells queued by k_update (counts known on the device only): re-derivation of the hydro
-// state of floored cells, and (mixed form) the double con2prim of cells whose float phase did not settle.
+// Pass over the cells queued by k_update (count known on the device only): the double con2prim of cells
+// whose float phase did not settle. (Floored cells are re-derived inside k_update in this form.)
 cudaError_t cell_passes(const DevParams& p, void* P, const StageArgs& a, cudaStream_t s) {
   const int g2 = grid_for(p.isize / 8 + 1, 128);
-  if (a.floorlist) {
-    if (p.metric == KERR_SCHILD)
-      k_update_floors<KERR_SCHILD, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
-    else
-      k_update_floors<MINKOWSKI, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
   if (a.worklist == nullptr) return cudaSuccess;
   if (p.metric == KERR_SCHILD)
     k_update_deferred<KERR_SCHILD, T><<<g2, 128, 0, s>>>((T*)P, a, p);

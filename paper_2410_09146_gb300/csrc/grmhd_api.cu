@@ -29,7 +29,8 @@ struct grmhd_ctx {
   uint8_t* status;
   int* worklist;             // mixed form: deferred con2prim cells (NULL in the FP64 form)
   double* wl_mu;             // mixed form: the double iterate each deferred cell resumes from
-  int* floorlist;            // cells whose hydro state is re-derived after floors
+  int* floorlist;            // FP64 form: floored cells (hydro state re-derived in a pass); mixed form:
+                             // deferred cells that need the full double con2prim
   unsigned long long* scal;  // [0..2] max speed bits, [3] dt (double), [8..15] stats, [16] worklist count,
                              // [17] floor-list count, [20..23] batch work counters
   double* Bslot[3];          // face-centred CT: face field slots [3][gsize], paired with Uslot
@@ -642,8 +643,13 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   a.worklist = c->worklist;
   a.wl_count = (unsigned int*)(c->scal + 16);
   a.wl_mu = c->wl_mu;
-  a.floorlist = c->floorlist;
-  a.fl_count = (unsigned int*)(c->scal + 17);
+  if (c->worklist) {  // mixed form: floored cells re-derived in place; the list holds the full solves
+    a.solvelist = c->floorlist;
+    a.sl_count = (unsigned int*)(c->scal + 17);
+  } else {
+    a.floorlist = c->floorlist;
+    a.fl_count = (unsigned int*)(c->scal + 17);
+  }
   if (face) {
     CK(L.emf_face(dp, c->P, c->F[0], c->F[1], c->F[2], c->Ecc, c->E, s), "upwind EMF");
     CK(L.face_update(dp, c->Bslot[c->s0], c->Bslot[c->sc], c->Bslot[dst], c->E, a, s), "face update");
@@ -755,8 +761,13 @@ static int batch_stage(grmhd_ctx* c, double g0, double g1, double beta, double d
   a.worklist = c->worklist;
   a.wl_count = (unsigned int*)(c->scal + 16);
   a.wl_mu = c->wl_mu;
-  a.floorlist = c->floorlist;
-  a.fl_count = (unsigned int*)(c->scal + 17);
+  if (c->worklist) {  // mixed form: floored cells re-derived in place; the list holds the full solves
+    a.solvelist = c->floorlist;
+    a.sl_count = (unsigned int*)(c->scal + 17);
+  } else {
+    a.floorlist = c->floorlist;
+    a.fl_count = (unsigned int*)(c->scal + 17);
+  }
   if (c->use_graph) {
     const std::vector<double> key = {g0, g1, beta, dt, (double)s0, (double)c->sc, (double)dst, (double)c->tile};
     auto it = c->graphs.find(key);

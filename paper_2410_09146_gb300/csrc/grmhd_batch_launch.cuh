@@ -39,13 +39,18 @@ struct BatchLaunch {
       k_batch_update<MINKOWSKI, R, T><<<grid, 128, 0, s>>>(b, it, n, ctr, a);
     return cudaGetLastError();
   }
+  // the two passes of deferred_cell (the second over the cells the first queued, when there is a solve list)
   static cudaError_t deferred(const BlockDesc* b, int nblocks, const BatchArgs& a, int metric, int grid,
                               cudaStream_t s) {
-    if (metric == KERR_SCHILD)
-      k_batch_deferred<KERR_SCHILD, T><<<grid, 128, 0, s>>>(b, nblocks, a);
-    else
-      k_batch_deferred<MINKOWSKI, T><<<grid, 128, 0, s>>>(b, nblocks, a);
-    return cudaGetLastError();
+    for (int full = 0; full < (a.solvelist ? 2 : 1); ++full) {
+      if (metric == KERR_SCHILD)
+        k_batch_deferred<KERR_SCHILD, T><<<grid, 128, 0, s>>>(b, nblocks, a, full);
+      else
+        k_batch_deferred<MINKOWSKI, T><<<grid, 128, 0, s>>>(b, nblocks, a, full);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   static cudaError_t floors(const BlockDesc* b, int nblocks, const BatchArgs& a, int metric, int grid,
                             cudaStream_t s) {

@@ -121,6 +121,8 @@ struct StageArgs {
   int* floorlist;                // cells whose floors / status re-derive U in a compacted pass (NULL: inline)
   unsigned int* fl_count;        // number of entries in floorlist
   const double* bface_new;       // face-centred CT: the advanced faces [3][gsize]; NULL: flux-CT
+  int* solvelist;                // mixed form: worklist cells whose resumed double step did not settle, for
+  unsigned int* sl_count;        // the full double iteration in a last pass (NULL: inline); its count
 };
 
 
@@ -201,6 +203,8 @@ struct BatchArgs {
   double* wl_mu;
   int* floorlist;
   unsigned int* fl_count;
+  int* solvelist;
+  unsigned int* sl_count;
 };
 
 // ------------------------------------------------------------------ metric (Sec. 2.3)
@@ -953,34 +957,27 @@ __device__ __forceinline__ bool c2p_accept_step(const C2PIn<double>& c, const C2
   return true;
 }
 
-// The double pass of a deferred cell: from the double iterate mu_r of the first pass (when it has one),
-// one more evaluation and the same acceptance as the first pass; otherwise the full double con2prim.
+// The resumed step of a deferred cell: from the double iterate mu_r of the first pass (when it has one), one
+// more evaluation and the same acceptance as the first pass. False: the cell needs the full double con2prim.
 template <class R>
-__device__ __forceinline__ int con2prim_resume(const DevParams& p, const Metric<R>& m, const double Uc[NV],
-                                               double mu_guess, double mu_r, double Pout[NV], int& iters) {
+__device__ __forceinline__ bool con2prim_resume_step(const DevParams& p, const Metric<R>& m, const double Uc[NV],
+                                                     double mu_r, double Pout[NV], int& iters) {
   iters = 0;
-  if (mu_r > 0.0) {
-    C2PIn<double> c;
-    double ru[3], bu[3];
-    if (c2p_setup<R>(p, m, Uc, c, ru, bu) == 0) {
-      C2PIn<float> cf;
-      cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
-      cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
-      const float mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
-      const C2PEval<double> e = c2p_master(c, mu_r);
-      iters = 1;
-      double mu;
-      C2PEval<double> ev;
-      if (c2p_accept_step(c, e, mu_r, mupf, mu, ev)) {
-        c2p_output_eval(c, ev, mu, ru, bu, Uc, Pout);
-        return 0;
-      }
-    }
-  }
-  int it2 = 0;
-  const int st = con2prim<R>(p, m, Uc, mu_guess, Pout, it2, true);
-  iters += it2;
-  return st;
+  if (!(mu_r > 0.0)) return false;
+  C2PIn<double> c;
+  double ru[3], bu[3];
+  if (c2p_setup<R>(p, m, Uc, c, ru, bu) != 0) return false;
+  C2PIn<float> cf;
+  cf.D = (float)c.D; cf.q = (float)c.q; cf.r2 = (float)c.r2; cf.b2 = (float)c.b2; cf.rb = (float)c.rb;
+  cf.rb2 = (float)c.rb2; cf.gm1 = (float)c.gm1; cf.v0sq = (float)c.v0sq;
+  const float mupf = c2p_mu_plus<float>(cf, -1.f, 1e-7f, 40);
+  const C2PEval<double> e = c2p_master(c, mu_r);
+  iters = 1;
+  double mu;
+  C2PEval<double> ev;
+  if (!c2p_accept_step(c, e, mu_r, mupf, mu, ev)) return false;
+  c2p_output_eval(c, ev, mu, ru, bu, Uc, Pout);
+  return true;
 }
 
 // Returned by con2prim_mixed_f(defer = true): the cell needs the double iteration of deferred_cell.

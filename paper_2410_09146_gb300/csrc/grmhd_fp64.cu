@@ -58,23 +58,15 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
   return cudaGetLastError();
 }
 
-// Passes over the cells queued by k_update (counts known on the device only): re-derivation of the hydro
-// state of floored cells, and (mixed form) the double con2prim of cells whose float phase did not settle.
+// Pass over the cells queued by k_update (count known on the device only): re-derivation of the hydro
+// state of floored cells. (This form has no deferred con2prim cells.)
 cudaError_t cell_passes(const DevParams& p, void* P, const StageArgs& a, cudaStream_t s) {
+  if (a.floorlist == nullptr) return cudaSuccess;
   const int g2 = grid_for(p.isize / 8 + 1, 128);
-  if (a.floorlist) {
-    if (p.metric == KERR_SCHILD)
-      k_update_floors<KERR_SCHILD, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
-    else
-      k_update_floors<MINKOWSKI, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (a.worklist == nullptr) return cudaSuccess;
   if (p.metric == KERR_SCHILD)
-    k_update_deferred<KERR_SCHILD, T><<<g2, 128, 0, s>>>((T*)P, a, p);
+    k_update_floors<KERR_SCHILD, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
   else
-    k_update_deferred<MINKOWSKI, T><<<g2, 128, 0, s>>>((T*)P, a, p);
+    k_update_floors<MINKOWSKI, T><<<g2, 128, 0, s>>>((const T*)P, a, p);
   return cudaGetLastError();
 }
 

@@ -728,12 +728,15 @@ __global__ void __launch_bounds__(128, kUpdateMinBlocks<T>) k_update(T* __restri
   cs.flush(a.stats);
 }
 
-// Mixed form, second pass for cell t: the double con2prim of a cell whose first pass did not settle,
-// resumed from that pass's double iterate mu_r when it has one (grouped so that a warp's lanes do the
-// same work). Unew holds its conserved state.
+// Mixed form, passes over the cells whose float con2prim phase in k_update did not settle (Unew holds their
+// conserved state). Pass 1 (full = false, cell t with tag wl_tag + t from the worklist): one double Newton
+// step resumed from that phase's double iterate mu_r; a cell whose step does not settle is queued on the
+// solve list (or solved in place without one). Pass 2 (full = true, from the solve list): the full double
+// con2prim, warm-started from the current primitives. Nine in ten worklist cells settle in pass 1, and the
+// full iteration, ten times as long, runs only in warps of cells that need it.
 template <int METRIC, class T>
 __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict__ P, const StageArgs& a, long long t,
-                                              double mu_r, CellStats& cs) {
+                                              double mu_r, bool full, long long wl_tag, CellStats& cs) {
   const long long n = p.isize, G = p.gsize;
   const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
   const long long g = gidx(p, i, j, k);
@@ -741,18 +744,25 @@ __device__ __forceinline__ void deferred_cell(const DevParams& p, T* __restrict_
   double isg, fr;
   cell_metric<METRIC>(p, t, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
                       p.x0[2] + (k + 0.5) * p.dx[2], m, isg, fr);
-  double Pc[NV], Un[NV], Uc[NV];
+  double Uc[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    Pc[q] = (double)LDC(P, q * G + g, NV * G);
-    Un[q] = LDC(a.Unew, q * n + t, NV * n);
-  }
-#pragma unroll
-  for (int q = 0; q < NV; ++q) Uc[q] = Un[q] * isg;
-  const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
+  for (int q = 0; q < NV; ++q) Uc[q] = LDC(a.Unew, q * n + t, NV * n) * isg;
   double Pn[NV];
-  int iters;
-  int st = con2prim_resume<double>(p, m, Uc, mu0, mu_r, Pn, iters);
+  int iters = 0, st = 0;
+  if (full || !con2prim_resume_step<double>(p, m, Uc, mu_r, Pn, iters)) {
+    if (!full && a.solvelist != nullptr) {
+      STC(a.solvelist, atomicAdd(a.sl_count, 1u), n, (int)(wl_tag + t));
+      cs.it_sum += iters;
+      return;
+    }
+    double Pc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Pc[q] = (double)LDC(P, q * G + g, NV * G);
+    const double mu0 = mu_of_prims<double>(Pc, m.gam, p.gamma_eos);
+    int it2 = 0;
+    st = con2prim<double>(p, m, Uc, mu0, Pn, it2, true);
+    iters += it2;
+  }
   st |= apply_floors_fr(p, m.gam, fr, Pn);
   if (st) {
     double U5[5];
@@ -793,13 +803,17 @@ __global__ void __launch_bounds__(128) k_update_floors(const T* __restrict__ P, 
 }
 
 template <int METRIC, class T>
-__global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, StageArgs a, DevParams p) {
-  const unsigned int cnt = *a.wl_count;
+__global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, StageArgs a, DevParams p, int full) {
+  const unsigned int cnt = full ? *a.sl_count : *a.wl_count;
   CellStats cs;
-  for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x)
-    deferred_cell<METRIC, T>(p, P, a, LDC(a.worklist, w, p.isize), LDC(a.wl_mu, w, p.isize), cs);
+  for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
+    if (full)
+      deferred_cell<METRIC, T>(p, P, a, LDC(a.solvelist, w, p.isize), 0.0, true, 0, cs);
+    else
+      deferred_cell<METRIC, T>(p, P, a, LDC(a.worklist, w, p.isize), LDC(a.wl_mu, w, p.isize), false, 0, cs);
+  }
   cs.flush(a.stats);
-  if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
+  if (!full && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
 }
 
 // ------------------------------------------------------------------ batched (many meshblocks)
@@ -831,6 +845,8 @@ __device__ __forceinline__ StageArgs block_stage_args(const BlockDesc& b, const 
   s.wl_mu = a.wl_mu;
   s.floorlist = a.floorlist;
   s.fl_count = a.fl_count;
+  s.solvelist = a.solvelist;
+  s.sl_count = a.sl_count;
   return s;
 }
 
@@ -934,14 +950,14 @@ __global__ void __launch_bounds__(128) k_batch_update(const BlockDesc* __restric
   cs.flush(a.stats);
 }
 
-// Deferred con2prim cells of the batch: worklist entries are batch-wide cell indices.
+// Deferred con2prim cells of the batch (deferred_cell's two passes): list entries are batch-wide cell indices.
 template <int METRIC, class T>
 __global__ void __launch_bounds__(128) k_batch_deferred(const BlockDesc* __restrict__ blocks, int nblocks,
-                                                        BatchArgs a) {
-  const unsigned int cnt = *a.wl_count;
+                                                        BatchArgs a, int full) {
+  const unsigned int cnt = full ? *a.sl_count : *a.wl_count;
   CellStats cs;
   for (unsigned int w = blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += gridDim.x * blockDim.x) {
-    const long long gcell = a.worklist[w];
+    const long long gcell = full ? a.solvelist[w] : a.worklist[w];
     int lo = 0, hi = nblocks - 1;  // last block whose cell_offset <= gcell
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -949,10 +965,11 @@ __global__ void __launch_bounds__(128) k_batch_deferred(const BlockDesc* __restr
     }
     const BlockDesc& b = blocks[lo];
     const StageArgs sa = block_stage_args(b, a);
-    deferred_cell<METRIC, T>(b.p, (T*)b.P, sa, gcell - b.cell_offset, a.wl_mu[w], cs);
+    deferred_cell<METRIC, T>(b.p, (T*)b.P, sa, gcell - b.cell_offset, full ? 0.0 : a.wl_mu[w], full != 0,
+                             b.cell_offset, cs);
   }
   cs.flush(a.stats);
-  if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
+  if (!full && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
 }
 
 template <int METRIC, class T>

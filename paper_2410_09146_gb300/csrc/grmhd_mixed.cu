@@ -58,16 +58,21 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
   return cudaGetLastError();
 }
 
-// Pass over the cells queued by k_update (count known on the device only): the double con2prim of cells
-// whose float phase did not settle. (Floored cells are re-derived inside k_update in this form.)
+// Passes over the cells queued by k_update (counts known on the device only): the double con2prim of cells
+// whose float phase did not settle, resumed (pass 1), then in full for those whose resumed step did not
+// settle (pass 2). (Floored cells are re-derived inside k_update in this form.)
 cudaError_t cell_passes(const DevParams& p, void* P, const StageArgs& a, cudaStream_t s) {
-  const int g2 = grid_for(p.isize / 8 + 1, 128);
   if (a.worklist == nullptr) return cudaSuccess;
-  if (p.metric == KERR_SCHILD)
-    k_update_deferred<KERR_SCHILD, T><<<g2, 128, 0, s>>>((T*)P, a, p);
-  else
-    k_update_deferred<MINKOWSKI, T><<<g2, 128, 0, s>>>((T*)P, a, p);
-  return cudaGetLastError();
+  const int g2 = grid_for(p.isize / 8 + 1, 128);
+  for (int full = 0; full < (a.solvelist ? 2 : 1); ++full) {
+    if (p.metric == KERR_SCHILD)
+      k_update_deferred<KERR_SCHILD, T><<<g2, 128, 0, s>>>((T*)P, a, p, full);
+    else
+      k_update_deferred<MINKOWSKI, T><<<g2, 128, 0, s>>>((T*)P, a, p, full);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t prim2con(const DevParams& p, const void* P, double* U, cudaStream_t s) {

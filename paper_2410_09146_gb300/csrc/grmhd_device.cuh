@@ -218,12 +218,20 @@ __host__ __device__ constexpr int sym3(int i, int j) {
   return i <= j ? (i == 0 ? j : (i == 1 ? 2 + j : 5)) : (j == 0 ? i : (j == 1 ? 2 + i : 5));
 }
 
-// Geometry cache entries: alpha, beta^i (3), gamma_ij (6), gamma^ij (6), sqrt(gamma), 1/sqrt(gamma) and
-// the floor radius factor r^-floor_r_exp.
-constexpr int NGEO = 19;
+// Geometry cache entries: alpha, beta^i (3), gamma_ij (6), gamma^ij (6), sqrt(gamma), 1/sqrt(gamma), the
+// floor radius factor r^-floor_r_exp, then the Kerr-Schild factors f, kappa = f/(1+f) and l_i (5), from which
+// gamma_ij = delta_ij + f l_i l_j and gamma^ij = delta^ij - kappa l^i l^j: the mixed form's con2prim reads
+// these and 1/sqrt(gamma) (6 doubles) instead of the two matrices (13).
+constexpr int NGEO = 24;
+
+// The spatial metric as the mixed form's con2prim takes it: gamma_ij = delta_ij + f l_i l_j,
+// gamma^ij = delta^ij - kappa l^i l^j (Kerr-Schild, kappa = f/(1+f); flat space: f = kappa = 0).
+struct KSGeo {
+  double f, kappa, l[3];
+};
 
 __device__ __forceinline__ void geo_store(double* __restrict__ geo, long long n, long long t, const Metric<double>& m,
-                                          double isg, double fr) {
+                                          double isg, double fr, const KSGeo& k) {
   geo[t] = m.alpha;
 #pragma unroll
   for (int i = 0; i < 3; ++i) geo[(1 + i) * n + t] = m.beta[i];
@@ -235,6 +243,10 @@ __device__ __forceinline__ void geo_store(double* __restrict__ geo, long long n,
   geo[16 * n + t] = m.sqrtgam;
   geo[17 * n + t] = isg;
   geo[18 * n + t] = fr;
+  geo[19 * n + t] = k.f;
+  geo[20 * n + t] = k.kappa;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) geo[(21 + i) * n + t] = k.l[i];
 }
 
 __device__ __forceinline__ void geo_load(const double* __restrict__ geo, long long n, long long t, Metric<double>& m,
@@ -997,7 +1009,7 @@ enum { C2P_DEFERRED = 256 };
 // root equals f's. Returns the status bits of the solve (floors are applied by the caller) or C2P_DEFERRED
 // when the double step from the float root is not small (defer == true; mu_r then holds the double iterate
 // the double pass resumes from); without defer such a cell takes the full double iteration here.
-__device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric<double>& m, double isg,
+__device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const KSGeo& gm, double isg,
                                                 const double Un[NV], float mu_guess, bool defer, float Pf[NV],
                                                 int& iters, double& mu_r) {
   // Lanes entering together; each of them reaches the __syncwarp below exactly once (no return before it).
@@ -1021,13 +1033,14 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Metric
     const double rl[3] = {Un[1] * s, Un[2] * s, Un[3] * s};
     const double tb = isg * isD;
     const double bu[3] = {Un[5] * tb, Un[6] * tb, Un[7] * tb};
-    double ru[3], bl[3];
-    lower3(m.gamu, rl, ru);
-    lower3(m.gam, bu, bl);
+    // r^i = gamma^ij r_j = r_i - kappa (l.r) l^i, b^2 = b.b + f (l.b)^2 (Kerr-Schild form of the 3-metric)
+    const double klr = gm.kappa * (gm.l[0] * rl[0] + gm.l[1] * rl[1] + gm.l[2] * rl[2]);
+    const double ru[3] = {rl[0] - klr * gm.l[0], rl[1] - klr * gm.l[1], rl[2] - klr * gm.l[2]};
+    const double lb = gm.l[0] * bu[0] + gm.l[1] * bu[1] + gm.l[2] * bu[2];
     c.D = D;
     c.q = Un[4] * s;
     c.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
-    c.b2 = bu[0] * bl[0] + bu[1] * bl[1] + bu[2] * bl[2];
+    c.b2 = bu[0] * bu[0] + bu[1] * bu[1] + bu[2] * bu[2] + gm.f * lb * lb;
     c.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
     c.rb2 = c.rb * c.rb;
     c.gm1 = p.gamma_eos - 1.0;

@@ -451,9 +451,15 @@ __global__ void k_geometry(DevParams p, double* __restrict__ geo) {
     const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
     Metric<double> m;
     double r;
-    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
-                              p.x0[2] + (k + 0.5) * p.dx[2], m, &r);
-    geo_store(geo, p.isize, t, m, 1.0 / m.sqrtgam, METRIC == KERR_SCHILD ? floor_factor(p, r) : 1.0);
+    const double x = p.x0[0] + (i + 0.5) * p.dx[0], y = p.x0[1] + (j + 0.5) * p.dx[1], z = p.x0[2] + (k + 0.5) * p.dx[2];
+    metric_at<double, METRIC>(p, x, y, z, m, &r);
+    KSGeo kg{0.0, 0.0, {0.0, 0.0, 0.0}};
+    if (METRIC == KERR_SCHILD) {
+      double rr, r2;
+      ks_core<double>(x, y, z, p.a, p.M, rr, r2, kg.f, kg.l);
+      kg.kappa = kg.f / (1.0 + kg.f);
+    }
+    geo_store(geo, p.isize, t, m, 1.0 / m.sqrtgam, METRIC == KERR_SCHILD ? floor_factor(p, r) : 1.0, kg);
   }
 }
 
@@ -493,14 +499,14 @@ struct CellStats {
   }
 };
 
-// The part of a geometry-cache entry the mixed form's con2prim needs in double: gamma_ij, gamma^ij, 1/sqrt(gamma).
-__device__ __forceinline__ void geo_load_c2p(const double* __restrict__ geo, long long n, long long t,
-                                             Metric<double>& m, double& isg) {
+// The part of a geometry-cache entry the mixed form's con2prim needs in double: the Kerr-Schild factors of
+// the 3-metric and 1/sqrt(gamma).
+__device__ __forceinline__ void geo_load_c2p(const double* __restrict__ geo, long long n, long long t, KSGeo& k,
+                                             double& isg) {
+  k.f = geo[19 * n + t];
+  k.kappa = geo[20 * n + t];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    m.gam[i] = geo[(4 + i) * n + t];
-    m.gamu[i] = geo[(10 + i) * n + t];
-  }
+  for (int i = 0; i < 3; ++i) k.l[i] = geo[(21 + i) * n + t];
   isg = geo[17 * n + t];
 }
 
@@ -544,8 +550,8 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
     Un[6] = 0.5 * (LDC(bn, G + g, 3 * G) + LDC(bn, G + g + sy, 3 * G));
     Un[7] = 0.5 * (LDC(bn, 2 * G + g, 3 * G) + LDC(bn, 2 * G + g + sz, 3 * G));
   }
-  Metric<double> m;
-  double isg;
+  KSGeo gm{0.0, 0.0, {0.0, 0.0, 0.0}};  // flat space
+  double isg = 1.0;
   if (METRIC == KERR_SCHILD && p.geo != nullptr) {
 #ifdef GRMHD_BOUNDS_CHECK
     if (t < 0 || t >= n) {
@@ -553,18 +559,20 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
       t = 0;
     }
 #endif
-    geo_load_c2p(p.geo, n, t, m, isg);
-  } else {
-    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
-                              p.x0[2] + (k + 0.5) * p.dx[2], m);
-    isg = 1.0 / m.sqrtgam;
+    geo_load_c2p(p.geo, n, t, gm, isg);
+  } else if (METRIC == KERR_SCHILD) {
+    double r, r2;
+    ks_core<double>(p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1], p.x0[2] + (k + 0.5) * p.dx[2],
+                    p.a, p.M, r, r2, gm.f, gm.l);
+    gm.kappa = gm.f / (1.0 + gm.f);
+    isg = 1.0 / sqrt(1.0 + gm.f);
   }
   // warm start mu = 1/(h W) of the current primitives, in float (it only seeds the float phase)
   const float mu0 = mu_of_prims<float>(Pr, mr.gam, p.fgamma);
   float Pn[NV];
   int iters;
   double mu_r;
-  int st = con2prim_mixed_f(p, m, isg, Un, mu0, a.worklist != nullptr, Pn, iters, mu_r);
+  int st = con2prim_mixed_f(p, gm, isg, Un, mu0, a.worklist != nullptr, Pn, iters, mu_r);
   if (st == C2P_DEFERRED) {
     // finished by deferred_cell: keep P (the warm start), store the new conserved state
 #pragma unroll

@@ -630,12 +630,13 @@ def run_batched(G, I, steps, warmup, rank):
 # on the 96^3 Kerr-Schild random block (summaries under profiles/): double-precision flops (DADD + DMUL +
 # 2 DFMA, active lanes) per cell of k_update (mean of the g0 = 0 and g0 != 0 stages), float flops (FADD + FMUL
 # + 2 FFMA) per face of k_flux_cc (mean of the three directions), DRAM bytes (read + write) per unit.
-UPDATE_FP64_FLOP_PER_CELL = 194.7
-UPDATE_DRAM_BYTES_PER_CELL = 387.6
+UPDATE_FP64_FLOP_PER_CELL = 158.0
+UPDATE_DRAM_BYTES_PER_CELL = 324.2
 # algorithmic bytes per cell of k_update: P (8 float) + Ucur (8 double) + U0 (8 double, stages with g0 != 0)
-# + 3 x 8 face fluxes (float) + 3 EMFs (float) + 13 doubles of cached geometry read; Unew (8 double) + P (8
-# float) + status written; the mean over the two stages of an RK2 step
-UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 104 + 64 + 32 + 1
+# + 3 x 8 face fluxes (float) + 3 EMFs (float) + 6 doubles of cached geometry (the Kerr-Schild f, f/(1+f),
+# l_i and 1/sqrt(gamma)) read; Unew (8 double) + P (8 float) + status written; the mean over the two stages
+# of an RK2 step
+UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 48 + 64 + 32 + 1
 FLUX_FP32_FLOP_PER_FACE = 2400.0
 FLUX_DRAM_BYTES_PER_FACE = 41.6
 
@@ -677,8 +678,8 @@ def roofline(dom, ms, n, stats, fp_peaks, ms_stage, peaks):
                 "hbm_frac": UPDATE_ALGO_BYTES_PER_CELL * cells / (ms / 1e3) / 1e9 / hbm if hbm else None,
                 "stage_hbm": stage_hbm,
                 "note": "FP64 pipe (issue-bound: one warp FP64 instruction costs the same pipe time whatever its "
-                        "active lanes; ncu: FP64 pipe 75% busy at 58% active lanes per instruction, the rest are "
-                        "float<->double conversions); peak = the DFMA rate measured live on this GPU by grmhd_fp_peaks "
+                        "active lanes; ncu: FP64 pipe ~70% busy, the rest of its time float<->double conversions and "
+                        "partly active warps); peak = the DFMA rate measured live on this GPU by grmhd_fp_peaks "
                         "(MEASURED_PEAKS.json has no FP64 figure); traffic scaled from the 96^3 ncu capture by "
                         "cell count"}
     faces = 3 * (n + 1) * (n + 2) ** 2 / 3.0

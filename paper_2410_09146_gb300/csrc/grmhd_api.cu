@@ -241,11 +241,11 @@ cudaError_t collect_timing(grmhd_ctx* c) {
 constexpr int kMinTile = 128;
 
 // Units per work item of a phase: `tile` faces / edges / cells; for the run units of the cell-centric
-// five-point fluxes (~FLUX_RUN faces each) tile / FLUX_RUN of them, at least 128 so that a CTA is filled.
+// five-point fluxes (~flux_run faces each) tile / flux_run of them, at least 128 so that a CTA is filled.
 // The x units of those fluxes are lanes of whole warps: their items hold a multiple of 32 of them.
 int phase_tile(const DevParams& p, int tile, int phase) {
   if ((phase == 1 || phase == 2) && cell_centric(p.recon)) {
-    const int t = tile / FLUX_RUN;
+    const int t = tile / (p.flux_run > 0 ? p.flux_run : FLUX_RUN);
     return t < 128 ? 128 : t;
   }
   if (phase == 0 && cell_centric(p.recon)) return (tile + 31) / 32 * 32;
@@ -411,6 +411,12 @@ int grmhd_create(const grmhd_params* p, void* workspace, size_t bytes, void* str
   }
   c->prm = *p;
   c->dp = dev_params(p);
+  {  // runs of the y / z flux units sized to fill this GPU with this one block (batches keep FLUX_RUN)
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      c->dp.flux_run = flux_run_for(p->nx, p->ny, p->nz, nsm);
+  }
   c->L = p->precision == GRMHD_MIXED ? &mixed_launchers() : &fp64_launchers();
   c->stream = (cudaStream_t)stream;
   c->ws = (char*)workspace;

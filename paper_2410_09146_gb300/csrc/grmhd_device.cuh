@@ -50,6 +50,7 @@ struct DevParams {
   float fx0[3], fdx[3], fidx[3], fa, fM, fgamma, fweno_eps, frho_floor0, feps_floor0, fw_max2, fshift[3];
   float fv0sq_cap;
   int floor_r2;  // floor_r_exp == 2 (the radius factor is 1/r^2)
+  int flux_run;  // faces per run of the cell-centric y / z flux units (0: FLUX_RUN)
   // Bounds-check build (GRMHD_BOUNDS_CHECK): the word where the first out-of-range access of a stage kernel
   // is recorded (see bounds_fault); unused otherwise.
   unsigned long long* fault;
@@ -680,20 +681,33 @@ __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
 }
 
 // Work units of the flux phase of direction d: faces (face-centric reconstructions), or, for
-// WENO5-Z-AOAH, (transverse position, run of ~FLUX_RUN faces along d) pairs (cell-centric: each cell
-// reconstructed once per direction). The transverse positions span [-1, n] in both directions. Runs of 32
-// faces: at 256^3 the y / z sweeps take 1.95 ms against 2.08 with runs of 16 and 2.23 with runs of 8 (each
-// run reloads and reconstructs the window of the cell before it).
+// WENO5-Z-AOAH and MP5, (transverse position, run of ~p.flux_run faces along d) pairs (cell-centric: each
+// cell reconstructed once per direction, plus the cell before each run). The transverse positions span
+// [-1, n] in both directions. Runs of 32 faces by default: at 256^3 the y / z sweeps took 1.95 ms against
+// 2.08 with runs of 16 and 2.23 with runs of 8. A single-block context picks shorter runs (down to
+// FLUX_RUN_MIN) when its columns are too few to fill the GPU with runs of 32 (flux_run_for).
 constexpr int FLUX_RUN = 32;
+constexpr int FLUX_RUN_MIN = 8;
+
+// Run length for a block of nx x ny x nz cells alone on a GPU of nsm SMs: long enough to amortise the extra
+// cell of each run, short enough that the y / z units give every SM two waves of 8 CTAs of 128 threads.
+__host__ __forceinline__ int flux_run_for(int nx, int ny, int nz, int nsm) {
+  const long long target = (long long)nsm * 8 * 128 * 2;
+  const long long cols = (long long)(nx + 2) * ((ny < nz ? ny : nz) + 2);
+  const int nd = ny > nz ? ny : nz;
+  long long run = (long long)(nd + 1) * cols / (target > 0 ? target : 1);
+  run = run < FLUX_RUN_MIN ? FLUX_RUN_MIN : (run > FLUX_RUN ? FLUX_RUN : run);
+  return (int)run;
+}
 
 // Runs per column of nd + 1 faces (nd + 1 >= FLUX_RUN: runs of FLUX_RUN to 2 FLUX_RUN - 1 faces) and their
 // common length (the last run takes the remainder).
-__host__ __device__ __forceinline__ int flux_runs(int nd) {
-  const int r = (nd + 1) / FLUX_RUN;
+__host__ __device__ __forceinline__ int flux_runs(const DevParams& p, int nd) {
+  const int r = (nd + 1) / (p.flux_run > 0 ? p.flux_run : FLUX_RUN);
   return r > 0 ? r : 1;
 }
-__host__ __device__ __forceinline__ int flux_run_length(int nd) {
-  const int r = flux_runs(nd);
+__host__ __device__ __forceinline__ int flux_run_length(const DevParams& p, int nd) {
+  const int r = flux_runs(p, nd);
   return (nd + 1 + r - 1) / r;
 }
 
@@ -712,7 +726,7 @@ __host__ __device__ __forceinline__ long long flux_units(const DevParams& p, int
   if (cell_centric(p.recon)) {
     const int nd = d == 0 ? p.nx : (d == 1 ? p.ny : p.nz);
     const int na = d == 0 ? p.ny : p.nx, nb = d == 2 ? p.ny : p.nz;
-    return (long long)(na + 2) * (nb + 2) * flux_runs(nd);
+    return (long long)(na + 2) * (nb + 2) * flux_runs(p, nd);
   }
   int ex, ey;
   return face_box(p, d, ex, ey);

@@ -171,34 +171,23 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   const int a = (int)(t % (na + 2)) - 1;
   const long long rest = t / (na + 2);
   const int b = (int)(rest % (nb + 2)) - 1;
-  const int run = flux_run_length(nd);
+  const int run = flux_run_length(p, nd);
   const int f0 = (int)(rest / (nb + 2)) * run;
   const int f1 = min(f0 + run, nd + 1);
-  int i = d == 0 ? f0 : a;
-  int j = d == 1 ? f0 : (d == 0 ? a : b);
-  int k = d == 2 ? f0 : b;
+  // start at the cell before the run: its plus side is the left state of the run's first face
+  int i = d == 0 ? f0 - 1 : a;
+  int j = d == 1 ? f0 - 1 : (d == 0 ? a : b);
+  int k = d == 2 ? f0 - 1 : b;
   const bool inner_t = a >= 0 && a < na && b >= 0 && b < nb;  // interior transverse position
   long long g = gidx(p, i, j, k);
-  // The cell before the run is reconstructed before the loop, every other cell inside it. In the float
-  // form the two inlined copies may round differently under FMA contraction, so a cell's face values can
-  // differ in the last bit with where runs start (they move with the block size): the float form is
-  // bitwise reproducible for one block layout, not across layouts. One call site for all cells costs
-  // ~0.45 ms per 256^3 stage (measured), so the faster form is kept; the double form is built without
-  // contraction and does not depend on the layout.
-  // plus side of cell f0 - 1
+  // Every cell, the one before the run included, is reconstructed at the one call site below, so a cell's
+  // face values do not depend on where runs start (float FMA contraction could otherwise round two inlined
+  // copies differently): the float form gives the same bits for any run layout, hence for any run length
+  // and block size.
   R PL[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    const long long c0 = q * p.gsize + g - sd;
-    R qm, qp;
-    recon_cell<R, RECON>(R(LDC(P, c0 - 2 * sd, NV * p.gsize)), R(LDC(P, c0 - sd, NV * p.gsize)),
-                         R(LDC(P, c0, NV * p.gsize)), R(LDC(P, c0 + sd, NV * p.gsize)),
-                         R(LDC(P, c0 + 2 * sd, NV * p.gsize)), eps, qm, qp);
-    PL[q] = qp;
-  }
   R cm_run = R(0);
-  for (int f = f0; f < f1; ++f) {
-    // window of cell f: cells f - 2 .. f + 2
+  for (int f = f0 - 1; f < f1; ++f) {
+    // stencil of cell f: cells f - 2 .. f + 2
     R PR[NV], QP[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
@@ -210,14 +199,15 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
       PR[q] = qm;
       QP[q] = qp;
     }
-    R Fh[NV];
-    const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
+    if (f >= f0) {  // face f: the plus side of cell f - 1 and the minus side of cell f
+      R Fh[NV];
+      const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      STC(F, q * p.gsize + g, NV * p.gsize, Fh[q]);
-      PL[q] = QP[q];
+      for (int q = 0; q < NV; ++q) STC(F, q * p.gsize + g, NV * p.gsize, Fh[q]);
+      if (inner_t && cm > cm_run) cm_run = cm;
     }
-    if (inner_t && cm > cm_run) cm_run = cm;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) PL[q] = QP[q];
     g += sd;
     if (d == 0) ++i; else if (d == 1) ++j; else ++k;
   }

@@ -637,8 +637,8 @@ UPDATE_DRAM_BYTES_PER_CELL = 324.2
 # l_i and 1/sqrt(gamma)) read; Unew (8 double) + P (8 float) + status written; the mean over the two stages
 # of an RK2 step
 UPDATE_ALGO_BYTES_PER_CELL = 32 + 64 + 32 + 96 + 12 + 48 + 64 + 32 + 1
-FLUX_FP32_FLOP_PER_FACE = 2400.0
-FLUX_DRAM_BYTES_PER_FACE = 41.6
+FLUX_FP32_FLOP_PER_FACE = 1811.2
+FLUX_DRAM_BYTES_PER_FACE = 48.4
 
 
 # Algorithmic bytes per interior zone per stage of the fused-ideal mixed form (primitives in float, state in

@@ -301,21 +301,25 @@ static void flux_from_fluid(const Geom& G, const Fluid& F, const double* U, int 
 
 // Characteristic speeds in direction d. The paper does not state them; this is the
 // Valencia sound-speed formula (Banyuls et al. 1997) with the sound speed replaced by
-// the approximate fast speed c^2 = vA^2 + cs^2 (1 - vA^2).
+// the approximate fast speed c^2 = vA^2 + cs^2 (1 - vA^2). Its factors 1 - v^2, 1 - c^2 and
+// 1 - v^2 c^2 are taken in the equal forms 1/W^2 (the Lorentz factor's definition),
+// (1 - vA^2)(1 - cs^2) with 1 - vA^2 = rho h/(rho h + b^2), and (1 - c^2) + c^2 (1 - v^2): the
+// differences 1 - v^2 etc. would round with an error amplified by W^2 (1e4 at the W cap).
 static void speeds_from_fluid(const orc_params& p, const Geom& G, const Fluid& F, int d, double& lm, double& lp) {
   const double rhoh = F.rho * F.h;
   const double cs2 = p.gamma_eos * F.p / rhoh;
   const double va2 = F.b2 / (rhoh + F.b2);
   const double c2 = va2 + cs2 * (1.0 - va2);
-  double v2 = 0.0;
-  for (int i = 1; i <= 3; ++i) v2 += F.v[i] * F.vl[i];
+  const double one_v2 = 1.0 / (F.W * F.W);
+  const double one_c2 = rhoh / (rhoh + F.b2) * (1.0 - cs2);
+  const double one_v2c2 = one_c2 + c2 * one_v2;
   const double vd = F.v[d];
-  double disc = (1.0 - v2) * (G.gamu[d][d] * (1.0 - v2 * c2) - vd * vd * (1.0 - c2));
+  double disc = one_v2 * (G.gamu[d][d] * one_v2c2 - vd * vd * one_c2);
   if (disc < 0.0) disc = 0.0;
   const double c = std::sqrt(c2);
-  const double pre = G.alpha / (1.0 - v2 * c2);
-  lp = pre * (vd * (1.0 - c2) + c * std::sqrt(disc)) - G.beta[d];
-  lm = pre * (vd * (1.0 - c2) - c * std::sqrt(disc)) - G.beta[d];
+  const double pre = G.alpha / one_v2c2;
+  lp = pre * (vd * one_c2 + c * std::sqrt(disc)) - G.beta[d];
+  lm = pre * (vd * one_c2 - c * std::sqrt(disc)) - G.beta[d];
 }
 
 // Stress-energy tensor (eq. T^{mu nu}).

@@ -421,19 +421,11 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   const R cs2 = fdiv(gamma_eos * pgas, rhoh);
   const R va2 = fdiv(b2, rhoh + b2);
   const R c2 = va2 + cs2 * (R(1) - va2);
-  R one_v2, one_c2, one_v2c2;  // 1 - v^2, 1 - c^2 and 1 - v^2 c^2
-  if constexpr (sizeof(R) == 4) {
-    // float faces: 1 - v^2 = 1/W^2, 1 - c^2 = (1 - vA^2)(1 - cs^2) with 1 - vA^2 = rho h/(rho h + b^2), and
-    // 1 - v^2 c^2 = (1 - c^2) + c^2/W^2, instead of differences whose rounding grows like W^2
-    one_v2 = iW * iW;
-    one_c2 = fdiv(rhoh, rhoh + b2) * (R(1) - cs2);
-    one_v2c2 = one_c2 + c2 * one_v2;
-  } else {
-    const R v2 = usq * iW * iW;
-    one_v2 = R(1) - v2;
-    one_c2 = R(1) - c2;
-    one_v2c2 = R(1) - v2 * c2;
-  }
+  // 1 - v^2 = 1/W^2, 1 - c^2 = (1 - vA^2)(1 - cs^2) with 1 - vA^2 = rho h/(rho h + b^2), and
+  // 1 - v^2 c^2 = (1 - c^2) + c^2/W^2, instead of differences whose rounding grows like W^2
+  const R one_v2 = rcp(W * W);
+  const R one_c2 = fdiv(rhoh, rhoh + b2) * (R(1) - cs2);
+  const R one_v2c2 = one_c2 + c2 * one_v2;
   R disc = one_v2 * (sel3(d, m.gamu[0], m.gamu[3], m.gamu[5]) * one_v2c2 - vd * vd * one_c2);
   disc = disc > R(0) ? disc : R(0);
   const R pre = fdiv(m.alpha, one_v2c2);

@@ -677,9 +677,10 @@ __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
 // cell reconstructed once per direction, plus the cell before each run). The transverse positions span
 // [-1, n] in both directions. Runs of 32 faces by default: at 256^3 the y / z sweeps took 1.95 ms against
 // 2.08 with runs of 16 and 2.23 with runs of 8. A single-block context picks shorter runs (down to
-// FLUX_RUN_MIN) when its columns are too few to fill the GPU with runs of 32 (flux_run_for).
+// FLUX_RUN_MIN) when its columns are too few to fill the GPU with runs of 32 (flux_run_for): at 64^3 the
+// y / z sweeps take 0.039 ms with runs of 4, 0.047 with 8; at 96^3 and 128^3 runs of 4 to 8 tie.
 constexpr int FLUX_RUN = 32;
-constexpr int FLUX_RUN_MIN = 8;
+constexpr int FLUX_RUN_MIN = 4;
 
 // Run length for a block of nx x ny x nz cells alone on a GPU of nsm SMs: long enough to amortise the extra
 // cell of each run, short enough that the y / z units give every SM two waves of 8 CTAs of 128 threads.

@@ -251,8 +251,8 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
 }
 
 // Resident CTAs per SM the float cell-centric flux kernels are compiled for: 8 x 128 threads at 64
-// registers, the best of the occupancy / spill trade-off measured at 256^3 (the loads of the P window are
-// latency-bound; the double form is bound by FP64 issue and keeps its registers).
+// registers, the best of the occupancy / spill trade-off measured at 256^3 (6 CTAs at 80 registers: the
+// same x time, y / z 1.15 ms against 1.13; the double form is bound by FP64 issue and keeps its registers).
 template <class R>
 constexpr int kFluxMinBlocks = sizeof(R) == 4 ? 8 : 1;
 
@@ -709,9 +709,9 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
   }
 }
 
-// Resident CTAs per SM the update kernel is compiled for: the mixed form's (double solve, ~190 registers
-// unbounded) is latency-bound at two CTAs per SM; held to four (128 registers, no spills) it runs 6.7 ms per
-// 256^3 stage against 8.45 (two) and 7.62 (three); the FP64 form keeps its registers.
+// Resident CTAs per SM the update kernel is compiled for: the mixed form's (double solve, ~170 registers
+// unbounded) is latency-bound at two CTAs per SM; held to four (123 registers, no spills) it runs 5.38 ms per
+// 256^3 stage, against 6.35 at five (96 registers, spilling); the FP64 form keeps its registers.
 template <class T>
 constexpr int kUpdateMinBlocks = sizeof(T) == 4 ? 4 : 1;
 

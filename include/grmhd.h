@@ -47,6 +47,13 @@ extern "C" {
 /* options */
 #define GRMHD_MINKOWSKI 0     /* flat space, optionally with a constant shift (params.shift) */
 #define GRMHD_KERR_SCHILD 1 /* Cartesian Kerr-Schild, spin a = spin * mass along z */
+/* Kerr-Schild in spherical coordinates (x^1, x^2, x^3) = (ln r, theta, phi) (Sec. 2.3; the coordinates of the
+ * paper's accretion set-ups, Sec. 3.2): r and the angles of the Cartesian form through x + i y = (r + i a)
+ * e^{i phi} sin(theta), z = r cos(theta). Single-block contexts, all-FP64 form, flux-CT, no passive scalar;
+ * GRMHD_BC_FIXED or GRMHD_BC_SPHERICAL. Theta faces on the polar axis carry no flux, sin(theta) times the phi
+ * components of W v and B is reconstructed, and on the axis the EMF along phi is zero and the EMF along r is
+ * its mean over phi. mass >= 0 (0: flat space in spherical coordinates). */
+#define GRMHD_KERR_SCHILD_SPHERICAL 2
 
 #define GRMHD_RECON_CONSTANT 0
 #define GRMHD_RECON_PLM_MINMOD 1
@@ -59,6 +66,10 @@ extern "C" {
 
 #define GRMHD_BC_PERIODIC 0     /* ghosts refilled from the interior at the start of every stage */
 #define GRMHD_BC_FIXED 1        /* ghosts keep the values given to grmhd_set_prims */
+/* GRMHD_KERR_SCHILD_SPHERICAL over theta in [0, pi] and phi in [0, 2 pi) with nz even: phi periodic, a ghost
+ * beyond a pole the cell mirrored across it and turned by pi in phi (the theta components of W v and B
+ * negated), refilled at the start of every stage; the radial ghosts keep their given values. */
+#define GRMHD_BC_SPHERICAL 2
 
 #define GRMHD_FP64 0            /* every step in double precision */
 #define GRMHD_MIXED 1           /* reconstruction, fluxes, EMFs and sources in float; P stored in float;
@@ -100,7 +111,7 @@ typedef struct {
   int nx, ny, nz, ng;         /* interior cells per direction (0,0,0 for a con2prim-only context); ghosts */
   double x0[3];               /* coordinate of the interior's lower corner */
   double dx[3];               /* cell widths */
-  int metric;                 /* GRMHD_MINKOWSKI | GRMHD_KERR_SCHILD (Sec. 2.3) */
+  int metric;                 /* GRMHD_MINKOWSKI | GRMHD_KERR_SCHILD | GRMHD_KERR_SCHILD_SPHERICAL (Sec. 2.3) */
   double spin, mass;          /* Kerr-Schild a/M and M */
   double gamma_eos;           /* ideal-gas index, P = (gamma_eos - 1) rho eps (Sec. 2.2) */
   int recon, riemann, precision, bc;

@@ -98,11 +98,17 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
     const double cells = (double)(p->nx + 2 * p->ng) * (p->ny + 2 * p->ng) * (p->nz + 2 * p->ng);
     if (cells > 4.0e9) { snprintf(msg, n, "block too large"); return false; }
   }
-  if (p->metric != GRMHD_MINKOWSKI && p->metric != GRMHD_KERR_SCHILD) { snprintf(msg, n, "unknown metric"); return false; }
+  if (p->metric != GRMHD_MINKOWSKI && p->metric != GRMHD_KERR_SCHILD && p->metric != GRMHD_KERR_SCHILD_SPHERICAL) {
+    snprintf(msg, n, "unknown metric");
+    return false;
+  }
   if (p->recon < 0 || p->recon > 4) { snprintf(msg, n, "unknown reconstruction"); return false; }
   if (p->riemann != GRMHD_RIEMANN_LLF && p->riemann != GRMHD_RIEMANN_HLL) { snprintf(msg, n, "unknown Riemann solver"); return false; }
   if (p->precision != GRMHD_FP64 && p->precision != GRMHD_MIXED) { snprintf(msg, n, "unknown precision"); return false; }
-  if (p->bc != GRMHD_BC_PERIODIC && p->bc != GRMHD_BC_FIXED) { snprintf(msg, n, "unknown boundary condition"); return false; }
+  if (p->bc != GRMHD_BC_PERIODIC && p->bc != GRMHD_BC_FIXED && p->bc != GRMHD_BC_SPHERICAL) {
+    snprintf(msg, n, "unknown boundary condition");
+    return false;
+  }
   if (!(p->gamma_eos > 1.0)) { snprintf(msg, n, "gamma_eos must be > 1"); return false; }
   if (!(p->c2p_tol > 0.0) || p->c2p_max_iter < 1) { snprintf(msg, n, "bad con2prim tolerance / iteration cap"); return false; }
   if (!(p->w_max > 1.0)) { snprintf(msg, n, "w_max must be > 1"); return false; }
@@ -114,6 +120,27 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   if (p->metric == GRMHD_MINKOWSKI && !(p->shift[0] * p->shift[0] + p->shift[1] * p->shift[1] + p->shift[2] * p->shift[2] < 1.0)) {
     snprintf(msg, n, "the shift must have |beta| < 1");
     return false;
+  }
+  if (p->metric == GRMHD_KERR_SCHILD_SPHERICAL) {
+    const char* why = !(p->mass >= 0.0)            ? "mass must be >= 0"
+                      : !(std::fabs(p->spin) < 1.0) ? "|spin| must be < 1"
+                      : p->precision != GRMHD_FP64  ? "spherical Kerr-Schild runs in the all-FP64 form (GRMHD_FP64)"
+                      : p->ct != GRMHD_CT_FLUX      ? "spherical Kerr-Schild runs with flux-CT (GRMHD_CT_FLUX)"
+                      : p->scalar                   ? "spherical Kerr-Schild runs without a passive scalar"
+                      : p->bc == GRMHD_BC_PERIODIC  ? "spherical Kerr-Schild takes fixed or spherical ghosts"
+                                                    : nullptr;
+    if (why) { snprintf(msg, n, "%s", why); return false; }
+  }
+  if (p->bc == GRMHD_BC_SPHERICAL) {
+    const double pi = 3.14159265358979323846;
+    const char* why =
+        p->metric != GRMHD_KERR_SCHILD_SPHERICAL ? "spherical ghosts need the spherical Kerr-Schild metric"
+        : !(std::fabs(p->x0[1]) < 1e-12 && std::fabs(p->x0[1] + p->ny * p->dx[1] - pi) < 1e-9)
+            ? "spherical ghosts need a block over theta in [0, pi]"
+        : !(std::fabs(p->nz * p->dx[2] - 2.0 * pi) < 1e-9) || p->nz % 2 ? "spherical ghosts need phi over [0, 2 pi) with nz even"
+        : p->ng > p->ny ? "spherical ghosts need ng <= ny"
+                        : nullptr;
+    if (why) { snprintf(msg, n, "%s", why); return false; }
   }
   return true;
 }
@@ -627,6 +654,8 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
   if (c->prm.bc == GRMHD_BC_PERIODIC) {
     CK(L.ghost(dp, c->P, s), "ghost fill");
     if (face) CK(L.ghost_faces(dp, c->Bslot[c->sc], s), "face ghost fill");
+  } else if (c->prm.bc == GRMHD_BC_SPHERICAL) {
+    CK(L.ghost(dp, c->P, s), "polar and azimuthal ghost fill");
   }
   for (int d = 0; d < 3; ++d) {
     TMARK(1 + d);
@@ -939,6 +968,7 @@ size_t grmhd_batch_workspace_bytes(const grmhd_params* p, int nblocks, const grm
   q.nx = blocks[0].nx; q.ny = blocks[0].ny; q.nz = blocks[0].nz;
   for (int i = 0; i < 3; ++i) q.dx[i] = blocks[0].dx[i];
   if (!valid_params(&q, msg, sizeof msg)) return 0;
+  if (p->metric == GRMHD_KERR_SCHILD_SPHERICAL) return 0;
   for (int b = 0; b < nblocks; ++b)
     if (!valid_block(blocks[b], p->ng, msg, sizeof msg)) return 0;
   return batch_layout(p, nblocks, blocks).total;
@@ -959,6 +989,10 @@ int grmhd_batch_create(const grmhd_params* p, int nblocks, const grmhd_block* bl
   q.nx = blocks[0].nx; q.ny = blocks[0].ny; q.nz = blocks[0].nz;
   for (int i = 0; i < 3; ++i) q.dx[i] = blocks[0].dx[i];
   if (!valid_params(&q, g_create_err, sizeof g_create_err)) return GRMHD_E_INVALID;
+  if (p->metric == GRMHD_KERR_SCHILD_SPHERICAL) {
+    snprintf(g_create_err, sizeof g_create_err, "batches run the Cartesian metrics (spherical Kerr-Schild: grmhd_create)");
+    return GRMHD_E_UNSUPPORTED;
+  }
   if (p->bc != GRMHD_BC_FIXED) {
     snprintf(g_create_err, sizeof g_create_err, "batched blocks take their ghosts as given (GRMHD_BC_FIXED)");
     return GRMHD_E_UNSUPPORTED;

@@ -13,7 +13,10 @@
 
 namespace grmhd {
 
-enum { MINKOWSKI = 0, KERR_SCHILD = 1 };
+// metrics: flat, Cartesian Kerr-Schild, Kerr-Schild in spherical coordinates (x^1, x^2, x^3) = (ln r, theta, phi)
+enum { MINKOWSKI = 0, KERR_SCHILD = 1, KERR_SCHILD_SPHERICAL = 2 };
+// boundaries: periodic, fixed ghosts, spherical (polar ghosts mirrored across the axis, phi periodic)
+enum { BC_PERIODIC = 0, BC_FIXED = 1, BC_SPHERICAL = 2 };
 enum { RECON_CONSTANT = 0, RECON_PLM_MINMOD = 1, RECON_PLM_MC = 2, RECON_WENO5Z = 3, RECON_MP5 = 4 };
 
 // Five-point reconstructions (WENO5-Z-AOAH, MP5) run on the cell-centric flux path.
@@ -310,6 +313,37 @@ __device__ __forceinline__ void metric_at(const DevParams& p, R x, R y, R z, Met
 #pragma unroll
     for (int t = 0; t < 6; ++t) m.gam[t] = m.gamu[t] = (t == 0 || t == 3 || t == 5) ? R(1) : R(0);
     if (rks) *rks = R(1);
+  } else if (METRIC == KERR_SCHILD_SPHERICAL) {
+    // (x, y, z) = (ln r, theta, phi). In (r, theta, phi), with Sigma = r^2 + a^2 cos^2, q = 2 M r / Sigma:
+    // alpha = (1+q)^-1/2, beta^r = q/(1+q) (beta^theta = beta^phi = 0), gamma_rr = 1+q, gamma_rphi =
+    // -a sin^2 (1+q), gamma_thth = Sigma, gamma_phph = sin^2 (Sigma + a^2 sin^2 (1+q)); the inverse of the
+    // (r, phi) block has determinant (1+q) sin^2 Sigma, so gamma^rr = 1/(1+q) + a^2 sin^2/Sigma, gamma^rphi =
+    // a/Sigma, gamma^phph = 1/(Sigma sin^2), gamma^thth = 1/Sigma; sqrt(gamma) = Sigma |sin| (1+q)^1/2. Each r
+    // index then carries a factor r (dr = r dx^1), an upper one 1/r.
+    const R a = par<R>(p.a, p.fa), M = par<R>(p.M, p.fM);
+    const R r = exp(x), sn = sin(y), cs = cos(y), s2 = sn * sn;
+    const R Sig = r * r + a * a * cs * cs;
+    const R iS = rcp(Sig);
+    const R q = R(2) * M * r * iS;
+    const R ip = rcp(R(1) + q);
+    const R ir = rcp(r);
+    m.alpha = sqrt(ip);
+    m.beta[0] = q * ip * ir;
+    m.beta[1] = m.beta[2] = R(0);
+    m.gam[0] = r * r * (R(1) + q);
+    m.gam[1] = R(0);
+    m.gam[2] = -r * a * s2 * (R(1) + q);
+    m.gam[3] = Sig;
+    m.gam[4] = R(0);
+    m.gam[5] = s2 * (Sig + a * a * s2 * (R(1) + q));
+    m.gamu[0] = (ip + a * a * s2 * iS) * ir * ir;
+    m.gamu[1] = R(0);
+    m.gamu[2] = a * iS * ir;
+    m.gamu[3] = iS;
+    m.gamu[4] = R(0);
+    m.gamu[5] = iS * rcp(s2);
+    m.sqrtgam = r * Sig * fabs(sn) * sqrt(R(1) + q);
+    if (rks) *rks = r;
   } else {
     R r, r2, f, l[3];
     ks_core<R>(x, y, z, par<R>(p.a, p.fa), par<R>(p.M, p.fM), r, r2, f, l);
@@ -353,9 +387,10 @@ struct FaceSide {
   R U[NV], F[NV], lm, lp;
 };
 
+// smg: sqrt(-g) at the face (1 in the Cartesian metrics, where the flux needs no factor).
 template <class R>
 __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, int d, R gamma_eos,
-                                             FaceSide<R>& s) {
+                                             FaceSide<R>& s, R smg = R(1)) {
   const R rho = P[0], u = P[4];
   const R ut[3] = {P[1], P[2], P[3]};
   const R B[3] = {P[5], P[6], P[7]};
@@ -416,7 +451,9 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
 #pragma unroll
   for (int k = 0; k < 3; ++k) s.F[5 + k] = B[k] * vtd - Bd * vt[k] * ia;
 #pragma unroll
-  for (int q = 0; q < NV; ++q) s.U[q] = m.sqrtgam * Uc[q];  // sqrt(-g) = 1: F is already densitized
+  for (int q = 0; q < NV; ++q) s.U[q] = m.sqrtgam * Uc[q];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) s.F[q] *= smg;  // densitized flux sqrt(-g) F^d (a no-op in Cartesian metrics)
   // Valencia characteristic speeds with the approximate fast speed c^2 = vA^2 + cs^2 (1 - vA^2).
   const R cs2 = fdiv(gamma_eos * pgas, rhoh);
   const R va2 = fdiv(b2, rhoh + b2);
@@ -1228,7 +1265,7 @@ __device__ __forceinline__ double floor_factor(const DevParams& p, double r) {
 
 template <int METRIC>
 __device__ __forceinline__ int apply_floors(const DevParams& p, const double gam[6], double r, double P[NV]) {
-  return apply_floors_fr(p, gam, METRIC == KERR_SCHILD ? floor_factor(p, r) : 1.0, P);
+  return apply_floors_fr(p, gam, METRIC != MINKOWSKI ? floor_factor(p, r) : 1.0, P);
 }
 
 // mu = 1/(h W) of a primitive state, the con2prim warm start (in the arithmetic type R).

@@ -58,10 +58,16 @@ __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, 
   const R xd = sel3(d, par<R>(p.x0[0], p.fx0[0]), par<R>(p.x0[1], p.fx0[1]), par<R>(p.x0[2], p.fx0[2])) +
                R(cd) * sel3(d, par<R>(p.dx[0], p.fdx[0]), par<R>(p.dx[1], p.fdx[1]), par<R>(p.dx[2], p.fdx[2]));
   if (d == 0) xf[0] = xd; else if (d == 1) xf[1] = xd; else xf[2] = xd;
+  if (METRIC == KERR_SCHILD_SPHERICAL && d == 1 && fabs(sin(xf[1])) < R(1e-12)) {
+    // a theta face on the polar axis has zero area (sqrt(-g) = 0 there, where the metric is singular): no flux
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Fh[q] = R(0);
+    return R(0);
+  }
   Metric<R> m;
   R rks = R(1);
   metric_at<R, METRIC>(p, xf[0], xf[1], xf[2], m, &rks);
-  const R fr = METRIC == KERR_SCHILD ? (p.floor_r2 ? rcp(rks * rks) : R(pow((double)rks, -p.floor_r_exp)))
+  const R fr = METRIC != MINKOWSKI ? (p.floor_r2 ? rcp(rks * rks) : R(pow((double)rks, -p.floor_r_exp)))
                                      : R(1);
   const R rho_flr = par<R>(p.rho_floor0, p.frho_floor0) * fr, eps_flr = par<R>(p.eps_floor0, p.feps_floor0) * fr;
   if (!(PL[0] >= rho_flr)) PL[0] = rho_flr;
@@ -75,8 +81,9 @@ __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, 
     else { PL[7] = bn; PR[7] = bn; }
   }
   FaceSide<R> L, Rs;
-  prim_to_face<R>(PL, m, d, par<R>(p.gamma_eos, p.fgamma), L);
-  prim_to_face<R>(PR, m, d, par<R>(p.gamma_eos, p.fgamma), Rs);
+  const R smg = METRIC == KERR_SCHILD_SPHERICAL ? m.alpha * m.sqrtgam : R(1);  // sqrt(-g) at the face
+  prim_to_face<R>(PL, m, d, par<R>(p.gamma_eos, p.fgamma), L, smg);
+  prim_to_face<R>(PR, m, d, par<R>(p.gamma_eos, p.fgamma), Rs, smg);
   return riemann_flux<R>(p.riemann, L, Rs, Fh);
 }
 
@@ -94,20 +101,34 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
   const long long g = gidx(p, i, j, k);
   R PL[NV], PR[NV];
   const R eps = par<R>(p.weno_eps, p.fweno_eps);
+  // Spherical coordinates: the phi components of W v and B (variables 3 and 7) grow like 1/sin(theta)
+  // towards the axis, and sin(theta) times them is regular there (continuing through it with the sign of
+  // sin(theta)), so that product is reconstructed and divided by sin(theta) at the face. The stencil cell
+  // at offset o along d has theta index j + o for d = 1, j otherwise.
+  const bool sph = METRIC == KERR_SCHILD_SPHERICAL;
+  R sfc = R(1), sw[6] = {R(1), R(1), R(1), R(1), R(1), R(1)};
+  if (sph) {
+    const R th0 = par<R>(p.x0[1], p.fx0[1]), dth = par<R>(p.dx[1], p.fdx[1]);
+    sfc = sin(d == 1 ? th0 + R(j) * dth : th0 + (R(j) + R(0.5)) * dth);
+#pragma unroll
+    for (int o = 0; o < 6; ++o) sw[o] = sin(th0 + (R(j + (d == 1 ? o - 3 : 0)) + R(0.5)) * dth);
+  }
+  const bool reg_ok = sph && fabs(sfc) > R(1e-12);
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const long long c0 = q * p.gsize + g, PN = NV * p.gsize;
-    const R fm3 = cell_centric(RECON) ? R(LDC(P, c0 - 3 * stride, PN)) : R(0);
-    const R fm2 = RECON != RECON_CONSTANT ? R(LDC(P, c0 - 2 * stride, PN)) : R(0);
-    const R fm1 = R(LDC(P, c0 - stride, PN));
-    const R f0 = R(LDC(P, c0, PN));
-    const R fp1 = RECON != RECON_CONSTANT ? R(LDC(P, c0 + stride, PN)) : R(0);
-    const R fp2 = cell_centric(RECON) ? R(LDC(P, c0 + 2 * stride, PN)) : R(0);
+    const bool reg = reg_ok && (q == 3 || q == 7);
+    const R fm3 = cell_centric(RECON) ? R(LDC(P, c0 - 3 * stride, PN)) * (reg ? sw[0] : R(1)) : R(0);
+    const R fm2 = RECON != RECON_CONSTANT ? R(LDC(P, c0 - 2 * stride, PN)) * (reg ? sw[1] : R(1)) : R(0);
+    const R fm1 = R(LDC(P, c0 - stride, PN)) * (reg ? sw[2] : R(1));
+    const R f0 = R(LDC(P, c0, PN)) * (reg ? sw[3] : R(1));
+    const R fp1 = RECON != RECON_CONSTANT ? R(LDC(P, c0 + stride, PN)) * (reg ? sw[4] : R(1)) : R(0);
+    const R fp2 = cell_centric(RECON) ? R(LDC(P, c0 + 2 * stride, PN)) * (reg ? sw[5] : R(1)) : R(0);
     R qm, qp;
     recon_cell<R, RECON>(fm3, fm2, fm1, f0, fp1, eps, qm, qp);  // cell c - e_d
-    PL[q] = qp;
+    PL[q] = reg ? qp / sfc : qp;
     recon_cell<R, RECON>(fm2, fm1, f0, fp1, fp2, eps, qm, qp);  // cell c
-    PR[q] = qm;
+    PR[q] = reg ? qm / sfc : qm;
   }
   R Fh[NV];
   const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
@@ -270,6 +291,157 @@ __global__ void __launch_bounds__(128, kFluxMinBlocks<R>) k_flux_cc(const T* __r
   if (track_speed) block_max_to<R>(cm_local, ms + d);
 }
 
+// Geometric sources in spherical Kerr-Schild coordinates (x^1, x^2, x^3) = (ln r, theta, phi), not
+// densitized (Sec. 2.1 eq. (source vector), without the radiation four-force). The metric is stationary and
+// axisymmetric, so only d_1 and d_2 of g_{mu nu} are nonzero, and for a symmetric T the momentum source
+// T^{mu nu}(d_mu g_{nu j} - Gamma^d_{nu mu} g_{d j}) reduces to S_j = 1/2 T^{mu nu} d_j g_{mu nu} (S_3 = 0).
+// The energy source alpha (T^{mu 0} d_mu ln alpha - T^{mu nu} Gamma^0_{mu nu}) uses
+// T^{mu nu} Gamma^0_{mu nu} = g^{0 d} (T^{mu nu} d_mu g_{d nu} - 1/2 T^{mu nu} d_d g_{mu nu}), where
+// g^{00} = -(1+q), g^{01} = q/r and g^{02} = g^{03} = 0. The 4-metric in (t, r, theta, phi): g_tt = -(1-q),
+// g_tr = q, g_tphi = -a sin^2 q, g_rr = 1+q, g_rphi = -a sin^2 (1+q), g_thth = Sigma, g_phph =
+// sin^2 (Sigma + a^2 sin^2 (1+q)); a component with k r indices carries r^k, and d_1 = r d/dr.
+template <class R>
+__device__ __forceinline__ void sks_sources(const DevParams& p, R x, R y, const R P[NV], const Metric<R>& m,
+                                            R S[5]) {
+  const R a = par<R>(p.a, p.fa), M = par<R>(p.M, p.fM);
+  const R r = exp(x), sn = sin(y), cs = cos(y), s2 = sn * sn, sc = sn * cs;
+  const R Sig = r * r + a * a * cs * cs;
+  const R q = R(2) * M * r / Sig;
+  const R dSr = R(2) * r, dSt = -R(2) * a * a * sc;         // d Sigma / dr, d Sigma / dtheta
+  const R dqr = R(2) * M * (Sig - r * dSr) / (Sig * Sig);    // dq / dr
+  const R dqt = -R(2) * M * r * dSt / (Sig * Sig);           // dq / dtheta
+  const R Ep = Sig + a * a * s2 * (R(1) + q);
+  // g, d_r g, d_theta g in (t, r, theta, phi), upper triangle: 00 01 03 11 13 22 33
+  const R gs[7] = {-(R(1) - q), q, -a * s2 * q, R(1) + q, -a * s2 * (R(1) + q), Sig, s2 * Ep};
+  const R gr[7] = {dqr, dqr, -a * s2 * dqr, dqr, -a * s2 * dqr, dSr, s2 * (dSr + a * a * s2 * dqr)};
+  const R gt[7] = {dqt, dqt, -a * (R(2) * sc * q + s2 * dqt), dqt, -a * (R(2) * sc * (R(1) + q) + s2 * dqt), dSt,
+                   R(2) * sc * Ep + s2 * (dSt + a * a * (R(2) * sc * (R(1) + q) + s2 * dqt))};
+  const int mi[7] = {0, 0, 0, 1, 1, 2, 3}, ni[7] = {0, 1, 3, 1, 3, 2, 3};
+  // in (t, x^1, theta, phi): d_1 (r^k g) = k r^k g + r^k r d_r g, d_2 (r^k g) = r^k d_theta g
+  R d1[4][4], d2[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) d1[u][v] = d2[u][v] = R(0);
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    const int k = (mi[c] == 1) + (ni[c] == 1);
+    const R fac = k == 0 ? R(1) : (k == 1 ? r : r * r);
+    const R v1 = R(k) * fac * gs[c] + fac * r * gr[c], v2 = fac * gt[c];
+    d1[mi[c]][ni[c]] = d1[ni[c]][mi[c]] = v1;
+    d2[mi[c]][ni[c]] = d2[ni[c]][mi[c]] = v2;
+  }
+  // fluid four-vectors and T^{mu nu}, from the 3+1 metric
+  const R ut[3] = {P[1], P[2], P[3]};
+  const R B[3] = {P[5], P[6], P[7]};
+  R utl[3], Bl[3];
+  lower3(m.gam, ut, utl);
+  lower3(m.gam, B, Bl);
+  const R W = sqrt(R(1) + ut[0] * utl[0] + ut[1] * utl[1] + ut[2] * utl[2]);
+  const R iW = R(1) / W, ia = R(1) / m.alpha;
+  R vt[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) vt[i] = m.alpha * ut[i] * iW - m.beta[i];
+  const R Bv = (B[0] * utl[0] + B[1] * utl[1] + B[2] * utl[2]) * iW;
+  const R B2 = B[0] * Bl[0] + B[1] * Bl[1] + B[2] * Bl[2];
+  const R ab0 = W * Bv;
+  const R b2 = (B2 + ab0 * ab0) * iW * iW;
+  R uc[4], bc[4];
+  uc[0] = W * ia;
+  bc[0] = ab0 * ia;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    uc[1 + i] = W * ia * vt[i];
+    bc[1 + i] = B[i] * iW + bc[0] * vt[i];
+  }
+  const R pg = (par<R>(p.gamma_eos, p.fgamma) - R(1)) * P[4];
+  const R w = P[0] + P[4] + pg + b2;
+  const R pt = pg + R(0.5) * b2;
+  const R ia2 = ia * ia;
+  R gu[4][4];
+  gu[0][0] = -ia2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gu[0][1 + i] = gu[1 + i][0] = m.beta[i] * ia2;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gu[1 + i][1 + j] = m.gamu[sym3(i, j)] - m.beta[i] * m.beta[j] * ia2;
+  }
+  R T[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) T[u][v] = w * uc[u] * uc[v] + pt * gu[u][v] - bc[u] * bc[v];
+  R td1 = R(0), td2 = R(0);  // T^{mu nu} d_1 g_{mu nu}, T^{mu nu} d_2 g_{mu nu}
+  R h0 = R(0), h1 = R(0);    // T^{mu nu} d_mu g_{0 nu}, T^{mu nu} d_mu g_{1 nu} (mu = 1, 2)
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      td1 += T[u][v] * d1[u][v];
+      td2 += T[u][v] * d2[u][v];
+    }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    h0 += T[1][v] * d1[0][v] + T[2][v] * d2[0][v];
+    h1 += T[1][v] * d1[1][v] + T[2][v] * d2[1][v];
+  }
+  S[0] = R(0);
+  S[1] = R(0.5) * td1;
+  S[2] = R(0.5) * td2;
+  S[3] = R(0);
+  const R g00 = -(R(1) + q), g01 = q / r;
+  const R TG = g00 * h0 + g01 * (h1 - R(0.5) * td1);   // T^{mu nu} Gamma^0_{mu nu}
+  // d_mu ln alpha = -1/2 d_mu q / (1 + q): d_1 with d_1 q = r dq/dr, d_2 with dq/dtheta
+  const R dla1 = -R(0.5) * r * dqr / (R(1) + q), dla2 = -R(0.5) * dqt / (R(1) + q);
+  S[4] = m.alpha * (T[1][0] * dla1 + T[2][0] * dla2 - TG);
+}
+
+// Spherical coordinates: the edges along r on the polar axis (theta faces 0 and ny) are one line for every
+// phi, where E_r is single-valued: each takes the mean over phi of the values k_emf computed there (summed
+// in phi order). One thread per (radial cell, pole).
+template <class R>
+__global__ void k_emf_axis(R* __restrict__ E, DevParams p) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * p.nx) return;
+  const int i = t % p.nx, fj = t < p.nx ? 0 : p.ny;
+  if (!(fabs(sin(p.x0[1] + fj * p.dx[1])) < 1e-12)) return;
+  const long long G = p.gsize;
+  R m = R(0);
+  for (int fk = 0; fk < p.nz; ++fk) m += LDC(E, gidx(p, i, fj, fk), 3 * G);
+  m /= R(p.nz);
+  for (int fk = 0; fk <= p.nz; ++fk) STC(E, gidx(p, i, fj, fk), 3 * G, m);
+}
+
+// a0 for a spherical block covering theta in [0, pi] and phi in [0, 2 pi) (nz even): phi is periodic, and a
+// ghost beyond a pole is the cell mirrored across it and turned by pi in phi, where the coordinate map
+// continues through the pole with d/dtheta reversed: the theta components of W v and B (variables 2 and 6)
+// change sign, the rest is copied. Radial ghosts keep their loaded values.
+template <class T>
+__global__ void k_ghost_spherical(T* __restrict__ P, DevParams p) {
+  const long long n = p.gsize;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % p.gx) - p.ng;
+    const int j = (int)((t / p.gx) % p.gy) - p.ng;
+    const int k = (int)(t / ((long long)p.gx * p.gy)) - p.ng;
+    if (i < 0 || i >= p.nx) continue;
+    const bool jin = j >= 0 && j < p.ny, kin = k >= 0 && k < p.nz;
+    if (jin && kin) continue;
+    int sj = j, sk = ((k % p.nz) + p.nz) % p.nz;
+    bool flip = false;
+    if (!jin) {
+      sj = j < 0 ? -j - 1 : 2 * p.ny - j - 1;
+      sk = (sk + p.nz / 2) % p.nz;
+      flip = true;
+    }
+    const long long src = gidx(p, i, sj, sk);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const T v = LDC(P, q * n + src, NV * n);
+      STC(P, q * n + t, NV * n, (flip && (q == 2 || q == 6)) ? -v : v);
+    }
+  }
+}
+
 // a7: dt = cfl / max_d(max|lambda_d| / dx_d)
 static __global__ void k_finalize_dt(const unsigned long long* ms, double* dt, DevParams p) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -289,9 +461,12 @@ __device__ __forceinline__ void emf_edge(const DevParams& p, const R* __restrict
   const long long sy = p.gx, sz = (long long)p.gx * p.gy;
   const int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
   const long long g = gidx(p, i, j, k);
+  // spherical coordinates: an edge along phi on the polar axis has zero length, hence a zero EMF (Omega_phi,
+  // the covariant phi component of E, carries a factor sin(theta))
+  const bool axis_z = p.metric == KERR_SCHILD_SPHERICAL && fabs(sin(p.x0[1] + j * p.dx[1])) < 1e-12;
   if (k < p.nz)  // Omega_z(fi = i, fj = j, k)
-    STC(E, 2 * G + g, 3 * G, R(0.25) * (LDC(Fy, 5 * G + g - 1, 8 * G) + LDC(Fy, 5 * G + g, 8 * G) -
-                                       LDC(Fx, 6 * G + g - sy, 8 * G) - LDC(Fx, 6 * G + g, 8 * G)));
+    STC(E, 2 * G + g, 3 * G, axis_z ? R(0) : R(0.25) * (LDC(Fy, 5 * G + g - 1, 8 * G) + LDC(Fy, 5 * G + g, 8 * G) -
+                                                     LDC(Fx, 6 * G + g - sy, 8 * G) - LDC(Fx, 6 * G + g, 8 * G)));
   if (i < p.nx)  // Omega_x(i, fj = j, fk = k)
     STC(E, 0 * G + g, 3 * G, R(0.25) * (LDC(Fz, 6 * G + g - sy, 8 * G) + LDC(Fz, 6 * G + g, 8 * G) -
                                        LDC(Fy, 7 * G + g - sz, 8 * G) - LDC(Fy, 7 * G + g, 8 * G)));
@@ -430,7 +605,7 @@ __device__ __forceinline__ void cell_metric(const DevParams& p, long long t, dou
     double r;
     metric_at<double, METRIC>(p, xc, yc, zc, m, &r);
     isg = 1.0 / m.sqrtgam;
-    fr = METRIC == KERR_SCHILD ? floor_factor(p, r) : 1.0;
+    fr = METRIC != MINKOWSKI ? floor_factor(p, r) : 1.0;
   }
 }
 
@@ -664,6 +839,12 @@ __device__ __forceinline__ void update_cell(const DevParams& p, T* __restrict__ 
       ks_sources<R>(p, xr, yr, zr, Pr, mr, Sr);
 #pragma unroll
       for (int q = 1; q < 5; ++q) L[q] += Sr[q];
+    } else if (METRIC == KERR_SCHILD_SPHERICAL) {
+      R Sr[5];
+      sks_sources<R>(p, xr, yr, Pr, mr, Sr);
+      const R smg = mr.alpha * mr.sqrtgam;  // sqrt(-g) S
+#pragma unroll
+      for (int q = 1; q < 5; ++q) L[q] += smg * Sr[q];
     }
     double Un[NV];
 #pragma unroll

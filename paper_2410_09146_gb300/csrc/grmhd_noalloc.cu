@@ -71,6 +71,7 @@ extern "C" int grmhd_stage_noalloc(const grmhd_params* p, double* P, const doubl
   if (p->precision != GRMHD_FP64) return fail(GRMHD_E_INVALID, "only the all-FP64 form is available");
   if (p->ct != GRMHD_CT_FLUX) return fail(GRMHD_E_INVALID, "face-centred CT needs a context (grmhd_create)");
   if (p->scalar) return fail(GRMHD_E_INVALID, "the passive scalar needs a context (grmhd_create)");
+  if (p->metric == GRMHD_KERR_SCHILD_SPHERICAL) return fail(GRMHD_E_INVALID, "spherical Kerr-Schild needs a context (grmhd_create)");
   const double G = (double)(p->nx + 2 * p->ng) * (p->ny + 2 * p->ng) * (p->nz + 2 * p->ng);
   // scratch: scalars, three flux arrays [8][G] and the EMFs [3][G], all double
   const double need_bytes = (double)kScalarBytes + (3.0 * 8.0 + 3.0) * 8.0 * G;

@@ -25,8 +25,8 @@ GRMHD_GET_SCALAR_CONS = 7
 GRMHD_GET_PRIMS_F32 = 8
 RECON = {"constant": 0, "plm_minmod": 1, "plm_mc": 2, "weno5z_aoah": 3, "mp5": 4}
 RIEMANN = {"llf": 0, "hll": 1}
-METRIC = {"minkowski": 0, "kerr_schild": 1}
-BC = {"periodic": 0, "fixed": 1}
+METRIC = {"minkowski": 0, "kerr_schild": 1, "kerr_schild_spherical": 2}
+BC = {"periodic": 0, "fixed": 1, "spherical": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 CT = {"flux": 0, "face": 1}
 ST_RHO_FLOOR, ST_EPS_FLOOR, ST_W_CAP, ST_NOT_CONVERGED, ST_BAD_INPUT = 1, 2, 4, 8, 16

@@ -593,6 +593,37 @@ def torus_setup(n, r_lo, r_hi, th_lo, th_hi, spin=0.9, recon="weno5z_aoah", riem
                  riemann=riemann, bc="fixed")
 
 
+def full_sphere_setup(nr, nth, nph, r_lo=3.0, r_hi=10.0, spin=0.9, mass=1.0, recon="weno5z_aoah", riemann="hll",
+                      precision="fp64") -> Setup:
+    """Block over ln r in [ln r_lo, ln r_hi], theta in [0, pi], phi in [0, 2 pi) in spherical Kerr-Schild
+    coordinates, with the spherical boundary (polar and azimuthal ghosts; radial ghosts fixed)."""
+    return Setup(n=(nr, nth, nph), x0=(math.log(r_lo), 0.0, 0.0),
+                 dx=(math.log(r_hi / r_lo) / nr, math.pi / nth, 2 * math.pi / nph), metric="kerr_schild_spherical",
+                 spin=spin, mass=mass, bc="spherical", recon=recon, riemann=riemann, precision=precision)
+
+
+def spherical_random_prims(s: Setup, seed: int, amp=0.2):
+    """Seeded primitives on every cell (ghosts included) of a spherical Kerr-Schild block: density and
+    internal energy around 1 and 0.5, a rotation about the axis (u~^phi = 0.1 / r, smooth through the axis)
+    and a field with components along r, theta, phi, each perturbed by uniform noise of relative size amp.
+    Contravariant components in (ln r, theta, phi): a physical component of size v along r is v / r."""
+    rng = np.random.default_rng(seed)
+    x1, th = s.cell_centres(0), s.cell_centres(1)
+    shape = s.prim_shape()[1:]                      # [phi][theta][ln r]
+    r = np.broadcast_to(np.exp(x1)[None, None, :], shape)
+    noise = lambda: 1.0 + amp * rng.uniform(-1.0, 1.0, shape)
+    P = np.zeros(s.prim_shape())
+    P[0] = noise()
+    P[4] = 0.5 * noise()
+    P[1] = 0.05 * (noise() - 1.0) / r
+    P[2] = 0.05 * (noise() - 1.0) / r
+    P[3] = 0.1 * noise() / r
+    P[5] = 0.1 * noise() / r
+    P[6] = 0.05 * (noise() - 1.0) / r
+    P[7] = 0.05 * noise() / r
+    return P
+
+
 def _bl_inverse_t_phi(r, th, a, M=1.0):
     """g^{tt}, g^{t phi}, g^{phi phi} of Kerr in Boyer-Lindquist coordinates."""
     s2 = np.sin(th) ** 2
@@ -605,9 +636,11 @@ def _bl_inverse_t_phi(r, th, a, M=1.0):
 
 
 def _u_t(r, th, l, a):
-    """u_t of the purely azimuthal flow with specific angular momentum l = -u_phi / u_t (u_t < 0)."""
+    """u_t of the purely azimuthal flow with specific angular momentum l = -u_phi / u_t (u_t < 0); NaN where no
+    such flow exists (near the axis, where l would need a superluminal velocity: those cells are atmosphere)."""
     itt, itp, ipp, _ = _bl_inverse_t_phi(r, th, a)
-    return -1.0 / np.sqrt(-(itt - 2 * l * itp + l * l * ipp))
+    with np.errstate(invalid="ignore"):
+        return -1.0 / np.sqrt(-(itt - 2 * l * itp + l * l * ipp))
 
 
 def torus_l(r_max, a, M=1.0):

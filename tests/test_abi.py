@@ -5,6 +5,8 @@ validation of grmhd_create.
 """
 import ctypes
 
+import numpy as np
+
 import pytest
 
 from paper_2410_09146_gb300 import build as B
@@ -106,3 +108,21 @@ def test_noalloc_refusals_on_the_host(lib):
     # 9 x 10 x 863 = 77,670 ghosted cells: one more than the 16 MiB scratch holds
     assert call(G.params(I.linear_wave_setup(1, 2, 855))) == G.GRMHD_E_INVALID
     assert b"77669" in lib.grmhd_last_error(None)
+
+
+def test_spherical_kerr_schild_parameter_validation(lib):
+    """Host-side checks of the spherical Kerr-Schild metric and the spherical boundary (no device work)."""
+    import dataclasses
+    s = I.full_sphere_setup(8, 12, 16)
+    assert G.grmhd_workspace_bytes(G.params(s)) > 0
+    assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, bc="fixed"))) > 0
+    assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, mass=0.0, spin=0.0))) > 0
+    for bad in (dict(precision="mixed"), dict(ct="face"), dict(scalar=True), dict(bc="periodic"),
+                dict(mass=-1.0), dict(spin=1.0),
+                dict(n=(8, 12, 15), dx=(s.dx[0], s.dx[1], 2 * np.pi / 15)),     # odd nz
+                dict(x0=(s.x0[0], 0.1, 0.0)),                                   # theta range not [0, pi]
+                dict(n=(8, 2, 16), dx=(s.dx[0], np.pi / 2, s.dx[2]))):          # ng > ny
+        assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, **bad))) == 0, bad
+    # the spherical boundary needs the spherical metric
+    assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(I.kerr_schild_setup(16), bc="spherical"))) == 0
+

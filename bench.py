@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-face-ct", action="store_true")
     ap.add_argument("--no-two-level", action="store_true")
     ap.add_argument("--no-scalar", action="store_true")
+    ap.add_argument("--no-spherical", action="store_true")
     ap.add_argument("--guess-states", type=int, default=100_000_000)
     ap.add_argument("--guess-only", action="store_true",
                     help="run only the learned-guess con2prim section and print its JSON (profiling aid)")
@@ -267,6 +268,7 @@ def run_ours(args):
     face_ct = None if args.no_face_ct else run_face_ct(G, s_mix, P, Bf, args.steps, args.warmup)
     two_level = None if args.no_two_level else run_two_level(G, I, s_mix.recon, args.steps, args.warmup)
     scalar = None if args.no_scalar else run_scalar(G, s_mix, P, args.steps, args.warmup, ms / args.steps)
+    spherical = None if args.no_spherical else run_spherical(G, I, args.steps, args.warmup)
     del Bf
     guess = None if args.no_guess else run_guess(G, I, rank, n_states=args.guess_states)
     batched = None
@@ -310,7 +312,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": {"value": world * cells * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
-        # per stage: 3 flux, EMF, update, floored-cell pass, deferred con2prim; the CFL finalisation per step
+        # per stage: 3 flux, EMF, update, the two deferred con2prim passes; the CFL finalisation per step
         "gpu_launches": 7 * args.steps + (args.steps + 1) // 2,
     }
     if face_ct is not None:
@@ -319,6 +321,8 @@ def run_ours(args):
         out["two_level"] = two_level
     if scalar is not None:
         out["scalar"] = scalar
+    if spherical is not None:
+        out["spherical"] = spherical
     if batched is not None:
         out["batched"] = batched
     if guess is not None:
@@ -558,6 +562,32 @@ def run_scalar(G, s_mix, P, steps, warmup, ms_plain):
            "X reconstructed like the primitives and taken on the upwind side"}
     del ctx
     torch.cuda.empty_cache()
+    return out
+
+
+def run_spherical(G, I, steps, warmup):
+    """Spherical Kerr-Schild coordinates (ln r, theta, phi): the stationary torus around the a = 0.9 hole (specific
+    angular momentum Keplerian at r = 12, inner edge r = 6) on a full sphere with polar and azimuthal ghosts,
+    128 x 96 x 64 cells over r in [2, 40], WENO5-Z-AOAH + HLL; mixed and all-FP64 forms, CFL time step."""
+    import torch
+    out = {}
+    nr, nth, nph = 128, 96, 64
+    zones = nr * nth * nph
+    for prec in ("mixed", "fp64"):
+        s = I.full_sphere_setup(nr, nth, nph, r_lo=2.0, r_hi=40.0, precision=prec)
+        ctx = G.Context(s)
+        ctx.set_prims(I.torus_prims(s))
+        for k in range(warmup + (warmup % 2)):
+            ctx.stage(*stage_coeffs(k), 0.0)
+        torch.cuda.synchronize()
+        n = steps if prec == "mixed" else max(2, steps // 5 // 2 * 2)
+        ms = time_stages(ctx, 0, n)
+        out[prec] = {"value": zones * n / (ms / 1e3), "unit": UNIT, "ms_per_stage": ms / n, "steps": n}
+        del ctx
+        torch.cuda.empty_cache()
+    out["speedup_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["workload"] = (f"torus in spherical Kerr-Schild coordinates, full sphere {nr} x {nth} x {nph} (ln r, theta, "
+                       "phi), r in [2, 40], a = 0.9, WENO5-Z-AOAH + HLL")
     return out
 
 

@@ -49,7 +49,7 @@ extern "C" {
 #define GRMHD_KERR_SCHILD 1 /* Cartesian Kerr-Schild, spin a = spin * mass along z */
 /* Kerr-Schild in spherical coordinates (x^1, x^2, x^3) = (ln r, theta, phi) (Sec. 2.3; the coordinates of the
  * paper's accretion set-ups, Sec. 3.2): r and the angles of the Cartesian form through x + i y = (r + i a)
- * e^{i phi} sin(theta), z = r cos(theta). Single-block contexts, all-FP64 form, flux-CT, no passive scalar;
+ * e^{i phi} sin(theta), z = r cos(theta). Single-block contexts (both forms), flux-CT, no passive scalar;
  * GRMHD_BC_FIXED or GRMHD_BC_SPHERICAL. Theta faces on the polar axis carry no flux, sin(theta) times the phi
  * components of W v and B is reconstructed, and on the axis the EMF along phi is zero and the EMF along r is
  * its mean over phi. mass >= 0 (0: flat space in spherical coordinates). */

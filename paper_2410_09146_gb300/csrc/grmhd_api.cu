@@ -124,7 +124,6 @@ bool valid_params(const grmhd_params* p, char* msg, size_t n) {
   if (p->metric == GRMHD_KERR_SCHILD_SPHERICAL) {
     const char* why = !(p->mass >= 0.0)            ? "mass must be >= 0"
                       : !(std::fabs(p->spin) < 1.0) ? "|spin| must be < 1"
-                      : p->precision != GRMHD_FP64  ? "spherical Kerr-Schild runs in the all-FP64 form (GRMHD_FP64)"
                       : p->ct != GRMHD_CT_FLUX      ? "spherical Kerr-Schild runs with flux-CT (GRMHD_CT_FLUX)"
                       : p->scalar                   ? "spherical Kerr-Schild runs without a passive scalar"
                       : p->bc == GRMHD_BC_PERIODIC  ? "spherical Kerr-Schild takes fixed or spherical ghosts"

@@ -8,6 +8,7 @@
 // float for the reconstruction / flux / EMF / source part of the mixed form).
 #pragma once
 
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1053,7 +1054,25 @@ enum { C2P_DEFERRED = 256 };
 // root equals f's. Returns the status bits of the solve (floors are applied by the caller) or C2P_DEFERRED
 // when the double step from the float root is not small (defer == true; mu_r then holds the double iterate
 // the double pass resumes from); without defer such a cell takes the full double iteration here.
-__device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const KSGeo& gm, double isg,
+// The two contractions of the solve's invariants with the 3-metric: r^i = gamma^ij r_j and b^2 = gamma_ij b^i b^j,
+// from the Cartesian Kerr-Schild factors (r_i - kappa (l.r) l^i, b.b + f (l.b)^2) or from the matrices.
+__device__ __forceinline__ double c2p_contract(const KSGeo& gm, const double rl[3], const double bu[3], double ru[3]) {
+  const double klr = gm.kappa * (gm.l[0] * rl[0] + gm.l[1] * rl[1] + gm.l[2] * rl[2]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) ru[i] = rl[i] - klr * gm.l[i];
+  const double lb = gm.l[0] * bu[0] + gm.l[1] * bu[1] + gm.l[2] * bu[2];
+  return bu[0] * bu[0] + bu[1] * bu[1] + bu[2] * bu[2] + gm.f * lb * lb;
+}
+__device__ __forceinline__ double c2p_contract(const Metric<double>& m, const double rl[3], const double bu[3],
+                                               double ru[3]) {
+  double bl[3];
+  lower3(m.gamu, rl, ru);
+  lower3(m.gam, bu, bl);
+  return bu[0] * bl[0] + bu[1] * bl[1] + bu[2] * bl[2];
+}
+
+template <class Geo>
+__device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const Geo& gm, double isg,
                                                 const double Un[NV], float mu_guess, bool defer, float Pf[NV],
                                                 int& iters, double& mu_r) {
   // Lanes entering together; each of them reaches the __syncwarp below exactly once (no return before it).
@@ -1077,14 +1096,11 @@ __device__ __forceinline__ int con2prim_mixed_f(const DevParams& p, const KSGeo&
     const double rl[3] = {Un[1] * s, Un[2] * s, Un[3] * s};
     const double tb = isg * isD;
     const double bu[3] = {Un[5] * tb, Un[6] * tb, Un[7] * tb};
-    // r^i = gamma^ij r_j = r_i - kappa (l.r) l^i, b^2 = b.b + f (l.b)^2 (Kerr-Schild form of the 3-metric)
-    const double klr = gm.kappa * (gm.l[0] * rl[0] + gm.l[1] * rl[1] + gm.l[2] * rl[2]);
-    const double ru[3] = {rl[0] - klr * gm.l[0], rl[1] - klr * gm.l[1], rl[2] - klr * gm.l[2]};
-    const double lb = gm.l[0] * bu[0] + gm.l[1] * bu[1] + gm.l[2] * bu[2];
+    double ru[3];
+    c.b2 = c2p_contract(gm, rl, bu, ru);
     c.D = D;
     c.q = Un[4] * s;
     c.r2 = rl[0] * ru[0] + rl[1] * ru[1] + rl[2] * ru[2];
-    c.b2 = bu[0] * bu[0] + bu[1] * bu[1] + bu[2] * bu[2] + gm.f * lb * lb;
     c.rb = rl[0] * bu[0] + rl[1] * bu[1] + rl[2] * bu[2];
     c.rb2 = c.rb * c.rb;
     c.gm1 = p.gamma_eos - 1.0;

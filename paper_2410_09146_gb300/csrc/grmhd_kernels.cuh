@@ -58,8 +58,9 @@ __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, 
   const R xd = sel3(d, par<R>(p.x0[0], p.fx0[0]), par<R>(p.x0[1], p.fx0[1]), par<R>(p.x0[2], p.fx0[2])) +
                R(cd) * sel3(d, par<R>(p.dx[0], p.fdx[0]), par<R>(p.dx[1], p.fdx[1]), par<R>(p.dx[2], p.fdx[2]));
   if (d == 0) xf[0] = xd; else if (d == 1) xf[1] = xd; else xf[2] = xd;
-  if (METRIC == KERR_SCHILD_SPHERICAL && d == 1 && fabs(sin(xf[1])) < R(1e-12)) {
-    // a theta face on the polar axis has zero area (sqrt(-g) = 0 there, where the metric is singular): no flux
+  if (METRIC == KERR_SCHILD_SPHERICAL && d == 1 && fabs(sin(p.x0[1] + j * p.dx[1])) < 1e-12) {
+    // a theta face on the polar axis has zero area (sqrt(-g) = 0 there, where the metric is singular): no flux.
+    // Decided in double from the double parameters: a float theta of pi (3.1415927) has sin ~ -9e-8.
 #pragma unroll
     for (int q = 0; q < NV; ++q) Fh[q] = R(0);
     return R(0);
@@ -113,7 +114,8 @@ __device__ __forceinline__ R flux_face(const DevParams& p, const T* __restrict__
 #pragma unroll
     for (int o = 0; o < 6; ++o) sw[o] = sin(th0 + (R(j + (d == 1 ? o - 3 : 0)) + R(0.5)) * dth);
   }
-  const bool reg_ok = sph && fabs(sfc) > R(1e-12);
+  // no weighting on an axis face (it carries no flux; decided in double, as in face_flux)
+  const bool reg_ok = sph && !(d == 1 && fabs(sin(p.x0[1] + j * p.dx[1])) < 1e-12);
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     const long long c0 = q * p.gsize + g, PN = NV * p.gsize;
@@ -693,6 +695,12 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
     ks_sources<float>(p, xr, yr, zr, Pr, mr, Sr);
 #pragma unroll
     for (int q = 1; q < 5; ++q) L[q] += Sr[q];
+  } else if (METRIC == KERR_SCHILD_SPHERICAL) {
+    float Sr[5];
+    sks_sources<float>(p, xr, yr, Pr, mr, Sr);
+    const float smg = mr.alpha * mr.sqrtgam;  // sqrt(-g) S
+#pragma unroll
+    for (int q = 1; q < 5; ++q) L[q] += smg * Sr[q];
   }
   // the RK combination in double; a first stage of SSP-RK2 (g0 = 0, g1 = 1) skips the zero and unit terms
   const double bdt = a.beta * dt;
@@ -715,9 +723,15 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
     Un[6] = 0.5 * (LDC(bn, G + g, 3 * G) + LDC(bn, G + g + sy, 3 * G));
     Un[7] = 0.5 * (LDC(bn, 2 * G + g, 3 * G) + LDC(bn, 2 * G + g + sz, 3 * G));
   }
-  KSGeo gm{0.0, 0.0, {0.0, 0.0, 0.0}};  // flat space
+  // the 3-metric of the double solve: the Kerr-Schild factors (Cartesian metrics), or the matrices
+  using Geo = typename std::conditional<METRIC == KERR_SCHILD_SPHERICAL, Metric<double>, KSGeo>::type;
+  Geo gm{};
   double isg = 1.0;
-  if (METRIC == KERR_SCHILD && p.geo != nullptr) {
+  if constexpr (METRIC == KERR_SCHILD_SPHERICAL) {
+    metric_at<double, METRIC>(p, p.x0[0] + (i + 0.5) * p.dx[0], p.x0[1] + (j + 0.5) * p.dx[1],
+                              p.x0[2] + (k + 0.5) * p.dx[2], gm);
+    isg = 1.0 / gm.sqrtgam;
+  } else if (METRIC == KERR_SCHILD && p.geo != nullptr) {
 #ifdef GRMHD_BOUNDS_CHECK
     if (t < 0 || t >= n) {
       bounds_fault(p, __LINE__, t);
@@ -748,7 +762,7 @@ __device__ __forceinline__ void update_cell_mixed(const DevParams& p, float* __r
     cs.it_sum += iters;
     return;
   }
-  const float fr = METRIC == KERR_SCHILD ? (p.floor_r2 ? 1.f / (rf * rf) : powf(rf, -(float)p.floor_r_exp))
+  const float fr = METRIC != MINKOWSKI ? (p.floor_r2 ? 1.f / (rf * rf) : powf(rf, -(float)p.floor_r_exp))
                                          : 1.f;
   st |= apply_floors_f(p, mr.gam, fr, Pn);
   if (st) {

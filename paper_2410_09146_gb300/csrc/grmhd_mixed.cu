@@ -17,6 +17,17 @@ template <int METRIC>
 cudaError_t flux_m(const DevParams& p, const T* P, R* F, unsigned long long* ms, int d, int track, cudaStream_t s) {
   const long long n = (long long)(p.nx + (d == 0 ? 1 : 2)) * (p.ny + (d == 1 ? 1 : 2)) * (p.nz + (d == 2 ? 1 : 2));
   const int g = grid_for(n, 128);
+  if (METRIC == KERR_SCHILD_SPHERICAL) {  // face-centric for every reconstruction (its sin(theta) weighting)
+    switch (p.recon) {
+      case RECON_CONSTANT: k_flux<R, T, METRIC, RECON_CONSTANT><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+      case RECON_PLM_MINMOD: k_flux<R, T, METRIC, RECON_PLM_MINMOD><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+      case RECON_PLM_MC: k_flux<R, T, METRIC, RECON_PLM_MC><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+      case RECON_WENO5Z: k_flux<R, T, METRIC, RECON_WENO5Z><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+      case RECON_MP5: k_flux<R, T, METRIC, RECON_MP5><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   switch (p.recon) {
     case RECON_CONSTANT: k_flux<R, T, METRIC, RECON_CONSTANT><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
     case RECON_PLM_MINMOD: k_flux<R, T, METRIC, RECON_PLM_MINMOD><<<g, 128, 0, s>>>(P, F, ms, p, d, track); break;
@@ -33,11 +44,15 @@ cudaError_t flux_m(const DevParams& p, const T* P, R* F, unsigned long long* ms,
 }
 
 cudaError_t ghost(const DevParams& p, void* P, cudaStream_t s) {
-  k_ghost_periodic<T><<<grid_for(p.gsize, 256), 256, 0, s>>>((T*)P, p);
+  if (p.bc == BC_SPHERICAL)
+    k_ghost_spherical<T><<<grid_for(p.gsize, 256), 256, 0, s>>>((T*)P, p);
+  else
+    k_ghost_periodic<T><<<grid_for(p.gsize, 256), 256, 0, s>>>((T*)P, p);
   return cudaGetLastError();
 }
 
 cudaError_t flux(const DevParams& p, const void* P, void* F, unsigned long long* ms, int d, int track, cudaStream_t s) {
+  if (p.metric == KERR_SCHILD_SPHERICAL) return flux_m<KERR_SCHILD_SPHERICAL>(p, (const T*)P, (R*)F, ms, d, track, s);
   return p.metric == KERR_SCHILD ? flux_m<KERR_SCHILD>(p, (const T*)P, (R*)F, ms, d, track, s)
                                  : flux_m<MINKOWSKI>(p, (const T*)P, (R*)F, ms, d, track, s);
 }
@@ -45,6 +60,11 @@ cudaError_t flux(const DevParams& p, const void* P, void* F, unsigned long long*
 cudaError_t emf(const DevParams& p, const void* Fx, const void* Fy, const void* Fz, void* E, cudaStream_t s) {
   const long long n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
   k_emf<R><<<grid_for(n, 256), 256, 0, s>>>((const R*)Fx, (const R*)Fy, (const R*)Fz, (R*)E, p);
+  if (p.metric == KERR_SCHILD_SPHERICAL) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_emf_axis<R><<<(2 * p.nx + 127) / 128, 128, 0, s>>>((R*)E, p);
+  }
   return cudaGetLastError();
 }
 
@@ -53,6 +73,9 @@ cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, 
   const int g = grid_for(p.isize, 128);
   if (p.metric == KERR_SCHILD)
     k_update<KERR_SCHILD, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
+  else if (p.metric == KERR_SCHILD_SPHERICAL)
+    k_update<KERR_SCHILD_SPHERICAL, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz,
+                                                            (const R*)E, a, p);
   else
     k_update<MINKOWSKI, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
   return cudaGetLastError();
@@ -67,6 +90,8 @@ cudaError_t cell_passes(const DevParams& p, void* P, const StageArgs& a, cudaStr
   for (int full = 0; full < (a.solvelist ? 2 : 1); ++full) {
     if (p.metric == KERR_SCHILD)
       k_update_deferred<KERR_SCHILD, T><<<g2, 128, 0, s>>>((T*)P, a, p, full);
+    else if (p.metric == KERR_SCHILD_SPHERICAL)
+      k_update_deferred<KERR_SCHILD_SPHERICAL, T><<<g2, 128, 0, s>>>((T*)P, a, p, full);
     else
       k_update_deferred<MINKOWSKI, T><<<g2, 128, 0, s>>>((T*)P, a, p, full);
     const cudaError_t e = cudaGetLastError();
@@ -79,6 +104,8 @@ cudaError_t prim2con(const DevParams& p, const void* P, double* U, cudaStream_t 
   const int g = grid_for(p.isize, 128);
   if (p.metric == KERR_SCHILD)
     k_prim2con<KERR_SCHILD, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+  else if (p.metric == KERR_SCHILD_SPHERICAL)
+    k_prim2con<KERR_SCHILD_SPHERICAL, T><<<g, 128, 0, s>>>((const T*)P, U, p);
   else
     k_prim2con<MINKOWSKI, T><<<g, 128, 0, s>>>((const T*)P, U, p);
   return cudaGetLastError();

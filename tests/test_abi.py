@@ -117,7 +117,8 @@ def test_spherical_kerr_schild_parameter_validation(lib):
     assert G.grmhd_workspace_bytes(G.params(s)) > 0
     assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, bc="fixed"))) > 0
     assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, mass=0.0, spin=0.0))) > 0
-    for bad in (dict(precision="mixed"), dict(ct="face"), dict(scalar=True), dict(bc="periodic"),
+    assert G.grmhd_workspace_bytes(G.params(dataclasses.replace(s, precision="mixed"))) > 0
+    for bad in (dict(ct="face"), dict(scalar=True), dict(bc="periodic"),
                 dict(mass=-1.0), dict(spin=1.0),
                 dict(n=(8, 12, 15), dx=(s.dx[0], s.dx[1], 2 * np.pi / 15)),     # odd nz
                 dict(x0=(s.x0[0], 0.1, 0.0)),                                   # theta range not [0, pi]

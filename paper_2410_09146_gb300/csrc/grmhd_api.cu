@@ -210,7 +210,7 @@ Layout layout_of(const grmhd_params* p) {
     l.P = take(8 * G * pb);
     for (int s = 0; s < 3; ++s) l.U[s] = take(8 * I * sizeof(double));
     for (int d = 0; d < 3; ++d) l.F[d] = take(8 * G * pb);
-    l.E = take(3 * G * pb);
+    l.E = take(3 * G * (p->ct == GRMHD_CT_FACE ? sizeof(double) : pb));  // face-centred CT: upwind EMFs in double
     l.status = take(I);
     if (p->precision == GRMHD_MIXED) {
       l.worklist = take(I * sizeof(int));

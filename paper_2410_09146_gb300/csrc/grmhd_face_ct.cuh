@@ -72,20 +72,23 @@ __device__ __forceinline__ R emf_upwind_edge(const R* __restrict__ Fa, const R* 
   return R(0.25) * (oa_lo + oa_hi + ob_lo + ob_hi) + R(0.25) * (xb_lo - xb_hi) + R(0.25) * (xa_lo - xa_hi);
 }
 
-// Upwind edge EMFs for edge box index t in [0, nx] x [0, ny] x [0, nz] (the edges flux-CT covers).
+// Upwind edge EMFs for edge box index t in [0, nx] x [0, ny] x [0, nz] (the edges flux-CT covers), formed in
+// the flux type and stored in double: k_face_update differences them in double, and a conversion here, once
+// per edge in a kernel that leaves the FP64 pipe idle, saves four in that FP64-bound kernel (each edge
+// bounds four faces); the values are the same bits.
 template <class R>
 __global__ void __launch_bounds__(128) k_emf_upwind(const R* __restrict__ Fx, const R* __restrict__ Fy,
                                                     const R* __restrict__ Fz, const R* __restrict__ Ecc,
-                                                    R* __restrict__ E, DevParams p) {
+                                                    double* __restrict__ E, DevParams p) {
   const int ex = p.nx + 1, ey = p.ny + 1;
   const long long n = (long long)ex * ey * (p.nz + 1);
   const long long G = p.gsize, sx = 1, sy = p.gx, sz = (long long)p.gx * p.gy;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
     const long long g = gidx(p, i, j, k);
-    if (i < p.nx) E[g] = emf_upwind_edge<R>(Fy, Fz, Ecc, G, g, sy, sz, 1, 2);                      // x: a = y, b = z
-    if (j < p.ny) E[G + g] = emf_upwind_edge<R>(Fz, Fx, Ecc + G, G, g, sz, sx, 2, 0);            // y: a = z, b = x
-    if (k < p.nz) E[2 * G + g] = emf_upwind_edge<R>(Fx, Fy, Ecc + 2 * G, G, g, sx, sy, 0, 1);    // z: a = x, b = y
+    if (i < p.nx) E[g] = (double)emf_upwind_edge<R>(Fy, Fz, Ecc, G, g, sy, sz, 1, 2);               // x: a = y, b = z
+    if (j < p.ny) E[G + g] = (double)emf_upwind_edge<R>(Fz, Fx, Ecc + G, G, g, sz, sx, 2, 0);     // y: a = z, b = x
+    if (k < p.nz) E[2 * G + g] = (double)emf_upwind_edge<R>(Fx, Fy, Ecc + 2 * G, G, g, sx, sy, 0, 1);  // z: a = x, b = y
   }
 }
 
@@ -93,10 +96,10 @@ __global__ void __launch_bounds__(128) k_emf_upwind(const R* __restrict__ Fx, co
 //   Bfnew = g0 Bf0 + g1 Bfcur + beta dt curl(E), curl differenced in double (so that the face divergence
 //   changes by double roundoff only, whatever the EMF type):
 //   x: -dE_z/dy + dE_y/dz,  y: dE_z/dx - dE_x/dz,  z: -dE_y/dx + dE_x/dy.
-template <class R>
+template <class R>  // the form's flux type (one instance per form; the EMFs are double in both)
 __global__ void __launch_bounds__(256) k_face_update(const double* __restrict__ Bf0, const double* __restrict__ Bfc,
-                                                     double* __restrict__ Bfn, const R* __restrict__ E, StageArgs a,
-                                                     DevParams p) {
+                                                     double* __restrict__ Bfn, const double* __restrict__ E,
+                                                     StageArgs a, DevParams p) {
   const int ex = p.nx + 1, ey = p.ny + 1;
   const long long n = (long long)ex * ey * (p.nz + 1);
   const long long G = p.gsize, sy = p.gx, sz = (long long)p.gx * p.gy;
@@ -104,25 +107,25 @@ __global__ void __launch_bounds__(256) k_face_update(const double* __restrict__ 
   const double bdt = a.beta * dt;
   const double cx = bdt * p.idx[0], cy = bdt * p.idx[1], cz = bdt * p.idx[2];  // beta dt / dx_d
   const bool with0 = a.g0 != 0.0;  // uniform: first stages have no step-start term
-  const R* Ex = E;
-  const R* Ey = E + G;
-  const R* Ez = E + 2 * G;
+  const double* Ex = E;
+  const double* Ey = E + G;
+  const double* Ez = E + 2 * G;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % ex), j = (int)((t / ex) % ey), k = (int)(t / ((long long)ex * ey));
     const long long g = gidx(p, i, j, k);
-    const double ez = (double)Ez[g], ey_ = (double)Ey[g], ex_ = (double)Ex[g];
+    const double ez = Ez[g], ey_ = Ey[g], ex_ = Ex[g];
     if (j < p.ny && k < p.nz) {
-      double b = a.g1 * Bfc[g] + (((double)Ey[g + sz] - ey_) * cz - ((double)Ez[g + sy] - ez) * cy);
+      double b = a.g1 * Bfc[g] + ((Ey[g + sz] - ey_) * cz - (Ez[g + sy] - ez) * cy);
       if (with0) b += a.g0 * Bf0[g];
       Bfn[g] = b;
     }
     if (i < p.nx && k < p.nz) {
-      double b = a.g1 * Bfc[G + g] + (((double)Ez[g + 1] - ez) * cx - ((double)Ex[g + sz] - ex_) * cz);
+      double b = a.g1 * Bfc[G + g] + ((Ez[g + 1] - ez) * cx - (Ex[g + sz] - ex_) * cz);
       if (with0) b += a.g0 * Bf0[G + g];
       Bfn[G + g] = b;
     }
     if (i < p.nx && j < p.ny) {
-      double b = a.g1 * Bfc[2 * G + g] + (((double)Ex[g + sy] - ex_) * cy - ((double)Ey[g + 1] - ey_) * cx);
+      double b = a.g1 * Bfc[2 * G + g] + ((Ex[g + sy] - ex_) * cy - (Ey[g + 1] - ey_) * cx);
       if (with0) b += a.g0 * Bf0[2 * G + g];
       Bfn[2 * G + g] = b;
     }
@@ -161,13 +164,13 @@ struct FaceCtLaunch {
     if (e != cudaSuccess) return e;
     const long long nedge = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
     k_emf_upwind<R><<<grid_for(nedge, 128), 128, 0, s>>>((const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)Ecc,
-                                                         (R*)E, p);
+                                                         (double*)E, p);
     return cudaGetLastError();
   }
   static cudaError_t faces(const DevParams& p, const double* Bf0, const double* Bfc, double* Bfn, const void* E,
                            const StageArgs& a, cudaStream_t s) {
     const long long n = (long long)(p.nx + 1) * (p.ny + 1) * (p.nz + 1);
-    k_face_update<R><<<grid_for(n, 256), 256, 0, s>>>(Bf0, Bfc, Bfn, (const R*)E, a, p);
+    k_face_update<R><<<grid_for(n, 256), 256, 0, s>>>(Bf0, Bfc, Bfn, (const double*)E, a, p);
     return cudaGetLastError();
   }
   static cudaError_t to_cells(const DevParams& p, const double* Bf, void* P, cudaStream_t s) {

@@ -139,7 +139,10 @@ size_t grmhd_workspace_bytes(const grmhd_params* p);
  * [8][nz+2ng][ny+2ng][nx+2ng], host or device (where), read during the call, copied into the context's P
  * without conversion; otherwise as grmhd_set_prims (U formed, a previous scalar or face field discarded).
  * The same state as grmhd_set_prims with these values in double (its load rounds to float), at half the
- * bytes. Errors: GRMHD_E_INVALID (an all-FP64 or batch context, P NULL, bad where), GRMHD_E_CUDA. */
+ * bytes. A host P is copied in slabs of z rows whose prim->cons overlaps the next slab's copy (on a stream the
+ * context creates on its first host load and destroys with the context); the call returns once P has been
+ * read, and later work on the context's stream waits for the prim->cons. Errors: GRMHD_E_INVALID (an
+ * all-FP64 or batch context, P NULL, bad where), GRMHD_E_CUDA. */
 int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where);
 
 /* Passive scalar (params.scalar = 1; Sec. 2.1: Phoebus evolves passive scalars X, the electron fraction

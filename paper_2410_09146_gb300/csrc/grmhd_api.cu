@@ -15,6 +15,8 @@
 
 using namespace grmhd;
 
+constexpr int kLoadChunks = 8;  // slabs of a chunked host load (grmhd_set_prims_f32)
+
 struct grmhd_ctx {
   grmhd_params prm;
   DevParams dp;
@@ -44,6 +46,10 @@ struct grmhd_ctx {
   bool has_faces;            // face-centred CT: grmhd_set_face_b called since grmhd_set_prims
   int s0, sc;                // slot of U0 and of the current state
   bool has_state;
+  // host loads of the float primitives: chunks copied on `stream`, their prim->cons on `load_stream` (created
+  // on the first such load), so the two overlap; load_ev[k] marks chunk k's copies, load_ev[kLoadChunks] the end
+  cudaStream_t load_stream;
+  cudaEvent_t load_ev[kLoadChunks + 1];
   bool timing;               // record CUDA events around each kernel group
   cudaEvent_t ev[8];         // ghost | flux x | flux y | flux z | emf | update | cell passes | end
   double t_ms[7];            // accumulated ms per kernel group since the last read
@@ -502,7 +508,7 @@ int grmhd_set_prims(grmhd_ctx* c, const double* P, int where) {
   }
   CK(c->L->load_prims(c->dp, src, c->P, c->stream), "loading primitives");
   c->s0 = c->sc = 0;
-  CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], c->stream), "prim->cons");
+  CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], 0, c->dp.isize, c->stream), "prim->cons");
   c->has_state = true;
   c->has_faces = false;
   c->has_scalar = false;
@@ -525,7 +531,7 @@ int grmhd_set_face_b(grmhd_ctx* c, const double* Bf, int where) {
   for (int k = 0; k < 3; ++k)
     if (c->Bslot[k] != cur) CK(cudaMemcpyAsync(c->Bslot[k], cur, bytes, cudaMemcpyDeviceToDevice, c->stream), "copying faces");
   CK(c->L->face_to_cells(c->dp, cur, c->P, c->stream), "cell field from the faces");
-  CK(c->L->prim2con(c->dp, c->P, c->Uslot[c->sc], c->stream), "prim->cons");
+  CK(c->L->prim2con(c->dp, c->P, c->Uslot[c->sc], 0, c->dp.isize, c->stream), "prim->cons");
   if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
   c->has_faces = true;
   return GRMHD_OK;
@@ -537,12 +543,40 @@ int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) {
   if (c->L->p_bytes != 4) return fail(c, GRMHD_E_INVALID, "single-precision primitives need a GRMHD_MIXED context");
   if (where != GRMHD_HOST && where != GRMHD_DEVICE) return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");
   const size_t bytes = sizeof(float) * NV * (size_t)c->dp.gsize;
-  CK(cudaMemcpyAsync(c->P, P, bytes, where == GRMHD_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream),
-     "copying P");
-  // a host P (pinned or not) is read before the call returns
-  if (where == GRMHD_HOST) CK(cudaStreamSynchronize(c->stream), "synchronising");
   c->s0 = c->sc = 0;
-  CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], c->stream), "prim->cons");
+  if (where == GRMHD_DEVICE) {
+    CK(cudaMemcpyAsync(c->P, P, bytes, cudaMemcpyDeviceToDevice, c->stream), "copying P");
+    CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], 0, c->dp.isize, c->stream), "prim->cons");
+  } else {
+    // In kLoadChunks slabs of ghosted z rows: a slab's rows of the 8 variables are copied on the context's
+    // stream, and the prim->cons of the interior cells in those rows runs on the loading stream once they
+    // have landed, beside the next slab's copies (a 256^3 load: 0.6 GB at ~210 GB/s, 2.8 ms, against 2.9 ms
+    // of double-precision prim->cons). The call returns once the host P has been read; the context's stream
+    // waits for the last prim->cons.
+    if (!c->load_stream) {
+      CK(cudaStreamCreateWithFlags(&c->load_stream, cudaStreamNonBlocking), "creating the loading stream");
+      for (cudaEvent_t& e : c->load_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "creating an event");
+    }
+    const long long row = (long long)c->dp.gx * c->dp.gy, G = c->dp.gsize, plane = (long long)c->dp.nx * c->dp.ny;
+    const int gz = c->dp.gz, ng = c->dp.ng, nz = c->dp.nz;
+    const int nch = gz < kLoadChunks ? gz : kLoadChunks;
+    int r0 = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int r1 = (int)((long long)gz * (ch + 1) / nch);
+      for (int q = 0; q < NV; ++q)
+        CK(cudaMemcpyAsync((float*)c->P + q * G + r0 * row, P + q * G + r0 * row, sizeof(float) * (r1 - r0) * row,
+                           cudaMemcpyHostToDevice, c->stream),
+           "copying P");
+      CK(cudaEventRecord(c->load_ev[ch], c->stream), "recording a load event");
+      CK(cudaStreamWaitEvent(c->load_stream, c->load_ev[ch], 0), "ordering the loading stream");
+      const int k0 = r0 - ng > 0 ? r0 - ng : 0, k1 = r1 - ng < nz ? r1 - ng : nz;  // interior z of these rows
+      if (k1 > k0) CK(c->L->prim2con(c->dp, c->P, c->Uslot[0], k0 * plane, k1 * plane, c->load_stream), "prim->cons");
+      r0 = r1;
+    }
+    CK(cudaEventRecord(c->load_ev[kLoadChunks], c->load_stream), "recording a load event");
+    CK(cudaStreamWaitEvent(c->stream, c->load_ev[kLoadChunks], 0), "ordering the context's stream");
+    CK(cudaEventSynchronize(c->load_ev[nch - 1]), "synchronising");  // the host P has been read
+  }
   c->has_state = true;
   c->has_faces = false;
   c->has_scalar = false;
@@ -951,6 +985,10 @@ const char* grmhd_last_error(const grmhd_ctx* c) { return c ? c->err : g_create_
 void grmhd_destroy(grmhd_ctx* c) {
   if (c && c->timing)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(c->ev[k]);
+  if (c && c->load_stream) {
+    for (cudaEvent_t e : c->load_ev) cudaEventDestroy(e);
+    cudaStreamDestroy(c->load_stream);
+  }
   if (c) {
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1217,7 +1255,7 @@ int grmhd_batch_set_prims(grmhd_ctx* c, int block, const double* P, int where) {
     return fail(c, GRMHD_E_INVALID, "where must be GRMHD_HOST or GRMHD_DEVICE");
   }
   CK(c->L->load_prims(b.p, src, b.P, c->stream), "loading primitives");
-  CK(c->L->prim2con(b.p, b.P, b.U[0], c->stream), "prim->cons");
+  CK(c->L->prim2con(b.p, b.P, b.U[0], 0, b.p.isize, c->stream), "prim->cons");
   c->s0 = c->sc = 0;
   c->has_state = true;
   if (!c->block_scalar.empty()) c->block_scalar[block] = 0;

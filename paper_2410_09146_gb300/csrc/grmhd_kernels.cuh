@@ -1195,11 +1195,11 @@ static __global__ void k_batch_finalize_dt(const unsigned long long* ms, double*
   if (threadIdx.x == 0 && blockIdx.x == 0) *dt = cfl / __longlong_as_double((long long)ms[0]);
 }
 
-// Densitized conserved state of the interior from the primitives (set-up and checkpoint restore).
+// Densitized conserved state of interior cells t0 <= t < t1 from the primitives (set-up and checkpoint restore).
 template <int METRIC, class T>
-__global__ void k_prim2con(const T* __restrict__ P, double* __restrict__ U, DevParams p) {
+__global__ void k_prim2con(const T* __restrict__ P, double* __restrict__ U, DevParams p, long long t0, long long t1) {
   const long long n = p.isize, G = p.gsize;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+  for (long long t = t0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; t < t1; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % p.nx), j = (int)((t / p.nx) % p.ny), k = (int)(t / ((long long)p.nx * p.ny));
     const long long g = gidx(p, i, j, k);
     double Pc[NV];

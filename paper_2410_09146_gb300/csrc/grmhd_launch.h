@@ -19,7 +19,8 @@ struct FormLaunchers {
                         const StageArgs& a, cudaStream_t s);
   // the passes over the cells queued by update (floored cells; deferred con2prim in the mixed form)
   cudaError_t (*cell_passes)(const DevParams& p, void* P, const StageArgs& a, cudaStream_t s);
-  cudaError_t (*prim2con)(const DevParams& p, const void* P, double* U, cudaStream_t s);
+  // prim->cons of interior cells t0 <= t < t1
+  cudaError_t (*prim2con)(const DevParams& p, const void* P, double* U, long long t0, long long t1, cudaStream_t s);
   cudaError_t (*load_prims)(const DevParams& p, const double* src, void* P, cudaStream_t s);   // double -> storage
   cudaError_t (*store_prims)(const DevParams& p, const void* P, double* dst, cudaStream_t s);  // storage -> double
   // batched persistent kernels (many meshblocks, one launch per phase)

@@ -100,14 +100,15 @@ cudaError_t cell_passes(const DevParams& p, void* P, const StageArgs& a, cudaStr
   return cudaSuccess;
 }
 
-cudaError_t prim2con(const DevParams& p, const void* P, double* U, cudaStream_t s) {
-  const int g = grid_for(p.isize, 128);
+cudaError_t prim2con(const DevParams& p, const void* P, double* U, long long t0, long long t1, cudaStream_t s) {
+  if (t1 <= t0) return cudaSuccess;
+  const int g = grid_for(t1 - t0, 128);
   if (p.metric == KERR_SCHILD)
-    k_prim2con<KERR_SCHILD, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+    k_prim2con<KERR_SCHILD, T><<<g, 128, 0, s>>>((const T*)P, U, p, t0, t1);
   else if (p.metric == KERR_SCHILD_SPHERICAL)
-    k_prim2con<KERR_SCHILD_SPHERICAL, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+    k_prim2con<KERR_SCHILD_SPHERICAL, T><<<g, 128, 0, s>>>((const T*)P, U, p, t0, t1);
   else
-    k_prim2con<MINKOWSKI, T><<<g, 128, 0, s>>>((const T*)P, U, p);
+    k_prim2con<MINKOWSKI, T><<<g, 128, 0, s>>>((const T*)P, U, p, t0, t1);
   return cudaGetLastError();
 }
 

@@ -388,10 +388,12 @@ struct FaceSide {
   R U[NV], F[NV], lm, lp;
 };
 
-// smg: sqrt(-g) at the face (1 in the Cartesian metrics, where the flux needs no factor).
+// smg: sqrt(-g) at the face (1 in the Cartesian metrics, where the flux needs no factor). The double form;
+// float faces are formed two sides at a time by prim_to_face_x2.
 template <class R>
 __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, int d, R gamma_eos,
                                              FaceSide<R>& s, R smg = R(1)) {
+  static_assert(sizeof(R) == 8, "float face states are formed by prim_to_face_x2");
   const R rho = P[0], u = P[4];
   const R ut[3] = {P[1], P[2], P[3]};
   const R B[3] = {P[5], P[6], P[7]};
@@ -422,24 +424,10 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   const R D = rho * W;
   R Uc[NV];
   Uc[0] = D;
-  if constexpr (sizeof(R) == 4) {
-    // Float faces: S_j and tau in forms without cancellation. The printed forms
-    // S_j = (rho h + b^2) W^2 v_j - alpha b^0 b_j and tau = (rho h + b^2) W^2 - p* - (alpha b^0)^2 - D
-    // subtract terms of size W^2 (B.v)^2 (and rho W from rho h W^2), so their float rounding grows
-    // like W^2 in magnetised, relativistic cells. With b^2 W^2 = B^2 + (alpha b^0)^2 they are equal to
-    //   S_j = (rho h W^2 + B^2) v_j - (B.v) B_j,
-    //   tau = rho W u^2/(W + 1) + rho eps W^2 + p u^2 + B^2 - (B^2 + (alpha b^0)^2)/(2 W^2)   (u^2 = W^2 - 1),
-    // whose terms are all of the size of the result.
-    const R rhohW2 = rhoh * W * W;
+  const R wW2 = (rhoh + b2) * W * W;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Uc[1 + j] = (rhohW2 + B2) * vl[j] - Bv * Bl[j];
-    Uc[4] = fdiv(D * usq, W + R(1)) + u * W * W + pgas * usq + (B2 - R(0.5) * b2);
-  } else {
-    const R wW2 = (rhoh + b2) * W * W;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Uc[1 + j] = wW2 * vl[j] - ab0 * bl[j];
-    Uc[4] = wW2 - pstar - ab0 * ab0 - D;
-  }
+  for (int j = 0; j < 3; ++j) Uc[1 + j] = wW2 * vl[j] - ab0 * bl[j];
+  Uc[4] = wW2 - pstar - ab0 * ab0 - D;
 #pragma unroll
   for (int k = 0; k < 3; ++k) Uc[5 + k] = B[k];
   const R vtd = sel3(d, vt[0], vt[1], vt[2]) * ia;
@@ -472,6 +460,113 @@ __device__ __forceinline__ void prim_to_face(const R P[NV], const Metric<R>& m, 
   const R bd = sel3(d, m.beta[0], m.beta[1], m.beta[2]);
   s.lp = pre * (base + sq) - bd;
   s.lm = pre * (base - sq) - bd;
+}
+
+// Paired FP32 arithmetic: one f32x2 instruction applies the operation to both halves, each rounded as the
+// scalar instruction rounds it, in one issue slot.
+__device__ __forceinline__ float2 x2(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, x2(-1.f), a); }  // a - b, exact product
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
+__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ float2 dot2(const float2 a[3], const float2 b[3]) {
+  return fma2(a[2], b[2], fma2(a[1], b[1], mul2(a[0], b[0])));
+}
+
+// prim_to_face of both sides of a face at once, in float: the left state in the x halves of P and the right
+// state in the y halves; every add, multiply and fma is issued once for the two sides (f32x2), the square
+// roots and reciprocals per side. Outputs the densitized U and F^d of each side (F not yet times sqrt(-g))
+// and their characteristic speeds.
+// S_j and tau are taken in forms without cancellation. The printed forms
+// S_j = (rho h + b^2) W^2 v_j - alpha b^0 b_j and tau = (rho h + b^2) W^2 - p* - (alpha b^0)^2 - D subtract
+// terms of size W^2 (B.v)^2 (and rho W from rho h W^2), so their float rounding grows like W^2 in magnetised,
+// relativistic cells. With b^2 W^2 = B^2 + (alpha b^0)^2 they are equal to
+//   S_j = (rho h W^2 + B^2) v_j - (B.v) B_j,
+//   tau = rho W u^2/(W + 1) + rho eps W^2 + p u^2 + B^2 - (B^2 + (alpha b^0)^2)/(2 W^2)   (u^2 = W^2 - 1),
+// whose terms are all of the size of the result. The speeds use 1 - v^2 = 1/W^2 and
+// 1 - c^2 = (1 - vA^2)(1 - cs^2) (prim_to_face).
+__device__ __forceinline__ void prim_to_face_x2(const float2 P[NV], const Metric<float>& m, int d, float gamma_eos,
+                                                float2 U[NV], float2 F[NV], float2& lm, float2& lp) {
+  const float2 rho = P[0], u = P[4];
+  const float2 ut[3] = {P[1], P[2], P[3]};
+  const float2 B[3] = {P[5], P[6], P[7]};
+  const float2 g0 = x2(m.gam[0]), g1 = x2(m.gam[1]), g2 = x2(m.gam[2]), g3 = x2(m.gam[3]), g4 = x2(m.gam[4]),
+               g5 = x2(m.gam[5]);
+  float2 utl[3], Bl[3];
+  utl[0] = fma2(g2, ut[2], fma2(g1, ut[1], mul2(g0, ut[0])));
+  utl[1] = fma2(g4, ut[2], fma2(g3, ut[1], mul2(g1, ut[0])));
+  utl[2] = fma2(g5, ut[2], fma2(g4, ut[1], mul2(g2, ut[0])));
+  Bl[0] = fma2(g2, B[2], fma2(g1, B[1], mul2(g0, B[0])));
+  Bl[1] = fma2(g4, B[2], fma2(g3, B[1], mul2(g1, B[0])));
+  Bl[2] = fma2(g5, B[2], fma2(g4, B[1], mul2(g2, B[0])));
+  const float2 one = x2(1.f), neg = x2(-1.f);
+  const float2 usq = dot2(ut, utl);
+  const float2 W = sqrt2(add2(one, usq));
+  const float2 iW = rcp2(W);
+  const float ia = rcp(m.alpha);
+  const float2 al = x2(m.alpha);
+  float2 v[3], vl[3], vt[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    v[i] = mul2(ut[i], iW);
+    vl[i] = mul2(utl[i], iW);
+    vt[i] = fma2(al, v[i], x2(-m.beta[i]));
+  }
+  const float2 B2 = dot2(B, Bl);
+  const float2 Bv = dot2(B, vl);
+  const float2 ab0 = mul2(W, Bv);                              // alpha b^0
+  const float2 W2 = mul2(W, W);
+  const float2 b2 = mul2(mul2(fma2(ab0, ab0, B2), iW), iW);    // b^2
+  const float2 pgas = mul2(x2(gamma_eos - 1.f), u);
+  const float2 rhoh = add2(add2(rho, u), pgas);
+  const float2 pstar = fma2(x2(0.5f), b2, pgas);
+  const float2 D = mul2(rho, W);
+  float2 Uc[NV];
+  Uc[0] = D;
+  const float2 wB = fma2(rhoh, W2, B2);                        // rho h W^2 + B^2
+  const float2 nBv = mul2(Bv, neg);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Uc[1 + j] = fma2(wB, vl[j], mul2(nBv, Bl[j]));
+  Uc[4] = add2(mul2(mul2(D, usq), rcp2(add2(W, one))), fma2(u, W2, fma2(pgas, usq, fma2(x2(-0.5f), b2, B2))));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Uc[5 + k] = B[k];
+  const float2 vtd = mul2(sel3(d, vt[0], vt[1], vt[2]), x2(ia));
+  const float2 Bd = sel3(d, B[0], B[1], B[2]);
+  const float2 vd = sel3(d, v[0], v[1], v[2]);
+  const float2 nBdiW = mul2(mul2(Bd, iW), neg);                // -B^d / W
+  F[0] = mul2(D, vtd);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    // b_j = B_j / W + alpha b^0 v_j
+    const float2 bl = fma2(ab0, vl[j], mul2(Bl[j], iW));
+    F[1 + j] = fma2(Uc[1 + j], vtd, fma2(bl, nBdiW, j == d ? pstar : x2(0.f)));
+  }
+  F[4] = fma2(Uc[4], vtd, fma2(pstar, vd, mul2(ab0, nBdiW)));
+  const float2 nBdia = mul2(Bd, x2(-ia));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) F[5 + k] = fma2(B[k], vtd, mul2(nBdia, vt[k]));
+  const float2 sg = x2(m.sqrtgam);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) U[q] = mul2(sg, Uc[q]);
+  // Valencia characteristic speeds with the approximate fast speed c^2 = vA^2 + cs^2 (1 - vA^2)
+  const float2 irb = rcp2(add2(rhoh, b2));                     // 1 / (rho h + b^2)
+  const float2 cs2 = mul2(mul2(x2(gamma_eos), pgas), rcp2(rhoh));
+  const float2 va2 = mul2(b2, irb);
+  const float2 c2 = fma2(cs2, sub2(one, va2), va2);
+  const float2 one_v2 = rcp2(W2);
+  const float2 one_c2 = mul2(mul2(rhoh, irb), sub2(one, cs2));
+  const float2 one_v2c2 = fma2(c2, one_v2, one_c2);
+  float2 disc = mul2(one_v2, fma2(x2(sel3(d, m.gamu[0], m.gamu[3], m.gamu[5])), one_v2c2,
+                                  mul2(mul2(vd, vd), mul2(one_c2, neg))));
+  disc = make_float2(disc.x > 0.f ? disc.x : 0.f, disc.y > 0.f ? disc.y : 0.f);
+  const float2 pre = mul2(al, rcp2(one_v2c2));
+  const float2 sq = sqrt2(mul2(c2, disc));
+  const float2 base = mul2(vd, one_c2);
+  const float2 nbd = x2(-sel3(d, m.beta[0], m.beta[1], m.beta[2]));
+  lp = fma2(pre, add2(base, sq), nbd);
+  lm = fma2(pre, sub2(base, sq), nbd);
 }
 
 // Hydro part of the densitized conserved vector only (used after floors).
@@ -652,6 +747,68 @@ __device__ __forceinline__ void recon_cell(R f0, R f1, R f2, R f3, R f4, R eps, 
   }
 }
 
+// The MC slope of recon_cell from the paired differences dm, dp, their product and their mean c.
+__device__ __forceinline__ float mc_pick(float dm, float dp, float pr, float c) {
+  if (!(pr > 0.f)) return 0.f;
+  const float m = fminf(fminf(fabsf(dm + dm), fabsf(dp + dp)), fabsf(c));
+  return dm > 0.f ? m : -m;
+}
+
+// WENO5-Z-AOAH face values (recon_cell<float, RECON_WENO5Z>) of two variables at once, one in each half of
+// the float2 operands: the candidates, smoothness indicators, Z weights, the blend factor sigma and the
+// blend with the MC-limited linear values, every FP32 add, multiply and fma issued once for both
+// variables; the reciprocals and the limiter's compares stay per variable. The candidates are formed as
+// fmas with the coefficients divided by 6 and the weights applied before the sum, so the values agree with
+// recon_cell's float form to rounding (a few ulps), not bit for bit; the float cell-centric fluxes use this
+// form for every cell, so a cell's face values still do not depend on the run layout.
+__device__ __forceinline__ void recon_weno5z_x2(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4, float eps,
+                                                float2& qm, float2& qp) {
+  const float2 t3 = x2(1.f / 3.f), s6 = x2(-1.f / 6.f), f56 = x2(5.f / 6.f), e6 = x2(11.f / 6.f),
+               m76 = x2(-7.f / 6.f);
+  const float2 a11 = mul2(f2, e6), a5 = mul2(f2, f56), a3 = mul2(f2, t3);
+  const float2 P0 = fma2(f0, t3, fma2(f1, m76, a11));  // plus face: (2 f0 - 7 f1 + 11 f2) / 6
+  const float2 P1 = fma2(f1, s6, fma2(f3, t3, a5));    // (-f1 + 5 f2 + 2 f3) / 6
+  const float2 P2 = fma2(f4, s6, fma2(f3, f56, a3));   // (2 f2 + 5 f3 - f4) / 6
+  const float2 M0 = fma2(f4, t3, fma2(f3, m76, a11));  // minus face: the mirrored stencil
+  const float2 M1 = fma2(f3, s6, fma2(f1, t3, a5));
+  const float2 M2 = fma2(f0, s6, fma2(f1, f56, a3));
+  const float2 m2 = x2(-2.f), m4 = x2(-4.f), c3 = x2(3.f);
+  const float2 t0 = fma2(f1, m2, add2(f0, f2)), s0 = fma2(f1, m4, fma2(f2, c3, f0));
+  const float2 t1 = fma2(f2, m2, add2(f1, f3)), s1 = sub2(f1, f3);
+  const float2 t2 = fma2(f3, m2, add2(f2, f4)), s2 = fma2(f3, m4, fma2(f2, c3, f4));
+  const float2 k13 = x2(13.f / 12.f), k4 = x2(0.25f);
+  const float2 b0 = fma2(mul2(t0, k13), t0, mul2(mul2(s0, s0), k4));
+  const float2 b1 = fma2(mul2(t1, k13), t1, mul2(mul2(s1, s1), k4));
+  const float2 b2 = fma2(mul2(t2, k13), t2, mul2(mul2(s2, s2), k4));
+  const float2 db = sub2(b2, b0);
+  const float2 tau = make_float2(fabsf(db.x), fabsf(db.y));
+  const float2 e2 = x2(eps);
+  float2 q0 = mul2(tau, rcp2(add2(b0, e2))), q1 = mul2(tau, rcp2(add2(b1, e2))), q2 = mul2(tau, rcp2(add2(b2, e2)));
+  // q^2 kept inside the float range, as in recon_cell
+  q0 = make_float2(fminf(q0.x, 1e15f), fminf(q0.y, 1e15f));
+  q1 = make_float2(fminf(q1.x, 1e15f), fminf(q1.y, 1e15f));
+  q2 = make_float2(fminf(q2.x, 1e15f), fminf(q2.y, 1e15f));
+  const float2 one = x2(1.f);
+  const float2 z0 = fma2(q0, q0, one), z1 = fma2(q1, q1, one), z2 = fma2(q2, q2, one);
+  const float2 a0 = mul2(z0, x2(0.1f)), a1 = mul2(z1, x2(0.6f)), a2 = mul2(z2, x2(0.3f));  // plus side
+  const float2 c0 = mul2(z2, x2(0.1f)), c2 = mul2(z0, x2(0.3f));                           // minus side
+  const float2 is = rcp2(add2(add2(a0, a1), a2)), im = rcp2(add2(add2(c0, a1), c2));
+  const float2 P5p = fma2(mul2(a2, is), P2, fma2(mul2(a1, is), P1, mul2(mul2(a0, is), P0)));
+  const float2 P5m = fma2(mul2(c2, im), M2, fma2(mul2(a1, im), M1, mul2(mul2(c0, im), M0)));
+  // sigma = 15 / ((z0 + 3 z1 + z2) (1/z0 + 1/z1 + 1/z2)), at most 1
+  const float2 H = add2(add2(rcp2(z0), rcp2(z1)), rcp2(z2));
+  const float2 den = mul2(fma2(z1, c3, add2(z0, z2)), H);
+  float2 sg = mul2(x2(15.f), rcp2(den));
+  sg = make_float2(fminf(sg.x, 1.f), fminf(sg.y, 1.f));
+  const float2 dm = sub2(f2, f1), dp = sub2(f3, f2);
+  const float2 h = x2(0.5f), nh = x2(-0.5f);
+  const float2 pr = mul2(dm, dp), cs = mul2(h, add2(dm, dp));
+  const float2 s = make_float2(mc_pick(dm.x, dp.x, pr.x, cs.x), mc_pick(dm.y, dp.y, pr.y, cs.y));
+  const float2 om = sub2(one, sg);
+  qp = fma2(sg, P5p, mul2(om, fma2(s, h, f2)));
+  qm = fma2(sg, P5m, mul2(om, fma2(s, nh, f2)));
+}
+
 // ------------------------------------------------------------------ Riemann solvers (Sec. 3.1)
 template <class R>
 __device__ __forceinline__ R riemann_flux(int riemann, const FaceSide<R>& L, const FaceSide<R>& Rs, R Fh[NV]) {
@@ -670,6 +827,29 @@ __device__ __forceinline__ R riemann_flux(int riemann, const FaceSide<R>& L, con
       const R id = rcp(den);
 #pragma unroll
       for (int q = 0; q < NV; ++q) Fh[q] = (cr * L.F[q] - cl * Rs.F[q] + cr * cl * (Rs.U[q] - L.U[q])) * id;
+    }
+  }
+  return cmax;
+}
+
+// riemann_flux for the paired float sides of prim_to_face_x2 (left in the x halves, right in the y halves).
+__device__ __forceinline__ float riemann_flux_x2(int riemann, const float2 U[NV], const float2 F[NV], float2 lm,
+                                                 float2 lp, float Fh[NV]) {
+  const float cmax = fmaxf(fmaxf(fabsf(lm.x), fabsf(lp.x)), fmaxf(fabsf(lm.y), fabsf(lp.y)));
+  if (riemann == RIEMANN_LLF) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) Fh[q] = 0.5f * (F[q].x + F[q].y) - 0.5f * cmax * (U[q].y - U[q].x);
+  } else {
+    const float cl = fminf(0.f, fminf(lm.x, lm.y));
+    const float cr = fmaxf(0.f, fmaxf(lp.x, lp.y));
+    const float den = cr - cl;
+    if (den == 0.f) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Fh[q] = 0.5f * (F[q].x + F[q].y);
+    } else {
+      const float id = rcp(den);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Fh[q] = (cr * F[q].x - cl * F[q].y + cr * cl * (U[q].y - U[q].x)) * id;
     }
   }
   return cmax;

@@ -81,11 +81,24 @@ __device__ __forceinline__ R face_flux(const DevParams& p, int d, int i, int j, 
     else if (d == 1) { PL[6] = bn; PR[6] = bn; }
     else { PL[7] = bn; PR[7] = bn; }
   }
-  FaceSide<R> L, Rs;
   const R smg = METRIC == KERR_SCHILD_SPHERICAL ? m.alpha * m.sqrtgam : R(1);  // sqrt(-g) at the face
-  prim_to_face<R>(PL, m, d, par<R>(p.gamma_eos, p.fgamma), L, smg);
-  prim_to_face<R>(PR, m, d, par<R>(p.gamma_eos, p.fgamma), Rs, smg);
-  return riemann_flux<R>(p.riemann, L, Rs, Fh);
+  if constexpr (sizeof(R) == 4) {
+    // both sides at once in paired float arithmetic
+    float2 P2[NV], U2[NV], F2[NV], lm, lp;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) P2[q] = make_float2(PL[q], PR[q]);
+    prim_to_face_x2(P2, m, d, p.fgamma, U2, F2, lm, lp);
+    if constexpr (METRIC == KERR_SCHILD_SPHERICAL) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) F2[q] = mul2(F2[q], x2(smg));  // densitized flux sqrt(-g) F^d
+    }
+    return riemann_flux_x2(p.riemann, U2, F2, lm, lp, Fh);
+  } else {
+    FaceSide<R> L, Rs;
+    prim_to_face<R>(PL, m, d, p.gamma_eos, L, smg);
+    prim_to_face<R>(PR, m, d, p.gamma_eos, Rs, smg);
+    return riemann_flux<R>(p.riemann, L, Rs, Fh);
+  }
 }
 
 // a2 for face t of direction d: reconstruct the two cells beside the face, then face_flux. Writes F and
@@ -175,6 +188,50 @@ __global__ void __launch_bounds__(128) k_flux(const T* __restrict__ P, R* __rest
   if (track_speed) block_max_to<R>(cm_local, ms + d);
 }
 
+// Stencil rows ahead of the cell being reconstructed that the float y / z flux runs prefetch into L1: each
+// cell adds one row (its f + 2 neighbour) to the rows the cell before loaded, and that row is the one whose
+// load waits on L2.
+constexpr int kFluxPrefetch = 1;
+
+template <class T>
+__device__ __forceinline__ void prefetch_l1(const T* a) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+
+// Minus / plus face values of every variable of the cell at ghosted index g, its five-cell stencil along the
+// sweep at stride sd (zero when !live): the float WENO5-Z-AOAH form reconstructs the variables in pairs
+// (recon_weno5z_x2), the others one at a time (recon_cell).
+template <class R, class T, int RECON>
+__device__ __forceinline__ void recon_cell_all(const DevParams& p, const T* __restrict__ P, long long g,
+                                               long long sd, R eps, bool live, R qm[NV], R qp[NV]) {
+  const long long PN = NV * p.gsize;
+  if constexpr (sizeof(R) == 4 && RECON == RECON_WENO5Z) {
+#pragma unroll
+    for (int q = 0; q < NV; q += 2) {
+      float2 f[5];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        const long long c = q * p.gsize + g + (s - 2) * sd;
+        f[s] = live ? make_float2(float(LDC(P, c, PN)), float(LDC(P, c + p.gsize, PN))) : x2(0.f);
+      }
+      float2 m, pl;
+      recon_weno5z_x2(f[0], f[1], f[2], f[3], f[4], eps, m, pl);
+      qm[q] = m.x;
+      qm[q + 1] = m.y;
+      qp[q] = pl.x;
+      qp[q + 1] = pl.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      R f[5];
+#pragma unroll
+      for (int s = 0; s < 5; ++s) f[s] = live ? R(LDC(P, q * p.gsize + g + (s - 2) * sd, PN)) : R(0);
+      recon_cell<R, RECON>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
+    }
+  }
+}
+
 // Cell-centric fluxes of direction d = 1, 2 for WENO5-Z-AOAH, unit t of flux_units: one transverse
 // position and a run of flux_run_length faces along d. Each cell is reconstructed once (both of its faces),
 // and face f pairs the plus side of cell f - 1 with the minus side of cell f (face_flux, as in the
@@ -210,18 +267,17 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
   R PL[NV];
   R cm_run = R(0);
   for (int f = f0 - 1; f < f1; ++f) {
+    if constexpr (sizeof(R) == 4 && kFluxPrefetch > 0) {
+      // the row that cell f + kFluxPrefetch adds to its stencil, into L1 ahead of its use (when it is a cell
+      // of the ghosted block)
+      if (f + 2 + kFluxPrefetch < nd + p.ng) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) prefetch_l1(P + q * p.gsize + g + (2 + kFluxPrefetch) * sd);
+      }
+    }
     // stencil of cell f: cells f - 2 .. f + 2
     R PR[NV], QP[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const long long c0 = q * p.gsize + g;
-      R qm, qp;
-      recon_cell<R, RECON>(R(LDC(P, c0 - 2 * sd, NV * p.gsize)), R(LDC(P, c0 - sd, NV * p.gsize)),
-                           R(LDC(P, c0, NV * p.gsize)), R(LDC(P, c0 + sd, NV * p.gsize)),
-                           R(LDC(P, c0 + 2 * sd, NV * p.gsize)), eps, qm, qp);
-      PR[q] = qm;
-      QP[q] = qp;
-    }
+    recon_cell_all<R, T, RECON>(p, P, g, sd, eps, true, PR, QP);
     if (f >= f0) {  // face f: the plus side of cell f - 1 and the minus side of cell f
       R Fh[NV];
       const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
@@ -255,13 +311,7 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
   const R eps = par<R>(p.weno_eps, p.fweno_eps);
   const long long g = gidx(p, c, j, k);
   R qm[NV], qp[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) {
-    R f[5];
-#pragma unroll
-    for (int s = 0; s < 5; ++s) f[s] = live ? R(LDC(P, q * p.gsize + g + s - 2, NV * p.gsize)) : R(0);
-    recon_cell<R, RECON>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
-  }
+  recon_cell_all<R, T, RECON>(p, P, g, 1, eps, live, qm, qp);
   R PL[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) PL[q] = __shfl_up_sync(0xffffffffu, qp[q], 1);
@@ -273,11 +323,12 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
   return (j >= 0 && j < p.ny && k >= 0 && k < p.nz) ? cm : R(0);
 }
 
-// Resident CTAs per SM the float cell-centric flux kernels are compiled for: 8 x 128 threads at 64
-// registers, the best of the occupancy / spill trade-off measured at 256^3 (6 CTAs at 80 registers: the
-// same x time, y / z 1.15 ms against 1.13; the double form is bound by FP64 issue and keeps its registers).
+// Resident CTAs per SM the float cell-centric flux kernels are compiled for: 6 x 128 threads at 80
+// registers, the best of the occupancy / spill trade-off measured at 256^3 with the paired float arithmetic
+// (x / y / z 0.98 / 0.95 / 0.95 ms; 7 CTAs at 72 registers 1.00 / 0.96 / 0.96, 8 at 64 1.02 / 0.98 / 0.98);
+// the double form is bound by FP64 issue and keeps its registers.
 template <class R>
-constexpr int kFluxMinBlocks = sizeof(R) == 4 ? 8 : 1;
+constexpr int kFluxMinBlocks = sizeof(R) == 4 ? 6 : 1;
 
 template <class R, class T, int METRIC, int RECON>
 __global__ void __launch_bounds__(128, kFluxMinBlocks<R>) k_flux_cc(const T* __restrict__ P, R* __restrict__ F,

@@ -26,7 +26,9 @@ def lib():
         pytest.skip("nvcc not available")
     d = tempfile.mkdtemp(prefix="mesh_tables_")
     so = os.path.join(d, "libmt.so")
-    subprocess.run([nvcc, "-std=c++17", "-O1", "-Xcompiler", "-fPIC", "-shared", "-o", so,
+    # the library's device headers are written for sm_103a (paired FP32 instructions), so the shim is too
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O1", "-Xcompiler", "-fPIC",
+                    "-shared", "-o", so,
                     os.path.join(HERE, "mesh_tables_shim.cu")], check=True, capture_output=True)
     L = ctypes.CDLL(so)
     L.mt_build.restype = ctypes.c_int

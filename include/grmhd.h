@@ -197,6 +197,24 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt);
 /* One SSP-RK2 (Heun) step: stages (0, 1, 1) and (1/2, 1/2, 1/2) with the same dt (dt <= 0: CFL). */
 int grmhd_rk2_step(grmhd_ctx* c, double dt);
 
+/* One stage from host primitives to host primitives, for single-block GRMHD_MIXED contexts (float primitives,
+ * the layout of grmhd_set_prims_f32: float [8][nz+2ng][ny+2ng][nx+2ng], host memory, page-locked for the
+ * copies to overlap). Equivalent to
+ *   grmhd_set_prims_f32(c, P_in, GRMHD_HOST)                  (skipped when P_in is NULL)
+ *   grmhd_stage(c, g0, g1, beta, dt)
+ *   grmhd_get(c, GRMHD_GET_PRIMS_F32, P_out, GRMHD_HOST)      (skipped when P_out is NULL)
+ * with the same results bit for bit, but the read-back overlaps the stage: the update and its passes over
+ * deferred cells run in 8 slabs of interior z rows, and each slab's ghosted rows of P are copied to P_out
+ * while the next slab is updated (as the load overlaps its copies with the prim -> cons). P_in given: the
+ * stage starts a step (g0 == 0) and, for face-centred CT, needs grmhd_set_face_b, as after any load; P_in
+ * NULL: the stage continues from the context's state (e.g. the second stage of an RK2 step). Returns when
+ * P_out holds the stage's primitives (the device work that follows them, a passive scalar's update, may still
+ * run). The caller owns both buffers; P_out must not overlap P_in. With timing on, the slabs' updates and
+ * passes are counted together in the update group. Errors: GRMHD_E_INVALID (no single-block grid, not a
+ * GRMHD_MIXED context, the errors of the three calls above), GRMHD_E_CUDA. */
+int grmhd_stage_host_f32(grmhd_ctx* c, const float* P_in, float* P_out, double g0, double g1, double beta,
+                         double dt);
+
 /* Con2prim of a flat-space batch (a6 on its own; Sec. 3.1, the Kastaun et al. solve, and the Sec. 3.2
  * floors in their Minkowski form): U and P are device arrays [8][n] (structure of arrays) of densitized
  * conserved / primitive variables; status (uint8 [n]) and iters (int [n]) may be NULL. flags bit 0: P holds

@@ -50,6 +50,10 @@ struct grmhd_ctx {
   // on the first such load), so the two overlap; load_ev[k] marks chunk k's copies, load_ev[kLoadChunks] the end
   cudaStream_t load_stream;
   cudaEvent_t load_ev[kLoadChunks + 1];
+  // host reads overlapped with a stage (grmhd_stage_host_f32): out_ev[k] marks slab k's update on `stream`, whose
+  // rows are then copied on load_stream; out_ev[kLoadChunks] the end of the copies
+  cudaEvent_t out_ev[kLoadChunks + 1];
+  bool out_ev_made;
   bool timing;               // record CUDA events around each kernel group
   cudaEvent_t ev[8];         // ghost | flux x | flux y | flux z | emf | update | cell passes | end
   double t_ms[7];            // accumulated ms per kernel group since the last read
@@ -537,6 +541,15 @@ int grmhd_set_face_b(grmhd_ctx* c, const double* Bf, int where) {
   return GRMHD_OK;
 }
 
+// The loading stream and its events, made on first use.
+static cudaError_t ensure_load_stream(grmhd_ctx* c) {
+  if (c->load_stream) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->load_stream, cudaStreamNonBlocking);
+  for (cudaEvent_t& ev : c->load_ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  return e;
+}
+
 int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) {
   if (!c || !P) return c ? fail(c, GRMHD_E_INVALID, "P is NULL") : GRMHD_E_INVALID;
   if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
@@ -553,10 +566,7 @@ int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) {
     // have landed, beside the next slab's copies (a 256^3 load: 0.6 GB at ~210 GB/s, 2.8 ms, against 2.9 ms
     // of double-precision prim->cons). The call returns once the host P has been read; the context's stream
     // waits for the last prim->cons.
-    if (!c->load_stream) {
-      CK(cudaStreamCreateWithFlags(&c->load_stream, cudaStreamNonBlocking), "creating the loading stream");
-      for (cudaEvent_t& e : c->load_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "creating an event");
-    }
+    CK(ensure_load_stream(c), "creating the loading stream");
     const long long row = (long long)c->dp.gx * c->dp.gy, G = c->dp.gsize, plane = (long long)c->dp.nx * c->dp.ny;
     const int gz = c->dp.gz, ng = c->dp.ng, nz = c->dp.nz;
     const int nch = gz < kLoadChunks ? gz : kLoadChunks;
@@ -650,7 +660,9 @@ int grmhd_c2p_guess(grmhd_ctx* c, const void* mlp_ws, long long n, const double*
 
 static int grmhd_get_scalars(grmhd_ctx* c, int what, void* dst, int where);
 
-int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
+// One stage of a context (grmhd_stage); host_out != NULL (float primitives, single-block contexts): the stage's
+// primitives are also copied to host_out, overlapped with the update (grmhd_stage_host_f32).
+static int stage_impl(grmhd_ctx* c, double g0, double g1, double beta, double dt, float* host_out) {
   if (!c) return GRMHD_E_INVALID;
   if (c->nblocks > 0) return batch_stage(c, g0, g1, beta, dt);
   if (batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no grid");
@@ -726,9 +738,42 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
     CK(L.emf(dp, c->F[0], c->F[1], c->F[2], c->E, s), "EMF");
   }
   TMARK(5);
-  CK(L.update(dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
-  TMARK(6);
-  CK(L.cell_passes(dp, c->P, a, s), "floored and deferred cells");
+  if (!host_out) {
+    CK(L.update(dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
+    TMARK(6);
+    CK(L.cell_passes(dp, c->P, a, s), "floored and deferred cells");
+  } else {
+    // In kLoadChunks slabs of interior z rows: a slab's update and its passes over deferred cells on the
+    // context's stream, then the copy of its ghosted rows of P to the host on the loading stream, beside the
+    // next slab's update (a 256^3 read-back: 0.6 GB at ~190 GB/s, 3.1 ms, against ~6 ms of update). A cell's
+    // update and passes read and write only its own primitives, so the slabs' rows are final when copied.
+    CK(ensure_load_stream(c), "creating the loading stream");
+    if (!c->out_ev_made) {
+      for (cudaEvent_t& e : c->out_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "creating an event");
+      c->out_ev_made = true;
+    }
+    const long long plane = (long long)dp.nx * dp.ny, row = (long long)dp.gx * dp.gy, G = dp.gsize;
+    const int nz = dp.nz, ng = dp.ng, gz = dp.gz;
+    const int nch = nz < kLoadChunks ? nz : kLoadChunks;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int k0 = (int)((long long)nz * ch / nch), k1 = (int)((long long)nz * (ch + 1) / nch);
+      if (ch > 0 && c->worklist)
+        CK(cudaMemsetAsync(c->scal + 16, 0, 2 * sizeof(unsigned long long), s), "clearing the list counts");
+      a.t_begin = k0 * plane;
+      a.t_end = k1 * plane;
+      CK(L.update(dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
+      CK(L.cell_passes(dp, c->P, a, s), "floored and deferred cells");
+      CK(cudaEventRecord(c->out_ev[ch], s), "recording a read-back event");
+      CK(cudaStreamWaitEvent(c->load_stream, c->out_ev[ch], 0), "ordering the loading stream");
+      const int r0 = ch == 0 ? 0 : k0 + ng, r1 = ch == nch - 1 ? gz : k1 + ng;  // ghosted z rows of the slab
+      for (int q = 0; q < NV; ++q)
+        CK(cudaMemcpyAsync(host_out + q * G + r0 * row, (const float*)c->P + q * G + r0 * row,
+                           sizeof(float) * (r1 - r0) * row, cudaMemcpyDeviceToHost, c->load_stream),
+           "copying P to the host");
+    }
+    a.t_begin = a.t_end = 0;
+    TMARK(6);  // the timing groups count these updates and passes together as the update
+  }
   if (c->prm.scalar) {
     // the passive scalar: X of the stage's start, the stage's mass fluxes, its final D
     if (c->prm.bc == GRMHD_BC_PERIODIC) CK(L.scalar_ghost(dp, c->X, s), "scalar ghost fill");
@@ -740,7 +785,29 @@ int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
 #undef TMARK
   if (c->timing) c->t_pending = true;
   c->sc = dst;
+  if (host_out) {
+    // later work on the context's stream (a load into P) waits for the copies; the call returns once they are done
+    CK(cudaEventRecord(c->out_ev[kLoadChunks], c->load_stream), "recording a read-back event");
+    CK(cudaStreamWaitEvent(s, c->out_ev[kLoadChunks], 0), "ordering the context's stream");
+    CK(cudaEventSynchronize(c->out_ev[kLoadChunks]), "synchronising");
+  }
   return GRMHD_OK;
+}
+
+int grmhd_stage(grmhd_ctx* c, double g0, double g1, double beta, double dt) {
+  return stage_impl(c, g0, g1, beta, dt, nullptr);
+}
+
+int grmhd_stage_host_f32(grmhd_ctx* c, const float* P_in, float* P_out, double g0, double g1, double beta,
+                         double dt) {
+  if (!c) return GRMHD_E_INVALID;
+  if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
+  if (c->L->p_bytes != 4) return fail(c, GRMHD_E_INVALID, "single-precision primitives need a GRMHD_MIXED context");
+  if (P_in) {
+    const int r = grmhd_set_prims_f32(c, P_in, GRMHD_HOST);
+    if (r != GRMHD_OK) return r;
+  }
+  return stage_impl(c, g0, g1, beta, dt, P_out);
 }
 
 int grmhd_rk2_step(grmhd_ctx* c, double dt) {
@@ -985,6 +1052,8 @@ const char* grmhd_last_error(const grmhd_ctx* c) { return c ? c->err : g_create_
 void grmhd_destroy(grmhd_ctx* c) {
   if (c && c->timing)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(c->ev[k]);
+  if (c && c->out_ev_made)
+    for (cudaEvent_t e : c->out_ev) cudaEventDestroy(e);
   if (c && c->load_stream) {
     for (cudaEvent_t e : c->load_ev) cudaEventDestroy(e);
     cudaStreamDestroy(c->load_stream);

@@ -128,6 +128,7 @@ struct StageArgs {
   const double* bface_new;       // face-centred CT: the advanced faces [3][gsize]; NULL: flux-CT
   int* solvelist;                // mixed form: worklist cells whose resumed double step did not settle, for
   unsigned int* sl_count;        // the full double iteration in a last pass (NULL: inline); its count
+  long long t_begin, t_end;      // single-block update: interior cells [t_begin, t_end) (t_end = 0: all)
 };
 
 

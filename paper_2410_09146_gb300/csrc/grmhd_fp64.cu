@@ -70,7 +70,7 @@ cudaError_t emf(const DevParams& p, const void* Fx, const void* Fy, const void* 
 
 cudaError_t update(const DevParams& p, void* P, const void* Fx, const void* Fy, const void* Fz, const void* E,
                    const StageArgs& a, cudaStream_t s) {
-  const int g = grid_for(p.isize, 128);
+  const int g = grid_for((a.t_end > 0 ? a.t_end : p.isize) - a.t_begin, 128);
   if (p.metric == KERR_SCHILD)
     k_update<KERR_SCHILD, R, T><<<g, 128, 0, s>>>((T*)P, (const R*)Fx, (const R*)Fy, (const R*)Fz, (const R*)E, a, p);
   else if (p.metric == KERR_SCHILD_SPHERICAL)

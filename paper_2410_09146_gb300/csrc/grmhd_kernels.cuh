@@ -199,11 +199,11 @@ __device__ __forceinline__ void prefetch_l1(const T* a) {
 }
 
 // Minus / plus face values of every variable of the cell at ghosted index g, its five-cell stencil along the
-// sweep at stride sd (zero when !live): the float WENO5-Z-AOAH form reconstructs the variables in pairs
-// (recon_weno5z_x2), the others one at a time (recon_cell).
+// sweep at stride sd (every stencil cell inside the ghosted block): the float WENO5-Z-AOAH form reconstructs
+// the variables in pairs (recon_weno5z_x2), the others one at a time (recon_cell).
 template <class R, class T, int RECON>
 __device__ __forceinline__ void recon_cell_all(const DevParams& p, const T* __restrict__ P, long long g,
-                                               long long sd, R eps, bool live, R qm[NV], R qp[NV]) {
+                                               long long sd, R eps, R qm[NV], R qp[NV]) {
   const long long PN = NV * p.gsize;
   if constexpr (sizeof(R) == 4 && RECON == RECON_WENO5Z) {
 #pragma unroll
@@ -212,7 +212,7 @@ __device__ __forceinline__ void recon_cell_all(const DevParams& p, const T* __re
 #pragma unroll
       for (int s = 0; s < 5; ++s) {
         const long long c = q * p.gsize + g + (s - 2) * sd;
-        f[s] = live ? make_float2(float(LDC(P, c, PN)), float(LDC(P, c + p.gsize, PN))) : x2(0.f);
+        f[s] = make_float2(float(LDC(P, c, PN)), float(LDC(P, c + p.gsize, PN)));
       }
       float2 m, pl;
       recon_weno5z_x2(f[0], f[1], f[2], f[3], f[4], eps, m, pl);
@@ -226,7 +226,7 @@ __device__ __forceinline__ void recon_cell_all(const DevParams& p, const T* __re
     for (int q = 0; q < NV; ++q) {
       R f[5];
 #pragma unroll
-      for (int s = 0; s < 5; ++s) f[s] = live ? R(LDC(P, q * p.gsize + g + (s - 2) * sd, PN)) : R(0);
+      for (int s = 0; s < 5; ++s) f[s] = R(LDC(P, q * p.gsize + g + (s - 2) * sd, PN));
       recon_cell<R, RECON>(f[0], f[1], f[2], f[3], f[4], eps, qm[q], qp[q]);
     }
   }
@@ -277,7 +277,7 @@ __device__ __forceinline__ R flux_run(const DevParams& p, const T* __restrict__ 
     }
     // stencil of cell f: cells f - 2 .. f + 2
     R PR[NV], QP[NV];
-    recon_cell_all<R, T, RECON>(p, P, g, sd, eps, true, PR, QP);
+    recon_cell_all<R, T, RECON>(p, P, g, sd, eps, PR, QP);
     if (f >= f0) {  // face f: the plus side of cell f - 1 and the minus side of cell f
       R Fh[NV];
       const R cm = face_flux<R, METRIC>(p, d, i, j, k, PL, PR, Fh);
@@ -311,7 +311,9 @@ __device__ __forceinline__ R flux_lane(const DevParams& p, const T* __restrict__
   const R eps = par<R>(p.weno_eps, p.fweno_eps);
   const long long g = gidx(p, c, j, k);
   R qm[NV], qp[NV];
-  recon_cell_all<R, T, RECON>(p, P, g, 1, eps, live, qm, qp);
+  // a lane past either end of the sequence (!live) reconstructs cell (0, -1, -1), inside the ghosted block; its
+  // values reach no face
+  recon_cell_all<R, T, RECON>(p, P, g, 1, eps, qm, qp);
   R PL[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) PL[q] = __shfl_up_sync(0xffffffffu, qp[q], 1);
@@ -967,7 +969,9 @@ __global__ void __launch_bounds__(128, kUpdateMinBlocks<T>) k_update(T* __restri
                                                 const R* __restrict__ E, StageArgs a, DevParams p) {
   const double dt = a.use_dev_dt ? *a.dt_dev : a.dt;
   CellStats cs;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.isize; t += (long long)gridDim.x * blockDim.x)
+  const long long t1 = a.t_end > 0 ? a.t_end : p.isize;
+  for (long long t = a.t_begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; t < t1;
+       t += (long long)gridDim.x * blockDim.x)
     update_cell<METRIC, R, T>(p, P, Fx, Fy, Fz, E, a, dt, t, 0, cs);
   cs.flush(a.stats);
 }
@@ -1057,7 +1061,8 @@ __global__ void __launch_bounds__(128) k_update_deferred(T* __restrict__ P, Stag
       deferred_cell<METRIC, T>(p, P, a, LDC(a.worklist, w, p.isize), LDC(a.wl_mu, w, p.isize), false, 0, cs);
   }
   cs.flush(a.stats);
-  if (!full && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
+  // deferred cells of the stage (summed over the slabs of an update run in z slabs)
+  if (!full && a.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.stats + 7, (unsigned long long)cnt);
 }
 
 // ------------------------------------------------------------------ batched (many meshblocks)
@@ -1222,7 +1227,8 @@ __global__ void __launch_bounds__(128) k_batch_deferred(const BlockDesc* __restr
                              b.cell_offset, cs);
   }
   cs.flush(a.stats);
-  if (!full && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[7] = cnt;
+  // deferred cells of the stage
+  if (!full && a.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.stats + 7, (unsigned long long)cnt);
 }
 
 template <int METRIC, class T>

@@ -85,6 +85,8 @@ def lib():
         L.grmhd_batch_set_scalar.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_stage.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.grmhd_rk2_step.argtypes = [vp, ctypes.c_double]
+        L.grmhd_stage_host_f32.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double]
         L.grmhd_c2p.argtypes = [vp, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int]
         L.grmhd_get.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
         L.grmhd_set_timing.argtypes = [vp, ctypes.c_int]
@@ -209,6 +211,21 @@ def grmhd_stage(ctx: int, g0: float, g1: float, beta: float, dt: float) -> None:
 
 def grmhd_rk2_step(ctx: int, dt: float) -> None:
     _check(lib().grmhd_rk2_step(ctx, dt), ctx)
+
+
+def grmhd_stage_host_f32(ctx: int, P_in, P_out, g0: float, g1: float, beta: float, dt: float) -> None:
+    """One stage from host float primitives P_in (None: continue from the context's state) to host float
+    primitives P_out (None: no read-back), the read-back overlapped with the stage (C ABI grmhd_stage_host_f32).
+    P_in / P_out: CPU tensors or arrays of float32 in the layout of grmhd_set_prims_f32."""
+    def host_ptr(a):
+        if a is None:
+            return None
+        ptr, where = _ptr(a)
+        if where != GRMHD_HOST or "float32" not in str(a.dtype):
+            raise GrmhdError("grmhd_stage_host_f32 takes float32 host buffers")
+        return ptr
+    _check(lib().grmhd_stage_host_f32(ctx, ctypes.c_void_p(host_ptr(P_in)), ctypes.c_void_p(host_ptr(P_out)), g0,
+                                      g1, beta, dt), ctx)
 
 
 def grmhd_c2p(ctx: int, n: int, U_ptr: int, P_ptr: int, status_ptr: int = 0, iters_ptr: int = 0,

@@ -203,9 +203,11 @@ int grmhd_rk2_step(grmhd_ctx* c, double dt);
  *   grmhd_set_prims_f32(c, P_in, GRMHD_HOST)                  (skipped when P_in is NULL)
  *   grmhd_stage(c, g0, g1, beta, dt)
  *   grmhd_get(c, GRMHD_GET_PRIMS_F32, P_out, GRMHD_HOST)      (skipped when P_out is NULL)
- * with the same results bit for bit, but the read-back overlaps the stage: the update and its passes over
- * deferred cells run in 8 slabs of interior z rows, and each slab's ghosted rows of P are copied to P_out
- * while the next slab is updated (as the load overlaps its copies with the prim -> cons). P_in given: the
+ * with the same results bit for bit, but the copies overlap the device work: the load's copies run beside its
+ * prim -> cons (as in grmhd_set_prims_f32), whose last part runs beside the stage's ghost fill and fluxes
+ * (which read only P; the update waits for it), and the update and its passes over deferred cells run in 8
+ * slabs of interior z rows, each slab's ghosted rows of P copied to P_out while the next slab is updated.
+ * P_in is read and P_out written when the call returns, also when it fails. P_in given: the
  * stage starts a step (g0 == 0) and, for face-centred CT, needs grmhd_set_face_b, as after any load; P_in
  * NULL: the stage continues from the context's state (e.g. the second stage of an RK2 step). Returns when
  * P_out holds the stage's primitives (the device work that follows them, a passive scalar's update, may still

@@ -54,6 +54,7 @@ struct grmhd_ctx {
   // rows are then copied on load_stream; out_ev[kLoadChunks] the end of the copies
   cudaEvent_t out_ev[kLoadChunks + 1];
   bool out_ev_made;
+  int load_last;             // load_ev index of the last host load's last copies
   bool timing;               // record CUDA events around each kernel group
   cudaEvent_t ev[8];         // ghost | flux x | flux y | flux z | emf | update | cell passes | end
   double t_ms[7];            // accumulated ms per kernel group since the last read
@@ -550,7 +551,14 @@ static cudaError_t ensure_load_stream(grmhd_ctx* c) {
   return e;
 }
 
-int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) {
+// grmhd_set_prims_f32; join = false (host loads inside grmhd_stage_host_f32): the context's stream does not wait
+// for the prim->cons and the call does not wait for the copies; the stage that follows joins the prim->cons
+// before its update (load_ev[kLoadChunks]) and the caller waits for the copies (load_ev[last chunk]).
+static int set_prims_f32(grmhd_ctx* c, const float* P, int where, bool join);
+
+int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) { return set_prims_f32(c, P, where, true); }
+
+static int set_prims_f32(grmhd_ctx* c, const float* P, int where, bool join) {
   if (!c || !P) return c ? fail(c, GRMHD_E_INVALID, "P is NULL") : GRMHD_E_INVALID;
   if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
   if (c->L->p_bytes != 4) return fail(c, GRMHD_E_INVALID, "single-precision primitives need a GRMHD_MIXED context");
@@ -584,8 +592,11 @@ int grmhd_set_prims_f32(grmhd_ctx* c, const float* P, int where) {
       r0 = r1;
     }
     CK(cudaEventRecord(c->load_ev[kLoadChunks], c->load_stream), "recording a load event");
-    CK(cudaStreamWaitEvent(c->stream, c->load_ev[kLoadChunks], 0), "ordering the context's stream");
-    CK(cudaEventSynchronize(c->load_ev[nch - 1]), "synchronising");  // the host P has been read
+    c->load_last = nch - 1;
+    if (join) {
+      CK(cudaStreamWaitEvent(c->stream, c->load_ev[kLoadChunks], 0), "ordering the context's stream");
+      CK(cudaEventSynchronize(c->load_ev[nch - 1]), "synchronising");  // the host P has been read
+    }
   }
   c->has_state = true;
   c->has_faces = false;
@@ -661,8 +672,11 @@ int grmhd_c2p_guess(grmhd_ctx* c, const void* mlp_ws, long long n, const double*
 static int grmhd_get_scalars(grmhd_ctx* c, int what, void* dst, int where);
 
 // One stage of a context (grmhd_stage); host_out != NULL (float primitives, single-block contexts): the stage's
-// primitives are also copied to host_out, overlapped with the update (grmhd_stage_host_f32).
-static int stage_impl(grmhd_ctx* c, double g0, double g1, double beta, double dt, float* host_out) {
+// primitives are also copied to host_out, overlapped with the update (grmhd_stage_host_f32); join_load: a host
+// load without join precedes (its prim->cons, on the loading stream, may run beside the ghost fill and fluxes,
+// which read only P; the update waits for it).
+static int stage_impl(grmhd_ctx* c, double g0, double g1, double beta, double dt, float* host_out,
+                      bool join_load = false) {
   if (!c) return GRMHD_E_INVALID;
   if (c->nblocks > 0) return batch_stage(c, g0, g1, beta, dt);
   if (batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no grid");
@@ -737,6 +751,7 @@ static int stage_impl(grmhd_ctx* c, double g0, double g1, double beta, double dt
   } else {
     CK(L.emf(dp, c->F[0], c->F[1], c->F[2], c->E, s), "EMF");
   }
+  if (join_load) CK(cudaStreamWaitEvent(s, c->load_ev[kLoadChunks], 0), "joining the load's prim->cons");
   TMARK(5);
   if (!host_out) {
     CK(L.update(dp, c->P, c->F[0], c->F[1], c->F[2], c->E, a, s), "update");
@@ -804,10 +819,17 @@ int grmhd_stage_host_f32(grmhd_ctx* c, const float* P_in, float* P_out, double g
   if (c->nblocks > 0 || batch_only(c)) return fail(c, GRMHD_E_INVALID, "context has no single-block grid");
   if (c->L->p_bytes != 4) return fail(c, GRMHD_E_INVALID, "single-precision primitives need a GRMHD_MIXED context");
   if (P_in) {
-    const int r = grmhd_set_prims_f32(c, P_in, GRMHD_HOST);
+    const int r = set_prims_f32(c, P_in, GRMHD_HOST, false);
     if (r != GRMHD_OK) return r;
   }
-  return stage_impl(c, g0, g1, beta, dt, P_out);
+  const int r = stage_impl(c, g0, g1, beta, dt, P_out, P_in != nullptr);
+  if (P_in) {
+    // P_in has been read when the call returns, whatever the stage did
+    if (r != GRMHD_OK) cudaStreamWaitEvent(c->stream, c->load_ev[kLoadChunks], 0);
+    const cudaError_t e = cudaEventSynchronize(c->load_ev[c->load_last]);
+    if (r == GRMHD_OK && e != cudaSuccess) return fail(c, GRMHD_E_CUDA, "synchronising", e);
+  }
+  return r;
 }
 
 int grmhd_rk2_step(grmhd_ctx* c, double dt) {
